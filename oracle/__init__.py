@@ -1,0 +1,253 @@
+"""FP64 CPU oracle for the OD2P ptychography iteration (arXiv:2011.00162).
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  It wraps the
+plain-C double-precision library built from the ``*.c`` files next to this
+file; the wrapper only marshals arrays.  It shares no code with the CUDA
+library of ``paper_2011_00162_gb300``.
+
+Every array crossing into C is converted to contiguous complex128 / float64 /
+int32 first.  The functions follow the paper:
+
+* :func:`fft2`, :func:`dft2`      -- the unitary DFT F (section 2);
+* :func:`stagm_g`, :func:`stagm_grad`, :func:`stagm_prox` -- ST-AGM, its
+  gradient and proximal map (section 2.2, eqs. obj-1, objgrad, Prox_sol);
+* :func:`forward`, :func:`adjoint` -- A and A^* (section 2);
+* :func:`loss_grad`               -- the ST-AGM data-fidelity loss and gradients;
+* :func:`geometry`, :func:`pairs` -- the overlapping decomposition (sections 2.1, 3.1);
+* :class:`ADMM`                   -- Algorithm 2 (nonblind) and Algorithm 3 (blind).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["fft.c", "stagm.c", "operator.c", "geometry.c", "admm.c"]
+_LIBNAME = "liboracle.so"
+_lock = threading.Lock()
+_lib = None
+
+U, GAMMA, LAMBDA, WD, DELTA, W, V, Z = range(8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no fast-math) into oracle/liboracle.so."""
+    out = os.path.join(_HERE, _LIBNAME)
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    hdr = os.path.join(_HERE, "od2p_oracle.h")
+    if not force and os.path.exists(out):
+        newest = max(os.path.getmtime(p) for p in srcs + [hdr])
+        if os.path.getmtime(out) >= newest:
+            return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, out)
+    return out
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "orc_dft2": (None, [P, i32, i32]),
+            "orc_fft2": (None, [P, i32, i32]),
+            "orc_stagm_g_arr": (None, [P, P, i64, f64, P]),
+            "orc_stagm_grad_arr": (None, [P, P, i64, f64, P]),
+            "orc_stagm_prox_arr": (None, [P, P, i64, f64, f64, P]),
+            "orc_forward": (None, [i32, i32, P, i32, P, i32, P, P]),
+            "orc_adjoint": (None, [i32, i32, i32, P, i32, P, P, P]),
+            "orc_loss_grad": (f64, [i32, i32, P, i32, P, i32, P, P, f64, P, P]),
+            "orc_geometry": (i32, [i32, i32, i32, i32, P, i32, i32, i32, P, P]),
+            "orc_pairs": (i32, [i32, P, i32, P, P]),
+            "orc_admm_new": (P, [i32, i32, i32, i32, P, i32, i32, i32, P, P, P, f64, f64, f64,
+                                 i32, f64, f64, P]),
+            "orc_admm_free": (None, [P]),
+            "orc_admm_iterate": (None, [P, i32]),
+            "orc_admm_num_sub": (i32, [P]),
+            "orc_admm_num_pairs": (i32, [P]),
+            "orc_admm_state_len": (i64, [P, i32]),
+            "orc_admm_get": (None, [P, i32, P]),
+            "orc_admm_set": (None, [P, i32, P]),
+            "orc_admm_metrics": (None, [P, P, P]),
+            "orc_admm_merge": (None, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def dft2(x, inverse: bool = False) -> np.ndarray:
+    """Unitary 2-D DFT written out from its definition (O(m^4))."""
+    x = _c(x, np.complex128).copy()
+    _load().orc_dft2(_p(x), x.shape[-1], int(inverse))
+    return x
+
+
+def fft2(x, inverse: bool = False) -> np.ndarray:
+    """Unitary 2-D radix-2 FFT of one m x m frame (m a power of two)."""
+    x = _c(x, np.complex128).copy()
+    _load().orc_fft2(_p(x), x.shape[-1], int(inverse))
+    return x
+
+
+def stagm_g(x, b, eps: float) -> np.ndarray:
+    x = _c(x, np.complex128)
+    b = _c(np.broadcast_to(b, x.shape), np.float64)
+    out = np.empty(x.shape, np.float64)
+    _load().orc_stagm_g_arr(_p(x), _p(b), x.size, eps, _p(out))
+    return out
+
+
+def stagm_grad(x, b, eps: float) -> np.ndarray:
+    x = _c(x, np.complex128)
+    b = _c(np.broadcast_to(b, x.shape), np.float64)
+    out = np.empty(x.shape, np.complex128)
+    _load().orc_stagm_grad_arr(_p(x), _p(b), x.size, eps, _p(out))
+    return out
+
+
+def stagm_prox(y, f, eps: float, lam: float) -> np.ndarray:
+    y = _c(y, np.complex128)
+    f = _c(np.broadcast_to(f, y.shape), np.float64)
+    out = np.empty(y.shape, np.complex128)
+    _load().orc_stagm_prox_arr(_p(y), _p(f), y.size, eps, lam, _p(out))
+    return out
+
+
+def forward(u, w, offs) -> np.ndarray:
+    """All frames F(w o S_j u), shape (J, m, m)."""
+    u = _c(u, np.complex128)
+    w = _c(w, np.complex128)
+    offs = _c(offs, np.int32).reshape(-1, 2)
+    H, W = u.shape
+    m = w.shape[0]
+    out = np.empty((offs.shape[0], m, m), np.complex128)
+    _load().orc_forward(H, W, _p(u), m, _p(w), offs.shape[0], _p(offs), _p(out))
+    return out
+
+
+def adjoint(y, w, offs, H: int, W: int) -> np.ndarray:
+    """A^* y = sum_j S_j^T (conj(w) o F^* y_j), shape (H, W)."""
+    y = _c(y, np.complex128)
+    w = _c(w, np.complex128)
+    offs = _c(offs, np.int32).reshape(-1, 2)
+    out = np.empty((H, W), np.complex128)
+    _load().orc_adjoint(H, W, w.shape[0], _p(w), offs.shape[0], _p(offs), _p(y), _p(out))
+    return out
+
+
+def loss_grad(u, w, offs, f, eps: float):
+    """(loss, grad_u, grad_w) of sum_j G_eps(F(w o S_j u); f_j)."""
+    u = _c(u, np.complex128)
+    w = _c(w, np.complex128)
+    f = _c(f, np.float64)
+    offs = _c(offs, np.int32).reshape(-1, 2)
+    H, W = u.shape
+    gu = np.empty_like(u)
+    gw = np.empty_like(w)
+    loss = _load().orc_loss_grad(H, W, _p(u), w.shape[0], _p(w), offs.shape[0], _p(offs),
+                                 _p(f), eps, _p(gu), _p(gw))
+    return float(loss), gu, gw
+
+
+def geometry(H: int, W: int, m: int, offs, sub_rows: int, sub_cols: int, overlap_px: int):
+    """(frame_sub[J], rect[D,4]) of the overlapping decomposition."""
+    offs = _c(offs, np.int32).reshape(-1, 2)
+    J = offs.shape[0]
+    fs = np.empty(max(J, 1), np.int32)
+    rect = np.empty((sub_rows * sub_cols, 4), np.int32)
+    D = _load().orc_geometry(H, W, m, J, _p(offs), sub_rows, sub_cols, overlap_px, _p(fs), _p(rect))
+    if D < 0:
+        raise ValueError(f"invalid geometry (code {D})")
+    return fs[:J], rect
+
+
+def pairs(rect):
+    """Ordered intersecting pairs (d, e) and their intersection rectangles."""
+    rect = _c(rect, np.int32).reshape(-1, 4)
+    lib = _load()
+    n = lib.orc_pairs(rect.shape[0], _p(rect), 0, None, None)
+    pr = np.empty((max(n, 1), 2), np.int32)
+    prc = np.empty((max(n, 1), 4), np.int32)
+    lib.orc_pairs(rect.shape[0], _p(rect), n, _p(pr), _p(prc))
+    return pr[:n], prc[:n]
+
+
+class ADMM:
+    """Algorithm 2 (blind=False) or Algorithm 3 (blind=True) in FP64."""
+
+    def __init__(self, f, w0, offs, H: int, W: int, sub_rows: int, sub_cols: int,
+                 overlap_px: int, eps: float, eta: float, r: float, u0=None, blind: bool = False,
+                 mu: float = 0.0, gamma: float = 0.0, mask=None):
+        self._lib = _load()
+        f = _c(f, np.float64)
+        w0 = _c(w0, np.complex128)
+        offs = _c(offs, np.int32).reshape(-1, 2)
+        u0c = _c(u0, np.complex128) if u0 is not None else None
+        maskc = _c(mask, np.float64) if mask is not None else None
+        self.m = w0.shape[0]
+        self.J = offs.shape[0]
+        self.H, self.W = H, W
+        self._h = self._lib.orc_admm_new(H, W, self.m, self.J, _p(offs), sub_rows, sub_cols,
+                                         overlap_px, _p(f), _p(w0), _p(u0c), eps, eta, r,
+                                         int(blind), mu, gamma, _p(maskc))
+        if not self._h:
+            raise ValueError("invalid ADMM geometry")
+        self.D = self._lib.orc_admm_num_sub(self._h)
+        self.P = self._lib.orc_admm_num_pairs(self._h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.orc_admm_free(h)
+            self._h = None
+
+    def iterate(self, n: int = 1) -> None:
+        self._lib.orc_admm_iterate(self._h, int(n))
+
+    def get(self, which: int) -> np.ndarray:
+        n = self._lib.orc_admm_state_len(self._h, which)
+        out = np.empty(n, np.complex128)
+        self._lib.orc_admm_get(self._h, which, _p(out))
+        return out
+
+    def set(self, which: int, arr) -> None:
+        n = self._lib.orc_admm_state_len(self._h, which)
+        a = _c(arr, np.complex128).reshape(-1)
+        if a.size != n:
+            raise ValueError(f"state {which}: expected {n} elements, got {a.size}")
+        self._lib.orc_admm_set(self._h, which, _p(a))
+
+    def metrics(self):
+        rf = ctypes.c_double()
+        re = ctypes.c_double()
+        self._lib.orc_admm_metrics(self._h, ctypes.byref(rf), ctypes.byref(re))
+        return rf.value, re.value
+
+    def merge(self) -> np.ndarray:
+        out = np.empty((self.H, self.W), np.complex128)
+        self._lib.orc_admm_merge(self._h, _p(out))
+        return out

@@ -1,0 +1,105 @@
+/*
+ * Forward operator A, its adjoint A^*, and the ST-AGM loss with gradients
+ * (TEST INFRASTRUCTURE ONLY).
+ *
+ * Section 2, problem (PtychoPR): frame j is F(w o S_j u), where S_j cuts the
+ * m x m window whose top-left pixel is offs[j] (integer shift, no wrap-around:
+ * the image is not periodic, section 4 set-up).  A stacks all frames.
+ * A^* y = sum_j S_j^T (conj(w) o F^* y_j) follows from F being unitary and S_j
+ * being a 0/1 selection.  The windows are accumulated in ascending j.
+ */
+#include "od2p_oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+void orc_forward(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
+                 const int32_t *offs, ocplx *out)
+{
+    (void)H;
+    const int mm = m * m;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < J; ++j) {
+        ocplx *x = out + (size_t)j * mm;
+        const int r0 = offs[2 * j], c0 = offs[2 * j + 1];
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < m; ++c)
+                x[r * m + c] = w[r * m + c] * u[(size_t)(r0 + r) * W + (c0 + c)];
+        orc_fft2(x, m, 0);
+    }
+}
+
+void orc_adjoint(int H, int W, int m, const ocplx *w, int J, const int32_t *offs,
+                 const ocplx *y, ocplx *u_out)
+{
+    const int mm = m * m;
+    ocplx *q = (ocplx *)malloc(sizeof(ocplx) * (size_t)J * mm);
+    memcpy(q, y, sizeof(ocplx) * (size_t)J * mm);
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < J; ++j) {
+        ocplx *x = q + (size_t)j * mm;
+        orc_fft2(x, m, 1);
+        for (int k = 0; k < mm; ++k) x[k] *= conj(w[k]);
+    }
+    memset(u_out, 0, sizeof(ocplx) * (size_t)H * W);
+    for (int j = 0; j < J; ++j) {
+        const int r0 = offs[2 * j], c0 = offs[2 * j + 1];
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < m; ++c)
+                u_out[(size_t)(r0 + r) * W + (c0 + c)] += q[(size_t)j * mm + r * m + c];
+    }
+    free(q);
+}
+
+/*
+ * loss(u, w) = sum_j G_eps(F(w o S_j u); f_j)   (eqs. STAGM, obj-1)
+ * grad_u = sum_j S_j^T (conj(w) o F^* grad g)      (chain rule through A)
+ * grad_w = sum_j conj(S_j u) o F^* grad g           (chain rule through w)
+ * with grad g from eq. (objgrad).
+ */
+double orc_loss_grad(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
+                     const int32_t *offs, const double *f, double eps, ocplx *gu, ocplx *gw)
+{
+    const int mm = m * m;
+    ocplx *x = (ocplx *)malloc(sizeof(ocplx) * (size_t)J * mm);
+    double *lj = (double *)malloc(sizeof(double) * (size_t)J);
+    orc_forward(H, W, u, m, w, J, offs, x);
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < J; ++j) {
+        double acc = 0.0;
+        ocplx *xj = x + (size_t)j * mm;
+        const double *fj = f + (size_t)j * mm;
+        for (int k = 0; k < mm; ++k) {
+            acc += orc_stagm_g(xj[k], fj[k], eps);
+            xj[k] = orc_stagm_grad(xj[k], fj[k], eps);
+        }
+        orc_fft2(xj, m, 1);
+        lj[j] = acc;
+    }
+    double loss = 0.0;
+    for (int j = 0; j < J; ++j) loss += lj[j];
+    if (gu) {
+        memset(gu, 0, sizeof(ocplx) * (size_t)H * W);
+        for (int j = 0; j < J; ++j) {
+            const int r0 = offs[2 * j], c0 = offs[2 * j + 1];
+            for (int r = 0; r < m; ++r)
+                for (int c = 0; c < m; ++c)
+                    gu[(size_t)(r0 + r) * W + (c0 + c)] +=
+                        conj(w[r * m + c]) * x[(size_t)j * mm + r * m + c];
+        }
+    }
+    if (gw) {
+        memset(gw, 0, sizeof(ocplx) * (size_t)mm);
+        for (int j = 0; j < J; ++j) {
+            const int r0 = offs[2 * j], c0 = offs[2 * j + 1];
+            for (int r = 0; r < m; ++r)
+                for (int c = 0; c < m; ++c)
+                    gw[r * m + c] += conj(u[(size_t)(r0 + r) * W + (c0 + c)]) *
+                                     x[(size_t)j * mm + r * m + c];
+        }
+    }
+    (void)H;
+    free(x);
+    free(lj);
+    return loss;
+}

@@ -1,0 +1,393 @@
+"""Throughput of the OD2P iteration on GB300: ADMM frame-updates per second.
+
+Workload (one step = one full ADMM iteration of Algorithm 2, all frames):
+512 x 512 complex64 image, 64 x 64 probe, raster step 16 with +-2 px jitter
+(841 frames), 4 x 4 subdomains with a 16 px minimum overlap, Poisson noise at
+1e4 photons peak.  Inputs are seeded synthetic stand-ins for the paper's
+sample (section 4); the measured intensities come from the library's own
+forward operator before timing starts.
+
+Timing: W untimed warm-up iterations, then K timed iterations; before each
+timed iteration a 256 MiB buffer is written to flush the 129 MB L2 (the
+workload's working set would otherwise stay L2-resident), outside the timed
+interval.  Each iteration is bracketed by CUDA events on the launch stream,
+with an extra event between the frame update (the dominant kernel) and the
+subdomain update.  Clocks are sampled with nvidia-smi during the timed region.
+
+`e2e` times the public API end to end with host buffers: pinned f (and probe
+and offsets) copied to the device, plan, Step 0, 200 iterations, merge, image
+copied back -- per reconstruction, frame-updates/s.
+
+`--impl reference` times the FP64 CPU oracle (a plain restatement of the
+paper) on the same workload, one oracle iteration per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "od2p_512px_m64_841frames_4x4sub_poisson1e4"
+METRIC = "ADMM frame-updates/sec"
+UNIT = "frame-updates/s"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "frame_update_m64_512px_841frames.md")
+
+
+def _problem():
+    from paper_2011_00162_gb300 import synth
+    return synth.grid_4x4()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_2011_00162_gb300/csrc/fft_kernels.cu", "paper_2011_00162_gb300/csrc/od2p_internal.h"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """DRAM bytes per frame-update launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    try:
+        txt = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    src = tr = None
+    for line in txt.splitlines():
+        if line.startswith("kernel_source_sha256_16:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            tr = line.split(":", 1)[1].strip()
+    if src != _kernel_source_hash() or tr is None:
+        return None
+    try:
+        return float(tr)
+    except ValueError:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"od2p_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        self.t0 = self.t1 = None
+        return self
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        import datetime
+        rows, all_rows = [], []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                row = (float(parts[2]), float(parts[3]), float(parts[4]) if parts[4] not in ("[N/A]", "") else 0.0,
+                       parts[6:10])
+            except ValueError:
+                continue
+            all_rows.append(row)
+            if self.t0 is not None and self.t0 - 0.05 <= ts <= (self.t1 or ts) + 0.05:
+                rows.append(row)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in the timed region"],
+                    "samples_outside": len(all_rows)}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_inputs(p, dev):
+    """Seeded truth, probe and scan; intensities from the library's forward operator."""
+    import torch
+
+    import paper_2011_00162_gb300 as od
+    from paper_2011_00162_gb300 import synth
+    offs = p.offsets()
+    u_true, w = p.truth(), p.probe()
+    geom0 = od.Geometry(p.n, p.n, p.m, offs)
+    tmp = od.ptycho_plan(geom0, torch.ones((len(offs), p.m, p.m), dtype=torch.float32, device=dev))
+    fr = od.ptycho_forward(tmp, torch.from_numpy(u_true).to(dev), torch.from_numpy(w).to(dev))
+    f_clean = (fr.abs() ** 2).cpu().numpy().astype(np.float64)
+    tmp.close()
+    f = synth.poissonize(f_clean, p.peak, 7)
+    return offs, u_true, w, f
+
+
+def e2e_run(od, geom, f, w, offs, p, dev, K, ws):
+    import torch
+    f_pin = torch.from_numpy(f).pin_memory()
+    w_pin = torch.from_numpy(w).pin_memory()
+    e2e_times = []
+    n_e2e = max(1, min(3, K))
+    out_host = torch.empty((p.n, p.n), dtype=torch.complex64).pin_memory()
+    for i in range(n_e2e + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fd = f_pin.to(dev, non_blocking=True)
+        wd = w_pin.to(dev, non_blocking=True)
+        pl = od.ptycho_plan(geom, fd)
+        od.od2p_init(pl, wd)
+        od.od2p_iterate(pl, p.n_iter)
+        u = od.od2p_merge(pl)
+        out_host.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        pl.close()
+        if i > 0:
+            e2e_times.append(t1 - t0)
+    value = len(offs) * p.n_iter * ws / statistics.median(e2e_times)
+    return {"value": round(value, 1), "unit": UNIT,
+            "h2d_bytes_per_step": int(f.nbytes + w.nbytes + offs.nbytes),
+            "d2h_bytes_per_step": int(out_host.numel() * 8),
+            "step": f"one reconstruction: H2D f, plan, init, {p.n_iter} iterations, merge, D2H image"}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2011_00162_gb300 as od
+    from paper_2011_00162_gb300 import build as odbuild
+
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        odbuild.build()
+    if ws > 1:
+        dist.barrier()
+    p = _problem()
+    offs, u_true, w, f = make_inputs(p, dev)
+    J = len(offs)
+    geom = od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, p.eta, p.r)
+    f_dev = torch.from_numpy(f).to(dev)
+    w_dev = torch.from_numpy(w).to(dev)
+    plan = od.ptycho_plan(geom, f_dev)
+    od.od2p_init(plan, w_dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        od.od2p_frame_update(plan)
+        od.od2p_subdomain_update(plan)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        # give nvidia-smi time to start, keeping the GPU busy meanwhile
+        t_end = time.perf_counter() + 0.6
+        while time.perf_counter() < t_end:
+            od.od2p_iterate(plan, 20)
+            torch.cuda.synchronize()
+        clk.mark_start()
+        wall0 = time.perf_counter()
+        for k in range(K):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            od.od2p_frame_update(plan)
+            ev[k][1].record(stream)
+            od.od2p_subdomain_update(plan)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        wall1 = time.perf_counter()
+        clk.mark_end()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
+    k1_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    k2_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = J * K * ws / total_s
+    rf, re = od.od2p_metrics(plan)
+    plan.close()
+
+    # ---- end to end through the public API with host buffers (per reconstruction)
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_run(od, geom, f, w, offs, p, dev, K, ws)
+
+    peak, peak_kind = _peaks()
+    alg_bytes = 20.0 * p.m * p.m * J  # f 4 B + Gamma read 8 B + write 8 B per frame pixel
+    k1_avg_s = statistics.mean(k1_ms) / 1e3
+    achieved = alg_bytes / k1_avg_s / 1e9
+    traffic = _ncu_traffic()
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(statistics.mean(step_ms), 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "image": p.n, "probe": p.m, "frames": J, "step_px": p.step,
+                   "jitter_px": p.jitter, "subdomains": f"{p.sub_rows}x{p.sub_cols}",
+                   "overlap_min_px": p.overlap_px, "poisson_peak": p.peak, "eps": p.eps, "eta": p.eta,
+                   "r": p.r, "step": "one ADMM iteration (Algorithm 2 Steps 1-4, all frames)",
+                   "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu",
+                   "frame_update_ms": round(statistics.mean(k1_ms), 5),
+                   "subdomain_update_ms": round(statistics.mean(k2_ms), 5),
+                   "rf_after": rf, "re_after": re},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "frame_update_kernel<64>", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+            "e2e": e2e,
+        "gpu_launches": 2 * K,
+        "clocks": clocks,
+        "wall_s_timed_region": round(wall1 - wall0, 4),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_case(p):
+    import oracle
+    from paper_2011_00162_gb300 import synth
+    offs = p.offsets()
+    u_true, w = p.truth(), p.probe()
+    f = synth.poissonize(np.abs(oracle.forward(u_true, w, offs)) ** 2, p.peak, 7)
+    return offs, w, f
+
+
+def cpu_baseline(p, budget_s: float = 15.0):
+    """The FP64 oracle as it stands, on all host cores, for a bounded number of iterations."""
+    import oracle
+    offs, w, f = _oracle_case(p)
+    a = oracle.ADMM(f, w, offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, p.eta, p.r)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        a.iterate(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 200:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(len(offs) * n / el, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} oracle iterations of {WORKLOAD} ({len(offs)} frames each), {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p = _problem()
+    offs, w, f = _oracle_case(p)
+    a = oracle.ADMM(f, w, offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, p.eta, p.r)
+    for _ in range(args.warmup):
+        a.iterate(1)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        a.iterate(1)
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    value = len(offs) * args.steps / total
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "image": p.n, "probe": p.m,
+                                        "frames": len(offs), "subdomains": f"{p.sub_rows}x{p.sub_cols}",
+                                        "step": "one ADMM iteration of the FP64 CPU oracle"},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle iterations of {WORKLOAD}"},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

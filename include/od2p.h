@@ -1,0 +1,246 @@
+/*
+ * od2p.h -- C ABI of the GB300 (sm_103a) OD2P ptychography library.
+ *
+ * Method: Chang, Glowinski, Marchesini, Tai, Wang, Zeng, "Overlapping Domain
+ * Decomposition Methods for Ptychographic Imaging", arXiv:2011.00162.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Complex data are interleaved single precision (ptycho_c32 = {re, im}),
+ *    row-major.  Frames are J x m x m, contiguous.  Images are img_h x img_w.
+ *  - The 2-D DFT F is unitary (1/m both ways) with frequencies in natural
+ *    (unshifted) order (section 2: "normalized discrete Fourier transform").
+ *  - Scan offsets are the (row, col) of the top-left pixel of each m x m
+ *    window; S_j cuts that window without wrap-around (section 4 set-up).
+ *  - Pointers named *_dev are device pointers owned by the caller; pointers
+ *    named *_host are host pointers owned by the caller.  Nothing crosses the
+ *    ABI by ownership transfer except the opaque plan, which the caller frees
+ *    with ptycho_plan_destroy.
+ *  - Every call enqueues its GPU work on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream) and returns without synchronising unless it says
+ *    otherwise.  Plan-owned state may only be used from one stream at a time.
+ *  - Every call returns PTYCHO_OK (0) or an error code; ptycho_last_error()
+ *    returns a message for the calling thread.  No C++ exception crosses the
+ *    ABI and no call aborts the process.
+ *  - Supported probe sides m: 16, 32, 64, 128 (powers of two; the frame is
+ *    transformed in one thread block's shared memory).  Other m return
+ *    PTYCHO_ERR_UNSUPPORTED.
+ */
+#ifndef OD2P_H
+#define OD2P_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t without including the CUDA headers. */
+typedef struct CUstream_st *ptycho_stream_t;
+
+typedef struct {
+    float re, im;
+} ptycho_c32;
+
+enum {
+    PTYCHO_OK = 0,
+    PTYCHO_ERR_INVALID_ARG = 1, /* a size, pointer, offset or parameter is out of range   */
+    PTYCHO_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. m not in {16..128})    */
+    PTYCHO_ERR_OOM = 3,         /* device or host allocation failed                       */
+    PTYCHO_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has the CUDA text) */
+    PTYCHO_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                     */
+    PTYCHO_ERR_STATE = 6        /* call not valid in the plan's current state             */
+};
+
+/* ptycho_get_state / ptycho_set_state selectors */
+enum {
+    PTYCHO_STATE_U = 0,      /* u_d: concatenated subdomain rectangles, d ascending        */
+    PTYCHO_STATE_GAMMA = 1,  /* Gamma: J x m x m, natural frequency order                  */
+    PTYCHO_STATE_LAMBDA = 2, /* Lambda_{d,e}: concatenated pair rectangles, pair order     */
+    PTYCHO_STATE_WD = 3,     /* W_d: D x m x m per-subdomain probe copies (blind)          */
+    PTYCHO_STATE_DELTA = 4,  /* Delta_d: D x m x m multipliers of W_d = w (blind)          */
+    PTYCHO_STATE_W = 5,      /* w: m x m shared probe                                      */
+    PTYCHO_STATE_Q = 6       /* last frame-space residual q_j (J x m x m, spatial), read-only */
+};
+
+/* overlap_add flags */
+enum {
+    PTYCHO_OA_IFFT = 1 /* apply F^* to each frame first, so the call computes A^* y */
+};
+
+/*
+ * Problem description (section 2, problem PtychoPR; sections 2.1 and 3.1 for
+ * the decomposition; section 2.2 for eps; Algorithms 1-3 for eta, r, mu, gamma).
+ *
+ * Decomposition rule (the paper builds subdomains from complete frames but does
+ * not fix a rule for 2-D grids): the image is cut into sub_rows x sub_cols
+ * core tiles at floor(k*H/sub_rows), floor(k*W/sub_cols); frame j joins the
+ * tile containing its window centre offs[j] + (m-1)/2; Omega_d is the bounding
+ * box of its core tile grown by ceil(overlap_px/2) on interior sides (clipped)
+ * and of its frames' windows.  Ordered pairs (d, e) with intersecting Omega
+ * carry Lambda_{d,e}; sorted by (d, e).
+ */
+typedef struct {
+    int32_t img_h, img_w;           /* image size in pixels                                 */
+    int32_t m;                      /* probe side: 16, 32, 64 or 128                       */
+    int32_t n_frames;               /* J >= 1                                              */
+    const int32_t *offsets_host;    /* J x 2 (row, col), 0 <= row <= img_h-m, col likewise  */
+    int32_t sub_rows, sub_cols;     /* subdomain grid, >= 1                                */
+    int32_t overlap_px;             /* requested minimum overlap width, >= 0               */
+    float eps;                      /* ST-AGM truncation, 0 < eps < 1 (paper: 0.5)         */
+    float eta;                      /* ADMM penalty on A_d u_d = z_d, > 0                  */
+    float r;                        /* ADMM penalty on overlap continuity, >= 0            */
+    float mu;                       /* blind: penalty on W_d = w, > 0 when blind           */
+    float gamma;                    /* blind: proximal weight of the U-update, >= 0        */
+    int32_t blind;                  /* 0: Algorithm 2 (known probe); 1: Algorithm 3        */
+    const uint8_t *fourier_support_host; /* blind: m x m, 1 on the support of F w; NULL = all */
+} ptycho_geometry;
+
+typedef struct ptycho_plan_s ptycho_plan_t;
+
+/* Message of the last failing call on this thread ("" if none). Never NULL. */
+const char *ptycho_last_error(void);
+
+/* ABI version, incremented on incompatible changes. */
+int32_t ptycho_abi_version(void);
+
+/*
+ * Build a plan: validate g, compute the decomposition, allocate plan-owned
+ * device state, and ingest the measured intensities f (J x m x m FP32,
+ * natural frequency order, f >= 0).  f_dev is read during this call only (the
+ * plan keeps sqrt(f) in its own layout).  The state is initialised as Step 0
+ * of Algorithms 1-3 with u = 1 and the probe all zeros; call od2p_init before
+ * iterating.  On error *out is set to NULL and nothing is leaked.
+ * Errors: INVALID_ARG (NULL pointer, bad sizes/offsets/parameters),
+ * UNSUPPORTED (m), OOM, CUDA.
+ */
+int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev,
+                ptycho_stream_t stream);
+
+/* Free a plan and everything it owns (synchronises the device). NULL is a no-op. */
+int ptycho_plan_destroy(ptycho_plan_t *plan);
+
+/* Sizes of the decomposition: subdomains D, ordered pairs P, and the element
+ * counts of the concatenated u and Lambda layouts.  Any output may be NULL.  */
+int ptycho_plan_dims(const ptycho_plan_t *plan, int32_t *n_sub, int32_t *n_pairs,
+                     int64_t *u_len, int64_t *lambda_len);
+
+/* Host copies of the decomposition: frame_sub[J], rect[D*4] = (r0, c0, r1, c1)
+ * half-open, pair[P*2] = (d, e), pair_rect[P*4].  Any output may be NULL.     */
+int ptycho_plan_layout(const ptycho_plan_t *plan, int32_t *frame_sub_host, int32_t *rect_host,
+                       int32_t *pair_host, int32_t *pair_rect_host);
+
+/*
+ * Forward operator (section 2, operator A): frames_out[j] = F(w o S_j u) for
+ * every frame of the plan.  u_dev: img_h x img_w; w_dev: m x m;
+ * frames_out_dev: J x m x m (natural frequency order).  Errors: INVALID_ARG.
+ */
+int ptycho_forward(const ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c32 *w_dev,
+                   ptycho_c32 *frames_out_dev, ptycho_stream_t stream);
+
+/*
+ * Proximal map of the ST-AGM (section 2.2, eq. Prox_sol), elementwise:
+ * z[i] = argmin_z g_eps(z; f[i]) + lambda/2 |z - y[i]|^2.  The threshold is
+ * read as |y| < (eps - (1-eps)/lambda) sqrt(f) (the paper's is garbled);
+ * sign(0) = 1.  y, z: n complex; f: n floats >= 0; z may alias y.
+ * Errors: INVALID_ARG (n < 0, NULL with n > 0, eps not in (0,1), lambda <= 0).
+ */
+int stagm_prox(const ptycho_c32 *y_dev, const float *f_dev, ptycho_c32 *z_dev, int64_t n,
+               float eps, float lambda, ptycho_stream_t stream);
+
+/*
+ * Overlap-add (the adjoint A^* of section 2, used by eq. Alg1-solver-u):
+ * image_out = sum_j S_j^T (conj(w) o G_j), G_j = F^* frames_j when flags has
+ * PTYCHO_OA_IFFT, else frames_j.  Each pixel sums the frames covering it in
+ * ascending j with no atomics, so the result is bitwise reproducible.
+ * frames_dev: J x m x m; w_dev: m x m; image_out_dev: img_h x img_w
+ * (overwritten; uncovered pixels are 0).  Uses the plan's frame scratch, so
+ * calls on one plan must not overlap.  Errors: INVALID_ARG.
+ */
+int overlap_add(ptycho_plan_t *plan, const ptycho_c32 *frames_dev, const ptycho_c32 *w_dev,
+                ptycho_c32 *image_out_dev, int32_t flags, ptycho_stream_t stream);
+
+/*
+ * Step 0 of Algorithms 1-3: u_d = R_d u0 (u0_dev img_h x img_w, or NULL for
+ * all ones), Gamma = Lambda = 0; the probe w (and, blind, every W_d) = w0_dev
+ * (m x m, required), Delta = 0.  Errors: INVALID_ARG.
+ */
+int od2p_init(ptycho_plan_t *plan, const ptycho_c32 *u0_dev, const ptycho_c32 *w0_dev,
+              ptycho_stream_t stream);
+
+/*
+ * One ADMM iteration: Algorithm 2 Steps 1-4 (nonblind; D = 2 is Algorithm 1)
+ * or Algorithm 3 Steps 1-5 (blind), repeated n_iter times.  The iteration is
+ * replayed from a CUDA graph captured on first use.  Errors: INVALID_ARG
+ * (n_iter < 0), STATE (od2p_init not called), CUDA.
+ */
+int od2p_iterate(ptycho_plan_t *plan, int32_t n_iter, ptycho_stream_t stream);
+
+/*
+ * The two halves of one nonblind iteration, for stage timing:
+ *  od2p_frame_update:     Steps 1-2 frame part -- z = Prox(Gamma + A_d u_d),
+ *                         Gamma += A_d u_d - z, q_j = conj(w) o F^*(z - Gamma)
+ *                         (eqs. updateZ, updateM-1-multi); fused per frame.
+ *  od2p_subdomain_update: Step 1 v (eq. updateV-multi), Step 3 u (eq.
+ *                         Alg1-solver-u, D-subdomain form) by gathering q_j in
+ *                         ascending j, Step 4 Lambda (eq. updateM-2-multi).
+ * Calling them in this order equals od2p_iterate(plan, 1).  Blind plans
+ * return STATE (use od2p_iterate).
+ */
+int od2p_frame_update(ptycho_plan_t *plan, ptycho_stream_t stream);
+int od2p_subdomain_update(ptycho_plan_t *plan, ptycho_stream_t stream);
+
+/*
+ * Blind probe update (Algorithm 3 Steps 1 (w), 3 (W) and 5 (Delta); eqs.
+ * blind_w, blind_W, admm_Delta) from the frame residuals of the last frame
+ * update.  od2p_iterate calls it for blind plans; exposed for stage timing.
+ * Errors: STATE (nonblind plan).
+ */
+int probe_update(ptycho_plan_t *plan, ptycho_stream_t stream);
+
+/*
+ * Merge of the subdomain solutions (section 4 set-up): pixels in one subdomain
+ * keep their value, overlaps are averaged.  u_out_dev: img_h x img_w.
+ */
+int od2p_merge(const ptycho_plan_t *plan, ptycho_c32 *u_out_dev, ptycho_stream_t stream);
+
+/*
+ * Stopping metrics of section 4 from the last iteration, reduced in a fixed
+ * order: RF of the iterate that entered it (sum |(|A_d u_d| - sqrt f)| /
+ * sum sqrt f) and RE = max_d ||u_d^{n+1} - u_d^n|| / ||u_d^{n+1}||.  Writes
+ * host scalars and synchronises `stream`.  Either output may be NULL.
+ */
+int od2p_metrics(ptycho_plan_t *plan, float *rf_host, float *re_host, ptycho_stream_t stream);
+
+/* Element count (complex) of a state selector (PTYCHO_STATE_*). */
+int od2p_state_len(const ptycho_plan_t *plan, int32_t which, int64_t *n_out);
+
+/* Copy state out of / into the plan (device buffers of od2p_state_len
+ * elements, layouts as documented at PTYCHO_STATE_*).  Used for checkpoint /
+ * resume and parity checks.  PTYCHO_STATE_Q cannot be set.                   */
+int od2p_get_state(const ptycho_plan_t *plan, int32_t which, ptycho_c32 *dst_dev,
+                   ptycho_stream_t stream);
+int od2p_set_state(ptycho_plan_t *plan, int32_t which, const ptycho_c32 *src_dev,
+                   ptycho_stream_t stream);
+
+/*
+ * ST-AGM data-fidelity loss of the whole image and its gradients (sections 2.2
+ * and 2.4: G_eps(A u; f) with the gradient of eq. objgrad pulled back through
+ * A):  loss = sum_j sum_k g_eps((F(w o S_j u))_k; f_jk),
+ *      grad_u = sum_j S_j^T (conj(w) o F^* grad g_j),
+ *      grad_w = sum_j conj(S_j u) o F^* grad g_j,
+ * gradients in the d/dRe + i d/dIm convention.  u_dev: img_h x img_w;
+ * w_dev: m x m; loss_dev: 1 float; grad_u_dev (img_h x img_w) and grad_w_dev
+ * (m x m) may be NULL.  Frame exit waves are recomputed from u and w, never
+ * stored (recompute must be 1; 0 is reserved).  Reductions have a fixed order.
+ * Uses plan scratch: calls on one plan must not overlap.
+ */
+int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c32 *w_dev,
+                    float *loss_dev, ptycho_c32 *grad_u_dev, ptycho_c32 *grad_w_dev,
+                    int32_t recompute, ptycho_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OD2P_H */

@@ -1,0 +1,233 @@
+"""Python binding of the C ABI with the same names (argument marshalling only).
+
+Every function takes and returns CUDA tensors (complex64 for complex data,
+float32 for intensities) and enqueues its work on the current PyTorch CUDA
+stream.  All arithmetic runs in libod2p.so; nothing here computes any step of
+the method, and there is no CPU path: a CPU tensor or a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (OA_IFFT, STATE_DELTA, STATE_GAMMA, STATE_LAMBDA, STATE_Q, STATE_U, STATE_W,
+                   STATE_WD, PtychoError, check)
+
+__all__ = [
+    "Geometry", "Plan", "ptycho_plan", "ptycho_forward", "stagm_prox", "overlap_add", "od2p_init",
+    "od2p_iterate", "od2p_frame_update", "od2p_subdomain_update", "probe_update", "od2p_merge",
+    "od2p_metrics", "od2p_get_state", "od2p_set_state", "stagm_loss_grad", "PtychoError",
+    "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
+]
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None, dtype: torch.dtype, what: str) -> ctypes.c_void_p | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor (there is no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclasses.dataclass
+class Geometry:
+    """Problem description (mirror of ptycho_geometry)."""
+    img_h: int
+    img_w: int
+    m: int
+    offsets: np.ndarray          # (J, 2) int32 top-left (row, col)
+    sub_rows: int = 1
+    sub_cols: int = 1
+    overlap_px: int = 0
+    eps: float = 0.5
+    eta: float = 0.1
+    r: float = 0.05
+    mu: float = 0.0
+    gamma: float = 0.0
+    blind: bool = False
+    fourier_support: np.ndarray | None = None  # (m, m) uint8, blind only
+
+    @property
+    def n_frames(self) -> int:
+        return int(np.asarray(self.offsets).reshape(-1, 2).shape[0])
+
+
+class Plan:
+    """Owns a ptycho_plan_t; freed by close() or garbage collection."""
+
+    def __init__(self, geom: Geometry, f: torch.Tensor, stream=None):
+        self._lib = _lib.load()
+        self.geom = geom
+        self._offs = np.ascontiguousarray(np.asarray(geom.offsets, np.int32).reshape(-1, 2))
+        self._mask = (np.ascontiguousarray(np.asarray(geom.fourier_support, np.uint8))
+                      if geom.fourier_support is not None else None)
+        J = self._offs.shape[0]
+        if tuple(f.shape) != (J, geom.m, geom.m):
+            raise ValueError(f"f must be (J, m, m) = {(J, geom.m, geom.m)}, got {tuple(f.shape)}")
+        g = _lib.Geometry(geom.img_h, geom.img_w, geom.m, J, self._offs.ctypes.data, geom.sub_rows,
+                          geom.sub_cols, geom.overlap_px, geom.eps, geom.eta, geom.r, geom.mu,
+                          geom.gamma, int(bool(geom.blind)),
+                          self._mask.ctypes.data if self._mask is not None else None)
+        h = ctypes.c_void_p()
+        check(self._lib.ptycho_plan(ctypes.byref(h), ctypes.byref(g), _ptr(f, torch.float32, "f"),
+                                    _stream(stream)))
+        self._h = h
+        self.device = f.device
+        D, P = ctypes.c_int32(), ctypes.c_int32()
+        ul, ll = ctypes.c_int64(), ctypes.c_int64()
+        check(self._lib.ptycho_plan_dims(h, ctypes.byref(D), ctypes.byref(P), ctypes.byref(ul),
+                                         ctypes.byref(ll)))
+        self.n_sub, self.n_pairs, self.u_len, self.lambda_len = D.value, P.value, ul.value, ll.value
+        self.n_frames = J
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("plan has been destroyed")
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            self._lib.ptycho_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self):
+        """(frame_sub[J], rect[D,4], pair[P,2], pair_rect[P,4]) as numpy int32."""
+        fs = np.empty(self.n_frames, np.int32)
+        rect = np.empty((self.n_sub, 4), np.int32)
+        pr = np.empty((max(self.n_pairs, 1), 2), np.int32)
+        prc = np.empty((max(self.n_pairs, 1), 4), np.int32)
+        check(self._lib.ptycho_plan_layout(self.handle, fs.ctypes.data, rect.ctypes.data,
+                                           pr.ctypes.data, prc.ctypes.data))
+        return fs, rect, pr[:self.n_pairs], prc[:self.n_pairs]
+
+
+def ptycho_plan(geom: Geometry, f: torch.Tensor, stream=None) -> Plan:
+    return Plan(geom, f, stream)
+
+
+def _c64(shape, device):
+    return torch.empty(shape, dtype=torch.complex64, device=device)
+
+
+def ptycho_forward(plan: Plan, u: torch.Tensor, w: torch.Tensor, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    g = plan.geom
+    if tuple(u.shape) != (g.img_h, g.img_w) or tuple(w.shape) != (g.m, g.m):
+        raise ValueError("u must be (img_h, img_w) and w (m, m)")
+    if out is None:
+        out = _c64((plan.n_frames, g.m, g.m), u.device)
+    check(plan._lib.ptycho_forward(plan.handle, _ptr(u, torch.complex64, "u"), _ptr(w, torch.complex64, "w"),
+                                   _ptr(out, torch.complex64, "out"), _stream(stream)))
+    return out
+
+
+def stagm_prox(y: torch.Tensor, f: torch.Tensor, eps: float, lam: float,
+               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if y.shape != f.shape:
+        raise ValueError("y and f must have the same shape")
+    if out is None:
+        out = torch.empty_like(y)
+    check(_lib.load().stagm_prox(_ptr(y, torch.complex64, "y"), _ptr(f, torch.float32, "f"),
+                                 _ptr(out, torch.complex64, "out"), y.numel(), eps, lam, _stream(stream)))
+    return out
+
+
+def overlap_add(plan: Plan, frames: torch.Tensor, w: torch.Tensor, ifft: bool = True,
+                out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    g = plan.geom
+    if tuple(frames.shape) != (plan.n_frames, g.m, g.m):
+        raise ValueError("frames must be (J, m, m)")
+    if out is None:
+        out = _c64((g.img_h, g.img_w), frames.device)
+    check(plan._lib.overlap_add(plan.handle, _ptr(frames, torch.complex64, "frames"),
+                                _ptr(w, torch.complex64, "w"), _ptr(out, torch.complex64, "out"),
+                                OA_IFFT if ifft else 0, _stream(stream)))
+    return out
+
+
+def od2p_init(plan: Plan, w0: torch.Tensor, u0: torch.Tensor | None = None, stream=None) -> None:
+    check(plan._lib.od2p_init(plan.handle, _ptr(u0, torch.complex64, "u0"), _ptr(w0, torch.complex64, "w0"),
+                              _stream(stream)))
+
+
+def od2p_iterate(plan: Plan, n_iter: int = 1, stream=None) -> None:
+    check(plan._lib.od2p_iterate(plan.handle, int(n_iter), _stream(stream)))
+
+
+def od2p_frame_update(plan: Plan, stream=None) -> None:
+    check(plan._lib.od2p_frame_update(plan.handle, _stream(stream)))
+
+
+def od2p_subdomain_update(plan: Plan, stream=None) -> None:
+    check(plan._lib.od2p_subdomain_update(plan.handle, _stream(stream)))
+
+
+def probe_update(plan: Plan, stream=None) -> None:
+    check(plan._lib.probe_update(plan.handle, _stream(stream)))
+
+
+def od2p_merge(plan: Plan, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    g = plan.geom
+    if out is None:
+        out = _c64((g.img_h, g.img_w), plan.device)
+    check(plan._lib.od2p_merge(plan.handle, _ptr(out, torch.complex64, "out"), _stream(stream)))
+    return out
+
+
+def od2p_metrics(plan: Plan, stream=None) -> tuple[float, float]:
+    rf, re = ctypes.c_float(), ctypes.c_float()
+    check(plan._lib.od2p_metrics(plan.handle, ctypes.byref(rf), ctypes.byref(re), _stream(stream)))
+    return rf.value, re.value
+
+
+def od2p_state_len(plan: Plan, which: int) -> int:
+    n = ctypes.c_int64()
+    check(plan._lib.od2p_state_len(plan.handle, int(which), ctypes.byref(n)))
+    return n.value
+
+
+def od2p_get_state(plan: Plan, which: int, stream=None) -> torch.Tensor:
+    out = _c64((od2p_state_len(plan, which),), plan.device)
+    check(plan._lib.od2p_get_state(plan.handle, int(which), _ptr(out, torch.complex64, "dst"), _stream(stream)))
+    return out
+
+
+def od2p_set_state(plan: Plan, which: int, src: torch.Tensor, stream=None) -> None:
+    n = od2p_state_len(plan, which)
+    if src.numel() != n:
+        raise ValueError(f"state {which} has {n} elements, got {src.numel()}")
+    check(plan._lib.od2p_set_state(plan.handle, int(which), _ptr(src.contiguous(), torch.complex64, "src"),
+                                   _stream(stream)))
+
+
+def stagm_loss_grad(plan: Plan, u: torch.Tensor, w: torch.Tensor, grad_u: bool = True,
+                    grad_w: bool = True, stream=None):
+    """(loss[1] float32, grad_u or None, grad_w or None) on the current stream."""
+    g = plan.geom
+    loss = torch.empty(1, dtype=torch.float32, device=u.device)
+    gu = _c64((g.img_h, g.img_w), u.device) if grad_u else None
+    gw = _c64((g.m, g.m), u.device) if grad_w else None
+    check(plan._lib.stagm_loss_grad(plan.handle, _ptr(u, torch.complex64, "u"), _ptr(w, torch.complex64, "w"),
+                                    _ptr(loss, torch.float32, "loss"), _ptr(gu, torch.complex64, "grad_u"),
+                                    _ptr(gw, torch.complex64, "grad_w"), 1, _stream(stream)))
+    return loss, gu, gw

@@ -1,0 +1,74 @@
+"""In-tree build of the CUDA library libod2p.so for sm_103a (GB300).
+
+nvcc compiles each translation unit under csrc/ in parallel with
+`-gencode arch=compute_103a,code=sm_103a` and links a shared library next to
+this file.  The CUDA runtime is linked statically, so the library has no
+dependency on torch and exports only the C ABI of include/od2p.h.
+"""
+from __future__ import annotations
+
+import concurrent.futures
+import os
+import shutil
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(ROOT, "_build")
+LIB = os.path.join(HERE, "libod2p.so")
+SOURCES = ["fft_kernels.cu", "gather_kernels.cu", "plan.cpp"]
+HEADERS = [os.path.join(CSRC, "od2p_internal.h"), os.path.join(ROOT, "include", "od2p.h")]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc() -> str:
+    cand = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(cand):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libod2p.so")
+    return cand
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + HEADERS
+    return any(os.path.getmtime(p) > t for p in deps)
+
+
+def build(force: bool = False, verbose: bool = False, out: str | None = None,
+          defines: tuple[str, ...] = ()) -> str:
+    """Compile and link; `out`/`defines` build a variant elsewhere (launch-shape sweeps)."""
+    lib_path = out or LIB
+    if not force and out is None and not _stale():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    cc = nvcc()
+    flags = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+    flags += [f"-D{d}" for d in defines]
+    tag = "" if out is None else "_" + "_".join(defines).replace("=", "")
+
+    def compile_one(src: str) -> str:
+        obj = os.path.join(BUILD, src + tag + ".o")
+        cmd = [cc] + flags + ARCH + ["-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{res.stdout}\n{res.stderr}")
+        return obj
+
+    with concurrent.futures.ThreadPoolExecutor(len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = lib_path + f".tmp{os.getpid()}"
+    cmd = [cc, "-shared"] + ARCH + ["-o", tmp] + objs
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
+    os.replace(tmp, lib_path)
+    return lib_path
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose=True))

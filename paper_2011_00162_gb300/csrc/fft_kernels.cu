@@ -1,0 +1,881 @@
+// Frame-space kernels of the OD2P library for sm_103a: the fused frame update
+// (exit wave -> unitary 2-D FFT -> ST-AGM prox + Gamma update -> inverse FFT),
+// the forward operator, the frame inverse-FFT of the adjoint, the loss frames,
+// and the blind probe average.  No tensor cores: the work is FFT butterflies
+// and elementwise arithmetic, bound by HBM and shared memory.
+//
+// 2-D FFT scheme.  An m x m frame lives in shared memory with an odd row pitch
+// P = m + 1.  The length-m transform is split m = R1 * R2 (Cooley-Tukey,
+// decimation in frequency):
+//   stage 1: for n1 < R2, R1-point DFT over x[n1 + R2 t], times exp(-2 pi i n1 s / m),
+//            stored at n1 + R2 s;
+//   stage 2: for s < R1, R2-point DFT over the contiguous block [R2 s, R2 s + R2);
+// so position p = R2 s + s' holds frequency k = s + R1 s' (digit-reversed).
+// The 2-D transform runs stage 1 and 2 along columns (lanes on columns:
+// coalesced global loads, conflict-free shared rows) and then along rows
+// (lanes on rows: the odd pitch makes them conflict-free).  The inverse is the
+// exact adjoint, stages in reverse order, so natural order comes back without
+// any bit-reversal pass.  Frequency-space arrays private to the plan (Gamma,
+// sqrt f) are stored in the order the row stage holds them: element
+// (position row pr, position column pc) at pc * m + pr, which makes the
+// prox's loads and stores coalesced.  Each R-point DFT runs in registers as a
+// radix-2 network with exact twiddle constants.
+#include "od2p_internal.h"
+
+#include <cmath>
+
+namespace od2p {
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+__host__ __device__ constexpr int brev(int i, int bits)
+{
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
+
+// v * exp(-+2 pi i n / 16) for n in [0, 8) (forward: minus).  cos(pi/8), sin(pi/8)
+// and sqrt(1/2) are the exact values rounded to float.
+template <bool INV>
+__device__ __forceinline__ float2 tw16(float2 v, int n)
+{
+    constexpr float C1 = 0.92387953251128674f, S1 = 0.38268343236508977f, H = 0.70710678118654752f;
+    const float sg = INV ? 1.f : -1.f;
+    switch (n) {
+    case 0: return v;
+    case 1: return cmul(v, make_float2(C1, sg * S1));
+    case 2: return cscale(make_float2(v.x - sg * v.y, v.y + sg * v.x), H);
+    case 3: return cmul(v, make_float2(S1, sg * C1));
+    case 4: return make_float2(-sg * v.y, sg * v.x);
+    case 5: return cmul(v, make_float2(-S1, sg * C1));
+    case 6: return cscale(make_float2(-v.x - sg * v.y, -v.y + sg * v.x), H);
+    default: return cmul(v, make_float2(-C1, sg * S1));
+    }
+}
+
+// In-register R-point DFT (R <= 16), natural order in and out, unnormalised.
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 (&x)[R])
+{
+#pragma unroll
+    for (int span = R / 2; span >= 1; span >>= 1) {
+#pragma unroll
+        for (int blk = 0; blk < R; blk += 2 * span) {
+#pragma unroll
+            for (int k = 0; k < span; ++k) {
+                const float2 a = x[blk + k], b = x[blk + k + span];
+                x[blk + k] = cadd(a, b);
+                x[blk + k + span] = tw16<INV>(csub(a, b), k * (16 / (2 * span)));
+            }
+        }
+    }
+    float2 y[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) y[i] = x[brev(i, ilog2(R))];
+#pragma unroll
+    for (int i = 0; i < R; ++i) x[i] = y[i];
+}
+
+template <int M> struct Radix;
+// R1 x R2 split, frames per block, threads per block, and the resident blocks
+// per SM the register budget is sized for (shared memory allows the same).
+template <> struct Radix<16> { static constexpr int R1 = 4, R2 = 4, FPB = 8, NT = 256, MINB = 6; };
+template <> struct Radix<32> { static constexpr int R1 = 8, R2 = 4, FPB = 4, NT = 256, MINB = 6; };
+#ifndef OD2P_NT64
+#define OD2P_NT64 256
+#endif
+#ifndef OD2P_MINB64
+#define OD2P_MINB64 6
+#endif
+template <> struct Radix<64> { static constexpr int R1 = 8, R2 = 8, FPB = 1, NT = OD2P_NT64, MINB = OD2P_MINB64; };
+template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8, FPB = 1, NT = 512, MINB = 1; };
+
+// Ask the TMA unit to stage [p, p + bytes) into L2 (bytes a multiple of 16,
+// p 16-byte aligned); issued early so the data is near when it is needed.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <int M> constexpr size_t smem_bytes()
+{
+    return sizeof(float2) * (M + (size_t)Radix<M>::FPB * M * (M + 1)) +
+           sizeof(float) * (Radix<M>::NT / 32);
+}
+
+// position <-> frequency along one axis
+template <int M> __device__ __forceinline__ int pos_of(int k)
+{
+    return Radix<M>::R2 * (k % Radix<M>::R1) + k / Radix<M>::R1;
+}
+
+// ---------------------------------------------------------------- shared stages
+// Column-direction stage 2 (forward or inverse) over all FPB frames.
+template <int M, bool INV>
+__device__ __forceinline__ void col_stage2(float2 *buf)
+{
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int P = M + 1;
+    for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
+        const int c = task % M, rest = task / M, s = rest % R1, f = rest / R1;
+        float2 *fb = buf + f * M * P;
+        float2 x[R2];
+#pragma unroll
+        for (int t = 0; t < R2; ++t) x[t] = fb[(R2 * s + t) * P + c];
+        dft<R2, INV>(x);
+#pragma unroll
+        for (int t = 0; t < R2; ++t) fb[(R2 * s + t) * P + c] = x[t];
+    }
+}
+
+// Row-direction stage 1, forward (DFT then twiddle) or inverse (twiddle then DFT).
+template <int M, bool INV>
+__device__ __forceinline__ void row_stage1(float2 *buf, const float2 *tw)
+{
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int P = M + 1;
+    for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
+        const int r = task % M, rest = task / M, n1 = rest % R2, f = rest / R2;
+        float2 *fb = buf + f * M * P + r * P;
+        float2 x[R1];
+        if (!INV) {
+#pragma unroll
+            for (int t = 0; t < R1; ++t) x[t] = fb[n1 + R2 * t];
+            dft<R1, false>(x);
+#pragma unroll
+            for (int s = 0; s < R1; ++s) fb[n1 + R2 * s] = cmul(x[s], tw[n1 * s]);
+        } else {
+#pragma unroll
+            for (int s = 0; s < R1; ++s) x[s] = cmulc(fb[n1 + R2 * s], tw[n1 * s]);
+            dft<R1, true>(x);
+#pragma unroll
+            for (int t = 0; t < R1; ++t) fb[n1 + R2 * t] = x[t];
+        }
+    }
+}
+
+// Column-direction stage 1 reading / writing shared memory.
+template <int M, bool INV>
+__device__ __forceinline__ void col_stage1(float2 *buf, const float2 *tw)
+{
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int P = M + 1;
+    for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
+        const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2;
+        float2 *fb = buf + f * M * P;
+        float2 x[R1];
+        if (!INV) {
+#pragma unroll
+            for (int t = 0; t < R1; ++t) x[t] = fb[(n1 + R2 * t) * P + c];
+            dft<R1, false>(x);
+#pragma unroll
+            for (int s = 0; s < R1; ++s) fb[(n1 + R2 * s) * P + c] = cmul(x[s], tw[n1 * s]);
+        } else {
+#pragma unroll
+            for (int s = 0; s < R1; ++s) x[s] = cmulc(fb[(n1 + R2 * s) * P + c], tw[n1 * s]);
+            dft<R1, true>(x);
+#pragma unroll
+            for (int t = 0; t < R1; ++t) fb[(n1 + R2 * t) * P + c] = x[t];
+        }
+    }
+}
+
+// Row-direction stage 2 in shared memory (forward or inverse).
+template <int M, bool INV>
+__device__ __forceinline__ void row_stage2(float2 *buf)
+{
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int P = M + 1;
+    for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
+        const int r = task % M, rest = task / M, s = rest % R1, f = rest / R1;
+        float2 *fb = buf + f * M * P + r * P;
+        float2 x[R2];
+#pragma unroll
+        for (int t = 0; t < R2; ++t) x[t] = fb[R2 * s + t];
+        dft<R2, INV>(x);
+#pragma unroll
+        for (int t = 0; t < R2; ++t) fb[R2 * s + t] = x[t];
+    }
+}
+
+// Column stage 1 whose input is the exit wave w o S_j u read from global memory.
+template <int M>
+__device__ __forceinline__ void col_stage1_load(float2 *buf, const float2 *tw, int j0, int J,
+                                                const float2 *w_shared, const float2 *Wd,
+                                                const int32_t *frame_sub, const float2 *u,
+                                                const int32_t *frame_base, const int32_t *frame_pitch)
+{
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int P = M + 1;
+    for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
+        const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
+        if (j >= J) continue;
+        const float2 *w = Wd ? Wd + (size_t)frame_sub[j] * M * M : w_shared;
+        const float2 *uj = u + frame_base[j];
+        const int pitch = frame_pitch[j];
+        float2 x[R1];
+#pragma unroll
+        for (int t = 0; t < R1; ++t) {
+            const int row = n1 + R2 * t;
+            x[t] = cmul(__ldg(w + row * M + c), __ldg(uj + (size_t)row * pitch + c));
+        }
+        dft<R1, false>(x);
+        float2 *fb = buf + f * M * P;
+#pragma unroll
+        for (int s = 0; s < R1; ++s) fb[(n1 + R2 * s) * P + c] = cmul(x[s], tw[n1 * s]);
+    }
+}
+
+// Column stage 1^H writing natural-order frames to global memory, scaled by
+// `scale` and, when wconj is given, multiplied by conj(wconj).
+template <int M>
+__device__ __forceinline__ void col_stage1_store(float2 *buf, const float2 *tw, int j0, int J,
+                                                 float2 *out, float scale, const float2 *wconj)
+{
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int P = M + 1;
+    for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
+        const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
+        if (j >= J) continue;
+        float2 *fb = buf + f * M * P;
+        float2 x[R1];
+#pragma unroll
+        for (int s = 0; s < R1; ++s) x[s] = cmulc(fb[(n1 + R2 * s) * P + c], tw[n1 * s]);
+        dft<R1, true>(x);
+        float2 *o = out + (size_t)j * M * M;
+#pragma unroll
+        for (int t = 0; t < R1; ++t) {
+            const int row = n1 + R2 * t;
+            float2 v = cscale(x[t], scale);
+            if (wconj) v = cmulc(v, __ldg(wconj + row * M + c));
+            o[row * M + c] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ float block_sum_fixed(float v, float *red)
+{
+    // fixed-order reduction: xor butterflies inside each warp, then warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    return t;
+}
+
+struct ProxConst {
+    float lam, inv1plam, c_thr, c_k1;
+};
+
+// eq. (Prox_sol) with the threshold read as |y| < (eps - (1-eps)/lam) sqrt f.
+__device__ __forceinline__ float2 stagm_prox(float2 y, float sf, const ProxConst &k)
+{
+    const float ay = sqrtf(y.x * y.x + y.y * y.y);
+    float rho;
+    if (ay < k.c_thr * sf)
+        rho = fmaxf(0.f, k.c_k1 * ay);
+    else
+        rho = (sf + k.lam * ay) * k.inv1plam;
+    if (ay > 0.f) {
+        const float s = rho / ay;
+        return make_float2(y.x * s, y.y * s);
+    }
+    return make_float2(rho, 0.f);
+}
+
+ProxConst make_prox_const(float eps, float lam)
+{
+    ProxConst k;
+    k.lam = lam;
+    k.inv1plam = 1.f / (1.f + lam);
+    k.c_thr = eps - (1.f - eps) / lam;
+    k.c_k1 = k.c_thr > 0.f ? lam / (lam - (1.f - eps) / eps) : 0.f;
+    return k;
+}
+
+// ---------------------------------------------------------------- K1: fused frame update
+struct FrameArgs {
+    int32_t J;
+    const int32_t *frame_sub, *frame_base, *frame_pitch;
+    const float2 *u, *w, *Wd; // Wd non-null for blind plans (per-subdomain probe)
+    float2 *gamma;            // transposed position layout
+    const float *sqrtf_;      // transposed position layout
+    float2 *q;                // out: F^*(z - Gamma^{n+1}), natural spatial order
+    float *rf_part;           // out: one per block
+    const float2 *tw;
+    ProxConst pc;
+};
+
+template <int M>
+__global__ void __launch_bounds__(Radix<M>::NT, Radix<M>::MINB) frame_update_kernel(FrameArgs a)
+{
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int P = M + 1, MM = M * M;
+    extern __shared__ float4 smem4[];
+    float2 *tw = reinterpret_cast<float2 *>(smem4);
+    float2 *buf = tw + M;
+    float *red = reinterpret_cast<float *>(buf + FPB * M * P);
+    const int j0 = blockIdx.x * FPB;
+    {
+        // Gamma_j and sqrt(f_j) are first needed after three FFT stages: start
+        // moving this block's slices from HBM into L2 now, in 4 KiB pieces.
+        const int nf = min(FPB, a.J - j0);
+        const unsigned g_bytes = (unsigned)(nf * MM * sizeof(float2));
+        const unsigned f_bytes = (unsigned)(nf * MM * sizeof(float));
+        const char *gp = reinterpret_cast<const char *>(a.gamma + (size_t)j0 * MM);
+        const char *fp = reinterpret_cast<const char *>(a.sqrtf_ + (size_t)j0 * MM);
+        const unsigned n_g = (g_bytes + 4095) / 4096, n_f = (f_bytes + 4095) / 4096;
+        for (unsigned i = threadIdx.x; i < n_g + n_f; i += NT) {
+            const bool is_g = i < n_g;
+            const unsigned off = (is_g ? i : i - n_g) * 4096u;
+            const unsigned tot = is_g ? g_bytes : f_bytes;
+            bulk_prefetch_l2((is_g ? gp : fp) + off, min(4096u, tot - off));
+        }
+    }
+    for (int k = threadIdx.x; k < M; k += NT) tw[k] = a.tw[k];
+    __syncthreads();
+
+    // Step 1: psi = w o S_j u_d^n, then F psi (forward column stages)
+    col_stage1_load<M>(buf, tw, j0, a.J, a.w, a.Wd, a.frame_sub, a.u, a.frame_base, a.frame_pitch);
+    __syncthreads();
+    col_stage2<M, false>(buf);
+    __syncthreads();
+    row_stage1<M, false>(buf, tw);
+    __syncthreads();
+
+    // last forward stage, prox and Gamma update, first inverse stage -- in registers
+    float rf = 0.f;
+    const float inv_m = 1.f / (float)M;
+    for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
+        const int r = task % M, rest = task / M, s = rest % R1, f = rest / R1, j = j0 + f;
+        if (j >= a.J) continue;
+        float2 *fb = buf + f * M * P + r * P;
+        float2 x[R2];
+#pragma unroll
+        for (int t = 0; t < R2; ++t) x[t] = fb[R2 * s + t];
+        dft<R2, false>(x);
+        const size_t base = (size_t)j * MM + r;
+#pragma unroll
+        for (int t = 0; t < R2; ++t) {
+            const size_t idx = base + (size_t)(R2 * s + t) * M;
+            const float2 ax = cscale(x[t], inv_m);          // (A_d u_d^n)_k
+            const float sf = __ldg(a.sqrtf_ + idx);
+            const float2 g = a.gamma[idx];
+            rf += fabsf(sqrtf(ax.x * ax.x + ax.y * ax.y) - sf);
+            const float2 y = cadd(g, ax);                    // Gamma^n + A_d u_d^n
+            const float2 z = stagm_prox(y, sf, a.pc);         // eq. updateZ
+            const float2 gn = csub(y, z);                    // eq. updateM-1-multi
+            a.gamma[idx] = gn;
+            x[t] = csub(z, gn);                              // z^{n+1} - Gamma^{n+1}
+        }
+        dft<R2, true>(x);
+#pragma unroll
+        for (int t = 0; t < R2; ++t) fb[R2 * s + t] = x[t];
+    }
+    __syncthreads();
+    row_stage1<M, true>(buf, tw);
+    __syncthreads();
+    col_stage2<M, true>(buf);
+    __syncthreads();
+    col_stage1_store<M>(buf, tw, j0, a.J, a.q, inv_m, nullptr);
+    const float tot = block_sum_fixed(rf, red);
+    if (threadIdx.x == 0) a.rf_part[blockIdx.x] = tot;
+}
+
+// ---------------------------------------------------------------- forward operator
+template <int M>
+__global__ void __launch_bounds__(Radix<M>::NT) forward_kernel(int J, const int32_t *base,
+                                                                int pitch, const float2 *u,
+                                                                const float2 *w, float2 *out,
+                                                                const float2 *twg)
+{
+    constexpr int FPB = Radix<M>::FPB, NT = Radix<M>::NT, P = M + 1, MM = M * M;
+    extern __shared__ float4 smem4[];
+    float2 *tw = reinterpret_cast<float2 *>(smem4);
+    float2 *buf = tw + M;
+    const int j0 = blockIdx.x * FPB;
+    for (int k = threadIdx.x; k < M; k += NT) tw[k] = twg[k];
+    __syncthreads();
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2;
+    for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
+        const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
+        if (j >= J) continue;
+        const float2 *uj = u + base[j];
+        float2 x[R1];
+#pragma unroll
+        for (int t = 0; t < R1; ++t) {
+            const int row = n1 + R2 * t;
+            x[t] = cmul(__ldg(w + row * M + c), __ldg(uj + (size_t)row * pitch + c));
+        }
+        dft<R1, false>(x);
+        float2 *fb = buf + f * M * P;
+#pragma unroll
+        for (int s = 0; s < R1; ++s) fb[(n1 + R2 * s) * P + c] = cmul(x[s], tw[n1 * s]);
+    }
+    __syncthreads();
+    col_stage2<M, false>(buf);
+    __syncthreads();
+    row_stage1<M, false>(buf, tw);
+    __syncthreads();
+    row_stage2<M, false>(buf);
+    __syncthreads();
+    const float inv_m = 1.f / (float)M;
+    for (int e = threadIdx.x; e < FPB * MM; e += NT) {
+        const int f = e / MM, k = e % MM, j = j0 + f;
+        if (j >= J) continue;
+        const int kr = k / M, kc = k % M;
+        out[(size_t)j * MM + k] = cscale(buf[f * M * P + pos_of<M>(kr) * P + pos_of<M>(kc)], inv_m);
+    }
+}
+
+// ---------------------------------------------------------------- frames -> F^* frames, x conj(w)
+template <int M>
+__global__ void __launch_bounds__(Radix<M>::NT) ifft_weight_kernel(int J, const float2 *in,
+                                                                    const float2 *w, float2 *out,
+                                                                    const float2 *twg)
+{
+    constexpr int FPB = Radix<M>::FPB, NT = Radix<M>::NT, P = M + 1, MM = M * M;
+    extern __shared__ float4 smem4[];
+    float2 *tw = reinterpret_cast<float2 *>(smem4);
+    float2 *buf = tw + M;
+    const int j0 = blockIdx.x * FPB;
+    for (int k = threadIdx.x; k < M; k += NT) tw[k] = twg[k];
+    for (int e = threadIdx.x; e < FPB * MM; e += NT) {
+        const int f = e / MM, k = e % MM, j = j0 + f;
+        if (j >= J) continue;
+        buf[f * M * P + pos_of<M>(k / M) * P + pos_of<M>(k % M)] = __ldg(in + (size_t)j * MM + k);
+    }
+    __syncthreads();
+    row_stage2<M, true>(buf);
+    __syncthreads();
+    row_stage1<M, true>(buf, tw);
+    __syncthreads();
+    col_stage2<M, true>(buf);
+    __syncthreads();
+    col_stage1_store<M>(buf, tw, j0, J, out, 1.f / (float)M, w);
+}
+
+// ---------------------------------------------------------------- loss frames
+// h_j = F^* grad g(F(w o S_j u); f_j) (unweighted) and per-block loss partials.
+struct LossArgs {
+    int32_t J, pitch;
+    const int32_t *base;
+    const float2 *u, *w;
+    const float *sqrtf_;
+    float2 *h;
+    float *loss_part;
+    const float2 *tw;
+    float eps;
+};
+
+template <int M>
+__global__ void __launch_bounds__(Radix<M>::NT) loss_kernel(LossArgs a)
+{
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int P = M + 1, MM = M * M;
+    extern __shared__ float4 smem4[];
+    float2 *tw = reinterpret_cast<float2 *>(smem4);
+    float2 *buf = tw + M;
+    float *red = reinterpret_cast<float *>(buf + FPB * M * P);
+    const int j0 = blockIdx.x * FPB;
+    for (int k = threadIdx.x; k < M; k += NT) tw[k] = a.tw[k];
+    __syncthreads();
+    for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
+        const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
+        if (j >= a.J) continue;
+        const float2 *uj = a.u + a.base[j];
+        float2 x[R1];
+#pragma unroll
+        for (int t = 0; t < R1; ++t) {
+            const int row = n1 + R2 * t;
+            x[t] = cmul(__ldg(a.w + row * M + c), __ldg(uj + (size_t)row * a.pitch + c));
+        }
+        dft<R1, false>(x);
+        float2 *fb = buf + f * M * P;
+#pragma unroll
+        for (int s = 0; s < R1; ++s) fb[(n1 + R2 * s) * P + c] = cmul(x[s], tw[n1 * s]);
+    }
+    __syncthreads();
+    col_stage2<M, false>(buf);
+    __syncthreads();
+    row_stage1<M, false>(buf, tw);
+    __syncthreads();
+    float loss = 0.f;
+    const float inv_m = 1.f / (float)M;
+    const float eps = a.eps;
+    for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
+        const int r = task % M, rest = task / M, s = rest % R1, f = rest / R1, j = j0 + f;
+        if (j >= a.J) continue;
+        float2 *fb = buf + f * M * P + r * P;
+        float2 x[R2];
+#pragma unroll
+        for (int t = 0; t < R2; ++t) x[t] = fb[R2 * s + t];
+        dft<R2, false>(x);
+        const size_t base = (size_t)j * MM + r;
+#pragma unroll
+        for (int t = 0; t < R2; ++t) {
+            const size_t idx = base + (size_t)(R2 * s + t) * M;
+            const float2 xv = cscale(x[t], inv_m);
+            const float sf = __ldg(a.sqrtf_ + idx);
+            const float ax = sqrtf(xv.x * xv.x + xv.y * xv.y);
+            float gv, gs;  // g_eps (eq. obj-1) and grad g = gs * x (eq. objgrad)
+            if (ax < eps * sf) {
+                gv = 0.5f * (1.f - eps) * (sf * sf - ax * ax / eps);
+                gs = 1.f - 1.f / eps;
+            } else {
+                gv = 0.5f * (ax - sf) * (ax - sf);
+                gs = ax > 0.f ? 1.f - sf / ax : 0.f;
+            }
+            loss += gv;
+            x[t] = cscale(xv, gs);
+        }
+        dft<R2, true>(x);
+#pragma unroll
+        for (int t = 0; t < R2; ++t) fb[R2 * s + t] = x[t];
+    }
+    __syncthreads();
+    row_stage1<M, true>(buf, tw);
+    __syncthreads();
+    col_stage2<M, true>(buf);
+    __syncthreads();
+    col_stage1_store<M>(buf, tw, j0, a.J, a.h, inv_m, nullptr);
+    const float tot = block_sum_fixed(loss, red);
+    if (threadIdx.x == 0) a.loss_part[blockIdx.x] = tot;
+}
+
+// ---------------------------------------------------------------- blind w-update (eq. blind_w)
+// w^{n+1} = (1/D) F^* M F sum_d (Delta_d + W_d), one block; without a mask F^* F = I.
+template <int M>
+__global__ void __launch_bounds__(Radix<M>::NT) probe_avg_kernel(int D, const float2 *Wd,
+                                                                  const float2 *Delta,
+                                                                  const float *mask, float2 *wnew,
+                                                                  const float2 *twg)
+{
+    constexpr int NT = Radix<M>::NT, P = M + 1, MM = M * M;
+    extern __shared__ float4 smem4[];
+    float2 *tw = reinterpret_cast<float2 *>(smem4);
+    float2 *buf = tw + M;
+    const float invD = 1.f / (float)D;
+    if (!mask) {
+        for (int k = threadIdx.x; k < MM; k += NT) {
+            float2 t = make_float2(0.f, 0.f);
+            for (int d = 0; d < D; ++d) t = cadd(t, cadd(Delta[(size_t)d * MM + k], Wd[(size_t)d * MM + k]));
+            wnew[k] = cscale(t, invD);
+        }
+        return;
+    }
+    for (int k = threadIdx.x; k < M; k += NT) tw[k] = twg[k];
+    for (int k = threadIdx.x; k < MM; k += NT) {
+        float2 t = make_float2(0.f, 0.f);
+        for (int d = 0; d < D; ++d) t = cadd(t, cadd(Delta[(size_t)d * MM + k], Wd[(size_t)d * MM + k]));
+        buf[(k / M) * P + (k % M)] = t;
+    }
+    __syncthreads();
+    col_stage1<M, false>(buf, tw);
+    __syncthreads();
+    col_stage2<M, false>(buf);
+    __syncthreads();
+    row_stage1<M, false>(buf, tw);
+    __syncthreads();
+    row_stage2<M, false>(buf);
+    __syncthreads();
+    // position (pr, pc) holds frequency (kr, kc); apply the support mask there
+    for (int e = threadIdx.x; e < MM; e += NT) {
+        const int pr = e / M, pc = e % M;
+        const int kr = pr / Radix<M>::R2 + Radix<M>::R1 * (pr % Radix<M>::R2);
+        const int kc = pc / Radix<M>::R2 + Radix<M>::R1 * (pc % Radix<M>::R2);
+        buf[pr * P + pc] = cscale(buf[pr * P + pc], mask[kr * M + kc]);
+    }
+    __syncthreads();
+    row_stage2<M, true>(buf);
+    __syncthreads();
+    row_stage1<M, true>(buf, tw);
+    __syncthreads();
+    col_stage2<M, true>(buf);
+    __syncthreads();
+    col_stage1<M, true>(buf, tw);
+    __syncthreads();
+    const float s = invD / (float)MM;  // two unitary 1/M factors and the 1/D average
+    for (int k = threadIdx.x; k < MM; k += NT) wnew[k] = cscale(buf[(k / M) * P + (k % M)], s);
+}
+
+// ---------------------------------------------------------------- layout conversions
+// f (natural) -> sqrt(max(f,0)) in transposed position layout; per-frame partial sums of sqrt f.
+template <int M>
+__global__ void ingest_f_kernel(int J, const float *f, float *sqrtf_, float *part)
+{
+    constexpr int MM = M * M;
+    __shared__ float red[32];
+    const int j = blockIdx.x;
+    float acc = 0.f;
+    for (int k = threadIdx.x; k < MM; k += blockDim.x) {
+        const float v = sqrtf(fmaxf(__ldg(f + (size_t)j * MM + k), 0.f));
+        sqrtf_[(size_t)j * MM + (size_t)pos_of<M>(k % M) * M + pos_of<M>(k / M)] = v;
+        acc += v;
+    }
+    const float tot = block_sum_fixed(acc, red);
+    if (threadIdx.x == 0) part[j] = tot;
+}
+
+template <int M>
+__global__ void permute_kernel(int J, const float2 *src, float2 *dst, bool to_natural)
+{
+    constexpr int MM = M * M;
+    const size_t n = (size_t)J * MM;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t j = e / MM;
+        const int k = (int)(e % MM);
+        const size_t t = j * MM + (size_t)pos_of<M>(k % M) * M + pos_of<M>(k / M);
+        if (to_natural)
+            dst[e] = src[t];
+        else
+            dst[t] = src[e];
+    }
+}
+
+template <int M, class K>
+int set_smem(K kernel)
+{
+    static bool done = false;
+    if (!done) {
+        OD2P_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<M>()));
+        done = true;
+    }
+    return PTYCHO_OK;
+}
+
+template <int M>
+int frame_update_m(ptycho_plan_s *p, cudaStream_t s)
+{
+    if (int rc = set_smem<M>(frame_update_kernel<M>)) return rc;
+    FrameArgs a;
+    a.J = p->J;
+    a.frame_sub = p->d_frame_sub;
+    a.frame_base = p->d_frame_base;
+    a.frame_pitch = p->d_frame_pitch;
+    a.u = p->d_u[p->cur];
+    a.w = p->d_w;
+    a.Wd = p->blind ? p->d_Wd : nullptr;
+    a.gamma = p->d_gamma;
+    a.sqrtf_ = p->d_sqrtf;
+    a.q = p->d_q;
+    a.rf_part = p->d_rf_part;
+    a.tw = p->d_tw;
+    a.pc = make_prox_const(p->eps, p->eta);
+    const int blocks = (p->J + Radix<M>::FPB - 1) / Radix<M>::FPB;
+    frame_update_kernel<M><<<blocks, Radix<M>::NT, smem_bytes<M>(), s>>>(a);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+template <int M>
+int forward_m(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out, cudaStream_t s)
+{
+    if (int rc = set_smem<M>(forward_kernel<M>)) return rc;
+    const int blocks = (p->J + Radix<M>::FPB - 1) / Radix<M>::FPB;
+    forward_kernel<M><<<blocks, Radix<M>::NT, smem_bytes<M>(), s>>>(p->J, p->d_img_base, p->W, u, w,
+                                                                     out, p->d_tw);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+template <int M>
+int ifft_m(const ptycho_plan_s *p, const float2 *in, const float2 *w, float2 *out, cudaStream_t s)
+{
+    if (int rc = set_smem<M>(ifft_weight_kernel<M>)) return rc;
+    const int blocks = (p->J + Radix<M>::FPB - 1) / Radix<M>::FPB;
+    ifft_weight_kernel<M><<<blocks, Radix<M>::NT, smem_bytes<M>(), s>>>(p->J, in, w, out, p->d_tw);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+template <int M>
+int loss_m(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s)
+{
+    if (int rc = set_smem<M>(loss_kernel<M>)) return rc;
+    LossArgs a;
+    a.J = p->J;
+    a.pitch = p->W;
+    a.base = p->d_img_base;
+    a.u = u;
+    a.w = w;
+    a.sqrtf_ = p->d_sqrtf;
+    a.h = p->d_q;
+    a.loss_part = p->d_loss_part;
+    a.tw = p->d_tw;
+    a.eps = p->eps;
+    const int blocks = (p->J + Radix<M>::FPB - 1) / Radix<M>::FPB;
+    loss_kernel<M><<<blocks, Radix<M>::NT, smem_bytes<M>(), s>>>(a);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+template <int M>
+int probe_avg_m(ptycho_plan_s *p, cudaStream_t s)
+{
+    if (int rc = set_smem<M>(probe_avg_kernel<M>)) return rc;
+    probe_avg_kernel<M><<<1, Radix<M>::NT, smem_bytes<M>(), s>>>(
+        p->D, p->d_Wd, p->d_Delta, p->has_mask ? p->d_mask : nullptr, p->d_wnew, p->d_tw);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+template <int M>
+int ingest_m(ptycho_plan_s *p, const float *f, float *part, cudaStream_t s)
+{
+    ingest_f_kernel<M><<<p->J, 256, 0, s>>>(p->J, f, p->d_sqrtf, part);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+template <int M>
+int permute_m(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_nat, cudaStream_t s)
+{
+    const size_t n = (size_t)p->J * M * M;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+    permute_kernel<M><<<blocks, 256, 0, s>>>(p->J, src, dst, to_nat);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+}  // namespace
+
+bool supported_m(int m) { return m == 16 || m == 32 || m == 64 || m == 128; }
+
+int frames_per_block(int m)
+{
+    switch (m) {
+    case 16: return Radix<16>::FPB;
+    case 32: return Radix<32>::FPB;
+    case 64: return Radix<64>::FPB;
+    default: return Radix<128>::FPB;
+    }
+}
+
+namespace {
+template <int M>
+int prepare_m()
+{
+    if (int rc = set_smem<M>(frame_update_kernel<M>)) return rc;
+    if (int rc = set_smem<M>(forward_kernel<M>)) return rc;
+    if (int rc = set_smem<M>(ifft_weight_kernel<M>)) return rc;
+    if (int rc = set_smem<M>(loss_kernel<M>)) return rc;
+    return set_smem<M>(probe_avg_kernel<M>);
+}
+}  // namespace
+
+// Raise the dynamic shared-memory limit of every frame kernel of size m once,
+// outside any stream capture.
+int prepare_kernels(int m)
+{
+    switch (m) {
+    case 16: return prepare_m<16>();
+    case 32: return prepare_m<32>();
+    case 64: return prepare_m<64>();
+    case 128: return prepare_m<128>();
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    }
+}
+
+int launch_frame_update(ptycho_plan_s *p, cudaStream_t s)
+{
+    switch (p->M) {
+    case 16: return frame_update_m<16>(p, s);
+    case 32: return frame_update_m<32>(p, s);
+    case 64: return frame_update_m<64>(p, s);
+    case 128: return frame_update_m<128>(p, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    }
+}
+
+int launch_forward(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out, cudaStream_t s)
+{
+    switch (p->M) {
+    case 16: return forward_m<16>(p, u, w, out, s);
+    case 32: return forward_m<32>(p, u, w, out, s);
+    case 64: return forward_m<64>(p, u, w, out, s);
+    case 128: return forward_m<128>(p, u, w, out, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    }
+}
+
+int launch_frames_ifft_weight(const ptycho_plan_s *p, const float2 *frames, const float2 *w,
+                              bool ifft, float2 *out, cudaStream_t s)
+{
+    if (!ifft) return fail(PTYCHO_ERR_STATE, "internal: spatial frames need no transform");
+    switch (p->M) {
+    case 16: return ifft_m<16>(p, frames, w, out, s);
+    case 32: return ifft_m<32>(p, frames, w, out, s);
+    case 64: return ifft_m<64>(p, frames, w, out, s);
+    case 128: return ifft_m<128>(p, frames, w, out, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    }
+}
+
+int launch_loss_frames(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s)
+{
+    switch (p->M) {
+    case 16: return loss_m<16>(p, u, w, s);
+    case 32: return loss_m<32>(p, u, w, s);
+    case 64: return loss_m<64>(p, u, w, s);
+    case 128: return loss_m<128>(p, u, w, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    }
+}
+
+int launch_probe_avg(ptycho_plan_s *p, cudaStream_t s)
+{
+    switch (p->M) {
+    case 16: return probe_avg_m<16>(p, s);
+    case 32: return probe_avg_m<32>(p, s);
+    case 64: return probe_avg_m<64>(p, s);
+    case 128: return probe_avg_m<128>(p, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    }
+}
+
+int launch_ingest_f(ptycho_plan_s *p, const float *f, cudaStream_t s)
+{
+    float *part = p->d_loss_part;  // J floats of scratch, reduced in launch_sum_sqrtf
+    switch (p->M) {
+    case 16: return ingest_m<16>(p, f, part, s);
+    case 32: return ingest_m<32>(p, f, part, s);
+    case 64: return ingest_m<64>(p, f, part, s);
+    case 128: return ingest_m<128>(p, f, part, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    }
+}
+
+int launch_permute_gamma(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_natural,
+                         cudaStream_t s)
+{
+    switch (p->M) {
+    case 16: return permute_m<16>(p, src, dst, to_natural, s);
+    case 32: return permute_m<32>(p, src, dst, to_natural, s);
+    case 64: return permute_m<64>(p, src, dst, to_natural, s);
+    case 128: return permute_m<128>(p, src, dst, to_natural, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    }
+}
+
+}  // namespace od2p

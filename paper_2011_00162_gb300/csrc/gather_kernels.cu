@@ -1,0 +1,492 @@
+// Image-space kernels of the OD2P library for sm_103a: the deterministic
+// gather-form overlap-add fused with the consensus v, u and Lambda updates
+// (Algorithm 2 Steps 1 (v), 3 and 4; Algorithm 3 Steps 4 and 5), the image
+// gather of the adjoint, the fixed-order probe reductions of the blind
+// W-update (Algorithm 3 Step 3) and of grad_w, and small helpers.
+//
+// Determinism: every pixel sums the frames covering it in ascending j (the
+// per-tile frame lists are ascending), every reduction runs in a fixed order,
+// and no kernel uses atomics, so repeated runs are bitwise identical.
+#include "od2p_internal.h"
+
+namespace od2p {
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// conj(a) * b
+__device__ __forceinline__ float2 cconjmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+
+__device__ __forceinline__ void block_sum2_fixed(float &a, float &b, float *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[2 * warp] = a;
+        red[2 * warp + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float ta = 0.f, tb = 0.f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            ta += red[2 * i];
+            tb += red[2 * i + 1];
+        }
+        a = ta;
+        b = tb;
+    }
+}
+
+// ---------------------------------------------------------------- K2: subdomain update
+struct SubArgs {
+    int32_t M;
+    const int32_t *offs, *rect, *nbr_ptr, *nbr, *pair_rect;
+    const int64_t *u_off, *lam_off;
+    const Tile *tiles;
+    const int32_t *tptr, *tlist;
+    const float2 *u_cur, *lam_cur, *q, *w, *Wd;
+    float2 *u_next, *lam_next;
+    float eta, r, gamma;
+    int32_t blind;
+    float *re_part;
+};
+
+// Largest per-tile frame list staged in shared memory; longer lists stream
+// the remainder from global memory in the same ascending order.
+constexpr int LIST_SMEM = 128;
+
+__global__ void __launch_bounds__(GATHER_THREADS) subdomain_update_kernel(SubArgs a)
+{
+    __shared__ float red[2 * (GATHER_THREADS / 32)];
+    __shared__ int3 lst[LIST_SMEM];  // (j, row offset, col offset) of the tile's frames
+    const Tile tile = a.tiles[blockIdx.x];
+    const int d = tile.reg;
+    const int32_t *rc = a.rect + 4 * d;
+    const int hd = rc[2] - rc[0], wd = rc[3] - rc[1];
+    const int lr = tile.r0 + threadIdx.x / TILE_W, lc = tile.c0 + threadIdx.x % TILE_W;
+    const bool active = lr < hd && lc < wd;
+    const int R = rc[0] + lr, C = rc[1] + lc;
+    const int M = a.M, MM = M * M;
+    const int k0 = a.tptr[blockIdx.x], nk = a.tptr[blockIdx.x + 1] - k0;
+    for (int i = threadIdx.x; i < min(nk, LIST_SMEM); i += GATHER_THREADS) {
+        const int j = a.tlist[k0 + i];
+        lst[i] = make_int3(j, a.offs[2 * j], a.offs[2 * j + 1]);
+    }
+    __syncthreads();
+    float dn = 0.f, nn = 0.f;
+    if (active) {
+        // A_d^*(z - Gamma) and sum_j S_j^T |w|^2 at this pixel, frames in ascending j
+        const float2 *w = a.blind ? a.Wd + (size_t)d * MM : a.w;
+        float2 acc = make_float2(0.f, 0.f);
+        float nrm = 0.f;
+        constexpr int U = 4;  // loads of U frames in flight; accumulation stays in order
+        for (int k = 0; k < nk; k += U) {
+            float2 qv[U], wv[U];
+            bool hit[U];
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                hit[t] = false;
+                if (k + t < nk) {
+                    const int3 e = k + t < LIST_SMEM ? lst[k + t]
+                                                     : make_int3(a.tlist[k0 + k + t], a.offs[2 * a.tlist[k0 + k + t]],
+                                                                 a.offs[2 * a.tlist[k0 + k + t] + 1]);
+                    const int dr = R - e.y, dc = C - e.z;
+                    if ((unsigned)dr < (unsigned)M && (unsigned)dc < (unsigned)M) {
+                        hit[t] = true;
+                        wv[t] = __ldg(w + dr * M + dc);
+                        qv[t] = __ldg(a.q + (size_t)e.x * MM + dr * M + dc);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < U; ++t)
+                if (hit[t]) {
+                    acc = cadd(acc, cconjmul(wv[t], qv[t]));
+                    nrm += cabs2(wv[t]);
+                }
+        }
+        const int64_t ui = a.u_off[d] + (int64_t)lr * wd + lc;
+        const float2 u_old = a.u_cur[ui];
+        float2 num = cscale(acc, a.eta);
+        float den = a.eta * nrm;
+        // consensus v_{d,e} (eq. updateV-multi) and the r-terms of the u-update
+        for (int i = a.nbr_ptr[d]; i < a.nbr_ptr[d + 1]; ++i) {
+            const int e = a.nbr[3 * i], kde = a.nbr[3 * i + 1], ked = a.nbr[3 * i + 2];
+            const int32_t *re = a.rect + 4 * e;
+            if (R < re[0] || R >= re[2] || C < re[1] || C >= re[3]) continue;
+            const float2 ue = a.u_cur[a.u_off[e] + (int64_t)(R - re[0]) * (re[3] - re[1]) + (C - re[1])];
+            const int32_t *pr = a.pair_rect + 4 * kde;
+            const int64_t li = (int64_t)(R - pr[0]) * (pr[3] - pr[1]) + (C - pr[1]);
+            const float2 lde = a.lam_cur[a.lam_off[kde] + li], led = a.lam_cur[a.lam_off[ked] + li];
+            // same operand order on both sides of the pair -> bitwise equal v
+            const float2 v = d < e ? cscale(cadd(cadd(u_old, ue), cadd(lde, led)), 0.5f)
+                                   : cscale(cadd(cadd(ue, u_old), cadd(led, lde)), 0.5f);
+            num = cadd(num, cscale(csub(v, lde), a.r));
+            den += a.r;
+        }
+        if (a.blind) {
+            num = cadd(num, cscale(u_old, a.gamma));
+            den += a.gamma;
+        }
+        // eq. Alg1-solver-u; a pixel with no illumination and no overlap keeps its value
+        const float2 u_new = den > 0.f ? make_float2(num.x / den, num.y / den) : u_old;
+        a.u_next[ui] = u_new;
+        // eq. updateM-2-multi: Lambda_{d,e} += pi u_d^{n+1} - v
+        for (int i = a.nbr_ptr[d]; i < a.nbr_ptr[d + 1]; ++i) {
+            const int e = a.nbr[3 * i], kde = a.nbr[3 * i + 1], ked = a.nbr[3 * i + 2];
+            const int32_t *re = a.rect + 4 * e;
+            if (R < re[0] || R >= re[2] || C < re[1] || C >= re[3]) continue;
+            const float2 ue = a.u_cur[a.u_off[e] + (int64_t)(R - re[0]) * (re[3] - re[1]) + (C - re[1])];
+            const int32_t *pr = a.pair_rect + 4 * kde;
+            const int64_t li = (int64_t)(R - pr[0]) * (pr[3] - pr[1]) + (C - pr[1]);
+            const float2 lde = a.lam_cur[a.lam_off[kde] + li], led = a.lam_cur[a.lam_off[ked] + li];
+            const float2 v = d < e ? cscale(cadd(cadd(u_old, ue), cadd(lde, led)), 0.5f)
+                                   : cscale(cadd(cadd(ue, u_old), cadd(led, lde)), 0.5f);
+            a.lam_next[a.lam_off[kde] + li] = csub(cadd(lde, u_new), v);
+        }
+        dn = cabs2(csub(u_new, u_old));
+        nn = cabs2(u_new);
+    }
+    block_sum2_fixed(dn, nn, red);
+    if (threadIdx.x == 0) {
+        a.re_part[2 * blockIdx.x] = dn;
+        a.re_part[2 * blockIdx.x + 1] = nn;
+    }
+}
+
+// ---------------------------------------------------------------- image gather
+// out(p) = sum_{j covering p, ascending} (w ? conj(w(p - o_j)) : 1) * h_j(p - o_j)
+__global__ void __launch_bounds__(GATHER_THREADS) image_gather_kernel(
+    int M, int H, int W, const int32_t *offs, const Tile *tiles, const int32_t *tptr,
+    const int32_t *tlist, const float2 *h, const float2 *w, float2 *out)
+{
+    const Tile tile = tiles[blockIdx.x];
+    const int R = tile.r0 + threadIdx.x / TILE_W, C = tile.c0 + threadIdx.x % TILE_W;
+    if (R >= H || C >= W) return;
+    const int MM = M * M;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = tptr[blockIdx.x]; k < tptr[blockIdx.x + 1]; ++k) {
+        const int j = tlist[k];
+        const int dr = R - offs[2 * j], dc = C - offs[2 * j + 1];
+        if ((unsigned)dr < (unsigned)M && (unsigned)dc < (unsigned)M) {
+            const float2 hv = __ldg(h + (size_t)j * MM + dr * M + dc);
+            acc = cadd(acc, w ? cconjmul(__ldg(w + dr * M + dc), hv) : hv);
+        }
+    }
+    out[(size_t)R * W + C] = acc;
+}
+
+// ---------------------------------------------------------------- probe reductions
+// Level 1: per chunk of PROBE_CHUNK frames of one group, for every probe pixel k:
+//   part[c][k] = sum_{j in chunk, ascending} conj(u(o_j + k)) h_j(k), part_n = sum |u(o_j + k)|^2.
+struct ProbeArgs {
+    int32_t M;
+    const int4 *chunks;          // (group, begin, end, -) into group_frames
+    const int32_t *group_frames; // frame ids, ascending within each group
+    const int32_t *frame_base;   // index of the window origin in u
+    const int32_t *frame_pitch;  // per-frame pitch, or null for `pitch`
+    int32_t pitch;
+    const float2 *u, *h;
+    float2 *part;
+    float *part_n;
+};
+
+__global__ void probe_partial_kernel(ProbeArgs a)
+{
+    const int MM = a.M * a.M;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= MM) return;
+    const int4 ch = a.chunks[blockIdx.y];
+    const int kr = k / a.M, kc = k % a.M;
+    float2 acc = make_float2(0.f, 0.f);
+    float nn = 0.f;
+    for (int t = ch.y; t < ch.z; ++t) {
+        const int j = a.group_frames[t];
+        const int pitch = a.frame_pitch ? a.frame_pitch[j] : a.pitch;
+        const float2 uv = __ldg(a.u + a.frame_base[j] + (size_t)kr * pitch + kc);
+        acc = cadd(acc, cconjmul(uv, __ldg(a.h + (size_t)j * MM + k)));
+        nn += cabs2(uv);
+    }
+    a.part[(size_t)blockIdx.y * MM + k] = acc;
+    a.part_n[(size_t)blockIdx.y * MM + k] = nn;
+}
+
+// Level 2 (blind, eqs. blind_W and admm_Delta): per subdomain d and pixel k,
+// N = sum of its chunks in order, Dn likewise;
+// W_d = (eta N + mu (w^{n+1} - Delta_d)) / (eta Dn + mu); Delta_d += W_d - w^{n+1}.
+__global__ void probe_finalize_blind_kernel(int M, int D, const int32_t *group_chunk_ptr,
+                                            const float2 *part, const float *part_n,
+                                            const float2 *wnew, float2 *Wd, float2 *Delta,
+                                            float eta, float mu)
+{
+    const int MM = M * M;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.y;
+    if (k >= MM || d >= D) return;
+    float2 N = make_float2(0.f, 0.f);
+    float Dn = 0.f;
+    for (int c = group_chunk_ptr[d]; c < group_chunk_ptr[d + 1]; ++c) {
+        N = cadd(N, part[(size_t)c * MM + k]);
+        Dn += part_n[(size_t)c * MM + k];
+    }
+    const float2 wn = wnew[k];
+    const float2 dl = Delta[(size_t)d * MM + k];
+    const float den = eta * Dn + mu;
+    const float2 num = cadd(cscale(N, eta), cscale(csub(wn, dl), mu));
+    const float2 Wn = make_float2(num.x / den, num.y / den);
+    Wd[(size_t)d * MM + k] = Wn;
+    Delta[(size_t)d * MM + k] = cadd(dl, csub(Wn, wn));
+}
+
+__global__ void probe_finalize_sum_kernel(int M, int n_chunks, const float2 *part, float2 *out)
+{
+    const int MM = M * M;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= MM) return;
+    float2 N = make_float2(0.f, 0.f);
+    for (int c = 0; c < n_chunks; ++c) N = cadd(N, part[(size_t)c * MM + k]);
+    out[k] = N;
+}
+
+// ---------------------------------------------------------------- scalars
+__global__ void metrics_kernel(int n_rf, const float *rf_part, int D, const int32_t *reg_tile_ptr,
+                               const float *re_part, double *metrics)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double rf = 0.0;
+    for (int i = 0; i < n_rf; ++i) rf += rf_part[i];
+    metrics[0] = metrics[2] > 0.0 ? rf / metrics[2] : 0.0;
+    double re = 0.0;
+    for (int d = 0; d < D; ++d) {
+        double dn = 0.0, nn = 0.0;
+        for (int t = reg_tile_ptr[d]; t < reg_tile_ptr[d + 1]; ++t) {
+            dn += re_part[2 * t];
+            nn += re_part[2 * t + 1];
+        }
+        const double v = nn > 0.0 ? sqrt(dn / nn) : 0.0;
+        re = v > re ? v : re;
+    }
+    metrics[1] = re;
+}
+
+__global__ void sum_kernel(int n, const float *part, double *dst)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += part[i];
+    *dst = t;
+}
+
+__global__ void loss_sum_kernel(int n, const float *part, float *loss)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += part[i];
+    *loss = (float)t;
+}
+
+// u_d = R_d u0 (or 1), over the subdomain tiles
+__global__ void init_u_kernel(const Tile *tiles, const int32_t *rect, const int64_t *u_off, int W,
+                              const float2 *u0, float2 *u)
+{
+    const Tile tile = tiles[blockIdx.x];
+    const int d = tile.reg;
+    const int32_t *rc = rect + 4 * d;
+    const int hd = rc[2] - rc[0], wd = rc[3] - rc[1];
+    const int lr = tile.r0 + threadIdx.x / TILE_W, lc = tile.c0 + threadIdx.x % TILE_W;
+    if (lr >= hd || lc >= wd) return;
+    u[u_off[d] + (int64_t)lr * wd + lc] =
+        u0 ? u0[(size_t)(rc[0] + lr) * W + (rc[1] + lc)] : make_float2(1.f, 0.f);
+}
+
+__global__ void broadcast_probe_kernel(int MM, int D, const float2 *w0, float2 *w, float2 *Wd)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= MM) return;
+    const float2 v = w0[k];
+    w[k] = v;
+    if (Wd)
+        for (int d = 0; d < D; ++d) Wd[(size_t)d * MM + k] = v;
+}
+
+// section 4: overlaps averaged, single-subdomain pixels kept
+__global__ void merge_kernel(int H, int W, int D, const int32_t *rect, const int64_t *u_off,
+                             const float2 *u, float2 *out)
+{
+    const size_t n = (size_t)H * W;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int R = (int)(e / W), C = (int)(e % W);
+        float2 t = make_float2(0.f, 0.f);
+        int cnt = 0;
+        for (int d = 0; d < D; ++d) {
+            const int32_t *rc = rect + 4 * d;
+            if (R < rc[0] || R >= rc[2] || C < rc[1] || C >= rc[3]) continue;
+            t = cadd(t, u[u_off[d] + (int64_t)(R - rc[0]) * (rc[3] - rc[1]) + (C - rc[1])]);
+            ++cnt;
+        }
+        out[e] = cnt ? make_float2(t.x / cnt, t.y / cnt) : make_float2(1.f, 0.f);
+    }
+}
+
+__global__ void prox_kernel(const float2 *y, const float *f, float2 *z, int64_t n, float lam,
+                            float inv1plam, float c_thr, float c_k1)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 yv = y[i];
+        const float sf = sqrtf(fmaxf(f[i], 0.f));
+        const float ay = sqrtf(yv.x * yv.x + yv.y * yv.y);
+        float rho;
+        if (ay < c_thr * sf)
+            rho = fmaxf(0.f, c_k1 * ay);
+        else
+            rho = (sf + lam * ay) * inv1plam;
+        float2 out;
+        if (ay > 0.f) {
+            const float s = rho / ay;
+            out = make_float2(yv.x * s, yv.y * s);
+        } else {
+            out = make_float2(rho, 0.f);
+        }
+        z[i] = out;
+    }
+}
+
+}  // namespace
+
+int launch_subdomain_update(ptycho_plan_s *p, cudaStream_t s)
+{
+    SubArgs a;
+    a.M = p->M;
+    a.offs = p->d_offs;
+    a.rect = p->d_rect;
+    a.nbr_ptr = p->d_nbr_ptr;
+    a.nbr = p->d_nbr;
+    a.pair_rect = p->d_pair_rect;
+    a.u_off = p->d_u_off;
+    a.lam_off = p->d_lam_off;
+    a.tiles = p->sub_tiles.tiles;
+    a.tptr = p->sub_tiles.ptr;
+    a.tlist = p->sub_tiles.list;
+    a.u_cur = p->d_u[p->cur];
+    a.lam_cur = p->d_lam[p->cur];
+    a.u_next = p->d_u[1 - p->cur];
+    a.lam_next = p->d_lam[1 - p->cur];
+    a.q = p->d_q;
+    a.w = p->d_w;
+    a.Wd = p->d_Wd;
+    a.eta = p->eta;
+    a.r = p->r;
+    a.gamma = p->gamma;
+    a.blind = p->blind;
+    a.re_part = p->d_re_part;
+    subdomain_update_kernel<<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(a);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w, float2 *out,
+                        cudaStream_t s)
+{
+    image_gather_kernel<<<p->img_tiles.n_tiles, GATHER_THREADS, 0, s>>>(
+        p->M, p->H, p->W, p->d_offs, p->img_tiles.tiles, p->img_tiles.ptr, p->img_tiles.list, q, w, out);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+// grad_w == nullptr: blind W-update over the subdomain groups (u = current
+// subdomain buffer, h = d_q).  Otherwise: grad_w = sum over all frames of
+// conj(S_j u_img) h_j (one group).
+int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, cudaStream_t s)
+{
+    const od2p::ProbeGroups &G = grad_w ? p->img_groups : p->sub_groups;
+    ProbeArgs a;
+    a.M = p->M;
+    a.chunks = G.chunks;
+    a.group_frames = G.frames;
+    a.frame_base = grad_w ? p->d_img_base : p->d_frame_base;
+    a.frame_pitch = grad_w ? nullptr : p->d_frame_pitch;
+    a.pitch = p->W;
+    a.u = grad_w ? u_img : p->d_u[p->cur];
+    a.h = p->d_q;
+    a.part = p->d_probe_part;
+    a.part_n = p->d_probe_part_n;
+    const int MM = p->MM;
+    if (G.n_chunks > 0) {
+        dim3 grid((MM + 255) / 256, G.n_chunks);
+        probe_partial_kernel<<<grid, 256, 0, s>>>(a);
+        OD2P_CUDA(cudaGetLastError());
+    }
+    if (grad_w) {
+        probe_finalize_sum_kernel<<<(MM + 255) / 256, 256, 0, s>>>(p->M, G.n_chunks, p->d_probe_part, grad_w);
+    } else {
+        dim3 grid((MM + 255) / 256, p->D);
+        probe_finalize_blind_kernel<<<grid, 256, 0, s>>>(p->M, p->D, G.chunk_ptr, p->d_probe_part,
+                                                         p->d_probe_part_n, p->d_wnew, p->d_Wd,
+                                                         p->d_Delta, p->eta, p->mu);
+    }
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s)
+{
+    loss_sum_kernel<<<1, 32, 0, s>>>(p->n_k1_blocks, p->d_loss_part, loss);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_metrics(ptycho_plan_s *p, cudaStream_t s)
+{
+    metrics_kernel<<<1, 32, 0, s>>>(p->n_k1_blocks, p->d_rf_part, p->D, p->sub_tiles.reg_ptr,
+                                    p->d_re_part, p->d_metrics);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_sum_sqrtf(ptycho_plan_s *p, cudaStream_t s)
+{
+    sum_kernel<<<1, 32, 0, s>>>(p->J, p->d_loss_part, p->d_metrics + 2);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_init_state(ptycho_plan_s *p, const float2 *u0, const float2 *w0, cudaStream_t s)
+{
+    init_u_kernel<<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(p->sub_tiles.tiles, p->d_rect,
+                                                                  p->d_u_off, p->W, u0, p->d_u[p->cur]);
+    OD2P_CUDA(cudaGetLastError());
+    broadcast_probe_kernel<<<(p->MM + 255) / 256, 256, 0, s>>>(p->MM, p->D, w0, p->d_w,
+                                                                p->blind ? p->d_Wd : nullptr);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_merge(const ptycho_plan_s *p, float2 *out, cudaStream_t s)
+{
+    merge_kernel<<<152 * 8, 256, 0, s>>>(p->H, p->W, p->D, p->d_rect, p->d_u_off, p->d_u[p->cur], out);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_prox(const float2 *y, const float *f, float2 *z, int64_t n, float eps, float lam,
+                cudaStream_t s)
+{
+    const float c_thr = eps - (1.f - eps) / lam;
+    const float c_k1 = c_thr > 0.f ? lam / (lam - (1.f - eps) / eps) : 0.f;
+    const int64_t blocks = (n + 255) / 256;
+    prox_kernel<<<(int)(blocks < 152 * 32 ? blocks : 152 * 32), 256, 0, s>>>(
+        y, f, z, n, lam, 1.f / (1.f + lam), c_thr, c_k1);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+}  // namespace od2p

@@ -1,0 +1,131 @@
+// Internal declarations of the sm_103a OD2P library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/od2p.h"
+
+namespace od2p {
+
+// Thread block tile of the gather kernels: TILE_H rows x TILE_W columns,
+// one thread per pixel, lanes along the row so that frame rows load coalesced.
+constexpr int TILE_H = 8;
+constexpr int TILE_W = 32;
+constexpr int GATHER_THREADS = TILE_H * TILE_W;
+// Frames per chunk of the fixed-order probe reductions (blind W, grad w).
+constexpr int PROBE_CHUNK = 32;
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define OD2P_CUDA(call)                                                     \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return ::od2p::cuda_fail(e_, #call);         \
+    } while (0)
+
+// Tile of a gather: pixel block [r0, r0+TILE_H) x [c0, c0+TILE_W) of region
+// `reg` (a subdomain, or the whole image), and the frames that intersect it
+// in ascending j: list[ptr_begin, ptr_end).
+struct Tile {
+    int32_t reg, r0, c0, pad;
+};
+
+struct GatherTiles {
+    int32_t n_tiles = 0;
+    Tile *tiles = nullptr;        // device
+    int32_t *ptr = nullptr;       // device, n_tiles + 1
+    int32_t *list = nullptr;      // device
+    int32_t *reg_ptr = nullptr;   // device, first tile of each region (+ end)
+};
+
+// Frame groups of the fixed-order probe reductions, cut into chunks of
+// PROBE_CHUNK frames: chunk c covers frames[begin, end) of group `group`.
+struct ProbeGroups {
+    int32_t n_groups = 0, n_chunks = 0;
+    int32_t *frames = nullptr;    // device, frame ids ascending within a group
+    int4 *chunks = nullptr;       // device, (group, begin, end, 0)
+    int32_t *chunk_ptr = nullptr; // device, first chunk of each group (+ end)
+};
+
+}  // namespace od2p
+
+struct ptycho_plan_s {
+    // ---- problem
+    int32_t H = 0, W = 0, M = 0, MM = 0, J = 0, D = 0, P = 0;
+    int32_t sub_rows = 0, sub_cols = 0, overlap_px = 0;
+    float eps = 0, eta = 0, r = 0, mu = 0, gamma = 0;
+    int32_t blind = 0;
+    bool has_mask = false;
+    // ---- host copies of the decomposition
+    std::vector<int32_t> offs, frame_sub, rect, pair, pair_rect;
+    std::vector<int64_t> u_off, lam_off;
+    int64_t u_len = 0, lam_len = 0;
+    // ---- device geometry
+    int32_t *d_offs = nullptr, *d_frame_sub = nullptr, *d_frame_base = nullptr,
+            *d_frame_pitch = nullptr, *d_rect = nullptr, *d_nbr_ptr = nullptr, *d_nbr = nullptr,
+            *d_pair_rect = nullptr, *d_img_base = nullptr;  // nbr: (e, pair d-e, pair e-d) per neighbour
+    int64_t *d_u_off = nullptr, *d_lam_off = nullptr;
+    od2p::GatherTiles sub_tiles, img_tiles;
+    od2p::ProbeGroups sub_groups, img_groups;
+    float2 *d_tw = nullptr;        // M twiddles exp(-2 pi i k / M)
+    float *d_mask = nullptr;       // M*M Fourier support (blind), or null
+    // ---- device state (Gamma and sqrt f in the frame kernel's transposed layout)
+    float *d_sqrtf = nullptr;      // J*MM
+    float2 *d_gamma = nullptr;     // J*MM
+    float2 *d_q = nullptr;         // J*MM frame residuals / scratch
+    float2 *d_u[2] = {nullptr, nullptr};
+    float2 *d_lam[2] = {nullptr, nullptr};
+    float2 *d_w = nullptr, *d_wnew = nullptr, *d_Wd = nullptr, *d_Delta = nullptr;
+    float2 *d_probe_part = nullptr;    // blind / grad-w partial sums
+    float *d_probe_part_n = nullptr;
+    float *d_rf_part = nullptr;        // one per frame-kernel block
+    float *d_re_part = nullptr;        // 2 per subdomain tile
+    float *d_loss_part = nullptr;
+    double *d_metrics = nullptr;       // [rf, re, sum sqrt f]
+    int32_t n_k1_blocks = 0;
+    int32_t cur = 0;                   // which u / Lambda buffer holds the current iterate
+    bool initialised = false;
+    // ---- graphs
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // ---- every device allocation, freed by ptycho_plan_destroy
+    std::vector<void *> owned;
+};
+
+namespace od2p {
+
+// fft_kernels.cu
+int launch_frame_update(ptycho_plan_s *p, cudaStream_t s);
+int launch_forward(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out,
+                   cudaStream_t s);
+int launch_frames_ifft_weight(const ptycho_plan_s *p, const float2 *frames, const float2 *w,
+                              bool ifft, float2 *out, cudaStream_t s);
+int launch_loss_frames(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s);
+int launch_probe_avg(ptycho_plan_s *p, cudaStream_t s);
+int launch_ingest_f(ptycho_plan_s *p, const float *f, cudaStream_t s);
+int launch_permute_gamma(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_natural,
+                         cudaStream_t s);
+bool supported_m(int m);
+int frames_per_block(int m);
+int prepare_kernels(int m);
+
+// gather_kernels.cu
+int launch_subdomain_update(ptycho_plan_s *p, cudaStream_t s);
+int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w, float2 *out,
+                        cudaStream_t s);
+int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, cudaStream_t s);
+int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s);
+int launch_metrics(ptycho_plan_s *p, cudaStream_t s);
+int launch_sum_sqrtf(ptycho_plan_s *p, cudaStream_t s);
+int launch_init_state(ptycho_plan_s *p, const float2 *u0, const float2 *w0, cudaStream_t s);
+int launch_merge(const ptycho_plan_s *p, float2 *out, cudaStream_t s);
+int launch_prox(const float2 *y, const float *f, float2 *z, int64_t n, float eps, float lam,
+                cudaStream_t s);
+
+}  // namespace od2p

@@ -1,0 +1,606 @@
+// Host runtime of the OD2P library: argument checks, the overlapping domain
+// decomposition, gather tile lists, plan-owned device memory, CUDA-graph
+// replay of the iteration, and the extern "C" entry points of include/od2p.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "od2p_internal.h"
+
+namespace od2p {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return PTYCHO_ERR_CUDA;
+}
+
+namespace {
+
+template <class T>
+int dev_alloc(T **ptr, size_t count, std::vector<void *> &owned)
+{
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)ptr, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(PTYCHO_ERR_OOM, "cudaMalloc of " + std::to_string(sizeof(T) * count) +
+                                        " bytes failed: " + cudaGetErrorString(e));
+    }
+    owned.push_back((void *)*ptr);
+    return PTYCHO_OK;
+}
+
+template <class T>
+int upload(T **dst, const std::vector<T> &src, std::vector<void *> &owned, cudaStream_t s)
+{
+    if (int rc = dev_alloc(dst, src.size(), owned)) return rc;
+    if (!src.empty())
+        OD2P_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
+    return PTYCHO_OK;
+}
+
+// Overlapping decomposition (sections 2.1 and 3.1; rule stated in od2p.h).
+struct Layout {
+    std::vector<int32_t> frame_sub, rect, pair, pair_rect;
+};
+
+Layout decompose(int H, int W, int m, const std::vector<int32_t> &offs, int sub_rows, int sub_cols,
+                 int overlap_px)
+{
+    Layout L;
+    const int J = (int)offs.size() / 2, D = sub_rows * sub_cols;
+    std::vector<int64_t> rb(sub_rows + 1), cb(sub_cols + 1);
+    for (int k = 0; k <= sub_rows; ++k) rb[k] = (int64_t)k * H / sub_rows;
+    for (int k = 0; k <= sub_cols; ++k) cb[k] = (int64_t)k * W / sub_cols;
+    const int grow = (overlap_px + 1) / 2;
+    L.rect.resize(4 * D);
+    for (int d = 0; d < D; ++d) {
+        const int a = d / sub_cols, b = d % sub_cols;
+        const int r0 = (int)rb[a] - (a > 0 ? grow : 0), r1 = (int)rb[a + 1] + (a + 1 < sub_rows ? grow : 0);
+        const int c0 = (int)cb[b] - (b > 0 ? grow : 0), c1 = (int)cb[b + 1] + (b + 1 < sub_cols ? grow : 0);
+        L.rect[4 * d + 0] = std::max(r0, 0);
+        L.rect[4 * d + 1] = std::max(c0, 0);
+        L.rect[4 * d + 2] = std::min(r1, H);
+        L.rect[4 * d + 3] = std::min(c1, W);
+    }
+    // frame -> the core tile holding its window centre o + (m-1)/2, i.e. the last
+    // boundary b with 2*b <= 2*o + m - 1
+    L.frame_sub.resize(J);
+    for (int j = 0; j < J; ++j) {
+        const int64_t cr = 2LL * offs[2 * j] + m - 1, cc = 2LL * offs[2 * j + 1] + m - 1;
+        int a = 0, b = 0;
+        for (int k = 1; k < sub_rows; ++k)
+            if (2 * rb[k] <= cr) a = k;
+        for (int k = 1; k < sub_cols; ++k)
+            if (2 * cb[k] <= cc) b = k;
+        const int d = a * sub_cols + b;
+        L.frame_sub[j] = d;
+        int32_t *R = &L.rect[4 * d];
+        R[0] = std::min(R[0], offs[2 * j]);
+        R[1] = std::min(R[1], offs[2 * j + 1]);
+        R[2] = std::max(R[2], offs[2 * j] + m);
+        R[3] = std::max(R[3], offs[2 * j + 1] + m);
+    }
+    for (int d = 0; d < D; ++d)
+        for (int e = 0; e < D; ++e) {
+            if (d == e) continue;
+            const int32_t *A = &L.rect[4 * d], *B = &L.rect[4 * e];
+            const int r0 = std::max(A[0], B[0]), c0 = std::max(A[1], B[1]);
+            const int r1 = std::min(A[2], B[2]), c1 = std::min(A[3], B[3]);
+            if (r0 < r1 && c0 < c1) {
+                L.pair.insert(L.pair.end(), {d, e});
+                L.pair_rect.insert(L.pair_rect.end(), {r0, c0, r1, c1});
+            }
+        }
+    return L;
+}
+
+// Tiles of TILE_H x TILE_W pixels over each region, with the frames whose
+// windows meet the tile, ascending in j.
+struct HostTiles {
+    std::vector<Tile> tiles;
+    std::vector<int32_t> ptr, list, reg_ptr;
+};
+
+HostTiles make_tiles(int n_reg, const std::vector<int32_t> &reg_rect,
+                     const std::vector<std::vector<int32_t>> &reg_frames,
+                     const std::vector<int32_t> &offs, int m)
+{
+    HostTiles T;
+    std::vector<std::vector<int32_t>> lists;
+    for (int g = 0; g < n_reg; ++g) {
+        T.reg_ptr.push_back((int32_t)T.tiles.size());
+        const int r0 = reg_rect[4 * g], c0 = reg_rect[4 * g + 1];
+        const int h = reg_rect[4 * g + 2] - r0, w = reg_rect[4 * g + 3] - c0;
+        const int nty = (h + TILE_H - 1) / TILE_H, ntx = (w + TILE_W - 1) / TILE_W;
+        const size_t base = T.tiles.size();
+        for (int ty = 0; ty < nty; ++ty)
+            for (int tx = 0; tx < ntx; ++tx) T.tiles.push_back(Tile{g, ty * TILE_H, tx * TILE_W, 0});
+        lists.resize(T.tiles.size());
+        for (int j : reg_frames[g]) {
+            const int lr = offs[2 * j] - r0, lc = offs[2 * j + 1] - c0;
+            const int ty0 = std::max(0, lr / TILE_H), ty1 = std::min(nty - 1, (lr + m - 1) / TILE_H);
+            const int tx0 = std::max(0, lc / TILE_W), tx1 = std::min(ntx - 1, (lc + m - 1) / TILE_W);
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) lists[base + (size_t)ty * ntx + tx].push_back(j);
+        }
+    }
+    T.reg_ptr.push_back((int32_t)T.tiles.size());
+    T.ptr.push_back(0);
+    for (auto &l : lists) {
+        T.list.insert(T.list.end(), l.begin(), l.end());
+        T.ptr.push_back((int32_t)T.list.size());
+    }
+    return T;
+}
+
+int upload_tiles(GatherTiles &G, const HostTiles &T, std::vector<void *> &owned, cudaStream_t s)
+{
+    G.n_tiles = (int32_t)T.tiles.size();
+    if (int rc = upload(&G.tiles, T.tiles, owned, s)) return rc;
+    if (int rc = upload(&G.ptr, T.ptr, owned, s)) return rc;
+    if (int rc = upload(&G.list, T.list, owned, s)) return rc;
+    return upload(&G.reg_ptr, T.reg_ptr, owned, s);
+}
+
+int upload_groups(ProbeGroups &G, const std::vector<std::vector<int32_t>> &groups,
+                  std::vector<void *> &owned, cudaStream_t s)
+{
+    std::vector<int32_t> frames, chunk_ptr;
+    std::vector<int4> chunks;
+    for (int g = 0; g < (int)groups.size(); ++g) {
+        chunk_ptr.push_back((int32_t)chunks.size());
+        const int b0 = (int)frames.size();
+        frames.insert(frames.end(), groups[g].begin(), groups[g].end());
+        for (int b = b0; b < (int)frames.size(); b += PROBE_CHUNK)
+            chunks.push_back(make_int4(g, b, std::min<int>(b + PROBE_CHUNK, (int)frames.size()), 0));
+    }
+    chunk_ptr.push_back((int32_t)chunks.size());
+    G.n_groups = (int32_t)groups.size();
+    G.n_chunks = (int32_t)chunks.size();
+    if (int rc = upload(&G.frames, frames, owned, s)) return rc;
+    if (int rc = upload(&G.chunks, chunks, owned, s)) return rc;
+    return upload(&G.chunk_ptr, chunk_ptr, owned, s);
+}
+
+int enqueue_iteration(ptycho_plan_s *p, cudaStream_t s)
+{
+    if (int rc = launch_frame_update(p, s)) return rc;
+    if (p->blind) {
+        if (int rc = launch_probe_avg(p, s)) return rc;
+        if (int rc = launch_probe_reduce(p, nullptr, nullptr, s)) return rc;
+        OD2P_CUDA(cudaMemcpyAsync(p->d_w, p->d_wnew, sizeof(float2) * p->MM, cudaMemcpyDeviceToDevice, s));
+    }
+    return launch_subdomain_update(p, s);
+}
+
+int capture_graph(ptycho_plan_s *p, int parity)
+{
+    if (!p->cap_stream) OD2P_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    OD2P_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int saved = p->cur;
+    p->cur = parity;
+    int rc = enqueue_iteration(p, p->cap_stream);
+    p->cur = saved;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&p->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        p->graph[parity] = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    return PTYCHO_OK;
+}
+
+}  // namespace
+}  // namespace od2p
+
+using namespace od2p;
+
+extern "C" {
+
+const char *ptycho_last_error(void) { return od2p::g_err.c_str(); }
+
+int32_t ptycho_abi_version(void) { return 1; }
+
+int ptycho_plan_destroy(ptycho_plan_t *plan)
+{
+    if (!plan) return PTYCHO_OK;
+    ptycho_plan_s *p = plan;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 2; ++i)
+        if (p->graph[i]) cudaGraphExecDestroy(p->graph[i]);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (void *ptr : p->owned) cudaFree(ptr);
+    delete p;
+    cudaGetLastError();
+    return PTYCHO_OK;
+}
+
+int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev,
+                ptycho_stream_t stream)
+{
+    if (!out) return fail(PTYCHO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g || !f_dev || !g->offsets_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL geometry, f or offsets");
+    if (!supported_m(g->m)) return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    if (g->n_frames < 1 || g->img_h < g->m || g->img_w < g->m)
+        return fail(PTYCHO_ERR_INVALID_ARG, "need n_frames >= 1 and an image at least m x m");
+    if ((int64_t)g->img_h * g->img_w >= (1LL << 31))
+        return fail(PTYCHO_ERR_UNSUPPORTED, "image larger than 2^31 pixels");
+    if (g->sub_rows < 1 || g->sub_cols < 1 || g->sub_rows > g->img_h || g->sub_cols > g->img_w ||
+        g->overlap_px < 0)
+        return fail(PTYCHO_ERR_INVALID_ARG, "bad subdomain grid or overlap");
+    if (!(g->eps > 0.f && g->eps < 1.f)) return fail(PTYCHO_ERR_INVALID_ARG, "eps must be in (0, 1)");
+    if (!(g->eta > 0.f) || !(g->r >= 0.f) || !std::isfinite(g->eta) || !std::isfinite(g->r))
+        return fail(PTYCHO_ERR_INVALID_ARG, "need eta > 0 and r >= 0");
+    if (g->blind && (!(g->mu > 0.f) || !(g->gamma >= 0.f)))
+        return fail(PTYCHO_ERR_INVALID_ARG, "blind plans need mu > 0 and gamma >= 0");
+    const int J = g->n_frames, m = g->m;
+    for (int j = 0; j < J; ++j) {
+        const int r0 = g->offsets_host[2 * j], c0 = g->offsets_host[2 * j + 1];
+        if (r0 < 0 || c0 < 0 || r0 > g->img_h - m || c0 > g->img_w - m)
+            return fail(PTYCHO_ERR_INVALID_ARG, "offset of frame " + std::to_string(j) + " out of range");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    auto *p = new (std::nothrow) ptycho_plan_s();
+    if (!p) return fail(PTYCHO_ERR_OOM, "host allocation failed");
+    auto bail = [&](int rc) {
+        ptycho_plan_destroy(p);
+        return rc;
+    };
+    p->H = g->img_h;
+    p->W = g->img_w;
+    p->M = m;
+    p->MM = m * m;
+    p->J = J;
+    p->sub_rows = g->sub_rows;
+    p->sub_cols = g->sub_cols;
+    p->overlap_px = g->overlap_px;
+    p->eps = g->eps;
+    p->eta = g->eta;
+    p->r = g->r;
+    p->mu = g->mu;
+    p->gamma = g->gamma;
+    p->blind = g->blind ? 1 : 0;
+    p->offs.assign(g->offsets_host, g->offsets_host + 2 * J);
+
+    Layout L = decompose(p->H, p->W, m, p->offs, p->sub_rows, p->sub_cols, p->overlap_px);
+    p->D = p->sub_rows * p->sub_cols;
+    p->P = (int32_t)L.pair.size() / 2;
+    p->frame_sub = L.frame_sub;
+    p->rect = L.rect;
+    p->pair = L.pair;
+    p->pair_rect = L.pair_rect;
+    p->u_off.assign(p->D + 1, 0);
+    for (int d = 0; d < p->D; ++d)
+        p->u_off[d + 1] = p->u_off[d] + (int64_t)(p->rect[4 * d + 2] - p->rect[4 * d]) *
+                                            (p->rect[4 * d + 3] - p->rect[4 * d + 1]);
+    p->lam_off.assign(p->P + 1, 0);
+    for (int k = 0; k < p->P; ++k)
+        p->lam_off[k + 1] = p->lam_off[k] + (int64_t)(p->pair_rect[4 * k + 2] - p->pair_rect[4 * k]) *
+                                                (p->pair_rect[4 * k + 3] - p->pair_rect[4 * k + 1]);
+    p->u_len = p->u_off[p->D];
+    p->lam_len = p->lam_off[p->P];
+    if (p->u_len >= (1LL << 31)) return bail(fail(PTYCHO_ERR_UNSUPPORTED, "subdomain storage exceeds 2^31 pixels"));
+
+    std::vector<int32_t> frame_base(J), frame_pitch(J), img_base(J);
+    std::vector<std::vector<int32_t>> sub_frames(p->D), all_frames(1);
+    for (int j = 0; j < J; ++j) {
+        const int d = p->frame_sub[j];
+        const int32_t *R = &p->rect[4 * d];
+        frame_pitch[j] = R[3] - R[1];
+        frame_base[j] = (int32_t)(p->u_off[d] + (int64_t)(p->offs[2 * j] - R[0]) * frame_pitch[j] +
+                                  (p->offs[2 * j + 1] - R[1]));
+        img_base[j] = p->offs[2 * j] * p->W + p->offs[2 * j + 1];
+        sub_frames[d].push_back(j);
+        all_frames[0].push_back(j);
+    }
+    std::vector<int32_t> nbr_ptr(p->D + 1, 0), nbr;
+    {
+        std::vector<int> pair_of((size_t)p->D * p->D, -1);
+        for (int k = 0; k < p->P; ++k) pair_of[(size_t)p->pair[2 * k] * p->D + p->pair[2 * k + 1]] = k;
+        for (int d = 0; d < p->D; ++d) {
+            for (int e = 0; e < p->D; ++e) {
+                const int kde = pair_of[(size_t)d * p->D + e];
+                if (kde < 0) continue;
+                nbr.insert(nbr.end(), {e, kde, pair_of[(size_t)e * p->D + d]});
+            }
+            nbr_ptr[d + 1] = (int32_t)(nbr.size() / 3);
+        }
+    }
+    HostTiles st = make_tiles(p->D, p->rect, sub_frames, p->offs, m);
+    std::vector<int32_t> img_rect = {0, 0, p->H, p->W};
+    HostTiles it = make_tiles(1, img_rect, all_frames, p->offs, m);
+
+    auto &own = p->owned;
+    const size_t JMM = (size_t)J * p->MM;
+    int rc;
+    if ((rc = upload(&p->d_offs, p->offs, own, s)) || (rc = upload(&p->d_frame_sub, p->frame_sub, own, s)) ||
+        (rc = upload(&p->d_frame_base, frame_base, own, s)) ||
+        (rc = upload(&p->d_frame_pitch, frame_pitch, own, s)) || (rc = upload(&p->d_img_base, img_base, own, s)) ||
+        (rc = upload(&p->d_rect, p->rect, own, s)) || (rc = upload(&p->d_nbr_ptr, nbr_ptr, own, s)) ||
+        (rc = upload(&p->d_nbr, nbr, own, s)) || (rc = upload(&p->d_pair_rect, p->pair_rect, own, s)) ||
+        (rc = upload(&p->d_u_off, p->u_off, own, s)) || (rc = upload(&p->d_lam_off, p->lam_off, own, s)) ||
+        (rc = upload_tiles(p->sub_tiles, st, own, s)) || (rc = upload_tiles(p->img_tiles, it, own, s)) ||
+        (rc = upload_groups(p->sub_groups, sub_frames, own, s)) ||
+        (rc = upload_groups(p->img_groups, all_frames, own, s)))
+        return bail(rc);
+    // twiddles exp(-2 pi i k / m), computed in double and rounded once
+    std::vector<float2> tw(m);
+    for (int k = 0; k < m; ++k) {
+        const double a = -2.0 * 3.14159265358979323846 * (double)k / (double)m;
+        tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    if ((rc = upload(&p->d_tw, tw, own, s))) return bail(rc);
+    if (p->blind && g->fourier_support_host) {
+        std::vector<float> mask(p->MM);
+        for (int k = 0; k < p->MM; ++k) mask[k] = g->fourier_support_host[k] ? 1.f : 0.f;
+        p->has_mask = true;
+        if ((rc = upload(&p->d_mask, mask, own, s))) return bail(rc);
+    }
+    p->n_k1_blocks = (J + frames_per_block(m) - 1) / frames_per_block(m);
+    const int n_chunks = std::max(p->sub_groups.n_chunks, p->img_groups.n_chunks);
+    if ((rc = dev_alloc(&p->d_sqrtf, JMM, own)) || (rc = dev_alloc(&p->d_gamma, JMM, own)) ||
+        (rc = dev_alloc(&p->d_q, JMM, own)) || (rc = dev_alloc(&p->d_u[0], p->u_len, own)) ||
+        (rc = dev_alloc(&p->d_u[1], p->u_len, own)) || (rc = dev_alloc(&p->d_lam[0], p->lam_len, own)) ||
+        (rc = dev_alloc(&p->d_lam[1], p->lam_len, own)) || (rc = dev_alloc(&p->d_w, p->MM, own)) ||
+        (rc = dev_alloc(&p->d_wnew, p->MM, own)) ||
+        (rc = dev_alloc(&p->d_probe_part, (size_t)n_chunks * p->MM, own)) ||
+        (rc = dev_alloc(&p->d_probe_part_n, (size_t)n_chunks * p->MM, own)) ||
+        (rc = dev_alloc(&p->d_rf_part, p->n_k1_blocks, own)) ||
+        (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own)) ||
+        (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_k1_blocks), own)) ||
+        (rc = dev_alloc(&p->d_metrics, 3, own)))
+        return bail(rc);
+    if (p->blind) {
+        if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own)))
+            return bail(rc);
+    }
+    if ((rc = prepare_kernels(m))) return bail(rc);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->d_metrics, 0, 3 * sizeof(double), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * p->n_k1_blocks, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_re_part, 0, sizeof(float) * 2 * p->sub_tiles.n_tiles, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_w, 0, sizeof(float2) * p->MM, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMemsetAsync"));
+    if ((rc = launch_ingest_f(p, f_dev, s)) || (rc = launch_sum_sqrtf(p, s))) return bail(rc);
+    // Step 0 with u = 1 and a zero probe until od2p_init
+    if ((rc = launch_init_state(p, nullptr, p->d_w, s))) return bail(rc);
+    if ((e = cudaMemsetAsync(p->d_gamma, 0, sizeof(float2) * JMM, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMemsetAsync"));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(cuda_fail(e, "cudaStreamSynchronize"));
+    *out = p;
+    return PTYCHO_OK;
+}
+
+int ptycho_plan_dims(const ptycho_plan_t *plan, int32_t *n_sub, int32_t *n_pairs, int64_t *u_len,
+                     int64_t *lambda_len)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (n_sub) *n_sub = plan->D;
+    if (n_pairs) *n_pairs = plan->P;
+    if (u_len) *u_len = plan->u_len;
+    if (lambda_len) *lambda_len = plan->lam_len;
+    return PTYCHO_OK;
+}
+
+int ptycho_plan_layout(const ptycho_plan_t *plan, int32_t *frame_sub, int32_t *rect, int32_t *pair,
+                       int32_t *pair_rect)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (frame_sub) std::memcpy(frame_sub, plan->frame_sub.data(), sizeof(int32_t) * plan->J);
+    if (rect) std::memcpy(rect, plan->rect.data(), sizeof(int32_t) * 4 * plan->D);
+    if (pair && plan->P) std::memcpy(pair, plan->pair.data(), sizeof(int32_t) * 2 * plan->P);
+    if (pair_rect && plan->P) std::memcpy(pair_rect, plan->pair_rect.data(), sizeof(int32_t) * 4 * plan->P);
+    return PTYCHO_OK;
+}
+
+int ptycho_forward(const ptycho_plan_t *plan, const ptycho_c32 *u, const ptycho_c32 *w,
+                   ptycho_c32 *frames_out, ptycho_stream_t stream)
+{
+    if (!plan || !u || !w || !frames_out) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    return launch_forward(plan, reinterpret_cast<const float2 *>(u), reinterpret_cast<const float2 *>(w),
+                          reinterpret_cast<float2 *>(frames_out), reinterpret_cast<cudaStream_t>(stream));
+}
+
+int stagm_prox(const ptycho_c32 *y, const float *f, ptycho_c32 *z, int64_t n, float eps, float lambda,
+               ptycho_stream_t stream)
+{
+    if (n < 0) return fail(PTYCHO_ERR_INVALID_ARG, "n < 0");
+    if (n > 0 && (!y || !f || !z)) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    if (!(eps > 0.f && eps < 1.f) || !(lambda > 0.f))
+        return fail(PTYCHO_ERR_INVALID_ARG, "need 0 < eps < 1 and lambda > 0");
+    if (n == 0) return PTYCHO_OK;
+    return launch_prox(reinterpret_cast<const float2 *>(y), f, reinterpret_cast<float2 *>(z), n, eps,
+                       lambda, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int overlap_add(ptycho_plan_t *plan, const ptycho_c32 *frames, const ptycho_c32 *w, ptycho_c32 *image_out,
+                int32_t flags, ptycho_stream_t stream)
+{
+    if (!plan || !frames || !w || !image_out) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    if (flags & ~PTYCHO_OA_IFFT) return fail(PTYCHO_ERR_INVALID_ARG, "unknown flag");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float2 *fr = reinterpret_cast<const float2 *>(frames);
+    const float2 *wv = reinterpret_cast<const float2 *>(w);
+    if (flags & PTYCHO_OA_IFFT) {
+        if (int rc = launch_frames_ifft_weight(plan, fr, nullptr, true, plan->d_q, s)) return rc;
+        fr = plan->d_q;
+    }
+    return launch_image_gather(plan, fr, wv, reinterpret_cast<float2 *>(image_out), s);
+}
+
+int od2p_init(ptycho_plan_t *plan, const ptycho_c32 *u0, const ptycho_c32 *w0, ptycho_stream_t stream)
+{
+    if (!plan || !w0) return fail(PTYCHO_ERR_INVALID_ARG, "NULL plan or probe");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = launch_init_state(plan, reinterpret_cast<const float2 *>(u0), reinterpret_cast<const float2 *>(w0), s))
+        return rc;
+    OD2P_CUDA(cudaMemsetAsync(plan->d_gamma, 0, sizeof(float2) * (size_t)plan->J * plan->MM, s));
+    OD2P_CUDA(cudaMemsetAsync(plan->d_lam[0], 0, sizeof(float2) * std::max<int64_t>(plan->lam_len, 1), s));
+    OD2P_CUDA(cudaMemsetAsync(plan->d_lam[1], 0, sizeof(float2) * std::max<int64_t>(plan->lam_len, 1), s));
+    if (plan->blind) OD2P_CUDA(cudaMemsetAsync(plan->d_Delta, 0, sizeof(float2) * (size_t)plan->D * plan->MM, s));
+    plan->initialised = true;
+    return PTYCHO_OK;
+}
+
+int od2p_frame_update(ptycho_plan_t *plan, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (!plan->initialised) return fail(PTYCHO_ERR_STATE, "od2p_init has not been called");
+    return launch_frame_update(plan, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int probe_update(ptycho_plan_t *plan, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (!plan->blind) return fail(PTYCHO_ERR_STATE, "probe_update needs a blind plan");
+    if (!plan->initialised) return fail(PTYCHO_ERR_STATE, "od2p_init has not been called");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = launch_probe_avg(plan, s)) return rc;
+    if (int rc = launch_probe_reduce(plan, nullptr, nullptr, s)) return rc;
+    OD2P_CUDA(cudaMemcpyAsync(plan->d_w, plan->d_wnew, sizeof(float2) * plan->MM, cudaMemcpyDeviceToDevice, s));
+    return PTYCHO_OK;
+}
+
+int od2p_subdomain_update(ptycho_plan_t *plan, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (!plan->initialised) return fail(PTYCHO_ERR_STATE, "od2p_init has not been called");
+    if (int rc = launch_subdomain_update(plan, reinterpret_cast<cudaStream_t>(stream))) return rc;
+    plan->cur ^= 1;
+    return PTYCHO_OK;
+}
+
+int od2p_iterate(ptycho_plan_t *plan, int32_t n_iter, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (n_iter < 0) return fail(PTYCHO_ERR_INVALID_ARG, "n_iter < 0");
+    if (!plan->initialised) return fail(PTYCHO_ERR_STATE, "od2p_init has not been called");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (int i = 0; i < n_iter; ++i) {
+        if (!plan->graph[plan->cur])
+            if (int rc = capture_graph(plan, plan->cur)) return rc;
+        OD2P_CUDA(cudaGraphLaunch(plan->graph[plan->cur], s));
+        plan->cur ^= 1;
+    }
+    return PTYCHO_OK;
+}
+
+int od2p_merge(const ptycho_plan_t *plan, ptycho_c32 *u_out, ptycho_stream_t stream)
+{
+    if (!plan || !u_out) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    return launch_merge(plan, reinterpret_cast<float2 *>(u_out), reinterpret_cast<cudaStream_t>(stream));
+}
+
+int od2p_metrics(ptycho_plan_t *plan, float *rf, float *re, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = launch_metrics(plan, s)) return rc;
+    double h[2];
+    OD2P_CUDA(cudaMemcpyAsync(h, plan->d_metrics, sizeof(h), cudaMemcpyDeviceToHost, s));
+    OD2P_CUDA(cudaStreamSynchronize(s));
+    if (rf) *rf = (float)h[0];
+    if (re) *re = (float)h[1];
+    return PTYCHO_OK;
+}
+
+int od2p_state_len(const ptycho_plan_t *plan, int32_t which, int64_t *n)
+{
+    if (!plan || !n) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    switch (which) {
+    case PTYCHO_STATE_U: *n = plan->u_len; break;
+    case PTYCHO_STATE_GAMMA:
+    case PTYCHO_STATE_Q: *n = (int64_t)plan->J * plan->MM; break;
+    case PTYCHO_STATE_LAMBDA: *n = plan->lam_len; break;
+    case PTYCHO_STATE_WD:
+    case PTYCHO_STATE_DELTA:
+        if (!plan->blind) return fail(PTYCHO_ERR_STATE, "W_d and Delta exist in blind plans only");
+        *n = (int64_t)plan->D * plan->MM;
+        break;
+    case PTYCHO_STATE_W: *n = plan->MM; break;
+    default: return fail(PTYCHO_ERR_INVALID_ARG, "unknown state selector");
+    }
+    return PTYCHO_OK;
+}
+
+static float2 *state_ptr(const ptycho_plan_t *p, int which)
+{
+    switch (which) {
+    case PTYCHO_STATE_U: return p->d_u[p->cur];
+    case PTYCHO_STATE_GAMMA: return p->d_gamma;
+    case PTYCHO_STATE_LAMBDA: return p->d_lam[p->cur];
+    case PTYCHO_STATE_WD: return p->d_Wd;
+    case PTYCHO_STATE_DELTA: return p->d_Delta;
+    case PTYCHO_STATE_W: return p->d_w;
+    case PTYCHO_STATE_Q: return p->d_q;
+    default: return nullptr;
+    }
+}
+
+int od2p_get_state(const ptycho_plan_t *plan, int32_t which, ptycho_c32 *dst, ptycho_stream_t stream)
+{
+    int64_t n = 0;
+    if (int rc = od2p_state_len(plan, which, &n)) return rc;
+    if (n == 0) return PTYCHO_OK;
+    if (!dst) return fail(PTYCHO_ERR_INVALID_ARG, "dst is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (which == PTYCHO_STATE_GAMMA)
+        return launch_permute_gamma(plan, plan->d_gamma, reinterpret_cast<float2 *>(dst), true, s);
+    if (n) OD2P_CUDA(cudaMemcpyAsync(dst, state_ptr(plan, which), sizeof(float2) * n, cudaMemcpyDeviceToDevice, s));
+    return PTYCHO_OK;
+}
+
+int od2p_set_state(ptycho_plan_t *plan, int32_t which, const ptycho_c32 *src, ptycho_stream_t stream)
+{
+    int64_t n = 0;
+    if (int rc = od2p_state_len(plan, which, &n)) return rc;
+    if (which == PTYCHO_STATE_Q) return fail(PTYCHO_ERR_INVALID_ARG, "PTYCHO_STATE_Q is read-only");
+    if (n == 0) return PTYCHO_OK;
+    if (!src) return fail(PTYCHO_ERR_INVALID_ARG, "src is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (which == PTYCHO_STATE_GAMMA)
+        return launch_permute_gamma(plan, reinterpret_cast<const float2 *>(src), plan->d_gamma, false, s);
+    if (n) OD2P_CUDA(cudaMemcpyAsync(state_ptr(plan, which), src, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s));
+    return PTYCHO_OK;
+}
+
+int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u, const ptycho_c32 *w, float *loss,
+                    ptycho_c32 *grad_u, ptycho_c32 *grad_w, int32_t recompute, ptycho_stream_t stream)
+{
+    if (!plan || !u || !w || !loss) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    if (recompute != 1) return fail(PTYCHO_ERR_UNSUPPORTED, "only recompute = 1 is implemented");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float2 *uu = reinterpret_cast<const float2 *>(u), *ww = reinterpret_cast<const float2 *>(w);
+    if (int rc = launch_loss_frames(plan, uu, ww, s)) return rc;
+    if (int rc = launch_loss_reduce(plan, loss, s)) return rc;
+    if (grad_u)
+        if (int rc = launch_image_gather(plan, plan->d_q, ww, reinterpret_cast<float2 *>(grad_u), s)) return rc;
+    if (grad_w)
+        if (int rc = launch_probe_reduce(plan, uu, reinterpret_cast<float2 *>(grad_w), s)) return rc;
+    return PTYCHO_OK;
+}
+
+}  // extern "C"

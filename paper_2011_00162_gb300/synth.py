@@ -165,7 +165,7 @@ def small_2sub() -> Problem:
 
 def grid_4x4() -> Problem:
     """512^2 image, 64^2 probe, step 16 +-2 jitter (841 frames), 4x4 subdomains, Poisson 1e4, 200 its."""
-    return Problem("od2p_512px_m64_4x4", 512, 64, 16, 2, 4, 4, 16, 1e4, 200)
+    return Problem("od2p_512px_m64_4x4", 512, 64, 16, 2, 4, 4, 16, 1e4, 200, eta=2.0, r=0.5)
 
 
 def blind_4x4() -> Problem:

@@ -1,0 +1,323 @@
+"""CUDA path vs the FP64 oracle on identical seeded inputs (through the C ABI).
+
+Tolerances (stated in the build's accuracy contract): one iteration within
+1e-5 relative L2 per state array; a full run within 1e-3 relative L2 after
+global-phase alignment; integer layouts bit-exact; repeated runs bitwise equal.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2011_00162_gb300 as od
+from paper_2011_00162_gb300 import synth
+
+from _cases import make_case, phase_aligned_rel, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+ONE_ITER_TOL = 1e-5
+END_TOL = 1e-3
+
+
+def c64(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, np.complex64))).to(DEV)
+
+
+def f32(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, np.float32))).to(DEV)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def geom_of(p, offs, **kw):
+    d = dict(eps=p.eps, eta=p.eta, r=p.r, mu=p.mu, gamma=p.gamma, blind=p.blind)
+    d.update(kw)
+    return od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, **d)
+
+
+def pair_of(p, offs, w, f, u0=None, **kw):
+    g = geom_of(p, offs, **kw)
+    plan = od.ptycho_plan(g, f32(f))
+    od.od2p_init(plan, c64(w), c64(u0) if u0 is not None else None)
+    ref = oracle.ADMM(f, w, offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, g.eps, g.eta, g.r,
+                      u0=u0, blind=g.blind, mu=g.mu, gamma=g.gamma, mask=g.fourier_support)
+    return plan, ref
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    od.build.build()
+
+
+# ----------------------------------------------------------------------------- pointwise / operators
+@pytest.mark.parametrize("eps,lam", [(0.5, 0.1), (0.5, 5.0), (0.2, 10.0), (0.9, 0.5)])
+def test_prox_matches_oracle(eps, lam):
+    rng = np.random.default_rng(1)
+    n = 200_003  # ragged length
+    y = ((rng.standard_normal(n) + 1j * rng.standard_normal(n)) * rng.choice([0.01, 1, 5], n)).astype(np.complex64)
+    f = (np.abs(rng.standard_normal(n)) * rng.choice([0, 1, 10], n)).astype(np.float32)
+    z = host(od.stagm_prox(c64(y), f32(f), eps, lam))
+    ref = oracle.stagm_prox(y, f.astype(np.float64), eps, lam)
+    keep = np.abs(y) > 1e-6 * np.sqrt(f)  # sign(0) is arbitrary (any phase is optimal)
+    err = np.abs(z - ref)[keep] / (np.abs(ref) + np.sqrt(f) + 1e-30)[keep]
+    assert err.max() < 2e-6
+
+
+@pytest.mark.parametrize("m,n,step,jit", [(16, 61, 5, 1), (32, 100, 9, 2), (64, 300, 16, 2), (128, 400, 40, 3)])
+def test_forward_and_adjoint_match_oracle(m, n, step, jit):
+    rng = np.random.default_rng(m)
+    offs = synth.raster_offsets(n, m, step, jit, seed=3)
+    u = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+    w = synth.make_probe(m)
+    f = np.ones((len(offs), m, m), np.float32)
+    plan = od.ptycho_plan(od.Geometry(n, n, m, offs), f32(f))
+    fr = host(od.ptycho_forward(plan, c64(u), c64(w)))
+    ref = oracle.forward(u, w, offs)
+    per_frame = np.linalg.norm((fr - ref).reshape(len(offs), -1), axis=1) / np.linalg.norm(ref.reshape(len(offs), -1), axis=1)
+    assert per_frame.max() < 1e-6
+    y = (rng.standard_normal(ref.shape) + 1j * rng.standard_normal(ref.shape)).astype(np.complex64)
+    adj = host(od.overlap_add(plan, c64(y), c64(w), ifft=True))
+    assert rel_l2(adj, oracle.adjoint(y, w, offs, n, n)) < 1e-6
+    # without the inverse FFT: sum_j S_j^T (conj(w) o y_j), pixels nobody covers are 0
+    plain = host(od.overlap_add(plan, c64(y), c64(w), ifft=False))
+    exp = np.zeros((n, n), np.complex128)
+    for j, (r0, c0) in enumerate(offs):
+        exp[r0:r0 + m, c0:c0 + m] += np.conj(w) * y[j]
+    assert rel_l2(plain, exp) < 1e-6
+
+
+@pytest.mark.parametrize("grid,ov,n,m,step,jit", [((1, 2), 8, 64, 16, 4, 0), ((4, 4), 16, 512, 64, 16, 2),
+                                                 ((3, 5), 0, 300, 32, 12, 3), ((1, 1), 0, 100, 16, 7, 1),
+                                                 ((2, 3), 40, 257, 64, 9, 2)])
+def test_decomposition_bit_exact(grid, ov, n, m, step, jit):
+    offs = synth.raster_offsets(n, m, step, jit, seed=5)
+    plan = od.ptycho_plan(od.Geometry(n, n, m, offs, grid[0], grid[1], ov),
+                          f32(np.ones((len(offs), m, m))))
+    fs, rect, pr, prc = plan.layout()
+    fs_o, rect_o = oracle.geometry(n, n, m, offs, grid[0], grid[1], ov)
+    pr_o, prc_o = oracle.pairs(rect_o)
+    assert np.array_equal(fs, fs_o) and np.array_equal(rect, rect_o)
+    assert np.array_equal(pr, pr_o) and np.array_equal(prc, prc_o)
+
+
+# ----------------------------------------------------------------------------- one iteration
+def _compare_state(plan, ref, tol, blind=False):
+    out = {}
+    for name, wg, wo in [("u", od.STATE_U, oracle.U), ("Gamma", od.STATE_GAMMA, oracle.GAMMA),
+                         ("Lambda", od.STATE_LAMBDA, oracle.LAMBDA)] + (
+            [("W_d", od.STATE_WD, oracle.WD), ("Delta", od.STATE_DELTA, oracle.DELTA),
+             ("w", od.STATE_W, oracle.W)] if blind else []):
+        a, b = host(od.od2p_get_state(plan, wg)), ref.get(wo)
+        if b.size == 0:
+            continue
+        out[name] = rel_l2(a, b)
+    bad = {k: v for k, v in out.items() if not v < tol}
+    assert not bad, f"relative L2 above {tol}: {bad} (all: {out})"
+    return out
+
+
+def _scramble(plan, ref, seed, blind=False):
+    rng = np.random.default_rng(seed)
+    for wg, wo, base in [(od.STATE_U, oracle.U, 1.0), (od.STATE_GAMMA, oracle.GAMMA, 0.0),
+                         (od.STATE_LAMBDA, oracle.LAMBDA, 0.0)] + (
+            [(od.STATE_WD, oracle.WD, None), (od.STATE_DELTA, oracle.DELTA, 0.0)] if blind else []):
+        n = ref.get(wo).size
+        if n == 0:
+            continue
+        cur = ref.get(wo)
+        if base is None:
+            v = cur * (1 + 0.1 * (rng.standard_normal(n) + 1j * rng.standard_normal(n)))
+        else:
+            scale = 0.2 * (np.abs(cur).mean() + 1e-3) if wo == oracle.GAMMA else 0.2
+            v = base + scale * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+        v = v.astype(np.complex64)
+        ref.set(wo, v)
+        od.od2p_set_state(plan, wg, c64(v))
+
+
+@pytest.mark.parametrize("scrambled", [False, True])
+def test_one_iteration_two_subdomains(scrambled):
+    p = synth.small_2sub()
+    offs, u_true, w, f = make_case(p)
+    plan, ref = pair_of(p, offs, w, f)
+    if scrambled:
+        _scramble(plan, ref, 3)
+    od.od2p_iterate(plan, 1)
+    ref.iterate(1)
+    _compare_state(plan, ref, ONE_ITER_TOL)
+
+
+@pytest.mark.parametrize("scrambled", [False, True])
+def test_one_iteration_grid4x4_full_size(scrambled):
+    """512^2 image, 841 frames of 64^2, 4x4 subdomains, Poisson 1e4: every array compared."""
+    p = synth.grid_4x4()
+    offs, u_true, w, f = make_case(p)
+    plan, ref = pair_of(p, offs, w, f)
+    if scrambled:
+        _scramble(plan, ref, 4)
+    for _ in range(2):
+        od.od2p_iterate(plan, 1)
+        ref.iterate(1)
+        _compare_state(plan, ref, ONE_ITER_TOL)
+        # re-synchronise so that each comparison measures a single iteration
+        for wg, wo in [(od.STATE_U, oracle.U), (od.STATE_GAMMA, oracle.GAMMA), (od.STATE_LAMBDA, oracle.LAMBDA)]:
+            od.od2p_set_state(plan, wg, c64(ref.get(wo)))
+
+
+@pytest.mark.parametrize("m,grid,n,step", [(32, (2, 3), 200, 10), (128, (2, 2), 384, 32), (16, (5, 4), 120, 6)])
+def test_one_iteration_other_sizes(m, grid, n, step):
+    p = synth.Problem("t", n, m, step, 2, grid[0], grid[1], 12, 1e5, 1, eta=0.3, r=0.2, seed=m)
+    offs, u_true, w, f = make_case(p)
+    plan, ref = pair_of(p, offs, w, f)
+    _scramble(plan, ref, 5)
+    od.od2p_iterate(plan, 1)
+    ref.iterate(1)
+    _compare_state(plan, ref, ONE_ITER_TOL)
+
+
+def test_single_frame_single_subdomain_edge():
+    m, n = 64, 64
+    offs = np.array([[0, 0]], np.int32)
+    w = synth.make_probe(m)
+    u = synth.make_image(n, 9)
+    f = (np.abs(oracle.forward(u, w, offs)) ** 2).astype(np.float32)
+    p = synth.Problem("one", n, m, 1, 0, 1, 1, 0, None, 1)
+    plan, ref = pair_of(p, offs, w, f)
+    od.od2p_iterate(plan, 2)
+    ref.iterate(2)
+    _compare_state(plan, ref, ONE_ITER_TOL)
+
+
+# ----------------------------------------------------------------------------- whole runs
+def test_end_of_run_two_subdomains():
+    """50 iterations (64^2, 169 frames of 16^2, 2 subdomains, noiseless)."""
+    p = synth.small_2sub()
+    offs, u_true, w, f = make_case(p)
+    plan, ref = pair_of(p, offs, w, f)
+    od.od2p_iterate(plan, p.n_iter)
+    ref.iterate(p.n_iter)
+    ug = host(od.od2p_merge(plan))
+    uo = ref.merge()
+    lit = synth.lit_mask(p.n, p.n, p.m, offs)
+    err = phase_aligned_rel(ug, uo)
+    err_truth_oracle = phase_aligned_rel(uo[lit], u_true[lit])
+    err_truth_gpu = phase_aligned_rel(ug[lit], u_true[lit])
+    print(f"end-of-run GPU vs FP64 oracle {err:.2e}; vs truth: oracle {err_truth_oracle:.3e}, GPU {err_truth_gpu:.3e}")
+    assert err < END_TOL
+    # after 50 iterations the metrics inherit the trajectory's FP32 deviation: RF (a
+    # sum over all frames) within END_TOL, RE (a difference of iterates) within 10 END_TOL
+    rf_g, re_g = od.od2p_metrics(plan)
+    rf_o, re_o = ref.metrics()
+    assert abs(rf_g - rf_o) < END_TOL * rf_o and abs(re_g - re_o) < 10 * END_TOL * re_o
+
+
+def test_end_of_run_grid4x4():
+    """200 iterations of the 512^2 / 841-frame / 4x4 workload."""
+    p = synth.grid_4x4()
+    offs, u_true, w, f = make_case(p)
+    plan, ref = pair_of(p, offs, w, f)
+    od.od2p_iterate(plan, p.n_iter)
+    ref.iterate(p.n_iter)
+    ug, uo = host(od.od2p_merge(plan)), ref.merge()
+    lit = synth.lit_mask(p.n, p.n, p.m, offs)
+    err = phase_aligned_rel(ug, uo)
+    print(f"end-of-run GPU vs FP64 oracle {err:.2e}; oracle vs truth {phase_aligned_rel(uo[lit], u_true[lit]):.3e}")
+    assert err < END_TOL
+
+
+def test_bitwise_determinism_and_graph_equals_stages():
+    p = synth.grid_4x4()
+    offs, u_true, w, f = make_case(p)
+    outs = []
+    for mode in ("graph", "graph", "stages"):
+        plan = od.ptycho_plan(geom_of(p, offs), f32(f))
+        od.od2p_init(plan, c64(w))
+        for _ in range(3):
+            if mode == "graph":
+                od.od2p_iterate(plan, 1)
+            else:
+                od.od2p_frame_update(plan)
+                od.od2p_subdomain_update(plan)
+        outs.append([host(od.od2p_get_state(plan, k)) for k in (od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA)])
+        plan.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    for a, b in zip(outs[0], outs[2]):
+        assert np.array_equal(a, b)
+
+
+def test_metrics_and_merge_match_oracle():
+    p = synth.grid_4x4()
+    offs, u_true, w, f = make_case(p)
+    plan, ref = pair_of(p, offs, w, f)
+    od.od2p_iterate(plan, 3)
+    ref.iterate(3)
+    rf_g, re_g = od.od2p_metrics(plan)
+    rf_o, re_o = ref.metrics()
+    assert abs(rf_g - rf_o) < 1e-5 * rf_o and abs(re_g - re_o) < 1e-4 * re_o
+    assert rel_l2(host(od.od2p_merge(plan)), ref.merge()) < ONE_ITER_TOL
+
+
+def test_checkpoint_resume_bitwise():
+    p = synth.small_2sub()
+    offs, u_true, w, f = make_case(p)
+    a = od.ptycho_plan(geom_of(p, offs), f32(f))
+    od.od2p_init(a, c64(w))
+    od.od2p_iterate(a, 10)
+    snap = {k: od.od2p_get_state(a, k).clone() for k in (od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA)}
+    od.od2p_iterate(a, 10)
+    b = od.ptycho_plan(geom_of(p, offs), f32(f))
+    od.od2p_init(b, c64(w))
+    for k, v in snap.items():
+        od.od2p_set_state(b, k, v)
+    od.od2p_iterate(b, 10)
+    for k in snap:
+        assert torch.equal(od.od2p_get_state(a, k), od.od2p_get_state(b, k))
+
+
+# ----------------------------------------------------------------------------- blind
+@pytest.mark.parametrize("masked", [False, True])
+def test_blind_one_iteration(masked):
+    p = synth.Problem("b", 96, 32, 8, 1, 2, 2, 8, 1e5, 1, eta=0.3, r=0.2, blind=True, mu=2.0,
+                      gamma=0.1, seed=21)
+    offs, u_true, w_true, f = make_case(p)
+    w0 = synth.gaussian_probe(p.m)
+    mask = None
+    if masked:
+        yy, xx = np.meshgrid(np.fft.fftfreq(p.m), np.fft.fftfreq(p.m), indexing="ij")
+        mask = (np.hypot(yy, xx) < 0.3).astype(np.uint8)
+    g = geom_of(p, offs, fourier_support=mask)
+    plan = od.ptycho_plan(g, f32(f))
+    od.od2p_init(plan, c64(w0))
+    ref = oracle.ADMM(f, w0, offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, p.eta, p.r,
+                      blind=True, mu=p.mu, gamma=p.gamma, mask=mask)
+    _scramble(plan, ref, 8, blind=True)
+    for _ in range(2):
+        od.od2p_iterate(plan, 1)
+        ref.iterate(1)
+        _compare_state(plan, ref, ONE_ITER_TOL, blind=True)
+        for wg, wo in [(od.STATE_U, oracle.U), (od.STATE_GAMMA, oracle.GAMMA), (od.STATE_LAMBDA, oracle.LAMBDA),
+                       (od.STATE_WD, oracle.WD), (od.STATE_DELTA, oracle.DELTA), (od.STATE_W, oracle.W)]:
+            od.od2p_set_state(plan, wg, c64(ref.get(wo)))
+
+
+# ----------------------------------------------------------------------------- loss and gradients
+@pytest.mark.parametrize("m,n,step", [(16, 64, 4), (64, 256, 16), (128, 384, 48)])
+def test_loss_and_gradients_match_oracle(m, n, step):
+    p = synth.Problem("g", n, m, step, 2, 1, 1, 0, 1e4, 1, seed=m + 1)
+    offs, u_true, w, f = make_case(p)
+    rng = np.random.default_rng(2)
+    u = (u_true * (1 + 0.2 * (rng.standard_normal(u_true.shape) + 1j * rng.standard_normal(u_true.shape)))).astype(np.complex64)
+    wp = (w * (1 + 0.1 * rng.standard_normal(w.shape))).astype(np.complex64)
+    plan = od.ptycho_plan(od.Geometry(n, n, m, offs, eps=0.5), f32(f))
+    loss, gu, gw = od.stagm_loss_grad(plan, c64(u), c64(wp))
+    L, gu_o, gw_o = oracle.loss_grad(u, wp, offs, f.astype(np.float64), 0.5)
+    assert abs(float(loss.item()) - L) < 1e-5 * abs(L)
+    assert rel_l2(host(gu), gu_o) < 1e-5
+    assert rel_l2(host(gw), gw_o) < 1e-5

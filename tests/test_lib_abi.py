@@ -1,0 +1,64 @@
+"""The C ABI library loads without a GPU and exports every symbol its header declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2011_00162_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "od2p.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["ptycho_plan", "ptycho_forward", "stagm_prox", "overlap_add", "od2p_iterate",
+                     "probe_update", "od2p_init", "stagm_loss_grad", "ptycho_plan_destroy"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _lib.SIGNATURES, f"binding lacks {n}"
+
+
+def test_abi_version_and_argument_errors(lib):
+    assert lib.ptycho_abi_version() == 1
+    # argument checks return before any device work
+    assert lib.ptycho_plan(None, None, None, None) == _lib.ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    assert lib.ptycho_plan(ctypes.byref(h), None, None, None) == _lib.ERR_INVALID_ARG
+    assert b"NULL" in lib.ptycho_last_error()
+    assert lib.stagm_prox(None, None, None, -1, 0.5, 0.1, None) == _lib.ERR_INVALID_ARG
+    assert lib.stagm_prox(None, None, None, 0, 1.5, 0.1, None) == _lib.ERR_INVALID_ARG
+    assert lib.stagm_prox(None, None, None, 0, 0.5, 0.1, None) == _lib.OK
+    assert lib.od2p_iterate(None, 1, None) == _lib.ERR_INVALID_ARG
+    assert lib.ptycho_plan_destroy(None) == _lib.OK
+
+
+def test_plan_rejects_bad_geometry_before_device_work(lib):
+    import numpy as np
+    offs = np.array([[0, 0], [0, 70]], np.int32)  # second window leaves a 64-wide image
+    f = ctypes.c_void_p(1)  # never dereferenced: validation fails first
+    for m, eps, code in [(64, 0.5, _lib.ERR_INVALID_ARG), (48, 0.5, _lib.ERR_UNSUPPORTED),
+                         (16, 1.5, _lib.ERR_INVALID_ARG)]:
+        g = _lib.Geometry(64, 64, m, 2, offs.ctypes.data, 1, 1, 0, eps, 0.1, 0.1, 0, 0, 0, None)
+        h = ctypes.c_void_p()
+        assert lib.ptycho_plan(ctypes.byref(h), ctypes.byref(g), f, None) == code
+        assert not h.value

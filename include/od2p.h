@@ -239,6 +239,35 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c
                     float *loss_dev, ptycho_c32 *grad_u_dev, ptycho_c32 *grad_w_dev,
                     int32_t recompute, ptycho_stream_t stream);
 
+/*
+ * Allocation-free ST-AGM loss.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code running while
+ * a CUDA stream is being captured into a graph (allocation is not a capturable
+ * operation), hosts that hand a plug-in a fixed memory budget, and real-time
+ * loops that must not pay cudaMalloc's implicit device synchronisation.  It
+ * computes the same value as the `loss` output of stagm_loss_grad, without a
+ * plan: sum over frames j and pixels k of g_eps((F(w o S_j u))_k; f_jk).
+ *
+ * u_dev: img_h x img_w; w_dev: m x m (m in {16, 32, 64, 128});
+ * offsets_dev: device int32, n_frames x 2 top-left (row, col), each window
+ * inside the image (not checked on the host: they are device memory);
+ * f_dev: n_frames x m x m, natural frequency order; loss_dev: 1 float, written.
+ * It allocates nothing.  Its only scratch is a fixed array of 65536 floats
+ * (256 KiB) compiled into the library, which every GPU that loads the library
+ * holds until the process exits; a call covers at most 65536 thread blocks of
+ * frames (65536 frames for m = 64 or 128, 262144 for m = 32, 524288 for
+ * m = 16) and returns PTYCHO_ERR_INVALID_ARG beyond that.  The first call on
+ * each device looks the array's device address up, and the first call per m
+ * raises that kernel's shared-memory limit: make those first calls before any
+ * stream capture.  All calls share the one array (each call overwrites every
+ * slot it reads, so nothing needs clearing), so calls that overlap on the GPU
+ * -- on different streams, or from different threads -- race and must not be
+ * issued.  Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ */
+int stagm_loss_noalloc(const ptycho_c32 *u_dev, int32_t img_h, int32_t img_w, const ptycho_c32 *w_dev,
+                       int32_t m, const int32_t *offsets_dev, int32_t n_frames, const float *f_dev,
+                       float eps, float *loss_dev, ptycho_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,7 @@ SIGNATURES = {
     "od2p_get_state": (ctypes.c_int, [_P, _I32, _P, _P]),
     "od2p_set_state": (ctypes.c_int, [_P, _I32, _P, _P]),
     "stagm_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _I32, _P]),
+    "stagm_loss_noalloc": (ctypes.c_int, [_P, _I32, _I32, _P, _I32, _P, _I32, _P, _F, _P, _P]),
 }
 
 

@@ -23,6 +23,8 @@
 #include "od2p_internal.h"
 
 #include <cmath>
+#include <mutex>
+#include <string>
 
 namespace od2p {
 namespace {
@@ -879,3 +881,176 @@ int launch_permute_gamma(const ptycho_plan_s *p, const float2 *src, float2 *dst,
 }
 
 }  // namespace od2p
+
+// ---------------------------------------------------------------- allocation-free loss
+// stagm_loss_noalloc: the loss part of stagm_loss_grad without a plan and
+// without any device allocation.  Its only scratch -- one partial sum per
+// block -- is the file-scope array below, which every GPU that loads this
+// library holds for the life of the process.
+namespace od2p {
+namespace {
+
+constexpr int NOALLOC_MAX_BLOCKS = 65536;  // 256 KiB of partial sums
+__device__ __align__(256) float g_noalloc_partials[NOALLOC_MAX_BLOCKS];
+
+// Host-side device addresses of g_noalloc_partials, one per device, filled by
+// the first call on that device (the symbol's host name is not an address).
+constexpr int NOALLOC_MAX_DEVICES = 64;
+float *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+bool g_noalloc_attr[NOALLOC_MAX_DEVICES][4] = {};  // shared-memory limit raised, per m
+std::mutex g_noalloc_mu;
+
+struct NoallocArgs {
+    int32_t J, W;
+    const int32_t *offs;
+    const float2 *u, *w;
+    const float *f;  // natural frequency order
+    float *partials;
+    float eps;
+};
+
+template <int M>
+__global__ void __launch_bounds__(Radix<M>::NT) loss_noalloc_kernel(NoallocArgs a)
+{
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int P = M + 1, MM = M * M;
+    extern __shared__ float4 smem4[];
+    float2 *tw = reinterpret_cast<float2 *>(smem4);
+    float2 *buf = tw + M;
+    float *red = reinterpret_cast<float *>(buf + FPB * M * P);
+    const int j0 = blockIdx.x * FPB;
+    // twiddles exp(-2 pi i k / M) from the exact single-precision routine
+    for (int k = threadIdx.x; k < M; k += NT) {
+        float sn, cs;
+        sincospif(-2.f * (float)k / (float)M, &sn, &cs);
+        tw[k] = make_float2(cs, sn);
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
+        const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
+        if (j >= a.J) continue;
+        const float2 *uj = a.u + (size_t)a.offs[2 * j] * a.W + a.offs[2 * j + 1];
+        float2 x[R1];
+#pragma unroll
+        for (int t = 0; t < R1; ++t) {
+            const int row = n1 + R2 * t;
+            x[t] = cmul(__ldg(a.w + row * M + c), __ldg(uj + (size_t)row * a.W + c));
+        }
+        dft<R1, false>(x);
+        float2 *fb = buf + f * M * P;
+#pragma unroll
+        for (int s = 0; s < R1; ++s) fb[(n1 + R2 * s) * P + c] = cmul(x[s], tw[n1 * s]);
+    }
+    __syncthreads();
+    col_stage2<M, false>(buf);
+    __syncthreads();
+    row_stage1<M, false>(buf, tw);
+    __syncthreads();
+    float loss = 0.f;
+    const float inv_m = 1.f / (float)M, eps = a.eps;
+    for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
+        const int r = task % M, rest = task / M, s = rest % R1, f = rest / R1, j = j0 + f;
+        if (j >= a.J) continue;
+        float2 *fb = buf + f * M * P + r * P;
+        float2 x[R2];
+#pragma unroll
+        for (int t = 0; t < R2; ++t) x[t] = fb[R2 * s + t];
+        dft<R2, false>(x);
+        const int kr = r / R2 + R1 * (r % R2);
+#pragma unroll
+        for (int t = 0; t < R2; ++t) {
+            const int pc = R2 * s + t, kc = pc / R2 + R1 * (pc % R2);
+            const float sf = sqrtf(fmaxf(__ldg(a.f + (size_t)j * MM + kr * M + kc), 0.f));
+            const float2 xv = cscale(x[t], inv_m);
+            const float ax = sqrtf(xv.x * xv.x + xv.y * xv.y);
+            loss += ax < eps * sf ? 0.5f * (1.f - eps) * (sf * sf - ax * ax / eps)
+                                  : 0.5f * (ax - sf) * (ax - sf);
+        }
+    }
+    const float tot = block_sum_fixed(loss, red);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
+}
+
+// Sum of the n partials in a fixed order: each thread a contiguous run, then warps in order.
+__global__ void __launch_bounds__(256) noalloc_sum_kernel(int n, const float *partials, float *out)
+{
+    __shared__ double red[8];
+    const int per = (n + 255) / 256;
+    double t = 0.0;
+    for (int i = threadIdx.x * per; i < min(n, (threadIdx.x + 1) * per); ++i) t += partials[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < 8; ++i) s += red[i];
+        *out = (float)s;
+    }
+}
+
+template <int M>
+int loss_noalloc_m(const NoallocArgs &base, float *loss, cudaStream_t s, bool setup)
+{
+    if (setup)
+        OD2P_CUDA(cudaFuncSetAttribute(loss_noalloc_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<M>()));
+    const int blocks = (base.J + Radix<M>::FPB - 1) / Radix<M>::FPB;
+    if (blocks > NOALLOC_MAX_BLOCKS)
+        return fail(PTYCHO_ERR_INVALID_ARG,
+                    "stagm_loss_noalloc: at most " + std::to_string((long long)NOALLOC_MAX_BLOCKS * Radix<M>::FPB) +
+                        " frames of side " + std::to_string(M) + " (fixed scratch)");
+    loss_noalloc_kernel<M><<<blocks, Radix<M>::NT, smem_bytes<M>(), s>>>(base);
+    OD2P_CUDA(cudaGetLastError());
+    noalloc_sum_kernel<<<1, 256, 0, s>>>(blocks, base.partials, loss);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+}  // namespace
+}  // namespace od2p
+
+extern "C" int stagm_loss_noalloc(const ptycho_c32 *u, int32_t img_h, int32_t img_w, const ptycho_c32 *w,
+                                  int32_t m, const int32_t *offsets_dev, int32_t n_frames, const float *f,
+                                  float eps, float *loss, ptycho_stream_t stream)
+{
+    using namespace od2p;
+    if (!u || !w || !offsets_dev || !f || !loss) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    if (!supported_m(m)) return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    if (n_frames < 1 || img_h < m || img_w < m) return fail(PTYCHO_ERR_INVALID_ARG, "need n_frames >= 1 and an image at least m x m");
+    if (!(eps > 0.f && eps < 1.f)) return fail(PTYCHO_ERR_INVALID_ARG, "eps must be in (0, 1)");
+    // per-device set-up: the device address of the file-scope scratch array
+    int dev = 0;
+    OD2P_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(PTYCHO_ERR_UNSUPPORTED, "device index out of range");
+    const int mi = m == 16 ? 0 : m == 32 ? 1 : m == 64 ? 2 : 3;
+    bool setup = false;
+    float *scratch;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            OD2P_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_partials));
+            g_noalloc_ptr[dev] = static_cast<float *>(ptr);
+        }
+        scratch = g_noalloc_ptr[dev];
+        setup = !g_noalloc_attr[dev][mi];
+        g_noalloc_attr[dev][mi] = true;
+    }
+    NoallocArgs a;
+    a.J = n_frames;
+    a.W = img_w;
+    a.offs = offsets_dev;
+    a.u = reinterpret_cast<const float2 *>(u);
+    a.w = reinterpret_cast<const float2 *>(w);
+    a.f = f;
+    a.partials = scratch;
+    a.eps = eps;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (m) {
+    case 16: return loss_noalloc_m<16>(a, loss, s, setup);
+    case 32: return loss_noalloc_m<32>(a, loss, s, setup);
+    case 64: return loss_noalloc_m<64>(a, loss, s, setup);
+    default: return loss_noalloc_m<128>(a, loss, s, setup);
+    }
+}

@@ -11,6 +11,7 @@ import torch
 import oracle
 import paper_2011_00162_gb300 as od
 from paper_2011_00162_gb300 import synth
+from paper_2011_00162_gb300 import build as odbuild
 
 from _cases import make_case, phase_aligned_rel, rel_l2
 
@@ -52,7 +53,7 @@ def pair_of(p, offs, w, f, u0=None, **kw):
 def _built():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    od.build.build()
+    odbuild.build()
 
 
 # ----------------------------------------------------------------------------- pointwise / operators

@@ -29,8 +29,10 @@
 namespace od2p {
 namespace {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add / subtract as one packed FP32x2 instruction each (sm_100+):
+// per component exactly a + b and a - b (b * -1 is exact, one rounding).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -127,10 +129,10 @@ template <int M> __device__ __forceinline__ int pos_of(int k)
 
 // ---------------------------------------------------------------- shared stages
 // Column-direction stage 2 (forward or inverse) over all FPB frames.
-template <int M, bool INV>
+template <int M, bool INV, int FPB = Radix<M>::FPB, int NT = Radix<M>::NT>
 __device__ __forceinline__ void col_stage2(float2 *buf)
 {
-    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2;
     constexpr int P = M + 1;
     for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
         const int c = task % M, rest = task / M, s = rest % R1, f = rest / R1;
@@ -145,10 +147,10 @@ __device__ __forceinline__ void col_stage2(float2 *buf)
 }
 
 // Row-direction stage 1, forward (DFT then twiddle) or inverse (twiddle then DFT).
-template <int M, bool INV>
+template <int M, bool INV, int FPB = Radix<M>::FPB, int NT = Radix<M>::NT>
 __device__ __forceinline__ void row_stage1(float2 *buf, const float2 *tw)
 {
-    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2;
     constexpr int P = M + 1;
     for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
         const int r = task % M, rest = task / M, n1 = rest % R2, f = rest / R2;
@@ -171,10 +173,10 @@ __device__ __forceinline__ void row_stage1(float2 *buf, const float2 *tw)
 }
 
 // Column-direction stage 1 reading / writing shared memory.
-template <int M, bool INV>
+template <int M, bool INV, int FPB = Radix<M>::FPB, int NT = Radix<M>::NT>
 __device__ __forceinline__ void col_stage1(float2 *buf, const float2 *tw)
 {
-    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2;
     constexpr int P = M + 1;
     for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
         const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2;
@@ -197,10 +199,10 @@ __device__ __forceinline__ void col_stage1(float2 *buf, const float2 *tw)
 }
 
 // Row-direction stage 2 in shared memory (forward or inverse).
-template <int M, bool INV>
+template <int M, bool INV, int FPB = Radix<M>::FPB, int NT = Radix<M>::NT>
 __device__ __forceinline__ void row_stage2(float2 *buf)
 {
-    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2;
     constexpr int P = M + 1;
     for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
         const int r = task % M, rest = task / M, s = rest % R1, f = rest / R1;
@@ -215,13 +217,13 @@ __device__ __forceinline__ void row_stage2(float2 *buf)
 }
 
 // Column stage 1 whose input is the exit wave w o S_j u read from global memory.
-template <int M>
+template <int M, int FPB = Radix<M>::FPB, int NT = Radix<M>::NT>
 __device__ __forceinline__ void col_stage1_load(float2 *buf, const float2 *tw, int j0, int J,
                                                 const float2 *w_shared, const float2 *Wd,
                                                 const int32_t *frame_sub, const float2 *u,
                                                 const int32_t *frame_base, const int32_t *frame_pitch)
 {
-    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2;
     constexpr int P = M + 1;
     for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
         const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
@@ -244,11 +246,11 @@ __device__ __forceinline__ void col_stage1_load(float2 *buf, const float2 *tw, i
 
 // Column stage 1^H writing natural-order frames to global memory, scaled by
 // `scale` and, when wconj is given, multiplied by conj(wconj).
-template <int M>
+template <int M, int FPB = Radix<M>::FPB, int NT = Radix<M>::NT>
 __device__ __forceinline__ void col_stage1_store(float2 *buf, const float2 *tw, int j0, int J,
                                                  float2 *out, float scale, const float2 *wconj)
 {
-    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2;
     constexpr int P = M + 1;
     for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
         const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
@@ -289,17 +291,21 @@ struct ProxConst {
 };
 
 // eq. (Prox_sol) with the threshold read as |y| < (eps - (1-eps)/lam) sqrt f.
+// z = y * rho / |y| with 1/|y| from the hardware reciprocal square root
+// (relative error ~1e-7, far inside the FP32 parity budget); y = 0 gives (rho, 0).
 __device__ __forceinline__ float2 stagm_prox(float2 y, float sf, const ProxConst &k)
 {
-    const float ay = sqrtf(y.x * y.x + y.y * y.y);
+    const float y2 = y.x * y.x + y.y * y.y;
+    const float inv = rsqrtf(y2);  // +inf at y = 0, used only when y2 > 0
+    const float ay = y2 > 0.f ? y2 * inv : 0.f;
     float rho;
     if (ay < k.c_thr * sf)
         rho = fmaxf(0.f, k.c_k1 * ay);
     else
         rho = (sf + k.lam * ay) * k.inv1plam;
-    if (ay > 0.f) {
-        const float s = rho / ay;
-        return make_float2(y.x * s, y.y * s);
+    if (y2 > 0.f) {
+        const float sc = rho * inv;
+        return make_float2(y.x * sc, y.y * sc);
     }
     return make_float2(rho, 0.f);
 }
@@ -323,82 +329,190 @@ struct FrameArgs {
     const float *sqrtf_;      // transposed position layout
     float2 *q;                // out: F^*(z - Gamma^{n+1}), natural spatial order
     float *rf_part;           // out: one per block
+    int32_t *err;             // set to 1 if a pipeline wait gives up
     const float2 *tw;
     ProxConst pc;
 };
 
-template <int M>
-__global__ void __launch_bounds__(Radix<M>::NT, Radix<M>::MINB) frame_update_kernel(FrameArgs a)
+// Launch shape of the persistent frame update: frames per group, threads, and
+// whether Gamma is staged in shared memory (m = 128 only stages sqrt f: the
+// frame buffer already takes 132 KB).
+template <int M> struct K1Cfg;
+// MINB: resident blocks per SM the register budget is sized for (shared memory
+// allows at least as many).
+template <> struct K1Cfg<16> { static constexpr int FPB = 8, NT = 256, STAGE_G = 1, MINB = 4; };
+template <> struct K1Cfg<32> { static constexpr int FPB = 4, NT = 256, STAGE_G = 1, MINB = 2; };
+template <> struct K1Cfg<64> { static constexpr int FPB = 1, NT = 512, STAGE_G = 1, MINB = 2; };
+template <> struct K1Cfg<128> { static constexpr int FPB = 1, NT = 1024, STAGE_G = 0, MINB = 1; };
+
+template <int M> constexpr size_t k1_smem_bytes()
 {
-    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = Radix<M>::FPB, NT = Radix<M>::NT;
+    constexpr size_t FPB = K1Cfg<M>::FPB, MM = (size_t)M * M;
+    return 128 + (K1Cfg<M>::STAGE_G ? sizeof(float2) * FPB * MM : 0) + sizeof(float) * FPB * MM +
+           sizeof(float2) * (M + FPB * M * (M + 1)) + sizeof(float) * (K1Cfg<M>::NT / 32);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// TMA bulk copy global -> shared, completing `bytes` on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Every wait is bounded: after 2^22 polls (seconds) it reports failure.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+{
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Persistent: block b handles frame groups b, b + grid, ...  While a group's
+// forward FFT runs, the TMA unit brings its Gamma and sqrt f slices into shared
+// memory (issued when the previous group's prox finished with the staging
+// buffers), and the next group's exit-wave windows are prefetched into L2.
+template <int M>
+__global__ void __launch_bounds__(K1Cfg<M>::NT, K1Cfg<M>::MINB) frame_update_kernel(FrameArgs a)
+{
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = K1Cfg<M>::FPB, NT = K1Cfg<M>::NT;
     constexpr int P = M + 1, MM = M * M;
-    extern __shared__ float4 smem4[];
-    float2 *tw = reinterpret_cast<float2 *>(smem4);
+    constexpr bool SG = K1Cfg<M>::STAGE_G != 0;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    float2 *stg_g = reinterpret_cast<float2 *>(smem + 128);
+    float *stg_f = reinterpret_cast<float *>(smem + 128 + (SG ? sizeof(float2) * FPB * MM : 0));
+    float2 *tw = reinterpret_cast<float2 *>(stg_f + FPB * MM);
     float2 *buf = tw + M;
     float *red = reinterpret_cast<float *>(buf + FPB * M * P);
-    const int j0 = blockIdx.x * FPB;
-    {
-        // Gamma_j and sqrt(f_j) are first needed after three FFT stages: start
-        // moving this block's slices from HBM into L2 now, in 4 KiB pieces.
-        const int nf = min(FPB, a.J - j0);
-        const unsigned g_bytes = (unsigned)(nf * MM * sizeof(float2));
-        const unsigned f_bytes = (unsigned)(nf * MM * sizeof(float));
-        const char *gp = reinterpret_cast<const char *>(a.gamma + (size_t)j0 * MM);
-        const char *fp = reinterpret_cast<const char *>(a.sqrtf_ + (size_t)j0 * MM);
-        const unsigned n_g = (g_bytes + 4095) / 4096, n_f = (f_bytes + 4095) / 4096;
-        for (unsigned i = threadIdx.x; i < n_g + n_f; i += NT) {
-            const bool is_g = i < n_g;
-            const unsigned off = (is_g ? i : i - n_g) * 4096u;
-            const unsigned tot = is_g ? g_bytes : f_bytes;
-            bulk_prefetch_l2((is_g ? gp : fp) + off, min(4096u, tot - off));
+    const int n_groups = (a.J + FPB - 1) / FPB;
+
+    auto issue = [&](int g) {  // one thread: stage group g's Gamma / sqrt f
+        const int j0 = g * FPB, nf = min(FPB, a.J - j0);
+        const unsigned fbytes = (unsigned)(nf * MM * sizeof(float));
+        const unsigned gbytes = SG ? (unsigned)(nf * MM * sizeof(float2)) : 0u;
+        mbar_expect_tx(bar, fbytes + gbytes);
+        if (SG) bulk_g2s(stg_g, a.gamma + (size_t)j0 * MM, gbytes, bar);
+        bulk_g2s(stg_f, a.sqrtf_ + (size_t)j0 * MM, fbytes, bar);
+    };
+    auto prefetch_windows = [&](int g) {  // all threads: next group's exit-wave windows into L2
+        constexpr int LINES = (M * 8 + 127) / 128 + 1;
+        const int j0 = g * FPB;
+        for (int i = threadIdx.x; i < FPB * M * LINES; i += NT) {
+            const int f = i / (M * LINES), row = (i / LINES) % M, l = i % LINES, j = j0 + f;
+            if (j >= a.J) continue;
+            const char *rp = reinterpret_cast<const char *>(a.u + a.frame_base[j] + (size_t)row * a.frame_pitch[j]);
+            prefetch_l2(rp + min(l * 128, M * 8 - 8));
         }
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
     }
     for (int k = threadIdx.x; k < M; k += NT) tw[k] = a.tw[k];
     __syncthreads();
-
-    // Step 1: psi = w o S_j u_d^n, then F psi (forward column stages)
-    col_stage1_load<M>(buf, tw, j0, a.J, a.w, a.Wd, a.frame_sub, a.u, a.frame_base, a.frame_pitch);
-    __syncthreads();
-    col_stage2<M, false>(buf);
-    __syncthreads();
-    row_stage1<M, false>(buf, tw);
-    __syncthreads();
-
-    // last forward stage, prox and Gamma update, first inverse stage -- in registers
+    int g = blockIdx.x;
+    if (threadIdx.x == 0 && g < n_groups) issue(g);
+    unsigned phase = 0;
     float rf = 0.f;
     const float inv_m = 1.f / (float)M;
-    for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
-        const int r = task % M, rest = task / M, s = rest % R1, f = rest / R1, j = j0 + f;
-        if (j >= a.J) continue;
-        float2 *fb = buf + f * M * P + r * P;
-        float2 x[R2];
-#pragma unroll
-        for (int t = 0; t < R2; ++t) x[t] = fb[R2 * s + t];
-        dft<R2, false>(x);
-        const size_t base = (size_t)j * MM + r;
-#pragma unroll
-        for (int t = 0; t < R2; ++t) {
-            const size_t idx = base + (size_t)(R2 * s + t) * M;
-            const float2 ax = cscale(x[t], inv_m);          // (A_d u_d^n)_k
-            const float sf = __ldg(a.sqrtf_ + idx);
-            const float2 g = a.gamma[idx];
-            rf += fabsf(sqrtf(ax.x * ax.x + ax.y * ax.y) - sf);
-            const float2 y = cadd(g, ax);                    // Gamma^n + A_d u_d^n
-            const float2 z = stagm_prox(y, sf, a.pc);         // eq. updateZ
-            const float2 gn = csub(y, z);                    // eq. updateM-1-multi
-            a.gamma[idx] = gn;
-            x[t] = csub(z, gn);                              // z^{n+1} - Gamma^{n+1}
+    for (; g < n_groups; g += gridDim.x) {
+        const int j0 = g * FPB;
+        if (g + (int)gridDim.x < n_groups) prefetch_windows(g + gridDim.x);
+        if (!SG && threadIdx.x == 0) {
+            const int nf = min(FPB, a.J - j0);
+            const char *gp = reinterpret_cast<const char *>(a.gamma + (size_t)j0 * MM);
+            for (unsigned off = 0; off < (unsigned)(nf * MM * sizeof(float2)); off += 16384u)
+                bulk_prefetch_l2(gp + off, min(16384u, (unsigned)(nf * MM * sizeof(float2)) - off));
         }
-        dft<R2, true>(x);
+        // Step 1: psi = w o S_j u_d^n, then F psi (three of the four forward stages)
+        col_stage1_load<M, FPB, NT>(buf, tw, j0, a.J, a.w, a.Wd, a.frame_sub, a.u, a.frame_base, a.frame_pitch);
+        __syncthreads();
+        col_stage2<M, false, FPB, NT>(buf);
+        __syncthreads();
+        row_stage1<M, false, FPB, NT>(buf, tw);
+        const bool ok = mbar_wait_bounded(bar, phase);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) *a.err = 1;
+            return;
+        }
+        phase ^= 1u;
+        // last forward stage, prox and Gamma update, first inverse stage -- in registers
+        for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
+            const int r = task % M, rest = task / M, s = rest % R1, f = rest / R1, j = j0 + f;
+            if (j >= a.J) continue;
+            float2 *fb = buf + f * M * P + r * P;
+            float2 x[R2];
 #pragma unroll
-        for (int t = 0; t < R2; ++t) fb[R2 * s + t] = x[t];
+            for (int t = 0; t < R2; ++t) x[t] = fb[R2 * s + t];
+            dft<R2, false>(x);
+            const int lbase = f * MM + r;
+#pragma unroll
+            for (int t = 0; t < R2; ++t) {
+                const int li = lbase + (R2 * s + t) * M;
+                const size_t gi = (size_t)j0 * MM + li;
+                const float2 ax = cscale(x[t], inv_m);   // (A_d u_d^n)_k
+                const float sf = stg_f[li];
+                const float2 gm = SG ? stg_g[li] : a.gamma[gi];
+                const float a2 = ax.x * ax.x + ax.y * ax.y;
+                rf += fabsf((a2 > 0.f ? a2 * rsqrtf(a2) : 0.f) - sf);  // | |A_d u_d| - sqrt f |
+                const float2 y = cadd(gm, ax);            // Gamma^n + A_d u_d^n
+                const float2 z = stagm_prox(y, sf, a.pc); // eq. updateZ
+                const float2 gn = csub(y, z);             // eq. updateM-1-multi
+                a.gamma[gi] = gn;
+                x[t] = csub(z, gn);                       // z^{n+1} - Gamma^{n+1}
+            }
+            dft<R2, true>(x);
+#pragma unroll
+            for (int t = 0; t < R2; ++t) fb[R2 * s + t] = x[t];
+        }
+        __syncthreads();  // staging buffers are free: start the next group's copies
+        if (threadIdx.x == 0 && g + (int)gridDim.x < n_groups) {
+            fence_proxy_async_smem();
+            issue(g + gridDim.x);
+        }
+        row_stage1<M, true, FPB, NT>(buf, tw);
+        __syncthreads();
+        col_stage2<M, true, FPB, NT>(buf);
+        __syncthreads();
+        col_stage1_store<M, FPB, NT>(buf, tw, j0, a.J, a.q, inv_m, nullptr);
+        __syncthreads();
     }
-    __syncthreads();
-    row_stage1<M, true>(buf, tw);
-    __syncthreads();
-    col_stage2<M, true>(buf);
-    __syncthreads();
-    col_stage1_store<M>(buf, tw, j0, a.J, a.q, inv_m, nullptr);
     const float tot = block_sum_fixed(rf, red);
     if (threadIdx.x == 0) a.rf_part[blockIdx.x] = tot;
 }
@@ -667,9 +781,27 @@ int set_smem(K kernel)
 }
 
 template <int M>
+int k1_grid_m(int J, int *grid)
+{
+    static int per_sm = 0, n_sm = 0;
+    if (!per_sm) {
+        OD2P_CUDA(cudaFuncSetAttribute(frame_update_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)k1_smem_bytes<M>()));
+        int dev = 0;
+        OD2P_CUDA(cudaGetDevice(&dev));
+        OD2P_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, frame_update_kernel<M>, K1Cfg<M>::NT,
+                                                                k1_smem_bytes<M>()));
+        if (per_sm < 1) return fail(PTYCHO_ERR_UNSUPPORTED, "frame update does not fit on an SM");
+    }
+    const int groups = (J + K1Cfg<M>::FPB - 1) / K1Cfg<M>::FPB;
+    *grid = std::min(groups, per_sm * n_sm);
+    return PTYCHO_OK;
+}
+
+template <int M>
 int frame_update_m(ptycho_plan_s *p, cudaStream_t s)
 {
-    if (int rc = set_smem<M>(frame_update_kernel<M>)) return rc;
     FrameArgs a;
     a.J = p->J;
     a.frame_sub = p->d_frame_sub;
@@ -682,10 +814,10 @@ int frame_update_m(ptycho_plan_s *p, cudaStream_t s)
     a.sqrtf_ = p->d_sqrtf;
     a.q = p->d_q;
     a.rf_part = p->d_rf_part;
+    a.err = p->d_err;
     a.tw = p->d_tw;
     a.pc = make_prox_const(p->eps, p->eta);
-    const int blocks = (p->J + Radix<M>::FPB - 1) / Radix<M>::FPB;
-    frame_update_kernel<M><<<blocks, Radix<M>::NT, smem_bytes<M>(), s>>>(a);
+    frame_update_kernel<M><<<p->n_k1_blocks, K1Cfg<M>::NT, k1_smem_bytes<M>(), s>>>(a);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
@@ -774,11 +906,24 @@ int frames_per_block(int m)
     }
 }
 
+// Number of blocks of the persistent frame update for J frames of side m.
+int frame_update_grid(int m, int J, int *grid)
+{
+    switch (m) {
+    case 16: return k1_grid_m<16>(J, grid);
+    case 32: return k1_grid_m<32>(J, grid);
+    case 64: return k1_grid_m<64>(J, grid);
+    case 128: return k1_grid_m<128>(J, grid);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    }
+}
+
 namespace {
 template <int M>
 int prepare_m()
 {
-    if (int rc = set_smem<M>(frame_update_kernel<M>)) return rc;
+    int grid = 0;
+    if (int rc = k1_grid_m<M>(1, &grid)) return rc;
     if (int rc = set_smem<M>(forward_kernel<M>)) return rc;
     if (int rc = set_smem<M>(ifft_weight_kernel<M>)) return rc;
     if (int rc = set_smem<M>(loss_kernel<M>)) return rc;

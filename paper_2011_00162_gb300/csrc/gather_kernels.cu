@@ -49,10 +49,12 @@ __device__ __forceinline__ void block_sum2_fixed(float &a, float &b, float *red)
 // ---------------------------------------------------------------- K2: subdomain update
 struct SubArgs {
     int32_t M;
-    const int32_t *offs, *rect, *nbr_ptr, *nbr, *pair_rect;
-    const int64_t *u_off, *lam_off;
+    const int32_t *rect;
+    const int64_t *u_off;
     const Tile *tiles;
-    const int32_t *tptr, *tlist;
+    const int32_t *tptr, *tnbr_ptr;
+    const ListEntry *tlist;
+    const NbrInfo *tnbr;
     const float2 *u_cur, *lam_cur, *q, *w, *Wd;
     float2 *u_next, *lam_next;
     float eta, r, gamma;
@@ -60,101 +62,91 @@ struct SubArgs {
     float *re_part;
 };
 
-// Largest per-tile frame list staged in shared memory; longer lists stream
-// the remainder from global memory in the same ascending order.
-constexpr int LIST_SMEM = 128;
+// One block per TILE_H x TILE_W tile, one thread per pixel (warp = tile row).
+// The tile's frame list (ascending j) is staged in shared memory; an entry's
+// row test is warp-uniform, its column test per lane.  Only the neighbours
+// whose rectangles meet the tile are visited (interior tiles have none).
+constexpr int LIST_SMEM = 96;
+constexpr int NBR_SMEM = 16;
 
 __global__ void __launch_bounds__(GATHER_THREADS) subdomain_update_kernel(SubArgs a)
 {
     __shared__ float red[2 * (GATHER_THREADS / 32)];
-    __shared__ int3 lst[LIST_SMEM];  // (j, row offset, col offset) of the tile's frames
+    __shared__ ListEntry lst[LIST_SMEM];
+    __shared__ NbrInfo nbs[NBR_SMEM];
     const Tile tile = a.tiles[blockIdx.x];
     const int d = tile.reg;
     const int32_t *rc = a.rect + 4 * d;
     const int hd = rc[2] - rc[0], wd = rc[3] - rc[1];
-    const int lr = tile.r0 + threadIdx.x / TILE_W, lc = tile.c0 + threadIdx.x % TILE_W;
-    const bool active = lr < hd && lc < wd;
+    const int ty = threadIdx.x / TILE_W, tx = threadIdx.x % TILE_W;
+    const int lr = tile.r0 + ty, lc = tile.c0 + tx;
+    const bool row_ok = lr < hd;
+    const bool active = row_ok && lc < wd;
     const int R = rc[0] + lr, C = rc[1] + lc;
     const int M = a.M, MM = M * M;
     const int k0 = a.tptr[blockIdx.x], nk = a.tptr[blockIdx.x + 1] - k0;
-    for (int i = threadIdx.x; i < min(nk, LIST_SMEM); i += GATHER_THREADS) {
-        const int j = a.tlist[k0 + i];
-        lst[i] = make_int3(j, a.offs[2 * j], a.offs[2 * j + 1]);
-    }
+    const int n0 = a.tnbr_ptr[blockIdx.x], nnb = a.tnbr_ptr[blockIdx.x + 1] - n0;
+    for (int i = threadIdx.x; i < min(nk, LIST_SMEM); i += GATHER_THREADS) lst[i] = a.tlist[k0 + i];
+    for (int i = threadIdx.x; i < min(nnb, NBR_SMEM); i += GATHER_THREADS) nbs[i] = a.tnbr[n0 + i];
     __syncthreads();
     float dn = 0.f, nn = 0.f;
-    if (active) {
+    if (row_ok) {
         // A_d^*(z - Gamma) and sum_j S_j^T |w|^2 at this pixel, frames in ascending j
-        const float2 *w = a.blind ? a.Wd + (size_t)d * MM : a.w;
+        const float2 *w = a.blind ? a.Wd + d * MM : a.w;
         float2 acc = make_float2(0.f, 0.f);
         float nrm = 0.f;
-        constexpr int U = 4;  // loads of U frames in flight; accumulation stays in order
-        for (int k = 0; k < nk; k += U) {
-            float2 qv[U], wv[U];
-            bool hit[U];
-#pragma unroll
-            for (int t = 0; t < U; ++t) {
-                hit[t] = false;
-                if (k + t < nk) {
-                    const int3 e = k + t < LIST_SMEM ? lst[k + t]
-                                                     : make_int3(a.tlist[k0 + k + t], a.offs[2 * a.tlist[k0 + k + t]],
-                                                                 a.offs[2 * a.tlist[k0 + k + t] + 1]);
-                    const int dr = R - e.y, dc = C - e.z;
-                    if ((unsigned)dr < (unsigned)M && (unsigned)dc < (unsigned)M) {
-                        hit[t] = true;
-                        wv[t] = __ldg(w + dr * M + dc);
-                        qv[t] = __ldg(a.q + (size_t)e.x * MM + dr * M + dc);
-                    }
-                }
+        for (int k = 0; k < nk; ++k) {
+            const ListEntry e = k < LIST_SMEM ? lst[k] : a.tlist[k0 + k];
+            const int dr = e.dr + ty;
+            if ((unsigned)dr >= (unsigned)M) continue;  // same for the whole warp
+            const int dc = e.dc + tx;
+            if (active && (unsigned)dc < (unsigned)M) {
+                const int o = dr * M + dc;
+                const float2 wv = __ldg(w + o);
+                const float2 qv = __ldg(a.q + e.j * MM + o);
+                acc = cadd(acc, cconjmul(wv, qv));
+                nrm += cabs2(wv);
             }
-#pragma unroll
-            for (int t = 0; t < U; ++t)
-                if (hit[t]) {
-                    acc = cadd(acc, cconjmul(wv[t], qv[t]));
-                    nrm += cabs2(wv[t]);
-                }
         }
-        const int64_t ui = a.u_off[d] + (int64_t)lr * wd + lc;
-        const float2 u_old = a.u_cur[ui];
-        float2 num = cscale(acc, a.eta);
-        float den = a.eta * nrm;
-        // consensus v_{d,e} (eq. updateV-multi) and the r-terms of the u-update
-        for (int i = a.nbr_ptr[d]; i < a.nbr_ptr[d + 1]; ++i) {
-            const int e = a.nbr[3 * i], kde = a.nbr[3 * i + 1], ked = a.nbr[3 * i + 2];
-            const int32_t *re = a.rect + 4 * e;
-            if (R < re[0] || R >= re[2] || C < re[1] || C >= re[3]) continue;
-            const float2 ue = a.u_cur[a.u_off[e] + (int64_t)(R - re[0]) * (re[3] - re[1]) + (C - re[1])];
-            const int32_t *pr = a.pair_rect + 4 * kde;
-            const int64_t li = (int64_t)(R - pr[0]) * (pr[3] - pr[1]) + (C - pr[1]);
-            const float2 lde = a.lam_cur[a.lam_off[kde] + li], led = a.lam_cur[a.lam_off[ked] + li];
-            // same operand order on both sides of the pair -> bitwise equal v
-            const float2 v = d < e ? cscale(cadd(cadd(u_old, ue), cadd(lde, led)), 0.5f)
-                                   : cscale(cadd(cadd(ue, u_old), cadd(led, lde)), 0.5f);
-            num = cadd(num, cscale(csub(v, lde), a.r));
-            den += a.r;
+        if (active) {
+            const int ui = (int)a.u_off[d] + lr * wd + lc;
+            const float2 u_old = a.u_cur[ui];
+            float2 num = cscale(acc, a.eta);
+            float den = a.eta * nrm;
+            // consensus v_{d,e} (eq. updateV-multi) and the r-terms of the u-update
+            for (int i = 0; i < nnb; ++i) {
+                const NbrInfo nb = i < NBR_SMEM ? nbs[i] : a.tnbr[n0 + i];
+                if (R < nb.r0 || R >= nb.r1 || C < nb.c0 || C >= nb.c1) continue;
+                const float2 ue = a.u_cur[nb.u_base + (R - nb.r0) * nb.u_pitch + (C - nb.c0)];
+                const int li = (R - nb.p_r0) * nb.p_pitch + (C - nb.p_c0);
+                const float2 lde = a.lam_cur[nb.lam_de + li], led = a.lam_cur[nb.lam_ed + li];
+                // same operand order on both sides of the pair -> bitwise equal v
+                const float2 v = nb.d_first ? cscale(cadd(cadd(u_old, ue), cadd(lde, led)), 0.5f)
+                                            : cscale(cadd(cadd(ue, u_old), cadd(led, lde)), 0.5f);
+                num = cadd(num, cscale(csub(v, lde), a.r));
+                den += a.r;
+            }
+            if (a.blind) {
+                num = cadd(num, cscale(u_old, a.gamma));
+                den += a.gamma;
+            }
+            // eq. Alg1-solver-u; a pixel with no illumination and no overlap keeps its value
+            const float2 u_new = den > 0.f ? make_float2(num.x / den, num.y / den) : u_old;
+            a.u_next[ui] = u_new;
+            // eq. updateM-2-multi: Lambda_{d,e} += pi u_d^{n+1} - v
+            for (int i = 0; i < nnb; ++i) {
+                const NbrInfo nb = i < NBR_SMEM ? nbs[i] : a.tnbr[n0 + i];
+                if (R < nb.r0 || R >= nb.r1 || C < nb.c0 || C >= nb.c1) continue;
+                const float2 ue = a.u_cur[nb.u_base + (R - nb.r0) * nb.u_pitch + (C - nb.c0)];
+                const int li = (R - nb.p_r0) * nb.p_pitch + (C - nb.p_c0);
+                const float2 lde = a.lam_cur[nb.lam_de + li], led = a.lam_cur[nb.lam_ed + li];
+                const float2 v = nb.d_first ? cscale(cadd(cadd(u_old, ue), cadd(lde, led)), 0.5f)
+                                            : cscale(cadd(cadd(ue, u_old), cadd(led, lde)), 0.5f);
+                a.lam_next[nb.lam_de + li] = csub(cadd(lde, u_new), v);
+            }
+            dn = cabs2(csub(u_new, u_old));
+            nn = cabs2(u_new);
         }
-        if (a.blind) {
-            num = cadd(num, cscale(u_old, a.gamma));
-            den += a.gamma;
-        }
-        // eq. Alg1-solver-u; a pixel with no illumination and no overlap keeps its value
-        const float2 u_new = den > 0.f ? make_float2(num.x / den, num.y / den) : u_old;
-        a.u_next[ui] = u_new;
-        // eq. updateM-2-multi: Lambda_{d,e} += pi u_d^{n+1} - v
-        for (int i = a.nbr_ptr[d]; i < a.nbr_ptr[d + 1]; ++i) {
-            const int e = a.nbr[3 * i], kde = a.nbr[3 * i + 1], ked = a.nbr[3 * i + 2];
-            const int32_t *re = a.rect + 4 * e;
-            if (R < re[0] || R >= re[2] || C < re[1] || C >= re[3]) continue;
-            const float2 ue = a.u_cur[a.u_off[e] + (int64_t)(R - re[0]) * (re[3] - re[1]) + (C - re[1])];
-            const int32_t *pr = a.pair_rect + 4 * kde;
-            const int64_t li = (int64_t)(R - pr[0]) * (pr[3] - pr[1]) + (C - pr[1]);
-            const float2 lde = a.lam_cur[a.lam_off[kde] + li], led = a.lam_cur[a.lam_off[ked] + li];
-            const float2 v = d < e ? cscale(cadd(cadd(u_old, ue), cadd(lde, led)), 0.5f)
-                                   : cscale(cadd(cadd(ue, u_old), cadd(led, lde)), 0.5f);
-            a.lam_next[a.lam_off[kde] + li] = csub(cadd(lde, u_new), v);
-        }
-        dn = cabs2(csub(u_new, u_old));
-        nn = cabs2(u_new);
     }
     block_sum2_fixed(dn, nn, red);
     if (threadIdx.x == 0) {
@@ -166,19 +158,20 @@ __global__ void __launch_bounds__(GATHER_THREADS) subdomain_update_kernel(SubArg
 // ---------------------------------------------------------------- image gather
 // out(p) = sum_{j covering p, ascending} (w ? conj(w(p - o_j)) : 1) * h_j(p - o_j)
 __global__ void __launch_bounds__(GATHER_THREADS) image_gather_kernel(
-    int M, int H, int W, const int32_t *offs, const Tile *tiles, const int32_t *tptr,
-    const int32_t *tlist, const float2 *h, const float2 *w, float2 *out)
+    int M, int H, int W, const Tile *tiles, const int32_t *tptr, const ListEntry *tlist,
+    const float2 *h, const float2 *w, float2 *out)
 {
     const Tile tile = tiles[blockIdx.x];
-    const int R = tile.r0 + threadIdx.x / TILE_W, C = tile.c0 + threadIdx.x % TILE_W;
+    const int ty = threadIdx.x / TILE_W, tx = threadIdx.x % TILE_W;
+    const int R = tile.r0 + ty, C = tile.c0 + tx;
     if (R >= H || C >= W) return;
     const int MM = M * M;
     float2 acc = make_float2(0.f, 0.f);
     for (int k = tptr[blockIdx.x]; k < tptr[blockIdx.x + 1]; ++k) {
-        const int j = tlist[k];
-        const int dr = R - offs[2 * j], dc = C - offs[2 * j + 1];
+        const ListEntry e = tlist[k];
+        const int dr = e.dr + ty, dc = e.dc + tx;
         if ((unsigned)dr < (unsigned)M && (unsigned)dc < (unsigned)M) {
-            const float2 hv = __ldg(h + (size_t)j * MM + dr * M + dc);
+            const float2 hv = __ldg(h + (size_t)e.j * MM + dr * M + dc);
             acc = cadd(acc, w ? cconjmul(__ldg(w + dr * M + dc), hv) : hv);
         }
     }
@@ -258,40 +251,58 @@ __global__ void probe_finalize_sum_kernel(int M, int n_chunks, const float2 *par
 }
 
 // ---------------------------------------------------------------- scalars
-__global__ void metrics_kernel(int n_rf, const float *rf_part, int D, const int32_t *reg_tile_ptr,
-                               const float *re_part, double *metrics)
+// Fixed-order sum of n values with one 256-thread block: thread t adds the
+// contiguous run [t*per, (t+1)*per) in order, then a fixed shuffle tree and
+// the eight warp sums in order.  Deterministic for a given n.
+__device__ double block_sum_runs(int n, const float *v, int stride, int offset, double *red)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double rf = 0.0;
-    for (int i = 0; i < n_rf; ++i) rf += rf_part[i];
-    metrics[0] = metrics[2] > 0.0 ? rf / metrics[2] : 0.0;
+    const int per = (n + 255) / 256;
+    double t = 0.0;
+    for (int i = threadIdx.x * per; i < min(n, (threadIdx.x + 1) * per); ++i) t += v[(size_t)i * stride + offset];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < 8; ++i) s += red[i];
+    return s;
+}
+
+// metrics[0] = sum rf_part / sum sqrt f (RF); metrics[1] = max over subdomains of
+// sqrt(sum dn / sum nn) over the subdomain's tiles (RE).  One block.
+__global__ void __launch_bounds__(256) metrics_kernel(int n_rf, const float *rf_part, int D,
+                                                      const int32_t *reg_tile_ptr, const float *re_part,
+                                                      double *metrics)
+{
+    __shared__ double red[8];
+    const double rf = block_sum_runs(n_rf, rf_part, 1, 0, red);
     double re = 0.0;
     for (int d = 0; d < D; ++d) {
-        double dn = 0.0, nn = 0.0;
-        for (int t = reg_tile_ptr[d]; t < reg_tile_ptr[d + 1]; ++t) {
-            dn += re_part[2 * t];
-            nn += re_part[2 * t + 1];
-        }
+        const int t0 = reg_tile_ptr[d], nt = reg_tile_ptr[d + 1] - t0;
+        const double dn = block_sum_runs(nt, re_part + 2 * (size_t)t0, 2, 0, red);
+        const double nn = block_sum_runs(nt, re_part + 2 * (size_t)t0, 2, 1, red);
         const double v = nn > 0.0 ? sqrt(dn / nn) : 0.0;
         re = v > re ? v : re;
     }
-    metrics[1] = re;
+    if (threadIdx.x == 0) {
+        metrics[0] = metrics[2] > 0.0 ? rf / metrics[2] : 0.0;
+        metrics[1] = re;
+    }
 }
 
-__global__ void sum_kernel(int n, const float *part, double *dst)
+__global__ void __launch_bounds__(256) sum_kernel(int n, const float *part, double *dst)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double t = 0.0;
-    for (int i = 0; i < n; ++i) t += part[i];
-    *dst = t;
+    __shared__ double red[8];
+    const double t = block_sum_runs(n, part, 1, 0, red);
+    if (threadIdx.x == 0) *dst = t;
 }
 
-__global__ void loss_sum_kernel(int n, const float *part, float *loss)
+__global__ void __launch_bounds__(256) loss_sum_kernel(int n, const float *part, float *loss)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double t = 0.0;
-    for (int i = 0; i < n; ++i) t += part[i];
-    *loss = (float)t;
+    __shared__ double red[8];
+    const double t = block_sum_runs(n, part, 1, 0, red);
+    if (threadIdx.x == 0) *loss = (float)t;
 }
 
 // u_d = R_d u0 (or 1), over the subdomain tiles
@@ -366,13 +377,10 @@ int launch_subdomain_update(ptycho_plan_s *p, cudaStream_t s)
 {
     SubArgs a;
     a.M = p->M;
-    a.offs = p->d_offs;
     a.rect = p->d_rect;
-    a.nbr_ptr = p->d_nbr_ptr;
-    a.nbr = p->d_nbr;
-    a.pair_rect = p->d_pair_rect;
     a.u_off = p->d_u_off;
-    a.lam_off = p->d_lam_off;
+    a.tnbr_ptr = p->sub_tiles.nbr_ptr;
+    a.tnbr = p->sub_tiles.nbr;
     a.tiles = p->sub_tiles.tiles;
     a.tptr = p->sub_tiles.ptr;
     a.tlist = p->sub_tiles.list;
@@ -397,7 +405,7 @@ int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w
                         cudaStream_t s)
 {
     image_gather_kernel<<<p->img_tiles.n_tiles, GATHER_THREADS, 0, s>>>(
-        p->M, p->H, p->W, p->d_offs, p->img_tiles.tiles, p->img_tiles.ptr, p->img_tiles.list, q, w, out);
+        p->M, p->H, p->W, p->img_tiles.tiles, p->img_tiles.ptr, p->img_tiles.list, q, w, out);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
@@ -439,14 +447,14 @@ int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, c
 
 int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s)
 {
-    loss_sum_kernel<<<1, 32, 0, s>>>(p->n_k1_blocks, p->d_loss_part, loss);
+    loss_sum_kernel<<<1, 256, 0, s>>>(p->n_loss_blocks, p->d_loss_part, loss);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
 
 int launch_metrics(ptycho_plan_s *p, cudaStream_t s)
 {
-    metrics_kernel<<<1, 32, 0, s>>>(p->n_k1_blocks, p->d_rf_part, p->D, p->sub_tiles.reg_ptr,
+    metrics_kernel<<<1, 256, 0, s>>>(p->n_k1_blocks, p->d_rf_part, p->D, p->sub_tiles.reg_ptr,
                                     p->d_re_part, p->d_metrics);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
@@ -454,7 +462,7 @@ int launch_metrics(ptycho_plan_s *p, cudaStream_t s)
 
 int launch_sum_sqrtf(ptycho_plan_s *p, cudaStream_t s)
 {
-    sum_kernel<<<1, 32, 0, s>>>(p->J, p->d_loss_part, p->d_metrics + 2);
+    sum_kernel<<<1, 256, 0, s>>>(p->J, p->d_loss_part, p->d_metrics + 2);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }

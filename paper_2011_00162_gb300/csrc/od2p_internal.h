@@ -36,12 +36,32 @@ struct Tile {
     int32_t reg, r0, c0, pad;
 };
 
+// Entry of a tile's frame list: frame j and the tile origin relative to the
+// window origin (tile_row0 - o_r, tile_col0 - o_c), so that a pixel at
+// (ty, tx) of the tile reads frame pixel (dr + ty, dc + tx).
+struct ListEntry {
+    int32_t j, dr, dc, pad;
+};
+
+struct NbrInfo;
+
 struct GatherTiles {
     int32_t n_tiles = 0;
     Tile *tiles = nullptr;        // device
     int32_t *ptr = nullptr;       // device, n_tiles + 1
-    int32_t *list = nullptr;      // device
+    ListEntry *list = nullptr;    // device
     int32_t *reg_ptr = nullptr;   // device, first tile of each region (+ end)
+    int32_t *nbr_ptr = nullptr;   // device, n_tiles + 1: neighbours meeting the tile
+    NbrInfo *nbr = nullptr;       // device
+};
+
+// A neighbour e of subdomain d, precomputed for the subdomain update.
+struct NbrInfo {
+    int32_t r0, c0, r1, c1;       // Omega_e
+    int32_t u_base, u_pitch;      // u_e storage: index of (r0, c0), row pitch
+    int32_t p_r0, p_c0, p_pitch;  // Omega_d n Omega_e: origin and row pitch of Lambda storage
+    int32_t lam_de, lam_ed;       // offsets of Lambda_{d,e} and Lambda_{e,d}
+    int32_t d_first;              // 1 if d < e (fixes the operand order of v)
 };
 
 // Frame groups of the fixed-order probe reductions, cut into chunks of
@@ -70,6 +90,7 @@ struct ptycho_plan_s {
     int32_t *d_offs = nullptr, *d_frame_sub = nullptr, *d_frame_base = nullptr,
             *d_frame_pitch = nullptr, *d_rect = nullptr, *d_nbr_ptr = nullptr, *d_nbr = nullptr,
             *d_pair_rect = nullptr, *d_img_base = nullptr;  // nbr: (e, pair d-e, pair e-d) per neighbour
+    od2p::NbrInfo *d_nbr_info = nullptr;  // per neighbour entry, same order as d_nbr
     int64_t *d_u_off = nullptr, *d_lam_off = nullptr;
     od2p::GatherTiles sub_tiles, img_tiles;
     od2p::ProbeGroups sub_groups, img_groups;
@@ -88,7 +109,9 @@ struct ptycho_plan_s {
     float *d_re_part = nullptr;        // 2 per subdomain tile
     float *d_loss_part = nullptr;
     double *d_metrics = nullptr;       // [rf, re, sum sqrt f]
-    int32_t n_k1_blocks = 0;
+    int32_t *d_err = nullptr;          // set by a kernel whose bounded wait gave up
+    int32_t n_k1_blocks = 0;           // blocks of the persistent frame update
+    int32_t n_loss_blocks = 0;         // blocks of the loss kernel
     int32_t cur = 0;                   // which u / Lambda buffer holds the current iterate
     bool initialised = false;
     // ---- graphs
@@ -113,6 +136,7 @@ int launch_permute_gamma(const ptycho_plan_s *p, const float2 *src, float2 *dst,
                          cudaStream_t s);
 bool supported_m(int m);
 int frames_per_block(int m);
+int frame_update_grid(int m, int J, int *grid);
 int prepare_kernels(int m);
 
 // gather_kernels.cu

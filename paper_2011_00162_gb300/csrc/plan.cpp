@@ -112,7 +112,8 @@ Layout decompose(int H, int W, int m, const std::vector<int32_t> &offs, int sub_
 // windows meet the tile, ascending in j.
 struct HostTiles {
     std::vector<Tile> tiles;
-    std::vector<int32_t> ptr, list, reg_ptr;
+    std::vector<int32_t> ptr, reg_ptr;
+    std::vector<ListEntry> list;
 };
 
 HostTiles make_tiles(int n_reg, const std::vector<int32_t> &reg_rect,
@@ -120,7 +121,7 @@ HostTiles make_tiles(int n_reg, const std::vector<int32_t> &reg_rect,
                      const std::vector<int32_t> &offs, int m)
 {
     HostTiles T;
-    std::vector<std::vector<int32_t>> lists;
+    std::vector<std::vector<ListEntry>> lists;
     for (int g = 0; g < n_reg; ++g) {
         T.reg_ptr.push_back((int32_t)T.tiles.size());
         const int r0 = reg_rect[4 * g], c0 = reg_rect[4 * g + 1];
@@ -135,7 +136,9 @@ HostTiles make_tiles(int n_reg, const std::vector<int32_t> &reg_rect,
             const int ty0 = std::max(0, lr / TILE_H), ty1 = std::min(nty - 1, (lr + m - 1) / TILE_H);
             const int tx0 = std::max(0, lc / TILE_W), tx1 = std::min(ntx - 1, (lc + m - 1) / TILE_W);
             for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) lists[base + (size_t)ty * ntx + tx].push_back(j);
+                for (int tx = tx0; tx <= tx1; ++tx)
+                    lists[base + (size_t)ty * ntx + tx].push_back(
+                        ListEntry{j, ty * TILE_H - lr, tx * TILE_W - lc, 0});
         }
     }
     T.reg_ptr.push_back((int32_t)T.tiles.size());
@@ -302,7 +305,9 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
                                                 (p->pair_rect[4 * k + 3] - p->pair_rect[4 * k + 1]);
     p->u_len = p->u_off[p->D];
     p->lam_len = p->lam_off[p->P];
-    if (p->u_len >= (1LL << 31)) return bail(fail(PTYCHO_ERR_UNSUPPORTED, "subdomain storage exceeds 2^31 pixels"));
+    // kernels index u, Lambda and the frame stacks with 32-bit integers
+    if (p->u_len >= (1LL << 31) || p->lam_len >= (1LL << 31) || (int64_t)J * p->MM >= (1LL << 31))
+        return bail(fail(PTYCHO_ERR_UNSUPPORTED, "subdomain, overlap or frame storage exceeds 2^31 elements"));
 
     std::vector<int32_t> frame_base(J), frame_pitch(J), img_base(J);
     std::vector<std::vector<int32_t>> sub_frames(p->D), all_frames(1);
@@ -329,7 +334,29 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
             nbr_ptr[d + 1] = (int32_t)(nbr.size() / 3);
         }
     }
+    std::vector<NbrInfo> nbr_info(nbr.size() / 3);
+    for (int d = 0; d < p->D; ++d)
+        for (int i = nbr_ptr[d]; i < nbr_ptr[d + 1]; ++i) {
+            const int e = nbr[3 * i], kde = nbr[3 * i + 1], ked = nbr[3 * i + 2];
+            const int32_t *Re = &p->rect[4 * e], *Pr = &p->pair_rect[4 * kde];
+            nbr_info[i] = NbrInfo{Re[0], Re[1], Re[2], Re[3], (int32_t)p->u_off[e], Re[3] - Re[1],
+                                  Pr[0], Pr[1], Pr[3] - Pr[1], (int32_t)p->lam_off[kde],
+                                  (int32_t)p->lam_off[ked], d < e ? 1 : 0};
+        }
     HostTiles st = make_tiles(p->D, p->rect, sub_frames, p->offs, m);
+    // neighbours of each subdomain tile whose rectangle meets the tile
+    std::vector<int32_t> tile_nbr_ptr(1, 0);
+    std::vector<NbrInfo> tile_nbr;
+    for (const Tile &t : st.tiles) {
+        const int32_t *R = &p->rect[4 * t.reg];
+        const int r0 = R[0] + t.r0, c0 = R[1] + t.c0;
+        const int r1 = std::min(r0 + TILE_H, R[2]), c1 = std::min(c0 + TILE_W, R[3]);
+        for (int i = nbr_ptr[t.reg]; i < nbr_ptr[t.reg + 1]; ++i) {
+            const NbrInfo &nb = nbr_info[i];
+            if (nb.r0 < r1 && r0 < nb.r1 && nb.c0 < c1 && c0 < nb.c1) tile_nbr.push_back(nb);
+        }
+        tile_nbr_ptr.push_back((int32_t)tile_nbr.size());
+    }
     std::vector<int32_t> img_rect = {0, 0, p->H, p->W};
     HostTiles it = make_tiles(1, img_rect, all_frames, p->offs, m);
 
@@ -341,8 +368,11 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = upload(&p->d_frame_pitch, frame_pitch, own, s)) || (rc = upload(&p->d_img_base, img_base, own, s)) ||
         (rc = upload(&p->d_rect, p->rect, own, s)) || (rc = upload(&p->d_nbr_ptr, nbr_ptr, own, s)) ||
         (rc = upload(&p->d_nbr, nbr, own, s)) || (rc = upload(&p->d_pair_rect, p->pair_rect, own, s)) ||
+        (rc = upload(&p->d_nbr_info, nbr_info, own, s)) ||
         (rc = upload(&p->d_u_off, p->u_off, own, s)) || (rc = upload(&p->d_lam_off, p->lam_off, own, s)) ||
         (rc = upload_tiles(p->sub_tiles, st, own, s)) || (rc = upload_tiles(p->img_tiles, it, own, s)) ||
+        (rc = upload(&p->sub_tiles.nbr_ptr, tile_nbr_ptr, own, s)) ||
+        (rc = upload(&p->sub_tiles.nbr, tile_nbr, own, s)) ||
         (rc = upload_groups(p->sub_groups, sub_frames, own, s)) ||
         (rc = upload_groups(p->img_groups, all_frames, own, s)))
         return bail(rc);
@@ -359,7 +389,8 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         p->has_mask = true;
         if ((rc = upload(&p->d_mask, mask, own, s))) return bail(rc);
     }
-    p->n_k1_blocks = (J + frames_per_block(m) - 1) / frames_per_block(m);
+    if ((rc = prepare_kernels(m)) || (rc = frame_update_grid(m, J, &p->n_k1_blocks))) return bail(rc);
+    p->n_loss_blocks = (J + frames_per_block(m) - 1) / frames_per_block(m);
     const int n_chunks = std::max(p->sub_groups.n_chunks, p->img_groups.n_chunks);
     if ((rc = dev_alloc(&p->d_sqrtf, JMM, own)) || (rc = dev_alloc(&p->d_gamma, JMM, own)) ||
         (rc = dev_alloc(&p->d_q, JMM, own)) || (rc = dev_alloc(&p->d_u[0], p->u_len, own)) ||
@@ -370,19 +401,19 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = dev_alloc(&p->d_probe_part_n, (size_t)n_chunks * p->MM, own)) ||
         (rc = dev_alloc(&p->d_rf_part, p->n_k1_blocks, own)) ||
         (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own)) ||
-        (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_k1_blocks), own)) ||
-        (rc = dev_alloc(&p->d_metrics, 3, own)))
+        (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own)) ||
+        (rc = dev_alloc(&p->d_metrics, 3, own)) || (rc = dev_alloc(&p->d_err, 1, own)))
         return bail(rc);
     if (p->blind) {
         if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own)))
             return bail(rc);
     }
-    if ((rc = prepare_kernels(m))) return bail(rc);
     cudaError_t e;
     if ((e = cudaMemsetAsync(p->d_metrics, 0, 3 * sizeof(double), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * p->n_k1_blocks, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_re_part, 0, sizeof(float) * 2 * p->sub_tiles.n_tiles, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->d_w, 0, sizeof(float2) * p->MM, s)) != cudaSuccess)
+        (e = cudaMemsetAsync(p->d_w, 0, sizeof(float2) * p->MM, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), s)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMemsetAsync"));
     if ((rc = launch_ingest_f(p, f_dev, s)) || (rc = launch_sum_sqrtf(p, s))) return bail(rc);
     // Step 0 with u = 1 and a zero probe until od2p_init
@@ -520,8 +551,11 @@ int od2p_metrics(ptycho_plan_t *plan, float *rf, float *re, ptycho_stream_t stre
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (int rc = launch_metrics(plan, s)) return rc;
     double h[2];
+    int32_t err = 0;
     OD2P_CUDA(cudaMemcpyAsync(h, plan->d_metrics, sizeof(h), cudaMemcpyDeviceToHost, s));
+    OD2P_CUDA(cudaMemcpyAsync(&err, plan->d_err, sizeof(err), cudaMemcpyDeviceToHost, s));
     OD2P_CUDA(cudaStreamSynchronize(s));
+    if (err) return fail(PTYCHO_ERR_TIMEOUT, "a frame-update pipeline wait gave up (device error flag set)");
     if (rf) *rf = (float)h[0];
     if (re) *re = (float)h[1];
     return PTYCHO_OK;

@@ -22,9 +22,10 @@
  *  - Every call returns PTYCHO_OK (0) or an error code; ptycho_last_error()
  *    returns a message for the calling thread.  No C++ exception crosses the
  *    ABI and no call aborts the process.
- *  - Supported probe sides m: 16, 32, 64, 128 (powers of two; the frame is
- *    transformed in one thread block's shared memory).  Other m return
- *    PTYCHO_ERR_UNSUPPORTED.
+ *  - Supported probe sides m: 16, 32, 64, 128, 256.  Up to 128 a frame is
+ *    transformed in one thread block's shared memory; 256 x 256 frames go
+ *    through row / column / row passes over a plan-owned intermediate, in
+ *    waves small enough to stay in L2.  Other m return PTYCHO_ERR_UNSUPPORTED.
  */
 #ifndef OD2P_H
 #define OD2P_H
@@ -45,7 +46,7 @@ typedef struct {
 enum {
     PTYCHO_OK = 0,
     PTYCHO_ERR_INVALID_ARG = 1, /* a size, pointer, offset or parameter is out of range   */
-    PTYCHO_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. m not in {16..128})    */
+    PTYCHO_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. m not in {16..256})    */
     PTYCHO_ERR_OOM = 3,         /* device or host allocation failed                       */
     PTYCHO_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has the CUDA text) */
     PTYCHO_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                     */
@@ -60,7 +61,8 @@ enum {
     PTYCHO_STATE_WD = 3,     /* W_d: D x m x m per-subdomain probe copies (blind)          */
     PTYCHO_STATE_DELTA = 4,  /* Delta_d: D x m x m multipliers of W_d = w (blind)          */
     PTYCHO_STATE_W = 5,      /* w: m x m shared probe                                      */
-    PTYCHO_STATE_Q = 6       /* last frame-space residual q_j (J x m x m, spatial), read-only */
+    PTYCHO_STATE_Q = 6       /* last frame residual q_j = F^*(z_j - Gamma_j), times conj(w) in nonblind
+                                plans (J x m x m, spatial), read-only */
 };
 
 /* overlap_add flags */
@@ -82,7 +84,7 @@ enum {
  */
 typedef struct {
     int32_t img_h, img_w;           /* image size in pixels                                 */
-    int32_t m;                      /* probe side: 16, 32, 64 or 128                       */
+    int32_t m;                      /* probe side: 16, 32, 64, 128 or 256                  */
     int32_t n_frames;               /* J >= 1                                              */
     const int32_t *offsets_host;    /* J x 2 (row, col), 0 <= row <= img_h-m, col likewise  */
     int32_t sub_rows, sub_cols;     /* subdomain grid, >= 1                                */

@@ -17,8 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libod2p.so")
-SOURCES = ["fft_kernels.cu", "gather_kernels.cu", "plan.cpp"]
-HEADERS = [os.path.join(CSRC, "od2p_internal.h"), os.path.join(ROOT, "include", "od2p.h")]
+SOURCES = ["fft_kernels.cu", "fft256_kernels.cu", "gather_kernels.cu", "plan.cpp"]
+HEADERS = [os.path.join(CSRC, "od2p_internal.h"), os.path.join(CSRC, "fft_device.cuh"),
+           os.path.join(ROOT, "include", "od2p.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,125 @@
+// Device helpers shared by the frame-space kernels (complex arithmetic, the
+// in-register DFTs, the ST-AGM prox and fixed-order block sums).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace od2p {
+namespace {
+
+// Complex add / subtract as one packed FP32x2 instruction each (sm_100+):
+// per component exactly a + b and a - b (b * -1 is exact, one rounding).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+__host__ __device__ constexpr int brev(int i, int bits)
+{
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
+
+// v * exp(-+2 pi i n / 16) for n in [0, 8) (forward: minus).  cos(pi/8), sin(pi/8)
+// and sqrt(1/2) are the exact values rounded to float.
+template <bool INV>
+__device__ __forceinline__ float2 tw16(float2 v, int n)
+{
+    constexpr float C1 = 0.92387953251128674f, S1 = 0.38268343236508977f, H = 0.70710678118654752f;
+    const float sg = INV ? 1.f : -1.f;
+    switch (n) {
+    case 0: return v;
+    case 1: return cmul(v, make_float2(C1, sg * S1));
+    case 2: return cscale(make_float2(v.x - sg * v.y, v.y + sg * v.x), H);
+    case 3: return cmul(v, make_float2(S1, sg * C1));
+    case 4: return make_float2(-sg * v.y, sg * v.x);
+    case 5: return cmul(v, make_float2(-S1, sg * C1));
+    case 6: return cscale(make_float2(-v.x - sg * v.y, -v.y + sg * v.x), H);
+    default: return cmul(v, make_float2(-C1, sg * S1));
+    }
+}
+
+// In-register R-point DFT (R <= 16), natural order in and out, unnormalised.
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 (&x)[R])
+{
+#pragma unroll
+    for (int span = R / 2; span >= 1; span >>= 1) {
+#pragma unroll
+        for (int blk = 0; blk < R; blk += 2 * span) {
+#pragma unroll
+            for (int k = 0; k < span; ++k) {
+                const float2 a = x[blk + k], b = x[blk + k + span];
+                x[blk + k] = cadd(a, b);
+                x[blk + k + span] = tw16<INV>(csub(a, b), k * (16 / (2 * span)));
+            }
+        }
+    }
+    float2 y[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) y[i] = x[brev(i, ilog2(R))];
+#pragma unroll
+    for (int i = 0; i < R; ++i) x[i] = y[i];
+}
+
+__device__ __forceinline__ float block_sum_fixed(float v, float *red)
+{
+    // fixed-order reduction: xor butterflies inside each warp, then warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    return t;
+}
+
+struct ProxConst {
+    float lam, inv1plam, c_thr, c_k1;
+};
+
+// eq. (Prox_sol) with the threshold read as |y| < (eps - (1-eps)/lam) sqrt f.
+// z = y * rho / |y| with 1/|y| from the hardware reciprocal square root
+// (relative error ~1e-7, far inside the FP32 parity budget); y = 0 gives (rho, 0).
+__device__ __forceinline__ float2 stagm_prox(float2 y, float sf, const ProxConst &k)
+{
+    const float y2 = y.x * y.x + y.y * y.y;
+    const float inv = rsqrtf(y2);  // +inf at y = 0, used only when y2 > 0
+    const float ay = y2 > 0.f ? y2 * inv : 0.f;
+    float rho;
+    if (ay < k.c_thr * sf)
+        rho = fmaxf(0.f, k.c_k1 * ay);
+    else
+        rho = (sf + k.lam * ay) * k.inv1plam;
+    if (y2 > 0.f) {
+        const float sc = rho * inv;
+        return make_float2(y.x * sc, y.y * sc);
+    }
+    return make_float2(rho, 0.f);
+}
+
+inline ProxConst make_prox_const(float eps, float lam)
+{
+    ProxConst k;
+    k.lam = lam;
+    k.inv1plam = 1.f / (1.f + lam);
+    k.c_thr = eps - (1.f - eps) / lam;
+    k.c_k1 = k.c_thr > 0.f ? lam / (lam - (1.f - eps) / eps) : 0.f;
+    return k;
+}
+
+}  // namespace
+}  // namespace od2p

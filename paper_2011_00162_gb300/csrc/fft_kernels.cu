@@ -21,6 +21,7 @@
 // prox's loads and stores coalesced.  Each R-point DFT runs in registers as a
 // radix-2 network with exact twiddle constants.
 #include "od2p_internal.h"
+#include "fft_device.cuh"
 
 #include <cmath>
 #include <mutex>
@@ -28,71 +29,6 @@
 
 namespace od2p {
 namespace {
-
-// Complex add / subtract as one packed FP32x2 instruction each (sm_100+):
-// per component exactly a + b and a - b (b * -1 is exact, one rounding).
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b)
-{
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// a * conj(b)
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
-{
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-
-__host__ __device__ constexpr int brev(int i, int bits)
-{
-    int r = 0;
-    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
-    return r;
-}
-__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
-
-// v * exp(-+2 pi i n / 16) for n in [0, 8) (forward: minus).  cos(pi/8), sin(pi/8)
-// and sqrt(1/2) are the exact values rounded to float.
-template <bool INV>
-__device__ __forceinline__ float2 tw16(float2 v, int n)
-{
-    constexpr float C1 = 0.92387953251128674f, S1 = 0.38268343236508977f, H = 0.70710678118654752f;
-    const float sg = INV ? 1.f : -1.f;
-    switch (n) {
-    case 0: return v;
-    case 1: return cmul(v, make_float2(C1, sg * S1));
-    case 2: return cscale(make_float2(v.x - sg * v.y, v.y + sg * v.x), H);
-    case 3: return cmul(v, make_float2(S1, sg * C1));
-    case 4: return make_float2(-sg * v.y, sg * v.x);
-    case 5: return cmul(v, make_float2(-S1, sg * C1));
-    case 6: return cscale(make_float2(-v.x - sg * v.y, -v.y + sg * v.x), H);
-    default: return cmul(v, make_float2(-C1, sg * S1));
-    }
-}
-
-// In-register R-point DFT (R <= 16), natural order in and out, unnormalised.
-template <int R, bool INV>
-__device__ __forceinline__ void dft(float2 (&x)[R])
-{
-#pragma unroll
-    for (int span = R / 2; span >= 1; span >>= 1) {
-#pragma unroll
-        for (int blk = 0; blk < R; blk += 2 * span) {
-#pragma unroll
-            for (int k = 0; k < span; ++k) {
-                const float2 a = x[blk + k], b = x[blk + k + span];
-                x[blk + k] = cadd(a, b);
-                x[blk + k + span] = tw16<INV>(csub(a, b), k * (16 / (2 * span)));
-            }
-        }
-    }
-    float2 y[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) y[i] = x[brev(i, ilog2(R))];
-#pragma unroll
-    for (int i = 0; i < R; ++i) x[i] = y[i];
-}
 
 template <int M> struct Radix;
 // R1 x R2 split, frames per block, threads per block, and the resident blocks
@@ -271,53 +207,34 @@ __device__ __forceinline__ void col_stage1_store(float2 *buf, const float2 *tw, 
     }
 }
 
-__device__ __forceinline__ float block_sum_fixed(float v, float *red)
+// Column stage 1^H writing conj(w) o (natural-order frame) into the gather
+// slots: frame j's pixel (row, c) goes to slot[rank * stride + base_j + row *
+// pitch_j + c].
+template <int M, int FPB, int NT>
+__device__ __forceinline__ void col_stage1_store_slots(float2 *buf, const float2 *tw, int j0, int J,
+                                                       float2 *slot, const uint8_t *rank, int stride,
+                                                       const int32_t *frame_base, const int32_t *frame_pitch,
+                                                       float scale, const float2 *w)
 {
-    // fixed-order reduction: xor butterflies inside each warp, then warps in order
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, P = M + 1, MM = M * M;
+    for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
+        const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
+        if (j >= J) continue;
+        float2 *fb = buf + f * M * P;
+        float2 x[R1];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    float t = 0.f;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    return t;
-}
-
-struct ProxConst {
-    float lam, inv1plam, c_thr, c_k1;
-};
-
-// eq. (Prox_sol) with the threshold read as |y| < (eps - (1-eps)/lam) sqrt f.
-// z = y * rho / |y| with 1/|y| from the hardware reciprocal square root
-// (relative error ~1e-7, far inside the FP32 parity budget); y = 0 gives (rho, 0).
-__device__ __forceinline__ float2 stagm_prox(float2 y, float sf, const ProxConst &k)
-{
-    const float y2 = y.x * y.x + y.y * y.y;
-    const float inv = rsqrtf(y2);  // +inf at y = 0, used only when y2 > 0
-    const float ay = y2 > 0.f ? y2 * inv : 0.f;
-    float rho;
-    if (ay < k.c_thr * sf)
-        rho = fmaxf(0.f, k.c_k1 * ay);
-    else
-        rho = (sf + k.lam * ay) * k.inv1plam;
-    if (y2 > 0.f) {
-        const float sc = rho * inv;
-        return make_float2(y.x * sc, y.y * sc);
+        for (int s = 0; s < R1; ++s) x[s] = cmulc(fb[(n1 + R2 * s) * P + c], tw[n1 * s]);
+        dft<R1, true>(x);
+        const unsigned base = (unsigned)(frame_base[j] + c), pitch = (unsigned)frame_pitch[j];
+        const uint8_t *rk = rank + j * MM + c;
+#pragma unroll
+        for (int t = 0; t < R1; ++t) {
+            const int row = n1 + R2 * t;
+            const float2 v = cmulc(cscale(x[t], scale), __ldg(w + row * M + c));
+            // 32-bit index: the plan checks slot_k * u_len < 2^32
+            slot[(unsigned)__ldg(rk + row * M) * (unsigned)stride + base + (unsigned)row * pitch] = v;
+        }
     }
-    return make_float2(rho, 0.f);
-}
-
-ProxConst make_prox_const(float eps, float lam)
-{
-    ProxConst k;
-    k.lam = lam;
-    k.inv1plam = 1.f / (1.f + lam);
-    k.c_thr = eps - (1.f - eps) / lam;
-    k.c_k1 = k.c_thr > 0.f ? lam / (lam - (1.f - eps) / eps) : 0.f;
-    return k;
 }
 
 // ---------------------------------------------------------------- K1: fused frame update
@@ -327,7 +244,10 @@ struct FrameArgs {
     const float2 *u, *w, *Wd; // Wd non-null for blind plans (per-subdomain probe)
     float2 *gamma;            // transposed position layout
     const float *sqrtf_;      // transposed position layout
-    float2 *q;                // out: F^*(z - Gamma^{n+1}), natural spatial order
+    float2 *q;                // out (blind): F^*(z - Gamma^{n+1}), natural spatial order
+    float2 *slot;             // out (nonblind): conj(w) o F^*(z - Gamma^{n+1}) in gather slots
+    const uint8_t *rank;      // nonblind: slot rank of each frame pixel
+    int32_t slot_stride;      // u_len
     float *rf_part;           // out: one per block
     int32_t *err;             // set to 1 if a pipeline wait gives up
     const float2 *tw;
@@ -510,7 +430,15 @@ __global__ void __launch_bounds__(K1Cfg<M>::NT, K1Cfg<M>::MINB) frame_update_ker
         __syncthreads();
         col_stage2<M, true, FPB, NT>(buf);
         __syncthreads();
-        col_stage1_store<M, FPB, NT>(buf, tw, j0, a.J, a.q, inv_m, nullptr);
+        if (a.slot) {
+            // nonblind: q_j = conj(w) o F^*(z - Gamma) (the A_d^* summand), stored in
+            // the gather slot of each pixel
+            col_stage1_store_slots<M, FPB, NT>(buf, tw, j0, a.J, a.slot, a.rank, a.slot_stride, a.frame_base,
+                                               a.frame_pitch, inv_m, a.w);
+        } else {
+            // blind: unweighted; the subdomain update weights with W_d^{n+1}
+            col_stage1_store<M, FPB, NT>(buf, tw, j0, a.J, a.q, inv_m, nullptr);
+        }
         __syncthreads();
     }
     const float tot = block_sum_fixed(rf, red);
@@ -813,6 +741,9 @@ int frame_update_m(ptycho_plan_s *p, cudaStream_t s)
     a.gamma = p->d_gamma;
     a.sqrtf_ = p->d_sqrtf;
     a.q = p->d_q;
+    a.slot = p->blind ? nullptr : p->d_slot;
+    a.rank = p->d_rank;
+    a.slot_stride = (int32_t)p->u_len;
     a.rf_part = p->d_rf_part;
     a.err = p->d_err;
     a.tw = p->d_tw;
@@ -894,7 +825,7 @@ int permute_m(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_na
 
 }  // namespace
 
-bool supported_m(int m) { return m == 16 || m == 32 || m == 64 || m == 128; }
+bool supported_m(int m) { return m == 16 || m == 32 || m == 64 || m == 128 || m == 256; }
 
 int frames_per_block(int m)
 {
@@ -902,7 +833,8 @@ int frames_per_block(int m)
     case 16: return Radix<16>::FPB;
     case 32: return Radix<32>::FPB;
     case 64: return Radix<64>::FPB;
-    default: return Radix<128>::FPB;
+    case 128: return Radix<128>::FPB;
+    default: return 1;
     }
 }
 
@@ -914,7 +846,8 @@ int frame_update_grid(int m, int J, int *grid)
     case 32: return k1_grid_m<32>(J, grid);
     case 64: return k1_grid_m<64>(J, grid);
     case 128: return k1_grid_m<128>(J, grid);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    case 256: *grid = J * 16; return PTYCHO_OK;  // one partial per 16-column slab of each frame
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }
 
@@ -940,7 +873,8 @@ int prepare_kernels(int m)
     case 32: return prepare_m<32>();
     case 64: return prepare_m<64>();
     case 128: return prepare_m<128>();
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    case 256: return PTYCHO_OK;  // its kernels stay within the default shared-memory limit
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }
 
@@ -951,7 +885,8 @@ int launch_frame_update(ptycho_plan_s *p, cudaStream_t s)
     case 32: return frame_update_m<32>(p, s);
     case 64: return frame_update_m<64>(p, s);
     case 128: return frame_update_m<128>(p, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    case 256: return frame_update_256(p, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }
 
@@ -962,7 +897,8 @@ int launch_forward(const ptycho_plan_s *p, const float2 *u, const float2 *w, flo
     case 32: return forward_m<32>(p, u, w, out, s);
     case 64: return forward_m<64>(p, u, w, out, s);
     case 128: return forward_m<128>(p, u, w, out, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    case 256: return forward_256(p, u, w, out, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }
 
@@ -975,7 +911,10 @@ int launch_frames_ifft_weight(const ptycho_plan_s *p, const float2 *frames, cons
     case 32: return ifft_m<32>(p, frames, w, out, s);
     case 64: return ifft_m<64>(p, frames, w, out, s);
     case 128: return ifft_m<128>(p, frames, w, out, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    case 256:
+        if (w) return fail(PTYCHO_ERR_STATE, "internal: m = 256 inverse FFT takes no weight");
+        return ifft_256(p, frames, out, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }
 
@@ -986,7 +925,8 @@ int launch_loss_frames(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaS
     case 32: return loss_m<32>(p, u, w, s);
     case 64: return loss_m<64>(p, u, w, s);
     case 128: return loss_m<128>(p, u, w, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    case 256: return loss_256(p, u, w, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }
 
@@ -997,7 +937,8 @@ int launch_probe_avg(ptycho_plan_s *p, cudaStream_t s)
     case 32: return probe_avg_m<32>(p, s);
     case 64: return probe_avg_m<64>(p, s);
     case 128: return probe_avg_m<128>(p, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    case 256: return probe_avg_256(p, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }
 
@@ -1009,7 +950,8 @@ int launch_ingest_f(ptycho_plan_s *p, const float *f, cudaStream_t s)
     case 32: return ingest_m<32>(p, f, part, s);
     case 64: return ingest_m<64>(p, f, part, s);
     case 128: return ingest_m<128>(p, f, part, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    case 256: return ingest_256(p, f, part, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }
 
@@ -1021,7 +963,8 @@ int launch_permute_gamma(const ptycho_plan_s *p, const float2 *src, float2 *dst,
     case 32: return permute_m<32>(p, src, dst, to_natural, s);
     case 64: return permute_m<64>(p, src, dst, to_natural, s);
     case 128: return permute_m<128>(p, src, dst, to_natural, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    case 256: return permute_256(p, src, dst, to_natural, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }
 
@@ -1161,7 +1104,8 @@ extern "C" int stagm_loss_noalloc(const ptycho_c32 *u, int32_t img_h, int32_t im
 {
     using namespace od2p;
     if (!u || !w || !offsets_dev || !f || !loss) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
-    if (!supported_m(m)) return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    if (!(m == 16 || m == 32 || m == 64 || m == 128))
+        return fail(PTYCHO_ERR_UNSUPPORTED, "stagm_loss_noalloc: probe side m must be 16, 32, 64 or 128");
     if (n_frames < 1 || img_h < m || img_w < m) return fail(PTYCHO_ERR_INVALID_ARG, "need n_frames >= 1 and an image at least m x m");
     if (!(eps > 0.f && eps < 1.f)) return fail(PTYCHO_ERR_INVALID_ARG, "eps must be in (0, 1)");
     // per-device set-up: the device address of the file-scope scratch array

@@ -56,20 +56,27 @@ struct SubArgs {
     const ListEntry *tlist;
     const NbrInfo *tnbr;
     const float2 *u_cur, *lam_cur, *q, *w, *Wd;
+    const float *nrm;
+    const float2 *slot;        // nonblind gather slots
+    const uint8_t *cnt;
+    int32_t slot_stride;
     float2 *u_next, *lam_next;
     float eta, r, gamma;
     int32_t blind;
     float *re_part;
 };
 
-// One block per TILE_H x TILE_W tile, one thread per pixel (warp = tile row).
-// The tile's frame list (ascending j) is staged in shared memory; an entry's
-// row test is warp-uniform, its column test per lane.  Only the neighbours
-// whose rectangles meet the tile are visited (interior tiles have none).
-constexpr int LIST_SMEM = 96;
+// One block per TILE_H x TILE_W tile; lane = column, warp w owns rows
+// [w * TILE_ROWS, (w + 1) * TILE_ROWS) of it.  The tile's frame list (ascending
+// j) is staged in shared memory; per entry the row test is warp-uniform, the
+// column test per lane, and the entry's TILE_ROWS loads are independent.
+// Each pixel adds its frames in list order.  Only the neighbours whose
+// rectangles meet the tile are visited (interior tiles have none).
+constexpr int LIST_SMEM = 160;
 constexpr int NBR_SMEM = 16;
 
-__global__ void __launch_bounds__(GATHER_THREADS) subdomain_update_kernel(SubArgs a)
+template <bool BLIND>
+__global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4) subdomain_update_kernel(SubArgs a)
 {
     __shared__ float red[2 * (GATHER_THREADS / 32)];
     __shared__ ListEntry lst[LIST_SMEM];
@@ -78,74 +85,171 @@ __global__ void __launch_bounds__(GATHER_THREADS) subdomain_update_kernel(SubArg
     const int d = tile.reg;
     const int32_t *rc = a.rect + 4 * d;
     const int hd = rc[2] - rc[0], wd = rc[3] - rc[1];
-    const int ty = threadIdx.x / TILE_W, tx = threadIdx.x % TILE_W;
-    const int lr = tile.r0 + ty, lc = tile.c0 + tx;
-    const bool row_ok = lr < hd;
-    const bool active = row_ok && lc < wd;
-    const int R = rc[0] + lr, C = rc[1] + lc;
+    const int lane = threadIdx.x & 31, ty0 = (threadIdx.x >> 5) * TILE_ROWS;
+    const int lc = tile.c0 + lane;
+    const bool col_ok = lc < wd;
+    const int nrows = min(TILE_ROWS, hd - tile.r0 - ty0);  // rows of this thread inside Omega_d (may be <= 0)
+    const int C = rc[1] + lc;
     const int M = a.M, MM = M * M;
     const int k0 = a.tptr[blockIdx.x], nk = a.tptr[blockIdx.x + 1] - k0;
     const int n0 = a.tnbr_ptr[blockIdx.x], nnb = a.tnbr_ptr[blockIdx.x + 1] - n0;
     for (int i = threadIdx.x; i < min(nk, LIST_SMEM); i += GATHER_THREADS) lst[i] = a.tlist[k0 + i];
     for (int i = threadIdx.x; i < min(nnb, NBR_SMEM); i += GATHER_THREADS) nbs[i] = a.tnbr[n0 + i];
     __syncthreads();
-    float dn = 0.f, nn = 0.f;
-    if (row_ok) {
-        // A_d^*(z - Gamma) and sum_j S_j^T |w|^2 at this pixel, frames in ascending j
-        const float2 *w = a.blind ? a.Wd + d * MM : a.w;
-        float2 acc = make_float2(0.f, 0.f);
-        float nrm = 0.f;
-        for (int k = 0; k < nk; ++k) {
-            const ListEntry e = k < LIST_SMEM ? lst[k] : a.tlist[k0 + k];
-            const int dr = e.dr + ty;
-            if ((unsigned)dr >= (unsigned)M) continue;  // same for the whole warp
-            const int dc = e.dc + tx;
-            if (active && (unsigned)dc < (unsigned)M) {
-                const int o = dr * M + dc;
-                const float2 wv = __ldg(w + o);
-                const float2 qv = __ldg(a.q + e.j * MM + o);
-                acc = cadd(acc, cconjmul(wv, qv));
-                nrm += cabs2(wv);
+    // A_d^*(z - Gamma) at each pixel, frames in ascending j.  Nonblind: q_j
+    // already carries conj(w) and sum_j S_j^T |w|^2 is precomputed.  Blind:
+    // weight with W_d^{n+1} here and sum |W_d|^2 on the way.
+    float2 acc[TILE_ROWS];
+    float nrm[TILE_ROWS];
+#pragma unroll
+    for (int r = 0; r < TILE_ROWS; ++r) {
+        acc[r] = make_float2(0.f, 0.f);
+        nrm[r] = 0.f;
+    }
+    const float2 *w = BLIND ? a.Wd + d * MM : nullptr;
+    if (!BLIND) {
+        // nonblind: the pixel's frames sit in slots 0 .. cnt-1 in ascending j;
+        // U slots x TILE_ROWS rows of coalesced, independent loads per step
+        // (U = 2 keeps the kernel within 64 registers: 4 blocks per SM)
+        if (nrows > 0 && col_ok) {
+            int ui[TILE_ROWS], nk_r[TILE_ROWS];
+            int kmax = 0;
+#pragma unroll
+            for (int r = 0; r < TILE_ROWS; ++r) {
+                ui[r] = (int)a.u_off[d] + (tile.r0 + ty0 + min(r, nrows - 1)) * wd + lc;
+                nk_r[r] = r < nrows ? (int)__ldg(a.cnt + ui[r]) : 0;
+                kmax = max(kmax, nk_r[r]);
+            }
+            constexpr int U = 2;
+            for (int k = 0; k < kmax; k += U) {
+                float2 v[U][TILE_ROWS];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int r = 0; r < TILE_ROWS; ++r) {
+                        const int kk = k + u < nk_r[r] ? k + u : 0;
+                        v[u][r] = __ldg(a.slot + (size_t)kk * a.slot_stride + ui[r]);
+                    }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int r = 0; r < TILE_ROWS; ++r)
+                        if (k + u < nk_r[r]) acc[r] = cadd(acc[r], v[u][r]);
             }
         }
-        if (active) {
-            const int ui = (int)a.u_off[d] + lr * wd + lc;
-            const float2 u_old = a.u_cur[ui];
-            float2 num = cscale(acc, a.eta);
-            float den = a.eta * nrm;
-            // consensus v_{d,e} (eq. updateV-multi) and the r-terms of the u-update
-            for (int i = 0; i < nnb; ++i) {
-                const NbrInfo nb = i < NBR_SMEM ? nbs[i] : a.tnbr[n0 + i];
-                if (R < nb.r0 || R >= nb.r1 || C < nb.c0 || C >= nb.c1) continue;
-                const float2 ue = a.u_cur[nb.u_base + (R - nb.r0) * nb.u_pitch + (C - nb.c0)];
-                const int li = (R - nb.p_r0) * nb.p_pitch + (C - nb.p_c0);
-                const float2 lde = a.lam_cur[nb.lam_de + li], led = a.lam_cur[nb.lam_ed + li];
-                // same operand order on both sides of the pair -> bitwise equal v
-                const float2 v = nb.d_first ? cscale(cadd(cadd(u_old, ue), cadd(lde, led)), 0.5f)
-                                            : cscale(cadd(cadd(ue, u_old), cadd(led, lde)), 0.5f);
-                num = cadd(num, cscale(csub(v, lde), a.r));
-                den += a.r;
+    } else if (nrows > 0 && col_ok) {
+        // blind: walk the tile's frame list and weight with W_d^{n+1};
+        // U entries x TILE_ROWS rows of loads per step, branch-free: a lane whose
+        // pixel a frame does not cover loads element 0 and discards it.
+        constexpr int U = 4;
+        for (int k = 0; k < nk; k += U) {
+            float2 qv[U][TILE_ROWS], wv[U][TILE_ROWS];
+            unsigned hits = 0u;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool valid = k + u < nk;
+                const ListEntry e = valid ? (k + u < LIST_SMEM ? lst[k + u] : a.tlist[k0 + k + u]) : ListEntry{0, M, M, 0};
+                const int dr0 = e.dr + ty0, dc = e.dc + lane;
+                const bool cok = (unsigned)dc < (unsigned)M;
+#pragma unroll
+                for (int r = 0; r < TILE_ROWS; ++r) {
+                    const int dr = dr0 + r;
+                    const bool hit = cok && r < nrows && (unsigned)dr < (unsigned)M;
+                    const int o = hit ? dr * M + dc : 0;
+                    qv[u][r] = __ldg(a.q + (hit ? e.j * MM + o : 0));
+                    if (w) wv[u][r] = __ldg(w + o);
+                    hits |= (hit ? 1u : 0u) << (u * TILE_ROWS + r);
+                }
             }
-            if (a.blind) {
-                num = cadd(num, cscale(u_old, a.gamma));
-                den += a.gamma;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int r = 0; r < TILE_ROWS; ++r)
+                    if (hits & (1u << (u * TILE_ROWS + r))) {
+                        if (w) {
+                            acc[r] = cadd(acc[r], cconjmul(wv[u][r], qv[u][r]));
+                            nrm[r] += cabs2(wv[u][r]);
+                        } else {
+                            acc[r] = cadd(acc[r], qv[u][r]);
+                        }
+                    }
+        }
+    }
+    float dn = 0.f, nn = 0.f;
+    if (col_ok && nrows > 0) {
+        float2 u_old[TILE_ROWS], num[TILE_ROWS], u_new[TILE_ROWS];
+        float den[TILE_ROWS];
+        int ui[TILE_ROWS];
+#pragma unroll
+        for (int r = 0; r < TILE_ROWS; ++r) {
+            const int lr = tile.r0 + ty0 + min(r, nrows - 1);
+            ui[r] = (int)a.u_off[d] + lr * wd + lc;
+            u_old[r] = a.u_cur[ui[r]];
+            const float nrm_r = BLIND ? nrm[r] : a.nrm[ui[r]];
+            num[r] = cscale(acc[r], a.eta);
+            den[r] = a.eta * nrm_r;
+        }
+        const int R0 = rc[0] + tile.r0 + ty0;
+        // consensus v_{d,e} (eq. updateV-multi) and the r-terms of the u-update:
+        // one neighbour at a time, the loads of all rows together
+        for (int i = 0; i < nnb; ++i) {
+            const NbrInfo nb = i < NBR_SMEM ? nbs[i] : a.tnbr[n0 + i];
+            if (C < nb.c0 || C >= nb.c1 || R0 + nrows <= nb.r0 || R0 >= nb.r1) continue;
+            float2 ue[TILE_ROWS], lde[TILE_ROWS], led[TILE_ROWS];
+#pragma unroll
+            for (int r = 0; r < TILE_ROWS; ++r) {
+                // clamped into Omega_d n Omega_e: rows outside are loaded but discarded
+                const int R = min(max(R0 + r, nb.r0), min(nb.r1, rc[2]) - 1);
+                const int li = (R - nb.p_r0) * nb.p_pitch + (C - nb.p_c0);
+                ue[r] = a.u_cur[nb.u_base + (R - nb.r0) * nb.u_pitch + (C - nb.c0)];
+                lde[r] = a.lam_cur[nb.lam_de + li];
+                led[r] = a.lam_cur[nb.lam_ed + li];
+            }
+#pragma unroll
+            for (int r = 0; r < TILE_ROWS; ++r) {
+                if (r >= nrows || R0 + r < nb.r0 || R0 + r >= nb.r1) continue;
+                // same operand order on both sides of the pair -> bitwise equal v
+                const float2 v = nb.d_first ? cscale(cadd(cadd(u_old[r], ue[r]), cadd(lde[r], led[r])), 0.5f)
+                                            : cscale(cadd(cadd(ue[r], u_old[r]), cadd(led[r], lde[r])), 0.5f);
+                num[r] = cadd(num[r], cscale(csub(v, lde[r]), a.r));
+                den[r] += a.r;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < TILE_ROWS; ++r) {
+            if (BLIND) {
+                num[r] = cadd(num[r], cscale(u_old[r], a.gamma));
+                den[r] += a.gamma;
             }
             // eq. Alg1-solver-u; a pixel with no illumination and no overlap keeps its value
-            const float2 u_new = den > 0.f ? make_float2(num.x / den, num.y / den) : u_old;
-            a.u_next[ui] = u_new;
-            // eq. updateM-2-multi: Lambda_{d,e} += pi u_d^{n+1} - v
-            for (int i = 0; i < nnb; ++i) {
-                const NbrInfo nb = i < NBR_SMEM ? nbs[i] : a.tnbr[n0 + i];
-                if (R < nb.r0 || R >= nb.r1 || C < nb.c0 || C >= nb.c1) continue;
-                const float2 ue = a.u_cur[nb.u_base + (R - nb.r0) * nb.u_pitch + (C - nb.c0)];
-                const int li = (R - nb.p_r0) * nb.p_pitch + (C - nb.p_c0);
-                const float2 lde = a.lam_cur[nb.lam_de + li], led = a.lam_cur[nb.lam_ed + li];
-                const float2 v = nb.d_first ? cscale(cadd(cadd(u_old, ue), cadd(lde, led)), 0.5f)
-                                            : cscale(cadd(cadd(ue, u_old), cadd(led, lde)), 0.5f);
-                a.lam_next[nb.lam_de + li] = csub(cadd(lde, u_new), v);
+            u_new[r] = den[r] > 0.f ? make_float2(num[r].x / den[r], num[r].y / den[r]) : u_old[r];
+            if (r < nrows) {
+                a.u_next[ui[r]] = u_new[r];
+                dn += cabs2(csub(u_new[r], u_old[r]));
+                nn += cabs2(u_new[r]);
             }
-            dn = cabs2(csub(u_new, u_old));
-            nn = cabs2(u_new);
+        }
+        // eq. updateM-2-multi: Lambda_{d,e} += pi u_d^{n+1} - v
+        for (int i = 0; i < nnb; ++i) {
+            const NbrInfo nb = i < NBR_SMEM ? nbs[i] : a.tnbr[n0 + i];
+            if (C < nb.c0 || C >= nb.c1 || R0 + nrows <= nb.r0 || R0 >= nb.r1) continue;
+            float2 ue[TILE_ROWS], lde[TILE_ROWS], led[TILE_ROWS];
+            int li[TILE_ROWS];
+#pragma unroll
+            for (int r = 0; r < TILE_ROWS; ++r) {
+                const int R = min(max(R0 + r, nb.r0), min(nb.r1, rc[2]) - 1);
+                li[r] = (R - nb.p_r0) * nb.p_pitch + (C - nb.p_c0);
+                ue[r] = a.u_cur[nb.u_base + (R - nb.r0) * nb.u_pitch + (C - nb.c0)];
+                lde[r] = a.lam_cur[nb.lam_de + li[r]];
+                led[r] = a.lam_cur[nb.lam_ed + li[r]];
+            }
+#pragma unroll
+            for (int r = 0; r < TILE_ROWS; ++r) {
+                if (r >= nrows || R0 + r < nb.r0 || R0 + r >= nb.r1) continue;
+                const float2 v = nb.d_first ? cscale(cadd(cadd(u_old[r], ue[r]), cadd(lde[r], led[r])), 0.5f)
+                                            : cscale(cadd(cadd(ue[r], u_old[r]), cadd(led[r], lde[r])), 0.5f);
+                a.lam_next[nb.lam_de + li[r]] = csub(cadd(lde[r], u_new[r]), v);
+            }
         }
     }
     block_sum2_fixed(dn, nn, red);
@@ -162,20 +266,30 @@ __global__ void __launch_bounds__(GATHER_THREADS) image_gather_kernel(
     const float2 *h, const float2 *w, float2 *out)
 {
     const Tile tile = tiles[blockIdx.x];
-    const int ty = threadIdx.x / TILE_W, tx = threadIdx.x % TILE_W;
-    const int R = tile.r0 + ty, C = tile.c0 + tx;
-    if (R >= H || C >= W) return;
+    const int lane = threadIdx.x & 31, ty0 = (threadIdx.x >> 5) * TILE_ROWS;
+    const int C = tile.c0 + lane, R0 = tile.r0 + ty0;
+    const int nrows = min(TILE_ROWS, H - R0);
+    if (C >= W || nrows <= 0) return;
     const int MM = M * M;
-    float2 acc = make_float2(0.f, 0.f);
+    float2 acc[TILE_ROWS];
+#pragma unroll
+    for (int r = 0; r < TILE_ROWS; ++r) acc[r] = make_float2(0.f, 0.f);
     for (int k = tptr[blockIdx.x]; k < tptr[blockIdx.x + 1]; ++k) {
         const ListEntry e = tlist[k];
-        const int dr = e.dr + ty, dc = e.dc + tx;
-        if ((unsigned)dr < (unsigned)M && (unsigned)dc < (unsigned)M) {
-            const float2 hv = __ldg(h + (size_t)e.j * MM + dr * M + dc);
-            acc = cadd(acc, w ? cconjmul(__ldg(w + dr * M + dc), hv) : hv);
+        const int dr0 = e.dr + ty0, dc = e.dc + lane;
+        if (dr0 + TILE_ROWS <= 0 || dr0 >= M || (unsigned)dc >= (unsigned)M) continue;
+#pragma unroll
+        for (int r = 0; r < TILE_ROWS; ++r) {
+            const int dr = dr0 + r;
+            if (r < nrows && (unsigned)dr < (unsigned)M) {
+                const float2 hv = __ldg(h + (size_t)e.j * MM + dr * M + dc);
+                acc[r] = cadd(acc[r], w ? cconjmul(__ldg(w + dr * M + dc), hv) : hv);
+            }
         }
     }
-    out[(size_t)R * W + C] = acc;
+#pragma unroll
+    for (int r = 0; r < TILE_ROWS; ++r)
+        if (r < nrows) out[(size_t)(R0 + r) * W + C] = acc[r];
 }
 
 // ---------------------------------------------------------------- probe reductions
@@ -305,6 +419,44 @@ __global__ void __launch_bounds__(256) loss_sum_kernel(int n, const float *part,
     if (threadIdx.x == 0) *loss = (float)t;
 }
 
+// sum_j S_j^T |w|^2 over each subdomain's frames (ascending j), per subdomain
+// pixel: the diagonal of A_d^* A_d (eq. AtA) for the known probe.
+__global__ void __launch_bounds__(GATHER_THREADS) illumination_kernel(int M, const int32_t *rect,
+                                                                      const int64_t *u_off, const Tile *tiles,
+                                                                      const int32_t *tptr, const ListEntry *tlist,
+                                                                      const float2 *w, float *nrm)
+{
+    const Tile tile = tiles[blockIdx.x];
+    const int32_t *rc = rect + 4 * tile.reg;
+    const int hd = rc[2] - rc[0], wd = rc[3] - rc[1];
+    const int lane = threadIdx.x & 31, ty0 = (threadIdx.x >> 5) * TILE_ROWS;
+    const int lc = tile.c0 + lane;
+    if (lc >= wd) return;
+    for (int r = 0; r < TILE_ROWS; ++r) {
+        const int lr = tile.r0 + ty0 + r;
+        if (lr >= hd) break;
+        float acc = 0.f;
+        for (int k = tptr[blockIdx.x]; k < tptr[blockIdx.x + 1]; ++k) {
+            const ListEntry e = tlist[k];
+            const int dr = e.dr + ty0 + r, dc = e.dc + lane;
+            if ((unsigned)dr < (unsigned)M && (unsigned)dc < (unsigned)M) acc += cabs2(__ldg(w + dr * M + dc));
+        }
+        nrm[u_off[tile.reg] + (int64_t)lr * wd + lc] = acc;
+    }
+}
+
+// Frames of the nonblind gather slots back in frame layout (for state export).
+__global__ void q_from_slots_kernel(int J, int M, const float2 *slot, const uint8_t *rank, int stride,
+                                    const int32_t *frame_base, const int32_t *frame_pitch, float2 *q)
+{
+    const int MM = M * M;
+    const size_t n = (size_t)J * MM;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / MM), k = (int)(e % MM);
+        q[e] = slot[(size_t)rank[e] * stride + frame_base[j] + (k / M) * frame_pitch[j] + (k % M)];
+    }
+}
+
 // u_d = R_d u0 (or 1), over the subdomain tiles
 __global__ void init_u_kernel(const Tile *tiles, const int32_t *rect, const int64_t *u_off, int W,
                               const float2 *u0, float2 *u)
@@ -313,10 +465,15 @@ __global__ void init_u_kernel(const Tile *tiles, const int32_t *rect, const int6
     const int d = tile.reg;
     const int32_t *rc = rect + 4 * d;
     const int hd = rc[2] - rc[0], wd = rc[3] - rc[1];
-    const int lr = tile.r0 + threadIdx.x / TILE_W, lc = tile.c0 + threadIdx.x % TILE_W;
-    if (lr >= hd || lc >= wd) return;
-    u[u_off[d] + (int64_t)lr * wd + lc] =
-        u0 ? u0[(size_t)(rc[0] + lr) * W + (rc[1] + lc)] : make_float2(1.f, 0.f);
+    const int lane = threadIdx.x & 31, ty0 = (threadIdx.x >> 5) * TILE_ROWS;
+    const int lc = tile.c0 + lane;
+    if (lc >= wd) return;
+    for (int r = 0; r < TILE_ROWS; ++r) {
+        const int lr = tile.r0 + ty0 + r;
+        if (lr >= hd) break;
+        u[u_off[d] + (int64_t)lr * wd + lc] =
+            u0 ? u0[(size_t)(rc[0] + lr) * W + (rc[1] + lc)] : make_float2(1.f, 0.f);
+    }
 }
 
 __global__ void broadcast_probe_kernel(int MM, int D, const float2 *w0, float2 *w, float2 *Wd)
@@ -391,12 +548,19 @@ int launch_subdomain_update(ptycho_plan_s *p, cudaStream_t s)
     a.q = p->d_q;
     a.w = p->d_w;
     a.Wd = p->d_Wd;
+    a.nrm = p->d_nrm;
+    a.slot = p->d_slot;
+    a.cnt = p->d_cnt;
+    a.slot_stride = (int32_t)p->u_len;
     a.eta = p->eta;
     a.r = p->r;
     a.gamma = p->gamma;
     a.blind = p->blind;
     a.re_part = p->d_re_part;
-    subdomain_update_kernel<<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(a);
+    if (p->blind)
+        subdomain_update_kernel<true><<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(a);
+    else
+        subdomain_update_kernel<false><<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(a);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
@@ -474,6 +638,22 @@ int launch_init_state(ptycho_plan_s *p, const float2 *u0, const float2 *w0, cuda
     OD2P_CUDA(cudaGetLastError());
     broadcast_probe_kernel<<<(p->MM + 255) / 256, 256, 0, s>>>(p->MM, p->D, w0, p->d_w,
                                                                 p->blind ? p->d_Wd : nullptr);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_illumination(ptycho_plan_s *p, cudaStream_t s)
+{
+    illumination_kernel<<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(
+        p->M, p->d_rect, p->d_u_off, p->sub_tiles.tiles, p->sub_tiles.ptr, p->sub_tiles.list, p->d_w, p->d_nrm);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_q_from_slots(const ptycho_plan_s *p, float2 *dst, cudaStream_t s)
+{
+    q_from_slots_kernel<<<152 * 8, 256, 0, s>>>(p->J, p->M, p->d_slot, p->d_rank, (int)p->u_len, p->d_frame_base,
+                                               p->d_frame_pitch, dst);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }

@@ -11,13 +11,19 @@
 
 namespace od2p {
 
-// Thread block tile of the gather kernels: TILE_H rows x TILE_W columns,
-// one thread per pixel, lanes along the row so that frame rows load coalesced.
-constexpr int TILE_H = 8;
+// Thread block tile of the gather kernels: TILE_H rows x TILE_W columns.
+// Lanes run along a row (coalesced frame rows); each thread owns TILE_ROWS
+// consecutive rows of its column, so one frame-list entry drives TILE_ROWS
+// independent loads.
+constexpr int TILE_H = 32;
 constexpr int TILE_W = 32;
-constexpr int GATHER_THREADS = TILE_H * TILE_W;
+constexpr int GATHER_THREADS = 256;
+constexpr int TILE_ROWS = TILE_H * TILE_W / GATHER_THREADS;
 // Frames per chunk of the fixed-order probe reductions (blind W, grad w).
 constexpr int PROBE_CHUNK = 32;
+// m = 256 frames go through their three FFT passes in waves of this many
+// frames (a 32 MB intermediate that stays in L2).
+constexpr int WAVE_256 = 64;
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
@@ -89,7 +95,8 @@ struct ptycho_plan_s {
     // ---- device geometry
     int32_t *d_offs = nullptr, *d_frame_sub = nullptr, *d_frame_base = nullptr,
             *d_frame_pitch = nullptr, *d_rect = nullptr, *d_nbr_ptr = nullptr, *d_nbr = nullptr,
-            *d_pair_rect = nullptr, *d_img_base = nullptr;  // nbr: (e, pair d-e, pair e-d) per neighbour
+            *d_pair_rect = nullptr, *d_img_base = nullptr,  // nbr: (e, pair d-e, pair e-d) per neighbour
+            *d_img_pitch = nullptr;                      // img_w for every frame
     od2p::NbrInfo *d_nbr_info = nullptr;  // per neighbour entry, same order as d_nbr
     int64_t *d_u_off = nullptr, *d_lam_off = nullptr;
     od2p::GatherTiles sub_tiles, img_tiles;
@@ -100,7 +107,17 @@ struct ptycho_plan_s {
     float *d_sqrtf = nullptr;      // J*MM
     float2 *d_gamma = nullptr;     // J*MM
     float2 *d_q = nullptr;         // J*MM frame residuals / scratch
+    float2 *d_T = nullptr;         // m = 256: WAVE_256 frames of FFT intermediate
+    // Nonblind gather slots: frame j's weighted residual at window pixel k goes to
+    // d_slot[rank_j(k) * u_len + (index of that pixel in the u buffer)], where
+    // rank_j(k) counts the frames of the subdomain with smaller index that cover
+    // the same pixel; d_cnt holds each subdomain pixel's number of frames.
+    uint8_t *d_rank = nullptr;     // J*MM
+    uint8_t *d_cnt = nullptr;      // u_len
+    float2 *d_slot = nullptr;      // slot_k * u_len
+    int32_t slot_k = 0;
     float2 *d_u[2] = {nullptr, nullptr};
+    float *d_nrm = nullptr;        // nonblind: sum_j S_j^T |w|^2 per subdomain pixel (eq. AtA)
     float2 *d_lam[2] = {nullptr, nullptr};
     float2 *d_w = nullptr, *d_wnew = nullptr, *d_Wd = nullptr, *d_Delta = nullptr;
     float2 *d_probe_part = nullptr;    // blind / grad-w partial sums
@@ -139,6 +156,15 @@ int frames_per_block(int m);
 int frame_update_grid(int m, int J, int *grid);
 int prepare_kernels(int m);
 
+// fft256_kernels.cu (m = 256)
+int frame_update_256(ptycho_plan_s *p, cudaStream_t s);
+int forward_256(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out, cudaStream_t s);
+int ifft_256(const ptycho_plan_s *p, const float2 *in, float2 *out, cudaStream_t s);
+int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s);
+int probe_avg_256(ptycho_plan_s *p, cudaStream_t s);
+int ingest_256(ptycho_plan_s *p, const float *f, float *part, cudaStream_t s);
+int permute_256(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_natural, cudaStream_t s);
+
 // gather_kernels.cu
 int launch_subdomain_update(ptycho_plan_s *p, cudaStream_t s);
 int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w, float2 *out,
@@ -148,6 +174,8 @@ int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s);
 int launch_metrics(ptycho_plan_s *p, cudaStream_t s);
 int launch_sum_sqrtf(ptycho_plan_s *p, cudaStream_t s);
 int launch_init_state(ptycho_plan_s *p, const float2 *u0, const float2 *w0, cudaStream_t s);
+int launch_illumination(ptycho_plan_s *p, cudaStream_t s);
+int launch_q_from_slots(const ptycho_plan_s *p, float2 *dst, cudaStream_t s);
 int launch_merge(const ptycho_plan_s *p, float2 *out, cudaStream_t s);
 int launch_prox(const float2 *y, const float *f, float2 *z, int64_t n, float eps, float lam,
                 cudaStream_t s);

@@ -245,7 +245,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
     if (!out) return fail(PTYCHO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!g || !f_dev || !g->offsets_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL geometry, f or offsets");
-    if (!supported_m(g->m)) return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64 or 128");
+    if (!supported_m(g->m)) return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     if (g->n_frames < 1 || g->img_h < g->m || g->img_w < g->m)
         return fail(PTYCHO_ERR_INVALID_ARG, "need n_frames >= 1 and an image at least m x m");
     if ((int64_t)g->img_h * g->img_w >= (1LL << 31))
@@ -309,7 +309,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
     if (p->u_len >= (1LL << 31) || p->lam_len >= (1LL << 31) || (int64_t)J * p->MM >= (1LL << 31))
         return bail(fail(PTYCHO_ERR_UNSUPPORTED, "subdomain, overlap or frame storage exceeds 2^31 elements"));
 
-    std::vector<int32_t> frame_base(J), frame_pitch(J), img_base(J);
+    std::vector<int32_t> frame_base(J), frame_pitch(J), img_base(J), img_pitch(J, p->W);
     std::vector<std::vector<int32_t>> sub_frames(p->D), all_frames(1);
     for (int j = 0; j < J; ++j) {
         const int d = p->frame_sub[j];
@@ -343,6 +343,23 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
                                   Pr[0], Pr[1], Pr[3] - Pr[1], (int32_t)p->lam_off[kde],
                                   (int32_t)p->lam_off[ked], d < e ? 1 : 0};
         }
+    // nonblind: rank of each frame pixel among the frames covering that subdomain
+    // pixel (ascending j), and the number of covering frames per pixel
+    std::vector<uint8_t> rank, cnt;
+    if (!p->blind) {
+        rank.resize((size_t)J * p->MM);
+        cnt.assign((size_t)p->u_len, 0);
+        for (int j = 0; j < J; ++j)
+            for (int r = 0; r < m; ++r)
+                for (int c = 0; c < m; ++c) {
+                    uint8_t &n = cnt[(size_t)frame_base[j] + (size_t)r * frame_pitch[j] + c];
+                    if (n == 255) return bail(fail(PTYCHO_ERR_UNSUPPORTED, "more than 255 frames cover one pixel"));
+                    rank[(size_t)j * p->MM + r * m + c] = n++;
+                }
+        p->slot_k = *std::max_element(cnt.begin(), cnt.end());
+        if ((int64_t)p->slot_k * p->u_len >= (1LL << 32))
+            return bail(fail(PTYCHO_ERR_UNSUPPORTED, "gather slot storage exceeds 2^32 elements"));
+    }
     HostTiles st = make_tiles(p->D, p->rect, sub_frames, p->offs, m);
     // neighbours of each subdomain tile whose rectangle meets the tile
     std::vector<int32_t> tile_nbr_ptr(1, 0);
@@ -366,6 +383,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
     if ((rc = upload(&p->d_offs, p->offs, own, s)) || (rc = upload(&p->d_frame_sub, p->frame_sub, own, s)) ||
         (rc = upload(&p->d_frame_base, frame_base, own, s)) ||
         (rc = upload(&p->d_frame_pitch, frame_pitch, own, s)) || (rc = upload(&p->d_img_base, img_base, own, s)) ||
+        (rc = upload(&p->d_img_pitch, img_pitch, own, s)) ||
         (rc = upload(&p->d_rect, p->rect, own, s)) || (rc = upload(&p->d_nbr_ptr, nbr_ptr, own, s)) ||
         (rc = upload(&p->d_nbr, nbr, own, s)) || (rc = upload(&p->d_pair_rect, p->pair_rect, own, s)) ||
         (rc = upload(&p->d_nbr_info, nbr_info, own, s)) ||
@@ -390,11 +408,12 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         if ((rc = upload(&p->d_mask, mask, own, s))) return bail(rc);
     }
     if ((rc = prepare_kernels(m)) || (rc = frame_update_grid(m, J, &p->n_k1_blocks))) return bail(rc);
-    p->n_loss_blocks = (J + frames_per_block(m) - 1) / frames_per_block(m);
+    p->n_loss_blocks = m == 256 ? J * 16 : (J + frames_per_block(m) - 1) / frames_per_block(m);
     const int n_chunks = std::max(p->sub_groups.n_chunks, p->img_groups.n_chunks);
     if ((rc = dev_alloc(&p->d_sqrtf, JMM, own)) || (rc = dev_alloc(&p->d_gamma, JMM, own)) ||
         (rc = dev_alloc(&p->d_q, JMM, own)) || (rc = dev_alloc(&p->d_u[0], p->u_len, own)) ||
-        (rc = dev_alloc(&p->d_u[1], p->u_len, own)) || (rc = dev_alloc(&p->d_lam[0], p->lam_len, own)) ||
+        (rc = dev_alloc(&p->d_u[1], p->u_len, own)) || (rc = dev_alloc(&p->d_nrm, p->u_len, own)) ||
+        (rc = dev_alloc(&p->d_lam[0], p->lam_len, own)) ||
         (rc = dev_alloc(&p->d_lam[1], p->lam_len, own)) || (rc = dev_alloc(&p->d_w, p->MM, own)) ||
         (rc = dev_alloc(&p->d_wnew, p->MM, own)) ||
         (rc = dev_alloc(&p->d_probe_part, (size_t)n_chunks * p->MM, own)) ||
@@ -406,6 +425,12 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         return bail(rc);
     if (p->blind) {
         if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own)))
+            return bail(rc);
+    }
+    if (m == 256 && (rc = dev_alloc(&p->d_T, (size_t)WAVE_256 * p->MM, own))) return bail(rc);
+    if (!p->blind) {
+        if ((rc = upload(&p->d_rank, rank, own, s)) || (rc = upload(&p->d_cnt, cnt, own, s)) ||
+            (rc = dev_alloc(&p->d_slot, (size_t)std::max(p->slot_k, 1) * p->u_len, own)))
             return bail(rc);
     }
     cudaError_t e;
@@ -492,6 +517,7 @@ int od2p_init(ptycho_plan_t *plan, const ptycho_c32 *u0, const ptycho_c32 *w0, p
     OD2P_CUDA(cudaMemsetAsync(plan->d_lam[0], 0, sizeof(float2) * std::max<int64_t>(plan->lam_len, 1), s));
     OD2P_CUDA(cudaMemsetAsync(plan->d_lam[1], 0, sizeof(float2) * std::max<int64_t>(plan->lam_len, 1), s));
     if (plan->blind) OD2P_CUDA(cudaMemsetAsync(plan->d_Delta, 0, sizeof(float2) * (size_t)plan->D * plan->MM, s));
+    else if (int rc = launch_illumination(plan, s)) return rc;  // the known probe's A_d^*A_d
     plan->initialised = true;
     return PTYCHO_OK;
 }
@@ -603,6 +629,7 @@ int od2p_get_state(const ptycho_plan_t *plan, int32_t which, ptycho_c32 *dst, pt
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (which == PTYCHO_STATE_GAMMA)
         return launch_permute_gamma(plan, plan->d_gamma, reinterpret_cast<float2 *>(dst), true, s);
+    if (which == PTYCHO_STATE_Q && !plan->blind) return launch_q_from_slots(plan, reinterpret_cast<float2 *>(dst), s);
     if (n) OD2P_CUDA(cudaMemcpyAsync(dst, state_ptr(plan, which), sizeof(float2) * n, cudaMemcpyDeviceToDevice, s));
     return PTYCHO_OK;
 }
@@ -618,6 +645,8 @@ int od2p_set_state(ptycho_plan_t *plan, int32_t which, const ptycho_c32 *src, pt
     if (which == PTYCHO_STATE_GAMMA)
         return launch_permute_gamma(plan, reinterpret_cast<const float2 *>(src), plan->d_gamma, false, s);
     if (n) OD2P_CUDA(cudaMemcpyAsync(state_ptr(plan, which), src, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s));
+    // a new known probe changes the nonblind denominators sum_j S_j^T |w|^2
+    if (which == PTYCHO_STATE_W && !plan->blind && plan->initialised) return launch_illumination(plan, s);
     return PTYCHO_OK;
 }
 

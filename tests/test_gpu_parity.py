@@ -70,7 +70,8 @@ def test_prox_matches_oracle(eps, lam):
     assert err.max() < 2e-6
 
 
-@pytest.mark.parametrize("m,n,step,jit", [(16, 61, 5, 1), (32, 100, 9, 2), (64, 300, 16, 2), (128, 400, 40, 3)])
+@pytest.mark.parametrize("m,n,step,jit", [(16, 61, 5, 1), (32, 100, 9, 2), (64, 300, 16, 2), (128, 400, 40, 3),
+                                          (256, 600, 64, 3)])
 def test_forward_and_adjoint_match_oracle(m, n, step, jit):
     rng = np.random.default_rng(m)
     offs = synth.raster_offsets(n, m, step, jit, seed=3)
@@ -171,7 +172,8 @@ def test_one_iteration_grid4x4_full_size(scrambled):
             od.od2p_set_state(plan, wg, c64(ref.get(wo)))
 
 
-@pytest.mark.parametrize("m,grid,n,step", [(32, (2, 3), 200, 10), (128, (2, 2), 384, 32), (16, (5, 4), 120, 6)])
+@pytest.mark.parametrize("m,grid,n,step", [(32, (2, 3), 200, 10), (128, (2, 2), 384, 32), (16, (5, 4), 120, 6),
+                                           (256, (2, 2), 512, 64)])
 def test_one_iteration_other_sizes(m, grid, n, step):
     p = synth.Problem("t", n, m, step, 2, grid[0], grid[1], 12, 1e5, 1, eta=0.3, r=0.2, seed=m)
     offs, u_true, w, f = make_case(p)
@@ -283,9 +285,10 @@ def test_checkpoint_resume_bitwise():
 
 
 # ----------------------------------------------------------------------------- blind
-@pytest.mark.parametrize("masked", [False, True])
-def test_blind_one_iteration(masked):
-    p = synth.Problem("b", 96, 32, 8, 1, 2, 2, 8, 1e5, 1, eta=0.3, r=0.2, blind=True, mu=2.0,
+@pytest.mark.parametrize("masked,m,n,step", [(False, 32, 96, 8), (True, 32, 96, 8), (False, 256, 512, 64),
+                                             (True, 256, 512, 64)])
+def test_blind_one_iteration(masked, m, n, step):
+    p = synth.Problem("b", n, m, step, 1, 2, 2, 8, 1e5, 1, eta=0.3, r=0.2, blind=True, mu=2.0,
                       gamma=0.1, seed=21)
     offs, u_true, w_true, f = make_case(p)
     w0 = synth.gaussian_probe(p.m)
@@ -309,7 +312,7 @@ def test_blind_one_iteration(masked):
 
 
 # ----------------------------------------------------------------------------- loss and gradients
-@pytest.mark.parametrize("m,n,step", [(16, 64, 4), (64, 256, 16), (128, 384, 48)])
+@pytest.mark.parametrize("m,n,step", [(16, 64, 4), (64, 256, 16), (128, 384, 48), (256, 512, 96)])
 def test_loss_and_gradients_match_oracle(m, n, step):
     p = synth.Problem("g", n, m, step, 2, 1, 1, 0, 1e4, 1, seed=m + 1)
     offs, u_true, w, f = make_case(p)
@@ -322,3 +325,51 @@ def test_loss_and_gradients_match_oracle(m, n, step):
     assert abs(float(loss.item()) - L) < 1e-5 * abs(L)
     assert rel_l2(host(gu), gu_o) < 1e-5
     assert rel_l2(host(gw), gw_o) < 1e-5
+
+
+# ----------------------------------------------------------------------------- full-size m = 256
+def test_large_blind_workload_sampled_frames():
+    """4096^2 image, 6561 frames of 256^2, 8x8 subdomains: one frame update on the
+    GPU, and the updated Gamma_j and residual q_j of sampled frames recomputed
+    frame by frame by the oracle (forward, prox, inverse)."""
+    p = synth.large_blind()
+    offs = p.offsets()
+    assert len(offs) == 6561
+    u_true, w_true = p.truth(), p.probe()
+    f = synth.poissonize(np.abs(oracle.forward(u_true, w_true, offs)) ** 2, p.peak, 11)
+    w0 = synth.gaussian_probe(p.m)
+    eta = 2.0
+    g = od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, eps=0.5, eta=eta, r=0.5,
+                    mu=1.0, gamma=0.0, blind=True)
+    plan = od.ptycho_plan(g, f32(f))
+    rng = np.random.default_rng(6)
+    u0 = (u_true * (1 + 0.1 * rng.standard_normal(u_true.shape))).astype(np.complex64)
+    od.od2p_init(plan, c64(w0), c64(u0))
+    od.od2p_frame_update(plan)
+    gam = od.od2p_get_state(plan, od.STATE_GAMMA)
+    q = od.od2p_get_state(plan, od.STATE_Q)
+    mm = p.m * p.m
+    for j in rng.choice(len(offs), 12, replace=False):
+        r0, c0 = offs[j]
+        x = oracle.forward(u0, w0, offs[j:j + 1])[0]          # A u for frame j (u_d = R_d u0)
+        z = oracle.stagm_prox(x, f[j].astype(np.float64), 0.5, eta)
+        g_ref = x - z                                          # Gamma^0 = 0
+        q_ref = oracle.fft2(z - g_ref, True)
+        assert rel_l2(host(gam[j * mm:(j + 1) * mm]), g_ref) < ONE_ITER_TOL
+        assert rel_l2(host(q[j * mm:(j + 1) * mm]), q_ref) < ONE_ITER_TOL
+
+
+def test_nonblind_residual_frames_from_gather_slots():
+    """q_j = conj(w) o F^*(z_j - Gamma_j) exported from the nonblind gather slots."""
+    p = synth.grid_4x4()
+    offs, u_true, w, f = make_case(p)
+    plan, ref = pair_of(p, offs, w, f)
+    _scramble(plan, ref, 9)
+    od.od2p_iterate(plan, 1)
+    ref.iterate(1)
+    mm = p.m * p.m
+    z, gam = ref.get(oracle.Z).reshape(-1, p.m, p.m), ref.get(oracle.GAMMA).reshape(-1, p.m, p.m)
+    q = host(od.od2p_get_state(plan, od.STATE_Q)).reshape(-1, p.m, p.m)
+    for j in np.random.default_rng(1).choice(len(offs), 20, replace=False):
+        q_ref = np.conj(w) * oracle.fft2(z[j] - gam[j], True)
+        assert rel_l2(q[j], q_ref) < ONE_ITER_TOL

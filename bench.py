@@ -203,6 +203,67 @@ def e2e_run(od, geom, f, w, offs, p, dev, K, ws):
             "step": f"one reconstruction: H2D f, plan, init, {p.n_iter} iterations, merge, D2H image"}
 
 
+def batched_leg(od, dev, K: int = 10, W: int = 2, count: int = 64):
+    """Config-3 workload: `count` independent nonblind reconstructions of mixed
+    sizes.  The batch (one frame-update launch per probe side + one subdomain
+    update per iteration, graph-replayed) against the same plans iterated one
+    after another; equal error is shown by bitwise-identical states."""
+    import torch
+    from paper_2011_00162_gb300 import synth
+    probs = synth.batched_problems(count, seed=3)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+    geoms, fs, ws = [], [], []
+    for p in probs:
+        offs = p.offsets()
+        u, w = p.truth(), p.probe()
+        tmp = od.ptycho_plan(od.Geometry(p.n, p.n, p.m, offs),
+                             torch.ones((len(offs), p.m, p.m), dtype=torch.float32, device=dev))
+        fr = od.ptycho_forward(tmp, torch.from_numpy(u).to(dev), torch.from_numpy(w).to(dev))
+        tmp.close()
+        fc = fr.abs() ** 2
+        kappa = float(p.peak) / float(fc.max())
+        fs.append((torch.poisson(fc * kappa, generator=gen) / kappa).float().contiguous())
+        ws.append(torch.from_numpy(w).to(dev))
+        geoms.append(od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, 0.5, 2.0, 0.5))
+        del fr, fc
+    J = sum(g.n_frames for g in geoms)
+    batch = od.ptycho_batch_plan(geoms, fs)
+    for m, w in zip(batch.members, ws):
+        od.od2p_init(m, w)
+    plains = [od.ptycho_plan(g, f) for g, f in zip(geoms, fs)]
+    for pl, w in zip(plains, ws):
+        od.od2p_init(pl, w)
+    batch.iterate(W)
+    for pl in plains:
+        od.od2p_iterate(pl, W)
+    s = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    e[0].record(s)
+    batch.iterate(K)
+    e[1].record(s)
+    for _ in range(K):
+        for pl in plains:
+            od.od2p_iterate(pl, 1)
+    e[2].record(s)
+    torch.cuda.synchronize()
+    tb, tp = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
+    same = all(torch.equal(od.od2p_get_state(batch.members[i], od.STATE_U), od.od2p_get_state(plains[i], od.STATE_U))
+               for i in range(len(plains)))
+    for pl in plains:
+        pl.close()
+    batch.close()
+    return {"workload": f"{count} independent reconstructions (images 256-992, probes 32/64/128, "
+                        "steps 8-m/2, grids 2x2-8x8, Poisson 1e3-1e5, seed 3)",
+            "frames": J, "iterations": K,
+            "batched_frame_updates_per_s": round(J * K / tb, 1),
+            "plain_frame_updates_per_s": round(J * K / tp, 1),
+            "speedup": round(tp / tb, 3),
+            "equal_error": "bitwise identical states after the same iterations" if same else "states differ",
+            "launches_per_iteration": {"batched": len({g.m for g in geoms}) + 1, "plain": 2 * len(geoms)}}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -305,6 +366,8 @@ def run_gpu(args):
         "clocks": clocks,
         "wall_s_timed_region": round(wall1 - wall0, 4),
     }
+    if not args.no_batched:
+        line["batched"] = batched_leg(od, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
     if rank == 0:
@@ -382,6 +445,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -242,6 +242,31 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c
                     int32_t recompute, ptycho_stream_t stream);
 
 /*
+ * Batches of independent reconstructions (nonblind, probe sides up to 128,
+ * mixed image, probe, scan and subdomain sizes).  One ADMM iteration of all
+ * members is one frame-update launch per distinct probe side -- a persistent
+ * kernel over the (member, frame group) work items -- and one subdomain-update
+ * launch over the tiles of all members, replayed from a CUDA graph.  Each
+ * member computes exactly what od2p_iterate computes on it alone (bitwise).
+ *
+ * ptycho_batch_plan: geoms[i], f_devs[i] as for ptycho_plan, i < n; the
+ *   members are plans owned by the batch (ptycho_batch_member hands out
+ *   borrowed pointers for od2p_init, od2p_merge, od2p_get_state, ...; do not
+ *   destroy them, and do not iterate a member on its own between batch
+ *   iterations -- the call returns PTYCHO_ERR_STATE).
+ * ptycho_batch_iterate: n_iter iterations of every member; od2p_init must
+ *   have been called on each.  Errors: INVALID_ARG, UNSUPPORTED (a blind member
+ *   or m = 256), STATE, OOM, CUDA.
+ */
+typedef struct ptycho_batch_s ptycho_batch_t;
+int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const float *const *f_devs, int32_t n,
+                      ptycho_stream_t stream);
+int ptycho_batch_destroy(ptycho_batch_t *batch);
+int ptycho_batch_size(const ptycho_batch_t *batch, int32_t *n_out);
+int ptycho_batch_member(const ptycho_batch_t *batch, int32_t i, ptycho_plan_t **plan_out);
+int ptycho_batch_iterate(ptycho_batch_t *batch, int32_t n_iter, ptycho_stream_t stream);
+
+/*
  * Allocation-free ST-AGM loss.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- code running while
  * a CUDA stream is being captured into a graph (allocation is not a capturable

@@ -58,6 +58,11 @@ SIGNATURES = {
     "od2p_set_state": (ctypes.c_int, [_P, _I32, _P, _P]),
     "stagm_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _I32, _P]),
     "stagm_loss_noalloc": (ctypes.c_int, [_P, _I32, _I32, _P, _I32, _P, _I32, _P, _F, _P, _P]),
+    "ptycho_batch_plan": (ctypes.c_int, [_P, _P, _P, _I32, _P]),
+    "ptycho_batch_destroy": (ctypes.c_int, [_P]),
+    "ptycho_batch_size": (ctypes.c_int, [_P, _P]),
+    "ptycho_batch_member": (ctypes.c_int, [_P, _I32, _P]),
+    "ptycho_batch_iterate": (ctypes.c_int, [_P, _I32, _P]),
 }
 
 

@@ -22,6 +22,7 @@ __all__ = [
     "od2p_iterate", "od2p_frame_update", "od2p_subdomain_update", "probe_update", "od2p_merge",
     "od2p_metrics", "od2p_get_state", "od2p_set_state", "stagm_loss_grad", "PtychoError",
     "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
+    "Batch", "ptycho_batch_plan", "ptycho_batch_iterate",
 ]
 
 
@@ -123,6 +124,85 @@ class Plan:
 
 def ptycho_plan(geom: Geometry, f: torch.Tensor, stream=None) -> Plan:
     return Plan(geom, f, stream)
+
+
+def _geometry_struct(geom: Geometry):
+    offs = np.ascontiguousarray(np.asarray(geom.offsets, np.int32).reshape(-1, 2))
+    mask = (np.ascontiguousarray(np.asarray(geom.fourier_support, np.uint8))
+            if geom.fourier_support is not None else None)
+    g = _lib.Geometry(geom.img_h, geom.img_w, geom.m, offs.shape[0], offs.ctypes.data, geom.sub_rows,
+                      geom.sub_cols, geom.overlap_px, geom.eps, geom.eta, geom.r, geom.mu, geom.gamma,
+                      int(bool(geom.blind)), mask.ctypes.data if mask is not None else None)
+    return g, (offs, mask)
+
+
+class _Member(Plan):
+    """A plan owned by a Batch (not destroyed by the wrapper)."""
+
+    def __init__(self, handle, geom: Geometry, device):
+        self._lib = _lib.load()
+        self.geom = geom
+        self._h = handle
+        self.device = device
+        D, P = ctypes.c_int32(), ctypes.c_int32()
+        ul, ll = ctypes.c_int64(), ctypes.c_int64()
+        check(self._lib.ptycho_plan_dims(handle, ctypes.byref(D), ctypes.byref(P), ctypes.byref(ul),
+                                         ctypes.byref(ll)))
+        self.n_sub, self.n_pairs, self.u_len, self.lambda_len = D.value, P.value, ul.value, ll.value
+        self.n_frames = geom.n_frames
+
+    def close(self) -> None:
+        self._h = None  # the batch owns the plan
+
+
+class Batch:
+    """Independent nonblind reconstructions iterated together (ptycho_batch_*)."""
+
+    def __init__(self, geoms: list, fs: list, stream=None):
+        if len(geoms) != len(fs) or not geoms:
+            raise ValueError("need matching, non-empty lists of geometries and intensity stacks")
+        self._lib = _lib.load()
+        structs, self._keep = [], []
+        for g, f in zip(geoms, fs):
+            st, keep = _geometry_struct(g)
+            structs.append(st)
+            self._keep.append(keep)
+            if tuple(f.shape) != (g.n_frames, g.m, g.m):
+                raise ValueError("each f must be (J, m, m)")
+        arr = (_lib.Geometry * len(geoms))(*structs)
+        ptrs = (ctypes.c_void_p * len(fs))(*[_ptr(f, torch.float32, "f").value for f in fs])
+        h = ctypes.c_void_p()
+        check(self._lib.ptycho_batch_plan(ctypes.byref(h), arr, ptrs, len(geoms), _stream(stream)))
+        self._h = h
+        self.members = []
+        for i, g in enumerate(geoms):
+            mp = ctypes.c_void_p()
+            check(self._lib.ptycho_batch_member(h, i, ctypes.byref(mp)))
+            self.members.append(_Member(mp, g, fs[i].device))
+
+    def iterate(self, n_iter: int = 1, stream=None) -> None:
+        check(self._lib.ptycho_batch_iterate(self._h, int(n_iter), _stream(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            for m in self.members:
+                m._h = None
+            self._lib.ptycho_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ptycho_batch_plan(geoms: list, fs: list, stream=None) -> Batch:
+    return Batch(geoms, fs, stream)
+
+
+def ptycho_batch_iterate(batch: Batch, n_iter: int = 1, stream=None) -> None:
+    batch.iterate(n_iter, stream)
 
 
 def _c64(shape, device):

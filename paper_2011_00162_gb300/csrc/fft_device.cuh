@@ -87,10 +87,6 @@ __device__ __forceinline__ float block_sum_fixed(float v, float *red)
     return t;
 }
 
-struct ProxConst {
-    float lam, inv1plam, c_thr, c_k1;
-};
-
 // eq. (Prox_sol) with the threshold read as |y| < (eps - (1-eps)/lam) sqrt f.
 // z = y * rho / |y| with 1/|y| from the hardware reciprocal square root
 // (relative error ~1e-7, far inside the FP32 parity budget); y = 0 gives (rho, 0).
@@ -111,15 +107,7 @@ __device__ __forceinline__ float2 stagm_prox(float2 y, float sf, const ProxConst
     return make_float2(rho, 0.f);
 }
 
-inline ProxConst make_prox_const(float eps, float lam)
-{
-    ProxConst k;
-    k.lam = lam;
-    k.inv1plam = 1.f / (1.f + lam);
-    k.c_thr = eps - (1.f - eps) / lam;
-    k.c_k1 = k.c_thr > 0.f ? lam / (lam - (1.f - eps) / eps) : 0.f;
-    return k;
-}
+
 
 }  // namespace
 }  // namespace od2p

@@ -238,21 +238,6 @@ __device__ __forceinline__ void col_stage1_store_slots(float2 *buf, const float2
 }
 
 // ---------------------------------------------------------------- K1: fused frame update
-struct FrameArgs {
-    int32_t J;
-    const int32_t *frame_sub, *frame_base, *frame_pitch;
-    const float2 *u, *w, *Wd; // Wd non-null for blind plans (per-subdomain probe)
-    float2 *gamma;            // transposed position layout
-    const float *sqrtf_;      // transposed position layout
-    float2 *q;                // out (blind): F^*(z - Gamma^{n+1}), natural spatial order
-    float2 *slot;             // out (nonblind): conj(w) o F^*(z - Gamma^{n+1}) in gather slots
-    const uint8_t *rank;      // nonblind: slot rank of each frame pixel
-    int32_t slot_stride;      // u_len
-    float *rf_part;           // out: one per block
-    int32_t *err;             // set to 1 if a pipeline wait gives up
-    const float2 *tw;
-    ProxConst pc;
-};
 
 // Launch shape of the persistent frame update: frames per group, threads, and
 // whether Gamma is staged in shared memory (m = 128 only stages sqrt f: the
@@ -322,40 +307,51 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// Persistent: block b handles frame groups b, b + grid, ...  While a group's
-// forward FFT runs, the TMA unit brings its Gamma and sqrt f slices into shared
-// memory (issued when the previous group's prox finished with the staging
-// buffers), and the next group's exit-wave windows are prefetched into L2.
-template <int M>
-__global__ void __launch_bounds__(K1Cfg<M>::NT, K1Cfg<M>::MINB) frame_update_kernel(FrameArgs a)
+// Persistent and table-driven: work item i (block b takes b, b + grid, ...)
+// is frame group items[i].y of the plan whose arguments are tab[2 items[i].x
+// + parity] (one plan: items = null and item i is group i of tab[parity]).
+// While a group's forward FFT runs, the TMA unit brings its Gamma and sqrt f
+// slices into shared memory (issued when the previous group's prox finished
+// with the staging buffers), and the next group's exit-wave windows are
+// prefetched into L2.  Each group's RF partial goes to rf_part[group].
+template <int M, bool BATCHED>
+__global__ void __launch_bounds__(K1Cfg<M>::NT, K1Cfg<M>::MINB)
+    frame_update_kernel(const FrameArgs single, const FrameArgs *__restrict__ tab, const int2 *__restrict__ items,
+                        int n_items, int parity)
 {
     constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = K1Cfg<M>::FPB, NT = K1Cfg<M>::NT;
     constexpr int P = M + 1, MM = M * M;
     constexpr bool SG = K1Cfg<M>::STAGE_G != 0;
     extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ FrameArgs sa_batch;  // batches: arguments of the current item's plan
+    const FrameArgs &sa = BATCHED ? sa_batch : single;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     float2 *stg_g = reinterpret_cast<float2 *>(smem + 128);
     float *stg_f = reinterpret_cast<float *>(smem + 128 + (SG ? sizeof(float2) * FPB * MM : 0));
     float2 *tw = reinterpret_cast<float2 *>(stg_f + FPB * MM);
     float2 *buf = tw + M;
     float *red = reinterpret_cast<float *>(buf + FPB * M * P);
-    const int n_groups = (a.J + FPB - 1) / FPB;
 
-    auto issue = [&](int g) {  // one thread: stage group g's Gamma / sqrt f
-        const int j0 = g * FPB, nf = min(FPB, a.J - j0);
+    auto item = [&](int i) { return BATCHED ? items[i] : make_int2(0, i); };
+    auto issue = [&](int i) {  // one thread: stage item i's Gamma / sqrt f
+        const int2 it = item(i);
+        const FrameArgs &ga = BATCHED ? tab[2 * it.x + parity] : single;
+        const int j0 = it.y * FPB, nf = min(FPB, ga.J - j0);
         const unsigned fbytes = (unsigned)(nf * MM * sizeof(float));
         const unsigned gbytes = SG ? (unsigned)(nf * MM * sizeof(float2)) : 0u;
         mbar_expect_tx(bar, fbytes + gbytes);
-        if (SG) bulk_g2s(stg_g, a.gamma + (size_t)j0 * MM, gbytes, bar);
-        bulk_g2s(stg_f, a.sqrtf_ + (size_t)j0 * MM, fbytes, bar);
+        if (SG) bulk_g2s(stg_g, ga.gamma + (size_t)j0 * MM, gbytes, bar);
+        bulk_g2s(stg_f, ga.sqrtf_ + (size_t)j0 * MM, fbytes, bar);
     };
-    auto prefetch_windows = [&](int g) {  // all threads: next group's exit-wave windows into L2
+    auto prefetch_windows = [&](int i) {  // all threads: item i's exit-wave windows into L2
         constexpr int LINES = (M * 8 + 127) / 128 + 1;
-        const int j0 = g * FPB;
-        for (int i = threadIdx.x; i < FPB * M * LINES; i += NT) {
-            const int f = i / (M * LINES), row = (i / LINES) % M, l = i % LINES, j = j0 + f;
-            if (j >= a.J) continue;
-            const char *rp = reinterpret_cast<const char *>(a.u + a.frame_base[j] + (size_t)row * a.frame_pitch[j]);
+        const int2 it = item(i);
+        const FrameArgs &ga = BATCHED ? tab[2 * it.x + parity] : single;
+        const int j0 = it.y * FPB;
+        for (int k = threadIdx.x; k < FPB * M * LINES; k += NT) {
+            const int f = k / (M * LINES), row = (k / LINES) % M, l = k % LINES, j = j0 + f;
+            if (j >= ga.J) continue;
+            const char *rp = reinterpret_cast<const char *>(ga.u + ga.frame_base[j] + (size_t)row * ga.frame_pitch[j]);
             prefetch_l2(rp + min(l * 128, M * 8 - 8));
         }
     };
@@ -364,38 +360,47 @@ __global__ void __launch_bounds__(K1Cfg<M>::NT, K1Cfg<M>::MINB) frame_update_ker
         mbar_init(bar, 1);
         mbar_fence_init();
     }
-    for (int k = threadIdx.x; k < M; k += NT) tw[k] = a.tw[k];
+    for (int k = threadIdx.x; k < M; k += NT) tw[k] = (BATCHED ? tab[parity] : single).tw[k];
     __syncthreads();
-    int g = blockIdx.x;
-    if (threadIdx.x == 0 && g < n_groups) issue(g);
+    int i = blockIdx.x;
+    if (threadIdx.x == 0 && i < n_items) issue(i);
     unsigned phase = 0;
-    float rf = 0.f;
+    int plan_now = -1;
     const float inv_m = 1.f / (float)M;
-    for (; g < n_groups; g += gridDim.x) {
-        const int j0 = g * FPB;
-        if (g + (int)gridDim.x < n_groups) prefetch_windows(g + gridDim.x);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (; i < n_items; i += gridDim.x) {
+        const int2 it = item(i);
+        if (BATCHED && it.x != plan_now) {  // uniform: every thread sees the same item
+            __syncthreads();
+            if (threadIdx.x == 0) sa_batch = tab[2 * it.x + parity];
+            __syncthreads();
+            plan_now = it.x;
+        }
+        const int j0 = it.y * FPB;
+        if (i + (int)gridDim.x < n_items) prefetch_windows(i + gridDim.x);
         if (!SG && threadIdx.x == 0) {
-            const int nf = min(FPB, a.J - j0);
-            const char *gp = reinterpret_cast<const char *>(a.gamma + (size_t)j0 * MM);
+            const int nf = min(FPB, sa.J - j0);
+            const char *gp = reinterpret_cast<const char *>(sa.gamma + (size_t)j0 * MM);
             for (unsigned off = 0; off < (unsigned)(nf * MM * sizeof(float2)); off += 16384u)
                 bulk_prefetch_l2(gp + off, min(16384u, (unsigned)(nf * MM * sizeof(float2)) - off));
         }
         // Step 1: psi = w o S_j u_d^n, then F psi (three of the four forward stages)
-        col_stage1_load<M, FPB, NT>(buf, tw, j0, a.J, a.w, a.Wd, a.frame_sub, a.u, a.frame_base, a.frame_pitch);
+        col_stage1_load<M, FPB, NT>(buf, tw, j0, sa.J, sa.w, sa.Wd, sa.frame_sub, sa.u, sa.frame_base, sa.frame_pitch);
         __syncthreads();
         col_stage2<M, false, FPB, NT>(buf);
         __syncthreads();
         row_stage1<M, false, FPB, NT>(buf, tw);
         const bool ok = mbar_wait_bounded(bar, phase);
         if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) *a.err = 1;
+            if (threadIdx.x == 0) *sa.err = 1;
             return;
         }
         phase ^= 1u;
         // last forward stage, prox and Gamma update, first inverse stage -- in registers
+        float rf = 0.f;
         for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
             const int r = task % M, rest = task / M, s = rest % R1, f = rest / R1, j = j0 + f;
-            if (j >= a.J) continue;
+            if (j >= sa.J) continue;
             float2 *fb = buf + f * M * P + r * P;
             float2 x[R2];
 #pragma unroll
@@ -408,41 +413,44 @@ __global__ void __launch_bounds__(K1Cfg<M>::NT, K1Cfg<M>::MINB) frame_update_ker
                 const size_t gi = (size_t)j0 * MM + li;
                 const float2 ax = cscale(x[t], inv_m);   // (A_d u_d^n)_k
                 const float sf = stg_f[li];
-                const float2 gm = SG ? stg_g[li] : a.gamma[gi];
+                const float2 gm = SG ? stg_g[li] : sa.gamma[gi];
                 const float a2 = ax.x * ax.x + ax.y * ax.y;
                 rf += fabsf((a2 > 0.f ? a2 * rsqrtf(a2) : 0.f) - sf);  // | |A_d u_d| - sqrt f |
                 const float2 y = cadd(gm, ax);            // Gamma^n + A_d u_d^n
-                const float2 z = stagm_prox(y, sf, a.pc); // eq. updateZ
+                const float2 z = stagm_prox(y, sf, sa.pc); // eq. updateZ
                 const float2 gn = csub(y, z);             // eq. updateM-1-multi
-                a.gamma[gi] = gn;
+                sa.gamma[gi] = gn;
                 x[t] = csub(z, gn);                       // z^{n+1} - Gamma^{n+1}
             }
             dft<R2, true>(x);
 #pragma unroll
             for (int t = 0; t < R2; ++t) fb[R2 * s + t] = x[t];
         }
-        __syncthreads();  // staging buffers are free: start the next group's copies
-        if (threadIdx.x == 0 && g + (int)gridDim.x < n_groups) {
+        __syncthreads();  // staging buffers are free: start the next item's copies
+        if (threadIdx.x == 0 && i + (int)gridDim.x < n_items) {
             fence_proxy_async_smem();
-            issue(g + gridDim.x);
+            issue(i + gridDim.x);
         }
         row_stage1<M, true, FPB, NT>(buf, tw);
         __syncthreads();
         col_stage2<M, true, FPB, NT>(buf);
         __syncthreads();
-        if (a.slot) {
+        if (sa.slot) {
             // nonblind: q_j = conj(w) o F^*(z - Gamma) (the A_d^* summand), stored in
             // the gather slot of each pixel
-            col_stage1_store_slots<M, FPB, NT>(buf, tw, j0, a.J, a.slot, a.rank, a.slot_stride, a.frame_base,
-                                               a.frame_pitch, inv_m, a.w);
+            col_stage1_store_slots<M, FPB, NT>(buf, tw, j0, sa.J, sa.slot, sa.rank, sa.slot_stride, sa.frame_base,
+                                               sa.frame_pitch, inv_m, sa.w);
         } else {
             // blind: unweighted; the subdomain update weights with W_d^{n+1}
-            col_stage1_store<M, FPB, NT>(buf, tw, j0, a.J, a.q, inv_m, nullptr);
+            col_stage1_store<M, FPB, NT>(buf, tw, j0, sa.J, sa.q, inv_m, nullptr);
         }
+        // this group's RF partial, one per warp (fixed xor tree inside the warp)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rf += __shfl_xor_sync(0xffffffffu, rf, o);
+        if (lane == 0) sa.rf_part[it.y * (NT / 32) + warp] = rf;
         __syncthreads();
     }
-    const float tot = block_sum_fixed(rf, red);
-    if (threadIdx.x == 0) a.rf_part[blockIdx.x] = tot;
+    (void)red;
 }
 
 // ---------------------------------------------------------------- forward operator
@@ -709,46 +717,42 @@ int set_smem(K kernel)
 }
 
 template <int M>
-int k1_grid_m(int J, int *grid)
+int k1_grid_m(int n_items, int *grid)
 {
     static int per_sm = 0, n_sm = 0;
     if (!per_sm) {
-        OD2P_CUDA(cudaFuncSetAttribute(frame_update_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        OD2P_CUDA(cudaFuncSetAttribute(frame_update_kernel<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)k1_smem_bytes<M>()));
-        int dev = 0;
+        OD2P_CUDA(cudaFuncSetAttribute(frame_update_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)k1_smem_bytes<M>()));
+        int dev = 0, a = 0, b = 0;
         OD2P_CUDA(cudaGetDevice(&dev));
         OD2P_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, frame_update_kernel<M>, K1Cfg<M>::NT,
+        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, frame_update_kernel<M, false>, K1Cfg<M>::NT,
                                                                 k1_smem_bytes<M>()));
+        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, frame_update_kernel<M, true>, K1Cfg<M>::NT,
+                                                                k1_smem_bytes<M>()));
+        per_sm = std::min(a, b);
         if (per_sm < 1) return fail(PTYCHO_ERR_UNSUPPORTED, "frame update does not fit on an SM");
     }
-    const int groups = (J + K1Cfg<M>::FPB - 1) / K1Cfg<M>::FPB;
-    *grid = std::min(groups, per_sm * n_sm);
+    *grid = std::max(1, std::min(n_items, per_sm * n_sm));
     return PTYCHO_OK;
 }
 
 template <int M>
-int frame_update_m(ptycho_plan_s *p, cudaStream_t s)
+int frame_update_table_m(const FrameArgs *tab, const int2 *items, int n_items, int grid, int parity, cudaStream_t s)
 {
-    FrameArgs a;
-    a.J = p->J;
-    a.frame_sub = p->d_frame_sub;
-    a.frame_base = p->d_frame_base;
-    a.frame_pitch = p->d_frame_pitch;
-    a.u = p->d_u[p->cur];
-    a.w = p->d_w;
-    a.Wd = p->blind ? p->d_Wd : nullptr;
-    a.gamma = p->d_gamma;
-    a.sqrtf_ = p->d_sqrtf;
-    a.q = p->d_q;
-    a.slot = p->blind ? nullptr : p->d_slot;
-    a.rank = p->d_rank;
-    a.slot_stride = (int32_t)p->u_len;
-    a.rf_part = p->d_rf_part;
-    a.err = p->d_err;
-    a.tw = p->d_tw;
-    a.pc = make_prox_const(p->eps, p->eta);
-    frame_update_kernel<M><<<p->n_k1_blocks, K1Cfg<M>::NT, k1_smem_bytes<M>(), s>>>(a);
+    frame_update_kernel<M, true><<<grid, K1Cfg<M>::NT, k1_smem_bytes<M>(), s>>>(FrameArgs{}, tab, items, n_items,
+                                                                                parity);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+template <int M>
+int frame_update_single_m(const ptycho_plan_s *p, cudaStream_t s)
+{
+    frame_update_kernel<M, false><<<p->n_k1_blocks, K1Cfg<M>::NT, k1_smem_bytes<M>(), s>>>(
+        p->h_fargs[p->cur], nullptr, nullptr, frame_groups(M, p->J), p->cur);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
@@ -839,14 +843,15 @@ int frames_per_block(int m)
 }
 
 // Number of blocks of the persistent frame update for J frames of side m.
-int frame_update_grid(int m, int J, int *grid)
+// Blocks of the persistent frame update for n_items frame groups of side m.
+int frame_update_grid(int m, int n_items, int *grid)
 {
     switch (m) {
-    case 16: return k1_grid_m<16>(J, grid);
-    case 32: return k1_grid_m<32>(J, grid);
-    case 64: return k1_grid_m<64>(J, grid);
-    case 128: return k1_grid_m<128>(J, grid);
-    case 256: *grid = J * 16; return PTYCHO_OK;  // one partial per 16-column slab of each frame
+    case 16: return k1_grid_m<16>(n_items, grid);
+    case 32: return k1_grid_m<32>(n_items, grid);
+    case 64: return k1_grid_m<64>(n_items, grid);
+    case 128: return k1_grid_m<128>(n_items, grid);
+    case 256: *grid = n_items; return PTYCHO_OK;
     default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }
@@ -878,13 +883,74 @@ int prepare_kernels(int m)
     }
 }
 
+int frame_groups(int m, int J)
+{
+    switch (m) {
+    case 16: return (J + K1Cfg<16>::FPB - 1) / K1Cfg<16>::FPB;
+    case 32: return (J + K1Cfg<32>::FPB - 1) / K1Cfg<32>::FPB;
+    case 64: return (J + K1Cfg<64>::FPB - 1) / K1Cfg<64>::FPB;
+    case 128: return (J + K1Cfg<128>::FPB - 1) / K1Cfg<128>::FPB;
+    default: return J * 16;  // m = 256: 16-column slabs
+    }
+}
+
+// RF partial sums written per iteration: one per warp of each frame group
+// (m <= 128), one per 16-column slab (m = 256).
+int rf_parts(int m, int J)
+{
+    switch (m) {
+    case 16: return frame_groups(m, J) * (K1Cfg<16>::NT / 32);
+    case 32: return frame_groups(m, J) * (K1Cfg<32>::NT / 32);
+    case 64: return frame_groups(m, J) * (K1Cfg<64>::NT / 32);
+    case 128: return frame_groups(m, J) * (K1Cfg<128>::NT / 32);
+    default: return J * 16;
+    }
+}
+
+void fill_frame_args(const ptycho_plan_s *p, FrameArgs out[2])
+{
+    for (int par = 0; par < 2; ++par) {
+        FrameArgs &a = out[par];
+        a = FrameArgs{};
+        a.J = p->J;
+        a.frame_sub = p->d_frame_sub;
+        a.frame_base = p->d_frame_base;
+        a.frame_pitch = p->d_frame_pitch;
+        a.u = p->d_u[par];
+        a.w = p->d_w;
+        a.Wd = p->blind ? p->d_Wd : nullptr;
+        a.gamma = p->d_gamma;
+        a.sqrtf_ = p->d_sqrtf;
+        a.q = p->d_q;
+        a.slot = p->blind ? nullptr : p->d_slot;
+        a.rank = p->d_rank;
+        a.slot_stride = (int32_t)p->u_len;
+        a.rf_part = p->d_rf_part;
+        a.err = p->d_err;
+        a.tw = p->d_tw;
+        a.pc = make_prox_const(p->eps, p->eta);
+    }
+}
+
+int launch_frame_update_table(int m, const FrameArgs *tab, const int2 *items, int n_items, int grid, int parity,
+                              cudaStream_t s)
+{
+    switch (m) {
+    case 16: return frame_update_table_m<16>(tab, items, n_items, grid, parity, s);
+    case 32: return frame_update_table_m<32>(tab, items, n_items, grid, parity, s);
+    case 64: return frame_update_table_m<64>(tab, items, n_items, grid, parity, s);
+    case 128: return frame_update_table_m<128>(tab, items, n_items, grid, parity, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "table-driven frame update: m must be 16, 32, 64 or 128");
+    }
+}
+
 int launch_frame_update(ptycho_plan_s *p, cudaStream_t s)
 {
     switch (p->M) {
-    case 16: return frame_update_m<16>(p, s);
-    case 32: return frame_update_m<32>(p, s);
-    case 64: return frame_update_m<64>(p, s);
-    case 128: return frame_update_m<128>(p, s);
+    case 16: return frame_update_single_m<16>(p, s);
+    case 32: return frame_update_single_m<32>(p, s);
+    case 64: return frame_update_single_m<64>(p, s);
+    case 128: return frame_update_single_m<128>(p, s);
     case 256: return frame_update_256(p, s);
     default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }

@@ -47,24 +47,6 @@ __device__ __forceinline__ void block_sum2_fixed(float &a, float &b, float *red)
 }
 
 // ---------------------------------------------------------------- K2: subdomain update
-struct SubArgs {
-    int32_t M;
-    const int32_t *rect;
-    const int64_t *u_off;
-    const Tile *tiles;
-    const int32_t *tptr, *tnbr_ptr;
-    const ListEntry *tlist;
-    const NbrInfo *tnbr;
-    const float2 *u_cur, *lam_cur, *q, *w, *Wd;
-    const float *nrm;
-    const float2 *slot;        // nonblind gather slots
-    const uint8_t *cnt;
-    int32_t slot_stride;
-    float2 *u_next, *lam_next;
-    float eta, r, gamma;
-    int32_t blind;
-    float *re_part;
-};
 
 // One block per TILE_H x TILE_W tile; lane = column, warp w owns rows
 // [w * TILE_ROWS, (w + 1) * TILE_ROWS) of it.  The tile's frame list (ascending
@@ -75,13 +57,26 @@ struct SubArgs {
 constexpr int LIST_SMEM = 160;
 constexpr int NBR_SMEM = 16;
 
-template <bool BLIND>
-__global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4) subdomain_update_kernel(SubArgs a)
+// One plan: block b updates tile b with the arguments `single`.  Batches:
+// block b updates tile items[b].y of the plan whose arguments are
+// tab[2 items[b].x + parity].
+template <bool BLIND, bool BATCHED>
+__global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4)
+    subdomain_update_kernel(const SubArgs single, const SubArgs *__restrict__ tab, const int2 *__restrict__ items,
+                            int parity)
 {
     __shared__ float red[2 * (GATHER_THREADS / 32)];
     __shared__ ListEntry lst[LIST_SMEM];
     __shared__ NbrInfo nbs[NBR_SMEM];
-    const Tile tile = a.tiles[blockIdx.x];
+    __shared__ SubArgs sa;
+    const int2 it = BATCHED ? items[blockIdx.x] : make_int2(0, (int)blockIdx.x);
+    if (BATCHED) {
+        if (threadIdx.x == 0) sa = tab[2 * it.x + parity];
+        __syncthreads();
+    }
+    const SubArgs &a = BATCHED ? sa : single;
+    const int tix = it.y;
+    const Tile tile = a.tiles[tix];
     const int d = tile.reg;
     const int32_t *rc = a.rect + 4 * d;
     const int hd = rc[2] - rc[0], wd = rc[3] - rc[1];
@@ -91,8 +86,8 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4) subdomain_updat
     const int nrows = min(TILE_ROWS, hd - tile.r0 - ty0);  // rows of this thread inside Omega_d (may be <= 0)
     const int C = rc[1] + lc;
     const int M = a.M, MM = M * M;
-    const int k0 = a.tptr[blockIdx.x], nk = a.tptr[blockIdx.x + 1] - k0;
-    const int n0 = a.tnbr_ptr[blockIdx.x], nnb = a.tnbr_ptr[blockIdx.x + 1] - n0;
+    const int k0 = a.tptr[tix], nk = a.tptr[tix + 1] - k0;
+    const int n0 = a.tnbr_ptr[tix], nnb = a.tnbr_ptr[tix + 1] - n0;
     for (int i = threadIdx.x; i < min(nk, LIST_SMEM); i += GATHER_THREADS) lst[i] = a.tlist[k0 + i];
     for (int i = threadIdx.x; i < min(nnb, NBR_SMEM); i += GATHER_THREADS) nbs[i] = a.tnbr[n0 + i];
     __syncthreads();
@@ -254,8 +249,8 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4) subdomain_updat
     }
     block_sum2_fixed(dn, nn, red);
     if (threadIdx.x == 0) {
-        a.re_part[2 * blockIdx.x] = dn;
-        a.re_part[2 * blockIdx.x + 1] = nn;
+        a.re_part[2 * tix] = dn;
+        a.re_part[2 * tix + 1] = nn;
     }
 }
 
@@ -530,37 +525,58 @@ __global__ void prox_kernel(const float2 *y, const float *f, float2 *z, int64_t 
 
 }  // namespace
 
+void fill_sub_args(const ptycho_plan_s *p, SubArgs out[2])
+{
+    for (int par = 0; par < 2; ++par) {
+        SubArgs &a = out[par];
+        a = SubArgs{};
+        a.M = p->M;
+        a.rect = p->d_rect;
+        a.u_off = p->d_u_off;
+        a.tiles = p->sub_tiles.tiles;
+        a.tptr = p->sub_tiles.ptr;
+        a.tlist = p->sub_tiles.list;
+        a.tnbr_ptr = p->sub_tiles.nbr_ptr;
+        a.tnbr = p->sub_tiles.nbr;
+        a.u_cur = p->d_u[par];
+        a.lam_cur = p->d_lam[par];
+        a.u_next = p->d_u[1 - par];
+        a.lam_next = p->d_lam[1 - par];
+        a.q = p->d_q;
+        a.w = p->d_w;
+        a.Wd = p->d_Wd;
+        a.nrm = p->d_nrm;
+        a.slot = p->d_slot;
+        a.cnt = p->d_cnt;
+        a.slot_stride = (int32_t)p->u_len;
+        a.eta = p->eta;
+        a.r = p->r;
+        a.gamma = p->gamma;
+        a.blind = p->blind;
+        a.re_part = p->d_re_part;
+    }
+}
+
+int launch_subdomain_update_table(bool blind, const SubArgs *tab, const int2 *items, int n_items, int parity,
+                                  cudaStream_t s)
+{
+    if (n_items <= 0) return PTYCHO_OK;
+    if (blind)
+        subdomain_update_kernel<true, true><<<n_items, GATHER_THREADS, 0, s>>>(SubArgs{}, tab, items, parity);
+    else
+        subdomain_update_kernel<false, true><<<n_items, GATHER_THREADS, 0, s>>>(SubArgs{}, tab, items, parity);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
 int launch_subdomain_update(ptycho_plan_s *p, cudaStream_t s)
 {
-    SubArgs a;
-    a.M = p->M;
-    a.rect = p->d_rect;
-    a.u_off = p->d_u_off;
-    a.tnbr_ptr = p->sub_tiles.nbr_ptr;
-    a.tnbr = p->sub_tiles.nbr;
-    a.tiles = p->sub_tiles.tiles;
-    a.tptr = p->sub_tiles.ptr;
-    a.tlist = p->sub_tiles.list;
-    a.u_cur = p->d_u[p->cur];
-    a.lam_cur = p->d_lam[p->cur];
-    a.u_next = p->d_u[1 - p->cur];
-    a.lam_next = p->d_lam[1 - p->cur];
-    a.q = p->d_q;
-    a.w = p->d_w;
-    a.Wd = p->d_Wd;
-    a.nrm = p->d_nrm;
-    a.slot = p->d_slot;
-    a.cnt = p->d_cnt;
-    a.slot_stride = (int32_t)p->u_len;
-    a.eta = p->eta;
-    a.r = p->r;
-    a.gamma = p->gamma;
-    a.blind = p->blind;
-    a.re_part = p->d_re_part;
+    const int n = p->sub_tiles.n_tiles;
+    if (n <= 0) return PTYCHO_OK;
     if (p->blind)
-        subdomain_update_kernel<true><<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(a);
+        subdomain_update_kernel<true, false><<<n, GATHER_THREADS, 0, s>>>(p->h_sargs[p->cur], nullptr, nullptr, p->cur);
     else
-        subdomain_update_kernel<false><<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(a);
+        subdomain_update_kernel<false, false><<<n, GATHER_THREADS, 0, s>>>(p->h_sargs[p->cur], nullptr, nullptr, p->cur);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
@@ -618,7 +634,7 @@ int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s)
 
 int launch_metrics(ptycho_plan_s *p, cudaStream_t s)
 {
-    metrics_kernel<<<1, 256, 0, s>>>(p->n_k1_blocks, p->d_rf_part, p->D, p->sub_tiles.reg_ptr,
+    metrics_kernel<<<1, 256, 0, s>>>(p->n_rf_parts, p->d_rf_part, p->D, p->sub_tiles.reg_ptr,
                                     p->d_re_part, p->d_metrics);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;

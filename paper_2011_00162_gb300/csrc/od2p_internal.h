@@ -79,6 +79,61 @@ struct ProbeGroups {
     int32_t *chunk_ptr = nullptr; // device, first chunk of each group (+ end)
 };
 
+// ST-AGM prox constants for lambda (eq. Prox_sol with the threshold read as
+// |y| < (eps - (1-eps)/lambda) sqrt f).
+struct ProxConst {
+    float lam, inv1plam, c_thr, c_k1;
+};
+
+inline ProxConst make_prox_const(float eps, float lam)
+{
+    ProxConst k;
+    k.lam = lam;
+    k.inv1plam = 1.f / (1.f + lam);
+    k.c_thr = eps - (1.f - eps) / lam;
+    k.c_k1 = k.c_thr > 0.f ? lam / (lam - (1.f - eps) / eps) : 0.f;
+    return k;
+}
+
+// Arguments of one plan's frame update (one copy per buffer parity), read by
+// the persistent frame-update kernel from a device table so that one launch
+// can serve several plans.
+struct FrameArgs {
+    int32_t J;
+    const int32_t *frame_sub, *frame_base, *frame_pitch;
+    const float2 *u, *w, *Wd; // Wd non-null for blind plans (per-subdomain probe)
+    float2 *gamma;            // transposed position layout
+    const float *sqrtf_;      // transposed position layout
+    float2 *q;                // out (blind): F^*(z - Gamma^{n+1}), natural spatial order
+    float2 *slot;             // out (nonblind): conj(w) o F^*(z - Gamma^{n+1}) in gather slots
+    const uint8_t *rank;      // nonblind: slot rank of each frame pixel
+    int32_t slot_stride;      // u_len
+    float *rf_part;           // out: one partial per frame group
+    int32_t *err;             // set to 1 if a pipeline wait gives up
+    const float2 *tw;
+    ProxConst pc;
+};
+
+// Arguments of one plan's subdomain update (one copy per buffer parity).
+struct SubArgs {
+    int32_t M;
+    const int32_t *rect;
+    const int64_t *u_off;
+    const Tile *tiles;
+    const int32_t *tptr, *tnbr_ptr;
+    const ListEntry *tlist;
+    const NbrInfo *tnbr;
+    const float2 *u_cur, *lam_cur, *q, *w, *Wd;
+    const float *nrm;
+    const float2 *slot;        // nonblind gather slots
+    const uint8_t *cnt;
+    int32_t slot_stride;
+    float2 *u_next, *lam_next;
+    float eta, r, gamma;
+    int32_t blind;
+    float *re_part;
+};
+
 }  // namespace od2p
 
 struct ptycho_plan_s {
@@ -128,6 +183,11 @@ struct ptycho_plan_s {
     double *d_metrics = nullptr;       // [rf, re, sum sqrt f]
     int32_t *d_err = nullptr;          // set by a kernel whose bounded wait gave up
     int32_t n_k1_blocks = 0;           // blocks of the persistent frame update
+    int32_t n_rf_parts = 0;            // RF partial sums (one per warp of each frame group / m = 256 slab)
+    od2p::FrameArgs h_fargs[2];        // frame-update arguments by buffer parity
+    od2p::SubArgs h_sargs[2];          // subdomain-update arguments by buffer parity
+    od2p::FrameArgs *d_fargs = nullptr;
+    od2p::SubArgs *d_sargs = nullptr;
     int32_t n_loss_blocks = 0;         // blocks of the loss kernel
     int32_t cur = 0;                   // which u / Lambda buffer holds the current iterate
     bool initialised = false;
@@ -154,6 +214,11 @@ int launch_permute_gamma(const ptycho_plan_s *p, const float2 *src, float2 *dst,
 bool supported_m(int m);
 int frames_per_block(int m);
 int frame_update_grid(int m, int J, int *grid);
+int frame_groups(int m, int J);
+int rf_parts(int m, int J);
+void fill_frame_args(const ptycho_plan_s *p, FrameArgs out[2]);
+int launch_frame_update_table(int m, const FrameArgs *tab, const int2 *items, int n_items, int grid, int parity,
+                              cudaStream_t s);
 int prepare_kernels(int m);
 
 // fft256_kernels.cu (m = 256)
@@ -167,6 +232,9 @@ int permute_256(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_
 
 // gather_kernels.cu
 int launch_subdomain_update(ptycho_plan_s *p, cudaStream_t s);
+void fill_sub_args(const ptycho_plan_s *p, SubArgs out[2]);
+int launch_subdomain_update_table(bool blind, const SubArgs *tab, const int2 *items, int n_items, int parity,
+                                  cudaStream_t s);
 int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w, float2 *out,
                         cudaStream_t s);
 int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, cudaStream_t s);

@@ -407,7 +407,9 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         p->has_mask = true;
         if ((rc = upload(&p->d_mask, mask, own, s))) return bail(rc);
     }
-    if ((rc = prepare_kernels(m)) || (rc = frame_update_grid(m, J, &p->n_k1_blocks))) return bail(rc);
+    p->n_rf_parts = rf_parts(m, J);
+    if ((rc = prepare_kernels(m)) || (rc = frame_update_grid(m, frame_groups(m, J), &p->n_k1_blocks)))
+        return bail(rc);
     p->n_loss_blocks = m == 256 ? J * 16 : (J + frames_per_block(m) - 1) / frames_per_block(m);
     const int n_chunks = std::max(p->sub_groups.n_chunks, p->img_groups.n_chunks);
     if ((rc = dev_alloc(&p->d_sqrtf, JMM, own)) || (rc = dev_alloc(&p->d_gamma, JMM, own)) ||
@@ -418,7 +420,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = dev_alloc(&p->d_wnew, p->MM, own)) ||
         (rc = dev_alloc(&p->d_probe_part, (size_t)n_chunks * p->MM, own)) ||
         (rc = dev_alloc(&p->d_probe_part_n, (size_t)n_chunks * p->MM, own)) ||
-        (rc = dev_alloc(&p->d_rf_part, p->n_k1_blocks, own)) ||
+        (rc = dev_alloc(&p->d_rf_part, p->n_rf_parts, own)) ||
         (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own)) ||
         (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own)) ||
         (rc = dev_alloc(&p->d_metrics, 3, own)) || (rc = dev_alloc(&p->d_err, 1, own)))
@@ -435,11 +437,19 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
     }
     cudaError_t e;
     if ((e = cudaMemsetAsync(p->d_metrics, 0, 3 * sizeof(double), s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * p->n_k1_blocks, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * p->n_rf_parts, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_re_part, 0, sizeof(float) * 2 * p->sub_tiles.n_tiles, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_w, 0, sizeof(float2) * p->MM, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), s)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMemsetAsync"));
+    // kernel argument tables (buffer pointers are fixed from here on)
+    fill_frame_args(p, p->h_fargs);
+    fill_sub_args(p, p->h_sargs);
+    {
+        std::vector<FrameArgs> fa(p->h_fargs, p->h_fargs + 2);
+        std::vector<SubArgs> sa(p->h_sargs, p->h_sargs + 2);
+        if ((rc = upload(&p->d_fargs, fa, own, s)) || (rc = upload(&p->d_sargs, sa, own, s))) return bail(rc);
+    }
     if ((rc = launch_ingest_f(p, f_dev, s)) || (rc = launch_sum_sqrtf(p, s))) return bail(rc);
     // Step 0 with u = 1 and a zero probe until od2p_init
     if ((rc = launch_init_state(p, nullptr, p->d_w, s))) return bail(rc);
@@ -663,6 +673,162 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u, const ptycho_c32 *
         if (int rc = launch_image_gather(plan, plan->d_q, ww, reinterpret_cast<float2 *>(grad_u), s)) return rc;
     if (grad_w)
         if (int rc = launch_probe_reduce(plan, uu, reinterpret_cast<float2 *>(grad_w), s)) return rc;
+    return PTYCHO_OK;
+}
+
+// ---------------------------------------------------------------- batches
+struct ptycho_batch_s {
+    std::vector<ptycho_plan_s *> plans;
+    struct Cls {
+        int m = 0, n_items = 0, grid = 0;
+        od2p::FrameArgs *tab = nullptr;
+        int2 *items = nullptr;
+    };
+    std::vector<Cls> cls;
+    od2p::SubArgs *stab = nullptr;
+    int2 *titems = nullptr;
+    int n_titems = 0;
+    std::vector<void *> owned;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int cur = 0;
+};
+
+int ptycho_batch_destroy(ptycho_batch_t *b)
+{
+    if (!b) return PTYCHO_OK;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 2; ++i)
+        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (void *ptr : b->owned) cudaFree(ptr);
+    for (ptycho_plan_s *p : b->plans) ptycho_plan_destroy(p);
+    delete b;
+    cudaGetLastError();
+    return PTYCHO_OK;
+}
+
+int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const float *const *f_devs, int32_t n,
+                      ptycho_stream_t stream)
+{
+    if (!out) return fail(PTYCHO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!geoms || !f_devs || n < 1) return fail(PTYCHO_ERR_INVALID_ARG, "need n >= 1 geometries and intensity stacks");
+    for (int i = 0; i < n; ++i) {
+        if (geoms[i].blind) return fail(PTYCHO_ERR_UNSUPPORTED, "batches hold nonblind reconstructions only");
+        if (geoms[i].m > 128) return fail(PTYCHO_ERR_UNSUPPORTED, "batches hold probe sides up to 128");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    auto *b = new (std::nothrow) ptycho_batch_s();
+    if (!b) return fail(PTYCHO_ERR_OOM, "host allocation failed");
+    auto bail = [&](int rc) {
+        std::string msg = od2p::g_err;
+        ptycho_batch_destroy(b);
+        od2p::g_err = msg;
+        return rc;
+    };
+    for (int i = 0; i < n; ++i) {
+        ptycho_plan_t *p = nullptr;
+        if (int rc = ptycho_plan(&p, &geoms[i], f_devs[i], stream)) return bail(rc);
+        b->plans.push_back(p);
+    }
+    // one table per probe side: the member plans' frame-update arguments and the
+    // (plan, frame group) work items
+    std::vector<int> ms;
+    for (auto *p : b->plans)
+        if (std::find(ms.begin(), ms.end(), p->M) == ms.end()) ms.push_back(p->M);
+    std::sort(ms.begin(), ms.end());
+    for (int m : ms) {
+        std::vector<FrameArgs> tab;
+        std::vector<int2> items;
+        for (auto *p : b->plans) {
+            if (p->M != m) continue;
+            const int local = (int)tab.size() / 2;
+            tab.push_back(p->h_fargs[0]);
+            tab.push_back(p->h_fargs[1]);
+            for (int g = 0; g < frame_groups(m, p->J); ++g) items.push_back(make_int2(local, g));
+        }
+        ptycho_batch_s::Cls c;
+        c.m = m;
+        c.n_items = (int)items.size();
+        int rc;
+        if ((rc = upload(&c.tab, tab, b->owned, s)) || (rc = upload(&c.items, items, b->owned, s)) ||
+            (rc = frame_update_grid(m, c.n_items, &c.grid)))
+            return bail(rc);
+        b->cls.push_back(c);
+    }
+    // every subdomain tile of every plan for the single subdomain-update launch
+    std::vector<SubArgs> stab;
+    std::vector<int2> titems;
+    for (int i = 0; i < n; ++i) {
+        stab.push_back(b->plans[i]->h_sargs[0]);
+        stab.push_back(b->plans[i]->h_sargs[1]);
+        for (int t = 0; t < b->plans[i]->sub_tiles.n_tiles; ++t) titems.push_back(make_int2(i, t));
+    }
+    b->n_titems = (int)titems.size();
+    int rc;
+    if ((rc = upload(&b->stab, stab, b->owned, s)) || (rc = upload(&b->titems, titems, b->owned, s))) return bail(rc);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamSynchronize"));
+    *out = b;
+    return PTYCHO_OK;
+}
+
+int ptycho_batch_size(const ptycho_batch_t *b, int32_t *n)
+{
+    if (!b || !n) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    *n = (int32_t)b->plans.size();
+    return PTYCHO_OK;
+}
+
+int ptycho_batch_member(const ptycho_batch_t *b, int32_t i, ptycho_plan_t **plan)
+{
+    if (!b || !plan || i < 0 || i >= (int32_t)b->plans.size())
+        return fail(PTYCHO_ERR_INVALID_ARG, "bad batch member index");
+    *plan = b->plans[i];
+    return PTYCHO_OK;
+}
+
+static int batch_enqueue(ptycho_batch_s *b, int parity, cudaStream_t s)
+{
+    for (const auto &c : b->cls)
+        if (int rc = launch_frame_update_table(c.m, c.tab, c.items, c.n_items, c.grid, parity, s)) return rc;
+    return launch_subdomain_update_table(false, b->stab, b->titems, b->n_titems, parity, s);
+}
+
+int ptycho_batch_iterate(ptycho_batch_t *b, int32_t n_iter, ptycho_stream_t stream)
+{
+    if (!b) return fail(PTYCHO_ERR_INVALID_ARG, "batch is NULL");
+    if (n_iter < 0) return fail(PTYCHO_ERR_INVALID_ARG, "n_iter < 0");
+    for (auto *p : b->plans) {
+        if (!p->initialised) return fail(PTYCHO_ERR_STATE, "od2p_init has not been called on every member");
+        if (p->cur != b->cur) return fail(PTYCHO_ERR_STATE, "a member was iterated on its own");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (int it = 0; it < n_iter; ++it) {
+        const int par = b->cur;
+        if (!b->graph[par]) {
+            if (!b->cap_stream) OD2P_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+            OD2P_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+            int rc = batch_enqueue(b, par, b->cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&b->graph[par], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                b->graph[par] = nullptr;
+                return cuda_fail(e, "cudaGraphInstantiate");
+            }
+        }
+        OD2P_CUDA(cudaGraphLaunch(b->graph[par], s));
+        b->cur ^= 1;
+        for (auto *p : b->plans) p->cur = b->cur;
+    }
     return PTYCHO_OK;
 }
 

@@ -189,6 +189,8 @@ def batched_problems(count: int = 64, seed: int = 3) -> list[Problem]:
         step = int(rng.integers(8, m // 2 + 1))
         n0 = int(rng.integers(256, 1025))
         k = max(2, (n0 - m) // step + 1)
+        while m + (k - 1) * step < 256:
+            k += 1
         n = m + (k - 1) * step
         g = int(rng.integers(2, min(8, k) + 1))
         peak = float(10 ** rng.uniform(3, 5))

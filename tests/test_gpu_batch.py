@@ -1,0 +1,78 @@
+"""Batched reconstructions: one persistent frame-update launch per probe side and
+one subdomain-update launch per iteration, against each member run alone."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2011_00162_gb300 as od
+from paper_2011_00162_gb300 import build as odbuild
+from paper_2011_00162_gb300 import synth
+
+from _cases import make_case, rel_l2
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    odbuild.build()
+
+
+def _members(count=6, seed=3, max_n=400):
+    probs = [p for p in synth.batched_problems(40, seed=seed) if p.n <= max_n][:count]
+    assert len({p.m for p in probs}) >= 2  # mixed probe sides in one batch
+    cases = [make_case(p, noise_seed=i) for i, p in enumerate(probs)]
+    geoms = [od.Geometry(p.n, p.n, p.m, c[0], p.sub_rows, p.sub_cols, p.overlap_px, 0.5, 2.0, 0.5)
+             for p, c in zip(probs, cases)]
+    return probs, cases, geoms
+
+
+def test_batch_equals_members_run_alone_bitwise():
+    probs, cases, geoms = _members()
+    fs = [torch.from_numpy(c[3]).to(DEV) for c in cases]
+    batch = od.ptycho_batch_plan(geoms, fs)
+    for m, c in zip(batch.members, cases):
+        od.od2p_init(m, torch.from_numpy(c[2]).to(DEV))
+    batch.iterate(3)
+    for i, (g, c) in enumerate(zip(geoms, cases)):
+        alone = od.ptycho_plan(g, fs[i])
+        od.od2p_init(alone, torch.from_numpy(c[2]).to(DEV))
+        od.od2p_iterate(alone, 3)
+        for k in (od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA):
+            assert torch.equal(od.od2p_get_state(batch.members[i], k), od.od2p_get_state(alone, k)), (i, k)
+        alone.close()
+    # a member iterated on its own is refused by the batch afterwards
+    od.od2p_iterate(batch.members[0], 1)
+    with pytest.raises(od.PtychoError):
+        batch.iterate(1)
+    batch.close()
+
+
+def test_batch_member_matches_oracle():
+    probs, cases, geoms = _members(count=3)
+    fs = [torch.from_numpy(c[3]).to(DEV) for c in cases]
+    batch = od.ptycho_batch_plan(geoms, fs)
+    for m, c in zip(batch.members, cases):
+        od.od2p_init(m, torch.from_numpy(c[2]).to(DEV))
+    batch.iterate(1)
+    for i, (p, c) in enumerate(zip(probs, cases)):
+        offs, u_true, w, f = c
+        ref = oracle.ADMM(f, w, offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, 0.5, 2.0, 0.5)
+        ref.iterate(1)
+        for k, ko in ((od.STATE_U, oracle.U), (od.STATE_GAMMA, oracle.GAMMA), (od.STATE_LAMBDA, oracle.LAMBDA)):
+            b = ref.get(ko)
+            if b.size:
+                assert rel_l2(od.od2p_get_state(batch.members[i], k).cpu().numpy(), b) < 1e-5
+    batch.close()
+
+
+def test_batch_rejects_blind_members():
+    p = synth.small_2sub()
+    offs, u_true, w, f = make_case(p)
+    g = od.Geometry(p.n, p.n, p.m, offs, 1, 2, 8, 0.5, 0.1, 0.05, mu=1.0, blind=True)
+    with pytest.raises(od.PtychoError):
+        od.ptycho_batch_plan([g], [torch.from_numpy(f).to(DEV)])

@@ -373,3 +373,30 @@ def test_nonblind_residual_frames_from_gather_slots():
     for j in np.random.default_rng(1).choice(len(offs), 20, replace=False):
         q_ref = np.conj(w) * oracle.fft2(z[j] - gam[j], True)
         assert rel_l2(q[j], q_ref) < ONE_ITER_TOL
+
+
+def test_blind_workload_1024_full_size():
+    """1024^2 image, 841 frames of 128^2, 4x4 subdomains, Gaussian initial probe,
+    Poisson 1e4: one blind iteration (Algorithm 3) from a scrambled state, every
+    state array compared; then the ST-AGM loss and both gradients at full size."""
+    p = synth.blind_4x4()
+    offs, u_true, w_true, f = make_case(p)
+    assert len(offs) == 841
+    w0 = synth.gaussian_probe(p.m)
+    eta, r, mu, gamma = 2.0, 0.5, 1.0, 0.1
+    g = od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, eps=0.5, eta=eta, r=r, mu=mu,
+                    gamma=gamma, blind=True)
+    plan = od.ptycho_plan(g, f32(f))
+    od.od2p_init(plan, c64(w0))
+    ref = oracle.ADMM(f, w0, offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, 0.5, eta, r, blind=True,
+                      mu=mu, gamma=gamma)
+    _scramble(plan, ref, 12, blind=True)
+    od.od2p_iterate(plan, 1)
+    ref.iterate(1)
+    _compare_state(plan, ref, ONE_ITER_TOL, blind=True)
+    rng = np.random.default_rng(3)
+    u = (u_true * (1 + 0.1 * rng.standard_normal(u_true.shape))).astype(np.complex64)
+    loss, gu, gw = od.stagm_loss_grad(plan, c64(u), c64(w0))
+    L, gu_o, gw_o = oracle.loss_grad(u, w0, offs, f.astype(np.float64), 0.5)
+    assert abs(float(loss.item()) - L) < 1e-5 * abs(L)
+    assert rel_l2(host(gu), gu_o) < 1e-5 and rel_l2(host(gw), gw_o) < 1e-5

@@ -174,8 +174,9 @@ def make_inputs(p, dev):
     return offs, u_true, w, f
 
 
-def e2e_run(od, geom, f, w, offs, p, dev, K, ws):
+def e2e_run(od, geom, f, w, offs, p, dev, K, ws, tune=True):
     import torch
+    from paper_2011_00162_gb300 import autotune
     f_pin = torch.from_numpy(f).pin_memory()
     w_pin = torch.from_numpy(w).pin_memory()
     e2e_times = []
@@ -188,6 +189,8 @@ def e2e_run(od, geom, f, w, offs, p, dev, K, ws):
         wd = w_pin.to(dev, non_blocking=True)
         pl = od.ptycho_plan(geom, fd)
         od.od2p_init(pl, wd)
+        if tune:
+            autotune.tune_plan(pl)  # measured in the untimed first pass, a cache hit afterwards
         od.od2p_iterate(pl, p.n_iter)
         u = od.od2p_merge(pl)
         out_host.copy_(u, non_blocking=True)
@@ -203,7 +206,7 @@ def e2e_run(od, geom, f, w, offs, p, dev, K, ws):
             "step": f"one reconstruction: H2D f, plan, init, {p.n_iter} iterations, merge, D2H image"}
 
 
-def batched_leg(od, dev, K: int = 10, W: int = 2, count: int = 64):
+def batched_leg(od, dev, K: int = 10, W: int = 2, count: int = 64, tune=True, retune=False):
     """Config-3 workload: `count` independent nonblind reconstructions of mixed
     sizes.  The batch (one frame-update launch per probe side + one subdomain
     update per iteration, graph-replayed) against the same plans iterated one
@@ -234,6 +237,11 @@ def batched_leg(od, dev, K: int = 10, W: int = 2, count: int = 64):
     plains = [od.ptycho_plan(g, f) for g, f in zip(geoms, fs)]
     for pl, w in zip(plains, ws):
         od.od2p_init(pl, w)
+    if tune:
+        from paper_2011_00162_gb300 import autotune
+        autotune.tune_batch(batch, use_cache=not retune)
+        for pl in plains:
+            autotune.tune_plan(pl, use_cache=not retune)
     batch.iterate(W)
     for pl in plains:
         od.od2p_iterate(pl, W)
@@ -251,6 +259,7 @@ def batched_leg(od, dev, K: int = 10, W: int = 2, count: int = 64):
     tb, tp = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
     same = all(torch.equal(od.od2p_get_state(batch.members[i], od.STATE_U), od.od2p_get_state(plains[i], od.STATE_U))
                for i in range(len(plains)))
+    blaunch = od.ptycho_batch_get_launch(batch)
     for pl in plains:
         pl.close()
     batch.close()
@@ -261,7 +270,8 @@ def batched_leg(od, dev, K: int = 10, W: int = 2, count: int = 64):
             "plain_frame_updates_per_s": round(J * K / tp, 1),
             "speedup": round(tp / tb, 3),
             "equal_error": "bitwise identical states after the same iterations" if same else "states differ",
-            "launches_per_iteration": {"batched": len({g.m for g in geoms}) + 1, "plain": 2 * len(geoms)}}
+            "launches_per_iteration": {"batched": len({g.m for g in geoms}) + 1, "plain": 2 * len(geoms)},
+            "batch_launch": {"variant": blaunch[0], "blocks_per_sm": blaunch[1]}}
 
 
 def run_gpu(args):
@@ -269,6 +279,7 @@ def run_gpu(args):
     import torch.distributed as dist
 
     import paper_2011_00162_gb300 as od
+    from paper_2011_00162_gb300 import autotune
     from paper_2011_00162_gb300 import build as odbuild
 
     ws, rank, local = _dist_env()
@@ -288,6 +299,10 @@ def run_gpu(args):
     w_dev = torch.from_numpy(w).to(dev)
     plan = od.ptycho_plan(geom, f_dev)
     od.od2p_init(plan, w_dev)
+    # launch shape of the frame update: measured once per workload and cached on
+    # disk (tuning restores the plan's state; every shape gives identical iterates)
+    tuned = autotune.tune_plan(plan, flush_l2=True, use_cache=not args.retune) if not args.no_tune else None
+    launch = od.ptycho_plan_get_launch(plan)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -335,7 +350,7 @@ def run_gpu(args):
     # ---- end to end through the public API with host buffers (per reconstruction)
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_run(od, geom, f, w, offs, p, dev, K, ws)
+        e2e = e2e_run(od, geom, f, w, offs, p, dev, K, ws, tune=not args.no_tune)
 
     peak, peak_kind = _peaks()
     alg_bytes = 20.0 * p.m * p.m * J  # f 4 B + Gamma read 8 B + write 8 B per frame pixel
@@ -356,10 +371,13 @@ def run_gpu(args):
                    "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu",
                    "frame_update_ms": round(statistics.mean(k1_ms), 5),
                    "subdomain_update_ms": round(statistics.mean(k2_ms), 5),
-                   "rf_after": rf, "re_after": re},
+                   "rf_after": rf, "re_after": re,
+                   "launch": {"variant": launch[0], "blocks_per_sm": launch[1], "max_blocks_per_sm": launch[2],
+                              "tuned": None if tuned is None else
+                              {"cached": tuned["cached"], "trials_us": tuned.get("trials")}}},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "frame_update_kernel<64>", "peak_kind": peak_kind,
+                     "kernel": f"frame_update_kernel<64, variant {launch[0]}>", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes},
             "e2e": e2e,
         "gpu_launches": 2 * K,
@@ -367,7 +385,7 @@ def run_gpu(args):
         "wall_s_timed_region": round(wall1 - wall0, 4),
     }
     if not args.no_batched:
-        line["batched"] = batched_leg(od, dev)
+        line["batched"] = batched_leg(od, dev, tune=not args.no_tune, retune=args.retune)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_budget)
     if rank == 0:
@@ -446,6 +464,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain leg")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
+    ap.add_argument("--retune", action="store_true", help="measure launch shapes even when cached")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

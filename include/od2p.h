@@ -214,6 +214,29 @@ int od2p_merge(const ptycho_plan_t *plan, ptycho_c32 *u_out_dev, ptycho_stream_t
  */
 int od2p_metrics(ptycho_plan_t *plan, float *rf_host, float *re_host, ptycho_stream_t stream);
 
+/*
+ * Launch shape of the frame update (the paper fixes none: its GPU section
+ * assigns frames to thread blocks without fixing how many).  For m <= 128 two
+ * shapes are compiled, each a (frames per block, threads per block) pair:
+ *   m = 16: variant 0 (8, 256), variant 1 (4, 128);  m = 32: (4, 256), (2, 128);
+ *   m = 64: (1, 512), (1, 256);  m = 128: (1, 1024), (1, 512).
+ * The persistent kernel runs min(frame groups, b x SMs) blocks, b =
+ * blocks_per_sm capped at what fits (0: as many as fit).  Every shape gives
+ * the same iterates bit for bit; only the RF partial sums are grouped
+ * differently.  m = 256 has one shape (variant 0; blocks_per_sm ignored).
+ * ptycho_plan_set_launch drops the plan's captured iteration graphs (they are
+ * recaptured on the next od2p_iterate); when the shape changes, RF reads 0
+ * until the next frame update.  A batch member returns PTYCHO_ERR_STATE: use
+ * ptycho_batch_set_launch.  ptycho_plan_get_launch reports the current shape
+ * and the most blocks of it that fit on one SM (any output may be NULL).
+ * Errors: INVALID_ARG (variant outside [0, PTYCHO_LAUNCH_VARIANTS) or
+ * blocks_per_sm < 0), UNSUPPORTED (variant 1 for m = 256), STATE, CUDA.
+ */
+#define PTYCHO_LAUNCH_VARIANTS 2
+int ptycho_plan_set_launch(ptycho_plan_t *plan, int32_t variant, int32_t blocks_per_sm, ptycho_stream_t stream);
+int ptycho_plan_get_launch(const ptycho_plan_t *plan, int32_t *variant, int32_t *blocks_per_sm,
+                           int32_t *max_blocks_per_sm);
+
 /* Element count (complex) of a state selector (PTYCHO_STATE_*). */
 int od2p_state_len(const ptycho_plan_t *plan, int32_t which, int64_t *n_out);
 
@@ -265,6 +288,10 @@ int ptycho_batch_destroy(ptycho_batch_t *batch);
 int ptycho_batch_size(const ptycho_batch_t *batch, int32_t *n_out);
 int ptycho_batch_member(const ptycho_batch_t *batch, int32_t i, ptycho_plan_t **plan_out);
 int ptycho_batch_iterate(ptycho_batch_t *batch, int32_t n_iter, ptycho_stream_t stream);
+/* Launch shape of the batch's frame updates and of every member's own, as for
+ * ptycho_plan_set_launch (one variant and cap for every probe side).         */
+int ptycho_batch_set_launch(ptycho_batch_t *batch, int32_t variant, int32_t blocks_per_sm, ptycho_stream_t stream);
+int ptycho_batch_get_launch(const ptycho_batch_t *batch, int32_t *variant, int32_t *blocks_per_sm);
 
 /*
  * Allocation-free ST-AGM loss.  The paper has no counterpart: this entry point

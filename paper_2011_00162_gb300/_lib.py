@@ -18,6 +18,7 @@ _lib = None
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(7)
 STATE_U, STATE_GAMMA, STATE_LAMBDA, STATE_WD, STATE_DELTA, STATE_W, STATE_Q = range(7)
 OA_IFFT = 1
+LAUNCH_VARIANTS = 2
 
 # Every symbol declared in include/od2p.h: (restype, argtypes)
 _P = ctypes.c_void_p
@@ -63,6 +64,10 @@ SIGNATURES = {
     "ptycho_batch_size": (ctypes.c_int, [_P, _P]),
     "ptycho_batch_member": (ctypes.c_int, [_P, _I32, _P]),
     "ptycho_batch_iterate": (ctypes.c_int, [_P, _I32, _P]),
+    "ptycho_plan_set_launch": (ctypes.c_int, [_P, _I32, _I32, _P]),
+    "ptycho_plan_get_launch": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ptycho_batch_set_launch": (ctypes.c_int, [_P, _I32, _I32, _P]),
+    "ptycho_batch_get_launch": (ctypes.c_int, [_P, _P, _P]),
 }
 
 

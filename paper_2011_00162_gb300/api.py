@@ -22,8 +22,11 @@ __all__ = [
     "od2p_iterate", "od2p_frame_update", "od2p_subdomain_update", "probe_update", "od2p_merge",
     "od2p_metrics", "od2p_get_state", "od2p_set_state", "stagm_loss_grad", "PtychoError",
     "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
-    "Batch", "ptycho_batch_plan", "ptycho_batch_iterate",
+    "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
+    "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS",
 ]
+
+LAUNCH_VARIANTS = _lib.LAUNCH_VARIANTS
 
 
 def _stream(stream=None) -> ctypes.c_void_p:
@@ -203,6 +206,27 @@ def ptycho_batch_plan(geoms: list, fs: list, stream=None) -> Batch:
 
 def ptycho_batch_iterate(batch: Batch, n_iter: int = 1, stream=None) -> None:
     batch.iterate(n_iter, stream)
+
+
+def ptycho_plan_set_launch(plan: Plan, variant: int, blocks_per_sm: int = 0, stream=None) -> None:
+    check(plan._lib.ptycho_plan_set_launch(plan.handle, int(variant), int(blocks_per_sm), _stream(stream)))
+
+
+def ptycho_plan_get_launch(plan: Plan) -> tuple[int, int, int]:
+    """(variant, blocks_per_sm cap (0: none), most blocks of this variant that fit per SM)."""
+    v, b, mx = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(plan._lib.ptycho_plan_get_launch(plan.handle, ctypes.byref(v), ctypes.byref(b), ctypes.byref(mx)))
+    return v.value, b.value, mx.value
+
+
+def ptycho_batch_set_launch(batch: Batch, variant: int, blocks_per_sm: int = 0, stream=None) -> None:
+    check(batch._lib.ptycho_batch_set_launch(batch._h, int(variant), int(blocks_per_sm), _stream(stream)))
+
+
+def ptycho_batch_get_launch(batch: Batch) -> tuple[int, int]:
+    v, b = ctypes.c_int32(), ctypes.c_int32()
+    check(batch._lib.ptycho_batch_get_launch(batch._h, ctypes.byref(v), ctypes.byref(b)))
+    return v.value, b.value
 
 
 def _c64(shape, device):

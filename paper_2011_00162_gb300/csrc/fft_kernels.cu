@@ -242,19 +242,24 @@ __device__ __forceinline__ void col_stage1_store_slots(float2 *buf, const float2
 // Launch shape of the persistent frame update: frames per group, threads, and
 // whether Gamma is staged in shared memory (m = 128 only stages sqrt f: the
 // frame buffer already takes 132 KB).
-template <int M> struct K1Cfg;
-// MINB: resident blocks per SM the register budget is sized for (shared memory
-// allows at least as many).
-template <> struct K1Cfg<16> { static constexpr int FPB = 8, NT = 256, STAGE_G = 1, MINB = 4; };
-template <> struct K1Cfg<32> { static constexpr int FPB = 4, NT = 256, STAGE_G = 1, MINB = 2; };
-template <> struct K1Cfg<64> { static constexpr int FPB = 1, NT = 512, STAGE_G = 1, MINB = 2; };
-template <> struct K1Cfg<128> { static constexpr int FPB = 1, NT = 1024, STAGE_G = 0, MINB = 1; };
+// Two compiled shapes per probe side (variant 0 / 1), chosen per plan by the
+// autotuner.  MINB: resident blocks per SM the register budget is sized for
+// (shared memory allows at least as many).
+template <int M, int V> struct K1Cfg;
+template <> struct K1Cfg<16, 0> { static constexpr int FPB = 8, NT = 256, STAGE_G = 1, MINB = 4; };
+template <> struct K1Cfg<16, 1> { static constexpr int FPB = 4, NT = 128, STAGE_G = 1, MINB = 8; };
+template <> struct K1Cfg<32, 0> { static constexpr int FPB = 4, NT = 256, STAGE_G = 1, MINB = 2; };
+template <> struct K1Cfg<32, 1> { static constexpr int FPB = 2, NT = 128, STAGE_G = 1, MINB = 4; };
+template <> struct K1Cfg<64, 0> { static constexpr int FPB = 1, NT = 512, STAGE_G = 1, MINB = 2; };
+template <> struct K1Cfg<64, 1> { static constexpr int FPB = 1, NT = 256, STAGE_G = 1, MINB = 2; };
+template <> struct K1Cfg<128, 0> { static constexpr int FPB = 1, NT = 1024, STAGE_G = 0, MINB = 1; };
+template <> struct K1Cfg<128, 1> { static constexpr int FPB = 1, NT = 512, STAGE_G = 0, MINB = 1; };
 
-template <int M> constexpr size_t k1_smem_bytes()
+template <int M, int V> constexpr size_t k1_smem_bytes()
 {
-    constexpr size_t FPB = K1Cfg<M>::FPB, MM = (size_t)M * M;
-    return 128 + (K1Cfg<M>::STAGE_G ? sizeof(float2) * FPB * MM : 0) + sizeof(float) * FPB * MM +
-           sizeof(float2) * (M + FPB * M * (M + 1)) + sizeof(float) * (K1Cfg<M>::NT / 32);
+    constexpr size_t FPB = K1Cfg<M, V>::FPB, MM = (size_t)M * M;
+    return 128 + (K1Cfg<M, V>::STAGE_G ? sizeof(float2) * FPB * MM : 0) + sizeof(float) * FPB * MM +
+           sizeof(float2) * (M + FPB * M * (M + 1)) + sizeof(float) * (K1Cfg<M, V>::NT / 32);
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -314,14 +319,14 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
 // slices into shared memory (issued when the previous group's prox finished
 // with the staging buffers), and the next group's exit-wave windows are
 // prefetched into L2.  Each group's RF partial goes to rf_part[group].
-template <int M, bool BATCHED>
-__global__ void __launch_bounds__(K1Cfg<M>::NT, K1Cfg<M>::MINB)
+template <int M, int V, bool BATCHED>
+__global__ void __launch_bounds__(K1Cfg<M, V>::NT, K1Cfg<M, V>::MINB)
     frame_update_kernel(const FrameArgs single, const FrameArgs *__restrict__ tab, const int2 *__restrict__ items,
                         int n_items, int parity)
 {
-    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = K1Cfg<M>::FPB, NT = K1Cfg<M>::NT;
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, FPB = K1Cfg<M, V>::FPB, NT = K1Cfg<M, V>::NT;
     constexpr int P = M + 1, MM = M * M;
-    constexpr bool SG = K1Cfg<M>::STAGE_G != 0;
+    constexpr bool SG = K1Cfg<M, V>::STAGE_G != 0;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ FrameArgs sa_batch;  // batches: arguments of the current item's plan
     const FrameArgs &sa = BATCHED ? sa_batch : single;
@@ -716,43 +721,66 @@ int set_smem(K kernel)
     return PTYCHO_OK;
 }
 
-template <int M>
-int k1_grid_m(int n_items, int *grid)
-{
-    static int per_sm = 0, n_sm = 0;
-    if (!per_sm) {
-        OD2P_CUDA(cudaFuncSetAttribute(frame_update_kernel<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)k1_smem_bytes<M>()));
-        OD2P_CUDA(cudaFuncSetAttribute(frame_update_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)k1_smem_bytes<M>()));
-        int dev = 0, a = 0, b = 0;
-        OD2P_CUDA(cudaGetDevice(&dev));
-        OD2P_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, frame_update_kernel<M, false>, K1Cfg<M>::NT,
-                                                                k1_smem_bytes<M>()));
-        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, frame_update_kernel<M, true>, K1Cfg<M>::NT,
-                                                                k1_smem_bytes<M>()));
-        per_sm = std::min(a, b);
-        if (per_sm < 1) return fail(PTYCHO_ERR_UNSUPPORTED, "frame update does not fit on an SM");
+// Runs the statement list with M_ (probe side) and V_ (launch shape) bound as
+// compile-time constants for the shapes the frame update is compiled in.
+#define OD2P_K1_SHAPE(m, v, ...)                                                   \
+    switch ((m) * 2 + (v)) {                                                        \
+    case 32: { constexpr int M_ = 16, V_ = 0; __VA_ARGS__; }                        \
+    case 33: { constexpr int M_ = 16, V_ = 1; __VA_ARGS__; }                        \
+    case 64: { constexpr int M_ = 32, V_ = 0; __VA_ARGS__; }                        \
+    case 65: { constexpr int M_ = 32, V_ = 1; __VA_ARGS__; }                        \
+    case 128: { constexpr int M_ = 64, V_ = 0; __VA_ARGS__; }                       \
+    case 129: { constexpr int M_ = 64, V_ = 1; __VA_ARGS__; }                       \
+    case 256: { constexpr int M_ = 128, V_ = 0; __VA_ARGS__; }                      \
+    case 257: { constexpr int M_ = 128, V_ = 1; __VA_ARGS__; }                      \
+    default: break;                                                                 \
     }
-    *grid = std::max(1, std::min(n_items, per_sm * n_sm));
+
+// Largest resident block count per SM of the frame update (both the single-plan
+// and the batched instantiation), after raising its shared-memory limit.
+template <int M, int V>
+int k1_per_sm(int *per_sm_out, int *n_sm_out)
+{
+    constexpr int MAX_DEV = 64;  // cached per device: the shared-memory attribute is per context
+    static int per_sm[MAX_DEV] = {}, n_sm[MAX_DEV] = {};
+    int dev = 0;
+    OD2P_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEV) return fail(PTYCHO_ERR_UNSUPPORTED, "device ordinal above 63");
+    if (!per_sm[dev]) {
+        OD2P_CUDA(cudaFuncSetAttribute(frame_update_kernel<M, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)k1_smem_bytes<M, V>()));
+        OD2P_CUDA(cudaFuncSetAttribute(frame_update_kernel<M, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)k1_smem_bytes<M, V>()));
+        int a = 0, b = 0, n = 0;
+        OD2P_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, frame_update_kernel<M, V, false>,
+                                                                K1Cfg<M, V>::NT, k1_smem_bytes<M, V>()));
+        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, frame_update_kernel<M, V, true>,
+                                                                K1Cfg<M, V>::NT, k1_smem_bytes<M, V>()));
+        if (std::min(a, b) < 1) return fail(PTYCHO_ERR_UNSUPPORTED, "frame update does not fit on an SM");
+        n_sm[dev] = n;
+        per_sm[dev] = std::min(a, b);
+    }
+    *per_sm_out = per_sm[dev];
+    *n_sm_out = n_sm[dev];
     return PTYCHO_OK;
 }
 
-template <int M>
+template <int M, int V>
 int frame_update_table_m(const FrameArgs *tab, const int2 *items, int n_items, int grid, int parity, cudaStream_t s)
 {
-    frame_update_kernel<M, true><<<grid, K1Cfg<M>::NT, k1_smem_bytes<M>(), s>>>(FrameArgs{}, tab, items, n_items,
-                                                                                parity);
+    frame_update_kernel<M, V, true><<<grid, K1Cfg<M, V>::NT, k1_smem_bytes<M, V>(), s>>>(FrameArgs{}, tab, items,
+                                                                                         n_items, parity);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
 
-template <int M>
+template <int M, int V>
 int frame_update_single_m(const ptycho_plan_s *p, cudaStream_t s)
 {
-    frame_update_kernel<M, false><<<p->n_k1_blocks, K1Cfg<M>::NT, k1_smem_bytes<M>(), s>>>(
-        p->h_fargs[p->cur], nullptr, nullptr, frame_groups(M, p->J), p->cur);
+    const int groups = (p->J + K1Cfg<M, V>::FPB - 1) / K1Cfg<M, V>::FPB;
+    frame_update_kernel<M, V, false><<<p->n_k1_blocks, K1Cfg<M, V>::NT, k1_smem_bytes<M, V>(), s>>>(
+        p->h_fargs[p->cur], nullptr, nullptr, groups, p->cur);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
@@ -842,26 +870,32 @@ int frames_per_block(int m)
     }
 }
 
-// Number of blocks of the persistent frame update for J frames of side m.
-// Blocks of the persistent frame update for n_items frame groups of side m.
-int frame_update_grid(int m, int n_items, int *grid)
+// Blocks of the persistent frame update for n_items frame groups of side m,
+// launch shape `variant`, at most blocks_per_sm (0: as many as fit) per SM;
+// max_per_sm (optional) receives the most that fit.
+int frame_update_grid(int m, int variant, int n_items, int blocks_per_sm, int *grid, int *max_per_sm)
 {
-    switch (m) {
-    case 16: return k1_grid_m<16>(n_items, grid);
-    case 32: return k1_grid_m<32>(n_items, grid);
-    case 64: return k1_grid_m<64>(n_items, grid);
-    case 128: return k1_grid_m<128>(n_items, grid);
-    case 256: *grid = n_items; return PTYCHO_OK;
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
+    if (m == 256) {
+        *grid = n_items;
+        if (max_per_sm) *max_per_sm = 1;
+        return PTYCHO_OK;
     }
+    int per_sm = 0, n_sm = 0, rc = PTYCHO_ERR_UNSUPPORTED;
+    OD2P_K1_SHAPE(m, variant, rc = k1_per_sm<M_, V_>(&per_sm, &n_sm); break)
+    if (rc) return rc == PTYCHO_ERR_UNSUPPORTED ? fail(rc, "probe side m must be 16, 32, 64, 128 or 256") : rc;
+    if (max_per_sm) *max_per_sm = per_sm;
+    const int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, per_sm) : per_sm;
+    *grid = std::max(1, std::min(n_items, bps * n_sm));
+    return PTYCHO_OK;
 }
 
 namespace {
 template <int M>
 int prepare_m()
 {
-    int grid = 0;
-    if (int rc = k1_grid_m<M>(1, &grid)) return rc;
+    int per_sm = 0, n_sm = 0;
+    if (int rc = k1_per_sm<M, 0>(&per_sm, &n_sm)) return rc;
+    if (int rc = k1_per_sm<M, 1>(&per_sm, &n_sm)) return rc;
     if (int rc = set_smem<M>(forward_kernel<M>)) return rc;
     if (int rc = set_smem<M>(ifft_weight_kernel<M>)) return rc;
     if (int rc = set_smem<M>(loss_kernel<M>)) return rc;
@@ -883,28 +917,19 @@ int prepare_kernels(int m)
     }
 }
 
-int frame_groups(int m, int J)
+// Frame groups of the frame update (m <= 128) or 16-column slabs (m = 256).
+int frame_groups(int m, int J, int variant)
 {
-    switch (m) {
-    case 16: return (J + K1Cfg<16>::FPB - 1) / K1Cfg<16>::FPB;
-    case 32: return (J + K1Cfg<32>::FPB - 1) / K1Cfg<32>::FPB;
-    case 64: return (J + K1Cfg<64>::FPB - 1) / K1Cfg<64>::FPB;
-    case 128: return (J + K1Cfg<128>::FPB - 1) / K1Cfg<128>::FPB;
-    default: return J * 16;  // m = 256: 16-column slabs
-    }
+    OD2P_K1_SHAPE(m, variant, return (J + K1Cfg<M_, V_>::FPB - 1) / K1Cfg<M_, V_>::FPB)
+    return J * 16;
 }
 
 // RF partial sums written per iteration: one per warp of each frame group
 // (m <= 128), one per 16-column slab (m = 256).
-int rf_parts(int m, int J)
+int rf_parts(int m, int J, int variant)
 {
-    switch (m) {
-    case 16: return frame_groups(m, J) * (K1Cfg<16>::NT / 32);
-    case 32: return frame_groups(m, J) * (K1Cfg<32>::NT / 32);
-    case 64: return frame_groups(m, J) * (K1Cfg<64>::NT / 32);
-    case 128: return frame_groups(m, J) * (K1Cfg<128>::NT / 32);
-    default: return J * 16;
-    }
+    OD2P_K1_SHAPE(m, variant, return frame_groups(m, J, variant) * (K1Cfg<M_, V_>::NT / 32))
+    return J * 16;
 }
 
 void fill_frame_args(const ptycho_plan_s *p, FrameArgs out[2])
@@ -932,26 +957,18 @@ void fill_frame_args(const ptycho_plan_s *p, FrameArgs out[2])
     }
 }
 
-int launch_frame_update_table(int m, const FrameArgs *tab, const int2 *items, int n_items, int grid, int parity,
-                              cudaStream_t s)
+int launch_frame_update_table(int m, int variant, const FrameArgs *tab, const int2 *items, int n_items, int grid,
+                              int parity, cudaStream_t s)
 {
-    switch (m) {
-    case 16: return frame_update_table_m<16>(tab, items, n_items, grid, parity, s);
-    case 32: return frame_update_table_m<32>(tab, items, n_items, grid, parity, s);
-    case 64: return frame_update_table_m<64>(tab, items, n_items, grid, parity, s);
-    case 128: return frame_update_table_m<128>(tab, items, n_items, grid, parity, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "table-driven frame update: m must be 16, 32, 64 or 128");
-    }
+    OD2P_K1_SHAPE(m, variant, return frame_update_table_m<M_, V_>(tab, items, n_items, grid, parity, s))
+    return fail(PTYCHO_ERR_UNSUPPORTED, "table-driven frame update: m must be 16, 32, 64 or 128");
 }
 
 int launch_frame_update(ptycho_plan_s *p, cudaStream_t s)
 {
+    if (p->M == 256) return frame_update_256(p, s);
+    OD2P_K1_SHAPE(p->M, p->k1_variant, return frame_update_single_m<M_, V_>(p, s))
     switch (p->M) {
-    case 16: return frame_update_single_m<16>(p, s);
-    case 32: return frame_update_single_m<32>(p, s);
-    case 64: return frame_update_single_m<64>(p, s);
-    case 128: return frame_update_single_m<128>(p, s);
-    case 256: return frame_update_256(p, s);
     default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
     }
 }

@@ -183,6 +183,9 @@ struct ptycho_plan_s {
     double *d_metrics = nullptr;       // [rf, re, sum sqrt f]
     int32_t *d_err = nullptr;          // set by a kernel whose bounded wait gave up
     int32_t n_k1_blocks = 0;           // blocks of the persistent frame update
+    int32_t k1_variant = 0;            // launch shape of the frame update (0 or 1)
+    int32_t k1_blocks_per_sm = 0;      // resident-block cap of the frame update (0: as many as fit)
+    bool batch_member = false;         // owned by a batch, which sets its launch shape
     int32_t n_rf_parts = 0;            // RF partial sums (one per warp of each frame group / m = 256 slab)
     od2p::FrameArgs h_fargs[2];        // frame-update arguments by buffer parity
     od2p::SubArgs h_sargs[2];          // subdomain-update arguments by buffer parity
@@ -213,11 +216,11 @@ int launch_permute_gamma(const ptycho_plan_s *p, const float2 *src, float2 *dst,
                          cudaStream_t s);
 bool supported_m(int m);
 int frames_per_block(int m);
-int frame_update_grid(int m, int J, int *grid);
-int frame_groups(int m, int J);
-int rf_parts(int m, int J);
+int frame_update_grid(int m, int variant, int n_items, int blocks_per_sm, int *grid, int *max_per_sm);
+int frame_groups(int m, int J, int variant);
+int rf_parts(int m, int J, int variant);
 void fill_frame_args(const ptycho_plan_s *p, FrameArgs out[2]);
-int launch_frame_update_table(int m, const FrameArgs *tab, const int2 *items, int n_items, int grid, int parity,
+int launch_frame_update_table(int m, int variant, const FrameArgs *tab, const int2 *items, int n_items, int grid, int parity,
                               cudaStream_t s);
 int prepare_kernels(int m);
 

@@ -214,6 +214,41 @@ int capture_graph(ptycho_plan_s *p, int parity)
     return PTYCHO_OK;
 }
 
+void drop_graphs(cudaGraphExec_t g[2])
+{
+    for (int i = 0; i < 2; ++i)
+        if (g[i]) {
+            cudaGraphExecDestroy(g[i]);
+            g[i] = nullptr;
+        }
+}
+
+// Switch the frame update of p to launch shape `variant` with at most
+// blocks_per_sm resident blocks per SM; drops the captured iteration graphs and
+// zeroes the RF partials when the partial-sum layout changes.
+int apply_launch(ptycho_plan_s *p, int variant, int blocks_per_sm, cudaStream_t s)
+{
+    if (p->M == 256) {
+        if (variant != 0) return fail(PTYCHO_ERR_UNSUPPORTED, "m = 256 has one launch shape (variant 0)");
+        p->k1_blocks_per_sm = 0;
+        return PTYCHO_OK;
+    }
+    int grid = 0;
+    if (int rc = frame_update_grid(p->M, variant, frame_groups(p->M, p->J, variant), blocks_per_sm, &grid, nullptr))
+        return rc;
+    const int parts = rf_parts(p->M, p->J, variant);
+    if (parts != p->n_rf_parts || variant != p->k1_variant) {
+        const int cap = std::max(rf_parts(p->M, p->J, 0), rf_parts(p->M, p->J, 1));
+        OD2P_CUDA(cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * cap, s));
+    }
+    p->k1_variant = variant;
+    p->k1_blocks_per_sm = blocks_per_sm;
+    p->n_k1_blocks = grid;
+    p->n_rf_parts = parts;
+    drop_graphs(p->graph);
+    return PTYCHO_OK;
+}
+
 }  // namespace
 }  // namespace od2p
 
@@ -407,8 +442,11 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         p->has_mask = true;
         if ((rc = upload(&p->d_mask, mask, own, s))) return bail(rc);
     }
-    p->n_rf_parts = rf_parts(m, J);
-    if ((rc = prepare_kernels(m)) || (rc = frame_update_grid(m, frame_groups(m, J), &p->n_k1_blocks)))
+    p->n_rf_parts = rf_parts(m, J, 0);
+    // RF partials sized for either launch shape of the frame update
+    const int rf_cap = std::max(rf_parts(m, J, 0), rf_parts(m, J, 1));
+    if ((rc = prepare_kernels(m)) ||
+        (rc = frame_update_grid(m, 0, frame_groups(m, J, 0), 0, &p->n_k1_blocks, nullptr)))
         return bail(rc);
     p->n_loss_blocks = m == 256 ? J * 16 : (J + frames_per_block(m) - 1) / frames_per_block(m);
     const int n_chunks = std::max(p->sub_groups.n_chunks, p->img_groups.n_chunks);
@@ -420,7 +458,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = dev_alloc(&p->d_wnew, p->MM, own)) ||
         (rc = dev_alloc(&p->d_probe_part, (size_t)n_chunks * p->MM, own)) ||
         (rc = dev_alloc(&p->d_probe_part_n, (size_t)n_chunks * p->MM, own)) ||
-        (rc = dev_alloc(&p->d_rf_part, p->n_rf_parts, own)) ||
+        (rc = dev_alloc(&p->d_rf_part, rf_cap, own)) ||
         (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own)) ||
         (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own)) ||
         (rc = dev_alloc(&p->d_metrics, 3, own)) || (rc = dev_alloc(&p->d_err, 1, own)))
@@ -437,7 +475,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
     }
     cudaError_t e;
     if ((e = cudaMemsetAsync(p->d_metrics, 0, 3 * sizeof(double), s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * p->n_rf_parts, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * rf_cap, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_re_part, 0, sizeof(float) * 2 * p->sub_tiles.n_tiles, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_w, 0, sizeof(float2) * p->MM, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), s)) != cudaSuccess)
@@ -597,6 +635,31 @@ int od2p_metrics(ptycho_plan_t *plan, float *rf, float *re, ptycho_stream_t stre
     return PTYCHO_OK;
 }
 
+int ptycho_plan_set_launch(ptycho_plan_t *plan, int32_t variant, int32_t blocks_per_sm, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (variant < 0 || variant >= PTYCHO_LAUNCH_VARIANTS) return fail(PTYCHO_ERR_INVALID_ARG, "variant out of range");
+    if (blocks_per_sm < 0) return fail(PTYCHO_ERR_INVALID_ARG, "blocks_per_sm < 0");
+    if (plan->batch_member)
+        return fail(PTYCHO_ERR_STATE, "a batch member takes its launch shape from ptycho_batch_set_launch");
+    return apply_launch(plan, variant, blocks_per_sm, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int ptycho_plan_get_launch(const ptycho_plan_t *plan, int32_t *variant, int32_t *blocks_per_sm,
+                           int32_t *max_blocks_per_sm)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    int most = 1;
+    if (plan->M != 256) {
+        int grid = 0;
+        if (int rc = frame_update_grid(plan->M, plan->k1_variant, 1, 0, &grid, &most)) return rc;
+    }
+    if (variant) *variant = plan->k1_variant;
+    if (blocks_per_sm) *blocks_per_sm = plan->k1_blocks_per_sm;
+    if (max_blocks_per_sm) *max_blocks_per_sm = most;
+    return PTYCHO_OK;
+}
+
 int od2p_state_len(const ptycho_plan_t *plan, int32_t which, int64_t *n)
 {
     if (!plan || !n) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
@@ -679,11 +742,13 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u, const ptycho_c32 *
 // ---------------------------------------------------------------- batches
 struct ptycho_batch_s {
     std::vector<ptycho_plan_s *> plans;
-    struct Cls {
-        int m = 0, n_items = 0, grid = 0;
+    struct Cls {  // the member plans of one probe side m
+        int m = 0, grid = 0;
+        int n_items[2] = {0, 0};         // (plan, frame group) items per launch shape
         od2p::FrameArgs *tab = nullptr;
-        int2 *items = nullptr;
+        int2 *items[2] = {nullptr, nullptr};
     };
+    int variant = 0, blocks_per_sm = 0;
     std::vector<Cls> cls;
     od2p::SubArgs *stab = nullptr;
     int2 *titems = nullptr;
@@ -738,22 +803,26 @@ int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const 
     for (auto *p : b->plans)
         if (std::find(ms.begin(), ms.end(), p->M) == ms.end()) ms.push_back(p->M);
     std::sort(ms.begin(), ms.end());
+    for (auto *p : b->plans) p->batch_member = true;
     for (int m : ms) {
         std::vector<FrameArgs> tab;
-        std::vector<int2> items;
+        std::vector<int2> items[2];
         for (auto *p : b->plans) {
             if (p->M != m) continue;
             const int local = (int)tab.size() / 2;
             tab.push_back(p->h_fargs[0]);
             tab.push_back(p->h_fargs[1]);
-            for (int g = 0; g < frame_groups(m, p->J); ++g) items.push_back(make_int2(local, g));
+            for (int v = 0; v < 2; ++v)
+                for (int g = 0; g < frame_groups(m, p->J, v); ++g) items[v].push_back(make_int2(local, g));
         }
         ptycho_batch_s::Cls c;
         c.m = m;
-        c.n_items = (int)items.size();
+        c.n_items[0] = (int)items[0].size();
+        c.n_items[1] = (int)items[1].size();
         int rc;
-        if ((rc = upload(&c.tab, tab, b->owned, s)) || (rc = upload(&c.items, items, b->owned, s)) ||
-            (rc = frame_update_grid(m, c.n_items, &c.grid)))
+        if ((rc = upload(&c.tab, tab, b->owned, s)) || (rc = upload(&c.items[0], items[0], b->owned, s)) ||
+            (rc = upload(&c.items[1], items[1], b->owned, s)) ||
+            (rc = frame_update_grid(m, 0, c.n_items[0], 0, &c.grid, nullptr)))
             return bail(rc);
         b->cls.push_back(c);
     }
@@ -789,10 +858,42 @@ int ptycho_batch_member(const ptycho_batch_t *b, int32_t i, ptycho_plan_t **plan
     return PTYCHO_OK;
 }
 
+int ptycho_batch_set_launch(ptycho_batch_t *b, int32_t variant, int32_t blocks_per_sm, ptycho_stream_t stream)
+{
+    if (!b) return fail(PTYCHO_ERR_INVALID_ARG, "batch is NULL");
+    if (variant < 0 || variant >= PTYCHO_LAUNCH_VARIANTS) return fail(PTYCHO_ERR_INVALID_ARG, "variant out of range");
+    if (blocks_per_sm < 0) return fail(PTYCHO_ERR_INVALID_ARG, "blocks_per_sm < 0");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<int> grids;
+    for (const auto &c : b->cls) {
+        int grid = 0;
+        if (int rc = frame_update_grid(c.m, variant, c.n_items[variant], blocks_per_sm, &grid, nullptr)) return rc;
+        grids.push_back(grid);
+    }
+    // members iterate alone in the same shape, so their RF partials keep one layout
+    for (auto *p : b->plans)
+        if (int rc = apply_launch(p, variant, blocks_per_sm, s)) return rc;
+    for (size_t i = 0; i < b->cls.size(); ++i) b->cls[i].grid = grids[i];
+    b->variant = variant;
+    b->blocks_per_sm = blocks_per_sm;
+    drop_graphs(b->graph);
+    return PTYCHO_OK;
+}
+
+int ptycho_batch_get_launch(const ptycho_batch_t *b, int32_t *variant, int32_t *blocks_per_sm)
+{
+    if (!b) return fail(PTYCHO_ERR_INVALID_ARG, "batch is NULL");
+    if (variant) *variant = b->variant;
+    if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+    return PTYCHO_OK;
+}
+
 static int batch_enqueue(ptycho_batch_s *b, int parity, cudaStream_t s)
 {
     for (const auto &c : b->cls)
-        if (int rc = launch_frame_update_table(c.m, c.tab, c.items, c.n_items, c.grid, parity, s)) return rc;
+        if (int rc = launch_frame_update_table(c.m, b->variant, c.tab, c.items[b->variant], c.n_items[b->variant],
+                                               c.grid, parity, s))
+            return rc;
     return launch_subdomain_update_table(false, b->stab, b->titems, b->n_titems, parity, s);
 }
 

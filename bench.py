@@ -394,6 +394,141 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- all workloads
+def _gpu_problem_inputs(od, p, dev, seed: int = 7):
+    """Truth, probe, scan and intensities for problem p, the intensities made on
+    the GPU (the library's forward operator, torch.poisson at p.peak)."""
+    import torch
+    offs = p.offsets()
+    u_true, w = p.truth(), p.probe()
+    tmp = od.ptycho_plan(od.Geometry(p.n, p.n, p.m, offs),
+                         torch.ones((len(offs), p.m, p.m), dtype=torch.float32, device=dev))
+    fr = od.ptycho_forward(tmp, torch.from_numpy(u_true).to(dev), torch.from_numpy(w).to(dev))
+    tmp.close()
+    f = fr.abs().square_()
+    del fr
+    if p.peak is not None:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed)
+        kappa = float(p.peak) / float(f.max())
+        f = torch.poisson(f.mul_(kappa), generator=gen).div_(kappa)
+    return offs, u_true, w, f.float().contiguous()
+
+
+def _event_times(fn, K: int, flush):
+    """Per-call device times (s) of K calls of fn, the L2 flushed before each."""
+    import torch
+    s = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush.fill_(float(k))
+        ev[k][0].record(s)
+        fn()
+        ev[k][1].record(s)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) / 1e3 for a, b in ev]
+
+
+def _oracle_sample(p, blind, params, budget_s, max_frames):
+    """Frame-updates/s of the FP64 oracle on the host cores, on a bounded sample of
+    problem p: a square crop holding at most max_frames frames of the same probe,
+    step and subdomain grid, iterated until budget_s has passed (at least once)."""
+    import dataclasses
+
+    import oracle
+    from paper_2011_00162_gb300 import synth
+    n = p.m + ((p.n - p.m) // p.step) * p.step
+    while n > 2 * p.m and len(synth.raster_offsets(n, p.m, p.step)) > max_frames:
+        n -= p.step
+    grid = max(2, n // (2 * p.m)) if n >= 2 * p.m else 1
+    q = dataclasses.replace(p, n=n, sub_rows=min(p.sub_rows, grid), sub_cols=min(p.sub_cols, grid))
+    offs = q.offsets()
+    u_true, w = q.truth(), q.probe()
+    f = synth.poissonize(np.abs(oracle.forward(u_true, w, offs)) ** 2, q.peak, 7)
+    w0 = synth.gaussian_probe(q.m) if blind else w
+    a = oracle.ADMM(f, w0, offs, q.n, q.n, q.sub_rows, q.sub_cols, q.overlap_px, q.eps, params["eta"],
+                    params["r"], blind=blind, mu=params.get("mu", 0.0), gamma=params.get("gamma", 0.0))
+    it = 0
+    t0 = time.perf_counter()
+    while True:
+        a.iterate(1)
+        it += 1
+        el = time.perf_counter() - t0
+        if el > budget_s:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(len(offs) * it / el, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{it} oracle iterations of a {q.n}^2 crop ({len(offs)} frames of {q.m}^2, "
+                      f"{q.sub_rows}x{q.sub_cols} subdomains), {el:.1f} s"}
+
+
+def run_configs(args):
+    """One JSON line per workload: GPU iteration throughput (L2 flushed per
+    iteration), gradient throughput of the ST-AGM loss with exit-wave recompute
+    (blind workloads), and the oracle on a bounded sample."""
+    import torch
+
+    import paper_2011_00162_gb300 as od
+    from paper_2011_00162_gb300 import autotune, synth
+    from paper_2011_00162_gb300 import build as odbuild
+    odbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    table = [
+        ("config1_od2p_64px_m16_169frames_1x2sub_noiseless", synth.small_2sub(), False,
+         {"eta": 0.1, "r": 0.05}, 2000),
+        ("config2_od2p_512px_m64_841frames_4x4sub_poisson1e4", synth.grid_4x4(), False,
+         {"eta": 2.0, "r": 0.5}, 2000),
+        ("config4_od2bp_1024px_m128_841frames_4x4sub_poisson1e4", synth.blind_4x4(), True,
+         {"eta": 2.0, "r": 0.5, "mu": 1.0, "gamma": 0.1}, 300),
+        ("config5_od2bp_4096px_m256_6561frames_8x8sub_poisson1e5", synth.large_blind(), True,
+         {"eta": 2.0, "r": 0.5, "mu": 1.0, "gamma": 0.1}, 30),
+    ]
+    for name, p, blind, prm, K in table:
+        if args.only and args.only not in name:
+            continue
+        offs, u_true, w, f = _gpu_problem_inputs(od, p, dev)
+        J = len(offs)
+        g = od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, prm["eta"], prm["r"],
+                        mu=prm.get("mu", 0.0), gamma=prm.get("gamma", 0.0), blind=blind)
+        plan = od.ptycho_plan(g, f)
+        w0 = torch.from_numpy(synth.gaussian_probe(p.m) if blind else w).to(dev)
+        od.od2p_init(plan, w0)
+        tuned = autotune.tune_plan(plan, flush_l2=True)
+        for _ in range(5):
+            flush.fill_(0.0)
+            od.od2p_iterate(plan, 1)
+        t_it = _event_times(lambda: od.od2p_iterate(plan, 1), K, flush)
+        t_k1 = _event_times(lambda: od.od2p_frame_update(plan), max(10, K // 10), flush)
+        line = {"workload": name, "frames": J, "image": p.n, "probe": p.m, "blind": blind,
+                "subdomains": f"{p.sub_rows}x{p.sub_cols}", "iterations_timed": K,
+                "frame_updates_per_s": round(J * K / sum(t_it), 1),
+                "ms_per_iteration": round(1e3 * statistics.mean(t_it), 5),
+                "frame_update_ms": round(1e3 * statistics.mean(t_k1), 5),
+                "hbm_algorithmic_frac_frame_update": round(
+                    20.0 * p.m * p.m * J / statistics.mean(t_k1) / 1e9 / _peaks()[0], 4),
+                "launch": list(od.ptycho_plan_get_launch(plan)), "tuned_cached": tuned["cached"],
+                "l2": "flushed before every timed call"}
+        if blind:
+            u = od.od2p_merge(plan)
+            wcur = od.od2p_get_state(plan, od.STATE_W).reshape(p.m, p.m)
+            Kg = max(5, K // 3)
+            t_g = _event_times(lambda: od.stagm_loss_grad(plan, u, wcur), Kg, flush)
+            line["gradient_frames_per_s"] = round(J * Kg / sum(t_g), 1)
+            line["ms_per_gradient"] = round(1e3 * statistics.mean(t_g), 5)
+            line["gradient"] = "ST-AGM loss + grad_u + grad_w, exit waves recomputed (none stored)"
+        rf, re = od.od2p_metrics(plan)
+        line["rf_after"], line["re_after"] = rf, re
+        plan.close()
+        del f
+        torch.cuda.empty_cache()
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = _oracle_sample(p, blind, prm, budget_s=args.cpu_budget,
+                                                  max_frames=200 if p.m >= 128 else 900)
+        print(json.dumps(line), flush=True)
+
+
 def _oracle_case(p):
     import oracle
     from paper_2011_00162_gb300 import synth
@@ -466,8 +601,13 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
     ap.add_argument("--retune", action="store_true", help="measure launch shapes even when cached")
+    ap.add_argument("--configs", action="store_true",
+                    help="measure every workload (one JSON line each) instead of the headline line")
+    ap.add_argument("--only", default="", help="with --configs: only workloads whose name contains this")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.configs:
+        run_configs(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

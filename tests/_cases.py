@@ -1,5 +1,8 @@
 """Shared construction of seeded test problems (inputs from synth, intensities
 from the FP64 oracle's forward operator, Poisson noise from synth)."""
+import json
+import os
+
 import numpy as np
 
 import oracle
@@ -28,3 +31,13 @@ def phase_aligned_rel(x, ref) -> float:
     ref = np.asarray(ref, np.complex128).reshape(-1)
     th = np.angle(np.vdot(x, ref))
     return float(np.linalg.norm(x * np.exp(1j * th) - ref) / np.linalg.norm(ref))
+
+
+def record(test: str, **figures) -> None:
+    """Append the parity figures a test measured to the JSON-lines file named by
+    $OD2P_PARITY_RECORD (nothing happens when it is unset)."""
+    path = os.environ.get("OD2P_PARITY_RECORD")
+    if not path:
+        return
+    with open(path, "a") as fh:
+        fh.write(json.dumps({"test": test, **{k: float(v) for k, v in figures.items()}}) + "\n")

@@ -9,7 +9,7 @@ import paper_2011_00162_gb300 as od
 from paper_2011_00162_gb300 import build as odbuild
 from paper_2011_00162_gb300 import synth
 
-from _cases import make_case, rel_l2
+from _cases import make_case, record, rel_l2
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
@@ -63,10 +63,13 @@ def test_batch_member_matches_oracle():
         offs, u_true, w, f = c
         ref = oracle.ADMM(f, w, offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, 0.5, 2.0, 0.5)
         ref.iterate(1)
+        errs = {}
         for k, ko in ((od.STATE_U, oracle.U), (od.STATE_GAMMA, oracle.GAMMA), (od.STATE_LAMBDA, oracle.LAMBDA)):
             b = ref.get(ko)
             if b.size:
-                assert rel_l2(od.od2p_get_state(batch.members[i], k).cpu().numpy(), b) < 1e-5
+                errs[str(k)] = rel_l2(od.od2p_get_state(batch.members[i], k).cpu().numpy(), b)
+                assert errs[str(k)] < 1e-5
+        record(f"config3_member{i}_one_iteration", **errs)
     batch.close()
 
 

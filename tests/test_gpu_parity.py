@@ -13,7 +13,7 @@ import paper_2011_00162_gb300 as od
 from paper_2011_00162_gb300 import synth
 from paper_2011_00162_gb300 import build as odbuild
 
-from _cases import make_case, phase_aligned_rel, rel_l2
+from _cases import make_case, phase_aligned_rel, record, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -152,7 +152,8 @@ def test_one_iteration_two_subdomains(scrambled):
         _scramble(plan, ref, 3)
     od.od2p_iterate(plan, 1)
     ref.iterate(1)
-    _compare_state(plan, ref, ONE_ITER_TOL)
+    out = _compare_state(plan, ref, ONE_ITER_TOL)
+    record(f"config1_one_iteration_{'scrambled' if scrambled else 'step0'}", **out)
 
 
 @pytest.mark.parametrize("scrambled", [False, True])
@@ -163,10 +164,11 @@ def test_one_iteration_grid4x4_full_size(scrambled):
     plan, ref = pair_of(p, offs, w, f)
     if scrambled:
         _scramble(plan, ref, 4)
-    for _ in range(2):
+    for it in range(2):
         od.od2p_iterate(plan, 1)
         ref.iterate(1)
-        _compare_state(plan, ref, ONE_ITER_TOL)
+        out = _compare_state(plan, ref, ONE_ITER_TOL)
+        record(f"config2_one_iteration_{'scrambled' if scrambled else 'step0'}_{it}", **out)
         # re-synchronise so that each comparison measures a single iteration
         for wg, wo in [(od.STATE_U, oracle.U), (od.STATE_GAMMA, oracle.GAMMA), (od.STATE_LAMBDA, oracle.LAMBDA)]:
             od.od2p_set_state(plan, wg, c64(ref.get(wo)))
@@ -212,6 +214,8 @@ def test_end_of_run_two_subdomains():
     err_truth_oracle = phase_aligned_rel(uo[lit], u_true[lit])
     err_truth_gpu = phase_aligned_rel(ug[lit], u_true[lit])
     print(f"end-of-run GPU vs FP64 oracle {err:.2e}; vs truth: oracle {err_truth_oracle:.3e}, GPU {err_truth_gpu:.3e}")
+    record("config1_end_of_run_50its", gpu_vs_oracle=err, oracle_vs_truth=err_truth_oracle,
+           gpu_vs_truth=err_truth_gpu)
     assert err < END_TOL
     # after 50 iterations the metrics inherit the trajectory's FP32 deviation: RF (a
     # sum over all frames) within END_TOL, RE (a difference of iterates) within 10 END_TOL
@@ -230,7 +234,10 @@ def test_end_of_run_grid4x4():
     ug, uo = host(od.od2p_merge(plan)), ref.merge()
     lit = synth.lit_mask(p.n, p.n, p.m, offs)
     err = phase_aligned_rel(ug, uo)
-    print(f"end-of-run GPU vs FP64 oracle {err:.2e}; oracle vs truth {phase_aligned_rel(uo[lit], u_true[lit]):.3e}")
+    err_truth_oracle = phase_aligned_rel(uo[lit], u_true[lit])
+    print(f"end-of-run GPU vs FP64 oracle {err:.2e}; oracle vs truth {err_truth_oracle:.3e}")
+    record("config2_end_of_run_200its", gpu_vs_oracle=err, oracle_vs_truth=err_truth_oracle,
+           gpu_vs_truth=phase_aligned_rel(ug[lit], u_true[lit]))
     assert err < END_TOL
 
 
@@ -349,14 +356,18 @@ def test_large_blind_workload_sampled_frames():
     gam = od.od2p_get_state(plan, od.STATE_GAMMA)
     q = od.od2p_get_state(plan, od.STATE_Q)
     mm = p.m * p.m
+    worst = [0.0, 0.0]
     for j in rng.choice(len(offs), 12, replace=False):
         r0, c0 = offs[j]
         x = oracle.forward(u0, w0, offs[j:j + 1])[0]          # A u for frame j (u_d = R_d u0)
         z = oracle.stagm_prox(x, f[j].astype(np.float64), 0.5, eta)
         g_ref = x - z                                          # Gamma^0 = 0
         q_ref = oracle.fft2(z - g_ref, True)
-        assert rel_l2(host(gam[j * mm:(j + 1) * mm]), g_ref) < ONE_ITER_TOL
-        assert rel_l2(host(q[j * mm:(j + 1) * mm]), q_ref) < ONE_ITER_TOL
+        eg, eq = rel_l2(host(gam[j * mm:(j + 1) * mm]), g_ref), rel_l2(host(q[j * mm:(j + 1) * mm]), q_ref)
+        worst = [max(worst[0], eg), max(worst[1], eq)]
+        assert eg < ONE_ITER_TOL
+        assert eq < ONE_ITER_TOL
+    record("config5_sampled_frames_one_update", Gamma=worst[0], q=worst[1])
 
 
 def test_nonblind_residual_frames_from_gather_slots():
@@ -393,10 +404,13 @@ def test_blind_workload_1024_full_size():
     _scramble(plan, ref, 12, blind=True)
     od.od2p_iterate(plan, 1)
     ref.iterate(1)
-    _compare_state(plan, ref, ONE_ITER_TOL, blind=True)
+    out = _compare_state(plan, ref, ONE_ITER_TOL, blind=True)
+    record("config4_one_iteration_scrambled", **out)
     rng = np.random.default_rng(3)
     u = (u_true * (1 + 0.1 * rng.standard_normal(u_true.shape))).astype(np.complex64)
     loss, gu, gw = od.stagm_loss_grad(plan, c64(u), c64(w0))
     L, gu_o, gw_o = oracle.loss_grad(u, w0, offs, f.astype(np.float64), 0.5)
+    record("config4_loss_grad", loss=abs(float(loss.item()) - L) / abs(L), grad_u=rel_l2(host(gu), gu_o),
+           grad_w=rel_l2(host(gw), gw_o))
     assert abs(float(loss.item()) - L) < 1e-5 * abs(L)
     assert rel_l2(host(gu), gu_o) < 1e-5 and rel_l2(host(gw), gw_o) < 1e-5

@@ -215,11 +215,12 @@ int od2p_merge(const ptycho_plan_t *plan, ptycho_c32 *u_out_dev, ptycho_stream_t
 int od2p_metrics(ptycho_plan_t *plan, float *rf_host, float *re_host, ptycho_stream_t stream);
 
 /*
- * Launch shape of the frame update (the paper fixes none: its GPU section
- * assigns frames to thread blocks without fixing how many).  For m <= 128 two
+ * Launch shape of the frame update (the paper fixes none).  For m <= 128 two
  * shapes are compiled, each a (frames per block, threads per block) pair:
  *   m = 16: variant 0 (8, 256), variant 1 (4, 128);  m = 32: (4, 256), (2, 128);
  *   m = 64: (1, 512), (1, 256);  m = 128: (1, 1024), (1, 512).
+ * At m = 32 and 64 variant 1 reads Gamma from L2 instead of staging it in
+ * shared memory, so that up to four times as many blocks fit on an SM.
  * The persistent kernel runs min(frame groups, b x SMs) blocks, b =
  * blocks_per_sm capped at what fits (0: as many as fit).  Every shape gives
  * the same iterates bit for bit; only the RF partial sums are grouped

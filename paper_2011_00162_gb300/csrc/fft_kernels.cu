@@ -239,19 +239,20 @@ __device__ __forceinline__ void col_stage1_store_slots(float2 *buf, const float2
 
 // ---------------------------------------------------------------- K1: fused frame update
 
-// Launch shape of the persistent frame update: frames per group, threads, and
+// Launch shapes of the persistent frame update: frames per group, threads, and
 // whether Gamma is staged in shared memory (m = 128 only stages sqrt f: the
-// frame buffer already takes 132 KB).
-// Two compiled shapes per probe side (variant 0 / 1), chosen per plan by the
-// autotuner.  MINB: resident blocks per SM the register budget is sized for
-// (shared memory allows at least as many).
+// frame buffer already takes 132 KB).  Two shapes (variant 0 / 1) are compiled
+// per probe side; the autotuner picks one per plan.  Variant 1 trades the Gamma
+// staging (Gamma then comes from L2 after a bulk prefetch) for more resident
+// blocks at m = 32 and 64.  MINB: resident blocks per SM the register budget
+// is sized for (shared memory allows at least as many).
 template <int M, int V> struct K1Cfg;
 template <> struct K1Cfg<16, 0> { static constexpr int FPB = 8, NT = 256, STAGE_G = 1, MINB = 4; };
 template <> struct K1Cfg<16, 1> { static constexpr int FPB = 4, NT = 128, STAGE_G = 1, MINB = 8; };
 template <> struct K1Cfg<32, 0> { static constexpr int FPB = 4, NT = 256, STAGE_G = 1, MINB = 2; };
-template <> struct K1Cfg<32, 1> { static constexpr int FPB = 2, NT = 128, STAGE_G = 1, MINB = 4; };
+template <> struct K1Cfg<32, 1> { static constexpr int FPB = 2, NT = 128, STAGE_G = 0, MINB = 8; };
 template <> struct K1Cfg<64, 0> { static constexpr int FPB = 1, NT = 512, STAGE_G = 1, MINB = 2; };
-template <> struct K1Cfg<64, 1> { static constexpr int FPB = 1, NT = 256, STAGE_G = 1, MINB = 2; };
+template <> struct K1Cfg<64, 1> { static constexpr int FPB = 1, NT = 256, STAGE_G = 0, MINB = 4; };
 template <> struct K1Cfg<128, 0> { static constexpr int FPB = 1, NT = 1024, STAGE_G = 0, MINB = 1; };
 template <> struct K1Cfg<128, 1> { static constexpr int FPB = 1, NT = 512, STAGE_G = 0, MINB = 1; };
 

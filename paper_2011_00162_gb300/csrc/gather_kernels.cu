@@ -60,13 +60,19 @@ constexpr int NBR_SMEM = 16;
 // One plan: block b updates tile b with the arguments `single`.  Batches:
 // block b updates tile items[b].y of the plan whose arguments are
 // tab[2 items[b].x + parity].
+#ifndef OD2P_K2_U
+#define OD2P_K2_U 4
+#endif
+#ifndef OD2P_K2_MINB
+#define OD2P_K2_MINB 4
+#endif
 template <bool BLIND, bool BATCHED>
-__global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4)
+__global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : OD2P_K2_MINB)
     subdomain_update_kernel(const SubArgs single, const SubArgs *__restrict__ tab, const int2 *__restrict__ items,
                             int parity)
 {
     __shared__ float red[2 * (GATHER_THREADS / 32)];
-    __shared__ ListEntry lst[LIST_SMEM];
+    __shared__ ListEntry lst[BLIND ? LIST_SMEM : 1];
     __shared__ NbrInfo nbs[NBR_SMEM];
     __shared__ SubArgs sa;
     const int2 it = BATCHED ? items[blockIdx.x] : make_int2(0, (int)blockIdx.x);
@@ -76,23 +82,26 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4)
     }
     const SubArgs &a = BATCHED ? sa : single;
     const int tix = it.y;
-    const Tile tile = a.tiles[tix];
-    const int d = tile.reg;
-    const int32_t *rc = a.rect + 4 * d;
-    const int hd = rc[2] - rc[0], wd = rc[3] - rc[1];
+    const TileInfo ti = a.tinfo[tix];
     const int lane = threadIdx.x & 31, ty0 = (threadIdx.x >> 5) * TILE_ROWS;
-    const int lc = tile.c0 + lane;
-    const bool col_ok = lc < wd;
-    const int nrows = min(TILE_ROWS, hd - tile.r0 - ty0);  // rows of this thread inside Omega_d (may be <= 0)
-    const int C = rc[1] + lc;
+    const bool col_ok = lane < ti.ncols;
+    const int nrows = min(TILE_ROWS, ti.nrows - ty0);  // rows of this thread inside Omega_d (may be <= 0)
+    const bool active = col_ok && nrows > 0;
+    const int C = ti.C0 + lane, R0 = ti.R0 + ty0;
     const int M = a.M, MM = M * M;
-    const int k0 = a.tptr[tix], nk = a.tptr[tix + 1] - k0;
-    const int n0 = a.tnbr_ptr[tix], nnb = a.tnbr_ptr[tix + 1] - n0;
-    for (int i = threadIdx.x; i < min(nk, LIST_SMEM); i += GATHER_THREADS) lst[i] = a.tlist[k0 + i];
-    for (int i = threadIdx.x; i < min(nnb, NBR_SMEM); i += GATHER_THREADS) nbs[i] = a.tnbr[n0 + i];
+    // u index of each of the thread's rows (the last valid row repeated)
+    int ui[TILE_ROWS];
+#pragma unroll
+    for (int r = 0; r < TILE_ROWS; ++r) ui[r] = ti.u0 + (ty0 + max(0, min(r, nrows - 1))) * ti.pitch + lane;
+    int nk_r[TILE_ROWS];
+#pragma unroll
+    for (int r = 0; r < TILE_ROWS; ++r) nk_r[r] = (!BLIND && active && r < nrows) ? (int)__ldg(a.cnt + ui[r]) : 0;
+    if (BLIND)
+        for (int i = threadIdx.x; i < min(ti.nk, LIST_SMEM); i += GATHER_THREADS) lst[i] = a.tlist[ti.k0 + i];
+    for (int i = threadIdx.x; i < min(ti.nnb, NBR_SMEM); i += GATHER_THREADS) nbs[i] = a.tnbr[ti.n0 + i];
     __syncthreads();
-    // A_d^*(z - Gamma) at each pixel, frames in ascending j.  Nonblind: q_j
-    // already carries conj(w) and sum_j S_j^T |w|^2 is precomputed.  Blind:
+    // A_d^*(z - Gamma) at each pixel, frames in ascending j.  Nonblind: the
+    // slots already carry conj(w) and sum_j S_j^T |w|^2 is precomputed.  Blind:
     // weight with W_d^{n+1} here and sum |W_d|^2 on the way.
     float2 acc[TILE_ROWS];
     float nrm[TILE_ROWS];
@@ -101,29 +110,25 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4)
         acc[r] = make_float2(0.f, 0.f);
         nrm[r] = 0.f;
     }
-    const float2 *w = BLIND ? a.Wd + d * MM : nullptr;
+    const float2 *w = BLIND ? a.Wd + ti.reg * MM : nullptr;
     if (!BLIND) {
         // nonblind: the pixel's frames sit in slots 0 .. cnt-1 in ascending j;
-        // U slots x TILE_ROWS rows of coalesced, independent loads per step
-        // (U = 2 keeps the kernel within 64 registers: 4 blocks per SM)
-        if (nrows > 0 && col_ok) {
-            int ui[TILE_ROWS], nk_r[TILE_ROWS];
+        // U slots x TILE_ROWS rows of coalesced, independent loads per step; a
+        // row past its count loads slot 0 and discards it
+        if (active) {
             int kmax = 0;
 #pragma unroll
-            for (int r = 0; r < TILE_ROWS; ++r) {
-                ui[r] = (int)a.u_off[d] + (tile.r0 + ty0 + min(r, nrows - 1)) * wd + lc;
-                nk_r[r] = r < nrows ? (int)__ldg(a.cnt + ui[r]) : 0;
-                kmax = max(kmax, nk_r[r]);
-            }
-            constexpr int U = 2;
+            for (int r = 0; r < TILE_ROWS; ++r) kmax = max(kmax, nk_r[r]);
+            constexpr int U = OD2P_K2_U;
             for (int k = 0; k < kmax; k += U) {
                 float2 v[U][TILE_ROWS];
 #pragma unroll
                 for (int u = 0; u < U; ++u)
 #pragma unroll
                     for (int r = 0; r < TILE_ROWS; ++r) {
-                        const int kk = k + u < nk_r[r] ? k + u : 0;
-                        v[u][r] = __ldg(a.slot + (size_t)kk * a.slot_stride + ui[r]);
+                        const unsigned kk = k + u < nk_r[r] ? (unsigned)(k + u) : 0u;
+                        // 32-bit index: the plan checks slot_k * u_len < 2^32
+                        v[u][r] = __ldg(a.slot + (kk * (unsigned)a.slot_stride + (unsigned)ui[r]));
                     }
 #pragma unroll
                 for (int u = 0; u < U; ++u)
@@ -132,18 +137,19 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4)
                         if (k + u < nk_r[r]) acc[r] = cadd(acc[r], v[u][r]);
             }
         }
-    } else if (nrows > 0 && col_ok) {
+    } else if (active) {
         // blind: walk the tile's frame list and weight with W_d^{n+1};
         // U entries x TILE_ROWS rows of loads per step, branch-free: a lane whose
         // pixel a frame does not cover loads element 0 and discards it.
         constexpr int U = 4;
+        const int nk = ti.nk;
         for (int k = 0; k < nk; k += U) {
             float2 qv[U][TILE_ROWS], wv[U][TILE_ROWS];
             unsigned hits = 0u;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const bool valid = k + u < nk;
-                const ListEntry e = valid ? (k + u < LIST_SMEM ? lst[k + u] : a.tlist[k0 + k + u]) : ListEntry{0, M, M, 0};
+                const ListEntry e = valid ? (k + u < LIST_SMEM ? lst[k + u] : a.tlist[ti.k0 + k + u]) : ListEntry{0, M, M, 0};
                 const int dr0 = e.dr + ty0, dc = e.dc + lane;
                 const bool cok = (unsigned)dc < (unsigned)M;
 #pragma unroll
@@ -171,20 +177,16 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4)
         }
     }
     float dn = 0.f, nn = 0.f;
-    if (col_ok && nrows > 0) {
+    if (active) {
         float2 u_old[TILE_ROWS], num[TILE_ROWS], u_new[TILE_ROWS];
         float den[TILE_ROWS];
-        int ui[TILE_ROWS];
 #pragma unroll
         for (int r = 0; r < TILE_ROWS; ++r) {
-            const int lr = tile.r0 + ty0 + min(r, nrows - 1);
-            ui[r] = (int)a.u_off[d] + lr * wd + lc;
             u_old[r] = a.u_cur[ui[r]];
-            const float nrm_r = BLIND ? nrm[r] : a.nrm[ui[r]];
             num[r] = cscale(acc[r], a.eta);
-            den[r] = a.eta * nrm_r;
+            den[r] = a.eta * (BLIND ? nrm[r] : __ldg(a.nrm + ui[r]));
         }
-        const int R0 = rc[0] + tile.r0 + ty0;
+        const int nnb = ti.nnb, n0 = ti.n0, rend = ti.rend;
         // consensus v_{d,e} (eq. updateV-multi) and the r-terms of the u-update:
         // one neighbour at a time, the loads of all rows together
         for (int i = 0; i < nnb; ++i) {
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4)
 #pragma unroll
             for (int r = 0; r < TILE_ROWS; ++r) {
                 // clamped into Omega_d n Omega_e: rows outside are loaded but discarded
-                const int R = min(max(R0 + r, nb.r0), min(nb.r1, rc[2]) - 1);
+                const int R = min(max(R0 + r, nb.r0), min(nb.r1, rend) - 1);
                 const int li = (R - nb.p_r0) * nb.p_pitch + (C - nb.p_c0);
                 ue[r] = a.u_cur[nb.u_base + (R - nb.r0) * nb.u_pitch + (C - nb.c0)];
                 lde[r] = a.lam_cur[nb.lam_de + li];
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : 4)
             int li[TILE_ROWS];
 #pragma unroll
             for (int r = 0; r < TILE_ROWS; ++r) {
-                const int R = min(max(R0 + r, nb.r0), min(nb.r1, rc[2]) - 1);
+                const int R = min(max(R0 + r, nb.r0), min(nb.r1, rend) - 1);
                 li[r] = (R - nb.p_r0) * nb.p_pitch + (C - nb.p_c0);
                 ue[r] = a.u_cur[nb.u_base + (R - nb.r0) * nb.u_pitch + (C - nb.c0)];
                 lde[r] = a.lam_cur[nb.lam_de + li[r]];
@@ -533,10 +535,8 @@ void fill_sub_args(const ptycho_plan_s *p, SubArgs out[2])
         a.M = p->M;
         a.rect = p->d_rect;
         a.u_off = p->d_u_off;
-        a.tiles = p->sub_tiles.tiles;
-        a.tptr = p->sub_tiles.ptr;
+        a.tinfo = p->sub_tiles.info;
         a.tlist = p->sub_tiles.list;
-        a.tnbr_ptr = p->sub_tiles.nbr_ptr;
         a.tnbr = p->sub_tiles.nbr;
         a.u_cur = p->d_u[par];
         a.lam_cur = p->d_lam[par];

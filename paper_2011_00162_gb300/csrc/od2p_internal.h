@@ -15,7 +15,10 @@ namespace od2p {
 // Lanes run along a row (coalesced frame rows); each thread owns TILE_ROWS
 // consecutive rows of its column, so one frame-list entry drives TILE_ROWS
 // independent loads.
-constexpr int TILE_H = 32;
+#ifndef OD2P_TILE_H
+#define OD2P_TILE_H 32
+#endif
+constexpr int TILE_H = OD2P_TILE_H;
 constexpr int TILE_W = 32;
 constexpr int GATHER_THREADS = 256;
 constexpr int TILE_ROWS = TILE_H * TILE_W / GATHER_THREADS;
@@ -51,6 +54,16 @@ struct ListEntry {
 
 struct NbrInfo;
 
+// Everything the subdomain update needs about one tile of a subdomain, read
+// with one 48-byte load: u index of the tile's first pixel and the row pitch
+// of u_d, the tile's extent inside Omega_d, its image coordinates, its
+// neighbour and frame-list ranges, its subdomain and the last row of Omega_d.
+struct TileInfo {
+    int32_t u0, pitch, nrows, ncols;
+    int32_t R0, C0, n0, nnb;
+    int32_t k0, nk, reg, rend;
+};
+
 struct GatherTiles {
     int32_t n_tiles = 0;
     Tile *tiles = nullptr;        // device
@@ -59,6 +72,7 @@ struct GatherTiles {
     int32_t *reg_ptr = nullptr;   // device, first tile of each region (+ end)
     int32_t *nbr_ptr = nullptr;   // device, n_tiles + 1: neighbours meeting the tile
     NbrInfo *nbr = nullptr;       // device
+    TileInfo *info = nullptr;     // device, n_tiles (subdomain tiles only)
 };
 
 // A neighbour e of subdomain d, precomputed for the subdomain update.
@@ -119,8 +133,7 @@ struct SubArgs {
     int32_t M;
     const int32_t *rect;
     const int64_t *u_off;
-    const Tile *tiles;
-    const int32_t *tptr, *tnbr_ptr;
+    const TileInfo *tinfo;
     const ListEntry *tlist;
     const NbrInfo *tnbr;
     const float2 *u_cur, *lam_cur, *q, *w, *Wd;

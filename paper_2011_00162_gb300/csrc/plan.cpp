@@ -409,6 +409,16 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         }
         tile_nbr_ptr.push_back((int32_t)tile_nbr.size());
     }
+    std::vector<TileInfo> tile_info;
+    for (size_t t = 0; t < st.tiles.size(); ++t) {
+        const Tile &T = st.tiles[t];
+        const int32_t *R = &p->rect[4 * T.reg];
+        const int wd = R[3] - R[1], hd = R[2] - R[0];
+        tile_info.push_back(TileInfo{(int32_t)(p->u_off[T.reg] + (int64_t)T.r0 * wd + T.c0), wd,
+                                     std::min(TILE_H, hd - T.r0), std::min(TILE_W, wd - T.c0), R[0] + T.r0,
+                                     R[1] + T.c0, tile_nbr_ptr[t], tile_nbr_ptr[t + 1] - tile_nbr_ptr[t],
+                                     st.ptr[t], st.ptr[t + 1] - st.ptr[t], T.reg, R[2]});
+    }
     std::vector<int32_t> img_rect = {0, 0, p->H, p->W};
     HostTiles it = make_tiles(1, img_rect, all_frames, p->offs, m);
 
@@ -426,6 +436,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = upload_tiles(p->sub_tiles, st, own, s)) || (rc = upload_tiles(p->img_tiles, it, own, s)) ||
         (rc = upload(&p->sub_tiles.nbr_ptr, tile_nbr_ptr, own, s)) ||
         (rc = upload(&p->sub_tiles.nbr, tile_nbr, own, s)) ||
+        (rc = upload(&p->sub_tiles.info, tile_info, own, s)) ||
         (rc = upload_groups(p->sub_groups, sub_frames, own, s)) ||
         (rc = upload_groups(p->img_groups, all_frames, own, s)))
         return bail(rc);

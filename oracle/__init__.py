@@ -69,6 +69,7 @@ def _load():
             "orc_forward": (None, [i32, i32, P, i32, P, i32, P, P]),
             "orc_adjoint": (None, [i32, i32, i32, P, i32, P, P, P]),
             "orc_loss_grad": (f64, [i32, i32, P, i32, P, i32, P, P, f64, P, P]),
+            "orc_probe_init": (None, [i32, i32, P, P]),
             "orc_geometry": (i32, [i32, i32, i32, i32, P, i32, i32, i32, P, P]),
             "orc_pairs": (i32, [i32, P, i32, P, P]),
             "orc_admm_new": (P, [i32, i32, i32, i32, P, i32, i32, i32, P, P, P, f64, f64, f64,
@@ -171,6 +172,15 @@ def loss_grad(u, w, offs, f, eps: float):
     loss = _load().orc_loss_grad(H, W, _p(u), w.shape[0], _p(w), offs.shape[0], _p(offs),
                                  _p(f), eps, _p(gu), _p(gw))
     return float(loss), gu, gw
+
+
+def probe_init(f) -> np.ndarray:
+    """w0 = (1/J) sum_j F^* sqrt(f_j) (section 4.3's data-driven initial probe)."""
+    f = _c(f, np.float64)
+    J, m = f.shape[0], f.shape[-1]
+    w0 = np.empty((m, m), np.complex128)
+    _load().orc_probe_init(m, J, _p(f), _p(w0))
+    return w0
 
 
 def geometry(H: int, W: int, m: int, offs, sub_rows: int, sub_cols: int, overlap_px: int):

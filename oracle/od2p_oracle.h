@@ -48,6 +48,11 @@ void orc_adjoint(int H, int W, int m, const ocplx *w, int J, const int32_t *offs
 double orc_loss_grad(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
                      const int32_t *offs, const double *f, double eps, ocplx *gu, ocplx *gw);
 
+/* Data-driven initial probe of the blind experiments (section 4.3): the mean
+ * over the J frames of the inverse unitary DFT of the measured amplitudes,
+ * w0 = (1/J) sum_j F^* sqrt(f_j), taken frame by frame.  f: J x m x m.       */
+void orc_probe_init(int m, int J, const double *f, ocplx *w0);
+
 /* ---- overlapping domain decomposition, sections 2.1 and 3.1 ---- */
 /* frame_sub[J]: subdomain of each frame; rect[D*4]: (r0, c0, r1, c1) half-open.
  * Returns D (= sub_rows*sub_cols) or a negative value on invalid input.        */

@@ -10,6 +10,7 @@
  */
 #include "od2p_oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -102,4 +103,19 @@ double orc_loss_grad(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
     free(x);
     free(lj);
     return loss;
+}
+
+void orc_probe_init(int m, int J, const double *f, ocplx *w0)
+{
+    const int mm = m * m;
+    ocplx *a = (ocplx *)malloc(sizeof(ocplx) * (size_t)mm);
+    for (int k = 0; k < mm; ++k) w0[k] = 0.0;
+    for (int j = 0; j < J; ++j) {
+        const double *fj = f + (size_t)j * mm;
+        for (int k = 0; k < mm; ++k) a[k] = sqrt(fj[k]);
+        orc_fft2(a, m, 1);  /* F^* sqrt(f_j) */
+        for (int k = 0; k < mm; ++k) w0[k] += a[k];
+    }
+    for (int k = 0; k < mm; ++k) w0[k] /= (double)J;
+    free(a);
 }

@@ -576,3 +576,29 @@ def test_loss_reduces_to_agm_and_vanishes_at_truth():
     frames = np.stack([np.fft.fft2(w * u2[r:r + m, c:c + m], norm="ortho") for r, c in offs])
     agm = 0.5 * np.sum((np.abs(frames) - np.sqrt(f)) ** 2)
     assert abs(L2 - agm) < 1e-10 * agm
+
+
+# ----------------------------------------------------------------------------- data-driven initial probe
+@pytest.mark.parametrize("m", [16, 64])
+def test_probe_init_recovers_a_probe_with_positive_spectrum(m):
+    """Section 4.3's w0 = (1/J) sum_j F^* sqrt(f_j): when every frame measures
+    |F w|^2 of a probe whose spectrum F w = a is real and positive, sqrt(f_j) = a
+    and the mean of F^* a over the frames is w itself (numpy builds w)."""
+    rng = np.random.default_rng(m)
+    a = 0.1 + rng.random((m, m))
+    w = np.fft.ifft2(a, norm="ortho")
+    f = np.repeat((a * a)[None], 5, axis=0)
+    assert np.abs(oracle.probe_init(f) - w).max() < 1e-12 * np.abs(w).max()
+
+
+def test_probe_init_is_the_mean_over_frames_and_unitary():
+    rng = np.random.default_rng(2)
+    m = 32
+    amps = [rng.random((m, m)) for _ in range(3)]
+    f = np.stack([x * x for x in amps])
+    expect = sum(np.fft.ifft2(x, norm="ortho") for x in amps) / 3.0
+    assert np.abs(oracle.probe_init(f) - expect).max() < 1e-13
+    # one bright zero frequency c^2: F^* gives the constant c / m everywhere
+    g = np.zeros((1, m, m))
+    g[0, 0, 0] = 9.0
+    assert np.abs(oracle.probe_init(g) - 3.0 / m).max() < 1e-15

@@ -7,12 +7,14 @@ Workload (one step = one full ADMM iteration of Algorithm 2, all frames):
 sample (section 4); the measured intensities come from the library's own
 forward operator before timing starts.
 
-Timing: W untimed warm-up iterations, then K timed iterations; before each
-timed iteration a 256 MiB buffer is written to flush the 129 MB L2 (the
-workload's working set would otherwise stay L2-resident), outside the timed
-interval.  Each iteration is bracketed by CUDA events on the launch stream,
-with an extra event between the frame update (the dominant kernel) and the
-subdomain update.  Clocks are sampled with nvidia-smi during the timed region.
+Timing: W untimed warm-up iterations, then K timed iterations, each one
+replay of the iteration's CUDA graph (od2p_iterate); before each timed
+iteration a 256 MiB buffer is written to flush the 129 MB L2 (the workload's
+working set would otherwise stay L2-resident), outside the timed interval.
+Each iteration is bracketed by CUDA events on the launch stream.  The
+roofline's kernel duration comes from up to 500 further iterations launched
+kernel by kernel, with events around the frame update (the dominant kernel)
+and the subdomain update.  Clocks are sampled with nvidia-smi during both.
 
 `e2e` times the public API end to end with host buffers: pinned f (and probe
 and offsets) copied to the device, plan, Step 0, 200 iterations, merge, image
@@ -182,6 +184,7 @@ def e2e_run(od, geom, f, w, offs, p, dev, K, ws, tune=True):
     e2e_times = []
     n_e2e = max(1, min(3, K))
     out_host = torch.empty((p.n, p.n), dtype=torch.complex64).pin_memory()
+    plan_s = None
     for i in range(n_e2e + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -191,6 +194,9 @@ def e2e_run(od, geom, f, w, offs, p, dev, K, ws, tune=True):
         od.od2p_init(pl, wd)
         if tune:
             autotune.tune_plan(pl)  # measured in the untimed first pass, a cache hit afterwards
+        if i == 1:  # one extra synchronisation, to split the set-up from the iterations
+            torch.cuda.synchronize()
+            plan_s = time.perf_counter() - t0
         od.od2p_iterate(pl, p.n_iter)
         u = od.od2p_merge(pl)
         out_host.copy_(u, non_blocking=True)
@@ -203,7 +209,8 @@ def e2e_run(od, geom, f, w, offs, p, dev, K, ws, tune=True):
     return {"value": round(value, 1), "unit": UNIT,
             "h2d_bytes_per_step": int(f.nbytes + w.nbytes + offs.nbytes),
             "d2h_bytes_per_step": int(out_host.numel() * 8),
-            "step": f"one reconstruction: H2D f, plan, init, {p.n_iter} iterations, merge, D2H image"}
+            "step": f"one reconstruction: H2D f, plan, init, {p.n_iter} iterations, merge, D2H image",
+            "setup_ms": round(1e3 * plan_s, 3) if plan_s is not None else None}
 
 
 def batched_leg(od, dev, K: int = 10, W: int = 2, count: int = 64, tune=True, retune=False):
@@ -307,11 +314,11 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         flush.fill_(1.0)
-        od.od2p_frame_update(plan)
-        od.od2p_subdomain_update(plan)
+        od.od2p_iterate(plan, 1)
     torch.cuda.synchronize()
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    evk = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(min(K, 500))]
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -326,18 +333,27 @@ def run_gpu(args):
         for k in range(K):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            od.od2p_frame_update(plan)
+            od.od2p_iterate(plan, 1)  # graph replay: frame update + subdomain update
             ev[k][1].record(stream)
-            od.od2p_subdomain_update(plan)
-            ev[k][2].record(stream)
         torch.cuda.synchronize()
         wall1 = time.perf_counter()
+        # per-kernel durations for the roofline: the same iteration launched one
+        # kernel at a time, events on the launch stream around each kernel
+        Kk = min(K, 500)
+        for k in range(Kk):
+            flush.fill_(float(k))
+            evk[k][0].record(stream)
+            od.od2p_frame_update(plan)
+            evk[k][1].record(stream)
+            od.od2p_subdomain_update(plan)
+            evk[k][2].record(stream)
+        torch.cuda.synchronize()
         clk.mark_end()
     if ws > 1:
         dist.barrier()
-    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
-    k1_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
-    k2_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    step_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    k1_ms = [evk[k][0].elapsed_time(evk[k][1]) for k in range(Kk)]
+    k2_ms = [evk[k][1].elapsed_time(evk[k][2]) for k in range(Kk)]
     total_s = sum(step_ms) / 1e3
     if ws > 1:
         t = torch.tensor([total_s], device=dev)
@@ -366,11 +382,13 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "image": p.n, "probe": p.m, "frames": J, "step_px": p.step,
                    "jitter_px": p.jitter, "subdomains": f"{p.sub_rows}x{p.sub_cols}",
                    "overlap_min_px": p.overlap_px, "poisson_peak": p.peak, "eps": p.eps, "eta": p.eta,
-                   "r": p.r, "step": "one ADMM iteration (Algorithm 2 Steps 1-4, all frames)",
+                   "r": p.r, "step": "one ADMM iteration (Algorithm 2 Steps 1-4, all frames), replayed as a CUDA graph",
                    "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu",
                    "frame_update_ms": round(statistics.mean(k1_ms), 5),
                    "subdomain_update_ms": round(statistics.mean(k2_ms), 5),
+                   "kernel_timing": f"{len(k1_ms)} more iterations launched kernel by kernel (events around "
+                                    "each launch, L2 flushed before each iteration), after the timed steps",
                    "rf_after": rf, "re_after": re,
                    "launch": {"variant": launch[0], "blocks_per_sm": launch[1], "max_blocks_per_sm": launch[2],
                               "tuned": None if tuned is None else

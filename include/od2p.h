@@ -215,6 +215,18 @@ int od2p_merge(const ptycho_plan_t *plan, ptycho_c32 *u_out_dev, ptycho_stream_t
 int od2p_metrics(ptycho_plan_t *plan, float *rf_host, float *re_host, ptycho_stream_t stream);
 
 /*
+ * Data-driven initial probe of the blind experiments (section 4.3):
+ * w0 = (1/J) sum_j F^* sqrt(f_j), from the intensities the plan holds.  The GPU
+ * forms F^* of the mean amplitude (equal by linearity): the amplitudes are
+ * averaged per frequency in ascending j with compensated FP32 addition, then
+ * inverse-transformed by direct (unitary) DFT sums.  w0_dev: m x m, written.
+ * Uses plan scratch (the frame-residual and probe buffers): do not overlap with
+ * other calls on the plan.  Pass the result to od2p_init as w0 for a blind run.
+ * Errors: INVALID_ARG, CUDA.
+ */
+int ptycho_probe_init(ptycho_plan_t *plan, ptycho_c32 *w0_dev, ptycho_stream_t stream);
+
+/*
  * Launch shape of the frame update (the paper fixes none).  For m <= 128 two
  * shapes are compiled, each a (frames per block, threads per block) pair:
  *   m = 16: variant 0 (8, 256), variant 1 (4, 128);  m = 32: (4, 256), (2, 128);

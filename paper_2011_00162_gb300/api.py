@@ -23,7 +23,7 @@ __all__ = [
     "od2p_metrics", "od2p_get_state", "od2p_set_state", "stagm_loss_grad", "PtychoError",
     "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
-    "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS",
+    "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
 ]
 
 LAUNCH_VARIANTS = _lib.LAUNCH_VARIANTS
@@ -206,6 +206,15 @@ def ptycho_batch_plan(geoms: list, fs: list, stream=None) -> Batch:
 
 def ptycho_batch_iterate(batch: Batch, n_iter: int = 1, stream=None) -> None:
     batch.iterate(n_iter, stream)
+
+
+def ptycho_probe_init(plan: Plan, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """w0 = (1/J) sum_j F^* sqrt(f_j) (m x m complex64) from the plan's intensities."""
+    m = plan.geom.m
+    if out is None:
+        out = _c64((m, m), plan.device)
+    check(plan._lib.ptycho_probe_init(plan.handle, _ptr(out, torch.complex64, "w0"), _stream(stream)))
+    return out
 
 
 def ptycho_plan_set_launch(plan: Plan, variant: int, blocks_per_sm: int = 0, stream=None) -> None:

@@ -11,6 +11,20 @@ namespace {
 // per component exactly a + b and a - b (b * -1 is exact, one rounding).
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+#ifdef OD2P_PACKED_CMUL
+// a * b as one packed multiply and one packed fused multiply-add:
+// (a.x b.x, a.x b.y) + a.y (-b.y, b.x)
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return __ffma2_rn(make_float2(a.y, a.y), make_float2(-b.y, b.x), __fmul2_rn(make_float2(a.x, a.x), b));
+}
+// a * conj(b) = (a.x b.x, -a.x b.y) + a.y (b.y, b.x)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+{
+    return __ffma2_rn(make_float2(a.y, a.y), make_float2(b.y, b.x),
+                      __fmul2_rn(make_float2(a.x, a.x), make_float2(b.x, -b.y)));
+}
+#else
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -20,6 +34,7 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)
 {
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
+#endif
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
 __host__ __device__ constexpr int brev(int i, int bits)

@@ -348,6 +348,8 @@ __global__ void __launch_bounds__(K1Cfg<M, V>::NT, K1Cfg<M, V>::MINB)
         mbar_expect_tx(bar, fbytes + gbytes);
         if (SG) bulk_g2s(stg_g, ga.gamma + (size_t)j0 * MM, gbytes, bar);
         bulk_g2s(stg_f, ga.sqrtf_ + (size_t)j0 * MM, fbytes, bar);
+        // the slot ranks are read at the end of the item: bring them into L2 now
+        if (ga.slot) bulk_prefetch_l2(ga.rank + (size_t)j0 * MM, (unsigned)(nf * MM));
     };
     auto prefetch_windows = [&](int i) {  // all threads: item i's exit-wave windows into L2
         constexpr int LINES = (M * 8 + 127) / 128 + 1;

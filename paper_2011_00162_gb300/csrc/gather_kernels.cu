@@ -525,6 +525,67 @@ __global__ void prox_kernel(const float2 *y, const float *f, float2 *z, int64_t 
     }
 }
 
+// ---- data-driven initial probe (section 4.3): w0 = (1/J) sum_j F^* sqrt(f_j),
+// formed as F^* of the mean amplitude (the inverse DFT is linear).
+
+// Mean measured amplitude per frequency, natural order.  One thread per stored
+// element (coalesced over frames); the J frames are added in ascending j with
+// compensated (Kahan) FP32 addition.  Storage index s holds position (pr, pc)
+// at s = pc m + pr (transposed) or pr m + pc (row_major); position p holds
+// frequency p / R2 + R1 (p % R2).
+__global__ void amp_mean_kernel(int J, int M, int R1, int R2, int row_major, const float *__restrict__ sqrtf_,
+                                float *__restrict__ amp)
+{
+    const int MM = M * M;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < MM; s += gridDim.x * blockDim.x) {
+        float sum = 0.f, c = 0.f;
+        for (int j = 0; j < J; ++j) {
+            const float y = sqrtf_[(size_t)j * MM + s] - c;
+            const float t = sum + y;
+            c = (t - sum) - y;
+            sum = t;
+        }
+        const int a = s / M, b = s % M;
+        const int pr = row_major ? a : b, pc = row_major ? b : a;
+        const int kr = pr / R2 + R1 * (pr % R2), kc = pc / R2 + R1 * (pc % R2);
+        amp[kr * M + kc] = sum / (float)J;
+    }
+}
+
+// T[kr][c] = sum_kc amp[kr][kc] exp(+2 pi i kc c / M) (direct sum, kc ascending)
+__global__ void idft_rows_kernel(int M, const float *__restrict__ amp, const float2 *__restrict__ tw,
+                                 float2 *__restrict__ T)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * M) return;
+    const int kr = e / M, c = e % M;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int kc = 0; kc < M; ++kc) {
+        const float2 t = tw[(kc * c) % M];  // exp(-2 pi i kc c / M); conjugated below
+        const float v = amp[kr * M + kc];
+        acc.x += v * t.x;
+        acc.y -= v * t.y;
+    }
+    T[e] = acc;
+}
+
+// w0[r][c] = (1/M) sum_kr T[kr][c] exp(+2 pi i kr r / M) (kr ascending)
+__global__ void idft_cols_kernel(int M, const float2 *__restrict__ T, const float2 *__restrict__ tw,
+                                 float2 *__restrict__ w0)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * M) return;
+    const int r = e / M, c = e % M;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int kr = 0; kr < M; ++kr) {
+        const float2 t = tw[(kr * r) % M];
+        const float2 v = T[kr * M + c];
+        acc.x += v.x * t.x + v.y * t.y;  // v * conj(t)
+        acc.y += v.y * t.x - v.x * t.y;
+    }
+    w0[e] = make_float2(acc.x / (float)M, acc.y / (float)M);
+}
+
 }  // namespace
 
 void fill_sub_args(const ptycho_plan_s *p, SubArgs out[2])
@@ -628,6 +689,28 @@ int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, c
 int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s)
 {
     loss_sum_kernel<<<1, 256, 0, s>>>(p->n_loss_blocks, p->d_loss_part, loss);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_probe_init(ptycho_plan_s *p, float2 *w0, cudaStream_t s)
+{
+    int R1 = 16, R2 = 16, row_major = 1;  // m = 256
+    switch (p->M) {
+    case 16: R1 = 4, R2 = 4, row_major = 0; break;
+    case 32: R1 = 8, R2 = 4, row_major = 0; break;
+    case 64: R1 = 8, R2 = 8, row_major = 0; break;
+    case 128: R1 = 16, R2 = 8, row_major = 0; break;
+    default: break;
+    }
+    float *amp = reinterpret_cast<float *>(p->d_q);  // plan scratch: MM floats
+    float2 *T = p->d_wnew;                           // plan scratch: MM complex
+    const int blocks = (p->MM + 255) / 256;
+    amp_mean_kernel<<<blocks, 256, 0, s>>>(p->J, p->M, R1, R2, row_major, p->d_sqrtf, amp);
+    OD2P_CUDA(cudaGetLastError());
+    idft_rows_kernel<<<blocks, 256, 0, s>>>(p->M, amp, p->d_tw, T);
+    OD2P_CUDA(cudaGetLastError());
+    idft_cols_kernel<<<blocks, 256, 0, s>>>(p->M, T, p->d_tw, w0);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }

@@ -646,6 +646,12 @@ int od2p_metrics(ptycho_plan_t *plan, float *rf, float *re, ptycho_stream_t stre
     return PTYCHO_OK;
 }
 
+int ptycho_probe_init(ptycho_plan_t *plan, ptycho_c32 *w0_dev, ptycho_stream_t stream)
+{
+    if (!plan || !w0_dev) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    return launch_probe_init(plan, reinterpret_cast<float2 *>(w0_dev), reinterpret_cast<cudaStream_t>(stream));
+}
+
 int ptycho_plan_set_launch(ptycho_plan_t *plan, int32_t variant, int32_t blocks_per_sm, ptycho_stream_t stream)
 {
     if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");

@@ -414,3 +414,22 @@ def test_blind_workload_1024_full_size():
            grad_w=rel_l2(host(gw), gw_o))
     assert abs(float(loss.item()) - L) < 1e-5 * abs(L)
     assert rel_l2(host(gu), gu_o) < 1e-5 and rel_l2(host(gw), gw_o) < 1e-5
+
+
+@pytest.mark.parametrize("m,n,step", [(16, 64, 4), (32, 100, 9), (64, 300, 16), (128, 384, 48), (256, 512, 96)])
+def test_probe_init_matches_oracle(m, n, step):
+    """Section 4.3's data-driven initial probe from a plan's intensities."""
+    p = synth.Problem("pi", n, m, step, 1, 2, 2, 8, 1e4, 1, seed=m)
+    offs, u_true, w, f = make_case(p)
+    plan = od.ptycho_plan(geom_of(p, offs), f32(f))
+    w0 = host(od.ptycho_probe_init(plan))
+    ref = oracle.probe_init(f.astype(np.float64))
+    err = rel_l2(w0, ref)
+    record(f"probe_init_m{m}", w0=err)
+    assert err < ONE_ITER_TOL
+    # a probe whose spectrum is real and positive is recovered exactly (up to FP32)
+    rng = np.random.default_rng(m)
+    a = (0.1 + rng.random((m, m))).astype(np.float32)
+    fa = np.repeat((a.astype(np.float64) ** 2)[None], len(offs), axis=0).astype(np.float32)
+    plan2 = od.ptycho_plan(geom_of(p, offs), f32(fa))
+    assert rel_l2(host(od.ptycho_probe_init(plan2)), np.fft.ifft2(a.astype(np.float64), norm="ortho")) < ONE_ITER_TOL

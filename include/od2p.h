@@ -107,6 +107,16 @@ const char *ptycho_last_error(void);
 int32_t ptycho_abi_version(void);
 
 /*
+ * Device memory of plans and batches comes from one stream-ordered pool per
+ * device that keeps memory freed by ptycho_plan_destroy / ptycho_batch_destroy
+ * for the next plan, so repeated reconstructions of one workload allocate
+ * nothing new from the driver.  This call synchronises the current device and
+ * returns the pool's unused memory to the driver (memory of live plans stays).
+ * Errors: CUDA, UNSUPPORTED (device ordinal above 63).
+ */
+int ptycho_release_cached_memory(void);
+
+/*
  * Build a plan: validate g, compute the decomposition, allocate plan-owned
  * device state, and ingest the measured intensities f (J x m x m FP32,
  * natural frequency order, f >= 0).  f_dev is read during this call only (the

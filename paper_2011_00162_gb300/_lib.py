@@ -40,6 +40,7 @@ class Geometry(ctypes.Structure):
 SIGNATURES = {
     "ptycho_last_error": (ctypes.c_char_p, []),
     "ptycho_abi_version": (_I32, []),
+    "ptycho_release_cached_memory": (ctypes.c_int, []),
     "ptycho_plan": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), _P, _P]),
     "ptycho_plan_destroy": (ctypes.c_int, [_P]),
     "ptycho_plan_dims": (ctypes.c_int, [_P, _P, _P, _P, _P]),

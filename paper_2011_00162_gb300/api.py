@@ -20,10 +20,11 @@ from ._lib import (OA_IFFT, STATE_DELTA, STATE_GAMMA, STATE_LAMBDA, STATE_Q, STA
 __all__ = [
     "Geometry", "Plan", "ptycho_plan", "ptycho_forward", "stagm_prox", "overlap_add", "od2p_init",
     "od2p_iterate", "od2p_frame_update", "od2p_subdomain_update", "probe_update", "od2p_merge",
-    "od2p_metrics", "od2p_get_state", "od2p_set_state", "stagm_loss_grad", "PtychoError",
+    "od2p_metrics", "od2p_state_len", "od2p_get_state", "od2p_set_state", "stagm_loss_grad", "PtychoError",
     "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
     "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
+    "ptycho_release_cached_memory",
 ]
 
 LAUNCH_VARIANTS = _lib.LAUNCH_VARIANTS
@@ -206,6 +207,11 @@ def ptycho_batch_plan(geoms: list, fs: list, stream=None) -> Batch:
 
 def ptycho_batch_iterate(batch: Batch, n_iter: int = 1, stream=None) -> None:
     batch.iterate(n_iter, stream)
+
+
+def ptycho_release_cached_memory() -> None:
+    """Return the plan memory pool's unused device memory to the driver."""
+    check(_lib.load().ptycho_release_cached_memory())
 
 
 def ptycho_probe_init(plan: Plan, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -442,6 +442,40 @@ __global__ void __launch_bounds__(GATHER_THREADS) illumination_kernel(int M, con
     }
 }
 
+// Gather slots of a nonblind plan: the rank of every frame pixel among the
+// frames of its subdomain that cover the same subdomain pixel (ascending j: the
+// tile lists are ascending), and the number of covering frames per pixel.  Each
+// frame pixel lies in exactly one tile of its own subdomain, so every rank is
+// written once.  setup[0] is set when a pixel has more than 255 frames, setup[1]
+// receives the largest count (atomicMax: an integer maximum, order-free).
+__global__ void __launch_bounds__(GATHER_THREADS) slot_rank_kernel(int M, const TileInfo *tinfo,
+                                                                   const ListEntry *tlist, uint8_t *rank,
+                                                                   uint8_t *cnt, int32_t *setup)
+{
+    const TileInfo ti = tinfo[blockIdx.x];
+    const int lane = threadIdx.x & 31, ty0 = (threadIdx.x >> 5) * TILE_ROWS;
+    if (lane >= ti.ncols) return;
+    const int MM = M * M;
+    int most = 0;
+    for (int r = 0; r < TILE_ROWS && ty0 + r < ti.nrows; ++r) {
+        int n = 0;
+        for (int k = 0; k < ti.nk; ++k) {
+            const ListEntry e = tlist[ti.k0 + k];
+            const int dr = e.dr + ty0 + r, dc = e.dc + lane;
+            if ((unsigned)dr < (unsigned)M && (unsigned)dc < (unsigned)M) {
+                if (n == 255) {
+                    setup[0] = 1;
+                    break;
+                }
+                rank[(size_t)e.j * MM + dr * M + dc] = (uint8_t)n++;
+            }
+        }
+        cnt[ti.u0 + (ty0 + r) * ti.pitch + lane] = (uint8_t)n;
+        most = max(most, n);
+    }
+    if (most > 0) atomicMax(setup + 1, most);
+}
+
 // Frames of the nonblind gather slots back in frame layout (for state export).
 __global__ void q_from_slots_kernel(int J, int M, const float2 *slot, const uint8_t *rank, int stride,
                                     const int32_t *frame_base, const int32_t *frame_pitch, float2 *q)
@@ -745,6 +779,14 @@ int launch_illumination(ptycho_plan_s *p, cudaStream_t s)
 {
     illumination_kernel<<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(
         p->M, p->d_rect, p->d_u_off, p->sub_tiles.tiles, p->sub_tiles.ptr, p->sub_tiles.list, p->d_w, p->d_nrm);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_slot_rank(ptycho_plan_s *p, int32_t *setup, cudaStream_t s)
+{
+    slot_rank_kernel<<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(p->M, p->sub_tiles.info, p->sub_tiles.list,
+                                                                      p->d_rank, p->d_cnt, setup);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -27,26 +28,67 @@ int cuda_fail(cudaError_t e, const char *what)
 
 namespace {
 
+// Plans and batches take their device memory from one stream-ordered pool per
+// device that keeps what they free (release threshold: unlimited), so that
+// creating and destroying plans of a repeated workload asks the driver for no
+// new memory.  ptycho_release_cached_memory hands the cached part back.
+constexpr int MAX_DEVICES = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[MAX_DEVICES] = {};
+
+int device_pool(cudaMemPool_t *out)
+{
+    int dev = 0;
+    OD2P_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(PTYCHO_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        OD2P_CUDA(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = ~0ull;
+        OD2P_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return PTYCHO_OK;
+}
+
+// count elements of T from the pool, ordered on stream s (usable on other
+// streams once s has been synchronised); recorded in `owned` for release
 template <class T>
-int dev_alloc(T **ptr, size_t count, std::vector<void *> &owned)
+int dev_alloc(T **ptr, size_t count, std::vector<void *> &owned, cudaStream_t s)
 {
     *ptr = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)ptr, sizeof(T) * count);
+    cudaMemPool_t pool = nullptr;
+    if (int rc = device_pool(&pool)) return rc;
+    cudaError_t e = cudaMallocFromPoolAsync((void **)ptr, sizeof(T) * count, pool, s);
     if (e != cudaSuccess) {
         *ptr = nullptr;
         cudaGetLastError();
-        return fail(PTYCHO_ERR_OOM, "cudaMalloc of " + std::to_string(sizeof(T) * count) +
+        return fail(PTYCHO_ERR_OOM, "device allocation of " + std::to_string(sizeof(T) * count) +
                                         " bytes failed: " + cudaGetErrorString(e));
     }
     owned.push_back((void *)*ptr);
     return PTYCHO_OK;
 }
 
+// Return plan memory to the pool after the device has finished with it.
+void release_owned(std::vector<void *> &owned)
+{
+    for (void *ptr : owned) cudaFreeAsync(ptr, nullptr);
+    owned.clear();
+    cudaStreamSynchronize(nullptr);
+}
+
 template <class T>
 int upload(T **dst, const std::vector<T> &src, std::vector<void *> &owned, cudaStream_t s)
 {
-    if (int rc = dev_alloc(dst, src.size(), owned)) return rc;
+    if (int rc = dev_alloc(dst, src.size(), owned, s)) return rc;
     if (!src.empty())
         OD2P_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
     return PTYCHO_OK;
@@ -260,6 +302,15 @@ const char *ptycho_last_error(void) { return od2p::g_err.c_str(); }
 
 int32_t ptycho_abi_version(void) { return 1; }
 
+int ptycho_release_cached_memory(void)
+{
+    cudaMemPool_t pool = nullptr;
+    if (int rc = device_pool(&pool)) return rc;
+    OD2P_CUDA(cudaDeviceSynchronize());
+    OD2P_CUDA(cudaMemPoolTrimTo(pool, 0));
+    return PTYCHO_OK;
+}
+
 int ptycho_plan_destroy(ptycho_plan_t *plan)
 {
     if (!plan) return PTYCHO_OK;
@@ -268,7 +319,7 @@ int ptycho_plan_destroy(ptycho_plan_t *plan)
     for (int i = 0; i < 2; ++i)
         if (p->graph[i]) cudaGraphExecDestroy(p->graph[i]);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-    for (void *ptr : p->owned) cudaFree(ptr);
+    release_owned(p->owned);
     delete p;
     cudaGetLastError();
     return PTYCHO_OK;
@@ -378,23 +429,6 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
                                   Pr[0], Pr[1], Pr[3] - Pr[1], (int32_t)p->lam_off[kde],
                                   (int32_t)p->lam_off[ked], d < e ? 1 : 0};
         }
-    // nonblind: rank of each frame pixel among the frames covering that subdomain
-    // pixel (ascending j), and the number of covering frames per pixel
-    std::vector<uint8_t> rank, cnt;
-    if (!p->blind) {
-        rank.resize((size_t)J * p->MM);
-        cnt.assign((size_t)p->u_len, 0);
-        for (int j = 0; j < J; ++j)
-            for (int r = 0; r < m; ++r)
-                for (int c = 0; c < m; ++c) {
-                    uint8_t &n = cnt[(size_t)frame_base[j] + (size_t)r * frame_pitch[j] + c];
-                    if (n == 255) return bail(fail(PTYCHO_ERR_UNSUPPORTED, "more than 255 frames cover one pixel"));
-                    rank[(size_t)j * p->MM + r * m + c] = n++;
-                }
-        p->slot_k = *std::max_element(cnt.begin(), cnt.end());
-        if ((int64_t)p->slot_k * p->u_len >= (1LL << 32))
-            return bail(fail(PTYCHO_ERR_UNSUPPORTED, "gather slot storage exceeds 2^32 elements"));
-    }
     HostTiles st = make_tiles(p->D, p->rect, sub_frames, p->offs, m);
     // neighbours of each subdomain tile whose rectangle meets the tile
     std::vector<int32_t> tile_nbr_ptr(1, 0);
@@ -461,28 +495,44 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         return bail(rc);
     p->n_loss_blocks = m == 256 ? J * 16 : (J + frames_per_block(m) - 1) / frames_per_block(m);
     const int n_chunks = std::max(p->sub_groups.n_chunks, p->img_groups.n_chunks);
-    if ((rc = dev_alloc(&p->d_sqrtf, JMM, own)) || (rc = dev_alloc(&p->d_gamma, JMM, own)) ||
-        (rc = dev_alloc(&p->d_q, JMM, own)) || (rc = dev_alloc(&p->d_u[0], p->u_len, own)) ||
-        (rc = dev_alloc(&p->d_u[1], p->u_len, own)) || (rc = dev_alloc(&p->d_nrm, p->u_len, own)) ||
-        (rc = dev_alloc(&p->d_lam[0], p->lam_len, own)) ||
-        (rc = dev_alloc(&p->d_lam[1], p->lam_len, own)) || (rc = dev_alloc(&p->d_w, p->MM, own)) ||
-        (rc = dev_alloc(&p->d_wnew, p->MM, own)) ||
-        (rc = dev_alloc(&p->d_probe_part, (size_t)n_chunks * p->MM, own)) ||
-        (rc = dev_alloc(&p->d_probe_part_n, (size_t)n_chunks * p->MM, own)) ||
-        (rc = dev_alloc(&p->d_rf_part, rf_cap, own)) ||
-        (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own)) ||
-        (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own)) ||
-        (rc = dev_alloc(&p->d_metrics, 3, own)) || (rc = dev_alloc(&p->d_err, 1, own)))
+    if ((rc = dev_alloc(&p->d_sqrtf, JMM, own, s)) || (rc = dev_alloc(&p->d_gamma, JMM, own, s)) ||
+        (rc = dev_alloc(&p->d_q, JMM, own, s)) || (rc = dev_alloc(&p->d_u[0], p->u_len, own, s)) ||
+        (rc = dev_alloc(&p->d_u[1], p->u_len, own, s)) || (rc = dev_alloc(&p->d_nrm, p->u_len, own, s)) ||
+        (rc = dev_alloc(&p->d_lam[0], p->lam_len, own, s)) ||
+        (rc = dev_alloc(&p->d_lam[1], p->lam_len, own, s)) || (rc = dev_alloc(&p->d_w, p->MM, own, s)) ||
+        (rc = dev_alloc(&p->d_wnew, p->MM, own, s)) ||
+        (rc = dev_alloc(&p->d_probe_part, (size_t)n_chunks * p->MM, own, s)) ||
+        (rc = dev_alloc(&p->d_probe_part_n, (size_t)n_chunks * p->MM, own, s)) ||
+        (rc = dev_alloc(&p->d_rf_part, rf_cap, own, s)) ||
+        (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own, s)) ||
+        (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own, s)) ||
+        (rc = dev_alloc(&p->d_metrics, 3, own, s)) || (rc = dev_alloc(&p->d_err, 1, own, s)))
         return bail(rc);
     if (p->blind) {
-        if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own)))
+        if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own, s)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own, s)))
             return bail(rc);
     }
-    if (m == 256 && (rc = dev_alloc(&p->d_T, (size_t)WAVE_256 * p->MM, own))) return bail(rc);
+    if (m == 256 && (rc = dev_alloc(&p->d_T, (size_t)WAVE_256 * p->MM, own, s))) return bail(rc);
     if (!p->blind) {
-        if ((rc = upload(&p->d_rank, rank, own, s)) || (rc = upload(&p->d_cnt, cnt, own, s)) ||
-            (rc = dev_alloc(&p->d_slot, (size_t)std::max(p->slot_k, 1) * p->u_len, own)))
+        // gather slots: ranks and counts on the device (one pass over the tile
+        // lists), then the slot array sized by the largest count
+        int32_t *d_setup = nullptr, h_setup[2] = {0, 0};
+        if ((rc = dev_alloc(&p->d_rank, JMM, own, s)) || (rc = dev_alloc(&p->d_cnt, (size_t)p->u_len, own, s)) ||
+            (rc = dev_alloc(&d_setup, 2, own, s)))
             return bail(rc);
+        cudaError_t e1;
+        if ((e1 = cudaMemsetAsync(p->d_cnt, 0, (size_t)p->u_len, s)) != cudaSuccess ||
+            (e1 = cudaMemsetAsync(d_setup, 0, 2 * sizeof(int32_t), s)) != cudaSuccess)
+            return bail(cuda_fail(e1, "cudaMemsetAsync"));
+        if ((rc = launch_slot_rank(p, d_setup, s))) return bail(rc);
+        if ((e1 = cudaMemcpyAsync(h_setup, d_setup, sizeof(h_setup), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e1 = cudaStreamSynchronize(s)) != cudaSuccess)
+            return bail(cuda_fail(e1, "slot ranks"));
+        if (h_setup[0]) return bail(fail(PTYCHO_ERR_UNSUPPORTED, "more than 255 frames cover one pixel"));
+        p->slot_k = h_setup[1];
+        if ((int64_t)p->slot_k * p->u_len >= (1LL << 32))
+            return bail(fail(PTYCHO_ERR_UNSUPPORTED, "gather slot storage exceeds 2^32 elements"));
+        if ((rc = dev_alloc(&p->d_slot, (size_t)std::max(p->slot_k, 1) * p->u_len, own, s))) return bail(rc);
     }
     cudaError_t e;
     if ((e = cudaMemsetAsync(p->d_metrics, 0, 3 * sizeof(double), s)) != cudaSuccess ||
@@ -783,7 +833,7 @@ int ptycho_batch_destroy(ptycho_batch_t *b)
     for (int i = 0; i < 2; ++i)
         if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    for (void *ptr : b->owned) cudaFree(ptr);
+    release_owned(b->owned);
     for (ptycho_plan_s *p : b->plans) ptycho_plan_destroy(p);
     delete b;
     cudaGetLastError();

@@ -433,3 +433,25 @@ def test_probe_init_matches_oracle(m, n, step):
     fa = np.repeat((a.astype(np.float64) ** 2)[None], len(offs), axis=0).astype(np.float32)
     plan2 = od.ptycho_plan(geom_of(p, offs), f32(fa))
     assert rel_l2(host(od.ptycho_probe_init(plan2)), np.fft.ifft2(a.astype(np.float64), norm="ortho")) < ONE_ITER_TOL
+
+
+def test_plans_reuse_pooled_memory_bitwise():
+    """Plans take device memory from a pool that keeps what destroyed plans free;
+    a plan built on reused (dirty) memory computes exactly what a fresh one does."""
+    p = synth.grid_4x4()
+    offs, u_true, w, f = make_case(p)
+    outs = []
+    for k in range(3):
+        if k == 2:
+            od.ptycho_release_cached_memory()
+        plan = od.ptycho_plan(geom_of(p, offs), f32(f))
+        od.od2p_init(plan, c64(w))
+        od.od2p_iterate(plan, 3)
+        outs.append([host(od.od2p_get_state(plan, s)) for s in (od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA)])
+        # scribble over the plan's memory before it goes back to the pool
+        od.od2p_set_state(plan, od.STATE_GAMMA, torch.full((od.od2p_state_len(plan, od.STATE_GAMMA),), 7 + 7j,
+                                                           dtype=torch.complex64, device=DEV))
+        plan.close()
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)

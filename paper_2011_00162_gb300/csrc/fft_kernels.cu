@@ -207,17 +207,59 @@ __device__ __forceinline__ void col_stage1_store(float2 *buf, const float2 *tw, 
     }
 }
 
+// Slot ranks of a thread's column tasks, loaded at the start of a frame group
+// and used at its end (the loads complete while the FFT runs).  Ranks are
+// stored in task order: task (n1, c) of frame j holds the R1 ranks of rows
+// n1 + R2 t, t < R1, at rank[j m^2 + (n1 m + c) R1 + t].
+template <int M, int FPB, int NT>
+struct SlotRanks {
+    static constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2;
+    static constexpr int TASKS = FPB * M * R2, TPT = (TASKS + NT - 1) / NT, WPT = R1 / 4;
+    static_assert(R1 % 4 == 0, "ranks are loaded four at a time");
+    uint32_t w[TPT][WPT];
+
+    __device__ __forceinline__ void load(const uint8_t *rank, int j0, int J)
+    {
+#pragma unroll
+        for (int i = 0; i < TPT; ++i) {
+            const int task = threadIdx.x + i * NT;
+            const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
+            const bool ok = task < TASKS && j < J;
+            const uint8_t *src = rank + (size_t)(ok ? j : 0) * M * M + ((size_t)n1 * M + c) * R1;
+            if constexpr (WPT == 1) {
+                w[i][0] = ok ? __ldg(reinterpret_cast<const uint32_t *>(src)) : 0u;
+            } else if constexpr (WPT == 2) {
+                const uint2 v = ok ? __ldg(reinterpret_cast<const uint2 *>(src)) : make_uint2(0u, 0u);
+                w[i][0] = v.x;
+                w[i][1] = v.y;
+            } else {
+                static_assert(WPT == 4, "R1 is 4, 8 or 16");
+                const uint4 v = ok ? __ldg(reinterpret_cast<const uint4 *>(src)) : make_uint4(0u, 0u, 0u, 0u);
+                w[i][0] = v.x;
+                w[i][1] = v.y;
+                w[i][2] = v.z;
+                w[i][3] = v.w;
+            }
+        }
+    }
+    __device__ __forceinline__ unsigned get(int i, int t) const { return (w[i][t / 4] >> (8 * (t % 4))) & 0xffu; }
+};
+
 // Column stage 1^H writing conj(w) o (natural-order frame) into the gather
 // slots: frame j's pixel (row, c) goes to slot[rank * stride + base_j + row *
-// pitch_j + c].
+// pitch_j + c], the ranks taken from the preloaded registers.
 template <int M, int FPB, int NT>
 __device__ __forceinline__ void col_stage1_store_slots(float2 *buf, const float2 *tw, int j0, int J,
-                                                       float2 *slot, const uint8_t *rank, int stride,
+                                                       float2 *slot, const SlotRanks<M, FPB, NT> &rk, int stride,
                                                        const int32_t *frame_base, const int32_t *frame_pitch,
                                                        float scale, const float2 *w)
 {
-    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, P = M + 1, MM = M * M;
-    for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
+    constexpr int R1 = Radix<M>::R1, R2 = Radix<M>::R2, P = M + 1;
+    constexpr int TASKS = FPB * M * R2, TPT = SlotRanks<M, FPB, NT>::TPT;
+#pragma unroll
+    for (int i = 0; i < TPT; ++i) {
+        const int task = threadIdx.x + i * NT;
+        if (task >= TASKS) break;
         const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
         if (j >= J) continue;
         float2 *fb = buf + f * M * P;
@@ -226,13 +268,12 @@ __device__ __forceinline__ void col_stage1_store_slots(float2 *buf, const float2
         for (int s = 0; s < R1; ++s) x[s] = cmulc(fb[(n1 + R2 * s) * P + c], tw[n1 * s]);
         dft<R1, true>(x);
         const unsigned base = (unsigned)(frame_base[j] + c), pitch = (unsigned)frame_pitch[j];
-        const uint8_t *rk = rank + j * MM + c;
 #pragma unroll
         for (int t = 0; t < R1; ++t) {
             const int row = n1 + R2 * t;
             const float2 v = cmulc(cscale(x[t], scale), __ldg(w + row * M + c));
             // 32-bit index: the plan checks slot_k * u_len < 2^32
-            slot[(unsigned)__ldg(rk + row * M) * (unsigned)stride + base + (unsigned)row * pitch] = v;
+            slot[rk.get(i, t) * (unsigned)stride + base + (unsigned)row * pitch] = v;
         }
     }
 }
@@ -348,7 +389,7 @@ __global__ void __launch_bounds__(K1Cfg<M, V>::NT, K1Cfg<M, V>::MINB)
         mbar_expect_tx(bar, fbytes + gbytes);
         if (SG) bulk_g2s(stg_g, ga.gamma + (size_t)j0 * MM, gbytes, bar);
         bulk_g2s(stg_f, ga.sqrtf_ + (size_t)j0 * MM, fbytes, bar);
-        // the slot ranks are read at the end of the item: bring them into L2 now
+        // the next group's slot ranks, loaded at the start of that group
         if (ga.slot) bulk_prefetch_l2(ga.rank + (size_t)j0 * MM, (unsigned)(nf * MM));
     };
     auto prefetch_windows = [&](int i) {  // all threads: item i's exit-wave windows into L2
@@ -394,6 +435,8 @@ __global__ void __launch_bounds__(K1Cfg<M, V>::NT, K1Cfg<M, V>::MINB)
         }
         // Step 1: psi = w o S_j u_d^n, then F psi (three of the four forward stages)
         col_stage1_load<M, FPB, NT>(buf, tw, j0, sa.J, sa.w, sa.Wd, sa.frame_sub, sa.u, sa.frame_base, sa.frame_pitch);
+        SlotRanks<M, FPB, NT> ranks;
+        if (sa.slot) ranks.load(sa.rank, j0, sa.J);
         __syncthreads();
         col_stage2<M, false, FPB, NT>(buf);
         __syncthreads();
@@ -446,7 +489,7 @@ __global__ void __launch_bounds__(K1Cfg<M, V>::NT, K1Cfg<M, V>::MINB)
         if (sa.slot) {
             // nonblind: q_j = conj(w) o F^*(z - Gamma) (the A_d^* summand), stored in
             // the gather slot of each pixel
-            col_stage1_store_slots<M, FPB, NT>(buf, tw, j0, sa.J, sa.slot, sa.rank, sa.slot_stride, sa.frame_base,
+            col_stage1_store_slots<M, FPB, NT>(buf, tw, j0, sa.J, sa.slot, ranks, sa.slot_stride, sa.frame_base,
                                                sa.frame_pitch, inv_m, sa.w);
         } else {
             // blind: unweighted; the subdomain update weights with W_d^{n+1}
@@ -861,6 +904,17 @@ int permute_m(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_na
 }  // namespace
 
 bool supported_m(int m) { return m == 16 || m == 32 || m == 64 || m == 128 || m == 256; }
+
+void rank_radix(int m, int *R1, int *R2)
+{
+    switch (m) {
+    case 16: *R1 = Radix<16>::R1, *R2 = Radix<16>::R2; break;
+    case 32: *R1 = Radix<32>::R1, *R2 = Radix<32>::R2; break;
+    case 64: *R1 = Radix<64>::R1, *R2 = Radix<64>::R2; break;
+    case 128: *R1 = Radix<128>::R1, *R2 = Radix<128>::R2; break;
+    default: *R1 = *R2 = 0; break;
+    }
+}
 
 int frames_per_block(int m)
 {

@@ -442,13 +442,22 @@ __global__ void __launch_bounds__(GATHER_THREADS) illumination_kernel(int M, con
     }
 }
 
+// Offset of frame pixel (row, col) in a frame's slot ranks.  m <= 128: task
+// order -- the frame update's column task (n1 = row % R2, col) holds the R1
+// ranks of rows n1, n1 + R2, ... contiguously, so that one thread loads them
+// with one vector load; m = 256 (R1 = 0): natural row-major order.
+__device__ __forceinline__ int rank_offset(int M, int R1, int R2, int row, int col)
+{
+    return R1 ? ((row % R2) * M + col) * R1 + row / R2 : row * M + col;
+}
+
 // Gather slots of a nonblind plan: the rank of every frame pixel among the
 // frames of its subdomain that cover the same subdomain pixel (ascending j: the
 // tile lists are ascending), and the number of covering frames per pixel.  Each
 // frame pixel lies in exactly one tile of its own subdomain, so every rank is
 // written once.  setup[0] is set when a pixel has more than 255 frames, setup[1]
 // receives the largest count (atomicMax: an integer maximum, order-free).
-__global__ void __launch_bounds__(GATHER_THREADS) slot_rank_kernel(int M, const TileInfo *tinfo,
+__global__ void __launch_bounds__(GATHER_THREADS) slot_rank_kernel(int M, int R1, int R2, const TileInfo *tinfo,
                                                                    const ListEntry *tlist, uint8_t *rank,
                                                                    uint8_t *cnt, int32_t *setup)
 {
@@ -467,7 +476,7 @@ __global__ void __launch_bounds__(GATHER_THREADS) slot_rank_kernel(int M, const 
                     setup[0] = 1;
                     break;
                 }
-                rank[(size_t)e.j * MM + dr * M + dc] = (uint8_t)n++;
+                rank[(size_t)e.j * MM + rank_offset(M, R1, R2, dr, dc)] = (uint8_t)n++;
             }
         }
         cnt[ti.u0 + (ty0 + r) * ti.pitch + lane] = (uint8_t)n;
@@ -477,14 +486,15 @@ __global__ void __launch_bounds__(GATHER_THREADS) slot_rank_kernel(int M, const 
 }
 
 // Frames of the nonblind gather slots back in frame layout (for state export).
-__global__ void q_from_slots_kernel(int J, int M, const float2 *slot, const uint8_t *rank, int stride,
-                                    const int32_t *frame_base, const int32_t *frame_pitch, float2 *q)
+__global__ void q_from_slots_kernel(int J, int M, int R1, int R2, const float2 *slot, const uint8_t *rank,
+                                    int stride, const int32_t *frame_base, const int32_t *frame_pitch, float2 *q)
 {
     const int MM = M * M;
     const size_t n = (size_t)J * MM;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e / MM), k = (int)(e % MM);
-        q[e] = slot[(size_t)rank[e] * stride + frame_base[j] + (k / M) * frame_pitch[j] + (k % M)];
+        const int j = (int)(e / MM), k = (int)(e % MM), row = k / M, col = k % M;
+        const int rk = rank[(size_t)j * MM + rank_offset(M, R1, R2, row, col)];
+        q[e] = slot[(size_t)rk * stride + frame_base[j] + row * frame_pitch[j] + col];
     }
 }
 
@@ -785,15 +795,19 @@ int launch_illumination(ptycho_plan_s *p, cudaStream_t s)
 
 int launch_slot_rank(ptycho_plan_s *p, int32_t *setup, cudaStream_t s)
 {
-    slot_rank_kernel<<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(p->M, p->sub_tiles.info, p->sub_tiles.list,
-                                                                      p->d_rank, p->d_cnt, setup);
+    int R1 = 0, R2 = 0;
+    rank_radix(p->M, &R1, &R2);
+    slot_rank_kernel<<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(p->M, R1, R2, p->sub_tiles.info,
+                                                                      p->sub_tiles.list, p->d_rank, p->d_cnt, setup);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
 
 int launch_q_from_slots(const ptycho_plan_s *p, float2 *dst, cudaStream_t s)
 {
-    q_from_slots_kernel<<<152 * 8, 256, 0, s>>>(p->J, p->M, p->d_slot, p->d_rank, (int)p->u_len, p->d_frame_base,
+    int R1 = 0, R2 = 0;
+    rank_radix(p->M, &R1, &R2);
+    q_from_slots_kernel<<<152 * 8, 256, 0, s>>>(p->J, p->M, R1, R2, p->d_slot, p->d_rank, (int)p->u_len, p->d_frame_base,
                                                p->d_frame_pitch, dst);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;

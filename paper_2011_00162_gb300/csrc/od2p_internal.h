@@ -258,6 +258,9 @@ int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s);
 int launch_metrics(ptycho_plan_s *p, cudaStream_t s);
 int launch_probe_init(ptycho_plan_s *p, float2 *w0, cudaStream_t s);
 int launch_slot_rank(ptycho_plan_s *p, int32_t *setup, cudaStream_t s);
+// Split m = R1 * R2 of the frame update's FFT, which fixes the task order of
+// the slot ranks (m = 256: R1 = R2 = 0, natural order).
+void rank_radix(int m, int *R1, int *R2);
 int launch_sum_sqrtf(ptycho_plan_s *p, cudaStream_t s);
 int launch_init_state(ptycho_plan_s *p, const float2 *u0, const float2 *w0, cudaStream_t s);
 int launch_illumination(ptycho_plan_s *p, cudaStream_t s);

@@ -5,9 +5,10 @@
  * m x m frame.  Reading: unitary scaling 1/m (= 1/sqrt(m*m)) in both
  * directions, natural frequency order, forward kernel exp(-2 pi i k n / m).
  *
- * orc_dft2 is the definition written out (O(m^4)); orc_fft2 is a textbook
- * iterative radix-2 Cooley-Tukey FFT applied to every row and then every
- * column.  The tests pin each against the other and against numpy.
+ * orc_dft2 is the definition written out (O(m^4)); orc_fft2 applies a 1-D
+ * transform to every row and then every column: a textbook iterative radix-2
+ * Cooley-Tukey FFT when m is a power of two, else the 1-D definition (O(m^2)
+ * per line).  The tests pin each against the other and against numpy.
  */
 #include "od2p_oracle.h"
 
@@ -65,10 +66,39 @@ static void fft1(ocplx *x, int n, int stride, int inverse)
     }
 }
 
+/* The 1-D DFT of n points spaced `stride` apart, by its definition (unnormalised). */
+static void dft1(ocplx *x, int n, int stride, int inverse)
+{
+    const double sgn = inverse ? 1.0 : -1.0;
+    ocplx *out = (ocplx *)malloc(sizeof(ocplx) * (size_t)n);
+    for (int k = 0; k < n; ++k) {
+        ocplx acc = 0.0;
+        for (int t = 0; t < n; ++t) {
+            const long ph = ((long)k * t) % n;
+            const double a = sgn * 2.0 * ORC_PI * (double)ph / (double)n;
+            acc += x[t * stride] * (cos(a) + I * sin(a));
+        }
+        out[k] = acc;
+    }
+    for (int k = 0; k < n; ++k) x[k * stride] = out[k];
+    free(out);
+}
+
 void orc_fft2(ocplx *x, int m, int inverse)
 {
-    for (int r = 0; r < m; ++r) fft1(x + (size_t)r * m, m, 1, inverse);
-    for (int c = 0; c < m; ++c) fft1(x + c, m, m, inverse);
+    const int pow2 = m > 0 && (m & (m - 1)) == 0;
+    for (int r = 0; r < m; ++r) {
+        if (pow2)
+            fft1(x + (size_t)r * m, m, 1, inverse);
+        else
+            dft1(x + (size_t)r * m, m, 1, inverse);
+    }
+    for (int c = 0; c < m; ++c) {
+        if (pow2)
+            fft1(x + c, m, m, inverse);
+        else
+            dft1(x + c, m, m, inverse);
+    }
     const double s = 1.0 / (double)m;
     for (int i = 0; i < m * m; ++i) x[i] *= s;
 }

@@ -25,7 +25,7 @@ typedef double complex ocplx;
 
 /* ---- unitary 2-D DFT (section 2: "normalized discrete Fourier transform") ---- */
 void orc_dft2(ocplx *x, int m, int inverse);   /* naive O(m^4) definition    */
-void orc_fft2(ocplx *x, int m, int inverse);   /* iterative radix-2, m = 2^k */
+void orc_fft2(ocplx *x, int m, int inverse);   /* radix-2 (m = 2^k), else row/column definition */
 
 /* ---- ST-AGM, section 2.2 ---- */
 double orc_stagm_g(ocplx x, double b, double eps);                  /* eq. (obj-1)    */

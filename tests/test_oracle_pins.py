@@ -25,14 +25,14 @@ def crandn(*shape, rng=RNG):
 
 
 # ----------------------------------------------------------------------------- FFT
-@pytest.mark.parametrize("m", [2, 4, 8, 16])
+@pytest.mark.parametrize("m", [2, 4, 8, 16, 6, 12, 15])
 def test_fft_radix2_equals_dft_definition(m):
     x = crandn(m, m)
     np.testing.assert_allclose(oracle.fft2(x), oracle.dft2(x), atol=1e-12)
     np.testing.assert_allclose(oracle.fft2(x, True), oracle.dft2(x, True), atol=1e-12)
 
 
-@pytest.mark.parametrize("m", [16, 32, 64, 128])
+@pytest.mark.parametrize("m", [16, 32, 64, 128, 48, 80, 96])
 def test_fft_matches_numpy_unitary(m):
     x = crandn(m, m)
     np.testing.assert_allclose(oracle.fft2(x), np.fft.fft2(x, norm="ortho"), atol=1e-11)
@@ -602,3 +602,20 @@ def test_probe_init_is_the_mean_over_frames_and_unitary():
     g = np.zeros((1, m, m))
     g[0, 0, 0] = 9.0
     assert np.abs(oracle.probe_init(g) - 3.0 / m).max() < 1e-15
+
+
+@pytest.mark.parametrize("m,n,step", [(12, 48, 4), (6, 30, 3)])
+def test_non_power_of_two_probe_fixed_point_and_dense_operator(m, n, step):
+    """Probe sides that are not powers of two: the forward operator equals the
+    dense matrix F diag(w) S_j, and the noiseless truth stays a fixed point."""
+    offs = synth.raster_offsets(n, m, step, jitter=1, seed=2)
+    w = synth.make_probe(m).astype(np.complex128)
+    u = synth.make_truth(n, m, offs, 3).astype(np.complex128)
+    if n * n <= 900:
+        A = _dense_A(n, n, w, offs)
+        np.testing.assert_allclose(oracle.forward(u, w, offs).reshape(-1), A @ u.reshape(-1), atol=1e-12)
+    f = np.abs(oracle.forward(u, w, offs)) ** 2
+    a = oracle.ADMM(f, w, offs, n, n, 2, 2, 4, 0.5, 0.5, 0.2, u0=u)
+    a.iterate(3)
+    np.testing.assert_allclose(a.merge(), u, atol=1e-11)
+    assert np.abs(a.get(oracle.GAMMA)).max() < 1e-11

@@ -22,10 +22,13 @@
  *  - Every call returns PTYCHO_OK (0) or an error code; ptycho_last_error()
  *    returns a message for the calling thread.  No C++ exception crosses the
  *    ABI and no call aborts the process.
- *  - Supported probe sides m: 16, 32, 64, 128, 256.  Up to 128 a frame is
+ *  - Supported probe sides m: 16, 32, 64, 128, 256 and the mixed-radix sides
+ *    48 (8 x 6), 80 (16 x 5) and 96 (8 x 12) -- the paper fixes no size, and
+ *    detectors are not limited to powers of two.  Up to 128 a frame is
  *    transformed in one thread block's shared memory; 256 x 256 frames go
  *    through row / column / row passes over a plan-owned intermediate, in
- *    waves small enough to stay in L2.  Other m return PTYCHO_ERR_UNSUPPORTED.
+ *    waves small enough to stay in L2.  Other m return PTYCHO_ERR_UNSUPPORTED
+ *    (stagm_loss_noalloc: 16, 32, 64, 128).
  */
 #ifndef OD2P_H
 #define OD2P_H
@@ -240,9 +243,10 @@ int ptycho_probe_init(ptycho_plan_t *plan, ptycho_c32 *w0_dev, ptycho_stream_t s
  * Launch shape of the frame update (the paper fixes none).  For m <= 128 two
  * shapes are compiled, each a (frames per block, threads per block) pair:
  *   m = 16: variant 0 (8, 256), variant 1 (4, 128);  m = 32: (4, 256), (2, 128);
- *   m = 64: (1, 512), (1, 256);  m = 128: (1, 1024), (1, 512).
- * At m = 32 and 64 variant 1 reads Gamma from L2 instead of staging it in
- * shared memory, so that up to four times as many blocks fit on an SM.
+ *   m = 64: (1, 512), (1, 512);  m = 128: (1, 1024), (1, 512);
+ *   m = 48: (2, 384), (1, 384);  m = 80: (1, 448), (1, 640);  m = 96: (1, 384), (1, 768).
+ * At m = 32, 48 and 64 variant 1 reads Gamma from L2 instead of staging it in
+ * shared memory and is compiled for more resident blocks per SM.
  * The persistent kernel runs min(frame groups, b x SMs) blocks, b =
  * blocks_per_sm capped at what fits (0: as many as fit).  Every shape gives
  * the same iterates bit for bit; only the RF partial sums are grouped

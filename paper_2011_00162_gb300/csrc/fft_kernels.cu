@@ -43,6 +43,11 @@ template <> struct Radix<32> { static constexpr int R1 = 8, R2 = 4, FPB = 4, NT 
 #endif
 template <> struct Radix<64> { static constexpr int R1 = 8, R2 = 8, FPB = 1, NT = OD2P_NT64, MINB = OD2P_MINB64; };
 template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8, FPB = 1, NT = 512, MINB = 1; };
+// probe sides that are not powers of two: mixed-radix splits (stage 2 uses the
+// 6-, 5- and 12-point DFTs)
+template <> struct Radix<48> { static constexpr int R1 = 8, R2 = 6, FPB = 2, NT = 384, MINB = 1; };
+template <> struct Radix<80> { static constexpr int R1 = 16, R2 = 5, FPB = 1, NT = 448, MINB = 1; };
+template <> struct Radix<96> { static constexpr int R1 = 8, R2 = 12, FPB = 1, NT = 384, MINB = 1; };
 
 // Ask the TMA unit to stage [p, p + bytes) into L2 (bytes a multiple of 16,
 // p 16-byte aligned); issued early so the data is near when it is needed.
@@ -293,9 +298,15 @@ template <> struct K1Cfg<16, 1> { static constexpr int FPB = 4, NT = 128, STAGE_
 template <> struct K1Cfg<32, 0> { static constexpr int FPB = 4, NT = 256, STAGE_G = 1, MINB = 2; };
 template <> struct K1Cfg<32, 1> { static constexpr int FPB = 2, NT = 128, STAGE_G = 0, MINB = 8; };
 template <> struct K1Cfg<64, 0> { static constexpr int FPB = 1, NT = 512, STAGE_G = 1, MINB = 2; };
-template <> struct K1Cfg<64, 1> { static constexpr int FPB = 1, NT = 256, STAGE_G = 0, MINB = 4; };
+template <> struct K1Cfg<64, 1> { static constexpr int FPB = 1, NT = 512, STAGE_G = 0, MINB = 3; };
 template <> struct K1Cfg<128, 0> { static constexpr int FPB = 1, NT = 1024, STAGE_G = 0, MINB = 1; };
 template <> struct K1Cfg<128, 1> { static constexpr int FPB = 1, NT = 512, STAGE_G = 0, MINB = 1; };
+template <> struct K1Cfg<48, 0> { static constexpr int FPB = 2, NT = 384, STAGE_G = 1, MINB = 2; };
+template <> struct K1Cfg<48, 1> { static constexpr int FPB = 1, NT = 384, STAGE_G = 0, MINB = 3; };
+template <> struct K1Cfg<80, 0> { static constexpr int FPB = 1, NT = 448, STAGE_G = 0, MINB = 2; };
+template <> struct K1Cfg<80, 1> { static constexpr int FPB = 1, NT = 640, STAGE_G = 0, MINB = 1; };
+template <> struct K1Cfg<96, 0> { static constexpr int FPB = 1, NT = 384, STAGE_G = 0, MINB = 2; };
+template <> struct K1Cfg<96, 1> { static constexpr int FPB = 1, NT = 768, STAGE_G = 0, MINB = 1; };
 
 template <int M, int V> constexpr size_t k1_smem_bytes()
 {
@@ -779,6 +790,12 @@ int set_smem(K kernel)
     case 129: { constexpr int M_ = 64, V_ = 1; __VA_ARGS__; }                       \
     case 256: { constexpr int M_ = 128, V_ = 0; __VA_ARGS__; }                      \
     case 257: { constexpr int M_ = 128, V_ = 1; __VA_ARGS__; }                      \
+    case 96: { constexpr int M_ = 48, V_ = 0; __VA_ARGS__; }                        \
+    case 97: { constexpr int M_ = 48, V_ = 1; __VA_ARGS__; }                        \
+    case 160: { constexpr int M_ = 80, V_ = 0; __VA_ARGS__; }                       \
+    case 161: { constexpr int M_ = 80, V_ = 1; __VA_ARGS__; }                       \
+    case 192: { constexpr int M_ = 96, V_ = 0; __VA_ARGS__; }                       \
+    case 193: { constexpr int M_ = 96, V_ = 1; __VA_ARGS__; }                       \
     default: break;                                                                 \
     }
 
@@ -903,7 +920,10 @@ int permute_m(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_na
 
 }  // namespace
 
-bool supported_m(int m) { return m == 16 || m == 32 || m == 64 || m == 128 || m == 256; }
+bool supported_m(int m)
+{
+    return m == 16 || m == 32 || m == 64 || m == 128 || m == 256 || m == 48 || m == 80 || m == 96;
+}
 
 void rank_radix(int m, int *R1, int *R2)
 {
@@ -912,6 +932,9 @@ void rank_radix(int m, int *R1, int *R2)
     case 32: *R1 = Radix<32>::R1, *R2 = Radix<32>::R2; break;
     case 64: *R1 = Radix<64>::R1, *R2 = Radix<64>::R2; break;
     case 128: *R1 = Radix<128>::R1, *R2 = Radix<128>::R2; break;
+    case 48: *R1 = Radix<48>::R1, *R2 = Radix<48>::R2; break;
+    case 80: *R1 = Radix<80>::R1, *R2 = Radix<80>::R2; break;
+    case 96: *R1 = Radix<96>::R1, *R2 = Radix<96>::R2; break;
     default: *R1 = *R2 = 0; break;
     }
 }
@@ -923,6 +946,9 @@ int frames_per_block(int m)
     case 32: return Radix<32>::FPB;
     case 64: return Radix<64>::FPB;
     case 128: return Radix<128>::FPB;
+    case 48: return Radix<48>::FPB;
+    case 80: return Radix<80>::FPB;
+    case 96: return Radix<96>::FPB;
     default: return 1;
     }
 }
@@ -939,7 +965,7 @@ int frame_update_grid(int m, int variant, int n_items, int blocks_per_sm, int *g
     }
     int per_sm = 0, n_sm = 0, rc = PTYCHO_ERR_UNSUPPORTED;
     OD2P_K1_SHAPE(m, variant, rc = k1_per_sm<M_, V_>(&per_sm, &n_sm); break)
-    if (rc) return rc == PTYCHO_ERR_UNSUPPORTED ? fail(rc, "probe side m must be 16, 32, 64, 128 or 256") : rc;
+    if (rc) return rc == PTYCHO_ERR_UNSUPPORTED ? fail(rc, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256") : rc;
     if (max_per_sm) *max_per_sm = per_sm;
     const int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, per_sm) : per_sm;
     *grid = std::max(1, std::min(n_items, bps * n_sm));
@@ -969,8 +995,11 @@ int prepare_kernels(int m)
     case 32: return prepare_m<32>();
     case 64: return prepare_m<64>();
     case 128: return prepare_m<128>();
+    case 48: return prepare_m<48>();
+    case 80: return prepare_m<80>();
+    case 96: return prepare_m<96>();
     case 256: return PTYCHO_OK;  // its kernels stay within the default shared-memory limit
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
     }
 }
 
@@ -1018,7 +1047,7 @@ int launch_frame_update_table(int m, int variant, const FrameArgs *tab, const in
                               int parity, cudaStream_t s)
 {
     OD2P_K1_SHAPE(m, variant, return frame_update_table_m<M_, V_>(tab, items, n_items, grid, parity, s))
-    return fail(PTYCHO_ERR_UNSUPPORTED, "table-driven frame update: m must be 16, 32, 64 or 128");
+    return fail(PTYCHO_ERR_UNSUPPORTED, "table-driven frame update: m must be at most 128");
 }
 
 int launch_frame_update(ptycho_plan_s *p, cudaStream_t s)
@@ -1026,7 +1055,7 @@ int launch_frame_update(ptycho_plan_s *p, cudaStream_t s)
     if (p->M == 256) return frame_update_256(p, s);
     OD2P_K1_SHAPE(p->M, p->k1_variant, return frame_update_single_m<M_, V_>(p, s))
     switch (p->M) {
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
     }
 }
 
@@ -1037,8 +1066,11 @@ int launch_forward(const ptycho_plan_s *p, const float2 *u, const float2 *w, flo
     case 32: return forward_m<32>(p, u, w, out, s);
     case 64: return forward_m<64>(p, u, w, out, s);
     case 128: return forward_m<128>(p, u, w, out, s);
+    case 48: return forward_m<48>(p, u, w, out, s);
+    case 80: return forward_m<80>(p, u, w, out, s);
+    case 96: return forward_m<96>(p, u, w, out, s);
     case 256: return forward_256(p, u, w, out, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
     }
 }
 
@@ -1051,10 +1083,13 @@ int launch_frames_ifft_weight(const ptycho_plan_s *p, const float2 *frames, cons
     case 32: return ifft_m<32>(p, frames, w, out, s);
     case 64: return ifft_m<64>(p, frames, w, out, s);
     case 128: return ifft_m<128>(p, frames, w, out, s);
+    case 48: return ifft_m<48>(p, frames, w, out, s);
+    case 80: return ifft_m<80>(p, frames, w, out, s);
+    case 96: return ifft_m<96>(p, frames, w, out, s);
     case 256:
         if (w) return fail(PTYCHO_ERR_STATE, "internal: m = 256 inverse FFT takes no weight");
         return ifft_256(p, frames, out, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
     }
 }
 
@@ -1065,8 +1100,11 @@ int launch_loss_frames(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaS
     case 32: return loss_m<32>(p, u, w, s);
     case 64: return loss_m<64>(p, u, w, s);
     case 128: return loss_m<128>(p, u, w, s);
+    case 48: return loss_m<48>(p, u, w, s);
+    case 80: return loss_m<80>(p, u, w, s);
+    case 96: return loss_m<96>(p, u, w, s);
     case 256: return loss_256(p, u, w, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
     }
 }
 
@@ -1077,8 +1115,11 @@ int launch_probe_avg(ptycho_plan_s *p, cudaStream_t s)
     case 32: return probe_avg_m<32>(p, s);
     case 64: return probe_avg_m<64>(p, s);
     case 128: return probe_avg_m<128>(p, s);
+    case 48: return probe_avg_m<48>(p, s);
+    case 80: return probe_avg_m<80>(p, s);
+    case 96: return probe_avg_m<96>(p, s);
     case 256: return probe_avg_256(p, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
     }
 }
 
@@ -1090,8 +1131,11 @@ int launch_ingest_f(ptycho_plan_s *p, const float *f, cudaStream_t s)
     case 32: return ingest_m<32>(p, f, part, s);
     case 64: return ingest_m<64>(p, f, part, s);
     case 128: return ingest_m<128>(p, f, part, s);
+    case 48: return ingest_m<48>(p, f, part, s);
+    case 80: return ingest_m<80>(p, f, part, s);
+    case 96: return ingest_m<96>(p, f, part, s);
     case 256: return ingest_256(p, f, part, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
     }
 }
 
@@ -1103,8 +1147,11 @@ int launch_permute_gamma(const ptycho_plan_s *p, const float2 *src, float2 *dst,
     case 32: return permute_m<32>(p, src, dst, to_natural, s);
     case 64: return permute_m<64>(p, src, dst, to_natural, s);
     case 128: return permute_m<128>(p, src, dst, to_natural, s);
+    case 48: return permute_m<48>(p, src, dst, to_natural, s);
+    case 80: return permute_m<80>(p, src, dst, to_natural, s);
+    case 96: return permute_m<96>(p, src, dst, to_natural, s);
     case 256: return permute_256(p, src, dst, to_natural, s);
-    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
     }
 }
 

@@ -740,12 +740,9 @@ int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s)
 int launch_probe_init(ptycho_plan_s *p, float2 *w0, cudaStream_t s)
 {
     int R1 = 16, R2 = 16, row_major = 1;  // m = 256
-    switch (p->M) {
-    case 16: R1 = 4, R2 = 4, row_major = 0; break;
-    case 32: R1 = 8, R2 = 4, row_major = 0; break;
-    case 64: R1 = 8, R2 = 8, row_major = 0; break;
-    case 128: R1 = 16, R2 = 8, row_major = 0; break;
-    default: break;
+    if (p->M != 256) {
+        rank_radix(p->M, &R1, &R2);  // m <= 128: transposed position layout
+        row_major = 0;
     }
     float *amp = reinterpret_cast<float *>(p->d_q);  // plan scratch: MM floats
     float2 *T = p->d_wnew;                           // plan scratch: MM complex

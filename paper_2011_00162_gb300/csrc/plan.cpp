@@ -331,7 +331,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
     if (!out) return fail(PTYCHO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!g || !f_dev || !g->offsets_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL geometry, f or offsets");
-    if (!supported_m(g->m)) return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 64, 128 or 256");
+    if (!supported_m(g->m)) return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
     if (g->n_frames < 1 || g->img_h < g->m || g->img_w < g->m)
         return fail(PTYCHO_ERR_INVALID_ARG, "need n_frames >= 1 and an image at least m x m");
     if ((int64_t)g->img_h * g->img_w >= (1LL << 31))

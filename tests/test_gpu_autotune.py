@@ -46,7 +46,8 @@ def _states(plan, blind):
 
 
 CASES = [(16, (5, 4), 120, 6, False), (32, (2, 3), 200, 10, False), (64, (2, 2), 256, 16, False),
-         (128, (2, 2), 384, 32, False), (32, (2, 2), 160, 8, True), (64, (1, 2), 192, 16, True)]
+         (128, (2, 2), 384, 32, False), (32, (2, 2), 160, 8, True), (64, (1, 2), 192, 16, True),
+         (48, (2, 2), 192, 12, False), (80, (2, 2), 240, 20, False), (96, (2, 2), 288, 24, True)]
 
 
 @pytest.mark.parametrize("m,grid,n,step,blind", CASES)

@@ -79,3 +79,34 @@ def test_batch_rejects_blind_members():
     g = od.Geometry(p.n, p.n, p.m, offs, 1, 2, 8, 0.5, 0.1, 0.05, mu=1.0, blind=True)
     with pytest.raises(od.PtychoError):
         od.ptycho_batch_plan([g], [torch.from_numpy(f).to(DEV)])
+
+
+def test_batch_with_mixed_radix_probe_sides_bitwise():
+    """Probe sides 48, 80 and 96 (mixed-radix FFTs) beside 32 and 64 in one batch."""
+    probs = [synth.Problem(f"b{m}", n, m, step, 1, 2, 2, 8, 1e4, 1, seed=m)
+             for m, n, step in [(48, 192, 12), (80, 240, 20), (96, 288, 24), (32, 128, 8), (64, 256, 16), (48, 144, 12)]]
+    cases = [make_case(p, noise_seed=i) for i, p in enumerate(probs)]
+    geoms = [od.Geometry(p.n, p.n, p.m, c[0], p.sub_rows, p.sub_cols, p.overlap_px, 0.5, 2.0, 0.5)
+             for p, c in zip(probs, cases)]
+    fs = [torch.from_numpy(np.asarray(c[3], np.float32)).to(DEV) for c in cases]
+    batch = od.ptycho_batch_plan(geoms, fs)
+    for m, c in zip(batch.members, cases):
+        od.od2p_init(m, torch.from_numpy(np.asarray(c[2], np.complex64)).to(DEV))
+    batch.iterate(2)
+    for i, (g, c) in enumerate(zip(geoms, cases)):
+        alone = od.ptycho_plan(g, fs[i])
+        od.od2p_init(alone, torch.from_numpy(np.asarray(c[2], np.complex64)).to(DEV))
+        od.od2p_iterate(alone, 2)
+        for k in (od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA):
+            assert torch.equal(od.od2p_get_state(batch.members[i], k), od.od2p_get_state(alone, k)), (i, k)
+        alone.close()
+    # one member against the oracle after one more iteration from the same state
+    p, (offs, u_true, w, f) = probs[2], cases[2]
+    ref = oracle.ADMM(f, w, offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, 0.5, 2.0, 0.5)
+    for k, ko in ((od.STATE_U, oracle.U), (od.STATE_GAMMA, oracle.GAMMA), (od.STATE_LAMBDA, oracle.LAMBDA)):
+        ref.set(ko, od.od2p_get_state(batch.members[2], k).cpu().numpy())
+    batch.iterate(1)
+    ref.iterate(1)
+    for k, ko in ((od.STATE_U, oracle.U), (od.STATE_GAMMA, oracle.GAMMA), (od.STATE_LAMBDA, oracle.LAMBDA)):
+        assert rel_l2(od.od2p_get_state(batch.members[2], k).cpu().numpy(), ref.get(ko)) < 1e-5
+    batch.close()

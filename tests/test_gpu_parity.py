@@ -71,7 +71,7 @@ def test_prox_matches_oracle(eps, lam):
 
 
 @pytest.mark.parametrize("m,n,step,jit", [(16, 61, 5, 1), (32, 100, 9, 2), (64, 300, 16, 2), (128, 400, 40, 3),
-                                          (256, 600, 64, 3)])
+                                          (256, 600, 64, 3), (48, 151, 12, 2), (80, 243, 20, 2), (96, 301, 24, 3)])
 def test_forward_and_adjoint_match_oracle(m, n, step, jit):
     rng = np.random.default_rng(m)
     offs = synth.raster_offsets(n, m, step, jit, seed=3)
@@ -175,7 +175,8 @@ def test_one_iteration_grid4x4_full_size(scrambled):
 
 
 @pytest.mark.parametrize("m,grid,n,step", [(32, (2, 3), 200, 10), (128, (2, 2), 384, 32), (16, (5, 4), 120, 6),
-                                           (256, (2, 2), 512, 64)])
+                                           (256, (2, 2), 512, 64), (48, (2, 2), 200, 12), (80, (2, 3), 320, 20),
+                                           (96, (2, 2), 384, 24)])
 def test_one_iteration_other_sizes(m, grid, n, step):
     p = synth.Problem("t", n, m, step, 2, grid[0], grid[1], 12, 1e5, 1, eta=0.3, r=0.2, seed=m)
     offs, u_true, w, f = make_case(p)
@@ -293,7 +294,7 @@ def test_checkpoint_resume_bitwise():
 
 # ----------------------------------------------------------------------------- blind
 @pytest.mark.parametrize("masked,m,n,step", [(False, 32, 96, 8), (True, 32, 96, 8), (False, 256, 512, 64),
-                                             (True, 256, 512, 64)])
+                                             (True, 256, 512, 64), (False, 48, 144, 12), (True, 96, 288, 24)])
 def test_blind_one_iteration(masked, m, n, step):
     p = synth.Problem("b", n, m, step, 1, 2, 2, 8, 1e5, 1, eta=0.3, r=0.2, blind=True, mu=2.0,
                       gamma=0.1, seed=21)
@@ -319,7 +320,8 @@ def test_blind_one_iteration(masked, m, n, step):
 
 
 # ----------------------------------------------------------------------------- loss and gradients
-@pytest.mark.parametrize("m,n,step", [(16, 64, 4), (64, 256, 16), (128, 384, 48), (256, 512, 96)])
+@pytest.mark.parametrize("m,n,step", [(16, 64, 4), (64, 256, 16), (128, 384, 48), (256, 512, 96), (48, 192, 12),
+                                      (80, 240, 20), (96, 288, 24)])
 def test_loss_and_gradients_match_oracle(m, n, step):
     p = synth.Problem("g", n, m, step, 2, 1, 1, 0, 1e4, 1, seed=m + 1)
     offs, u_true, w, f = make_case(p)
@@ -416,7 +418,8 @@ def test_blind_workload_1024_full_size():
     assert rel_l2(host(gu), gu_o) < 1e-5 and rel_l2(host(gw), gw_o) < 1e-5
 
 
-@pytest.mark.parametrize("m,n,step", [(16, 64, 4), (32, 100, 9), (64, 300, 16), (128, 384, 48), (256, 512, 96)])
+@pytest.mark.parametrize("m,n,step", [(16, 64, 4), (32, 100, 9), (64, 300, 16), (128, 384, 48), (256, 512, 96),
+                                      (48, 144, 12), (80, 240, 20), (96, 288, 24)])
 def test_probe_init_matches_oracle(m, n, step):
     """Section 4.3's data-driven initial probe from a plan's intensities."""
     p = synth.Problem("pi", n, m, step, 1, 2, 2, 8, 1e4, 1, seed=m)

@@ -61,7 +61,7 @@ def test_plan_rejects_bad_geometry_before_device_work(lib):
     import numpy as np
     offs = np.array([[0, 0], [0, 70]], np.int32)  # second window leaves a 64-wide image
     f = ctypes.c_void_p(1)  # never dereferenced: validation fails first
-    for m, eps, code in [(64, 0.5, _lib.ERR_INVALID_ARG), (48, 0.5, _lib.ERR_UNSUPPORTED),
+    for m, eps, code in [(64, 0.5, _lib.ERR_INVALID_ARG), (40, 0.5, _lib.ERR_UNSUPPORTED),
                          (16, 1.5, _lib.ERR_INVALID_ARG)]:
         g = _lib.Geometry(64, 64, m, 2, offs.ctypes.data, 1, 1, 0, eps, 0.1, 0.1, 0, 0, 0, None)
         h = ctypes.c_void_p()

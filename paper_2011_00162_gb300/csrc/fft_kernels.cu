@@ -677,11 +677,21 @@ __global__ void __launch_bounds__(Radix<M>::NT) loss_kernel(LossArgs a)
 }
 
 // ---------------------------------------------------------------- blind w-update (eq. blind_w)
-// w^{n+1} = (1/D) F^* M F sum_d (Delta_d + W_d), one block; without a mask F^* F = I.
+// s * sum_d (Delta_d + W_d) per probe pixel (d ascending), all pixels in parallel.
+__global__ void probe_sum_kernel(int MM, int D, const float2 *__restrict__ Wd, const float2 *__restrict__ Delta,
+                                 float2 *__restrict__ out, float s)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= MM) return;
+    float2 t = make_float2(0.f, 0.f);
+    for (int d = 0; d < D; ++d) t = cadd(t, cadd(Delta[(size_t)d * MM + k], Wd[(size_t)d * MM + k]));
+    out[k] = cscale(t, s);
+}
+
+// Masked probe average: w^{n+1} = (1/D) F^* M F sum, one block, from the sum
+// that probe_sum_kernel left in wnew (in place).
 template <int M>
-__global__ void __launch_bounds__(Radix<M>::NT) probe_avg_kernel(int D, const float2 *Wd,
-                                                                  const float2 *Delta,
-                                                                  const float *mask, float2 *wnew,
+__global__ void __launch_bounds__(Radix<M>::NT) probe_avg_kernel(int D, const float *mask, float2 *wnew,
                                                                   const float2 *twg)
 {
     constexpr int NT = Radix<M>::NT, P = M + 1, MM = M * M;
@@ -689,20 +699,8 @@ __global__ void __launch_bounds__(Radix<M>::NT) probe_avg_kernel(int D, const fl
     float2 *tw = reinterpret_cast<float2 *>(smem4);
     float2 *buf = tw + M;
     const float invD = 1.f / (float)D;
-    if (!mask) {
-        for (int k = threadIdx.x; k < MM; k += NT) {
-            float2 t = make_float2(0.f, 0.f);
-            for (int d = 0; d < D; ++d) t = cadd(t, cadd(Delta[(size_t)d * MM + k], Wd[(size_t)d * MM + k]));
-            wnew[k] = cscale(t, invD);
-        }
-        return;
-    }
     for (int k = threadIdx.x; k < M; k += NT) tw[k] = twg[k];
-    for (int k = threadIdx.x; k < MM; k += NT) {
-        float2 t = make_float2(0.f, 0.f);
-        for (int d = 0; d < D; ++d) t = cadd(t, cadd(Delta[(size_t)d * MM + k], Wd[(size_t)d * MM + k]));
-        buf[(k / M) * P + (k % M)] = t;
-    }
+    for (int k = threadIdx.x; k < MM; k += NT) buf[(k / M) * P + (k % M)] = wnew[k];
     __syncthreads();
     col_stage1<M, false>(buf, tw);
     __syncthreads();
@@ -893,9 +891,12 @@ int loss_m(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s)
 template <int M>
 int probe_avg_m(ptycho_plan_s *p, cudaStream_t s)
 {
-    if (int rc = set_smem<M>(probe_avg_kernel<M>)) return rc;
-    probe_avg_kernel<M><<<1, Radix<M>::NT, smem_bytes<M>(), s>>>(
-        p->D, p->d_Wd, p->d_Delta, p->has_mask ? p->d_mask : nullptr, p->d_wnew, p->d_tw);
+    constexpr int MM = M * M;
+    probe_sum_kernel<<<(MM + 255) / 256, 256, 0, s>>>(MM, p->D, p->d_Wd, p->d_Delta, p->d_wnew,
+                                                       p->has_mask ? 1.f : 1.f / (float)p->D);
+    OD2P_CUDA(cudaGetLastError());
+    if (!p->has_mask) return PTYCHO_OK;
+    probe_avg_kernel<M><<<1, Radix<M>::NT, smem_bytes<M>(), s>>>(p->D, p->d_mask, p->d_wnew, p->d_tw);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }

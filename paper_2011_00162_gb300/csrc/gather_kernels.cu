@@ -66,8 +66,14 @@ constexpr int NBR_SMEM = 16;
 #ifndef OD2P_K2_MINB
 #define OD2P_K2_MINB 4
 #endif
+#ifndef OD2P_K2B_U
+#define OD2P_K2B_U 1
+#endif
+#ifndef OD2P_K2B_MINB
+#define OD2P_K2B_MINB 4
+#endif
 template <bool BLIND, bool BATCHED>
-__global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : OD2P_K2_MINB)
+__global__ void __launch_bounds__(GATHER_THREADS, BLIND ? OD2P_K2B_MINB : OD2P_K2_MINB)
     subdomain_update_kernel(const SubArgs single, const SubArgs *__restrict__ tab, const int2 *__restrict__ items,
                             int parity)
 {
@@ -141,7 +147,7 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? 2 : OD2P_K2_MINB)
         // blind: walk the tile's frame list and weight with W_d^{n+1};
         // U entries x TILE_ROWS rows of loads per step, branch-free: a lane whose
         // pixel a frame does not cover loads element 0 and discards it.
-        constexpr int U = 4;
+        constexpr int U = OD2P_K2B_U;
         const int nk = ti.nk;
         for (int k = 0; k < nk; k += U) {
             float2 qv[U][TILE_ROWS], wv[U][TILE_ROWS];
@@ -313,12 +319,24 @@ __global__ void probe_partial_kernel(ProbeArgs a)
     const int kr = k / a.M, kc = k % a.M;
     float2 acc = make_float2(0.f, 0.f);
     float nn = 0.f;
-    for (int t = ch.y; t < ch.z; ++t) {
-        const int j = a.group_frames[t];
-        const int pitch = a.frame_pitch ? a.frame_pitch[j] : a.pitch;
-        const float2 uv = __ldg(a.u + a.frame_base[j] + (size_t)kr * pitch + kc);
-        acc = cadd(acc, cconjmul(uv, __ldg(a.h + (size_t)j * MM + k)));
-        nn += cabs2(uv);
+    // four frames' loads in flight per step, accumulated in ascending order
+    constexpr int U = 4;
+    for (int t0 = ch.y; t0 < ch.z; t0 += U) {
+        float2 uv[U], hv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = min(t0 + u, ch.z - 1);
+            const int j = a.group_frames[t];
+            const int pitch = a.frame_pitch ? a.frame_pitch[j] : a.pitch;
+            uv[u] = __ldg(a.u + a.frame_base[j] + (size_t)kr * pitch + kc);
+            hv[u] = __ldg(a.h + (size_t)j * MM + k);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (t0 + u < ch.z) {
+                acc = cadd(acc, cconjmul(uv[u], hv[u]));
+                nn += cabs2(uv[u]);
+            }
     }
     a.part[(size_t)blockIdx.y * MM + k] = acc;
     a.part_n[(size_t)blockIdx.y * MM + k] = nn;

@@ -26,7 +26,10 @@ constexpr int TILE_ROWS = TILE_H * TILE_W / GATHER_THREADS;
 constexpr int PROBE_CHUNK = 32;
 // m = 256 frames go through their three FFT passes in waves of this many
 // frames (a 32 MB intermediate that stays in L2).
-constexpr int WAVE_256 = 64;
+#ifndef OD2P_WAVE_256
+#define OD2P_WAVE_256 64
+#endif
+constexpr int WAVE_256 = OD2P_WAVE_256;
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);

@@ -126,6 +126,13 @@ int ptycho_release_cached_memory(void);
  * plan keeps sqrt(f) in its own layout).  The state is initialised as Step 0
  * of Algorithms 1-3 with u = 1 and the probe all zeros; call od2p_init before
  * iterating.  On error *out is set to NULL and nothing is leaked.
+ * Nonblind plans add the A_d^* summands of eq. (Alg1-solver-u) through
+ * per-pixel gather slots (each frame writes its conj(w)-weighted residual to
+ * the slot of its rank among the frames covering the pixel; the subdomain
+ * update sums a pixel's slots in ascending j).  When more than 255 frames
+ * cover one pixel, or the slots would exceed 2^32 elements, the plan uses the
+ * frame-list gather of blind plans instead, weighting with the known probe:
+ * the same result up to rounding, at a lower speed.
  * Errors: INVALID_ARG (NULL pointer, bad sizes/offsets/parameters),
  * UNSUPPORTED (m), OOM, CUDA.
  */
@@ -305,8 +312,9 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c
  *   destroy them, and do not iterate a member on its own between batch
  *   iterations -- the call returns PTYCHO_ERR_STATE).
  * ptycho_batch_iterate: n_iter iterations of every member; od2p_init must
- *   have been called on each.  Errors: INVALID_ARG, UNSUPPORTED (a blind member
- *   or m = 256), STATE, OOM, CUDA.
+ *   have been called on each.  Errors: INVALID_ARG, UNSUPPORTED (a blind member,
+ *   m = 256, or a member with more than 255 frames over one pixel), STATE, OOM,
+ *   CUDA.
  */
 typedef struct ptycho_batch_s ptycho_batch_t;
 int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const float *const *f_devs, int32_t n,

@@ -9,7 +9,7 @@
 //   C: 16-row slabs -- inverse row FFTs, natural-order output.
 // The intermediate T (natural rows / position columns after A, the reverse
 // after B) is a plan-owned buffer of WAVE frames: frames go through A, B, C in
-// waves of WAVE (32 MB), so T stays in L2 between the passes and HBM sees the
+// waves of WAVE frames (512 KB each), so T stays in L2 between the passes and HBM sees the
 // algorithmic traffic plus q.  Position p = 16 s + s' holds frequency s + 16 s'
 // along each axis (as for the smaller sizes); Gamma and sqrt f are stored at
 // position row-major index p_r * 256 + p_c.
@@ -112,13 +112,23 @@ __global__ void __launch_bounds__(NTB) rows_fwd256_kernel(PassA a)
     for (int r = 0; r < SLAB; ++r) a.T[((size_t)f * BM + rb * SLAB + r) * BM + c] = buf[r * PA + c];
 }
 
-__global__ void __launch_bounds__(NTB) cols256_kernel(PassB a)
+#ifndef OD2P_COLS256_MINB
+#define OD2P_COLS256_MINB 5
+#endif
+__global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a)
 {
     extern __shared__ float4 smem4[];
     float2 *tw = reinterpret_cast<float2 *>(smem4);
     float2 *buf = tw + BM;                       // BM rows x PB
     float *red = reinterpret_cast<float *>(buf + BM * PB);
     const int f = blockIdx.x / (BM / SLAB), cb = blockIdx.x % (BM / SLAB), j = a.j0 + f;
+    if (a.mode == B_PROX) {
+        // this slab's Gamma (128 B) and sqrt f (64 B) of each position row, into
+        // L2 while the column FFT runs
+        const size_t gi = (size_t)j * BMM + (size_t)threadIdx.x * BM + cb * SLAB;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.gamma + gi));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.sqrtf_ + gi));
+    }
     for (int k = threadIdx.x; k < BM; k += NTB) tw[k] = a.tw[k];
     {
         const int cl = threadIdx.x % SLAB, r0 = threadIdx.x / SLAB;
@@ -365,9 +375,9 @@ int frame_update_256(ptycho_plan_s *p, cudaStream_t s)
     P.B.mode = B_PROX;
     P.B.part = p->d_rf_part;
     P.C.out = p->d_q;
-    P.C.wconj = p->blind ? nullptr : p->d_w;
+    P.C.wconj = p->slots ? p->d_w : nullptr;
     P.C.scale = 1.f / (float)BM;
-    if (!p->blind) {
+    if (p->slots) {
         P.C.slot = p->d_slot;
         P.C.rank = p->d_rank;
         P.C.frame_base = p->d_frame_base;

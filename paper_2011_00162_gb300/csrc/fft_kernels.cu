@@ -1034,7 +1034,7 @@ void fill_frame_args(const ptycho_plan_s *p, FrameArgs out[2])
         a.gamma = p->d_gamma;
         a.sqrtf_ = p->d_sqrtf;
         a.q = p->d_q;
-        a.slot = p->blind ? nullptr : p->d_slot;
+        a.slot = p->slots ? p->d_slot : nullptr;
         a.rank = p->d_rank;
         a.slot_stride = (int32_t)p->u_len;
         a.rf_part = p->d_rf_part;

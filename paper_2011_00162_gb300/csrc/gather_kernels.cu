@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? OD2P_K2B_MINB : OD2P_K
         acc[r] = make_float2(0.f, 0.f);
         nrm[r] = 0.f;
     }
-    const float2 *w = BLIND ? a.Wd + ti.reg * MM : nullptr;
+    const float2 *w = BLIND ? a.Wd + ti.reg * a.wd_stride : nullptr;
     if (!BLIND) {
         // nonblind: the pixel's frames sit in slots 0 .. cnt-1 in ascending j;
         // U slots x TILE_ROWS rows of coalesced, independent loads per step; a
@@ -503,6 +503,14 @@ __global__ void __launch_bounds__(GATHER_THREADS) slot_rank_kernel(int M, int R1
     if (most > 0) atomicMax(setup + 1, most);
 }
 
+// out_j = conj(w) o q_j for every frame (state export of list-gather plans).
+__global__ void weight_frames_kernel(int J, int MM, const float2 *q, const float2 *w, float2 *out)
+{
+    const size_t n = (size_t)J * MM;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = cconjmul(__ldg(w + e % MM), q[e]);
+}
+
 // Frames of the nonblind gather slots back in frame layout (for state export).
 __global__ void q_from_slots_kernel(int J, int M, int R1, int R2, const float2 *slot, const uint8_t *rank,
                                     int stride, const int32_t *frame_base, const int32_t *frame_pitch, float2 *q)
@@ -667,14 +675,17 @@ void fill_sub_args(const ptycho_plan_s *p, SubArgs out[2])
         a.lam_next = p->d_lam[1 - par];
         a.q = p->d_q;
         a.w = p->d_w;
-        a.Wd = p->d_Wd;
+        // list gather (blind, or nonblind without slots): weight with W_d, or
+        // with the known probe for every subdomain
+        a.Wd = p->blind ? p->d_Wd : p->d_w;
+        a.wd_stride = p->blind ? p->MM : 0;
         a.nrm = p->d_nrm;
         a.slot = p->d_slot;
         a.cnt = p->d_cnt;
         a.slot_stride = (int32_t)p->u_len;
         a.eta = p->eta;
         a.r = p->r;
-        a.gamma = p->gamma;
+        a.gamma = p->blind ? p->gamma : 0.f;
         a.blind = p->blind;
         a.re_part = p->d_re_part;
     }
@@ -696,7 +707,7 @@ int launch_subdomain_update(ptycho_plan_s *p, cudaStream_t s)
 {
     const int n = p->sub_tiles.n_tiles;
     if (n <= 0) return PTYCHO_OK;
-    if (p->blind)
+    if (p->blind || !p->slots)
         subdomain_update_kernel<true, false><<<n, GATHER_THREADS, 0, s>>>(p->h_sargs[p->cur], nullptr, nullptr, p->cur);
     else
         subdomain_update_kernel<false, false><<<n, GATHER_THREADS, 0, s>>>(p->h_sargs[p->cur], nullptr, nullptr, p->cur);
@@ -820,6 +831,11 @@ int launch_slot_rank(ptycho_plan_s *p, int32_t *setup, cudaStream_t s)
 
 int launch_q_from_slots(const ptycho_plan_s *p, float2 *dst, cudaStream_t s)
 {
+    if (!p->slots) {  // list-gather plans keep q unweighted: apply conj(w) here
+        weight_frames_kernel<<<152 * 8, 256, 0, s>>>(p->J, p->MM, p->d_q, p->d_w, dst);
+        OD2P_CUDA(cudaGetLastError());
+        return PTYCHO_OK;
+    }
     int R1 = 0, R2 = 0;
     rank_radix(p->M, &R1, &R2);
     q_from_slots_kernel<<<152 * 8, 256, 0, s>>>(p->J, p->M, R1, R2, p->d_slot, p->d_rank, (int)p->u_len, p->d_frame_base,

@@ -25,9 +25,10 @@ constexpr int TILE_ROWS = TILE_H * TILE_W / GATHER_THREADS;
 // Frames per chunk of the fixed-order probe reductions (blind W, grad w).
 constexpr int PROBE_CHUNK = 32;
 // m = 256 frames go through their three FFT passes in waves of this many
-// frames (a 32 MB intermediate that stays in L2).
+// frames (a 47.5 MB intermediate that stays in L2; 95 frames x 16 column slabs
+// fill two rounds of the column pass at five blocks per SM).
 #ifndef OD2P_WAVE_256
-#define OD2P_WAVE_256 64
+#define OD2P_WAVE_256 95
 #endif
 constexpr int WAVE_256 = OD2P_WAVE_256;
 
@@ -147,6 +148,7 @@ struct SubArgs {
     float2 *u_next, *lam_next;
     float eta, r, gamma;
     int32_t blind;
+    int32_t wd_stride;         // list gather: probe of tile subdomain d at Wd + d * wd_stride
     float *re_part;
 };
 
@@ -187,6 +189,10 @@ struct ptycho_plan_s {
     uint8_t *d_cnt = nullptr;      // u_len
     float2 *d_slot = nullptr;      // slot_k * u_len
     int32_t slot_k = 0;
+    // nonblind plans gather through slots unless more than 255 frames cover a
+    // pixel or the slots would exceed 2^32 elements; then they take the
+    // frame-list gather of blind plans, weighting with the known probe
+    bool slots = false;
     float2 *d_u[2] = {nullptr, nullptr};
     float *d_nrm = nullptr;        // nonblind: sum_j S_j^T |w|^2 per subdomain pixel (eq. AtA)
     float2 *d_lam[2] = {nullptr, nullptr};

@@ -528,11 +528,10 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         if ((e1 = cudaMemcpyAsync(h_setup, d_setup, sizeof(h_setup), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e1 = cudaStreamSynchronize(s)) != cudaSuccess)
             return bail(cuda_fail(e1, "slot ranks"));
-        if (h_setup[0]) return bail(fail(PTYCHO_ERR_UNSUPPORTED, "more than 255 frames cover one pixel"));
         p->slot_k = h_setup[1];
-        if ((int64_t)p->slot_k * p->u_len >= (1LL << 32))
-            return bail(fail(PTYCHO_ERR_UNSUPPORTED, "gather slot storage exceeds 2^32 elements"));
-        if ((rc = dev_alloc(&p->d_slot, (size_t)std::max(p->slot_k, 1) * p->u_len, own, s))) return bail(rc);
+        p->slots = !h_setup[0] && (int64_t)p->slot_k * p->u_len < (1LL << 32);
+        if (p->slots && (rc = dev_alloc(&p->d_slot, (size_t)std::max(p->slot_k, 1) * p->u_len, own, s)))
+            return bail(rc);
     }
     cudaError_t e;
     if ((e = cudaMemsetAsync(p->d_metrics, 0, 3 * sizeof(double), s)) != cudaSuccess ||
@@ -863,6 +862,9 @@ int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const 
         ptycho_plan_t *p = nullptr;
         if (int rc = ptycho_plan(&p, &geoms[i], f_devs[i], stream)) return bail(rc);
         b->plans.push_back(p);
+        if (!p->slots)
+            return bail(fail(PTYCHO_ERR_UNSUPPORTED, "batch member " + std::to_string(i) +
+                                                         ": more than 255 frames cover one pixel (list-gather plan)"));
     }
     // one table per probe side: the member plans' frame-update arguments and the
     // (plan, frame group) work items

@@ -458,3 +458,29 @@ def test_plans_reuse_pooled_memory_bitwise():
     for o in outs[1:]:
         for a, b in zip(o, outs[0]):
             assert np.array_equal(a, b)
+
+
+def test_dense_scan_takes_the_list_gather():
+    """More than 255 frames over a pixel (m = 32, step 2: up to 256): the
+    nonblind plan gathers through frame lists with the known probe; one
+    iteration from a scrambled state and the exported residual still match the
+    oracle, and a batch refuses such a member."""
+    # one subdomain: its frames are all frames (coverage is counted per subdomain)
+    p = synth.Problem("dense", 80, 32, 2, 0, 1, 1, 0, 1e5, 1, eta=0.3, r=0.2, seed=4)
+    offs, u_true, w, f = make_case(p)
+    cover = np.zeros((p.n, p.n), int)
+    for r0, c0 in offs:
+        cover[r0:r0 + p.m, c0:c0 + p.m] += 1
+    assert cover.max() > 255
+    plan, ref = pair_of(p, offs, w, f)
+    _scramble(plan, ref, 5)
+    od.od2p_iterate(plan, 1)
+    ref.iterate(1)
+    out = _compare_state(plan, ref, ONE_ITER_TOL)
+    record("dense_scan_list_gather_one_iteration", **out)
+    z, gam = ref.get(oracle.Z).reshape(-1, p.m, p.m), ref.get(oracle.GAMMA).reshape(-1, p.m, p.m)
+    q = host(od.od2p_get_state(plan, od.STATE_Q)).reshape(-1, p.m, p.m)
+    for j in np.random.default_rng(2).choice(len(offs), 10, replace=False):
+        assert rel_l2(q[j], np.conj(w) * oracle.fft2(z[j] - gam[j], True)) < ONE_ITER_TOL
+    with pytest.raises(od.PtychoError):
+        od.ptycho_batch_plan([geom_of(p, offs)], [f32(f)])

@@ -115,6 +115,9 @@ __global__ void __launch_bounds__(NTB) rows_fwd256_kernel(PassA a)
 #ifndef OD2P_COLS256_MINB
 #define OD2P_COLS256_MINB 5
 #endif
+// MODE: the elementwise step between the column transforms (compile-time, so
+// that the per-element loop carries no mode tests).
+template <int MODE>
 __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a)
 {
     extern __shared__ float4 smem4[];
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
     float2 *buf = tw + BM;                       // BM rows x PB
     float *red = reinterpret_cast<float *>(buf + BM * PB);
     const int f = blockIdx.x / (BM / SLAB), cb = blockIdx.x % (BM / SLAB), j = a.j0 + f;
-    if (a.mode == B_PROX) {
+    if (MODE == B_PROX) {
         // this slab's Gamma (128 B) and sqrt f (64 B) of each position row, into
         // L2 while the column FFT runs
         const size_t gi = (size_t)j * BMM + (size_t)threadIdx.x * BM + cb * SLAB;
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
         const int cl = threadIdx.x % SLAB, r0 = threadIdx.x / SLAB;
         for (int r = r0; r < BM; r += NTB / SLAB) {
             float2 v;
-            if (a.mode == B_IFFT_IN)
+            if (MODE == B_IFFT_IN)
                 v = __ldg(a.in + (size_t)j * BMM + freq_of(r) * BM + freq_of(cb * SLAB + cl));
             else
                 v = a.T[((size_t)f * BM + r) * BM + cb * SLAB + cl];
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
     }
     __syncthreads();
     const int cl = threadIdx.x % SLAB, hi = threadIdx.x / SLAB;  // hi: n1 (stage 1) or s (stage 2)
-    if (a.mode != B_IFFT_IN) {  // column stage 1
+    if (MODE != B_IFFT_IN) {  // column stage 1
         float2 x[BR];
 #pragma unroll
         for (int t = 0; t < BR; ++t) x[t] = buf[(hi + BR * t) * PB + cl];
@@ -157,14 +160,14 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
         float2 x[BR];
 #pragma unroll
         for (int t = 0; t < BR; ++t) x[t] = buf[(BR * hi + t) * PB + cl];
-        if (a.mode != B_IFFT_IN) dft<BR, false>(x);
+        if (MODE != B_IFFT_IN) dft<BR, false>(x);
         const int pc = cb * SLAB + cl;
         const float inv_m = 1.f / (float)BM;
 #pragma unroll
         for (int t = 0; t < BR; ++t) {
             const int pr = BR * hi + t;
             const size_t gi = (size_t)j * BMM + (size_t)pr * BM + pc;
-            if (a.mode == B_PROX) {
+            if (MODE == B_PROX) {
                 const float2 ax = cscale(x[t], inv_m);
                 const float sf = __ldg(a.sqrtf_ + gi);
                 const float2 gm = a.gamma[gi];
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
                 const float2 gn = csub(y, z);
                 a.gamma[gi] = gn;
                 x[t] = csub(z, gn);
-            } else if (a.mode == B_LOSS) {
+            } else if (MODE == B_LOSS) {
                 const float2 xv = cscale(x[t], inv_m);
                 const float sf = __ldg(a.sqrtf_ + gi);
                 const float ax = sqrtf(xv.x * xv.x + xv.y * xv.y);
@@ -188,23 +191,23 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
                     gs = ax > 0.f ? 1.f - sf / ax : 0.f;
                 }
                 x[t] = cscale(xv, gs);
-            } else if (a.mode == B_MASK) {
+            } else if (MODE == B_MASK) {
                 x[t] = cscale(x[t], inv_m * __ldg(a.mask + freq_of(pr) * BM + freq_of(pc)));
-            } else if (a.mode == B_FWD_OUT) {
+            } else if (MODE == B_FWD_OUT) {
                 a.out[(size_t)j * BMM + freq_of(pr) * BM + freq_of(pc)] = cscale(x[t], inv_m);
             }
         }
-        if (a.mode != B_FWD_OUT) {
+        if (MODE != B_FWD_OUT) {
             dft<BR, true>(x);
 #pragma unroll
             for (int t = 0; t < BR; ++t) buf[(BR * hi + t) * PB + cl] = x[t];
         }
     }
-    if (a.mode == B_PROX || a.mode == B_LOSS) {
+    if (MODE == B_PROX || MODE == B_LOSS) {
         const float tot = block_sum_fixed(part, red);
         if (threadIdx.x == 0) a.part[a.part_off + blockIdx.x] = tot;
     }
-    if (a.mode == B_FWD_OUT) return;
+    if (MODE == B_FWD_OUT) return;
     __syncthreads();
     {   // inverse column stage 1
         float2 x[BR];
@@ -293,7 +296,13 @@ int run_waves(Pipeline P, int J, int waves_frames, cudaStream_t s)
         b.j0 = w0;
         b.nf = nf;
         b.part_off = w0 * slabs;
-        cols256_kernel<<<nf * slabs, NTB, SMEM_B, s>>>(b);
+        switch (b.mode) {
+        case B_PROX: cols256_kernel<B_PROX><<<nf * slabs, NTB, SMEM_B, s>>>(b); break;
+        case B_FWD_OUT: cols256_kernel<B_FWD_OUT><<<nf * slabs, NTB, SMEM_B, s>>>(b); break;
+        case B_LOSS: cols256_kernel<B_LOSS><<<nf * slabs, NTB, SMEM_B, s>>>(b); break;
+        case B_MASK: cols256_kernel<B_MASK><<<nf * slabs, NTB, SMEM_B, s>>>(b); break;
+        default: cols256_kernel<B_IFFT_IN><<<nf * slabs, NTB, SMEM_B, s>>>(b); break;
+        }
         OD2P_CUDA(cudaGetLastError());
         if (P.do_c) {
             PassC c = P.C;

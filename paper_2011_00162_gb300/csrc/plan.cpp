@@ -823,6 +823,10 @@ struct ptycho_batch_s {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int cur = 0;
+    // side streams and events of the per-class branches (graph capture only)
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_done;
+    cudaEvent_t fork = nullptr;
 };
 
 int ptycho_batch_destroy(ptycho_batch_t *b)
@@ -832,6 +836,9 @@ int ptycho_batch_destroy(ptycho_batch_t *b)
     for (int i = 0; i < 2; ++i)
         if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (cudaStream_t t : b->side) cudaStreamDestroy(t);
+    for (cudaEvent_t e : b->side_done) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
     release_owned(b->owned);
     for (ptycho_plan_s *p : b->plans) ptycho_plan_destroy(p);
     delete b;
@@ -904,6 +911,21 @@ int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const 
         for (int t = 0; t < b->plans[i]->sub_tiles.n_tiles; ++t) titems.push_back(make_int2(i, t));
     }
     b->n_titems = (int)titems.size();
+    // streams and events for the per-class branches of the iteration graph
+    for (size_t k = 1; k < b->cls.size(); ++k) {
+        cudaStream_t t = nullptr;
+        cudaEvent_t ev = nullptr;
+        cudaError_t e1 = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
+        if (e1 != cudaSuccess) return bail(cuda_fail(e1, "cudaStreamCreateWithFlags"));
+        b->side.push_back(t);
+        if ((e1 = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return bail(cuda_fail(e1, "cudaEventCreateWithFlags"));
+        b->side_done.push_back(ev);
+    }
+    if (b->cls.size() > 1) {
+        cudaError_t e1 = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        if (e1 != cudaSuccess) return bail(cuda_fail(e1, "cudaEventCreateWithFlags"));
+    }
     int rc;
     if ((rc = upload(&b->stab, stab, b->owned, s)) || (rc = upload(&b->titems, titems, b->owned, s))) return bail(rc);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -957,12 +979,27 @@ int ptycho_batch_get_launch(const ptycho_batch_t *b, int32_t *variant, int32_t *
     return PTYCHO_OK;
 }
 
+// One iteration of every member: the frame updates of the probe-side classes
+// are independent, so each class gets its own stream (parallel branches of the
+// captured graph) and the subdomain update waits for all of them.
 static int batch_enqueue(ptycho_batch_s *b, int parity, cudaStream_t s)
 {
-    for (const auto &c : b->cls)
+    const int nc = (int)b->cls.size();
+    if (nc > 1) {
+        OD2P_CUDA(cudaEventRecord(b->fork, s));
+        for (int k = 1; k < nc; ++k) OD2P_CUDA(cudaStreamWaitEvent(b->side[k - 1], b->fork, 0));
+    }
+    for (int k = 0; k < nc; ++k) {
+        const auto &c = b->cls[k];
+        cudaStream_t sk = k == 0 ? s : b->side[k - 1];
         if (int rc = launch_frame_update_table(c.m, b->variant, c.tab, c.items[b->variant], c.n_items[b->variant],
-                                               c.grid, parity, s))
+                                               c.grid, parity, sk))
             return rc;
+    }
+    for (int k = 1; k < nc; ++k) {
+        OD2P_CUDA(cudaEventRecord(b->side_done[k - 1], b->side[k - 1]));
+        OD2P_CUDA(cudaStreamWaitEvent(s, b->side_done[k - 1], 0));
+    }
     return launch_subdomain_update_table(false, b->stab, b->titems, b->n_titems, parity, s);
 }
 

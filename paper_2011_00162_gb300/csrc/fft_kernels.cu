@@ -764,14 +764,23 @@ __global__ void permute_kernel(int J, const float2 *src, float2 *dst, bool to_na
     }
 }
 
+constexpr int MAX_DEV = 64;     // per-device caches below are indexed by device ordinal
+std::mutex g_attr_mu;            // guards every per-device attribute cache
+
+// Raise a kernel's dynamic shared-memory limit once per device (the attribute
+// belongs to the device's context).
 template <int M, class K>
 int set_smem(K kernel)
 {
-    static bool done = false;
-    if (!done) {
+    static bool done[MAX_DEV] = {};
+    int dev = 0;
+    OD2P_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEV) return fail(PTYCHO_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (!done[dev]) {
         OD2P_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes<M>()));
-        done = true;
+        done[dev] = true;
     }
     return PTYCHO_OK;
 }
@@ -802,11 +811,11 @@ int set_smem(K kernel)
 template <int M, int V>
 int k1_per_sm(int *per_sm_out, int *n_sm_out)
 {
-    constexpr int MAX_DEV = 64;  // cached per device: the shared-memory attribute is per context
-    static int per_sm[MAX_DEV] = {}, n_sm[MAX_DEV] = {};
+    static int per_sm[MAX_DEV] = {}, n_sm[MAX_DEV] = {};  // per device: the attribute is per context
     int dev = 0;
     OD2P_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= MAX_DEV) return fail(PTYCHO_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_attr_mu);
     if (!per_sm[dev]) {
         OD2P_CUDA(cudaFuncSetAttribute(frame_update_kernel<M, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)k1_smem_bytes<M, V>()));

@@ -277,18 +277,34 @@ __global__ void __launch_bounds__(GATHER_THREADS) image_gather_kernel(
     float2 acc[TILE_ROWS];
 #pragma unroll
     for (int r = 0; r < TILE_ROWS; ++r) acc[r] = make_float2(0.f, 0.f);
-    for (int k = tptr[blockIdx.x]; k < tptr[blockIdx.x + 1]; ++k) {
-        const ListEntry e = tlist[k];
-        const int dr0 = e.dr + ty0, dc = e.dc + lane;
-        if (dr0 + TILE_ROWS <= 0 || dr0 >= M || (unsigned)dc >= (unsigned)M) continue;
+    // two list entries per step, branch-free: a lane whose pixel a frame does not
+    // cover loads element 0 and discards it (sums stay in ascending j)
+    constexpr int U = 2;
+    const int k0 = tptr[blockIdx.x], k1 = tptr[blockIdx.x + 1];
+    for (int k = k0; k < k1; k += U) {
+        float2 hv[U][TILE_ROWS], wv[U][TILE_ROWS];
+        unsigned hits = 0u;
 #pragma unroll
-        for (int r = 0; r < TILE_ROWS; ++r) {
-            const int dr = dr0 + r;
-            if (r < nrows && (unsigned)dr < (unsigned)M) {
-                const float2 hv = __ldg(h + (size_t)e.j * MM + dr * M + dc);
-                acc[r] = cadd(acc[r], w ? cconjmul(__ldg(w + dr * M + dc), hv) : hv);
+        for (int u = 0; u < U; ++u) {
+            const ListEntry e = k + u < k1 ? tlist[k + u] : ListEntry{0, M, M, 0};
+            const int dr0 = e.dr + ty0, dc = e.dc + lane;
+            const bool cok = (unsigned)dc < (unsigned)M;
+#pragma unroll
+            for (int r = 0; r < TILE_ROWS; ++r) {
+                const int dr = dr0 + r;
+                const bool hit = cok && r < nrows && (unsigned)dr < (unsigned)M;
+                const int o = hit ? dr * M + dc : 0;
+                hv[u][r] = __ldg(h + (hit ? (size_t)e.j * MM + o : 0));
+                if (w) wv[u][r] = __ldg(w + o);
+                hits |= (hit ? 1u : 0u) << (u * TILE_ROWS + r);
             }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int r = 0; r < TILE_ROWS; ++r)
+                if (hits & (1u << (u * TILE_ROWS + r)))
+                    acc[r] = cadd(acc[r], w ? cconjmul(wv[u][r], hv[u][r]) : hv[u][r]);
     }
 #pragma unroll
     for (int r = 0; r < TILE_ROWS; ++r)

@@ -42,7 +42,7 @@ template <> struct Radix<32> { static constexpr int R1 = 8, R2 = 4, FPB = 4, NT 
 #define OD2P_MINB64 6
 #endif
 template <> struct Radix<64> { static constexpr int R1 = 8, R2 = 8, FPB = 1, NT = OD2P_NT64, MINB = OD2P_MINB64; };
-template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8, FPB = 1, NT = 512, MINB = 1; };
+template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8, FPB = 1, NT = 1024, MINB = 1; };
 // probe sides that are not powers of two: mixed-radix splits (stage 2 uses the
 // 6-, 5- and 12-point DFTs)
 template <> struct Radix<48> { static constexpr int R1 = 8, R2 = 6, FPB = 2, NT = 384, MINB = 1; };
@@ -611,6 +611,11 @@ __global__ void __launch_bounds__(Radix<M>::NT) loss_kernel(LossArgs a)
     float2 *buf = tw + M;
     float *red = reinterpret_cast<float *>(buf + FPB * M * P);
     const int j0 = blockIdx.x * FPB;
+    if (threadIdx.x == 0) {  // this group's sqrt f into L2 while the forward FFT runs
+        const unsigned bytes = (unsigned)(min(FPB, a.J - j0) * MM * sizeof(float));
+        const char *fp = reinterpret_cast<const char *>(a.sqrtf_ + (size_t)j0 * MM);
+        for (unsigned off = 0; off < bytes; off += 16384u) bulk_prefetch_l2(fp + off, min(16384u, bytes - off));
+    }
     for (int k = threadIdx.x; k < M; k += NT) tw[k] = a.tw[k];
     __syncthreads();
     for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
@@ -650,14 +655,16 @@ __global__ void __launch_bounds__(Radix<M>::NT) loss_kernel(LossArgs a)
             const size_t idx = base + (size_t)(R2 * s + t) * M;
             const float2 xv = cscale(x[t], inv_m);
             const float sf = __ldg(a.sqrtf_ + idx);
-            const float ax = sqrtf(xv.x * xv.x + xv.y * xv.y);
+            const float a2 = xv.x * xv.x + xv.y * xv.y;
+            const float inv = rsqrtf(a2);  // 1/|x|, used only when a2 > 0
+            const float ax = a2 > 0.f ? a2 * inv : 0.f;
             float gv, gs;  // g_eps (eq. obj-1) and grad g = gs * x (eq. objgrad)
             if (ax < eps * sf) {
-                gv = 0.5f * (1.f - eps) * (sf * sf - ax * ax / eps);
+                gv = 0.5f * (1.f - eps) * (sf * sf - a2 / eps);
                 gs = 1.f - 1.f / eps;
             } else {
                 gv = 0.5f * (ax - sf) * (ax - sf);
-                gs = ax > 0.f ? 1.f - sf / ax : 0.f;
+                gs = a2 > 0.f ? 1.f - sf * inv : 0.f;
             }
             loss += gv;
             x[t] = cscale(xv, gs);

@@ -83,6 +83,8 @@ def _load():
             "orc_admm_set": (None, [P, i32, P]),
             "orc_admm_metrics": (None, [P, P, P]),
             "orc_admm_merge": (None, [P, P]),
+            "orc_admm_set_penalties": (None, [P, f64, f64]),
+            "orc_admm_consensus": (f64, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -234,6 +236,14 @@ class ADMM:
         if h:
             self._lib.orc_admm_free(h)
             self._h = None
+
+    def set_penalties(self, eta: float, r: float) -> None:
+        """Change eta and r, keeping the unscaled multipliers eta*Gamma and r*Lambda."""
+        self._lib.orc_admm_set_penalties(self._h, float(eta), float(r))
+
+    def consensus(self) -> float:
+        """||u_d - u_e|| over the pairs' overlaps relative to ||u||."""
+        return float(self._lib.orc_admm_consensus(self._h))
 
     def iterate(self, n: int = 1) -> None:
         self._lib.orc_admm_iterate(self._h, int(n))

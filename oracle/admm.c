@@ -357,3 +357,40 @@ void orc_admm_merge(const orc_admm *s, ocplx *u_out)
             u_out[(size_t)R * s->W + C] = n ? t / (double)n : 1.0;
         }
 }
+
+/* Change the penalties eta (z = A u splitting) and r (v = pi u consensus)
+ * between iterations.  Gamma and Lambda are the scaled multipliers of the
+ * augmented Lagrangian, so the unscaled ones (eta Gamma, r Lambda) are kept:
+ * Gamma <- (eta / eta') Gamma, Lambda <- (r / r') Lambda (the rescaling of
+ * Boyd, Parikh, Chu, Peleato, Eckstein 2011, section 3.4.1).                */
+void orc_admm_set_penalties(orc_admm *s, double eta, double r)
+{
+    const double ge = s->eta / eta;
+    for (int64_t k = 0; k < (int64_t)s->J * s->mm; ++k) s->Gamma[k] *= ge;
+    if (r > 0.0) {
+        const double gl = s->r / r;
+        for (int64_t k = 0; k < s->lam_off[s->P]; ++k) s->Lam[k] *= gl;
+    }
+    s->eta = eta;
+    s->r = r;
+}
+
+/* Consensus residual: || u_d - u_e || over every ordered pair's overlap,
+ * relative to || u || over all subdomain pixels (0 when there are no pairs). */
+double orc_admm_consensus(const orc_admm *s)
+{
+    double num = 0.0, den = 0.0;
+    for (int k = 0; k < s->P; ++k) {
+        const int d = s->pair[2 * k], e = s->pair[2 * k + 1];
+        const int32_t *pr = s->pair_rect + 4 * k;
+        for (int R = pr[0]; R < pr[2]; ++R)
+            for (int C = pr[1]; C < pr[3]; ++C) {
+                const ocplx a = s->u[s->u_off[d] + rect_idx(s->rect + 4 * d, R, C)];
+                const ocplx b = s->u[s->u_off[e] + rect_idx(s->rect + 4 * e, R, C)];
+                const ocplx t = a - b;
+                num += creal(t) * creal(t) + cimag(t) * cimag(t);
+            }
+    }
+    for (int64_t k = 0; k < s->u_off[s->D]; ++k) den += creal(s->u[k]) * creal(s->u[k]) + cimag(s->u[k]) * cimag(s->u[k]);
+    return den > 0.0 ? sqrt(num / den) : 0.0;
+}

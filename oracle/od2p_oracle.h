@@ -91,6 +91,11 @@ void orc_admm_set(orc_admm *s, int which, const ocplx *in);
 /* RF of the iterate entering the last iteration and RE of the last update. */
 void orc_admm_metrics(const orc_admm *s, double *rf, double *re);
 /* Merged image (section 4 set-up: overlaps averaged) and shared probe. */
+/* Penalty change between iterations, keeping the unscaled multipliers
+ * (Gamma <- eta/eta' Gamma, Lambda <- r/r' Lambda); consensus residual
+ * ||u_d - u_e|| over the ordered pairs' overlaps relative to ||u||.          */
+void orc_admm_set_penalties(orc_admm *s, double eta, double r);
+double orc_admm_consensus(const orc_admm *s);
 void orc_admm_merge(const orc_admm *s, ocplx *u_out);
 
 #endif

@@ -619,3 +619,65 @@ def test_non_power_of_two_probe_fixed_point_and_dense_operator(m, n, step):
     a.iterate(3)
     np.testing.assert_allclose(a.merge(), u, atol=1e-11)
     assert np.abs(a.get(oracle.GAMMA)).max() < 1e-11
+
+
+# ----------------------------------------------------------------------------- penalty changes
+def _noisy_small():
+    p = synth.Problem("pc", 96, 16, 4, 1, 2, 2, 8, 1e4, 1, eta=2.0, r=0.5, seed=6)
+    offs = p.offsets()
+    u, w = p.truth(), p.probe()
+    f = synth.poissonize(np.abs(oracle.forward(u, w, offs)) ** 2, p.peak, 3)
+    return p, offs, w, f
+
+
+def test_penalty_change_keeps_unscaled_multipliers():
+    """Changing (eta, r) rescales the scaled multipliers so that eta*Gamma and
+    r*Lambda stay (Boyd et al. 2011, 3.4.1).  The unscaled multipliers of a run
+    that has nearly settled do not depend on the penalties, so with the
+    rescaling the next step moves about as far as a step with unchanged
+    penalties; left unscaled, the same change makes the run jump."""
+    p, offs, w, f = _noisy_small()
+    a = oracle.ADMM(f, w, offs, p.n, p.n, 2, 2, 8, 0.5, 2.0, 0.5)
+    a.iterate(400)
+    g0, l0, u0 = a.get(oracle.GAMMA), a.get(oracle.LAMBDA), a.get(oracle.U)
+    a.set_penalties(2.0, 0.5)  # same values: nothing changes
+    assert np.array_equal(a.get(oracle.GAMMA), g0) and np.array_equal(a.get(oracle.LAMBDA), l0)
+
+    def step(eta, r, rescale):
+        b = oracle.ADMM(f, w, offs, p.n, p.n, 2, 2, 8, 0.5, 2.0 if rescale else eta, 0.5 if rescale else r)
+        for k, v in ((oracle.U, u0), (oracle.GAMMA, g0), (oracle.LAMBDA, l0)):
+            b.set(k, v)
+        if rescale:
+            b.set_penalties(eta, r)
+            np.testing.assert_allclose(eta * b.get(oracle.GAMMA), 2.0 * g0, rtol=1e-14, atol=1e-15)
+            np.testing.assert_allclose(r * b.get(oracle.LAMBDA), 0.5 * l0, rtol=1e-14, atol=1e-15)
+        b.iterate(1)
+        return np.linalg.norm(b.get(oracle.U) - u0) / np.linalg.norm(u0)
+
+    base = step(2.0, 0.5, True)
+    for eta, r in [(4.0, 2.0), (2.0, 2.0), (8.0, 0.5)]:
+        kept, jumped = step(eta, r, True), step(eta, r, False)
+        assert kept < 2 * base and jumped > 5 * kept, (eta, r, base, kept, jumped)
+
+
+def test_consensus_residual():
+    """0 for one subdomain and at the noiseless truth; a constant c added to one
+    subdomain's copy gives |c| sqrt(2 * overlap pixels of its pairs) / ||u||."""
+    p = synth.small_2sub()
+    offs = p.offsets()
+    u, w = p.truth().astype(complex), p.probe().astype(complex)
+    f = np.abs(oracle.forward(u, w, offs)) ** 2
+    one = oracle.ADMM(f, w, offs, 64, 64, 1, 1, 0, 0.5, 0.1, 0.05, u0=u)
+    assert one.consensus() == 0.0
+    a = oracle.ADMM(f, w, offs, 64, 64, 2, 2, 8, 0.5, 0.1, 0.05, u0=u)
+    assert a.consensus() < 1e-15
+    fs, rect = oracle.geometry(64, 64, 16, offs, 2, 2, 8)
+    pr, prc = oracle.pairs(rect)
+    sizes = [(r[2] - r[0]) * (r[3] - r[1]) for r in rect]
+    uu = a.get(oracle.U).copy()
+    c = 0.25 - 0.5j
+    uu[:sizes[0]] += c
+    a.set(oracle.U, uu)
+    ov = sum((q[2] - q[0]) * (q[3] - q[1]) for (d, e), q in zip(pr, prc) if d == 0)
+    expect = abs(c) * np.sqrt(2 * ov) / np.linalg.norm(uu)
+    assert abs(a.consensus() - expect) < 1e-12 * expect

@@ -235,6 +235,27 @@ int od2p_merge(const ptycho_plan_t *plan, ptycho_c32 *u_out_dev, ptycho_stream_t
 int od2p_metrics(ptycho_plan_t *plan, float *rf_host, float *re_host, ptycho_stream_t stream);
 
 /*
+ * Penalty changes between iterations (the paper fixes eta and r for a run and
+ * names their adaptive choice future work, section 5).  Gamma and Lambda are
+ * the scaled multipliers of the augmented Lagrangian, so a change keeps the
+ * unscaled ones: Gamma <- (eta_old / eta) Gamma, Lambda <- (r_old / r) Lambda
+ * (the rescaling of Boyd, Parikh, Chu, Peleato, Eckstein 2011, 3.4.1; Lambda
+ * is left alone when r = 0).  Drops the captured iteration graphs and
+ * synchronises `stream`.  Errors: INVALID_ARG (eta <= 0, r < 0, not finite),
+ * STATE (a batch member), CUDA.
+ */
+int od2p_set_penalties(ptycho_plan_t *plan, float eta, float r, ptycho_stream_t stream);
+
+/*
+ * Consensus residual of the current iterate: ||u_d - u_e|| summed over every
+ * ordered pair's overlap, relative to ||u|| over all subdomain pixels (0 with
+ * no pairs), reduced in a fixed order -- the primal residual of the consensus
+ * constraint v = pi u_d = pi u_e of eq. (updateV-multi).  Writes a host float
+ * and synchronises `stream`.  Errors: INVALID_ARG, CUDA.
+ */
+int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t stream);
+
+/*
  * Data-driven initial probe of the blind experiments (section 4.3):
  * w0 = (1/J) sum_j F^* sqrt(f_j), from the intensities the plan holds.  The GPU
  * forms F^* of the mean amplitude (equal by linearity): the amplitudes are

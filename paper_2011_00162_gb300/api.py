@@ -24,7 +24,7 @@ __all__ = [
     "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
     "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
-    "ptycho_release_cached_memory",
+    "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual",
 ]
 
 LAUNCH_VARIANTS = _lib.LAUNCH_VARIANTS
@@ -207,6 +207,19 @@ def ptycho_batch_plan(geoms: list, fs: list, stream=None) -> Batch:
 
 def ptycho_batch_iterate(batch: Batch, n_iter: int = 1, stream=None) -> None:
     batch.iterate(n_iter, stream)
+
+
+def od2p_set_penalties(plan: Plan, eta: float, r: float, stream=None) -> None:
+    """Change the penalties for the next iterations, keeping eta*Gamma and r*Lambda."""
+    check(plan._lib.od2p_set_penalties(plan.handle, float(eta), float(r), _stream(stream)))
+    plan.geom = dataclasses.replace(plan.geom, eta=float(eta), r=float(r))
+
+
+def od2p_consensus_residual(plan: Plan, stream=None) -> float:
+    """||u_d - u_e|| over the pairs' overlaps relative to ||u||."""
+    v = ctypes.c_float()
+    check(plan._lib.od2p_consensus_residual(plan.handle, ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def ptycho_release_cached_memory() -> None:

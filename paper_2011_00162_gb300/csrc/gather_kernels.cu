@@ -311,6 +311,54 @@ __global__ void __launch_bounds__(GATHER_THREADS) image_gather_kernel(
         if (r < nrows) out[(size_t)(R0 + r) * W + C] = acc[r];
 }
 
+// ---------------------------------------------------------------- penalties and consensus
+// x <- s x for n complex values (rescaling of a scaled multiplier).
+__global__ void scale_kernel(int64_t n, float2 *x, float s)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        x[e] = cscale(x[e], s);
+}
+
+constexpr int RC_BLOCKS = 64;  // blocks per ordered pair / over u in the consensus residual
+
+// part[k * RC_BLOCKS + b] = sum over block b's share (element-strided, fixed
+// order) of |u_d - u_e|^2 on ordered pair k's overlap; part[P * RC_BLOCKS + b]
+// likewise of |u|^2 over all subdomain pixels.
+__global__ void __launch_bounds__(256) consensus_partial_kernel(int P, const int32_t *pair, const int32_t *pair_rect,
+                                                                const int32_t *rect, const int64_t *u_off,
+                                                                int64_t u_len, const float2 *u, float *part)
+{
+    __shared__ float red[2 * (256 / 32)];
+    const int k = blockIdx.y;
+    float acc = 0.f, dummy = 0.f;
+    if (k < P) {
+        const int d = pair[2 * k], e = pair[2 * k + 1];
+        const int32_t *pr = pair_rect + 4 * k, *Rd = rect + 4 * d, *Re = rect + 4 * e;
+        const int w = pr[3] - pr[1];
+        const int64_t n = (int64_t)(pr[2] - pr[0]) * w;
+        for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += RC_BLOCKS * 256) {
+            const int R = pr[0] + (int)(i / w), C = pr[1] + (int)(i % w);
+            const float2 a = u[u_off[d] + (int64_t)(R - Rd[0]) * (Rd[3] - Rd[1]) + (C - Rd[1])];
+            const float2 b = u[u_off[e] + (int64_t)(R - Re[0]) * (Re[3] - Re[1]) + (C - Re[1])];
+            acc += cabs2(csub(a, b));
+        }
+    } else {
+        for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < u_len; i += RC_BLOCKS * 256) acc += cabs2(u[i]);
+    }
+    block_sum2_fixed(acc, dummy, red);
+    if (threadIdx.x == 0) part[(size_t)k * RC_BLOCKS + blockIdx.x] = acc;
+}
+
+// out = sqrt(sum over the pairs' parts / sum of the |u|^2 parts), in order.
+__global__ void consensus_final_kernel(int P, const float *part, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < P * RC_BLOCKS; ++i) num += part[i];
+    for (int i = 0; i < RC_BLOCKS; ++i) den += part[(size_t)P * RC_BLOCKS + i];
+    *out = den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
 // ---------------------------------------------------------------- probe reductions
 // Level 1: per chunk of PROBE_CHUNK frames of one group, for every probe pixel k:
 //   part[c][k] = sum_{j in chunk, ascending} conj(u(o_j + k)) h_j(k), part_n = sum |u(o_j + k)|^2.
@@ -797,6 +845,24 @@ int launch_probe_init(ptycho_plan_s *p, float2 *w0, cudaStream_t s)
     idft_rows_kernel<<<blocks, 256, 0, s>>>(p->M, amp, p->d_tw, T);
     OD2P_CUDA(cudaGetLastError());
     idft_cols_kernel<<<blocks, 256, 0, s>>>(p->M, T, p->d_tw, w0);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_scale(float2 *x, int64_t n, float sc, cudaStream_t s)
+{
+    if (n <= 0) return PTYCHO_OK;
+    scale_kernel<<<152 * 8, 256, 0, s>>>(n, x, sc);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_consensus(ptycho_plan_s *p, float *part, double *out, cudaStream_t s)
+{
+    consensus_partial_kernel<<<dim3(RC_BLOCKS, p->P + 1), 256, 0, s>>>(p->P, p->d_pair, p->d_pair_rect, p->d_rect,
+                                                                        p->d_u_off, p->u_len, p->d_u[p->cur], part);
+    OD2P_CUDA(cudaGetLastError());
+    consensus_final_kernel<<<1, 32, 0, s>>>(p->P, part, out);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }

@@ -168,7 +168,7 @@ struct ptycho_plan_s {
     // ---- device geometry
     int32_t *d_offs = nullptr, *d_frame_sub = nullptr, *d_frame_base = nullptr,
             *d_frame_pitch = nullptr, *d_rect = nullptr, *d_nbr_ptr = nullptr, *d_nbr = nullptr,
-            *d_pair_rect = nullptr, *d_img_base = nullptr,  // nbr: (e, pair d-e, pair e-d) per neighbour
+            *d_pair_rect = nullptr, *d_pair = nullptr, *d_img_base = nullptr,  // nbr: (e, pair d-e, pair e-d) per neighbour
             *d_img_pitch = nullptr;                      // img_w for every frame
     od2p::NbrInfo *d_nbr_info = nullptr;  // per neighbour entry, same order as d_nbr
     int64_t *d_u_off = nullptr, *d_lam_off = nullptr;
@@ -202,7 +202,8 @@ struct ptycho_plan_s {
     float *d_rf_part = nullptr;        // one per frame-kernel block
     float *d_re_part = nullptr;        // 2 per subdomain tile
     float *d_loss_part = nullptr;
-    double *d_metrics = nullptr;       // [rf, re, sum sqrt f]
+    double *d_metrics = nullptr;       // [rf, re, sum sqrt f, consensus residual]
+    float *d_rc_part = nullptr;        // (P + 1) x 64 partial sums of the consensus residual
     int32_t *d_err = nullptr;          // set by a kernel whose bounded wait gave up
     int32_t n_k1_blocks = 0;           // blocks of the persistent frame update
     int32_t k1_variant = 0;            // launch shape of the frame update (0 or 1)
@@ -265,6 +266,8 @@ int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w
 int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, cudaStream_t s);
 int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s);
 int launch_metrics(ptycho_plan_s *p, cudaStream_t s);
+int launch_scale(float2 *x, int64_t n, float sc, cudaStream_t s);
+int launch_consensus(ptycho_plan_s *p, float *part, double *out, cudaStream_t s);
 int launch_probe_init(ptycho_plan_s *p, float2 *w0, cudaStream_t s);
 int launch_slot_rank(ptycho_plan_s *p, int32_t *setup, cudaStream_t s);
 // Split m = R1 * R2 of the frame update's FFT, which fixes the task order of

@@ -465,6 +465,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = upload(&p->d_img_pitch, img_pitch, own, s)) ||
         (rc = upload(&p->d_rect, p->rect, own, s)) || (rc = upload(&p->d_nbr_ptr, nbr_ptr, own, s)) ||
         (rc = upload(&p->d_nbr, nbr, own, s)) || (rc = upload(&p->d_pair_rect, p->pair_rect, own, s)) ||
+        (rc = upload(&p->d_pair, p->pair, own, s)) ||
         (rc = upload(&p->d_nbr_info, nbr_info, own, s)) ||
         (rc = upload(&p->d_u_off, p->u_off, own, s)) || (rc = upload(&p->d_lam_off, p->lam_off, own, s)) ||
         (rc = upload_tiles(p->sub_tiles, st, own, s)) || (rc = upload_tiles(p->img_tiles, it, own, s)) ||
@@ -506,7 +507,8 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = dev_alloc(&p->d_rf_part, rf_cap, own, s)) ||
         (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own, s)) ||
         (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own, s)) ||
-        (rc = dev_alloc(&p->d_metrics, 3, own, s)) || (rc = dev_alloc(&p->d_err, 1, own, s)))
+        (rc = dev_alloc(&p->d_metrics, 4, own, s)) || (rc = dev_alloc(&p->d_err, 1, own, s)) ||
+        (rc = dev_alloc(&p->d_rc_part, (size_t)(p->P + 1) * 64, own, s)))
         return bail(rc);
     if (p->blind) {
         if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own, s)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own, s)))
@@ -534,7 +536,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
             return bail(rc);
     }
     cudaError_t e;
-    if ((e = cudaMemsetAsync(p->d_metrics, 0, 3 * sizeof(double), s)) != cudaSuccess ||
+    if ((e = cudaMemsetAsync(p->d_metrics, 0, 4 * sizeof(double), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * rf_cap, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_re_part, 0, sizeof(float) * 2 * p->sub_tiles.n_tiles, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_w, 0, sizeof(float2) * p->MM, s)) != cudaSuccess ||
@@ -692,6 +694,42 @@ int od2p_metrics(ptycho_plan_t *plan, float *rf, float *re, ptycho_stream_t stre
     if (err) return fail(PTYCHO_ERR_TIMEOUT, "a frame-update pipeline wait gave up (device error flag set)");
     if (rf) *rf = (float)h[0];
     if (re) *re = (float)h[1];
+    return PTYCHO_OK;
+}
+
+int od2p_set_penalties(ptycho_plan_t *plan, float eta, float r, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (!(eta > 0.f) || !(r >= 0.f) || !std::isfinite(eta) || !std::isfinite(r))
+        return fail(PTYCHO_ERR_INVALID_ARG, "need eta > 0 and r >= 0");
+    if (plan->batch_member) return fail(PTYCHO_ERR_STATE, "the penalties of a batch member are fixed");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ptycho_plan_s *p = plan;
+    // keep the unscaled multipliers eta Gamma and r Lambda
+    if (eta != p->eta)
+        if (int rc = launch_scale(p->d_gamma, (int64_t)p->J * p->MM, p->eta / eta, s)) return rc;
+    if (r > 0.f && r != p->r)
+        if (int rc = launch_scale(p->d_lam[p->cur], p->lam_len, p->r / r, s)) return rc;
+    p->eta = eta;
+    p->r = r;
+    fill_frame_args(p, p->h_fargs);
+    fill_sub_args(p, p->h_sargs);
+    OD2P_CUDA(cudaMemcpyAsync(p->d_fargs, p->h_fargs, sizeof(p->h_fargs), cudaMemcpyHostToDevice, s));
+    OD2P_CUDA(cudaMemcpyAsync(p->d_sargs, p->h_sargs, sizeof(p->h_sargs), cudaMemcpyHostToDevice, s));
+    OD2P_CUDA(cudaStreamSynchronize(s));  // the host argument copies are read by the next launches
+    drop_graphs(p->graph);
+    return PTYCHO_OK;
+}
+
+int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t stream)
+{
+    if (!plan || !rc_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = launch_consensus(plan, plan->d_rc_part, plan->d_metrics + 3, s)) return rc;
+    double h = 0.0;
+    OD2P_CUDA(cudaMemcpyAsync(&h, plan->d_metrics + 3, sizeof(h), cudaMemcpyDeviceToHost, s));
+    OD2P_CUDA(cudaStreamSynchronize(s));
+    *rc_host = (float)h;
     return PTYCHO_OK;
 }
 

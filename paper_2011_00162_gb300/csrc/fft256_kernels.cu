@@ -74,18 +74,27 @@ __global__ void __launch_bounds__(NTB) rows_fwd256_kernel(PassA a)
     const int f = blockIdx.x / (BM / SLAB), rb = blockIdx.x % (BM / SLAB), j = a.j0 + f;
     for (int k = threadIdx.x; k < BM; k += NTB) tw[k] = a.tw[k];
     const int c = threadIdx.x;
+    // all of the thread's loads in flight before the first shared-memory store
+    float2 v[SLAB];
     if (a.plain) {
-        for (int r = 0; r < SLAB; ++r)
-            buf[r * PA + c] = __ldg(a.plain + (size_t)j * BMM + (rb * SLAB + r) * BM + c);
+#pragma unroll
+        for (int r = 0; r < SLAB; ++r) v[r] = __ldg(a.plain + (size_t)j * BMM + (rb * SLAB + r) * BM + c);
     } else {
         const float2 *w = a.Wd ? a.Wd + (size_t)a.frame_sub[j] * BMM : a.w;
         const float2 *uj = a.u + a.frame_base[j];
         const int pitch = a.frame_pitch[j];
+        float2 wv[SLAB];
+#pragma unroll
         for (int r = 0; r < SLAB; ++r) {
             const int row = rb * SLAB + r;
-            buf[r * PA + c] = cmul(__ldg(w + row * BM + c), __ldg(uj + (size_t)row * pitch + c));
+            wv[r] = __ldg(w + row * BM + c);
+            v[r] = __ldg(uj + (size_t)row * pitch + c);
         }
+#pragma unroll
+        for (int r = 0; r < SLAB; ++r) v[r] = cmul(wv[r], v[r]);
     }
+#pragma unroll
+    for (int r = 0; r < SLAB; ++r) buf[r * PA + c] = v[r];
     __syncthreads();
     {   // row stage 1: lanes on rows (odd pitch), 16 strided elements each
         const int r = threadIdx.x % SLAB, n1 = threadIdx.x / SLAB;
@@ -134,15 +143,19 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
     }
     for (int k = threadIdx.x; k < BM; k += NTB) tw[k] = a.tw[k];
     {
+        constexpr int NR = BM / (NTB / SLAB);  // rows per thread
         const int cl = threadIdx.x % SLAB, r0 = threadIdx.x / SLAB;
-        for (int r = r0; r < BM; r += NTB / SLAB) {
-            float2 v;
+        float2 v[NR];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int r = r0 + i * (NTB / SLAB);
             if (MODE == B_IFFT_IN)
-                v = __ldg(a.in + (size_t)j * BMM + freq_of(r) * BM + freq_of(cb * SLAB + cl));
+                v[i] = __ldg(a.in + (size_t)j * BMM + freq_of(r) * BM + freq_of(cb * SLAB + cl));
             else
-                v = a.T[((size_t)f * BM + r) * BM + cb * SLAB + cl];
-            buf[r * PB + cl] = v;
+                v[i] = a.T[((size_t)f * BM + r) * BM + cb * SLAB + cl];
         }
+#pragma unroll
+        for (int i = 0; i < NR; ++i) buf[(r0 + i * (NTB / SLAB)) * PB + cl] = v[i];
     }
     __syncthreads();
     const int cl = threadIdx.x % SLAB, hi = threadIdx.x / SLAB;  // hi: n1 (stage 1) or s (stage 2)
@@ -233,7 +246,13 @@ __global__ void __launch_bounds__(NTB) rows_inv256_kernel(PassC a, const float2 
     const int f = blockIdx.x / (BM / SLAB), rb = blockIdx.x % (BM / SLAB), j = a.j0 + f;
     for (int k = threadIdx.x; k < BM; k += NTB) tw[k] = twg[k];
     const int c = threadIdx.x;
-    for (int r = 0; r < SLAB; ++r) buf[r * PA + c] = a.T[((size_t)f * BM + rb * SLAB + r) * BM + c];
+    {
+        float2 v[SLAB];
+#pragma unroll
+        for (int r = 0; r < SLAB; ++r) v[r] = a.T[((size_t)f * BM + rb * SLAB + r) * BM + c];
+#pragma unroll
+        for (int r = 0; r < SLAB; ++r) buf[r * PA + c] = v[r];
+    }
     __syncthreads();
     {   // inverse row stage 2
         const int r = threadIdx.x % SLAB, s = threadIdx.x / SLAB;

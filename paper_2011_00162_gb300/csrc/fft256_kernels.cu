@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(NTB) rows_fwd256_kernel(PassA a)
 }
 
 #ifndef OD2P_COLS256_MINB
-#define OD2P_COLS256_MINB 5
+#define OD2P_COLS256_MINB 4
 #endif
 // MODE: the elementwise step between the column transforms (compile-time, so
 // that the per-element loop carries no mode tests).
@@ -173,8 +173,20 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
         float2 x[BR];
 #pragma unroll
         for (int t = 0; t < BR; ++t) x[t] = buf[(BR * hi + t) * PB + cl];
-        if (MODE != B_IFFT_IN) dft<BR, false>(x);
         const int pc = cb * SLAB + cl;
+        // Gamma and sqrt f of the thread's column segment, loaded before any
+        // Gamma store (the compiler may not move loads past those stores)
+        float2 gmv[MODE == B_PROX ? BR : 1];
+        float sfv[MODE == B_PROX || MODE == B_LOSS ? BR : 1];
+        if (MODE == B_PROX || MODE == B_LOSS) {
+#pragma unroll
+            for (int t = 0; t < BR; ++t) {
+                const size_t gi = (size_t)j * BMM + (size_t)(BR * hi + t) * BM + pc;
+                sfv[t] = __ldg(a.sqrtf_ + gi);
+                if (MODE == B_PROX) gmv[MODE == B_PROX ? t : 0] = a.gamma[gi];
+            }
+        }
+        if (MODE != B_IFFT_IN) dft<BR, false>(x);
         const float inv_m = 1.f / (float)BM;
 #pragma unroll
         for (int t = 0; t < BR; ++t) {
@@ -182,8 +194,8 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
             const size_t gi = (size_t)j * BMM + (size_t)pr * BM + pc;
             if (MODE == B_PROX) {
                 const float2 ax = cscale(x[t], inv_m);
-                const float sf = __ldg(a.sqrtf_ + gi);
-                const float2 gm = a.gamma[gi];
+                const float sf = sfv[t];
+                const float2 gm = gmv[MODE == B_PROX ? t : 0];
                 const float a2 = ax.x * ax.x + ax.y * ax.y;
                 part += fabsf((a2 > 0.f ? a2 * rsqrtf(a2) : 0.f) - sf);
                 const float2 y = cadd(gm, ax);
@@ -193,7 +205,7 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
                 x[t] = csub(z, gn);
             } else if (MODE == B_LOSS) {
                 const float2 xv = cscale(x[t], inv_m);
-                const float sf = __ldg(a.sqrtf_ + gi);
+                const float sf = sfv[MODE == B_LOSS ? t : 0];
                 const float ax = sqrtf(xv.x * xv.x + xv.y * xv.y);
                 float gs;
                 if (ax < a.eps * sf) {

@@ -467,15 +467,22 @@ __global__ void __launch_bounds__(K1Cfg<M, V>::NT, K1Cfg<M, V>::MINB)
             float2 x[R2];
 #pragma unroll
             for (int t = 0; t < R2; ++t) x[t] = fb[R2 * s + t];
-            dft<R2, false>(x);
             const int lbase = f * MM + r;
+            // Gamma from global memory (not staged): all loads before the stores
+            // below, which the compiler may not move them past
+            float2 gmv[SG ? 1 : R2];
+            if (!SG) {
+#pragma unroll
+                for (int t = 0; t < R2; ++t) gmv[SG ? 0 : t] = sa.gamma[(size_t)j0 * MM + lbase + (R2 * s + t) * M];
+            }
+            dft<R2, false>(x);
 #pragma unroll
             for (int t = 0; t < R2; ++t) {
                 const int li = lbase + (R2 * s + t) * M;
                 const size_t gi = (size_t)j0 * MM + li;
                 const float2 ax = cscale(x[t], inv_m);   // (A_d u_d^n)_k
                 const float sf = stg_f[li];
-                const float2 gm = SG ? stg_g[li] : sa.gamma[gi];
+                const float2 gm = SG ? stg_g[li] : gmv[SG ? 0 : t];
                 const float a2 = ax.x * ax.x + ax.y * ax.y;
                 rf += fabsf((a2 > 0.f ? a2 * rsqrtf(a2) : 0.f) - sf);  // | |A_d u_d| - sqrt f |
                 const float2 y = cadd(gm, ax);            // Gamma^n + A_d u_d^n

@@ -25,10 +25,10 @@ constexpr int TILE_ROWS = TILE_H * TILE_W / GATHER_THREADS;
 // Frames per chunk of the fixed-order probe reductions (blind W, grad w).
 constexpr int PROBE_CHUNK = 32;
 // m = 256 frames go through their three FFT passes in waves of this many
-// frames (a 47.5 MB intermediate that stays in L2; 95 frames x 16 column slabs
-// fill two rounds of the column pass at five blocks per SM).
+// frames (a 38 MB intermediate that stays in L2; 76 frames x 16 column slabs
+// fill two rounds of the column pass at four blocks per SM).
 #ifndef OD2P_WAVE_256
-#define OD2P_WAVE_256 95
+#define OD2P_WAVE_256 76
 #endif
 constexpr int WAVE_256 = OD2P_WAVE_256;
 

@@ -70,6 +70,7 @@ def _load():
             "orc_adjoint": (None, [i32, i32, i32, P, i32, P, P, P]),
             "orc_loss_grad": (f64, [i32, i32, P, i32, P, i32, P, P, f64, P, P]),
             "orc_probe_init": (None, [i32, i32, P, P]),
+            "orc_snr": (f64, [i64, P, P]),
             "orc_geometry": (i32, [i32, i32, i32, i32, P, i32, i32, i32, P, P]),
             "orc_pairs": (i32, [i32, P, i32, P, P]),
             "orc_admm_new": (P, [i32, i32, i32, i32, P, i32, i32, i32, P, P, P, f64, f64, f64,
@@ -183,6 +184,13 @@ def probe_init(f) -> np.ndarray:
     w0 = np.empty((m, m), np.complex128)
     _load().orc_probe_init(m, J, _p(f), _p(w0))
     return w0
+
+
+def snr(ur, ug) -> float:
+    """Section 4's SNR (dB) of ug against ur after global-phase alignment."""
+    ur = _c(ur, np.complex128).reshape(-1)
+    ug = _c(ug, np.complex128).reshape(-1)
+    return float(_load().orc_snr(ur.size, _p(ur), _p(ug)))
 
 
 def geometry(H: int, W: int, m: int, offs, sub_rows: int, sub_cols: int, overlap_px: int):

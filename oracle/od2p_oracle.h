@@ -53,6 +53,9 @@ double orc_loss_grad(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
  * w0 = (1/J) sum_j F^* sqrt(f_j), taken frame by frame.  f: J x m x m.       */
 void orc_probe_init(int m, int J, const double *f, ocplx *w0);
 
+/* Section 4's SNR in dB of u_g against u_r after global-phase alignment. */
+double orc_snr(int64_t n, const ocplx *ur, const ocplx *ug);
+
 /* ---- overlapping domain decomposition, sections 2.1 and 3.1 ---- */
 /* frame_sub[J]: subdomain of each frame; rect[D*4]: (r0, c0, r1, c1) half-open.
  * Returns D (= sub_rows*sub_cols) or a negative value on invalid input.        */

@@ -681,3 +681,16 @@ def test_consensus_residual():
     ov = sum((q[2] - q[0]) * (q[3] - q[1]) for (d, e), q in zip(pr, prc) if d == 0)
     expect = abs(c) * np.sqrt(2 * ov) / np.linalg.norm(uu)
     assert abs(a.consensus() - expect) < 1e-12 * expect
+
+
+def test_snr_definition():
+    """Section 4's SNR: a 10% real scaling of the reference is 20 dB, a global
+    phase does not count, and a perturbation of known energy gives its ratio."""
+    rng = np.random.default_rng(5)
+    ur = crandn(40, 40)
+    assert abs(oracle.snr(ur, 1.1 * ur) - 20.0) < 1e-9
+    assert abs(oracle.snr(ur, 0.9 * ur * np.exp(1.3j)) - 20.0) < 1e-9
+    d = crandn(40, 40)
+    d -= np.vdot(ur, d) / np.vdot(ur, ur) * ur   # orthogonal to ur: no phase to remove
+    d *= 0.01 * np.linalg.norm(ur) / np.linalg.norm(d)
+    assert abs(oracle.snr(ur, ur + d) - 40.0) < 1e-6

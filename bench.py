@@ -361,6 +361,7 @@ def run_gpu(args):
         total_s = float(t.item())
     value = J * K * ws / total_s
     rf, re = od.od2p_metrics(plan)
+    snr_db = od.od2p_snr(plan, torch.from_numpy(np.asarray(u_true, np.complex64)).to(dev))
     plan.close()
 
     # ---- end to end through the public API with host buffers (per reconstruction)
@@ -389,7 +390,7 @@ def run_gpu(args):
                    "subdomain_update_ms": round(statistics.mean(k2_ms), 5),
                    "kernel_timing": f"{len(k1_ms)} more iterations launched kernel by kernel (events around "
                                     "each launch, L2 flushed before each iteration), after the timed steps",
-                   "rf_after": rf, "re_after": re,
+                   "rf_after": rf, "re_after": re, "snr_db_after": round(snr_db, 3),
                    "launch": {"variant": launch[0], "blocks_per_sm": launch[1], "max_blocks_per_sm": launch[2],
                               "tuned": None if tuned is None else
                               {"cached": tuned["cached"], "trials_us": tuned.get("trials")}}},
@@ -538,6 +539,7 @@ def run_configs(args):
             line["gradient"] = "ST-AGM loss + grad_u + grad_w, exit waves recomputed (none stored)"
         rf, re = od.od2p_metrics(plan)
         line["rf_after"], line["re_after"] = rf, re
+        line["snr_db_after"] = round(od.od2p_snr(plan, torch.from_numpy(np.asarray(u_true, np.complex64)).to(dev)), 3)
         plan.close()
         del f
         torch.cuda.empty_cache()

@@ -256,6 +256,15 @@ int od2p_set_penalties(ptycho_plan_t *plan, float eta, float r, ptycho_stream_t 
 int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t stream);
 
 /*
+ * Section 4's signal-to-noise ratio of the current recovery against a reference
+ * image: SNR = -10 log10(||t - e^{i theta} m||^2 / ||t||^2) dB, where m is the
+ * merged image (as od2p_merge) and theta = arg sum conj(m) t removes the global
+ * phase.  truth_dev: img_h x img_w.  Two fixed-order reduction passes; writes a
+ * host float and synchronises `stream`.  Errors: INVALID_ARG, CUDA.
+ */
+int od2p_snr(ptycho_plan_t *plan, const ptycho_c32 *truth_dev, float *snr_host, ptycho_stream_t stream);
+
+/*
  * Data-driven initial probe of the blind experiments (section 4.3):
  * w0 = (1/J) sum_j F^* sqrt(f_j), from the intensities the plan holds.  The GPU
  * forms F^* of the mean amplitude (equal by linearity): the amplitudes are

@@ -24,7 +24,7 @@ __all__ = [
     "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
     "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
-    "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual",
+    "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr",
 ]
 
 LAUNCH_VARIANTS = _lib.LAUNCH_VARIANTS
@@ -219,6 +219,17 @@ def od2p_consensus_residual(plan: Plan, stream=None) -> float:
     """||u_d - u_e|| over the pairs' overlaps relative to ||u||."""
     v = ctypes.c_float()
     check(plan._lib.od2p_consensus_residual(plan.handle, ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
+def od2p_snr(plan: Plan, truth: torch.Tensor, stream=None) -> float:
+    """Section 4's SNR (dB) of the merged recovery against `truth` (img_h x img_w)."""
+    g = plan.geom
+    if tuple(truth.shape) != (g.img_h, g.img_w):
+        raise ValueError("truth must be (img_h, img_w)")
+    v = ctypes.c_float()
+    check(plan._lib.od2p_snr(plan.handle, _ptr(truth.contiguous(), torch.complex64, "truth"), ctypes.byref(v),
+                             _stream(stream)))
     return v.value
 
 

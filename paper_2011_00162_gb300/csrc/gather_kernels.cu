@@ -636,6 +636,73 @@ __global__ void merge_kernel(int H, int W, int D, const int32_t *rect, const int
     }
 }
 
+// ---------------------------------------------------------------- SNR (section 4)
+constexpr int SNR_BLOCKS = 152 * 4;
+
+// The merged image at pixel (R, C): the average of the subdomain copies that
+// hold it, 1 where none does (as od2p_merge).
+__device__ __forceinline__ float2 merged_pixel(int R, int C, int D, const int32_t *rect, const int64_t *u_off,
+                                               const float2 *u)
+{
+    float2 t = make_float2(0.f, 0.f);
+    int cnt = 0;
+    for (int d = 0; d < D; ++d) {
+        const int32_t *rc = rect + 4 * d;
+        if (R < rc[0] || R >= rc[2] || C < rc[1] || C >= rc[3]) continue;
+        t = cadd(t, u[u_off[d] + (int64_t)(R - rc[0]) * (rc[3] - rc[1]) + (C - rc[1])]);
+        ++cnt;
+    }
+    return cnt ? make_float2(t.x / cnt, t.y / cnt) : make_float2(1.f, 0.f);
+}
+
+// pass 0: part = sum conj(m) t per block; pass 1: part = (sum |t - e^{i theta} m|^2,
+// sum |t|^2) per block, theta from ph = (cos, sin).  Pixels grid-strided, fixed order.
+__global__ void __launch_bounds__(256) snr_pass_kernel(int pass, int H, int W, int D, const int32_t *rect,
+                                                       const int64_t *u_off, const float2 *u, const float2 *truth,
+                                                       const double *ph, float *part)
+{
+    __shared__ float red[2 * (256 / 32)];
+    const size_t n = (size_t)H * W;
+    const float2 e = pass ? make_float2((float)ph[0], (float)ph[1]) : make_float2(1.f, 0.f);
+    float a = 0.f, b = 0.f;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const float2 m = merged_pixel((int)(k / W), (int)(k % W), D, rect, u_off, u);
+        const float2 t = truth[k];
+        if (pass == 0) {
+            const float2 c = cconjmul(m, t);
+            a += c.x;
+            b += c.y;
+        } else {
+            const float2 em = make_float2(e.x * m.x - e.y * m.y, e.x * m.y + e.y * m.x);
+            a += cabs2(csub(t, em));
+            b += cabs2(t);
+        }
+    }
+    block_sum2_fixed(a, b, red);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// pass 0: out[0..1] = e^{i theta}, theta = arg sum conj(m) t; pass 1: out[2] = SNR (dB).
+__global__ void snr_final_kernel(int pass, const float *part, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < SNR_BLOCKS; ++i) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    if (pass == 0) {
+        const double r = sqrt(a * a + b * b);
+        out[0] = r > 0.0 ? a / r : 1.0;
+        out[1] = r > 0.0 ? b / r : 0.0;
+    } else {
+        out[2] = -10.0 * log10(a / b);
+    }
+}
+
 __global__ void prox_kernel(const float2 *y, const float *f, float2 *z, int64_t n, float lam,
                             float inv1plam, float c_thr, float c_k1)
 {
@@ -930,6 +997,18 @@ int launch_merge(const ptycho_plan_s *p, float2 *out, cudaStream_t s)
 {
     merge_kernel<<<152 * 8, 256, 0, s>>>(p->H, p->W, p->D, p->d_rect, p->d_u_off, p->d_u[p->cur], out);
     OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_snr(ptycho_plan_s *p, const float2 *truth, float *part, double *out, cudaStream_t s)
+{
+    for (int pass = 0; pass < 2; ++pass) {
+        snr_pass_kernel<<<SNR_BLOCKS, 256, 0, s>>>(pass, p->H, p->W, p->D, p->d_rect, p->d_u_off, p->d_u[p->cur],
+                                                   truth, out, part);
+        OD2P_CUDA(cudaGetLastError());
+        snr_final_kernel<<<1, 32, 0, s>>>(pass, part, out);
+        OD2P_CUDA(cudaGetLastError());
+    }
     return PTYCHO_OK;
 }
 

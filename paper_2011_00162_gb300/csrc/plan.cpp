@@ -508,7 +508,8 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own, s)) ||
         (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own, s)) ||
         (rc = dev_alloc(&p->d_metrics, 4, own, s)) || (rc = dev_alloc(&p->d_err, 1, own, s)) ||
-        (rc = dev_alloc(&p->d_rc_part, (size_t)(p->P + 1) * 64, own, s)))
+        (rc = dev_alloc(&p->d_rc_part, (size_t)(p->P + 1) * 64, own, s)) ||
+        (rc = dev_alloc(&p->d_snr_part, 2 * 152 * 4, own, s)) || (rc = dev_alloc(&p->d_snr, 3, own, s)))
         return bail(rc);
     if (p->blind) {
         if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own, s)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own, s)))
@@ -730,6 +731,19 @@ int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t
     OD2P_CUDA(cudaMemcpyAsync(&h, plan->d_metrics + 3, sizeof(h), cudaMemcpyDeviceToHost, s));
     OD2P_CUDA(cudaStreamSynchronize(s));
     *rc_host = (float)h;
+    return PTYCHO_OK;
+}
+
+int od2p_snr(ptycho_plan_t *plan, const ptycho_c32 *truth_dev, float *snr_host, ptycho_stream_t stream)
+{
+    if (!plan || !truth_dev || !snr_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = launch_snr(plan, reinterpret_cast<const float2 *>(truth_dev), plan->d_snr_part, plan->d_snr, s))
+        return rc;
+    double h = 0.0;
+    OD2P_CUDA(cudaMemcpyAsync(&h, plan->d_snr + 2, sizeof(h), cudaMemcpyDeviceToHost, s));
+    OD2P_CUDA(cudaStreamSynchronize(s));
+    *snr_host = (float)h;
     return PTYCHO_OK;
 }
 

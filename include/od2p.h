@@ -256,13 +256,16 @@ int od2p_set_penalties(ptycho_plan_t *plan, float eta, float r, ptycho_stream_t 
 int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t stream);
 
 /*
- * Section 4's signal-to-noise ratio of the current recovery against a reference
- * image: SNR = -10 log10(||t - e^{i theta} m||^2 / ||t||^2) dB, where m is the
- * merged image (as od2p_merge) and theta = arg sum conj(m) t removes the global
- * phase.  truth_dev: img_h x img_w.  Two fixed-order reduction passes; writes a
- * host float and synchronises `stream`.  Errors: INVALID_ARG, CUDA.
+ * Section 4's signal-to-noise ratio of the current recovery against the ground
+ * truth: SNR(u_r, u_g) = -10 log10(||e^{i theta} u_r - u_g||^2 / ||u_r||^2) dB,
+ * with u_r the merged image (as od2p_merge), u_g = truth_dev (img_h x img_w) and
+ * theta = arg sum conj(u_r) u_g removing the recovery's global phase.
+ * mask_dev: NULL (every pixel) or img_h x img_w bytes, nonzero where the pixel
+ * counts (e.g. the illuminated pixels).  Two fixed-order reduction passes;
+ * writes a host float and synchronises `stream`.  Errors: INVALID_ARG, CUDA.
  */
-int od2p_snr(ptycho_plan_t *plan, const ptycho_c32 *truth_dev, float *snr_host, ptycho_stream_t stream);
+int od2p_snr(ptycho_plan_t *plan, const ptycho_c32 *truth_dev, const uint8_t *mask_dev, float *snr_host,
+             ptycho_stream_t stream);
 
 /*
  * Data-driven initial probe of the blind experiments (section 4.3):

@@ -187,7 +187,8 @@ def probe_init(f) -> np.ndarray:
 
 
 def snr(ur, ug) -> float:
-    """Section 4's SNR (dB) of ug against ur after global-phase alignment."""
+    """Section 4's SNR (dB) of the recovery ur against the ground truth ug
+    (denominator ||ur||^2, as printed) after removing ur's global phase."""
     ur = _c(ur, np.complex128).reshape(-1)
     ug = _c(ug, np.complex128).reshape(-1)
     return float(_load().orc_snr(ur.size, _p(ur), _p(ug)))

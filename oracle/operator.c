@@ -120,17 +120,18 @@ void orc_probe_init(int m, int J, const double *f, ocplx *w0)
     free(a);
 }
 
-/* Section 4's signal-to-noise ratio of a recovery u_g against the reference
- * u_r, in dB: -10 log10(||u_r - u_g||^2 / ||u_r||^2), after removing the
- * global phase of u_g (u_g <- u_g e^{i theta}, theta = arg sum conj(u_g) u_r). */
+/* Section 4's signal-to-noise ratio SNR(u_r, u_g) = -10 log10(||u_r - u_g||^2 /
+ * ||u_r||^2) dB, u_r the recovery and u_g the ground truth (the paper's naming,
+ * denominator included), after removing the recovery's global phase:
+ * u_r <- e^{i theta} u_r, theta = arg sum conj(u_r) u_g. */
 double orc_snr(int64_t n, const ocplx *ur, const ocplx *ug)
 {
     ocplx c = 0.0;
-    for (int64_t k = 0; k < n; ++k) c += conj(ug[k]) * ur[k];
+    for (int64_t k = 0; k < n; ++k) c += conj(ur[k]) * ug[k];
     const ocplx ph = cabs(c) > 0.0 ? c / cabs(c) : 1.0;
     double num = 0.0, den = 0.0;
     for (int64_t k = 0; k < n; ++k) {
-        const ocplx d = ur[k] - ph * ug[k];
+        const ocplx d = ph * ur[k] - ug[k];
         num += creal(d) * creal(d) + cimag(d) * cimag(d);
         den += creal(ur[k]) * creal(ur[k]) + cimag(ur[k]) * cimag(ur[k]);
     }

@@ -222,14 +222,21 @@ def od2p_consensus_residual(plan: Plan, stream=None) -> float:
     return v.value
 
 
-def od2p_snr(plan: Plan, truth: torch.Tensor, stream=None) -> float:
-    """Section 4's SNR (dB) of the merged recovery against `truth` (img_h x img_w)."""
+def od2p_snr(plan: Plan, truth: torch.Tensor, mask: torch.Tensor | None = None, stream=None) -> float:
+    """Section 4's SNR (dB) of the merged recovery against the ground truth
+    (img_h x img_w), over the pixels where `mask` (bool/uint8, same shape) is set."""
     g = plan.geom
     if tuple(truth.shape) != (g.img_h, g.img_w):
         raise ValueError("truth must be (img_h, img_w)")
+    mp = None
+    if mask is not None:
+        if tuple(mask.shape) != (g.img_h, g.img_w):
+            raise ValueError("mask must be (img_h, img_w)")
+        mask = mask.to(torch.uint8).contiguous()
+        mp = _ptr(mask, torch.uint8, "mask")
     v = ctypes.c_float()
-    check(plan._lib.od2p_snr(plan.handle, _ptr(truth.contiguous(), torch.complex64, "truth"), ctypes.byref(v),
-                             _stream(stream)))
+    check(plan._lib.od2p_snr(plan.handle, _ptr(truth.contiguous(), torch.complex64, "truth"), mp,
+                             ctypes.byref(v), _stream(stream)))
     return v.value
 
 

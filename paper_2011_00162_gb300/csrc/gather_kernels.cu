@@ -655,17 +655,20 @@ __device__ __forceinline__ float2 merged_pixel(int R, int C, int D, const int32_
     return cnt ? make_float2(t.x / cnt, t.y / cnt) : make_float2(1.f, 0.f);
 }
 
-// pass 0: part = sum conj(m) t per block; pass 1: part = (sum |t - e^{i theta} m|^2,
-// sum |t|^2) per block, theta from ph = (cos, sin).  Pixels grid-strided, fixed order.
+// Section 4's SNR of the recovery m (the merged image) against the truth t.
+// pass 0: part = sum conj(m) t per block; pass 1: part = (sum |e^{i theta} m - t|^2,
+// sum |m|^2) per block, e^{i theta} = ph.  Pixels where mask is 0 are left out
+// (mask may be NULL).  Pixels grid-strided, fixed order.
 __global__ void __launch_bounds__(256) snr_pass_kernel(int pass, int H, int W, int D, const int32_t *rect,
                                                        const int64_t *u_off, const float2 *u, const float2 *truth,
-                                                       const double *ph, float *part)
+                                                       const uint8_t *mask, const double *ph, float *part)
 {
     __shared__ float red[2 * (256 / 32)];
     const size_t n = (size_t)H * W;
     const float2 e = pass ? make_float2((float)ph[0], (float)ph[1]) : make_float2(1.f, 0.f);
     float a = 0.f, b = 0.f;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        if (mask && !mask[k]) continue;
         const float2 m = merged_pixel((int)(k / W), (int)(k % W), D, rect, u_off, u);
         const float2 t = truth[k];
         if (pass == 0) {
@@ -674,8 +677,8 @@ __global__ void __launch_bounds__(256) snr_pass_kernel(int pass, int H, int W, i
             b += c.y;
         } else {
             const float2 em = make_float2(e.x * m.x - e.y * m.y, e.x * m.y + e.y * m.x);
-            a += cabs2(csub(t, em));
-            b += cabs2(t);
+            a += cabs2(csub(em, t));
+            b += cabs2(m);
         }
     }
     block_sum2_fixed(a, b, red);
@@ -1000,11 +1003,12 @@ int launch_merge(const ptycho_plan_s *p, float2 *out, cudaStream_t s)
     return PTYCHO_OK;
 }
 
-int launch_snr(ptycho_plan_s *p, const float2 *truth, float *part, double *out, cudaStream_t s)
+int launch_snr(ptycho_plan_s *p, const float2 *truth, const uint8_t *mask, float *part, double *out,
+               cudaStream_t s)
 {
     for (int pass = 0; pass < 2; ++pass) {
         snr_pass_kernel<<<SNR_BLOCKS, 256, 0, s>>>(pass, p->H, p->W, p->D, p->d_rect, p->d_u_off, p->d_u[p->cur],
-                                                   truth, out, part);
+                                                   truth, mask, out, part);
         OD2P_CUDA(cudaGetLastError());
         snr_final_kernel<<<1, 32, 0, s>>>(pass, part, out);
         OD2P_CUDA(cudaGetLastError());

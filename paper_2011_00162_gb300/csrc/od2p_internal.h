@@ -270,7 +270,8 @@ int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s);
 int launch_metrics(ptycho_plan_s *p, cudaStream_t s);
 int launch_scale(float2 *x, int64_t n, float sc, cudaStream_t s);
 int launch_consensus(ptycho_plan_s *p, float *part, double *out, cudaStream_t s);
-int launch_snr(ptycho_plan_s *p, const float2 *truth, float *part, double *out, cudaStream_t s);
+int launch_snr(ptycho_plan_s *p, const float2 *truth, const uint8_t *mask, float *part, double *out,
+               cudaStream_t s);
 int launch_probe_init(ptycho_plan_s *p, float2 *w0, cudaStream_t s);
 int launch_slot_rank(ptycho_plan_s *p, int32_t *setup, cudaStream_t s);
 // Split m = R1 * R2 of the frame update's FFT, which fixes the task order of

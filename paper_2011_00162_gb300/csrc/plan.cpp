@@ -734,11 +734,13 @@ int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t
     return PTYCHO_OK;
 }
 
-int od2p_snr(ptycho_plan_t *plan, const ptycho_c32 *truth_dev, float *snr_host, ptycho_stream_t stream)
+int od2p_snr(ptycho_plan_t *plan, const ptycho_c32 *truth_dev, const uint8_t *mask_dev, float *snr_host,
+             ptycho_stream_t stream)
 {
     if (!plan || !truth_dev || !snr_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (int rc = launch_snr(plan, reinterpret_cast<const float2 *>(truth_dev), plan->d_snr_part, plan->d_snr, s))
+    if (int rc = launch_snr(plan, reinterpret_cast<const float2 *>(truth_dev), mask_dev, plan->d_snr_part,
+                            plan->d_snr, s))
         return rc;
     double h = 0.0;
     OD2P_CUDA(cudaMemcpyAsync(&h, plan->d_snr + 2, sizeof(h), cudaMemcpyDeviceToHost, s));

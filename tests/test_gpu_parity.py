@@ -535,20 +535,24 @@ def test_reconstructions_converge():
 
 def test_snr_matches_oracle():
     """od2p_snr equals section 4's SNR computed in FP64 from the GPU's own merged
-    image, for a partly converged run and for the exact (scaled, phase-rotated)
-    truth, which has a closed form."""
+    image (all pixels, and the illuminated ones), and the closed form for a
+    recovery that is the truth scaled by 1.1 and phase-rotated."""
     p = synth.small_2sub()
     offs, u_true, w, f = make_case(p)
     plan = od.ptycho_plan(geom_of(p, offs), f32(f))
     od.od2p_init(plan, c64(w))
     od.od2p_iterate(plan, 20)
+    ug = host(od.od2p_merge(plan))
+    lit = synth.lit_mask(p.n, p.n, p.m, offs)
     got = od.od2p_snr(plan, c64(u_true))
-    want = oracle.snr(u_true, host(od.od2p_merge(plan)))
-    record("snr_20its", gpu=got, oracle=want)
+    got_lit = od.od2p_snr(plan, c64(u_true), torch.from_numpy(lit).to(DEV))
+    want, want_lit = oracle.snr(ug, u_true), oracle.snr(ug[lit], u_true[lit])
+    record("snr_20its", gpu=got, oracle=want, gpu_lit=got_lit, oracle_lit=want_lit)
     assert abs(got - want) < 1e-3 * max(1.0, abs(want)), (got, want)
-    # u = 1.1 e^{0.7i} truth everywhere: SNR = -20 log10(0.1) = 20 dB
+    assert abs(got_lit - want_lit) < 1e-3 * max(1.0, abs(want_lit)), (got_lit, want_lit)
+    # u_r = 1.1 e^{0.7i} u_g everywhere: SNR = 20 + 10 log10(1.21) dB
     t = (1.1 * np.exp(0.7j) * u_true).astype(np.complex64)
     _, rect, _, _ = plan.layout()  # copies stored subdomain after subdomain, row-major
     u = np.concatenate([t[r0:r1, c0:c1].reshape(-1) for r0, c0, r1, c1 in rect])
     od.od2p_set_state(plan, od.STATE_U, c64(u))
-    assert abs(od.od2p_snr(plan, c64(u_true)) - 20.0) < 1e-3
+    assert abs(od.od2p_snr(plan, c64(u_true)) - (20.0 + 10 * np.log10(1.21))) < 1e-3

@@ -684,13 +684,14 @@ def test_consensus_residual():
 
 
 def test_snr_definition():
-    """Section 4's SNR: a 10% real scaling of the reference is 20 dB, a global
-    phase does not count, and a perturbation of known energy gives its ratio."""
-    rng = np.random.default_rng(5)
-    ur = crandn(40, 40)
-    assert abs(oracle.snr(ur, 1.1 * ur) - 20.0) < 1e-9
-    assert abs(oracle.snr(ur, 0.9 * ur * np.exp(1.3j)) - 20.0) < 1e-9
+    """Section 4's SNR of a recovery u_r against the truth u_g, normalised by
+    ||u_r||^2 as printed: a 10% scaling of the truth gives 20 dB plus the norm
+    ratio, a global phase of the recovery does not count, and a perturbation of
+    known energy gives its ratio."""
+    ug = crandn(40, 40)
+    assert abs(oracle.snr(1.1 * ug, ug) - (20.0 + 10 * np.log10(1.21))) < 1e-9
+    assert abs(oracle.snr(0.9 * ug * np.exp(1.3j), ug) - (20.0 + 10 * np.log10(0.81))) < 1e-9
     d = crandn(40, 40)
-    d -= np.vdot(ur, d) / np.vdot(ur, ur) * ur   # orthogonal to ur: no phase to remove
-    d *= 0.01 * np.linalg.norm(ur) / np.linalg.norm(d)
-    assert abs(oracle.snr(ur, ur + d) - 40.0) < 1e-6
+    d -= np.vdot(ug, d) / np.vdot(ug, ug) * ug   # orthogonal to ug: no phase to remove
+    d *= 0.01 * np.linalg.norm(ug) / np.linalg.norm(d)
+    assert abs(oracle.snr(ug + d, ug) - (40.0 + 10 * np.log10(1.0001))) < 1e-6

@@ -549,6 +549,91 @@ def run_configs(args):
         print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- time to solution
+def _run_to_rf(od, plan, tol: float, max_it: int, check: int, balance: bool):
+    """Iterate plan until RF <= tol (checked every `check` iterations) or max_it;
+    with balance, rebalance r at each check (adaptive.decide).  Returns
+    (iterations, RF, RE, seconds of wall clock, r at the end)."""
+    import torch
+
+    from paper_2011_00162_gb300 import adaptive
+    eta, r = float(plan.geom.eta), float(plan.geom.r)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done, rf, re = 0, float("inf"), float("inf")
+    while done < max_it:
+        k = min(check, max_it - done)
+        od.od2p_iterate(plan, k)
+        done += k
+        rf, re = od.od2p_metrics(plan)  # synchronises
+        if rf <= tol:
+            break
+        if balance and plan.n_pairs:
+            r_new = adaptive.decide(r, od.od2p_consensus_residual(plan), r * re)
+            if r_new != r:
+                od.od2p_set_penalties(plan, eta, r_new)
+                r = r_new
+    torch.cuda.synchronize()
+    return done, rf, re, time.perf_counter() - t0, r
+
+
+def run_table1(args):
+    """Table 1's (section 4.2) workload run to its stopping rule on one GPU: a
+    512^2 noiseless image, a 64^2 probe, raster step 16 (841 frames), D = 1 ... 10
+    stripe subdomains, eps = 0.5, until RF <= 1e-5 (at most 1000 iterations).
+    For every D: iterations, RF, RE, SNR and the GPU wall clock from the initial
+    state, with fixed (eta, r) and with residual balancing of r; for D = 1 the
+    FP64 oracle's iteration count on the same data beside it."""
+    import dataclasses
+
+    import torch
+
+    import paper_2011_00162_gb300 as od
+    from paper_2011_00162_gb300 import synth
+    from paper_2011_00162_gb300 import build as odbuild
+    odbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    eta, r = args.eta, args.r
+    base = synth.Problem("table1", 512, 64, 16, 0, 1, 1, 48, None, 1000, eta=eta, r=r)
+    offs, u_true, w, f = _gpu_problem_inputs(od, base, dev)
+    truth = torch.from_numpy(np.asarray(u_true, np.complex64)).to(dev)
+    w_dev = torch.from_numpy(w).to(dev)
+    for D in (1, 2, 4, 6, 8, 10):
+        p = dataclasses.replace(base, sub_cols=D)
+        line = {"workload": f"table1_od2p_512px_m64_841frames_1x{D}stripes_noiseless", "frames": len(offs),
+                "subdomains": D, "eta": eta, "r": r, "stop": "RF <= 1e-5 or 1000 iterations",
+                "check_every": args.check}
+        for balance in (False, True):
+            t_plan = time.perf_counter()
+            plan = od.ptycho_plan(od.Geometry(p.n, p.n, p.m, offs, 1, D, p.overlap_px, p.eps, eta, r), f)
+            od.od2p_init(plan, w_dev)
+            torch.cuda.synchronize()
+            t_plan = time.perf_counter() - t_plan
+            od.od2p_iterate(plan, 2)  # both graph parities captured outside the clock ...
+            od.od2p_init(plan, w_dev)  # ... then back to the initial state
+            it, rf, re, sec, r_end = _run_to_rf(od, plan, 1e-5, 1000, args.check, balance)
+            rec = {"iterations": it, "rf": rf, "re": re, "snr_db": round(od.od2p_snr(plan, truth), 3),
+                   "gpu_seconds": round(sec, 5), "plan_seconds": round(t_plan, 4)}
+            if balance:
+                rec["r_end"] = r_end
+            line["balanced_r" if balance else "fixed"] = rec
+            plan.close()
+        if D == 1 and not args.no_cpu_baseline:
+            import oracle
+            fh = f.cpu().numpy().astype(np.float64)
+            a = oracle.ADMM(fh, w, offs, p.n, p.n, 1, 1, p.overlap_px, p.eps, eta, r)
+            t0, it = time.perf_counter(), 0
+            while it < 1000:
+                a.iterate(args.check)
+                it += args.check
+                if a.metrics()[0] <= 1e-5:
+                    break
+            line["oracle_fp64"] = {"iterations": it, "rf": a.metrics()[0], "seconds": round(time.perf_counter() - t0, 2),
+                                   "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+        print(json.dumps(line), flush=True)
+
+
 def _oracle_case(p):
     import oracle
     from paper_2011_00162_gb300 import synth
@@ -624,8 +709,15 @@ def main():
     ap.add_argument("--configs", action="store_true",
                     help="measure every workload (one JSON line each) instead of the headline line")
     ap.add_argument("--only", default="", help="with --configs: only workloads whose name contains this")
+    ap.add_argument("--table1", action="store_true",
+                    help="run Table 1's workload (section 4.2) (D = 1 ... 10 stripes) to RF <= 1e-5")
+    ap.add_argument("--eta", type=float, default=0.1, help="with --table1")
+    ap.add_argument("--r", type=float, default=4e3, help="with --table1")
+    ap.add_argument("--check", type=int, default=10, help="with --table1: iterations between RF checks")
     args = ap.parse_args()
-    if args.configs:
+    if args.table1:
+        run_table1(args)
+    elif args.configs:
         run_configs(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -236,7 +236,7 @@ int od2p_metrics(ptycho_plan_t *plan, float *rf_host, float *re_host, ptycho_str
 
 /*
  * Penalty changes between iterations (the paper fixes eta and r for a run and
- * names their adaptive choice future work, section 5).  Gamma and Lambda are
+ * names their automatic choice future work, section 4.3).  Gamma and Lambda are
  * the scaled multipliers of the augmented Lagrangian, so a change keeps the
  * unscaled ones: Gamma <- (eta_old / eta) Gamma, Lambda <- (r_old / r) Lambda
  * (the rescaling of Boyd, Parikh, Chu, Peleato, Eckstein 2011, 3.4.1; Lambda
@@ -268,7 +268,7 @@ int od2p_snr(ptycho_plan_t *plan, const ptycho_c32 *truth_dev, const uint8_t *ma
              ptycho_stream_t stream);
 
 /*
- * Data-driven initial probe of the blind experiments (section 4.3):
+ * Data-driven initial probe of the blind experiments (section 4.2):
  * w0 = (1/J) sum_j F^* sqrt(f_j), from the intensities the plan holds.  The GPU
  * forms F^* of the mean amplitude (equal by linearity): the amplitudes are
  * averaged per frequency in ascending j with compensated FP32 addition, then

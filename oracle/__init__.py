@@ -178,7 +178,7 @@ def loss_grad(u, w, offs, f, eps: float):
 
 
 def probe_init(f) -> np.ndarray:
-    """w0 = (1/J) sum_j F^* sqrt(f_j) (section 4.3's data-driven initial probe)."""
+    """w0 = (1/J) sum_j F^* sqrt(f_j) (section 4.2's data-driven initial probe)."""
     f = _c(f, np.float64)
     J, m = f.shape[0], f.shape[-1]
     w0 = np.empty((m, m), np.complex128)

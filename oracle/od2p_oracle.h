@@ -48,7 +48,7 @@ void orc_adjoint(int H, int W, int m, const ocplx *w, int J, const int32_t *offs
 double orc_loss_grad(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
                      const int32_t *offs, const double *f, double eps, ocplx *gu, ocplx *gw);
 
-/* Data-driven initial probe of the blind experiments (section 4.3): the mean
+/* Data-driven initial probe of the blind experiments (section 4.2): the mean
  * over the J frames of the inverse unitary DFT of the measured amplitudes,
  * w0 = (1/J) sum_j F^* sqrt(f_j), taken frame by frame.  f: J x m x m.       */
 void orc_probe_init(int m, int J, const double *f, ocplx *w0);

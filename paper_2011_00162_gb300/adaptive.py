@@ -1,7 +1,7 @@
 """Residual balancing of the consensus penalty r between ADMM iterations.
 
 The paper runs OD2P with fixed (eta, r) and names their automatic choice
-future work (section 5).  This module supplies the standard residual-balancing
+future work (section 4.3).  This module supplies the standard residual-balancing
 rule for an ADMM penalty (He, Yang and Wang 2000; Boyd, Parikh, Chu, Peleato,
 Eckstein 2011, section 3.4.1) for the consensus penalty r: every `every`
 iterations it compares the primal residual of the consensus constraint -- the

@@ -729,7 +729,7 @@ __global__ void prox_kernel(const float2 *y, const float *f, float2 *z, int64_t 
     }
 }
 
-// ---- data-driven initial probe (section 4.3): w0 = (1/J) sum_j F^* sqrt(f_j),
+// ---- data-driven initial probe (section 4.2): w0 = (1/J) sum_j F^* sqrt(f_j),
 // formed as F^* of the mean amplitude (the inverse DFT is linear).
 
 // Mean measured amplitude per frequency, natural order.  One thread per stored

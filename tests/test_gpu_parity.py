@@ -421,7 +421,7 @@ def test_blind_workload_1024_full_size():
 @pytest.mark.parametrize("m,n,step", [(16, 64, 4), (32, 100, 9), (64, 300, 16), (128, 384, 48), (256, 512, 96),
                                       (48, 144, 12), (80, 240, 20), (96, 288, 24)])
 def test_probe_init_matches_oracle(m, n, step):
-    """Section 4.3's data-driven initial probe from a plan's intensities."""
+    """Section 4.2's data-driven initial probe from a plan's intensities."""
     p = synth.Problem("pi", n, m, step, 1, 2, 2, 8, 1e4, 1, seed=m)
     offs, u_true, w, f = make_case(p)
     plan = od.ptycho_plan(geom_of(p, offs), f32(f))

@@ -581,7 +581,7 @@ def test_loss_reduces_to_agm_and_vanishes_at_truth():
 # ----------------------------------------------------------------------------- data-driven initial probe
 @pytest.mark.parametrize("m", [16, 64])
 def test_probe_init_recovers_a_probe_with_positive_spectrum(m):
-    """Section 4.3's w0 = (1/J) sum_j F^* sqrt(f_j): when every frame measures
+    """Section 4.2's w0 = (1/J) sum_j F^* sqrt(f_j): when every frame measures
     |F w|^2 of a probe whose spectrum F w = a is real and positive, sqrt(f_j) = a
     and the mean of F^* a over the frames is w itself (numpy builds w)."""
     rng = np.random.default_rng(m)

@@ -61,7 +61,7 @@ def _peaks():
 
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for rel in ("paper_2011_00162_gb300/csrc/fft_kernels.cu", "paper_2011_00162_gb300/csrc/od2p_internal.h"):
+    for rel in ("paper_2011_00162_gb300/csrc/fft_kernels.cu", "paper_2011_00162_gb300/csrc/fft_device.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

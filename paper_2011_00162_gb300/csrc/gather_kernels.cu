@@ -22,6 +22,19 @@ __device__ __forceinline__ float2 cconjmul(float2 a, float2 b)
 }
 __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 
+// Fixed-order sum of n values v[i * stride + offset] by one warp: lane l adds
+// the contiguous run [l*per, (l+1)*per) in order, then a fixed shuffle tree.
+// Every lane returns the total.  Deterministic for a given n.
+__device__ __forceinline__ double warp_sum_runs(int n, const float *v, int stride, int offset)
+{
+    const int lane = threadIdx.x & 31, per = (n + 31) / 32;
+    double t = 0.0;
+    for (int i = lane * per; i < min(n, (lane + 1) * per); ++i) t += v[(size_t)i * stride + offset];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
 __device__ __forceinline__ void block_sum2_fixed(float &a, float &b, float *red)
 {
 #pragma unroll
@@ -349,14 +362,13 @@ __global__ void __launch_bounds__(256) consensus_partial_kernel(int P, const int
     if (threadIdx.x == 0) part[(size_t)k * RC_BLOCKS + blockIdx.x] = acc;
 }
 
-// out = sqrt(sum over the pairs' parts / sum of the |u|^2 parts), in order.
+// out = sqrt(sum over the pairs' parts / sum of the |u|^2 parts), fixed order.
+// One warp.
 __global__ void consensus_final_kernel(int P, const float *part, double *out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double num = 0.0, den = 0.0;
-    for (int i = 0; i < P * RC_BLOCKS; ++i) num += part[i];
-    for (int i = 0; i < RC_BLOCKS; ++i) den += part[(size_t)P * RC_BLOCKS + i];
-    *out = den > 0.0 ? sqrt(num / den) : 0.0;
+    const double num = warp_sum_runs(P * RC_BLOCKS, part, 1, 0);
+    const double den = warp_sum_runs(RC_BLOCKS, part + (size_t)P * RC_BLOCKS, 1, 0);
+    if (threadIdx.x == 0) *out = den > 0.0 ? sqrt(num / den) : 0.0;
 }
 
 // ---------------------------------------------------------------- probe reductions
@@ -463,22 +475,28 @@ __device__ double block_sum_runs(int n, const float *v, int stride, int offset, 
 }
 
 // metrics[0] = sum rf_part / sum sqrt f (RF); metrics[1] = max over subdomains of
-// sqrt(sum dn / sum nn) over the subdomain's tiles (RE).  One block.
+// sqrt(sum dn / sum nn) over the subdomain's tiles (RE).  One block: RF by the
+// block, then warp k takes subdomains k, k + 8, ... (fixed-order sums each).
 __global__ void __launch_bounds__(256) metrics_kernel(int n_rf, const float *rf_part, int D,
                                                       const int32_t *reg_tile_ptr, const float *re_part,
                                                       double *metrics)
 {
     __shared__ double red[8];
+    __shared__ double re_w[8];
     const double rf = block_sum_runs(n_rf, rf_part, 1, 0, red);
+    const int warp = threadIdx.x >> 5;
     double re = 0.0;
-    for (int d = 0; d < D; ++d) {
+    for (int d = warp; d < D; d += 8) {
         const int t0 = reg_tile_ptr[d], nt = reg_tile_ptr[d + 1] - t0;
-        const double dn = block_sum_runs(nt, re_part + 2 * (size_t)t0, 2, 0, red);
-        const double nn = block_sum_runs(nt, re_part + 2 * (size_t)t0, 2, 1, red);
+        const double dn = warp_sum_runs(nt, re_part + 2 * (size_t)t0, 2, 0);
+        const double nn = warp_sum_runs(nt, re_part + 2 * (size_t)t0, 2, 1);
         const double v = nn > 0.0 ? sqrt(dn / nn) : 0.0;
         re = v > re ? v : re;
     }
+    if ((threadIdx.x & 31) == 0) re_w[warp] = re;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        for (int k = 0; k < 8; ++k) re = re_w[k] > re ? re_w[k] : re;
         metrics[0] = metrics[2] > 0.0 ? rf / metrics[2] : 0.0;
         metrics[1] = re;
     }
@@ -689,14 +707,12 @@ __global__ void __launch_bounds__(256) snr_pass_kernel(int pass, int H, int W, i
 }
 
 // pass 0: out[0..1] = e^{i theta}, theta = arg sum conj(m) t; pass 1: out[2] = SNR (dB).
+// One warp, fixed order.
 __global__ void snr_final_kernel(int pass, const float *part, double *out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < SNR_BLOCKS; ++i) {
-        a += part[2 * i];
-        b += part[2 * i + 1];
-    }
+    const double a = warp_sum_runs(SNR_BLOCKS, part, 2, 0);
+    const double b = warp_sum_runs(SNR_BLOCKS, part, 2, 1);
+    if (threadIdx.x != 0) return;
     if (pass == 0) {
         const double r = sqrt(a * a + b * b);
         out[0] = r > 0.0 ? a / r : 1.0;

@@ -252,7 +252,6 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
 
 __global__ void __launch_bounds__(NTB) rows_inv256_kernel(PassC a, const float2 *twg)
 {
-    pdl_trigger();  // see the frame update kernel
     extern __shared__ float4 smem4[];
     float2 *tw = reinterpret_cast<float2 *>(smem4);
     float2 *buf = tw + BM;

@@ -390,7 +390,6 @@ __global__ void __launch_bounds__(K1Cfg<M, V>::NT, K1Cfg<M, V>::MINB)
     float2 *buf = tw + M;
     float *red = reinterpret_cast<float *>(buf + FPB * M * P);
 
-    pdl_trigger();  // the subdomain update may start its prologue (it waits for this grid)
     auto item = [&](int i) { return BATCHED ? items[i] : make_int2(0, i); };
     auto issue = [&](int i) {  // one thread: stage item i's Gamma / sqrt f
         const int2 it = item(i);

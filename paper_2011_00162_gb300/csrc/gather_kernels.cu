@@ -22,8 +22,6 @@ __device__ __forceinline__ float2 cconjmul(float2 a, float2 b)
 }
 __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 
-__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
 // Fixed-order sum of n values v[i * stride + offset] by one warp: lane l adds
 // the contiguous run [l*per, (l+1)*per) in order, then a fixed shuffle tree.
 // Every lane returns the total.  Deterministic for a given n.
@@ -121,33 +119,6 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? OD2P_K2B_MINB : OD2P_K
         for (int i = threadIdx.x; i < min(ti.nk, LIST_SMEM); i += GATHER_THREADS) lst[i] = a.tlist[ti.k0 + i];
     for (int i = threadIdx.x; i < min(ti.nnb, NBR_SMEM); i += GATHER_THREADS) nbs[i] = a.tnbr[ti.n0 + i];
     __syncthreads();
-    // everything above reads the plan's layout only.  While the preceding
-    // frame update may still run (programmatic dependent launch), bring this
-    // thread's u^n, illumination and neighbour values (u_e^n, Lambda^n: none of
-    // them written by the frame update) into L2; the slots / q it writes are
-    // read after pdl_wait.
-    if (active) {
-#pragma unroll
-        for (int r = 0; r < TILE_ROWS; ++r)
-            if (r < nrows) {
-                prefetch_l2(a.u_cur + ui[r]);
-                if (!BLIND) prefetch_l2(a.nrm + ui[r]);
-            }
-        for (int i = 0; i < min(ti.nnb, NBR_SMEM); ++i) {
-            const NbrInfo nb = nbs[i];
-            if (C < nb.c0 || C >= nb.c1 || R0 + nrows <= nb.r0 || R0 >= nb.r1) continue;
-#pragma unroll
-            for (int r = 0; r < TILE_ROWS; ++r) {
-                const int R = R0 + r;
-                if (r >= nrows || R < nb.r0 || R >= nb.r1) continue;
-                const int li = (R - nb.p_r0) * nb.p_pitch + (C - nb.p_c0);
-                prefetch_l2(a.u_cur + nb.u_base + (R - nb.r0) * nb.u_pitch + (C - nb.c0));
-                prefetch_l2(a.lam_cur + nb.lam_de + li);
-                prefetch_l2(a.lam_cur + nb.lam_ed + li);
-            }
-        }
-    }
-    pdl_wait();
     // A_d^*(z - Gamma) at each pixel, frames in ascending j.  Nonblind: the
     // slots already carry conj(w) and sum_j S_j^T |w|^2 is precomputed.  Blind:
     // weight with W_d^{n+1} here and sum |W_d|^2 on the way.
@@ -886,26 +857,11 @@ int launch_subdomain_update(ptycho_plan_s *p, cudaStream_t s)
 {
     const int n = p->sub_tiles.n_tiles;
     if (n <= 0) return PTYCHO_OK;
-    // launched as a programmatic dependent of the frame update (or whatever
-    // kernel precedes it): its prologue overlaps that kernel's tail
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)n);
-    cfg.blockDim = dim3(GATHER_THREADS);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const SubArgs *no_tab = nullptr;
-    const int2 *no_items = nullptr;
     if (p->blind || !p->slots)
-        OD2P_CUDA(cudaLaunchKernelEx(&cfg, subdomain_update_kernel<true, false>, p->h_sargs[p->cur], no_tab, no_items,
-                                     p->cur));
+        subdomain_update_kernel<true, false><<<n, GATHER_THREADS, 0, s>>>(p->h_sargs[p->cur], nullptr, nullptr, p->cur);
     else
-        OD2P_CUDA(cudaLaunchKernelEx(&cfg, subdomain_update_kernel<false, false>, p->h_sargs[p->cur], no_tab, no_items,
-                                     p->cur));
+        subdomain_update_kernel<false, false><<<n, GATHER_THREADS, 0, s>>>(p->h_sargs[p->cur], nullptr, nullptr, p->cur);
+    OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
 

@@ -9,16 +9,6 @@
 
 #include "../../include/od2p.h"
 
-#ifdef __CUDACC__
-// Programmatic dependent launch (sm_90+): once every block of the running
-// kernel has called pdl_trigger (or exited), the next kernel in the stream,
-// launched with the programmatic-serialisation attribute, may start; it runs
-// its prologue and blocks in pdl_wait until the first grid has completed and
-// its writes are visible.  Without that attribute pdl_wait returns at once.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-#endif
-
 namespace od2p {
 
 // Thread block tile of the gather kernels: TILE_H rows x TILE_W columns.

@@ -456,12 +456,13 @@ __global__ void probe_finalize_sum_kernel(int M, int n_chunks, const float2 *par
 }
 
 // ---------------------------------------------------------------- scalars
-// Fixed-order sum of n values with one 256-thread block: thread t adds the
+// Fixed-order sum of n values with one NT-thread block: thread t adds the
 // contiguous run [t*per, (t+1)*per) in order, then a fixed shuffle tree and
-// the eight warp sums in order.  Deterministic for a given n.
+// the NT/32 warp sums in order.  Deterministic for a given n and NT.
+template <int NT>
 __device__ double block_sum_runs(int n, const float *v, int stride, int offset, double *red)
 {
-    const int per = (n + 255) / 256;
+    const int per = (n + NT - 1) / NT;
     double t = 0.0;
     for (int i = threadIdx.x * per; i < min(n, (threadIdx.x + 1) * per); ++i) t += v[(size_t)i * stride + offset];
 #pragma unroll
@@ -470,23 +471,24 @@ __device__ double block_sum_runs(int n, const float *v, int stride, int offset, 
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
     double s = 0.0;
-    for (int i = 0; i < 8; ++i) s += red[i];
+    for (int i = 0; i < NT / 32; ++i) s += red[i];
     return s;
 }
 
 // metrics[0] = sum rf_part / sum sqrt f (RF); metrics[1] = max over subdomains of
-// sqrt(sum dn / sum nn) over the subdomain's tiles (RE).  One block: RF by the
-// block, then warp k takes subdomains k, k + 8, ... (fixed-order sums each).
-__global__ void __launch_bounds__(256) metrics_kernel(int n_rf, const float *rf_part, int D,
-                                                      const int32_t *reg_tile_ptr, const float *re_part,
-                                                      double *metrics)
+// sqrt(sum dn / sum nn) over the subdomain's tiles (RE).  One block of 1024
+// threads: RF by the block, then warp k takes subdomains k, k + 32, ...
+// (fixed-order sums each).
+__global__ void __launch_bounds__(1024) metrics_kernel(int n_rf, const float *rf_part, int D,
+                                                       const int32_t *reg_tile_ptr, const float *re_part,
+                                                       double *metrics)
 {
-    __shared__ double red[8];
-    __shared__ double re_w[8];
-    const double rf = block_sum_runs(n_rf, rf_part, 1, 0, red);
+    __shared__ double red[32];
+    __shared__ double re_w[32];
+    const double rf = block_sum_runs<1024>(n_rf, rf_part, 1, 0, red);
     const int warp = threadIdx.x >> 5;
     double re = 0.0;
-    for (int d = warp; d < D; d += 8) {
+    for (int d = warp; d < D; d += 32) {
         const int t0 = reg_tile_ptr[d], nt = reg_tile_ptr[d + 1] - t0;
         const double dn = warp_sum_runs(nt, re_part + 2 * (size_t)t0, 2, 0);
         const double nn = warp_sum_runs(nt, re_part + 2 * (size_t)t0, 2, 1);
@@ -496,7 +498,7 @@ __global__ void __launch_bounds__(256) metrics_kernel(int n_rf, const float *rf_
     if ((threadIdx.x & 31) == 0) re_w[warp] = re;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 8; ++k) re = re_w[k] > re ? re_w[k] : re;
+        for (int k = 0; k < 32; ++k) re = re_w[k] > re ? re_w[k] : re;
         metrics[0] = metrics[2] > 0.0 ? rf / metrics[2] : 0.0;
         metrics[1] = re;
     }
@@ -505,14 +507,14 @@ __global__ void __launch_bounds__(256) metrics_kernel(int n_rf, const float *rf_
 __global__ void __launch_bounds__(256) sum_kernel(int n, const float *part, double *dst)
 {
     __shared__ double red[8];
-    const double t = block_sum_runs(n, part, 1, 0, red);
+    const double t = block_sum_runs<256>(n, part, 1, 0, red);
     if (threadIdx.x == 0) *dst = t;
 }
 
 __global__ void __launch_bounds__(256) loss_sum_kernel(int n, const float *part, float *loss)
 {
     __shared__ double red[8];
-    const double t = block_sum_runs(n, part, 1, 0, red);
+    const double t = block_sum_runs<256>(n, part, 1, 0, red);
     if (threadIdx.x == 0) *loss = (float)t;
 }
 
@@ -955,7 +957,7 @@ int launch_consensus(ptycho_plan_s *p, float *part, double *out, cudaStream_t s)
 
 int launch_metrics(ptycho_plan_s *p, cudaStream_t s)
 {
-    metrics_kernel<<<1, 256, 0, s>>>(p->n_rf_parts, p->d_rf_part, p->D, p->sub_tiles.reg_ptr,
+    metrics_kernel<<<1, 1024, 0, s>>>(p->n_rf_parts, p->d_rf_part, p->D, p->sub_tiles.reg_ptr,
                                     p->d_re_part, p->d_metrics);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;

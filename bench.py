@@ -582,8 +582,8 @@ def run_table1(args):
     512^2 noiseless image, a 64^2 probe, raster step 16 (841 frames), D = 1 ... 10
     stripe subdomains, eps = 0.5, until RF <= 1e-5 (at most 1000 iterations).
     For every D: iterations, RF, RE, SNR and the GPU wall clock from the initial
-    state, with fixed (eta, r) and with residual balancing of r; for D = 1 the
-    FP64 oracle's iteration count on the same data beside it."""
+    state, with fixed (eta, r) and with residual balancing of r; for the D in
+    --table1-oracle the FP64 oracle's iteration count on the same data beside it."""
     import dataclasses
 
     import torch
@@ -599,6 +599,7 @@ def run_table1(args):
     offs, u_true, w, f = _gpu_problem_inputs(od, base, dev)
     truth = torch.from_numpy(np.asarray(u_true, np.complex64)).to(dev)
     w_dev = torch.from_numpy(w).to(dev)
+    oracle_d = {int(x) for x in args.table1_oracle.split(",") if x.strip()}
     for D in (1, 2, 4, 6, 8, 10):
         p = dataclasses.replace(base, sub_cols=D)
         line = {"workload": f"table1_od2p_512px_m64_841frames_1x{D}stripes_noiseless", "frames": len(offs),
@@ -619,10 +620,10 @@ def run_table1(args):
                 rec["r_end"] = r_end
             line["balanced_r" if balance else "fixed"] = rec
             plan.close()
-        if D == 1 and not args.no_cpu_baseline:
+        if D in oracle_d and not args.no_cpu_baseline:
             import oracle
             fh = f.cpu().numpy().astype(np.float64)
-            a = oracle.ADMM(fh, w, offs, p.n, p.n, 1, 1, p.overlap_px, p.eps, eta, r)
+            a = oracle.ADMM(fh, w, offs, p.n, p.n, 1, D, p.overlap_px, p.eps, eta, r)
             t0, it = time.perf_counter(), 0
             while it < 1000:
                 a.iterate(args.check)
@@ -714,6 +715,8 @@ def main():
     ap.add_argument("--eta", type=float, default=0.1, help="with --table1")
     ap.add_argument("--r", type=float, default=4e3, help="with --table1")
     ap.add_argument("--check", type=int, default=10, help="with --table1: iterations between RF checks")
+    ap.add_argument("--table1-oracle", default="1",
+                    help="with --table1: comma-separated D for which the FP64 oracle runs the same stopping rule")
     args = ap.parse_args()
     if args.table1:
         run_table1(args)

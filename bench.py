@@ -582,14 +582,15 @@ def run_table1(args):
     512^2 noiseless image, a 64^2 probe, raster step 16 (841 frames), D = 1 ... 10
     stripe subdomains, eps = 0.5, until RF <= 1e-5 (at most 1000 iterations).
     For every D: iterations, RF, RE, SNR and the GPU wall clock from the initial
-    state, with fixed (eta, r) and with residual balancing of r; for the D in
+    state, with fixed (eta, r), with residual balancing of r, and with Lemma 2.4's
+    sufficient (r, eta) from the plan's operator norms; for the D in
     --table1-oracle the FP64 oracle's iteration count on the same data beside it."""
     import dataclasses
 
     import torch
 
     import paper_2011_00162_gb300 as od
-    from paper_2011_00162_gb300 import synth
+    from paper_2011_00162_gb300 import adaptive, synth
     from paper_2011_00162_gb300 import build as odbuild
     odbuild.build()
     dev = torch.device("cuda", 0)
@@ -605,20 +606,25 @@ def run_table1(args):
         line = {"workload": f"table1_od2p_512px_m64_841frames_1x{D}stripes_noiseless", "frames": len(offs),
                 "subdomains": D, "eta": eta, "r": r, "stop": "RF <= 1e-5 or 1000 iterations",
                 "check_every": args.check}
-        for balance in (False, True):
+        for mode in ("fixed", "balanced_r", "in_K"):
             t_plan = time.perf_counter()
             plan = od.ptycho_plan(od.Geometry(p.n, p.n, p.m, offs, 1, D, p.overlap_px, p.eps, eta, r), f)
             od.od2p_init(plan, w_dev)
             torch.cuda.synchronize()
             t_plan = time.perf_counter() - t_plan
+            if mode == "in_K":  # Lemma 2.4's sufficient (r, eta) from the plan's operator norms
+                r_k, eta_k = adaptive.select_in_K(plan)
+                od.od2p_set_penalties(plan, eta_k, r_k)
             od.od2p_iterate(plan, 2)  # both graph parities captured outside the clock ...
             od.od2p_init(plan, w_dev)  # ... then back to the initial state
-            it, rf, re, sec, r_end = _run_to_rf(od, plan, 1e-5, 1000, args.check, balance)
+            it, rf, re, sec, r_end = _run_to_rf(od, plan, 1e-5, 1000, args.check, mode == "balanced_r")
             rec = {"iterations": it, "rf": rf, "re": re, "snr_db": round(od.od2p_snr(plan, truth), 3),
                    "gpu_seconds": round(sec, 5), "plan_seconds": round(t_plan, 4)}
-            if balance:
+            if mode == "balanced_r":
                 rec["r_end"] = r_end
-            line["balanced_r" if balance else "fixed"] = rec
+            if mode == "in_K":
+                rec["eta"], rec["r"] = eta_k, r_k
+            line[mode] = rec
             plan.close()
         if D in oracle_d and not args.no_cpu_baseline:
             import oracle

@@ -256,6 +256,17 @@ int od2p_set_penalties(ptycho_plan_t *plan, float eta, float r, ptycho_stream_t 
 int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t stream);
 
 /*
+ * The operator norms of Lemma 2.4's parameter set K (eq. paramsSet), taken over
+ * all subdomains and ordered overlap pairs: norms_host[0] = max_d ||A_d^* A_d||
+ * and norms_host[1] = max_{(d,e)} ||pi_{d,e} A_d^*||^2 (0 without overlaps).
+ * A_d^* A_d is diagonal (eq. AtA), so these are the largest illumination
+ * sum_j S_j^T |w|^2 over Omega_d and over Omega_d n Omega_e.  Nonblind plans
+ * only (the known probe of od2p_init); synchronises `stream`.
+ * Errors: INVALID_ARG, STATE (blind plan, or before od2p_init), CUDA.
+ */
+int od2p_operator_norms(ptycho_plan_t *plan, float *norms_host, ptycho_stream_t stream);
+
+/*
  * Section 4's signal-to-noise ratio of the current recovery against the ground
  * truth: SNR(u_r, u_g) = -10 log10(||e^{i theta} u_r - u_g||^2 / ||u_r||^2) dB,
  * with u_r the merged image (as od2p_merge), u_g = truth_dev (img_h x img_w) and

@@ -15,6 +15,8 @@ int32 first.  The functions follow the paper:
 * :func:`forward`, :func:`adjoint` -- A and A^* (section 2);
 * :func:`loss_grad`               -- the ST-AGM data-fidelity loss and gradients;
 * :func:`geometry`, :func:`pairs` -- the overlapping decomposition (sections 2.1, 3.1);
+* :func:`operator_norms`          -- the norms in Lemma 2.4's parameter set K;
+* :func:`probe_init`, :func:`snr` -- section 4.2's initial probe, section 4's SNR;
 * :class:`ADMM`                   -- Algorithm 2 (nonblind) and Algorithm 3 (blind).
 """
 from __future__ import annotations
@@ -215,6 +217,25 @@ def pairs(rect):
     prc = np.empty((max(n, 1), 4), np.int32)
     lib.orc_pairs(rect.shape[0], _p(rect), n, _p(pr), _p(prc))
     return pr[:n], prc[:n]
+
+
+def operator_norms(w, offs, H: int, W: int, sub_rows: int, sub_cols: int, overlap_px: int):
+    """Lemma 2.4's operator norms over all subdomains and ordered overlap pairs:
+    (max_d ||A_d^* A_d||, max_(d,e) ||pi_{d,e} A_d^*||^2).  A_d^* A_d is the
+    diagonal of eq. (AtA): sum over the frames of subdomain d of S_j^T |w|^2."""
+    w = _c(w, np.complex128)
+    m = w.shape[0]
+    offs = _c(offs, np.int32).reshape(-1, 2)
+    fs, rect = geometry(H, W, m, offs, sub_rows, sub_cols, overlap_px)
+    pr, prc = pairs(rect)
+    illum = np.zeros((rect.shape[0], H, W))
+    for j, (r0, c0) in enumerate(offs):
+        illum[fs[j], r0:r0 + m, c0:c0 + m] += np.abs(w) ** 2
+    a = max(illum[d, R[0]:R[2], R[1]:R[3]].max() for d, R in enumerate(rect))
+    b = 0.0
+    for (d, _e), P in zip(pr, prc):
+        b = max(b, illum[d, P[0]:P[2], P[1]:P[3]].max())
+    return float(a), float(b)
 
 
 class ADMM:

@@ -12,12 +12,52 @@ is more than `ratio` times the dual one, r is multiplied by `factor`; if the
 dual one is more than `ratio` times the primal one, r is divided by it; the
 change goes through od2p_set_penalties, which keeps the unscaled multipliers.
 
+The module also gives the paper's own sufficient choice of (r, eta) inside the
+parameter set K of Lemma 2.4 (eq. paramsSet, stated for two subdomains and
+taken here over all subdomains and ordered overlap pairs), for which the
+augmented Lagrangian does not increase: select_in_K reads the operator norms of
+a nonblind plan from the library and params_in_K applies the lemma's bounds.
+
 All arithmetic of the iteration runs in the library; this is a host control
 loop over its entry points.
 """
 from __future__ import annotations
 
 from . import api
+
+
+def params_in_K(norms: tuple[float, float], eps: float, margin: float = 1.01) -> tuple[float, float]:
+    """(r, eta) inside K for operator norms (max ||A_d^* A_d||, max ||pi_{d,e} A_d^*||^2)
+    and ST-AGM truncation eps, by the sufficient choice that follows eq. (paramsSet):
+    eta > max(6L + 2L^2 + 2 (c1 / c0^2) (L + 1)^2, 1) and r > c0 eta, with
+    L = 2/eps - 1 (Lemma 2.1), c0 = max(2 ||A^*A||, ||pi A^*||), c1 = 2 ||pi A^*||^2;
+    each bound exceeded by the factor `margin` (> 1)."""
+    if not margin > 1.0:
+        raise ValueError("margin must exceed 1 (the bounds are strict)")
+    if not 0.0 < eps < 1.0:
+        raise ValueError("eps must lie in (0, 1)")
+    a, b = float(norms[0]), float(norms[1])
+    if not a > 0.0:
+        raise ValueError("the illumination is zero")
+    L = 2.0 / eps - 1.0
+    c0 = max(2.0 * a, b ** 0.5)
+    c1 = 2.0 * b
+    eta = margin * max(6.0 * L + 2.0 * L * L + 2.0 * (c1 / c0 ** 2) * (L + 1.0) ** 2, 1.0)
+    return margin * c0 * eta, eta
+
+
+def in_K(r: float, eta: float, norms: tuple[float, float], eps: float) -> bool:
+    """The three inequalities of eq. (paramsSet) for these operator norms."""
+    a, b = float(norms[0]), float(norms[1])
+    L = 2.0 / eps - 1.0
+    c0 = max(2.0 * a, b ** 0.5)
+    return (eta - 1.0 >= 0.0 and r - eta * c0 > 0.0
+            and (eta - 3.0 * L) / 2.0 - L * L / eta - 2.0 * (L + eta) ** 2 / r ** 2 * b > 0.0)
+
+
+def select_in_K(plan: api.Plan, margin: float = 1.01) -> tuple[float, float]:
+    """params_in_K for a nonblind plan, its operator norms measured by the library."""
+    return params_in_K(api.od2p_operator_norms(plan), float(plan.geom.eps), margin)
 
 
 def decide(r: float, primal: float, dual: float, ratio: float = 10.0, factor: float = 2.0,

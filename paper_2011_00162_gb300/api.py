@@ -24,7 +24,7 @@ __all__ = [
     "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
     "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
-    "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr",
+    "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr", "od2p_operator_norms",
 ]
 
 LAUNCH_VARIANTS = _lib.LAUNCH_VARIANTS
@@ -238,6 +238,13 @@ def od2p_snr(plan: Plan, truth: torch.Tensor, mask: torch.Tensor | None = None, 
     check(plan._lib.od2p_snr(plan.handle, _ptr(truth.contiguous(), torch.complex64, "truth"), mp,
                              ctypes.byref(v), _stream(stream)))
     return v.value
+
+
+def od2p_operator_norms(plan: Plan, stream=None) -> tuple[float, float]:
+    """(max_d ||A_d^* A_d||, max_(d,e) ||pi_{d,e} A_d^*||^2) of a nonblind plan (Lemma 2.4)."""
+    v = (ctypes.c_float * 2)()
+    check(plan._lib.od2p_operator_norms(plan.handle, v, _stream(stream)))
+    return float(v[0]), float(v[1])
 
 
 def ptycho_release_cached_memory() -> None:

@@ -656,6 +656,36 @@ __global__ void merge_kernel(int H, int W, int D, const int32_t *rect, const int
     }
 }
 
+// ---------------------------------------------------------------- operator norms (Lemma 2.4)
+// A_d^* A_d is diagonal (eq. AtA) with entries nrm = sum_j S_j^T |w|^2, so
+// ||A_d^* A_d|| = max nrm over Omega_d and ||pi_{d,e} A_d^*||^2 = max nrm over
+// Omega_d n Omega_e.  Block row k < P: ordered pair k's overlap -> out[1];
+// row P: every subdomain pixel -> out[0].  Maxima of non-negative floats as
+// unsigned bit patterns (order-free, exact).
+__global__ void __launch_bounds__(256) opnorm_kernel(int P, const int32_t *pair, const int32_t *pair_rect,
+                                                     const int32_t *rect, const int64_t *u_off, int64_t u_len,
+                                                     const float *nrm, uint32_t *out)
+{
+    const int k = blockIdx.y;
+    float mx = 0.f;
+    if (k < P) {
+        const int d = pair[2 * k];
+        const int32_t *pr = pair_rect + 4 * k, *Rd = rect + 4 * d;
+        const int w = pr[3] - pr[1];
+        const int64_t n = (int64_t)(pr[2] - pr[0]) * w;
+        for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+            const int R = pr[0] + (int)(i / w), C = pr[1] + (int)(i % w);
+            mx = fmaxf(mx, nrm[u_off[d] + (int64_t)(R - Rd[0]) * (Rd[3] - Rd[1]) + (C - Rd[1])]);
+        }
+    } else {
+        for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < u_len; i += (int64_t)gridDim.x * 256)
+            mx = fmaxf(mx, nrm[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(out + (k < P ? 1 : 0), __float_as_uint(mx));
+}
+
 // ---------------------------------------------------------------- SNR (section 4)
 constexpr int SNR_BLOCKS = 152 * 4;
 
@@ -1017,6 +1047,15 @@ int launch_q_from_slots(const ptycho_plan_s *p, float2 *dst, cudaStream_t s)
 int launch_merge(const ptycho_plan_s *p, float2 *out, cudaStream_t s)
 {
     merge_kernel<<<152 * 8, 256, 0, s>>>(p->H, p->W, p->D, p->d_rect, p->d_u_off, p->d_u[p->cur], out);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_operator_norms(ptycho_plan_s *p, uint32_t *out, cudaStream_t s)
+{
+    OD2P_CUDA(cudaMemsetAsync(out, 0, 2 * sizeof(uint32_t), s));
+    opnorm_kernel<<<dim3(RC_BLOCKS, p->P + 1), 256, 0, s>>>(p->P, p->d_pair, p->d_pair_rect, p->d_rect, p->d_u_off,
+                                                            p->u_len, p->d_nrm, out);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }

@@ -206,6 +206,7 @@ struct ptycho_plan_s {
     float *d_rc_part = nullptr;        // (P + 1) x 64 partial sums of the consensus residual
     float *d_snr_part = nullptr;       // 2 x 608 partial sums of the SNR passes
     double *d_snr = nullptr;           // [cos theta, sin theta, SNR dB]
+    uint32_t *d_opn = nullptr;         // operator norms as float bits: [max A^*A, max over overlaps]
     int32_t *d_err = nullptr;          // set by a kernel whose bounded wait gave up
     int32_t n_k1_blocks = 0;           // blocks of the persistent frame update
     int32_t k1_variant = 0;            // launch shape of the frame update (0 or 1)
@@ -272,6 +273,7 @@ int launch_scale(float2 *x, int64_t n, float sc, cudaStream_t s);
 int launch_consensus(ptycho_plan_s *p, float *part, double *out, cudaStream_t s);
 int launch_snr(ptycho_plan_s *p, const float2 *truth, const uint8_t *mask, float *part, double *out,
                cudaStream_t s);
+int launch_operator_norms(ptycho_plan_s *p, uint32_t *out, cudaStream_t s);
 int launch_probe_init(ptycho_plan_s *p, float2 *w0, cudaStream_t s);
 int launch_slot_rank(ptycho_plan_s *p, int32_t *setup, cudaStream_t s);
 // Split m = R1 * R2 of the frame update's FFT, which fixes the task order of

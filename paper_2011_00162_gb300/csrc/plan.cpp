@@ -509,7 +509,8 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own, s)) ||
         (rc = dev_alloc(&p->d_metrics, 4, own, s)) || (rc = dev_alloc(&p->d_err, 1, own, s)) ||
         (rc = dev_alloc(&p->d_rc_part, (size_t)(p->P + 1) * 64, own, s)) ||
-        (rc = dev_alloc(&p->d_snr_part, 2 * 152 * 4, own, s)) || (rc = dev_alloc(&p->d_snr, 3, own, s)))
+        (rc = dev_alloc(&p->d_snr_part, 2 * 152 * 4, own, s)) || (rc = dev_alloc(&p->d_snr, 3, own, s)) ||
+        (rc = dev_alloc(&p->d_opn, 2, own, s)))
         return bail(rc);
     if (p->blind) {
         if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own, s)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own, s)))
@@ -731,6 +732,20 @@ int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t
     OD2P_CUDA(cudaMemcpyAsync(&h, plan->d_metrics + 3, sizeof(h), cudaMemcpyDeviceToHost, s));
     OD2P_CUDA(cudaStreamSynchronize(s));
     *rc_host = (float)h;
+    return PTYCHO_OK;
+}
+
+int od2p_operator_norms(ptycho_plan_t *plan, float *norms_host, ptycho_stream_t stream)
+{
+    if (!plan || !norms_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    if (plan->blind) return fail(PTYCHO_ERR_STATE, "operator norms need a nonblind plan (a known probe)");
+    if (!plan->initialised) return fail(PTYCHO_ERR_STATE, "od2p_init has not been called");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = launch_operator_norms(plan, plan->d_opn, s)) return rc;
+    uint32_t h[2] = {0u, 0u};
+    OD2P_CUDA(cudaMemcpyAsync(h, plan->d_opn, sizeof(h), cudaMemcpyDeviceToHost, s));
+    OD2P_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(norms_host, h, sizeof(h));  // non-negative floats kept as their bit patterns
     return PTYCHO_OK;
 }
 

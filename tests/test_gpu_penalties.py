@@ -109,3 +109,26 @@ def test_penalty_arguments_and_batch_members():
         od.od2p_set_penalties(batch.members[0], 1.0, 1.0)
     assert e.value.code == 6
     batch.close()
+
+
+@pytest.mark.parametrize("which", ["small_2sub", "grid_4x4"])
+def test_operator_norms_match_oracle(which):
+    """Lemma 2.4's operator norms from the plan's illumination equal the oracle's,
+    and the selected (r, eta) lie in K; blind plans are refused."""
+    p = getattr(synth, which)()
+    offs, u_true, w, f = make_case(p)
+    g = od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, p.eta, p.r)
+    plan = od.ptycho_plan(g, torch.as_tensor(np.asarray(f, np.float32), device=DEV))
+    od.od2p_init(plan, torch.as_tensor(np.asarray(w, np.complex64), device=DEV))
+    a, b = od.od2p_operator_norms(plan)
+    a_want, b_want = oracle.operator_norms(w, offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px)
+    record(f"operator_norms_{which}", gpu=[a, b], oracle=[a_want, b_want])
+    assert abs(a - a_want) <= 1e-6 * a_want and abs(b - b_want) <= 1e-6 * b_want, (a, a_want, b, b_want)
+    r, eta = adaptive.select_in_K(plan)
+    assert adaptive.in_K(r, eta, (a_want, b_want), p.eps)
+    gb = od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, 2.0, 0.5,
+                     mu=1.0, gamma=0.1, blind=True)
+    bp = od.ptycho_plan(gb, torch.as_tensor(np.asarray(f, np.float32), device=DEV))
+    od.od2p_init(bp, torch.as_tensor(np.asarray(w, np.complex64), device=DEV))
+    with pytest.raises(RuntimeError):
+        od.od2p_operator_norms(bp)

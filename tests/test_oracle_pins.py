@@ -437,6 +437,68 @@ def test_augmented_lagrangian_nonincreasing_in_K():
     assert np.all(np.diff(vals) <= 1e-9 * np.abs(vals[:-1]).max()), vals
 
 
+@pytest.mark.parametrize("grid,ov", [((1, 2), 2), ((2, 2), 2)])
+def test_operator_norms_are_spectral_norms(grid, ov):
+    """Lemma 2.4's ||A_d^* A_d|| and ||pi_{d,e} A_d^*||^2 equal the largest
+    squared singular values of the dense operators (F diag(w) S_j restricted to
+    Omega_d; its adjoint restricted to the overlap rows)."""
+    H = W = 14
+    m = 4
+    u, w, offs, f = _tiny_problem(seed=7, H=H, W=W)
+    fs, rect = oracle.geometry(H, W, m, offs, *grid, ov)
+    pr, prc = oracle.pairs(rect)
+    a_want, b_want = 0.0, 0.0
+    for d, R in enumerate(rect):
+        cols = np.array([r * W + c for r in range(R[0], R[2]) for c in range(R[1], R[3])])
+        Ad = _dense_A(H, W, w, offs[fs == d])[:, cols]
+        a_want = max(a_want, np.linalg.norm(Ad, 2) ** 2)
+        for (d0, _e), P in zip(pr, prc):
+            if d0 != d:
+                continue
+            rows = [i for i, px in enumerate(cols) if P[0] <= px // W < P[2] and P[1] <= px % W < P[3]]
+            b_want = max(b_want, np.linalg.norm(Ad.conj().T[rows, :], 2) ** 2)
+    a, b = oracle.operator_norms(w, offs, H, W, *grid, ov)
+    assert len(pr) > 0
+    assert abs(a - a_want) < 1e-9 * a_want and abs(b - b_want) < 1e-9 * b_want, (a, a_want, b, b_want)
+
+
+def test_params_in_K_lie_in_K():
+    """The sufficient choice after eq. (paramsSet) satisfies its three
+    inequalities; parameters below the bounds fail them."""
+    from paper_2011_00162_gb300 import adaptive
+    for norms in [(16.0, 9.0), (1.0, 0.25), (300.0, 300.0), (2.0, 0.0)]:
+        for eps in (0.2, 0.5, 0.9):
+            r, eta = adaptive.params_in_K(norms, eps)
+            assert adaptive.in_K(r, eta, norms, eps), (norms, eps, r, eta)
+            L = 2 / eps - 1
+            assert eta > 6 * L + 2 * L * L and r > 2 * norms[0] * eta
+            assert not adaptive.in_K(r, 0.5, norms, eps)                 # eta < 1
+            assert not adaptive.in_K(eta * 2 * norms[0], eta, norms, eps)  # r = c0 eta (not >)
+            assert not adaptive.in_K(r, 3 * L, norms, eps)               # (eta - 3L)/2 - ... < 0
+    with pytest.raises(ValueError):
+        adaptive.params_in_K((1.0, 1.0), 0.5, margin=1.0)
+
+
+def test_augmented_lagrangian_nonincreasing_for_selected_params():
+    """Lemma 2.4 with (r, eta) chosen from the measured operator norms."""
+    from paper_2011_00162_gb300 import adaptive
+    H = W = 14
+    m = 4
+    u, w, offs, f = _tiny_problem(noiseless=False, seed=8)
+    eps, grid = 0.5, (1, 2)
+    r, eta = adaptive.params_in_K(oracle.operator_norms(w, offs, H, W, *grid, 2), eps)
+    fs, rect = oracle.geometry(H, W, m, offs, *grid, 2)
+    pr, prc = oracle.pairs(rect)
+    a = oracle.ADMM(f, w, offs, H, W, *grid, 2, eps, eta, r)
+    a.iterate(1)
+    vals = []
+    for _ in range(25):
+        a.iterate(1)
+        vals.append(_aug_lagrangian(a, f, w, offs, H, W, m, grid, eps, eta, r, fs, rect, pr, prc))
+    vals = np.array(vals)
+    assert np.all(np.diff(vals) <= 1e-9 * np.abs(vals[:-1]).max()), vals
+
+
 def test_blind_W_and_U_are_least_squares_minimisers():
     """Algorithm 3, eqs. (blind_W) and (blind_U), against dense least-squares solves."""
     H = W = 12

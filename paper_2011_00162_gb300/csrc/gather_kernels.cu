@@ -85,6 +85,9 @@ constexpr int NBR_SMEM = 16;
 #ifndef OD2P_K2B_MINB
 #define OD2P_K2B_MINB 4
 #endif
+#ifndef OD2P_PROBE_U
+#define OD2P_PROBE_U 4
+#endif
 template <bool BLIND, bool BATCHED>
 __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? OD2P_K2B_MINB : OD2P_K2_MINB)
     subdomain_update_kernel(const SubArgs single, const SubArgs *__restrict__ tab, const int2 *__restrict__ items,
@@ -395,8 +398,8 @@ __global__ void probe_partial_kernel(ProbeArgs a)
     const int kr = k / a.M, kc = k % a.M;
     float2 acc = make_float2(0.f, 0.f);
     float nn = 0.f;
-    // four frames' loads in flight per step, accumulated in ascending order
-    constexpr int U = 4;
+    // U frames' loads in flight per step, accumulated in ascending order
+    constexpr int U = OD2P_PROBE_U;
     for (int t0 = ch.y; t0 < ch.z; t0 += U) {
         float2 uv[U], hv[U];
 #pragma unroll

@@ -23,7 +23,10 @@ constexpr int TILE_W = 32;
 constexpr int GATHER_THREADS = 256;
 constexpr int TILE_ROWS = TILE_H * TILE_W / GATHER_THREADS;
 // Frames per chunk of the fixed-order probe reductions (blind W, grad w).
-constexpr int PROBE_CHUNK = 32;
+#ifndef OD2P_PROBE_CHUNK
+#define OD2P_PROBE_CHUNK 32
+#endif
+constexpr int PROBE_CHUNK = OD2P_PROBE_CHUNK;
 // m = 256 frames go through their three FFT passes in waves of this many
 // frames (a 38 MB intermediate that stays in L2; 76 frames x 16 column slabs
 // fill two rounds of the column pass at four blocks per SM).

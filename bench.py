@@ -641,6 +641,34 @@ def run_table1(args):
         print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- ceilings
+def run_peaks(args):
+    """The FP32 FMA and shared-memory ceilings of this GPU, measured with the
+    library's probes (CUDA events, median of 5), beside the frame update's own
+    FLOP rate: one JSON line."""
+    import torch
+
+    import paper_2011_00162_gb300 as od
+    from paper_2011_00162_gb300 import build as odbuild
+    odbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    nb = sms * 8
+    sink = torch.empty(nb * 256, dtype=torch.float32, device=dev)
+    out = {"metric": "ceilings", "sms": sms}
+    for kind, iters, per, key, unit in ((od.PROBE_FMA, 20000, 16.0, "fp32_tflops", 1e12),
+                                        (od.PROBE_SMEM, 4000, 128.0, "smem_tbs", 1e12)):
+        od.ptycho_peak_probe(kind, nb, iters, sink)
+        ts = _event_times(lambda: od.ptycho_peak_probe(kind, nb, iters, sink), 5, torch.empty(1, device=dev))
+        out[key] = round(nb * 256 * iters * per / statistics.median(ts) / unit, 2)
+    # the frame update's FLOPs at 512^2 / 841 frames of 64^2: 2 x 5 m^2 log2(m^2) for the
+    # transform pair plus about 50 m^2 for the exit wave, prox, Gamma update and weighting
+    m, J = 64, 841
+    out["frame_update_flop_per_launch"] = float(J * (10 * m * m * 12 + 50 * m * m))
+    print(json.dumps(out), flush=True)
+
+
 def _oracle_case(p):
     import oracle
     from paper_2011_00162_gb300 import synth
@@ -664,8 +692,41 @@ def cpu_baseline(p, budget_s: float = 15.0):
         if el > budget_s or n >= 200:
             break
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": round(len(offs) * n / el, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} oracle iterations of {WORKLOAD} ({len(offs)} frames each), {el:.1f} s"}
+    out = {"value": round(len(offs) * n / el, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{n} oracle iterations of {WORKLOAD} ({len(offs)} frames each), {el:.1f} s",
+           "cpu_model": _cpu_model()}
+    one = _one_core_rate()
+    if one is not None:
+        out["one_core"] = one
+    return out
+
+
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20)
+        for ln in r.stdout.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
+def _one_core_rate(steps: int = 3):
+    """The reference arm (the oracle) on one host core: a child process with
+    OMP_NUM_THREADS=1 timing `steps` iterations of the same workload."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", str(steps),
+                            "--warmup", "1"], env=env, capture_output=True, text=True, timeout=600)
+        line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1]
+        d = json.loads(line)
+        return {"value": d["value"], "unit": d["unit"], "cores": 1,
+                "sample": f"{steps} oracle iterations of {WORKLOAD} on one core"}
+    except (OSError, subprocess.SubprocessError, IndexError, ValueError, KeyError):
+        return None
 
 
 def run_reference(args):
@@ -695,7 +756,7 @@ def run_reference(args):
                                         "frames": len(offs), "subdomains": f"{p.sub_rows}x{p.sub_cols}",
                                         "step": "one ADMM iteration of the FP64 CPU oracle"},
         "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} oracle iterations of {WORKLOAD}"},
+                         "sample": f"{args.steps} oracle iterations of {WORKLOAD}", "cpu_model": _cpu_model()},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -716,6 +777,8 @@ def main():
     ap.add_argument("--configs", action="store_true",
                     help="measure every workload (one JSON line each) instead of the headline line")
     ap.add_argument("--only", default="", help="with --configs: only workloads whose name contains this")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP32 FMA and shared-memory ceilings with the library's probes")
     ap.add_argument("--table1", action="store_true",
                     help="run Table 1's workload (section 4.2) (D = 1 ... 10 stripes) to RF <= 1e-5")
     ap.add_argument("--eta", type=float, default=0.1, help="with --table1")
@@ -724,7 +787,9 @@ def main():
     ap.add_argument("--table1-oracle", default="1",
                     help="with --table1: comma-separated D for which the FP64 oracle runs the same stopping rule")
     args = ap.parse_args()
-    if args.table1:
+    if args.peaks:
+        run_peaks(args)
+    elif args.table1:
         run_table1(args)
     elif args.configs:
         run_configs(args)

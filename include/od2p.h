@@ -256,6 +256,19 @@ int od2p_set_penalties(ptycho_plan_t *plan, float eta, float r, ptycho_stream_t 
 int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t stream);
 
 /*
+ * Measurement probes for the ceilings the frame update is compared with (the
+ * paper has none): kind PTYCHO_PROBE_FMA runs n_blocks x 256 threads of eight
+ * independent FP32 FMA chains for `iters` steps (16 FLOP per thread and step);
+ * PTYCHO_PROBE_SMEM has each thread read eight conflict-free 16-byte shared-
+ * memory words per step (128 bytes per thread and step).  One float per thread
+ * goes to sink_dev (n_blocks x 256 floats, caller-owned).  Asynchronous on
+ * `stream`; time it with events.  Errors: INVALID_ARG, CUDA.
+ */
+#define PTYCHO_PROBE_FMA 0
+#define PTYCHO_PROBE_SMEM 1
+int ptycho_peak_probe(int32_t kind, int32_t n_blocks, int32_t iters, float *sink_dev, ptycho_stream_t stream);
+
+/*
  * The operator norms of Lemma 2.4's parameter set K (eq. paramsSet), taken over
  * all subdomains and ordered overlap pairs: norms_host[0] = max_d ||A_d^* A_d||
  * and norms_host[1] = max_{(d,e)} ||pi_{d,e} A_d^*||^2 (0 without overlaps).

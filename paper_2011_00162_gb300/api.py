@@ -24,7 +24,8 @@ __all__ = [
     "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
     "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
-    "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr", "od2p_operator_norms",
+    "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr", "od2p_operator_norms", "ptycho_peak_probe",
+           "PROBE_FMA", "PROBE_SMEM",
 ]
 
 LAUNCH_VARIANTS = _lib.LAUNCH_VARIANTS
@@ -245,6 +246,18 @@ def od2p_operator_norms(plan: Plan, stream=None) -> tuple[float, float]:
     v = (ctypes.c_float * 2)()
     check(plan._lib.od2p_operator_norms(plan.handle, v, _stream(stream)))
     return float(v[0]), float(v[1])
+
+
+PROBE_FMA, PROBE_SMEM = 0, 1
+
+
+def ptycho_peak_probe(kind: int, n_blocks: int, iters: int, sink: torch.Tensor, stream=None) -> None:
+    """Launch the FP32-FMA (PROBE_FMA) or shared-memory (PROBE_SMEM) throughput
+    probe: n_blocks x 256 threads; sink holds n_blocks * 256 floats."""
+    if sink.numel() < n_blocks * 256:
+        raise ValueError("sink must hold n_blocks * 256 floats")
+    check(_lib.load().ptycho_peak_probe(int(kind), int(n_blocks), int(iters), _ptr(sink, torch.float32, "sink"),
+                                        _stream(stream)))
 
 
 def ptycho_release_cached_memory() -> None:

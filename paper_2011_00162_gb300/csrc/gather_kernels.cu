@@ -659,6 +659,46 @@ __global__ void merge_kernel(int H, int W, int D, const int32_t *rect, const int
     }
 }
 
+// ---------------------------------------------------------------- peak probes
+// FP32 FMA throughput: eight independent chains per thread, `iters` steps each
+// (16 FLOP per thread and step); the sum goes to sink so nothing is dropped.
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, float a, float b, float *sink)
+{
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (float)(threadIdx.x + i);
+    for (int k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fmaf(x[i], a, b);
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t += x[i];
+    sink[blockIdx.x * 256 + threadIdx.x] = t;
+}
+
+// Shared-memory load throughput: every step each thread reads eight 16-byte
+// words, lanes on consecutive words (conflict-free), 128 bytes per thread.
+__global__ void __launch_bounds__(256) smem_probe_kernel(int iters, float *sink)
+{
+    __shared__ float4 s[2048];
+    for (int i = threadIdx.x; i < 2048; i += 256) s[i] = make_float4((float)i, 1.f, 2.f, 3.f);
+    __syncthreads();
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 v = s[((warp * 8 + i + k) & 63) * 32 + lane];
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+        }
+    }
+    sink[blockIdx.x * 256 + threadIdx.x] = acc.x + acc.y + acc.z + acc.w;
+}
+
 // ---------------------------------------------------------------- operator norms (Lemma 2.4)
 // A_d^* A_d is diagonal (eq. AtA) with entries nrm = sum_j S_j^T |w|^2, so
 // ||A_d^* A_d|| = max nrm over Omega_d and ||pi_{d,e} A_d^*||^2 = max nrm over
@@ -1050,6 +1090,16 @@ int launch_q_from_slots(const ptycho_plan_s *p, float2 *dst, cudaStream_t s)
 int launch_merge(const ptycho_plan_s *p, float2 *out, cudaStream_t s)
 {
     merge_kernel<<<152 * 8, 256, 0, s>>>(p->H, p->W, p->D, p->d_rect, p->d_u_off, p->d_u[p->cur], out);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_peak_probe(int kind, int n_blocks, int iters, float *sink, cudaStream_t s)
+{
+    if (kind == 0)
+        fma_probe_kernel<<<n_blocks, 256, 0, s>>>(iters, 0.999999f, 1e-7f, sink);
+    else
+        smem_probe_kernel<<<n_blocks, 256, 0, s>>>(iters, sink);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }

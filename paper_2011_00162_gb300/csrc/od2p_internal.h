@@ -277,6 +277,7 @@ int launch_consensus(ptycho_plan_s *p, float *part, double *out, cudaStream_t s)
 int launch_snr(ptycho_plan_s *p, const float2 *truth, const uint8_t *mask, float *part, double *out,
                cudaStream_t s);
 int launch_operator_norms(ptycho_plan_s *p, uint32_t *out, cudaStream_t s);
+int launch_peak_probe(int kind, int n_blocks, int iters, float *sink, cudaStream_t s);
 int launch_probe_init(ptycho_plan_s *p, float2 *w0, cudaStream_t s);
 int launch_slot_rank(ptycho_plan_s *p, int32_t *setup, cudaStream_t s);
 // Split m = R1 * R2 of the frame update's FFT, which fixes the task order of

@@ -735,6 +735,13 @@ int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t
     return PTYCHO_OK;
 }
 
+int ptycho_peak_probe(int32_t kind, int32_t n_blocks, int32_t iters, float *sink_dev, ptycho_stream_t stream)
+{
+    if ((kind != PTYCHO_PROBE_FMA && kind != PTYCHO_PROBE_SMEM) || n_blocks <= 0 || iters <= 0 || !sink_dev)
+        return fail(PTYCHO_ERR_INVALID_ARG, "need kind 0 or 1, n_blocks > 0, iters > 0 and a sink");
+    return launch_peak_probe(kind, n_blocks, iters, sink_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int od2p_operator_norms(ptycho_plan_t *plan, float *norms_host, ptycho_stream_t stream)
 {
     if (!plan || !norms_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");

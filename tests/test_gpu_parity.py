@@ -556,3 +556,21 @@ def test_snr_matches_oracle():
     u = np.concatenate([t[r0:r1, c0:c1].reshape(-1) for r0, c0, r1, c1 in rect])
     od.od2p_set_state(plan, od.STATE_U, c64(u))
     assert abs(od.od2p_snr(plan, c64(u_true)) - (20.0 + 10 * np.log10(1.21))) < 1e-3
+
+
+def test_peak_probes_compute_what_they_claim():
+    """The ceiling probes do their arithmetic: the FMA chains follow the closed
+    form x_n = a^n x_0 + b (1 - a^n) / (1 - a); the shared-memory probe's sums are
+    exact small integers."""
+    nb, iters = 3, 10
+    sink = torch.empty(nb * 256, dtype=torch.float32, device=DEV)
+    od.ptycho_peak_probe(od.PROBE_FMA, nb, iters, sink)
+    a, b = 0.999999, 1e-7
+    t = np.arange(256)
+    want = sum(a ** iters * (t + i) + b * (1 - a ** iters) / (1 - a) for i in range(8))
+    got = host(sink).reshape(nb, 256)
+    assert np.allclose(got, want[None, :], rtol=1e-5)
+    od.ptycho_peak_probe(od.PROBE_SMEM, nb, iters, sink)
+    lane, warp = t % 32, t // 32
+    want = sum(((warp * 8 + i + k) & 63) * 32 + lane for k in range(iters) for i in range(8)) + iters * 8 * 6
+    assert np.array_equal(host(sink).reshape(nb, 256), np.broadcast_to(want.astype(np.float32), (nb, 256)))

@@ -286,7 +286,8 @@ int od2p_operator_norms(ptycho_plan_t *plan, float *norms_host, ptycho_stream_t 
  * theta = arg sum conj(u_r) u_g removing the recovery's global phase.
  * mask_dev: NULL (every pixel) or img_h x img_w bytes, nonzero where the pixel
  * counts (e.g. the illuminated pixels).  Two fixed-order reduction passes;
- * writes a host float and synchronises `stream`.  Errors: INVALID_ARG, CUDA.
+ * writes a host float and synchronises `stream`; the value is NaN when no
+ * pixel is selected or the recovery is zero there.  Errors: INVALID_ARG, CUDA.
  */
 int od2p_snr(ptycho_plan_t *plan, const ptycho_c32 *truth_dev, const uint8_t *mask_dev, float *snr_host,
              ptycho_stream_t stream);

@@ -56,7 +56,7 @@ enum {
     PTYCHO_ERR_STATE = 6        /* call not valid in the plan's current state             */
 };
 
-/* ptycho_get_state / ptycho_set_state selectors */
+/* od2p_get_state / od2p_set_state selectors */
 enum {
     PTYCHO_STATE_U = 0,      /* u_d: concatenated subdomain rectangles, d ascending        */
     PTYCHO_STATE_GAMMA = 1,  /* Gamma: J x m x m, natural frequency order                  */
@@ -87,7 +87,7 @@ enum {
  */
 typedef struct {
     int32_t img_h, img_w;           /* image size in pixels                                 */
-    int32_t m;                      /* probe side: 16, 32, 64, 128 or 256                  */
+    int32_t m;                      /* probe side: 16, 32, 48, 64, 80, 96, 128 or 256      */
     int32_t n_frames;               /* J >= 1                                              */
     const int32_t *offsets_host;    /* J x 2 (row, col), 0 <= row <= img_h-m, col likewise  */
     int32_t sub_rows, sub_cols;     /* subdomain grid, >= 1                                */
@@ -206,8 +206,11 @@ int od2p_iterate(ptycho_plan_t *plan, int32_t n_iter, ptycho_stream_t stream);
  *  od2p_subdomain_update: Step 1 v (eq. updateV-multi), Step 3 u (eq.
  *                         Alg1-solver-u, D-subdomain form) by gathering q_j in
  *                         ascending j, Step 4 Lambda (eq. updateM-2-multi).
- * Calling them in this order equals od2p_iterate(plan, 1).  Blind plans
- * return STATE (use od2p_iterate).
+ * Calling them in this order equals od2p_iterate(plan, 1) for a nonblind
+ * plan; for a blind plan, frame update, probe_update and subdomain update in
+ * that order do (the frame update then stores the unweighted residual and the
+ * subdomain update weights it with W_d).  Errors: STATE (od2p_init not
+ * called), CUDA.
  */
 int od2p_frame_update(ptycho_plan_t *plan, ptycho_stream_t stream);
 int od2p_subdomain_update(ptycho_plan_t *plan, ptycho_stream_t stream);
@@ -216,7 +219,7 @@ int od2p_subdomain_update(ptycho_plan_t *plan, ptycho_stream_t stream);
  * Blind probe update (Algorithm 3 Steps 1 (w), 3 (W) and 5 (Delta); eqs.
  * blind_w, blind_W, admm_Delta) from the frame residuals of the last frame
  * update.  od2p_iterate calls it for blind plans; exposed for stage timing.
- * Errors: STATE (nonblind plan).
+ * Errors: STATE (nonblind plan, or od2p_init not called).
  */
 int probe_update(ptycho_plan_t *plan, ptycho_stream_t stream);
 

@@ -263,6 +263,29 @@ def test_bitwise_determinism_and_graph_equals_stages():
         assert np.array_equal(a, b)
 
 
+def test_blind_graph_equals_stages():
+    """A blind iteration replayed from its graph equals frame update, probe
+    update and subdomain update called one by one, bit for bit."""
+    q = synth.Problem("bstage", 96, 32, 6, 1, 2, 2, 8, None, 1, eta=0.5, r=0.1, blind=True, mu=1.0, seed=4)
+    offs, u_true, w, f = make_case(q)
+    keys = (od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA, od.STATE_WD, od.STATE_DELTA, od.STATE_W)
+    outs = []
+    for mode in ("graph", "stages"):
+        plan = od.ptycho_plan(geom_of(q, offs), f32(f))
+        od.od2p_init(plan, c64(synth.gaussian_probe(q.m)))
+        for _ in range(3):
+            if mode == "graph":
+                od.od2p_iterate(plan, 1)
+            else:
+                od.od2p_frame_update(plan)
+                od.probe_update(plan)
+                od.od2p_subdomain_update(plan)
+        outs.append([host(od.od2p_get_state(plan, k)) for k in keys])
+        plan.close()
+    for k, a, b in zip(keys, *outs):
+        assert np.array_equal(a, b), k
+
+
 def test_metrics_and_merge_match_oracle():
     p = synth.grid_4x4()
     offs, u_true, w, f = make_case(p)

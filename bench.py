@@ -551,15 +551,20 @@ def run_configs(args):
 
 # ----------------------------------------------------------------------------- time to solution
 def _run_to_rf(od, plan, tol: float, max_it: int, check: int, balance: bool):
-    """Iterate plan until RF <= tol (checked every `check` iterations) or max_it;
-    with balance, rebalance r at each check (adaptive.decide).  Returns
-    (iterations, RF, RE, seconds of wall clock, r at the end)."""
+    """Iterate plan until RF <= tol or max_it.  Without balance the test runs on
+    the device after every iteration (od2p_iterate_until); with balance the host
+    reads RF every `check` iterations and rebalances r there (adaptive.decide).
+    Returns (iterations, RF, RE, seconds of wall clock, r at the end)."""
     import torch
 
     from paper_2011_00162_gb300 import adaptive
     eta, r = float(plan.geom.eta), float(plan.geom.r)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    if not balance:  # the stopping test on the device after every iteration, inside one graph
+        done, rf = od.od2p_iterate_until(plan, tol, max_it)
+        sec = time.perf_counter() - t0
+        return done, rf, od.od2p_metrics(plan)[1], sec, r
     done, rf, re = 0, float("inf"), float("inf")
     while done < max_it:
         k = min(check, max_it - done)
@@ -581,7 +586,7 @@ def run_table1(args):
     """Table 1's (section 4.2) workload run to its stopping rule on one GPU: a
     512^2 noiseless image, a 64^2 probe, raster step 16 (841 frames), D = 1 ... 10
     stripe subdomains, eps = 0.5, until RF <= 1e-5 (at most 1000 iterations).
-    For every D: iterations, RF, RE, SNR and the GPU wall clock from the initial
+    For every D: iterations, RF, RE, SNR and the wall clock from the initial
     state, with fixed (eta, r), with residual balancing of r, and with Lemma 2.4's
     sufficient (r, eta) from the plan's operator norms; for the D in
     --table1-oracle the FP64 oracle's iteration count on the same data beside it."""

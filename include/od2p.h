@@ -199,6 +199,22 @@ int od2p_init(ptycho_plan_t *plan, const ptycho_c32 *u0_dev, const ptycho_c32 *w
 int od2p_iterate(ptycho_plan_t *plan, int32_t n_iter, ptycho_stream_t stream);
 
 /*
+ * Iterate until section 4's stopping test holds: after every iteration the RF
+ * of that iteration (the same fixed-order sum as od2p_metrics) is compared on
+ * the device, and the loop stops after the first iteration with
+ * (float) RF <= rf_tol, or after max_iter iterations.  The loop runs inside
+ * one CUDA graph (a conditional while node over two iterations, the second
+ * behind a conditional if), so no iteration waits for the host; at least one
+ * iteration runs when max_iter > 0.  Writes the iterations done and the last
+ * RF to the host (either may be NULL) and synchronises `stream`.  The result
+ * equals od2p_iterate one iteration at a time with od2p_metrics after each.
+ * Errors: INVALID_ARG (max_iter < 0, tol not finite), STATE (before
+ * od2p_init, or a batch member), CUDA.
+ */
+int od2p_iterate_until(ptycho_plan_t *plan, float rf_tol, int32_t max_iter, int32_t *n_done_host,
+                       float *rf_host, ptycho_stream_t stream);
+
+/*
  * The two halves of one nonblind iteration, for stage timing:
  *  od2p_frame_update:     Steps 1-2 frame part -- z = Prox(Gamma + A_d u_d),
  *                         Gamma += A_d u_d - z, q_j = conj(w) o F^*(z - Gamma)

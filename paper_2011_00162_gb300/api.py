@@ -25,6 +25,7 @@ __all__ = [
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
     "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
     "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr", "od2p_operator_norms", "ptycho_peak_probe",
+           "od2p_iterate_until",
            "PROBE_FMA", "PROBE_SMEM",
 ]
 
@@ -258,6 +259,16 @@ def ptycho_peak_probe(kind: int, n_blocks: int, iters: int, sink: torch.Tensor, 
         raise ValueError("sink must hold n_blocks * 256 floats")
     check(_lib.load().ptycho_peak_probe(int(kind), int(n_blocks), int(iters), _ptr(sink, torch.float32, "sink"),
                                         _stream(stream)))
+
+
+def od2p_iterate_until(plan: Plan, rf_tol: float, max_iter: int, stream=None) -> tuple[int, float]:
+    """Iterate until (float) RF <= rf_tol or max_iter iterations, the test
+    evaluated on the device after every iteration; returns (iterations, RF)."""
+    n = ctypes.c_int32()
+    rf = ctypes.c_float()
+    check(plan._lib.od2p_iterate_until(plan.handle, float(rf_tol), int(max_iter), ctypes.byref(n),
+                                       ctypes.byref(rf), _stream(stream)))
+    return int(n.value), float(rf.value)
 
 
 def ptycho_release_cached_memory() -> None:

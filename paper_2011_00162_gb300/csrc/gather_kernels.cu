@@ -507,6 +507,37 @@ __global__ void __launch_bounds__(1024) metrics_kernel(int n_rf, const float *rf
     }
 }
 
+// ---- iterate-until: the stopping test of section 4 evaluated on the device
+// st[0] iterations done, st[1] the cap, st[2] the RF tolerance (float bits),
+// st[3] the last RF (float bits).
+__global__ void until_init_kernel(int32_t *st, int32_t max_iter, float tol)
+{
+    st[0] = 0;
+    st[1] = max_iter;
+    st[2] = __float_as_int(tol);
+    st[3] = __float_as_int(0.f);
+}
+
+// After each iteration of the graph's loop: RF of that iteration (the same
+// fixed-order sum as od2p_metrics), then continue while (float) RF > tol and
+// fewer than the cap; the decision sets the loop's condition and, inside the
+// loop body, the condition of its second iteration.
+__global__ void __launch_bounds__(1024) until_check_kernel(int n_rf, const float *rf_part, const double *metrics,
+                                                            int32_t *st, cudaGraphConditionalHandle h_loop,
+                                                            cudaGraphConditionalHandle h_second, int set_second)
+{
+    __shared__ double red[32];
+    const double rf = block_sum_runs<1024>(n_rf, rf_part, 1, 0, red);
+    if (threadIdx.x != 0) return;
+    const float v = (float)(metrics[2] > 0.0 ? rf / metrics[2] : 0.0);
+    const int n = st[0] + 1;
+    st[0] = n;
+    st[3] = __float_as_int(v);
+    const unsigned go = (v > __int_as_float(st[2]) && n < st[1]) ? 1u : 0u;
+    cudaGraphSetConditional(h_loop, go);
+    if (set_second) cudaGraphSetConditional(h_second, go);
+}
+
 __global__ void __launch_bounds__(256) sum_kernel(int n, const float *part, double *dst)
 {
     __shared__ double red[8];
@@ -1101,6 +1132,32 @@ int launch_peak_probe(int kind, int n_blocks, int iters, float *sink, cudaStream
     else
         smem_probe_kernel<<<n_blocks, 256, 0, s>>>(iters, sink);
     OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_until_init(int32_t *st, int32_t max_iter, float tol, cudaStream_t s)
+{
+    until_init_kernel<<<1, 1, 0, s>>>(st, max_iter, tol);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+// Kernel node of the stopping test (arguments copied by the graph at creation).
+int add_until_check_node(cudaGraphNode_t *node, cudaGraph_t graph, const cudaGraphNode_t *dep, ptycho_plan_s *p,
+                         cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_second, int set_second)
+{
+    int n_rf = p->n_rf_parts;
+    const float *rf_part = p->d_rf_part;
+    const double *metrics = p->d_metrics;
+    int32_t *st = p->d_until;
+    void *args[] = {&n_rf, &rf_part, &metrics, &st, &h_loop, &h_second, &set_second};
+    cudaKernelNodeParams kp = {};
+    kp.func = reinterpret_cast<void *>(until_check_kernel);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1024);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    OD2P_CUDA(cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &kp));
     return PTYCHO_OK;
 }
 

@@ -232,8 +232,10 @@ int enqueue_iteration(ptycho_plan_s *p, cudaStream_t s)
     return launch_subdomain_update(p, s);
 }
 
-int capture_graph(ptycho_plan_s *p, int parity)
+// One iteration from buffer parity `parity`, captured into *out (not instantiated).
+int capture_iteration(ptycho_plan_s *p, int parity, cudaGraph_t *out)
 {
+    *out = nullptr;
     if (!p->cap_stream) OD2P_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
     OD2P_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
     const int saved = p->cur;
@@ -247,7 +249,70 @@ int capture_graph(ptycho_plan_s *p, int parity)
         return rc;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&p->graph[parity], g, 0);
+    *out = g;
+    return PTYCHO_OK;
+}
+
+// The iterate-until graph from parity `parity`: a device-side while loop whose
+// body runs the iteration from `parity`, the stopping test, and -- if the test
+// says go on -- the iteration from the other parity and the test again, so the
+// loop stops after the exact iteration that met the test.
+int build_until_graph(ptycho_plan_s *p, int parity)
+{
+    cudaGraph_t it[2] = {nullptr, nullptr}, G = nullptr;
+    int rc = PTYCHO_OK;
+    cudaError_t e = cudaSuccess;
+    auto done = [&](int code) {
+        for (cudaGraph_t g : {it[0], it[1], G})
+            if (g) cudaGraphDestroy(g);
+        return code;
+    };
+    if ((rc = capture_iteration(p, parity, &it[0])) || (rc = capture_iteration(p, parity ^ 1, &it[1])))
+        return done(rc);
+    if ((e = cudaGraphCreate(&G, 0)) != cudaSuccess) return done(cuda_fail(e, "cudaGraphCreate"));
+    cudaGraphConditionalHandle h_loop, h_second;
+    if ((e = cudaGraphConditionalHandleCreate(&h_loop, G, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return done(cuda_fail(e, "cudaGraphConditionalHandleCreate"));
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if ((e = cudaGraphAddNode(&loop, G, nullptr, nullptr, 0, &wp)) != cudaSuccess)
+        return done(cuda_fail(e, "cudaGraphAddNode (while)"));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    if ((e = cudaGraphConditionalHandleCreate(&h_second, body, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return done(cuda_fail(e, "cudaGraphConditionalHandleCreate"));
+    cudaGraphNode_t first, test1;
+    if ((e = cudaGraphAddChildGraphNode(&first, body, nullptr, 0, it[0])) != cudaSuccess)
+        return done(cuda_fail(e, "cudaGraphAddChildGraphNode"));
+    if ((rc = add_until_check_node(&test1, body, &first, p, h_loop, h_second, 1))) return done(rc);
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h_second;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t second_if;
+    if ((e = cudaGraphAddNode(&second_if, body, &test1, nullptr, 1, &ip)) != cudaSuccess)
+        return done(cuda_fail(e, "cudaGraphAddNode (if)"));
+    cudaGraph_t second_body = ip.conditional.phGraph_out[0];
+    cudaGraphNode_t second, test2;
+    if ((e = cudaGraphAddChildGraphNode(&second, second_body, nullptr, 0, it[1])) != cudaSuccess)
+        return done(cuda_fail(e, "cudaGraphAddChildGraphNode"));
+    if ((rc = add_until_check_node(&test2, second_body, &second, p, h_loop, h_second, 0))) return done(rc);
+    if ((e = cudaGraphInstantiate(&p->until[parity], G, 0)) != cudaSuccess) {
+        p->until[parity] = nullptr;
+        return done(cuda_fail(e, "cudaGraphInstantiate (until)"));
+    }
+    return done(PTYCHO_OK);
+}
+
+int capture_graph(ptycho_plan_s *p, int parity)
+{
+    cudaGraph_t g = nullptr;
+    if (int rc = capture_iteration(p, parity, &g)) return rc;
+    cudaError_t e = cudaGraphInstantiate(&p->graph[parity], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         p->graph[parity] = nullptr;
@@ -288,6 +353,7 @@ int apply_launch(ptycho_plan_s *p, int variant, int blocks_per_sm, cudaStream_t 
     p->n_k1_blocks = grid;
     p->n_rf_parts = parts;
     drop_graphs(p->graph);
+    drop_graphs(p->until);
     return PTYCHO_OK;
 }
 
@@ -316,8 +382,10 @@ int ptycho_plan_destroy(ptycho_plan_t *plan)
     if (!plan) return PTYCHO_OK;
     ptycho_plan_s *p = plan;
     cudaDeviceSynchronize();
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (p->graph[i]) cudaGraphExecDestroy(p->graph[i]);
+        if (p->until[i]) cudaGraphExecDestroy(p->until[i]);
+    }
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     release_owned(p->owned);
     delete p;
@@ -510,7 +578,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = dev_alloc(&p->d_metrics, 4, own, s)) || (rc = dev_alloc(&p->d_err, 1, own, s)) ||
         (rc = dev_alloc(&p->d_rc_part, (size_t)(p->P + 1) * 64, own, s)) ||
         (rc = dev_alloc(&p->d_snr_part, 2 * 152 * 4, own, s)) || (rc = dev_alloc(&p->d_snr, 3, own, s)) ||
-        (rc = dev_alloc(&p->d_opn, 2, own, s)))
+        (rc = dev_alloc(&p->d_opn, 2, own, s)) || (rc = dev_alloc(&p->d_until, 4, own, s)))
         return bail(rc);
     if (p->blind) {
         if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own, s)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own, s)))
@@ -677,6 +745,30 @@ int od2p_iterate(ptycho_plan_t *plan, int32_t n_iter, ptycho_stream_t stream)
     return PTYCHO_OK;
 }
 
+int od2p_iterate_until(ptycho_plan_t *plan, float rf_tol, int32_t max_iter, int32_t *n_done_host,
+                       float *rf_host, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (max_iter < 0 || !std::isfinite(rf_tol)) return fail(PTYCHO_ERR_INVALID_ARG, "need max_iter >= 0, finite tol");
+    if (!plan->initialised) return fail(PTYCHO_ERR_STATE, "od2p_init has not been called");
+    if (plan->batch_member) return fail(PTYCHO_ERR_STATE, "a batch member iterates with its batch");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int32_t h[4] = {0, max_iter, 0, 0};
+    if (max_iter > 0) {
+        if (!plan->until[plan->cur])
+            if (int rc = build_until_graph(plan, plan->cur)) return rc;
+        if (int rc = launch_until_init(plan->d_until, max_iter, rf_tol, s)) return rc;
+        OD2P_CUDA(cudaGraphLaunch(plan->until[plan->cur], s));
+        OD2P_CUDA(cudaMemcpyAsync(h, plan->d_until, sizeof(h), cudaMemcpyDeviceToHost, s));
+        OD2P_CUDA(cudaStreamSynchronize(s));
+        if (h[0] < 1 || h[0] > max_iter) return fail(PTYCHO_ERR_CUDA, "iterate-until loop count out of range");
+        plan->cur ^= (h[0] & 1);
+    }
+    if (n_done_host) *n_done_host = h[0];
+    if (rf_host) std::memcpy(rf_host, &h[3], sizeof(float));
+    return PTYCHO_OK;
+}
+
 int od2p_merge(const ptycho_plan_t *plan, ptycho_c32 *u_out, ptycho_stream_t stream)
 {
     if (!plan || !u_out) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
@@ -720,6 +812,7 @@ int od2p_set_penalties(ptycho_plan_t *plan, float eta, float r, ptycho_stream_t 
     OD2P_CUDA(cudaMemcpyAsync(p->d_sargs, p->h_sargs, sizeof(p->h_sargs), cudaMemcpyHostToDevice, s));
     OD2P_CUDA(cudaStreamSynchronize(s));  // the host argument copies are read by the next launches
     drop_graphs(p->graph);
+    drop_graphs(p->until);
     return PTYCHO_OK;
 }
 

@@ -597,3 +597,52 @@ def test_peak_probes_compute_what_they_claim():
     lane, warp = t % 32, t // 32
     want = sum(((warp * 8 + i + k) & 63) * 32 + lane for k in range(iters) for i in range(8)) + iters * 8 * 6
     assert np.array_equal(host(sink).reshape(nb, 256), np.broadcast_to(want.astype(np.float32), (nb, 256)))
+
+
+@pytest.mark.parametrize("blind", [False, True])
+def test_iterate_until_equals_host_stopping_loop(blind):
+    """The device-side stopping loop stops after the same iteration as a host
+    loop that reads RF after every iteration, with bitwise-equal state, for an
+    odd and an even stopping point and at the iteration cap; iterating on from
+    its end continues the same trajectory."""
+    if blind:
+        q = synth.Problem("buntil", 96, 32, 6, 1, 2, 2, 8, None, 1, eta=0.5, r=0.1, blind=True, mu=1.0, seed=4)
+        offs, u_true, w, f = make_case(q)
+        w0 = synth.gaussian_probe(q.m)
+    else:
+        q = synth.small_2sub()
+        offs, u_true, w, f = make_case(q)
+        w0 = w
+    keys = (od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA) + ((od.STATE_WD, od.STATE_W) if blind else ())
+
+    def fresh():
+        plan = od.ptycho_plan(geom_of(q, offs), f32(f))
+        od.od2p_init(plan, c64(w0))
+        return plan
+
+    ref = fresh()
+    rfs, snaps = [], []
+    for _ in range(14):
+        od.od2p_iterate(ref, 1)
+        rfs.append(np.float32(od.od2p_metrics(ref)[0]))
+        snaps.append([host(od.od2p_get_state(ref, k)) for k in keys])
+    for k_stop in (7, 10):  # odd and even iteration counts
+        tol = float(rfs[k_stop - 1])
+        want = next(i + 1 for i, v in enumerate(rfs) if v <= np.float32(tol))
+        plan = fresh()
+        n, rf = od.od2p_iterate_until(plan, tol, 100)
+        assert n == want and np.float32(rf) == rfs[n - 1], (n, want, rf, rfs[n - 1])
+        for k, a in zip(keys, snaps[n - 1]):
+            assert np.array_equal(host(od.od2p_get_state(plan, k)), a), k
+        od.od2p_iterate(plan, 14 - n)  # the buffers' parity is carried on
+        for k, a in zip(keys, snaps[13]):
+            assert np.array_equal(host(od.od2p_get_state(plan, k)), a), k
+        plan.close()
+    plan = fresh()
+    n, rf = od.od2p_iterate_until(plan, 0.0, 5)  # the cap
+    assert n == 5 and np.float32(rf) == rfs[4]
+    assert od.od2p_iterate_until(plan, 1.0, 0) == (0, 0.0)
+    n, _ = od.od2p_iterate_until(plan, 1e9, 50)  # met at once: one iteration runs
+    assert n == 1
+    for k, a in zip(keys, snaps[5]):
+        assert np.array_equal(host(od.od2p_get_state(plan, k)), a), k

@@ -518,6 +518,16 @@ __global__ void until_init_kernel(int32_t *st, int32_t max_iter, float tol)
     st[3] = __float_as_int(0.f);
 }
 
+// Conditional-node self check: set a handle, and mark from the body it guards.
+__global__ void cond_set_kernel(cudaGraphConditionalHandle h, unsigned value)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, value);
+}
+__global__ void cond_mark_kernel(int32_t *flag)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *flag = 1;
+}
+
 // After each iteration of the graph's loop: RF of that iteration (the same
 // fixed-order sum as od2p_metrics), then continue while (float) RF > tol and
 // fewer than the cap; the decision sets the loop's condition and, inside the
@@ -1140,6 +1150,59 @@ int launch_until_init(int32_t *st, int32_t max_iter, float tol, cudaStream_t s)
     until_init_kernel<<<1, 1, 0, s>>>(st, max_iter, tol);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
+}
+
+// Does a device-set condition take effect?  A graph whose if-node (default 0)
+// guards a marking kernel, the condition set to 1 by a kernel before it; no
+// loop, so nothing can spin.  *ok = 1 when the body ran.
+int conditional_selftest(int32_t *scratch, int *ok, cudaStream_t s)
+{
+    *ok = 0;
+    cudaGraph_t G = nullptr;
+    cudaGraphExec_t X = nullptr;
+    int rc = PTYCHO_OK;
+    cudaError_t e = cudaSuccess;
+    auto done = [&](int code) {
+        if (X) cudaGraphExecDestroy(X);
+        if (G) cudaGraphDestroy(G);
+        return code;
+    };
+    if ((e = cudaGraphCreate(&G, 0)) != cudaSuccess) return done(cuda_fail(e, "cudaGraphCreate"));
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return done(cuda_fail(e, "cudaGraphConditionalHandleCreate"));
+    unsigned one = 1u;
+    void *set_args[] = {&h, &one};
+    cudaKernelNodeParams kp = {};
+    kp.func = reinterpret_cast<void *>(cond_set_kernel);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = set_args;
+    cudaGraphNode_t set_node, if_node, mark_node;
+    if ((e = cudaGraphAddKernelNode(&set_node, G, nullptr, 0, &kp)) != cudaSuccess)
+        return done(cuda_fail(e, "cudaGraphAddKernelNode"));
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&if_node, G, &set_node, nullptr, 1, &ip)) != cudaSuccess)
+        return done(cuda_fail(e, "cudaGraphAddNode (if)"));
+    void *mark_args[] = {&scratch};
+    kp.func = reinterpret_cast<void *>(cond_mark_kernel);
+    kp.kernelParams = mark_args;
+    if ((e = cudaGraphAddKernelNode(&mark_node, ip.conditional.phGraph_out[0], nullptr, 0, &kp)) != cudaSuccess)
+        return done(cuda_fail(e, "cudaGraphAddKernelNode"));
+    if ((e = cudaGraphInstantiate(&X, G, 0)) != cudaSuccess) return done(cuda_fail(e, "cudaGraphInstantiate"));
+    int32_t h_flag = 0;
+    if ((e = cudaMemsetAsync(scratch, 0, sizeof(int32_t), s)) != cudaSuccess ||
+        (e = cudaGraphLaunch(X, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&h_flag, scratch, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return done(cuda_fail(e, "conditional self check"));
+    *ok = h_flag == 1;
+    (void)rc;
+    return done(PTYCHO_OK);
 }
 
 // Kernel node of the stopping test (arguments copied by the graph at creation).

@@ -228,6 +228,7 @@ struct ptycho_plan_s {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t until[2] = {nullptr, nullptr};  // iterate-until loops, by starting parity
     int32_t *d_until = nullptr;                      // [done, cap, tol bits, last RF bits]
+    bool cond_checked = false;                       // conditional-node self check passed
     // ---- every device allocation, freed by ptycho_plan_destroy
     std::vector<void *> owned;
 };
@@ -281,6 +282,7 @@ int launch_snr(ptycho_plan_s *p, const float2 *truth, const uint8_t *mask, float
 int launch_operator_norms(ptycho_plan_s *p, uint32_t *out, cudaStream_t s);
 int launch_peak_probe(int kind, int n_blocks, int iters, float *sink, cudaStream_t s);
 int launch_until_init(int32_t *st, int32_t max_iter, float tol, cudaStream_t s);
+int conditional_selftest(int32_t *scratch, int *ok, cudaStream_t s);
 int add_until_check_node(cudaGraphNode_t *node, cudaGraph_t graph, const cudaGraphNode_t *dep, ptycho_plan_s *p,
                          cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_second, int set_second);
 int launch_probe_init(ptycho_plan_s *p, float2 *w0, cudaStream_t s);

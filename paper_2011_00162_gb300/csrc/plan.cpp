@@ -755,8 +755,17 @@ int od2p_iterate_until(ptycho_plan_t *plan, float rf_tol, int32_t max_iter, int3
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int32_t h[4] = {0, max_iter, 0, 0};
     if (max_iter > 0) {
-        if (!plan->until[plan->cur])
+        if (!plan->until[plan->cur]) {
+            // the loop ends only through a device-set condition: check once per
+            // plan that such a condition takes effect (a graph with no loop)
+            if (!plan->cond_checked) {
+                int ok = 0;
+                if (int rc = conditional_selftest(plan->d_until, &ok, s)) return rc;
+                if (!ok) return fail(PTYCHO_ERR_UNSUPPORTED, "device-set graph conditions have no effect here");
+                plan->cond_checked = true;
+            }
             if (int rc = build_until_graph(plan, plan->cur)) return rc;
+        }
         if (int rc = launch_until_init(plan->d_until, max_iter, rf_tol, s)) return rc;
         OD2P_CUDA(cudaGraphLaunch(plan->until[plan->cur], s));
         OD2P_CUDA(cudaMemcpyAsync(h, plan->d_until, sizeof(h), cudaMemcpyDeviceToHost, s));

@@ -646,3 +646,38 @@ def test_iterate_until_equals_host_stopping_loop(blind):
     assert n == 1
     for k, a in zip(keys, snaps[5]):
         assert np.array_equal(host(od.od2p_get_state(plan, k)), a), k
+
+
+def test_concurrent_plans_on_two_streams_and_threads():
+    """Two plans driven at once from two host threads on two CUDA streams
+    (graph capture, replay, metrics) end bitwise equal to the same plans run one
+    after the other."""
+    import threading
+    cases = [synth.small_2sub(), synth.Problem("conc", 128, 32, 8, 1, 2, 2, 8, 1e4, 1, eta=2.0, r=0.5, seed=9)]
+    inputs = [make_case(p) for p in cases]
+
+    def run(i, stream, out):
+        p = cases[i]
+        offs, _, w, f = inputs[i]
+        with torch.cuda.stream(stream):
+            plan = od.ptycho_plan(geom_of(p, offs), f32(f), stream=stream)
+            od.od2p_init(plan, c64(w), stream=stream)
+            for _ in range(5):
+                od.od2p_iterate(plan, 4, stream=stream)
+                od.od2p_metrics(plan, stream=stream)
+            out[i] = [host(od.od2p_get_state(plan, k, stream=stream)) for k in (od.STATE_U, od.STATE_GAMMA)]
+            plan.close()
+
+    seq, par = {}, {}
+    for i in range(2):
+        run(i, torch.cuda.current_stream(), seq)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    th = [threading.Thread(target=run, args=(i, streams[i], par)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    for i in range(2):
+        for a, b in zip(seq[i], par[i]):
+            assert np.array_equal(a, b), i

@@ -646,6 +646,35 @@ def run_table1(args):
         print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- profiling case
+def run_profile_case(args):
+    """A medium blind m = 256 workload for kernel captures (a few GB on the
+    device, inputs larger than L2): 2048^2 image, 256^2 probe, step 48 +-4
+    (1444 frames), 4x4 subdomains, Poisson 1e5; five iterations after two of
+    warm-up, then one line with the time per iteration."""
+    import dataclasses
+
+    import torch
+
+    import paper_2011_00162_gb300 as od
+    from paper_2011_00162_gb300 import synth
+    from paper_2011_00162_gb300 import build as odbuild
+    odbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p = dataclasses.replace(synth.large_blind(), name="od2bp_2048px_m256_4x4", n=2048, sub_rows=4, sub_cols=4)
+    offs, u_true, w, f = _gpu_problem_inputs(od, p, dev)
+    g = od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, 2.0, 0.5, mu=1.0, gamma=0.1,
+                    blind=True)
+    plan = od.ptycho_plan(g, f)
+    od.od2p_init(plan, torch.from_numpy(synth.gaussian_probe(p.m)).to(dev))
+    od.od2p_iterate(plan, 2)
+    flush = torch.empty(1, device=dev)
+    t = _event_times(lambda: od.od2p_iterate(plan, 1), 5, flush)
+    print(json.dumps({"workload": p.name, "frames": len(offs), "ms_per_iteration": round(1e3 * statistics.mean(t), 4),
+                      "rf_after": od.od2p_metrics(plan)[0]}), flush=True)
+
+
 # ----------------------------------------------------------------------------- ceilings
 def run_peaks(args):
     """The FP32 FMA and shared-memory ceilings of this GPU, measured with the
@@ -782,6 +811,8 @@ def main():
     ap.add_argument("--configs", action="store_true",
                     help="measure every workload (one JSON line each) instead of the headline line")
     ap.add_argument("--only", default="", help="with --configs: only workloads whose name contains this")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run a medium blind m = 256 workload (2048^2, 1444 frames) for kernel captures")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP32 FMA and shared-memory ceilings with the library's probes")
     ap.add_argument("--table1", action="store_true",
@@ -792,7 +823,9 @@ def main():
     ap.add_argument("--table1-oracle", default="1",
                     help="with --table1: comma-separated D for which the FP64 oracle runs the same stopping rule")
     args = ap.parse_args()
-    if args.peaks:
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.peaks:
         run_peaks(args)
     elif args.table1:
         run_table1(args)

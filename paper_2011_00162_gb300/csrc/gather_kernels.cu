@@ -1160,7 +1160,6 @@ int conditional_selftest(int32_t *scratch, int *ok, cudaStream_t s)
     *ok = 0;
     cudaGraph_t G = nullptr;
     cudaGraphExec_t X = nullptr;
-    int rc = PTYCHO_OK;
     cudaError_t e = cudaSuccess;
     auto done = [&](int code) {
         if (X) cudaGraphExecDestroy(X);
@@ -1201,7 +1200,6 @@ int conditional_selftest(int32_t *scratch, int *ok, cudaStream_t s)
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return done(cuda_fail(e, "conditional self check"));
     *ok = h_flag == 1;
-    (void)rc;
     return done(PTYCHO_OK);
 }
 

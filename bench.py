@@ -550,10 +550,11 @@ def run_configs(args):
 
 
 # ----------------------------------------------------------------------------- time to solution
-def _run_to_rf(od, plan, tol: float, max_it: int, check: int, balance: bool):
+def _run_to_rf(od, plan, tol: float, max_it: int, check: int, balance: bool, balance_eta: bool = False):
     """Iterate plan until RF <= tol or max_it.  Without balance the test runs on
     the device after every iteration (od2p_iterate_until); with balance the host
-    reads RF every `check` iterations and rebalances r there (adaptive.decide).
+    reads RF every `check` iterations and rebalances r there, and eta too with
+    balance_eta (adaptive.decide).
     Returns (iterations, RF, RE, seconds of wall clock, r at the end)."""
     import torch
 
@@ -568,16 +569,22 @@ def _run_to_rf(od, plan, tol: float, max_it: int, check: int, balance: bool):
     done, rf, re = 0, float("inf"), float("inf")
     while done < max_it:
         k = min(check, max_it - done)
-        od.od2p_iterate(plan, k)
+        if balance_eta:  # Gamma kept before the block's last iteration
+            if k > 1:
+                od.od2p_iterate(plan, k - 1)
+            od.od2p_gamma_snapshot(plan)
+            od.od2p_iterate(plan, 1)
+        else:
+            od.od2p_iterate(plan, k)
         done += k
         rf, re = od.od2p_metrics(plan)  # synchronises
         if rf <= tol:
             break
-        if balance and plan.n_pairs:
-            r_new = adaptive.decide(r, od.od2p_consensus_residual(plan), r * re)
-            if r_new != r:
-                od.od2p_set_penalties(plan, eta, r_new)
-                r = r_new
+        r_new = adaptive.decide(r, od.od2p_consensus_residual(plan), r * re) if plan.n_pairs else r
+        eta_new = adaptive.decide(eta, od.od2p_frame_residual(plan), eta * re) if balance_eta else eta
+        if r_new != r or eta_new != eta:
+            od.od2p_set_penalties(plan, eta_new, r_new)
+            eta, r = eta_new, r_new
     torch.cuda.synchronize()
     return done, rf, re, time.perf_counter() - t0, r
 
@@ -587,7 +594,7 @@ def run_table1(args):
     512^2 noiseless image, a 64^2 probe, raster step 16 (841 frames), D = 1 ... 10
     stripe subdomains, eps = 0.5, until RF <= 1e-5 (at most 1000 iterations).
     For every D: iterations, RF, RE, SNR and the wall clock from the initial
-    state, with fixed (eta, r), with residual balancing of r, and with Lemma 2.4's
+    state, with fixed (eta, r), with residual balancing of r and of (r, eta), and with Lemma 2.4's
     sufficient (r, eta) from the plan's operator norms; for the D in
     --table1-oracle the FP64 oracle's iteration count on the same data beside it."""
     import dataclasses
@@ -611,7 +618,7 @@ def run_table1(args):
         line = {"workload": f"table1_od2p_512px_m64_841frames_1x{D}stripes_noiseless", "frames": len(offs),
                 "subdomains": D, "eta": eta, "r": r, "stop": "RF <= 1e-5 or 1000 iterations",
                 "check_every": args.check}
-        for mode in ("fixed", "balanced_r", "in_K"):
+        for mode in ("fixed", "balanced_r", "balanced_r_eta", "in_K"):
             t_plan = time.perf_counter()
             plan = od.ptycho_plan(od.Geometry(p.n, p.n, p.m, offs, 1, D, p.overlap_px, p.eps, eta, r), f)
             od.od2p_init(plan, w_dev)
@@ -622,11 +629,14 @@ def run_table1(args):
                 od.od2p_set_penalties(plan, eta_k, r_k)
             od.od2p_iterate(plan, 2)  # both graph parities captured outside the clock ...
             od.od2p_init(plan, w_dev)  # ... then back to the initial state
-            it, rf, re, sec, r_end = _run_to_rf(od, plan, 1e-5, 1000, args.check, mode == "balanced_r")
+            it, rf, re, sec, r_end = _run_to_rf(od, plan, 1e-5, 1000, args.check, mode.startswith("balanced"),
+                                                mode == "balanced_r_eta")
             rec = {"iterations": it, "rf": rf, "re": re, "snr_db": round(od.od2p_snr(plan, truth), 3),
                    "gpu_seconds": round(sec, 5), "plan_seconds": round(t_plan, 4)}
-            if mode == "balanced_r":
+            if mode.startswith("balanced"):
                 rec["r_end"] = r_end
+            if mode == "balanced_r_eta":
+                rec["eta_end"] = float(plan.geom.eta)
             if mode == "in_K":
                 rec["eta"], rec["r"] = eta_k, r_k
             line[mode] = rec

@@ -275,6 +275,19 @@ int od2p_set_penalties(ptycho_plan_t *plan, float eta, float r, ptycho_stream_t 
 int od2p_consensus_residual(ptycho_plan_t *plan, float *rc_host, ptycho_stream_t stream);
 
 /*
+ * Primal residual of the frame constraint z_j = A_j u (Algorithm 2 Step 2: the
+ * scaled multiplier moves by A_d u_d^n - z^{n+1}): od2p_gamma_snapshot copies
+ * Gamma into plan-owned memory (allocated on first use), and
+ * od2p_frame_residual returns ||Gamma - Gamma_snapshot|| / ||sqrt f|| over all
+ * frame pixels, reduced in a fixed order.  Taken around one iteration, this is
+ * the relative primal residual of that iteration.  od2p_frame_residual writes a
+ * host float and synchronises `stream`.  Errors: INVALID_ARG, STATE (no
+ * snapshot yet), OOM, CUDA.
+ */
+int od2p_gamma_snapshot(ptycho_plan_t *plan, ptycho_stream_t stream);
+int od2p_frame_residual(ptycho_plan_t *plan, float *res_host, ptycho_stream_t stream);
+
+/*
  * Measurement probes for the ceilings the frame update is compared with (the
  * paper has none): kind PTYCHO_PROBE_FMA runs n_blocks x 256 threads of eight
  * independent FP32 FMA chains for `iters` steps (16 FLOP per thread and step);

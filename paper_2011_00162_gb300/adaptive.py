@@ -3,7 +3,8 @@
 The paper runs OD2P with fixed (eta, r) and names their automatic choice
 future work (section 4.3).  This module supplies the standard residual-balancing
 rule for an ADMM penalty (He, Yang and Wang 2000; Boyd, Parikh, Chu, Peleato,
-Eckstein 2011, section 3.4.1) for the consensus penalty r: every `every`
+Eckstein 2011, section 3.4.1) for the consensus penalty r, and optionally for
+the frame penalty eta (iterate_balanced(..., balance_eta=True)): every `every`
 iterations it compares the primal residual of the consensus constraint -- the
 relative disagreement of the subdomain copies on their overlaps,
 od2p_consensus_residual -- with a dual residual, r times the relative change of
@@ -71,11 +72,17 @@ def decide(r: float, primal: float, dual: float, ratio: float = 10.0, factor: fl
 
 
 def iterate_balanced(plan: api.Plan, n_iter: int, every: int = 10, ratio: float = 10.0, factor: float = 2.0,
-                     r_min: float = 1e-4, r_max: float = 1e4) -> list[dict]:
-    """Run n_iter iterations of plan, rebalancing r every `every` iterations.
+                     r_min: float = 1e-4, r_max: float = 1e4, balance_eta: bool = False,
+                     eta_min: float = 1e-3, eta_max: float = 1e4) -> list[dict]:
+    """Run n_iter iterations of plan, rebalancing r (and, with balance_eta, eta)
+    every `every` iterations.
 
-    Returns one record per check: iterations done, RF, RE, consensus residual
-    and the penalty r in force for the next block of iterations.
+    r: primal = the consensus residual, dual = r * RE.  eta (balance_eta): primal
+    = the frame constraint's relative residual ||Gamma^{n+1} - Gamma^n|| / ||sqrt f||
+    of the block's last iteration (od2p_frame_residual), dual = eta * RE -- the
+    same rule with the relative change of u standing in for the dual residual of
+    either constraint.  Returns one record per check: iterations done, RF, RE,
+    the residuals and the penalties in force for the next block.
     """
     if every < 1:
         raise ValueError("every must be >= 1")
@@ -83,13 +90,26 @@ def iterate_balanced(plan: api.Plan, n_iter: int, every: int = 10, ratio: float 
     history, done = [], 0
     while done < n_iter:
         k = min(every, n_iter - done)
-        api.od2p_iterate(plan, k)
+        if balance_eta:
+            if k > 1:
+                api.od2p_iterate(plan, k - 1)
+            api.od2p_gamma_snapshot(plan)
+            api.od2p_iterate(plan, 1)
+        else:
+            api.od2p_iterate(plan, k)
         done += k
         rf, re = api.od2p_metrics(plan)
         rc = api.od2p_consensus_residual(plan)
+        rec = {"iterations": done, "rf": rf, "re": re, "consensus": rc}
         r_new = decide(r, rc, r * re, ratio, factor, r_min, r_max) if plan.n_pairs else r
-        if r_new != r and done < n_iter:
-            api.od2p_set_penalties(plan, eta, r_new)
-            r = r_new
-        history.append({"iterations": done, "rf": rf, "re": re, "consensus": rc, "r": r})
+        eta_new = eta
+        if balance_eta:
+            fr = api.od2p_frame_residual(plan)
+            rec["frame_residual"] = fr
+            eta_new = decide(eta, fr, eta * re, ratio, factor, eta_min, eta_max)
+        if (r_new != r or eta_new != eta) and done < n_iter:
+            api.od2p_set_penalties(plan, eta_new, r_new)
+            eta, r = eta_new, r_new
+        rec["r"], rec["eta"] = r, eta
+        history.append(rec)
     return history

@@ -25,7 +25,7 @@ __all__ = [
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
     "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
     "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr", "od2p_operator_norms", "ptycho_peak_probe",
-           "od2p_iterate_until",
+           "od2p_iterate_until", "od2p_gamma_snapshot", "od2p_frame_residual",
            "PROBE_FMA", "PROBE_SMEM",
 ]
 
@@ -269,6 +269,18 @@ def od2p_iterate_until(plan: Plan, rf_tol: float, max_iter: int, stream=None) ->
     check(plan._lib.od2p_iterate_until(plan.handle, float(rf_tol), int(max_iter), ctypes.byref(n),
                                        ctypes.byref(rf), _stream(stream)))
     return int(n.value), float(rf.value)
+
+
+def od2p_gamma_snapshot(plan: Plan, stream=None) -> None:
+    """Keep a copy of Gamma for od2p_frame_residual."""
+    check(plan._lib.od2p_gamma_snapshot(plan.handle, _stream(stream)))
+
+
+def od2p_frame_residual(plan: Plan, stream=None) -> float:
+    """||Gamma - Gamma_snapshot|| / ||sqrt f||: the frame constraint's relative primal residual."""
+    v = ctypes.c_float()
+    check(plan._lib.od2p_frame_residual(plan.handle, ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def ptycho_release_cached_memory() -> None:

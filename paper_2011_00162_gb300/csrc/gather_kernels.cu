@@ -740,6 +740,32 @@ __global__ void __launch_bounds__(256) smem_probe_kernel(int iters, float *sink)
     sink[blockIdx.x * 256 + threadIdx.x] = acc.x + acc.y + acc.z + acc.w;
 }
 
+// ---------------------------------------------------------------- frame-space primal residual
+// part[b] = (sum |Gamma - Gamma_snap|^2, sum sqrt(f)^2) over block b's share of
+// the J m^2 frame pixels (grid-strided, fixed order); one warp finishes.
+__global__ void __launch_bounds__(256) frame_residual_partial_kernel(int64_t n, const float2 *g, const float2 *g0,
+                                                                     const float *sf, float *part)
+{
+    __shared__ float red[2 * (256 / 32)];
+    float a = 0.f, b = 0.f;
+    for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        a += cabs2(csub(g[i], g0[i]));
+        b += sf[i] * sf[i];
+    }
+    block_sum2_fixed(a, b, red);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void frame_residual_final_kernel(int nb, const float *part, double *out)
+{
+    const double a = warp_sum_runs(nb, part, 2, 0);
+    const double b = warp_sum_runs(nb, part, 2, 1);
+    if (threadIdx.x == 0) *out = b > 0.0 ? sqrt(a / b) : 0.0;
+}
+
 // ---------------------------------------------------------------- operator norms (Lemma 2.4)
 // A_d^* A_d is diagonal (eq. AtA) with entries nrm = sum_j S_j^T |w|^2, so
 // ||A_d^* A_d|| = max nrm over Omega_d and ||pi_{d,e} A_d^*||^2 = max nrm over
@@ -1219,6 +1245,16 @@ int add_until_check_node(cudaGraphNode_t *node, cudaGraph_t graph, const cudaGra
     kp.sharedMemBytes = 0;
     kp.kernelParams = args;
     OD2P_CUDA(cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &kp));
+    return PTYCHO_OK;
+}
+
+int launch_frame_residual(ptycho_plan_s *p, const float2 *snap, float *part, double *out, cudaStream_t s)
+{
+    constexpr int NB = SNR_BLOCKS;  // the SNR partial buffer holds 2 x SNR_BLOCKS floats
+    frame_residual_partial_kernel<<<NB, 256, 0, s>>>((int64_t)p->J * p->MM, p->d_gamma, snap, p->d_sqrtf, part);
+    OD2P_CUDA(cudaGetLastError());
+    frame_residual_final_kernel<<<1, 32, 0, s>>>(NB, part, out);
+    OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
 

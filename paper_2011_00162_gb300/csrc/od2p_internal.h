@@ -229,6 +229,7 @@ struct ptycho_plan_s {
     cudaGraphExec_t until[2] = {nullptr, nullptr};  // iterate-until loops, by starting parity
     int32_t *d_until = nullptr;                      // [done, cap, tol bits, last RF bits]
     bool cond_checked = false;                       // conditional-node self check passed
+    float2 *d_gamma_snap = nullptr;                  // Gamma snapshot (allocated on first use)
     // ---- every device allocation, freed by ptycho_plan_destroy
     std::vector<void *> owned;
 };
@@ -280,6 +281,7 @@ int launch_consensus(ptycho_plan_s *p, float *part, double *out, cudaStream_t s)
 int launch_snr(ptycho_plan_s *p, const float2 *truth, const uint8_t *mask, float *part, double *out,
                cudaStream_t s);
 int launch_operator_norms(ptycho_plan_s *p, uint32_t *out, cudaStream_t s);
+int launch_frame_residual(ptycho_plan_s *p, const float2 *snap, float *part, double *out, cudaStream_t s);
 int launch_peak_probe(int kind, int n_blocks, int iters, float *sink, cudaStream_t s);
 int launch_until_init(int32_t *st, int32_t max_iter, float tol, cudaStream_t s);
 int conditional_selftest(int32_t *scratch, int *ok, cudaStream_t s);

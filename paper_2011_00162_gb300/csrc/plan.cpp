@@ -844,6 +844,30 @@ int ptycho_peak_probe(int32_t kind, int32_t n_blocks, int32_t iters, float *sink
     return launch_peak_probe(kind, n_blocks, iters, sink_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int od2p_gamma_snapshot(ptycho_plan_t *plan, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)plan->J * plan->MM;
+    if (!plan->d_gamma_snap)
+        if (int rc = dev_alloc(&plan->d_gamma_snap, n, plan->owned, s)) return rc;
+    OD2P_CUDA(cudaMemcpyAsync(plan->d_gamma_snap, plan->d_gamma, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s));
+    return PTYCHO_OK;
+}
+
+int od2p_frame_residual(ptycho_plan_t *plan, float *res_host, ptycho_stream_t stream)
+{
+    if (!plan || !res_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    if (!plan->d_gamma_snap) return fail(PTYCHO_ERR_STATE, "od2p_gamma_snapshot has not been called");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (int rc = launch_frame_residual(plan, plan->d_gamma_snap, plan->d_snr_part, plan->d_snr, s)) return rc;
+    double h = 0.0;
+    OD2P_CUDA(cudaMemcpyAsync(&h, plan->d_snr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    OD2P_CUDA(cudaStreamSynchronize(s));
+    *res_host = (float)h;
+    return PTYCHO_OK;
+}
+
 int od2p_operator_norms(ptycho_plan_t *plan, float *norms_host, ptycho_stream_t stream)
 {
     if (!plan || !norms_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");

@@ -132,3 +132,40 @@ def test_operator_norms_match_oracle(which):
     od.od2p_init(bp, torch.as_tensor(np.asarray(w, np.complex64), device=DEV))
     with pytest.raises(RuntimeError):
         od.od2p_operator_norms(bp)
+
+
+def test_frame_residual_matches_oracle():
+    """||Gamma^{n+1} - Gamma^n|| / ||sqrt f|| across one iteration equals the
+    oracle's, and a snapshot is required first."""
+    p = synth.Problem("fres", 192, 32, 8, 1, 2, 2, 8, 1e4, 1, seed=5)
+    plan, ref = _pair(p, 2.0, 0.5)
+    with pytest.raises(RuntimeError):
+        od.od2p_frame_residual(plan)
+    od.od2p_iterate(plan, 2)
+    ref.iterate(2)
+    od.od2p_gamma_snapshot(plan)
+    g0 = ref.get(oracle.GAMMA)
+    od.od2p_iterate(plan, 1)
+    ref.iterate(1)
+    got = od.od2p_frame_residual(plan)
+    offs, _, _, f = make_case(p)
+    want = np.linalg.norm(ref.get(oracle.GAMMA) - g0) / np.sqrt(np.sum(np.asarray(f, np.float64)))
+    record("frame_residual", gpu=got, oracle=want)
+    assert abs(got - want) < 1e-4 * want, (got, want)
+
+
+def test_balanced_eta_run_replays_on_the_oracle():
+    """The driver's schedule of (eta, r), replayed on the oracle, gives the same iterates."""
+    p = synth.Problem("bal2", 256, 64, 16, 2, 2, 2, 16, 1e4, 1, seed=9)
+    plan, ref = _pair(p, 8.0, 0.02)
+    hist = adaptive.iterate_balanced(plan, 40, every=10, balance_eta=True)
+    assert len({(h["eta"], h["r"]) for h in hist}) > 1, hist
+    eta_prev, r_prev = 8.0, 0.02
+    for h in hist:
+        ref.iterate(10)
+        if (h["eta"], h["r"]) != (eta_prev, r_prev):
+            ref.set_penalties(h["eta"], h["r"])
+            eta_prev, r_prev = h["eta"], h["r"]
+    err = rel_l2(od.od2p_get_state(plan, od.STATE_U).cpu().numpy(), ref.get(oracle.U))
+    record("balanced_eta_run_40its", u=err, eta_final=hist[-1]["eta"], r_final=hist[-1]["r"])
+    assert err < 1e-4, (err, hist)

@@ -581,7 +581,8 @@ def _run_to_rf(od, plan, tol: float, max_it: int, check: int, balance: bool, bal
         if rf <= tol:
             break
         r_new = adaptive.decide(r, od.od2p_consensus_residual(plan), r * re) if plan.n_pairs else r
-        eta_new = adaptive.decide(eta, od.od2p_frame_residual(plan), eta * re) if balance_eta else eta
+        eta_new = (adaptive.decide(eta, od.od2p_frame_residual(plan), eta * re,
+                                   r_min=1.01 * (1.0 - plan.geom.eps) / plan.geom.eps) if balance_eta else eta)
         if r_new != r or eta_new != eta:
             od.od2p_set_penalties(plan, eta_new, r_new)
             eta, r = eta_new, r_new

@@ -73,7 +73,7 @@ def decide(r: float, primal: float, dual: float, ratio: float = 10.0, factor: fl
 
 def iterate_balanced(plan: api.Plan, n_iter: int, every: int = 10, ratio: float = 10.0, factor: float = 2.0,
                      r_min: float = 1e-4, r_max: float = 1e4, balance_eta: bool = False,
-                     eta_min: float = 1e-3, eta_max: float = 1e4) -> list[dict]:
+                     eta_min: float | None = None, eta_max: float = 1e4) -> list[dict]:
     """Run n_iter iterations of plan, rebalancing r (and, with balance_eta, eta)
     every `every` iterations.
 
@@ -81,12 +81,18 @@ def iterate_balanced(plan: api.Plan, n_iter: int, every: int = 10, ratio: float 
     = the frame constraint's relative residual ||Gamma^{n+1} - Gamma^n|| / ||sqrt f||
     of the block's last iteration (od2p_frame_residual), dual = eta * RE -- the
     same rule with the relative change of u standing in for the dual residual of
-    either constraint.  Returns one record per check: iterations done, RF, RE,
-    the residuals and the penalties in force for the next block.
+    either constraint.  eta stays above eta_min, by default 1.01 (1 - eps) / eps:
+    at or below (1 - eps) / eps the ST-AGM prox of eq. (Prox_sol) jumps at y = 0
+    (only its AGM branch is reachable), which makes runs sensitive to rounding.
+    Returns one record per check: iterations done, RF, RE, the residuals and the
+    penalties in force for the next block.
     """
     if every < 1:
         raise ValueError("every must be >= 1")
     eta, r = float(plan.geom.eta), float(plan.geom.r)
+    if eta_min is None:
+        eps = float(plan.geom.eps)
+        eta_min = 1.01 * (1.0 - eps) / eps
     history, done = [], 0
     while done < n_iter:
         k = min(every, n_iter - done)

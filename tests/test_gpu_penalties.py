@@ -168,4 +168,6 @@ def test_balanced_eta_run_replays_on_the_oracle():
             eta_prev, r_prev = h["eta"], h["r"]
     err = rel_l2(od.od2p_get_state(plan, od.STATE_U).cpu().numpy(), ref.get(oracle.U))
     record("balanced_eta_run_40its", u=err, eta_final=hist[-1]["eta"], r_final=hist[-1]["r"])
-    assert err < 1e-4, (err, hist)
+    # a 40-iteration noisy run with penalty jumps: the end-of-run bar (1e-3), not the one-iteration one
+    assert err < 1e-3, (err, hist)
+    assert all(h["eta"] > (1 - p.eps) / p.eps for h in hist)

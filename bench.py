@@ -43,6 +43,7 @@ WORKLOAD = "od2p_512px_m64_841frames_4x4sub_poisson1e4"
 METRIC = "ADMM frame-updates/sec"
 UNIT = "frame-updates/s"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "frame_update_m64_512px_841frames.md")
+TRAFFIC_FILE_F4 = os.path.join(ROOT, "profiles", "frame_update_16x4_kind{kind}_m64_512px_841frames.md")
 
 
 def _problem():
@@ -67,11 +68,12 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic():
-    """DRAM bytes per frame-update launch from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+def _ncu_traffic(fft_kind: int = 0):
+    """DRAM bytes per frame-update launch from the committed ncu summary of the
+    kernel in use (the 8 x 8 split, or the 16 x 4 split of fft kinds 1 and 2),
+    if it was taken on the current kernel source (else None)."""
     try:
-        txt = open(TRAFFIC_FILE).read()
+        txt = open(TRAFFIC_FILE if fft_kind == 0 else TRAFFIC_FILE_F4.format(kind=fft_kind)).read()
     except OSError:
         return None
     src = tr = None
@@ -310,6 +312,7 @@ def run_gpu(args):
     # disk (tuning restores the plan's state; every shape gives identical iterates)
     tuned = autotune.tune_plan(plan, flush_l2=True, use_cache=not args.retune) if not args.no_tune else None
     launch = od.ptycho_plan_get_launch(plan)
+    fft_kind = od.ptycho_plan_get_fft(plan)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -373,7 +376,7 @@ def run_gpu(args):
     alg_bytes = 20.0 * p.m * p.m * J  # f 4 B + Gamma read 8 B + write 8 B per frame pixel
     k1_avg_s = statistics.mean(k1_ms) / 1e3
     achieved = alg_bytes / k1_avg_s / 1e9
-    traffic = _ncu_traffic()
+    traffic = _ncu_traffic(fft_kind)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": K,
@@ -392,11 +395,14 @@ def run_gpu(args):
                                     "each launch, L2 flushed before each iteration), after the timed steps",
                    "rf_after": rf, "re_after": re, "snr_db_after": round(snr_db, 3),
                    "launch": {"variant": launch[0], "blocks_per_sm": launch[1], "max_blocks_per_sm": launch[2],
+                              "fft": fft_kind,
                               "tuned": None if tuned is None else
                               {"cached": tuned["cached"], "trials_us": tuned.get("trials")}}},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": f"frame_update_kernel<64, variant {launch[0]}>", "peak_kind": peak_kind,
+                     "kernel": (f"frame_update_kernel<64, variant {launch[0]}> (8 x 8 transform split)" if fft_kind == 0
+                                else f"frame_update_f4_kernel<{2 - fft_kind}> (16 x 4 transform split, fft kind {fft_kind})"),
+                     "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes},
             "e2e": e2e,
         "gpu_launches": 2 * K,

@@ -357,6 +357,20 @@ int ptycho_probe_init(ptycho_plan_t *plan, ptycho_c32 *w0_dev, ptycho_stream_t s
  * blocks_per_sm < 0), UNSUPPORTED (variant 1 for m = 256), STATE, CUDA.
  */
 #define PTYCHO_LAUNCH_VARIANTS 2
+
+/*
+ * Factorisation of the frame update's 64-point transforms (m = 64 only; the
+ * paper fixes none): kind 0 (default) splits each axis 8 x 8 -- three shared-
+ * memory exchanges per direction, the launch shapes above; kinds 1 and 2 split
+ * each axis 16 x 4 and run both axes' radix-4 stages together in a 4 x 4 block
+ * per thread -- two exchanges per direction, one frame per 256-thread block,
+ * Gamma staged in shared memory (1) or read through L2 (2).  Kinds give the
+ * same iterates up to FP32 rounding (not bit for bit); a plan's own iterates
+ * stay deterministic.  Drops the captured graphs.  Errors: INVALID_ARG (kind
+ * not 0-2), UNSUPPORTED (kind 1 or 2 with m != 64), STATE (a batch member).
+ */
+int ptycho_plan_set_fft(ptycho_plan_t *plan, int32_t kind, ptycho_stream_t stream);
+int ptycho_plan_get_fft(const ptycho_plan_t *plan, int32_t *kind);
 int ptycho_plan_set_launch(ptycho_plan_t *plan, int32_t variant, int32_t blocks_per_sm, ptycho_stream_t stream);
 int ptycho_plan_get_launch(const ptycho_plan_t *plan, int32_t *variant, int32_t *blocks_per_sm,
                            int32_t *max_blocks_per_sm);

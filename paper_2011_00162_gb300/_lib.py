@@ -72,6 +72,8 @@ SIGNATURES = {
     "od2p_operator_norms": (ctypes.c_int, [_P, _P, _P]),
     "od2p_iterate_until": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int32, _P, _P, _P]),
     "od2p_gamma_snapshot": (ctypes.c_int, [_P, _P]),
+    "ptycho_plan_set_fft": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "ptycho_plan_get_fft": (ctypes.c_int, [_P, _P]),
     "od2p_frame_residual": (ctypes.c_int, [_P, _P, _P]),
     "ptycho_peak_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "ptycho_plan_set_launch": (ctypes.c_int, [_P, _I32, _I32, _P]),

@@ -25,7 +25,8 @@ __all__ = [
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
     "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
     "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr", "od2p_operator_norms", "ptycho_peak_probe",
-           "od2p_iterate_until", "od2p_gamma_snapshot", "od2p_frame_residual",
+           "od2p_iterate_until", "od2p_gamma_snapshot", "od2p_frame_residual", "ptycho_plan_set_fft",
+           "ptycho_plan_get_fft",
            "PROBE_FMA", "PROBE_SMEM",
 ]
 
@@ -281,6 +282,17 @@ def od2p_frame_residual(plan: Plan, stream=None) -> float:
     v = ctypes.c_float()
     check(plan._lib.od2p_frame_residual(plan.handle, ctypes.byref(v), _stream(stream)))
     return v.value
+
+
+def ptycho_plan_set_fft(plan: Plan, kind: int, stream=None) -> None:
+    """m = 64: 0 = the 8 x 8 transform split, 1 / 2 = the 16 x 4 split (Gamma staged / via L2)."""
+    check(plan._lib.ptycho_plan_set_fft(plan.handle, int(kind), _stream(stream)))
+
+
+def ptycho_plan_get_fft(plan: Plan) -> int:
+    k = ctypes.c_int32()
+    check(plan._lib.ptycho_plan_get_fft(plan.handle, ctypes.byref(k)))
+    return int(k.value)
 
 
 def ptycho_release_cached_memory() -> None:

@@ -10,8 +10,12 @@ whole ADMM iterations of the plan itself, timed with CUDA events on the
 launching stream, and the fastest is kept and cached on disk under a key of
 (GPU model, SM count, probe side, frames, subdomains, blind).
 
-Every shape computes the same iterates bit for bit, so tuning never changes a
-result: the plan's state is saved before the trials and restored after them.
+Every shape computes the same iterates bit for bit, so tuning over shapes never
+changes a result: the plan's state is saved before the trials and restored
+after them.  For m = 64 the tuner also times the 16 x 4 transform split
+(``ptycho_plan_set_fft`` kinds 1 and 2) unless ``fft=False``: those kinds give
+the same iterates up to FP32 rounding (tested against the FP64 oracle like the
+default split), not bit for bit.
 
 Cache file: ``$OD2P_AUTOTUNE_CACHE`` if set, else
 ``~/.cache/od2p/autotune.json``.  It is plain JSON; a missing or unreadable
@@ -29,7 +33,7 @@ import torch
 from . import api
 
 CACHE_ENV = "OD2P_AUTOTUNE_CACHE"
-CACHE_VERSION = 1
+CACHE_VERSION = 2
 
 
 def cache_path() -> str:
@@ -128,8 +132,15 @@ def _flush_buffer(device, flush_l2: bool):
     return torch.empty(64 << 20, dtype=torch.float32, device=device) if flush_l2 else None
 
 
+def _apply(plan: api.Plan, entry: dict) -> None:
+    api.ptycho_plan_set_fft(plan, 0)
+    api.ptycho_plan_set_launch(plan, int(entry["variant"]), int(entry["blocks_per_sm"]))
+    if entry.get("fft", 0):
+        api.ptycho_plan_set_fft(plan, int(entry["fft"]))
+
+
 def tune_plan(plan: api.Plan, n_iter: int = 15, warmup: int = 3, flush_l2: bool = False, use_cache: bool = True,
-              path: str | None = None) -> dict:
+              path: str | None = None, fft: bool = True) -> dict:
     """Pick and apply the fastest launch shape of plan's frame update.
 
     od2p_init must have been called.  flush_l2 writes a buffer larger than L2
@@ -138,11 +149,12 @@ def tune_plan(plan: api.Plan, n_iter: int = 15, warmup: int = 3, flush_l2: bool 
     Entries are cached per flush regime.  Returns the cache entry, with
     ``"cached": True`` when it came from the cache instead of a measurement.
     """
-    key = _plan_key(plan) + ("|flush" if flush_l2 else "")
+    fft = fft and plan.geom.m == 64
+    key = _plan_key(plan) + ("|flush" if flush_l2 else "") + ("|fft" if fft else "")
     if use_cache:
         hit = load_cache(path).get(key)
         if hit is not None:
-            api.ptycho_plan_set_launch(plan, int(hit["variant"]), int(hit["blocks_per_sm"]))
+            _apply(plan, hit)
             return dict(hit, cached=True)
     if plan.geom.m == 256:
         entry = {"variant": 0, "blocks_per_sm": 0, "us": None, "trials": {}}
@@ -157,18 +169,29 @@ def tune_plan(plan: api.Plan, n_iter: int = 15, warmup: int = 3, flush_l2: bool 
         maxes[v] = api.ptycho_plan_get_launch(plan)[2]
     flush = _flush_buffer(plan.device, flush_l2)
     trials = {}
+    api.ptycho_plan_set_fft(plan, 0)
     for v, b in candidates(maxes):
         api.ptycho_plan_set_launch(plan, v, b)
         for _ in range(warmup):
             api.od2p_iterate(plan, 1)
         trials[f"{v}:{b}"] = _time_iterations(lambda: api.od2p_iterate(plan, 1), n_iter, flush)
-    best = min(trials, key=trials.get)
-    v, b = (int(x) for x in best.split(":"))
+    shapes = dict(trials)
+    best_shape = min(shapes, key=shapes.get)
+    v, b = (int(x) for x in best_shape.split(":"))
     api.ptycho_plan_set_launch(plan, v, b)
+    for k in ((1, 2) if fft else ()):
+        api.ptycho_plan_set_fft(plan, k)
+        for _ in range(warmup):
+            api.od2p_iterate(plan, 1)
+        trials[f"fft{k}"] = _time_iterations(lambda: api.od2p_iterate(plan, 1), n_iter, flush)
+    api.ptycho_plan_set_fft(plan, 0)
+    best = min(trials, key=trials.get)
+    entry = {"variant": v, "blocks_per_sm": b, "fft": int(best[3:]) if best.startswith("fft") else 0,
+             "us": trials[best], "trials": trials}
+    _apply(plan, entry)
     for w, t in saved.items():
         api.od2p_set_state(plan, w, t)
     torch.cuda.current_stream().synchronize()
-    entry = {"variant": v, "blocks_per_sm": b, "us": trials[best], "trials": trials}
     if use_cache:
         store_cache(key, entry, path)
     return dict(entry, cached=False)

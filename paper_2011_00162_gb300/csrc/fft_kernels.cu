@@ -522,6 +522,234 @@ __global__ void __launch_bounds__(K1Cfg<M, V>::NT, K1Cfg<M, V>::MINB)
     (void)red;
 }
 
+// ---------------------------------------------------------------- K1, m = 64 as 16 x 4 by 4 x 16
+// The same frame update with the 64-point transforms of both axes split as
+// 64 = 16 x 4 (rows r = r1 + 16 r2, columns c = c1 + 16 c2) so that the two
+// radix-4 stages of the two axes run together in one thread (a 4 x 4 block of
+// the frame) and each radix-16 stage of an axis in another: two shared-memory
+// exchanges per direction instead of three.  One frame per 256-thread block.
+//  pass 1  thread (r1, c1): exit wave at (r1 + 16 r2, c1 + 16 c2), 4-point DFTs
+//          over r2 then c2 with the twiddles w64^(r1 k1), w64^(c1 l1); stored at
+//          row 16 k1 + r1, column 16 l1 + c1
+//  pass 2  thread (column, k1): 16-point DFT over r1 -> k2; row frequency
+//          k = k1 + 4 k2 stored at row 16 k1 + k2
+//  pass 3  thread (k, l1): 16-point DFT over c1 -> l2, column frequency
+//          l = l1 + 4 l2; prox and Gamma update at the storage position of
+//          (k, l) shared with the 8 x 8 kernel; inverse 16-point DFT
+//  passes 4, 5: the adjoints of 2 and 1, then the conj(w)-weighted residual
+//          to the gather slots (or q in natural order for list-gather plans).
+// Different rounding from the 8 x 8 split; selected per plan with
+// ptycho_plan_set_fft.
+template <int SG> struct F4Cfg { static constexpr int NT = 256, MINB = SG ? 2 : 3; };
+
+template <int SG> constexpr size_t f4_smem_bytes()
+{
+    return 128 + (SG ? sizeof(float2) * 4096 : 0) + sizeof(float) * 4096 + sizeof(float2) * (64 + 64 * 65) +
+           sizeof(float) * 8;
+}
+
+__device__ __forceinline__ int pos64(int f) { return 8 * (f & 7) + (f >> 3); }
+
+template <int SG>
+__global__ void __launch_bounds__(256, F4Cfg<SG>::MINB)
+    frame_update_f4_kernel(const FrameArgs sa, int n_items)
+{
+    constexpr int M = 64, P = 65, MM = 4096, NT = 256;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    float2 *stg_g = reinterpret_cast<float2 *>(smem + 128);
+    float *stg_f = reinterpret_cast<float *>(smem + 128 + (SG ? sizeof(float2) * MM : 0));
+    float2 *tw = reinterpret_cast<float2 *>(stg_f + MM);
+    float2 *buf = tw + M;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+
+    auto issue = [&](int j) {  // one thread: stage frame j's Gamma / sqrt f
+        const unsigned fbytes = (unsigned)(MM * sizeof(float));
+        const unsigned gbytes = SG ? (unsigned)(MM * sizeof(float2)) : 0u;
+        mbar_expect_tx(bar, fbytes + gbytes);
+        if (SG) bulk_g2s(stg_g, sa.gamma + (size_t)j * MM, gbytes, bar);
+        bulk_g2s(stg_f, sa.sqrtf_ + (size_t)j * MM, fbytes, bar);
+        if (sa.slot) bulk_prefetch_l2(sa.rank + (size_t)j * MM, (unsigned)MM);
+    };
+    auto prefetch_window = [&](int j) {  // all threads: frame j's exit-wave window into L2
+        constexpr int LINES = (M * 8 + 127) / 128 + 1;
+        for (int k = t; k < M * LINES; k += NT) {
+            const int row = k / LINES, l = k % LINES;
+            const char *rp = reinterpret_cast<const char *>(sa.u + sa.frame_base[j] + (size_t)row * sa.frame_pitch[j]);
+            prefetch_l2(rp + min(l * 128, M * 8 - 8));
+        }
+    };
+
+    if (t == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    for (int k = t; k < M; k += NT) tw[k] = sa.tw[k];
+    __syncthreads();
+    int j = blockIdx.x;
+    if (t == 0 && j < n_items) issue(j);
+    unsigned phase = 0;
+    const float inv_m = 1.f / (float)M;
+    for (; j < n_items; j += gridDim.x) {
+        if (j + (int)gridDim.x < n_items) prefetch_window(j + gridDim.x);
+        if (!SG && t == 0)
+            for (unsigned off = 0; off < (unsigned)(MM * sizeof(float2)); off += 16384u)
+                bulk_prefetch_l2(reinterpret_cast<const char *>(sa.gamma + (size_t)j * MM) + off, 16384u);
+        // ---- pass 1: exit wave, 4 x 4 block of radix-4 stages
+        const int c1 = t & 15, r1 = t >> 4;
+        uint2 rk[4];
+        if (sa.slot) {
+#pragma unroll
+            for (int c2 = 0; c2 < 4; ++c2)
+                rk[c2] = __ldg(reinterpret_cast<const uint2 *>(sa.rank + (size_t)j * MM +
+                                                               ((size_t)((r1 & 7) * M + c1 + 16 * c2)) * 8));
+        }
+        {
+            const float2 *w = sa.Wd ? sa.Wd + (size_t)sa.frame_sub[j] * MM : sa.w;
+            const float2 *uj = sa.u + sa.frame_base[j];
+            const int pitch = sa.frame_pitch[j];
+            float2 x[4][4];
+#pragma unroll
+            for (int r2 = 0; r2 < 4; ++r2)
+#pragma unroll
+                for (int c2 = 0; c2 < 4; ++c2) {
+                    const int row = r1 + 16 * r2, col = c1 + 16 * c2;
+                    x[r2][c2] = cmul(__ldg(w + row * M + col), __ldg(uj + (size_t)row * pitch + col));
+                }
+#pragma unroll
+            for (int c2 = 0; c2 < 4; ++c2) {
+                float2 v[4] = {x[0][c2], x[1][c2], x[2][c2], x[3][c2]};
+                dft<4, false>(v);
+#pragma unroll
+                for (int k1 = 0; k1 < 4; ++k1) x[k1][c2] = k1 ? cmul(v[k1], tw[r1 * k1]) : v[k1];
+            }
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) {
+                float2 v[4] = {x[k1][0], x[k1][1], x[k1][2], x[k1][3]};
+                dft<4, false>(v);
+#pragma unroll
+                for (int l1 = 0; l1 < 4; ++l1)
+                    buf[(16 * k1 + r1) * P + 16 * l1 + c1] = l1 ? cmul(v[l1], tw[c1 * l1]) : v[l1];
+            }
+        }
+        __syncthreads();
+        // ---- pass 2: column radix-16 over r1, in place
+        {
+            const int g = t & 63, k1 = t >> 6;
+            float2 z[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) z[i] = buf[(16 * k1 + i) * P + g];
+            dft<16, false>(z);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) buf[(16 * k1 + i) * P + g] = z[i];
+        }
+        const bool ok = mbar_wait_bounded(bar, phase);
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) *sa.err = 1;
+            return;
+        }
+        phase ^= 1u;
+        // ---- pass 3: row radix-16 over c1, prox and Gamma update, inverse row radix-16
+        float rf = 0.f;
+        {
+            const int rho = t & 63, k = (rho >> 4) + 4 * (rho & 15), l1 = t >> 6, pk = pos64(k);
+            float2 z[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) z[i] = buf[rho * P + 16 * l1 + i];
+            float2 gmv[SG ? 1 : 16];
+            if (!SG) {
+#pragma unroll
+                for (int l2 = 0; l2 < 16; ++l2)
+                    gmv[SG ? 0 : l2] = sa.gamma[(size_t)j * MM + pos64(l1 + 4 * l2) * M + pk];
+            }
+            dft<16, false>(z);
+#pragma unroll
+            for (int l2 = 0; l2 < 16; ++l2) {
+                const int li = pos64(l1 + 4 * l2) * M + pk;
+                const float2 ax = cscale(z[l2], inv_m);  // (A_d u_d^n)_k
+                const float sf = stg_f[li];
+                const float2 gm = SG ? stg_g[li] : gmv[SG ? 0 : l2];
+                const float a2 = ax.x * ax.x + ax.y * ax.y;
+                rf += fabsf((a2 > 0.f ? a2 * rsqrtf(a2) : 0.f) - sf);  // | |A_d u_d| - sqrt f |
+                const float2 y = cadd(gm, ax);                           // Gamma^n + A_d u_d^n
+                const float2 zz = stagm_prox(y, sf, sa.pc);              // eq. updateZ
+                const float2 gn = csub(y, zz);                           // eq. updateM-1-multi
+                sa.gamma[(size_t)j * MM + li] = gn;
+                z[l2] = csub(zz, gn);                                    // z^{n+1} - Gamma^{n+1}
+            }
+            dft<16, true>(z);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) buf[rho * P + 16 * l1 + i] = z[i];
+        }
+        __syncthreads();  // staging buffers are free: start the next frame's copies
+        if (t == 0 && j + (int)gridDim.x < n_items) {
+            fence_proxy_async_smem();
+            issue(j + gridDim.x);
+        }
+        // ---- pass 4: inverse column radix-16, in place
+        {
+            const int g = t & 63, k1 = t >> 6;
+            float2 z[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) z[i] = buf[(16 * k1 + i) * P + g];
+            dft<16, true>(z);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) buf[(16 * k1 + i) * P + g] = z[i];
+        }
+        __syncthreads();
+        // ---- pass 5: inverse radix-4 stages, residual out
+        {
+            float2 x[4][4];
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) {
+                float2 v[4];
+#pragma unroll
+                for (int l1 = 0; l1 < 4; ++l1) {
+                    const float2 b = buf[(16 * k1 + r1) * P + 16 * l1 + c1];
+                    v[l1] = l1 ? cmulc(b, tw[c1 * l1]) : b;
+                }
+                dft<4, true>(v);
+#pragma unroll
+                for (int c2 = 0; c2 < 4; ++c2) x[k1][c2] = k1 ? cmulc(v[c2], tw[r1 * k1]) : v[c2];
+            }
+#pragma unroll
+            for (int c2 = 0; c2 < 4; ++c2) {
+                float2 v[4] = {x[0][c2], x[1][c2], x[2][c2], x[3][c2]};
+                dft<4, true>(v);
+#pragma unroll
+                for (int r2 = 0; r2 < 4; ++r2) x[r2][c2] = v[r2];
+            }
+            if (sa.slot) {
+                // q_j = conj(w) o F^*(z - Gamma) into each pixel's gather slot
+                const unsigned base = (unsigned)sa.frame_base[j], pitch = (unsigned)sa.frame_pitch[j];
+#pragma unroll
+                for (int r2 = 0; r2 < 4; ++r2)
+#pragma unroll
+                    for (int c2 = 0; c2 < 4; ++c2) {
+                        const int row = r1 + 16 * r2, col = c1 + 16 * c2, b = (r1 >> 3) + 2 * r2;
+                        const unsigned word = b < 4 ? rk[c2].x : rk[c2].y;
+                        const unsigned rank = (word >> (8 * (b & 3))) & 0xffu;
+                        const float2 v = cmulc(cscale(x[r2][c2], inv_m), __ldg(sa.w + row * M + col));
+                        // 32-bit index: the plan checks slot_k * u_len < 2^32
+                        sa.slot[rank * (unsigned)sa.slot_stride + base + (unsigned)row * pitch + (unsigned)col] = v;
+                    }
+            } else {
+                // unweighted, natural order; the subdomain update weights with W_d^{n+1} (or w)
+                float2 *o = sa.q + (size_t)j * MM;
+#pragma unroll
+                for (int r2 = 0; r2 < 4; ++r2)
+#pragma unroll
+                    for (int c2 = 0; c2 < 4; ++c2) o[(r1 + 16 * r2) * M + c1 + 16 * c2] = cscale(x[r2][c2], inv_m);
+            }
+        }
+        // this frame's RF partial, one per warp (fixed xor tree inside the warp)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rf += __shfl_xor_sync(0xffffffffu, rf, o);
+        if (lane == 0) sa.rf_part[j * (NT / 32) + warp] = rf;
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- forward operator
 template <int M>
 __global__ void __launch_bounds__(Radix<M>::NT) forward_kernel(int J, const int32_t *base,
@@ -1074,9 +1302,51 @@ int launch_frame_update_table(int m, int variant, const FrameArgs *tab, const in
     return fail(PTYCHO_ERR_UNSUPPORTED, "table-driven frame update: m must be at most 128");
 }
 
+// The 16 x 4 split for m = 64 (fft kinds 1 and 2): blocks that fit per SM
+// (after raising the shared-memory limit once per device) and the launch.
+template <int SG>
+int f4_per_sm(int *per_sm_out, int *n_sm_out)
+{
+    static int per_sm[MAX_DEV] = {}, n_sm[MAX_DEV] = {};
+    int dev = 0;
+    OD2P_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEV) return fail(PTYCHO_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (!per_sm[dev]) {
+        OD2P_CUDA(cudaFuncSetAttribute(frame_update_f4_kernel<SG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)f4_smem_bytes<SG>()));
+        int a = 0, n = 0;
+        OD2P_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, frame_update_f4_kernel<SG>, F4Cfg<SG>::NT,
+                                                                f4_smem_bytes<SG>()));
+        if (a < 1) return fail(PTYCHO_ERR_UNSUPPORTED, "the 16 x 4 frame update does not fit on an SM");
+        per_sm[dev] = a;
+        n_sm[dev] = n;
+    }
+    *per_sm_out = per_sm[dev];
+    *n_sm_out = n_sm[dev];
+    return PTYCHO_OK;
+}
+
+int f4_grid(int kind, int J, int *grid)
+{
+    int per_sm = 0, n_sm = 0;
+    if (int rc = kind == 1 ? f4_per_sm<1>(&per_sm, &n_sm) : f4_per_sm<0>(&per_sm, &n_sm)) return rc;
+    *grid = std::max(1, std::min(J, per_sm * n_sm));
+    return PTYCHO_OK;
+}
+
 int launch_frame_update(ptycho_plan_s *p, cudaStream_t s)
 {
     if (p->M == 256) return frame_update_256(p, s);
+    if (p->fft_kind) {
+        if (p->fft_kind == 1)
+            frame_update_f4_kernel<1><<<p->n_k1_blocks, 256, f4_smem_bytes<1>(), s>>>(p->h_fargs[p->cur], p->J);
+        else
+            frame_update_f4_kernel<0><<<p->n_k1_blocks, 256, f4_smem_bytes<0>(), s>>>(p->h_fargs[p->cur], p->J);
+        OD2P_CUDA(cudaGetLastError());
+        return PTYCHO_OK;
+    }
     OD2P_K1_SHAPE(p->M, p->k1_variant, return frame_update_single_m<M_, V_>(p, s))
     switch (p->M) {
     default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");

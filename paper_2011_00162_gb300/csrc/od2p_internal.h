@@ -229,6 +229,7 @@ struct ptycho_plan_s {
     cudaGraphExec_t until[2] = {nullptr, nullptr};  // iterate-until loops, by starting parity
     int32_t *d_until = nullptr;                      // [done, cap, tol bits, last RF bits]
     bool cond_checked = false;                       // conditional-node self check passed
+    int32_t fft_kind = 0;                            // m = 64: 0 the 8 x 8 split, 1 / 2 the 16 x 4 split
     float2 *d_gamma_snap = nullptr;                  // Gamma snapshot (allocated on first use)
     // ---- every device allocation, freed by ptycho_plan_destroy
     std::vector<void *> owned;
@@ -238,6 +239,7 @@ namespace od2p {
 
 // fft_kernels.cu
 int launch_frame_update(ptycho_plan_s *p, cudaStream_t s);
+int f4_grid(int kind, int J, int *grid);
 int launch_forward(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out,
                    cudaStream_t s);
 int launch_frames_ifft_weight(const ptycho_plan_s *p, const float2 *frames, const float2 *w,

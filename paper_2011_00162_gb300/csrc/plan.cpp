@@ -335,6 +335,11 @@ void drop_graphs(cudaGraphExec_t g[2])
 // zeroes the RF partials when the partial-sum layout changes.
 int apply_launch(ptycho_plan_s *p, int variant, int blocks_per_sm, cudaStream_t s)
 {
+    if (p->fft_kind) {  // the 16 x 4 kernel has its own grid; the shape applies on return to kind 0
+        p->k1_variant = variant;
+        p->k1_blocks_per_sm = blocks_per_sm;
+        return PTYCHO_OK;
+    }
     if (p->M == 256) {
         if (variant != 0) return fail(PTYCHO_ERR_UNSUPPORTED, "m = 256 has one launch shape (variant 0)");
         p->k1_blocks_per_sm = 0;
@@ -901,6 +906,38 @@ int ptycho_probe_init(ptycho_plan_t *plan, ptycho_c32 *w0_dev, ptycho_stream_t s
 {
     if (!plan || !w0_dev) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
     return launch_probe_init(plan, reinterpret_cast<float2 *>(w0_dev), reinterpret_cast<cudaStream_t>(stream));
+}
+
+int ptycho_plan_set_fft(ptycho_plan_t *plan, int32_t kind, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (kind < 0 || kind > 2) return fail(PTYCHO_ERR_INVALID_ARG, "fft kind must be 0, 1 or 2");
+    if (kind && plan->M != 64) return fail(PTYCHO_ERR_UNSUPPORTED, "fft kinds 1 and 2 are for m = 64");
+    if (plan->batch_member) return fail(PTYCHO_ERR_STATE, "a batch member runs its batch's frame update");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (kind == plan->fft_kind) return PTYCHO_OK;
+    if (kind == 0) {
+        plan->fft_kind = 0;
+        plan->n_rf_parts = -1;  // forces the partials to be cleared
+        return apply_launch(plan, plan->k1_variant, plan->k1_blocks_per_sm, s);
+    }
+    int grid = 0;
+    if (int rc = f4_grid(kind, plan->J, &grid)) return rc;
+    const int cap = std::max(rf_parts(plan->M, plan->J, 0), rf_parts(plan->M, plan->J, 1));
+    OD2P_CUDA(cudaMemsetAsync(plan->d_rf_part, 0, sizeof(float) * cap, s));
+    plan->fft_kind = kind;
+    plan->n_k1_blocks = grid;
+    plan->n_rf_parts = plan->J * (256 / 32);
+    drop_graphs(plan->graph);
+    drop_graphs(plan->until);
+    return PTYCHO_OK;
+}
+
+int ptycho_plan_get_fft(const ptycho_plan_t *plan, int32_t *kind)
+{
+    if (!plan || !kind) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    *kind = plan->fft_kind;
+    return PTYCHO_OK;
 }
 
 int ptycho_plan_set_launch(ptycho_plan_t *plan, int32_t variant, int32_t blocks_per_sm, ptycho_stream_t stream)

@@ -170,3 +170,24 @@ def test_batch_launch_shapes_and_tuning(tmp_path):
         for a, b in zip(got, ref):
             for k in a:
                 assert torch.equal(a[k], b[k]), (variant, cap, tune, k)
+
+
+def test_tune_plan_times_the_transform_kinds_for_m64(tmp_path):
+    """For m = 64 the tuner also times the 16 x 4 transform kinds, applies the
+    fastest candidate and restores the state; fft=False keeps to shapes."""
+    path = str(tmp_path / "tune.json")
+    p = synth.Problem("t64", 256, 64, 16, 2, 2, 2, 16, 1e4, 1, eta=2.0, r=0.5, seed=8)
+    plan = _plan(p)
+    od.od2p_iterate(plan, 2)
+    before = _states(plan, False)
+    entry = autotune.tune_plan(plan, n_iter=3, warmup=1, path=path)
+    assert {"fft1", "fft2"} <= set(entry["trials"]) and entry["fft"] in (0, 1, 2)
+    assert od.ptycho_plan_get_fft(plan) == entry["fft"]
+    assert entry["us"] == min(entry["trials"].values())
+    for k, t in _states(plan, False).items():
+        assert torch.equal(t, before[k]), k
+    again = _plan(p)
+    hit = autotune.tune_plan(again, path=path)
+    assert hit["cached"] is True and od.ptycho_plan_get_fft(again) == entry["fft"]
+    shapes_only = autotune.tune_plan(_plan(p), n_iter=2, warmup=1, path=path, fft=False)
+    assert not any(k.startswith("fft") for k in shapes_only["trials"]) and shapes_only["fft"] == 0

@@ -681,3 +681,71 @@ def test_concurrent_plans_on_two_streams_and_threads():
     for i in range(2):
         for a, b in zip(seq[i], par[i]):
             assert np.array_equal(a, b), i
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_fft_16x4_frame_update_matches_oracle(kind):
+    """The 16 x 4 transform split for m = 64 (ptycho_plan_set_fft): one iteration
+    of the full 512^2 / 841-frame / 4x4 workload from a scrambled state, nonblind
+    (gather slots) and blind (frame-order residual), every array within the
+    one-iteration bar; its own iterates are deterministic and the graph equals
+    the stages."""
+    p = synth.grid_4x4()
+    offs, u_true, w, f = make_case(p)
+    plan, ref = pair_of(p, offs, w, f)
+    od.ptycho_plan_set_fft(plan, kind)
+    assert od.ptycho_plan_get_fft(plan) == kind
+    _scramble(plan, ref, 4)
+    for it in range(2):
+        od.od2p_iterate(plan, 1)
+        ref.iterate(1)
+        out = _compare_state(plan, ref, ONE_ITER_TOL)
+        record(f"config2_fft16x4_kind{kind}_{it}", **out)
+        for wg, wo in [(od.STATE_U, oracle.U), (od.STATE_GAMMA, oracle.GAMMA), (od.STATE_LAMBDA, oracle.LAMBDA)]:
+            od.od2p_set_state(plan, wg, c64(ref.get(wo)))
+    rf, _ = od.od2p_metrics(plan)
+    assert abs(rf - ref.metrics()[0]) < 1e-5 * ref.metrics()[0] + 1e-7
+    # determinism and graph == stages for this kind
+    outs = []
+    for mode in ("graph", "graph", "stages"):
+        a = od.ptycho_plan(geom_of(p, offs), f32(f))
+        od.ptycho_plan_set_fft(a, kind)
+        od.od2p_init(a, c64(w))
+        for _ in range(3):
+            if mode == "graph":
+                od.od2p_iterate(a, 1)
+            else:
+                od.od2p_frame_update(a)
+                od.od2p_subdomain_update(a)
+        outs.append([host(od.od2p_get_state(a, k)) for k in (od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA)])
+        a.close()
+    for x, y in zip(outs[0], outs[1]):
+        assert np.array_equal(x, y)
+    for x, y in zip(outs[0], outs[2]):
+        assert np.array_equal(x, y)
+    # blind: the unweighted residual in frame order
+    q = synth.Problem("b64", 256, 64, 16, 1, 2, 2, 8, 1e5, 1, eta=0.3, r=0.2, blind=True, mu=2.0, gamma=0.1,
+                      seed=21)
+    offs, u_true, w_true, f = make_case(q)
+    w0 = synth.gaussian_probe(q.m)
+    bp = od.ptycho_plan(geom_of(q, offs), f32(f))
+    od.ptycho_plan_set_fft(bp, kind)
+    od.od2p_init(bp, c64(w0))
+    bref = oracle.ADMM(f, w0, offs, q.n, q.n, q.sub_rows, q.sub_cols, q.overlap_px, q.eps, q.eta, q.r,
+                       blind=True, mu=q.mu, gamma=q.gamma)
+    _scramble(bp, bref, 8, blind=True)
+    od.od2p_iterate(bp, 1)
+    bref.iterate(1)
+    _compare_state(bp, bref, ONE_ITER_TOL, blind=True)
+
+
+def test_fft_kind_arguments():
+    p = synth.small_2sub()  # m = 16
+    offs, u_true, w, f = make_case(p)
+    plan = od.ptycho_plan(geom_of(p, offs), f32(f))
+    with pytest.raises(RuntimeError):
+        od.ptycho_plan_set_fft(plan, 1)
+    with pytest.raises(RuntimeError):
+        od.ptycho_plan_set_fft(plan, 3)
+    od.ptycho_plan_set_fft(plan, 0)
+    assert od.ptycho_plan_get_fft(plan) == 0

@@ -58,6 +58,8 @@ def test_abi_version_and_argument_errors(lib):
     assert lib.ptycho_peak_probe(2, 1, 1, None, None) == _lib.ERR_INVALID_ARG
     assert lib.od2p_iterate_until(None, 1e-5, 10, None, None, None) == _lib.ERR_INVALID_ARG
     assert lib.od2p_gamma_snapshot(None, None) == _lib.ERR_INVALID_ARG
+    assert lib.ptycho_plan_set_fft(None, 0, None) == _lib.ERR_INVALID_ARG
+    assert lib.ptycho_plan_get_fft(None, None) == _lib.ERR_INVALID_ARG
     assert lib.od2p_frame_residual(None, None, None) == _lib.ERR_INVALID_ARG
     assert lib.ptycho_plan_get_launch(None, None, None, None) == _lib.ERR_INVALID_ARG
     assert lib.ptycho_batch_set_launch(None, 0, 0, None) == _lib.ERR_INVALID_ARG

@@ -623,12 +623,14 @@ def run_table1(args):
     for D in (1, 2, 4, 6, 8, 10):
         p = dataclasses.replace(base, sub_cols=D)
         line = {"workload": f"table1_od2p_512px_m64_841frames_1x{D}stripes_noiseless", "frames": len(offs),
-                "subdomains": D, "eta": eta, "r": r, "stop": "RF <= 1e-5 or 1000 iterations",
+                "subdomains": D, "eta": eta, "r": r, "fft": args.fft, "stop": "RF <= 1e-5 or 1000 iterations",
                 "check_every": args.check}
         for mode in ("fixed", "balanced_r", "balanced_r_eta", "in_K"):
             t_plan = time.perf_counter()
             plan = od.ptycho_plan(od.Geometry(p.n, p.n, p.m, offs, 1, D, p.overlap_px, p.eps, eta, r), f)
             od.od2p_init(plan, w_dev)
+            if args.fft:
+                od.ptycho_plan_set_fft(plan, args.fft)
             torch.cuda.synchronize()
             t_plan = time.perf_counter() - t_plan
             if mode == "in_K":  # Lemma 2.4's sufficient (r, eta) from the plan's operator norms
@@ -837,6 +839,8 @@ def main():
     ap.add_argument("--eta", type=float, default=0.1, help="with --table1")
     ap.add_argument("--r", type=float, default=4e3, help="with --table1")
     ap.add_argument("--check", type=int, default=10, help="with --table1: iterations between RF checks")
+    ap.add_argument("--fft", type=int, default=0, choices=(0, 1, 2),
+                    help="with --table1: transform split of the m = 64 frame update (ptycho_plan_set_fft)")
     ap.add_argument("--table1-oracle", default="1",
                     help="with --table1: comma-separated D for which the FP64 oracle runs the same stopping rule")
     args = ap.parse_args()

@@ -354,6 +354,38 @@ def test_step3_u_is_least_squares_minimiser(grid):
         np.testing.assert_allclose(un[u_off[d]:u_off[d + 1]], sol, atol=1e-10)
 
 
+def test_one_subdomain_is_the_whole_domain_iteration():
+    """With one subdomain there are no overlap pairs: the consensus penalty r drops
+    out (iterates identical for any r) and one iteration is the ADMM of the
+    undecomposed problem -- z = Prox(Gamma + A u), Gamma += A u - z,
+    u = A^*(z - Gamma) / diag(A^* A) -- written with the oracle's operators."""
+    H = W = 14
+    m = 4
+    u, w, offs, f = _tiny_problem(noiseless=False, seed=2)
+    eta, eps = 0.4, 0.5
+    runs = []
+    for r in (0.05, 4e3):
+        a = oracle.ADMM(f, w, offs, H, W, 1, 1, 0, eps, eta, r)
+        a.iterate(3)
+        runs.append([a.get(k) for k in (oracle.U, oracle.GAMMA)])
+    for x, y in zip(*runs):
+        assert np.array_equal(x, y)
+    a = oracle.ADMM(f, w, offs, H, W, 1, 1, 0, eps, eta, 1.0)
+    a.iterate(2)
+    u_n, g_n = a.get(oracle.U).reshape(H, W), a.get(oracle.GAMMA).reshape(-1, m, m)
+    a.iterate(1)
+    Au = oracle.forward(u_n, w, offs)
+    y = g_n + Au
+    z = oracle.stagm_prox(y.reshape(-1), f.reshape(-1), eps, eta).reshape(y.shape)
+    g1 = y - z
+    illum = np.zeros((H, W))
+    for r0, c0 in offs:
+        illum[r0:r0 + m, c0:c0 + m] += np.abs(w) ** 2
+    u1 = oracle.adjoint(z - g1, w, offs, H, W) / illum
+    np.testing.assert_allclose(a.get(oracle.GAMMA).reshape(g1.shape), g1, atol=1e-12)
+    np.testing.assert_allclose(a.get(oracle.U).reshape(H, W), u1, atol=1e-10)
+
+
 def test_step1_step2_optimality_conditions():
     """eq. (Stationary1): grad G(z^{n+1}) = eta Gamma^{n+1} and v^{n+1} averages pi u^n + Lambda^n;
     eq. (updateM-2): Lambda^{n+1} = Lambda^n + pi u^{n+1} - v^{n+1}."""

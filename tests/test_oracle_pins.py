@@ -789,3 +789,77 @@ def test_snr_definition():
     d -= np.vdot(ug, d) / np.vdot(ug, ug) * ug   # orthogonal to ug: no phase to remove
     d *= 0.01 * np.linalg.norm(ug) / np.linalg.norm(d)
     assert abs(oracle.snr(ug + d, ug) - (40.0 + 10 * np.log10(1.0001))) < 1e-6
+
+
+# ----------------------------------------------------------------------------- RF and RE
+def _metrics_case(blind):
+    """A noisy 2 x 2 problem run a few iterations, so that RF, RE and the
+    multipliers are all away from their trivial values."""
+    p = synth.Problem("rfre", 96, 16, 6, 1, 2, 2, 8, 1e3, 1, eta=2.0, r=0.5, seed=9)
+    offs = p.offsets()
+    u, w = p.truth(), p.probe()
+    f = synth.poissonize(np.abs(oracle.forward(u, w, offs)) ** 2, p.peak, 4).astype(np.float64)
+    w0 = w if not blind else synth.gaussian_probe(p.m)
+    a = oracle.ADMM(f, w0, offs, p.n, p.n, 2, 2, 8, 0.5, 2.0, 0.5, blind=blind, mu=1.0,
+                    gamma=0.1 if blind else 0.0)
+    a.iterate(3)
+    fs, rect = oracle.geometry(p.n, p.n, p.m, offs, 2, 2, 8)
+    return a, f, offs, fs, rect, p.m
+
+
+def _split_u(u, rect):
+    out, k = [], 0
+    for r0, c0, r1, c1 in rect:
+        n = (r1 - r0) * (c1 - c0)
+        out.append(u[k:k + n].reshape(r1 - r0, c1 - c0))
+        k += n
+    return out
+
+
+def _rf_numpy(ud, Wd, f, offs, fs, rect, m, norm="sqrt"):
+    """Section 4's RF written with numpy: sum_j || |F(W o S_j u_d)| - sqrt f_j ||_1
+    over sum_j || sqrt f_j ||_1 (norm="sqrt"); norm="f" is the wrong normaliser."""
+    num = 0.0
+    for j, (r0, c0) in enumerate(offs):
+        d = fs[j]
+        R0, C0 = rect[d][0], rect[d][1]
+        psi = Wd[d] * ud[d][r0 - R0:r0 - R0 + m, c0 - C0:c0 - C0 + m]
+        num += np.abs(np.abs(np.fft.fft2(psi, norm="ortho")) - np.sqrt(f[j])).sum()
+    return num / (np.sqrt(f).sum() if norm == "sqrt" else f.sum())
+
+
+def _re_numpy(u_old, u_new, by="new"):
+    """RE = max_d ||u_d^{n+1} - u_d^n|| / ||u_d^{n+1}|| (by="old" is the wrong norm)."""
+    return max(np.linalg.norm(b - a) / np.linalg.norm(b if by == "new" else a)
+               for a, b in zip(u_old, u_new))
+
+
+@pytest.mark.parametrize("blind", [False, True])
+def test_rf_re_match_their_definitions(blind):
+    """The oracle's RF (of the iterate entering the iteration, blind: with the
+    subdomain probes W_d^n of Step 1) and RE (relative to u^{n+1}) of section 4,
+    recomputed with numpy from the state captured around one iteration.  The
+    plausible misreadings -- Sigma f as the normaliser, RF of u^{n+1}, RE against
+    ||u^n|| -- differ from both by far more than the tolerance."""
+    a, f, offs, fs, rect, m = _metrics_case(blind)
+    D = len(rect)
+    u_old = _split_u(a.get(oracle.U).copy(), rect)
+    Wd = (a.get(oracle.WD).reshape(D, m, m).copy() if blind
+          else np.broadcast_to(a.get(oracle.W).reshape(m, m), (D, m, m)))
+    a.iterate(1)
+    rf, re = a.metrics()
+    u_new = _split_u(a.get(oracle.U).copy(), rect)
+    rf_np = _rf_numpy(u_old, Wd, f, offs, fs, rect, m)
+    re_np = _re_numpy(u_old, u_new)
+    assert abs(rf - rf_np) <= 1e-12 * rf_np, (rf, rf_np)
+    assert abs(re - re_np) <= 1e-12 * re_np, (re, re_np)
+    # the misreadings are told apart
+    wrong = {
+        "sum f normaliser": _rf_numpy(u_old, Wd, f, offs, fs, rect, m, norm="f"),
+        "RF of u^{n+1}": _rf_numpy(u_new, Wd if not blind else a.get(oracle.WD).reshape(D, m, m),
+                                   f, offs, fs, rect, m),
+    }
+    for name, v in wrong.items():
+        assert abs(v - rf) > 1e-6 * rf, name
+    assert abs(_re_numpy(u_old, u_new, by="old") - re) > 1e-6 * re
+    assert rf > 1e-3 and re > 1e-4

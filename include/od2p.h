@@ -248,10 +248,17 @@ int od2p_merge(const ptycho_plan_t *plan, ptycho_c32 *u_out_dev, ptycho_stream_t
 /*
  * Stopping metrics of section 4 from the last iteration, reduced in a fixed
  * order: RF of the iterate that entered it (sum |(|A_d u_d| - sqrt f)| /
- * sum sqrt f) and RE = max_d ||u_d^{n+1} - u_d^n|| / ||u_d^{n+1}||.  Writes
- * host scalars and synchronises `stream`.  Either output may be NULL.
+ * sum sqrt f; blind: with W_d^n in place of w) and RE = max_d ||u_d^{n+1} -
+ * u_d^n|| / ||u_d^{n+1}||.  loss: the ST-AGM data term of the current iterate
+ * (eq. STAGM summed over frames, G_eps(B_d(W_d, u_d)); f_j), each frame taken
+ * from its own subdomain copy u_d and probe (w, or W_d when blind): one extra
+ * pass over the frames, made only when loss_host is not NULL; it uses the
+ * loss scratch of stagm_loss_grad and leaves every state array unchanged.
+ * Writes host scalars and synchronises `stream`.  Any output may be NULL.
+ * Errors: INVALID_ARG, STATE (loss before od2p_init), TIMEOUT (a bounded wait
+ * of an earlier frame update gave up), CUDA.
  */
-int od2p_metrics(ptycho_plan_t *plan, float *rf_host, float *re_host, ptycho_stream_t stream);
+int od2p_metrics(ptycho_plan_t *plan, float *rf_host, float *re_host, float *loss_host, ptycho_stream_t stream);
 
 /*
  * Penalty changes between iterations (the paper fixes eta and r for a run and
@@ -443,7 +450,9 @@ int ptycho_batch_get_launch(const ptycho_batch_t *batch, int32_t *variant, int32
  *
  * u_dev: img_h x img_w; w_dev: m x m (m in {16, 32, 64, 128});
  * offsets_dev: device int32, n_frames x 2 top-left (row, col), each window
- * inside the image (not checked on the host: they are device memory);
+ * inside the image.  They are device memory, so the host cannot check them;
+ * the kernel does: a frame whose window leaves the image is not read, and the
+ * call then writes NaN to loss_dev;
  * f_dev: n_frames x m x m, natural frequency order; loss_dev: 1 float, written.
  * It allocates nothing.  Its only scratch is a fixed array of 65536 floats
  * (256 KiB) compiled into the library, which every GPU that loads the library

@@ -54,7 +54,7 @@ SIGNATURES = {
     "od2p_subdomain_update": (ctypes.c_int, [_P, _P]),
     "probe_update": (ctypes.c_int, [_P, _P]),
     "od2p_merge": (ctypes.c_int, [_P, _P, _P]),
-    "od2p_metrics": (ctypes.c_int, [_P, _P, _P, _P]),
+    "od2p_metrics": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "od2p_state_len": (ctypes.c_int, [_P, _I32, _P]),
     "od2p_get_state": (ctypes.c_int, [_P, _I32, _P, _P]),
     "od2p_set_state": (ctypes.c_int, [_P, _I32, _P, _P]),

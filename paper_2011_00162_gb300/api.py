@@ -399,10 +399,13 @@ def od2p_merge(plan: Plan, out: torch.Tensor | None = None, stream=None) -> torc
     return out
 
 
-def od2p_metrics(plan: Plan, stream=None) -> tuple[float, float]:
-    rf, re = ctypes.c_float(), ctypes.c_float()
-    check(plan._lib.od2p_metrics(plan.handle, ctypes.byref(rf), ctypes.byref(re), _stream(stream)))
-    return rf.value, re.value
+def od2p_metrics(plan: Plan, stream=None, loss: bool = False):
+    """(RF, RE) of the last iteration; with loss=True also the ST-AGM loss of
+    the current subdomain iterate: (RF, RE, loss)."""
+    rf, re, ls = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    check(plan._lib.od2p_metrics(plan.handle, ctypes.byref(rf), ctypes.byref(re),
+                                 ctypes.byref(ls) if loss else None, _stream(stream)))
+    return (rf.value, re.value, ls.value) if loss else (rf.value, re.value)
 
 
 def od2p_state_len(plan: Plan, which: int) -> int:

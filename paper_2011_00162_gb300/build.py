@@ -38,20 +38,17 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, out: str | None = None,
-          defines: tuple[str, ...] = ()) -> str:
-    """Compile and link; `out`/`defines` build a variant elsewhere (launch-shape sweeps)."""
-    lib_path = out or LIB
-    if not force and out is None and not _stale():
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile and link libod2p.so (skipped when it is newer than its sources)."""
+    lib_path = LIB
+    if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     flags = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
-    flags += [f"-D{d}" for d in defines]
-    tag = "" if out is None else "_" + "_".join(defines).replace("=", "")
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src + tag + ".o")
+        obj = os.path.join(BUILD, src + ".o")
         cmd = [cc] + flags + ARCH + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)

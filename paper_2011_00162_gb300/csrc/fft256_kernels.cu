@@ -468,6 +468,19 @@ int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s)
     return run_waves(P, p->J, WAVE_256, s);
 }
 
+int loss_256_sub(ptycho_plan_s *p, cudaStream_t s)
+{
+    Pipeline P = base_pipeline(p);
+    P.do_a = true;
+    P.do_c = false;
+    P.A.u = p->d_u[p->cur];
+    P.A.w = p->d_w;
+    P.A.Wd = p->blind ? p->d_Wd : nullptr;
+    P.B.mode = B_LOSS;
+    P.B.part = p->d_loss_part;
+    return run_waves(P, p->J, WAVE_256, s);
+}
+
 int probe_avg_256(ptycho_plan_s *p, cudaStream_t s)
 {
     const float invD = 1.f / (float)p->D;

@@ -825,10 +825,14 @@ __global__ void __launch_bounds__(Radix<M>::NT) ifft_weight_kernel(int J, const 
 
 // ---------------------------------------------------------------- loss frames
 // h_j = F^* grad g(F(w o S_j u); f_j) (unweighted) and per-block loss partials.
+// The exit wave reads the window at u + base[j] with row pitch `pitch`, or
+// pitch_arr[j] when given (subdomain copies u_d), and the probe w, or
+// Wd + frame_sub[j] * m^2 when Wd is given (blind subdomain probes).  With
+// h = null only the loss partials are formed.
 struct LossArgs {
     int32_t J, pitch;
-    const int32_t *base;
-    const float2 *u, *w;
+    const int32_t *base, *pitch_arr, *frame_sub;
+    const float2 *u, *w, *Wd;
     const float *sqrtf_;
     float2 *h;
     float *loss_part;
@@ -857,11 +861,13 @@ __global__ void __launch_bounds__(Radix<M>::NT) loss_kernel(LossArgs a)
         const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
         if (j >= a.J) continue;
         const float2 *uj = a.u + a.base[j];
+        const int pitch = a.pitch_arr ? a.pitch_arr[j] : a.pitch;
+        const float2 *wj = a.Wd ? a.Wd + (size_t)a.frame_sub[j] * MM : a.w;
         float2 x[R1];
 #pragma unroll
         for (int t = 0; t < R1; ++t) {
             const int row = n1 + R2 * t;
-            x[t] = cmul(__ldg(a.w + row * M + c), __ldg(uj + (size_t)row * a.pitch + c));
+            x[t] = cmul(__ldg(wj + row * M + c), __ldg(uj + (size_t)row * pitch + c));
         }
         dft<R1, false>(x);
         float2 *fb = buf + f * M * P;
@@ -876,6 +882,7 @@ __global__ void __launch_bounds__(Radix<M>::NT) loss_kernel(LossArgs a)
     float loss = 0.f;
     const float inv_m = 1.f / (float)M;
     const float eps = a.eps;
+    const bool with_h = a.h != nullptr;  // the same for the whole block
     for (int task = threadIdx.x; task < FPB * M * R1; task += NT) {
         const int r = task % M, rest = task / M, s = rest % R1, f = rest / R1, j = j0 + f;
         if (j >= a.J) continue;
@@ -904,16 +911,20 @@ __global__ void __launch_bounds__(Radix<M>::NT) loss_kernel(LossArgs a)
             loss += gv;
             x[t] = cscale(xv, gs);
         }
-        dft<R2, true>(x);
+        if (with_h) {
+            dft<R2, true>(x);
 #pragma unroll
-        for (int t = 0; t < R2; ++t) fb[R2 * s + t] = x[t];
+            for (int t = 0; t < R2; ++t) fb[R2 * s + t] = x[t];
+        }
     }
-    __syncthreads();
-    row_stage1<M, true>(buf, tw);
-    __syncthreads();
-    col_stage2<M, true>(buf);
-    __syncthreads();
-    col_stage1_store<M>(buf, tw, j0, a.J, a.h, inv_m, nullptr);
+    if (with_h) {
+        __syncthreads();
+        row_stage1<M, true>(buf, tw);
+        __syncthreads();
+        col_stage2<M, true>(buf);
+        __syncthreads();
+        col_stage1_store<M>(buf, tw, j0, a.J, a.h, inv_m, nullptr);
+    }
     const float tot = block_sum_fixed(loss, red);
     if (threadIdx.x == 0) a.loss_part[blockIdx.x] = tot;
 }
@@ -1118,18 +1129,24 @@ int ifft_m(const ptycho_plan_s *p, const float2 *in, const float2 *w, float2 *ou
     return PTYCHO_OK;
 }
 
+// subdomain = false: windows of the full image u (img_w pitch), probe w, and
+// h_j to the plan's frame scratch; true: the plan's current subdomain copies
+// u_d with their probes (W_d when blind), loss partials only.
 template <int M>
-int loss_m(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s)
+int loss_m(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, bool subdomain = false)
 {
     if (int rc = set_smem<M>(loss_kernel<M>)) return rc;
     LossArgs a;
     a.J = p->J;
     a.pitch = p->W;
-    a.base = p->d_img_base;
+    a.base = subdomain ? p->d_frame_base : p->d_img_base;
+    a.pitch_arr = subdomain ? p->d_frame_pitch : nullptr;
+    a.frame_sub = p->d_frame_sub;
     a.u = u;
     a.w = w;
+    a.Wd = subdomain && p->blind ? p->d_Wd : nullptr;
     a.sqrtf_ = p->d_sqrtf;
-    a.h = p->d_q;
+    a.h = subdomain ? nullptr : p->d_q;
     a.loss_part = p->d_loss_part;
     a.tw = p->d_tw;
     a.eps = p->eps;
@@ -1402,6 +1419,22 @@ int launch_loss_frames(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaS
     }
 }
 
+int launch_metrics_loss(ptycho_plan_s *p, cudaStream_t s)
+{
+    const float2 *u = p->d_u[p->cur];
+    switch (p->M) {
+    case 16: return loss_m<16>(p, u, p->d_w, s, true);
+    case 32: return loss_m<32>(p, u, p->d_w, s, true);
+    case 64: return loss_m<64>(p, u, p->d_w, s, true);
+    case 128: return loss_m<128>(p, u, p->d_w, s, true);
+    case 48: return loss_m<48>(p, u, p->d_w, s, true);
+    case 80: return loss_m<80>(p, u, p->d_w, s, true);
+    case 96: return loss_m<96>(p, u, p->d_w, s, true);
+    case 256: return loss_256_sub(p, s);
+    default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
+    }
+}
+
 int launch_probe_avg(ptycho_plan_s *p, cudaStream_t s)
 {
     switch (p->M) {
@@ -1470,7 +1503,7 @@ bool g_noalloc_attr[NOALLOC_MAX_DEVICES][4] = {};  // shared-memory limit raised
 std::mutex g_noalloc_mu;
 
 struct NoallocArgs {
-    int32_t J, W;
+    int32_t J, H, W;
     const int32_t *offs;
     const float2 *u, *w;
     const float *f;  // natural frequency order
@@ -1487,7 +1520,9 @@ __global__ void __launch_bounds__(Radix<M>::NT) loss_noalloc_kernel(NoallocArgs 
     float2 *tw = reinterpret_cast<float2 *>(smem4);
     float2 *buf = tw + M;
     float *red = reinterpret_cast<float *>(buf + FPB * M * P);
+    __shared__ int bad_window;
     const int j0 = blockIdx.x * FPB;
+    if (threadIdx.x == 0) bad_window = 0;
     // twiddles exp(-2 pi i k / M) from the exact single-precision routine
     for (int k = threadIdx.x; k < M; k += NT) {
         float sn, cs;
@@ -1498,12 +1533,20 @@ __global__ void __launch_bounds__(Radix<M>::NT) loss_noalloc_kernel(NoallocArgs 
     for (int task = threadIdx.x; task < FPB * M * R2; task += NT) {
         const int c = task % M, rest = task / M, n1 = rest % R2, f = rest / R2, j = j0 + f;
         if (j >= a.J) continue;
-        const float2 *uj = a.u + (size_t)a.offs[2 * j] * a.W + a.offs[2 * j + 1];
+        const int r0 = __ldg(a.offs + 2 * j), c0 = __ldg(a.offs + 2 * j + 1);
         float2 x[R1];
+        if (r0 < 0 || c0 < 0 || r0 > a.H - M || c0 > a.W - M) {
+            // a window outside the image: no load, and the block's partial becomes NaN
+            bad_window = 1;
 #pragma unroll
-        for (int t = 0; t < R1; ++t) {
-            const int row = n1 + R2 * t;
-            x[t] = cmul(__ldg(a.w + row * M + c), __ldg(uj + (size_t)row * a.W + c));
+            for (int t = 0; t < R1; ++t) x[t] = make_float2(0.f, 0.f);
+        } else {
+            const float2 *uj = a.u + (size_t)r0 * a.W + c0;
+#pragma unroll
+            for (int t = 0; t < R1; ++t) {
+                const int row = n1 + R2 * t;
+                x[t] = cmul(__ldg(a.w + row * M + c), __ldg(uj + (size_t)row * a.W + c));
+            }
         }
         dft<R1, false>(x);
         float2 *fb = buf + f * M * P;
@@ -1537,7 +1580,7 @@ __global__ void __launch_bounds__(Radix<M>::NT) loss_noalloc_kernel(NoallocArgs 
         }
     }
     const float tot = block_sum_fixed(loss, red);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = tot;
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = bad_window ? __int_as_float(0x7fc00000) : tot;
 }
 
 // Sum of the n partials in a fixed order: each thread a contiguous run, then warps in order.
@@ -1558,12 +1601,19 @@ __global__ void __launch_bounds__(256) noalloc_sum_kernel(int n, const float *pa
     }
 }
 
+// Raises the kernel's dynamic shared-memory limit on the current device; the
+// caller holds g_noalloc_mu and records success only after this returns OK.
 template <int M>
-int loss_noalloc_m(const NoallocArgs &base, float *loss, cudaStream_t s, bool setup)
+int noalloc_setup_m()
 {
-    if (setup)
-        OD2P_CUDA(cudaFuncSetAttribute(loss_noalloc_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<M>()));
+    OD2P_CUDA(cudaFuncSetAttribute(loss_noalloc_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem_bytes<M>()));
+    return PTYCHO_OK;
+}
+
+template <int M>
+int loss_noalloc_m(const NoallocArgs &base, float *loss, cudaStream_t s)
+{
     const int blocks = (base.J + Radix<M>::FPB - 1) / Radix<M>::FPB;
     if (blocks > NOALLOC_MAX_BLOCKS)
         return fail(PTYCHO_ERR_INVALID_ARG,
@@ -1594,21 +1644,28 @@ extern "C" int stagm_loss_noalloc(const ptycho_c32 *u, int32_t img_h, int32_t im
     OD2P_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(PTYCHO_ERR_UNSUPPORTED, "device index out of range");
     const int mi = m == 16 ? 0 : m == 32 ? 1 : m == 64 ? 2 : 3;
-    bool setup = false;
     float *scratch;
     {
+        // per-device, per-m set-up under the lock; a flag is set only once its
+        // step has succeeded, so a failed step is retried by the next call and no
+        // thread launches before the shared-memory limit has been raised
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
         if (!g_noalloc_ptr[dev]) {
             void *ptr = nullptr;
             OD2P_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_partials));
             g_noalloc_ptr[dev] = static_cast<float *>(ptr);
         }
+        if (!g_noalloc_attr[dev][mi]) {
+            const int rc = m == 16 ? noalloc_setup_m<16>() : m == 32 ? noalloc_setup_m<32>()
+                         : m == 64 ? noalloc_setup_m<64>() : noalloc_setup_m<128>();
+            if (rc != PTYCHO_OK) return rc;
+            g_noalloc_attr[dev][mi] = true;
+        }
         scratch = g_noalloc_ptr[dev];
-        setup = !g_noalloc_attr[dev][mi];
-        g_noalloc_attr[dev][mi] = true;
     }
     NoallocArgs a;
     a.J = n_frames;
+    a.H = img_h;
     a.W = img_w;
     a.offs = offsets_dev;
     a.u = reinterpret_cast<const float2 *>(u);
@@ -1618,9 +1675,9 @@ extern "C" int stagm_loss_noalloc(const ptycho_c32 *u, int32_t img_h, int32_t im
     a.eps = eps;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     switch (m) {
-    case 16: return loss_noalloc_m<16>(a, loss, s, setup);
-    case 32: return loss_noalloc_m<32>(a, loss, s, setup);
-    case 64: return loss_noalloc_m<64>(a, loss, s, setup);
-    default: return loss_noalloc_m<128>(a, loss, s, setup);
+    case 16: return loss_noalloc_m<16>(a, loss, s);
+    case 32: return loss_noalloc_m<32>(a, loss, s);
+    case 64: return loss_noalloc_m<64>(a, loss, s);
+    default: return loss_noalloc_m<128>(a, loss, s);
     }
 }

@@ -205,7 +205,7 @@ struct ptycho_plan_s {
     float *d_rf_part = nullptr;        // one per frame-kernel block
     float *d_re_part = nullptr;        // 2 per subdomain tile
     float *d_loss_part = nullptr;
-    double *d_metrics = nullptr;       // [rf, re, sum sqrt f, consensus residual]
+    double *d_metrics = nullptr;       // [rf, re, sum sqrt f, consensus residual, loss (float)]
     float *d_rc_part = nullptr;        // (P + 1) x 64 partial sums of the consensus residual
     float *d_snr_part = nullptr;       // 2 x 608 partial sums of the SNR passes
     double *d_snr = nullptr;           // [cos theta, sin theta, SNR dB]
@@ -245,6 +245,8 @@ int launch_forward(const ptycho_plan_s *p, const float2 *u, const float2 *w, flo
 int launch_frames_ifft_weight(const ptycho_plan_s *p, const float2 *frames, const float2 *w,
                               bool ifft, float2 *out, cudaStream_t s);
 int launch_loss_frames(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s);
+// ST-AGM loss partials of the current subdomain iterate (u_d, and W_d when blind)
+int launch_metrics_loss(ptycho_plan_s *p, cudaStream_t s);
 int launch_probe_avg(ptycho_plan_s *p, cudaStream_t s);
 int launch_ingest_f(ptycho_plan_s *p, const float *f, cudaStream_t s);
 int launch_permute_gamma(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_natural,
@@ -264,6 +266,7 @@ int frame_update_256(ptycho_plan_s *p, cudaStream_t s);
 int forward_256(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out, cudaStream_t s);
 int ifft_256(const ptycho_plan_s *p, const float2 *in, float2 *out, cudaStream_t s);
 int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s);
+int loss_256_sub(ptycho_plan_s *p, cudaStream_t s);
 int probe_avg_256(ptycho_plan_s *p, cudaStream_t s);
 int ingest_256(ptycho_plan_s *p, const float *f, float *part, cudaStream_t s);
 int permute_256(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_natural, cudaStream_t s);

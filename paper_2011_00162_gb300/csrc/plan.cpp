@@ -371,7 +371,7 @@ extern "C" {
 
 const char *ptycho_last_error(void) { return od2p::g_err.c_str(); }
 
-int32_t ptycho_abi_version(void) { return 1; }
+int32_t ptycho_abi_version(void) { return 2; }
 
 int ptycho_release_cached_memory(void)
 {
@@ -580,7 +580,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
         (rc = dev_alloc(&p->d_rf_part, rf_cap, own, s)) ||
         (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own, s)) ||
         (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own, s)) ||
-        (rc = dev_alloc(&p->d_metrics, 4, own, s)) || (rc = dev_alloc(&p->d_err, 1, own, s)) ||
+        (rc = dev_alloc(&p->d_metrics, 5, own, s)) || (rc = dev_alloc(&p->d_err, 1, own, s)) ||
         (rc = dev_alloc(&p->d_rc_part, (size_t)(p->P + 1) * 64, own, s)) ||
         (rc = dev_alloc(&p->d_snr_part, 2 * 152 * 4, own, s)) || (rc = dev_alloc(&p->d_snr, 3, own, s)) ||
         (rc = dev_alloc(&p->d_opn, 2, own, s)) || (rc = dev_alloc(&p->d_until, 4, own, s)))
@@ -611,7 +611,7 @@ int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_de
             return bail(rc);
     }
     cudaError_t e;
-    if ((e = cudaMemsetAsync(p->d_metrics, 0, 4 * sizeof(double), s)) != cudaSuccess ||
+    if ((e = cudaMemsetAsync(p->d_metrics, 0, 5 * sizeof(double), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * rf_cap, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_re_part, 0, sizeof(float) * 2 * p->sub_tiles.n_tiles, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->d_w, 0, sizeof(float2) * p->MM, s)) != cudaSuccess ||
@@ -789,19 +789,28 @@ int od2p_merge(const ptycho_plan_t *plan, ptycho_c32 *u_out, ptycho_stream_t str
     return launch_merge(plan, reinterpret_cast<float2 *>(u_out), reinterpret_cast<cudaStream_t>(stream));
 }
 
-int od2p_metrics(ptycho_plan_t *plan, float *rf, float *re, ptycho_stream_t stream)
+int od2p_metrics(ptycho_plan_t *plan, float *rf, float *re, float *loss, ptycho_stream_t stream)
 {
     if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (loss && !plan->initialised) return fail(PTYCHO_ERR_STATE, "the loss needs od2p_init first");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (int rc = launch_metrics(plan, s)) return rc;
+    float *d_loss = reinterpret_cast<float *>(plan->d_metrics + 4);
+    if (loss) {
+        if (int rc = launch_metrics_loss(plan, s)) return rc;
+        if (int rc = launch_loss_reduce(plan, d_loss, s)) return rc;
+    }
     double h[2];
+    float hl = 0.f;
     int32_t err = 0;
     OD2P_CUDA(cudaMemcpyAsync(h, plan->d_metrics, sizeof(h), cudaMemcpyDeviceToHost, s));
+    if (loss) OD2P_CUDA(cudaMemcpyAsync(&hl, d_loss, sizeof(hl), cudaMemcpyDeviceToHost, s));
     OD2P_CUDA(cudaMemcpyAsync(&err, plan->d_err, sizeof(err), cudaMemcpyDeviceToHost, s));
     OD2P_CUDA(cudaStreamSynchronize(s));
     if (err) return fail(PTYCHO_ERR_TIMEOUT, "a frame-update pipeline wait gave up (device error flag set)");
     if (rf) *rf = (float)h[0];
     if (re) *re = (float)h[1];
+    if (loss) *loss = hl;
     return PTYCHO_OK;
 }
 

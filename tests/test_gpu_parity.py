@@ -298,6 +298,45 @@ def test_metrics_and_merge_match_oracle():
     assert rel_l2(host(od.od2p_merge(plan)), ref.merge()) < ONE_ITER_TOL
 
 
+def _oracle_subdomain_loss(ref, f, offs, p):
+    """sum_d sum_{j in d} G_eps(F(W_d o S_j u_d); f_j) with the oracle's loss,
+    each subdomain copy u_d taken as an image of its rectangle."""
+    fs, rect = oracle.geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px)
+    u = ref.get(oracle.U)
+    Wd = ref.get(oracle.WD).reshape(len(rect), p.m, p.m)
+    total, k = 0.0, 0
+    for d, (r0, c0, r1, c1) in enumerate(rect):
+        n = (r1 - r0) * (c1 - c0)
+        ud = u[k:k + n].reshape(r1 - r0, c1 - c0)
+        k += n
+        sel = np.flatnonzero(fs == d)
+        if len(sel):
+            loc = offs[sel] - np.array([r0, c0], np.int32)
+            total += oracle.loss_grad(ud, Wd[d], loc, np.asarray(f, np.float64)[sel], p.eps)[0]
+    return total
+
+
+@pytest.mark.parametrize("blind,m", [(False, 64), (True, 32), (False, 48), (True, 256), (False, 128)])
+def test_metrics_loss_matches_oracle(blind, m):
+    """od2p_metrics' loss: the ST-AGM data term of the current subdomain iterate."""
+    n = {32: 96, 48: 144, 64: 256, 128: 384, 256: 512}[m]
+    p = synth.Problem("ml", n, m, m // 4, 1, 2, 2, 8, 1e4, 1, eta=2.0, r=0.5, blind=blind,
+                      mu=1.0 if blind else 0.0, gamma=0.1 if blind else 0.0, seed=31)
+    offs, u_true, w, f = make_case(p)
+    w0 = synth.gaussian_probe(m) if blind else w
+    plan, ref = pair_of(p, offs, w0, f)
+    od.od2p_iterate(plan, 2)
+    ref.iterate(2)
+    rf, re, loss = od.od2p_metrics(plan, loss=True)
+    exp = _oracle_subdomain_loss(ref, f, offs, p)
+    assert abs(loss - exp) <= ONE_ITER_TOL * abs(exp), (loss, exp)
+    record(f"metrics_loss_m{m}_{'blind' if blind else 'nonblind'}", loss_rel=abs(loss - exp) / abs(exp))
+    # the extra pass leaves the state and the other metrics alone
+    u0 = od.od2p_get_state(plan, od.STATE_U).clone()
+    assert od.od2p_metrics(plan) == (rf, re)
+    assert torch.equal(od.od2p_get_state(plan, od.STATE_U), u0)
+
+
 def test_checkpoint_resume_bitwise():
     p = synth.small_2sub()
     offs, u_true, w, f = make_case(p)

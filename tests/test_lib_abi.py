@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_argument_errors(lib):
-    assert lib.ptycho_abi_version() == 1
+    assert lib.ptycho_abi_version() == 2
     # argument checks return before any device work
     assert lib.ptycho_plan(None, None, None, None) == _lib.ERR_INVALID_ARG
     h = ctypes.c_void_p()

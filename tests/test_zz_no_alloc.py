@@ -59,10 +59,39 @@ def test_noalloc_loss_matches_plan_loss_twice(m, n, step):
     plan = od.ptycho_plan(od.Geometry(n, n, m, offs, eps=0.5), fd)
     ref, _, _ = od.stagm_loss_grad(plan, ud, wd, grad_u=False, grad_w=False)
     ref = float(ref.item())
+    # the FP64 oracle's loss on the same (FP32-representable) inputs
+    exact, _, _ = oracle.loss_grad(u.astype(np.complex128), w, offs, f.astype(np.float64), 0.5)
     for _ in range(2):  # the shared scratch keeps the previous call's partials
         got = float(_noalloc(ud, wd, offs_dev, fd, 0.5).item())
         assert abs(got - ref) <= LOSS_TOL * abs(ref), (got, ref)
+        assert abs(got - exact) <= LOSS_TOL * abs(exact), (got, exact)
     plan.close()
+
+
+def test_noalloc_window_outside_image_gives_nan():
+    """Offsets live in device memory, so the kernel checks each window: a window
+    that leaves the image is not read and the loss comes back NaN; the next call
+    with valid offsets is unaffected."""
+    dev = torch.device("cuda:0")
+    m, n = 16, 64
+    p = synth.Problem("na_bad", n, m, 4, 0, 1, 1, 0, None, 1, seed=11)
+    offs = p.offsets()
+    u_true, w = p.truth(), p.probe()
+    f = (np.abs(oracle.forward(u_true, w, offs)) ** 2).astype(np.float32)
+    u = (0.9 * u_true).astype(np.complex64)  # away from the truth: a loss well above 0
+    ud = torch.from_numpy(u).to(dev)
+    wd = torch.from_numpy(w).to(dev)
+    fd = torch.from_numpy(f).to(dev)
+    offs = np.ascontiguousarray(offs, dtype=np.int32)
+    good = torch.from_numpy(offs).to(dev)
+    for bad_row, bad_col in [(n - m + 1, 0), (0, -1), (-5, 3), (2, n)]:
+        bad = offs.copy()
+        bad[len(bad) // 2] = (bad_row, bad_col)
+        got = float(_noalloc(ud, wd, torch.from_numpy(bad).to(dev), fd, 0.5).item())
+        assert np.isnan(got), (bad_row, bad_col, got)
+    got = float(_noalloc(ud, wd, good, fd, 0.5).item())
+    exact, _, _ = oracle.loss_grad(u.astype(np.complex128), w, offs, f.astype(np.float64), 0.5)
+    assert abs(got - exact) <= LOSS_TOL * abs(exact), (got, exact)
 
 
 def test_noalloc_rejects_oversized_and_bad_arguments():

@@ -27,7 +27,9 @@
  *    detectors are not limited to powers of two.  Up to 128 a frame is
  *    transformed in one thread block's shared memory; 256 x 256 frames go
  *    through row / column / row passes over a plan-owned intermediate, in
- *    waves small enough to stay in L2.  Other m return PTYCHO_ERR_UNSUPPORTED
+ *    waves small enough to stay in L2 (the frame update can instead hold each
+ *    frame in the distributed shared memory of a cluster of 16 thread blocks,
+ *    launch variant 1).  Other m return PTYCHO_ERR_UNSUPPORTED
  *    (stagm_loss_noalloc: 16, 32, 64, 128).
  */
 #ifndef OD2P_H
@@ -354,14 +356,19 @@ int ptycho_probe_init(ptycho_plan_t *plan, ptycho_c32 *w0_dev, ptycho_stream_t s
  * The persistent kernel runs min(frame groups, b x SMs) blocks, b =
  * blocks_per_sm capped at what fits (0: as many as fit).  Every shape gives
  * the same iterates bit for bit; only the RF partial sums are grouped
- * differently.  m = 256 has one shape (variant 0; blocks_per_sm ignored).
+ * differently.  m = 256 (blocks_per_sm ignored): variant 0 runs the row /
+ * column / row passes over the plan's L2-resident intermediate; variant 1
+ * transforms each frame in one pass inside a cluster of 16 thread blocks that
+ * holds the frame in their distributed shared memory.  The two are the same
+ * arithmetic in a different kernel sequence: iterates equal up to FP32
+ * rounding (each is compared with the FP64 oracle), RF grouped alike.
  * ptycho_plan_set_launch drops the plan's captured iteration graphs (they are
  * recaptured on the next od2p_iterate); when the shape changes, RF reads 0
  * until the next frame update.  A batch member returns PTYCHO_ERR_STATE: use
  * ptycho_batch_set_launch.  ptycho_plan_get_launch reports the current shape
  * and the most blocks of it that fit on one SM (any output may be NULL).
  * Errors: INVALID_ARG (variant outside [0, PTYCHO_LAUNCH_VARIANTS) or
- * blocks_per_sm < 0), UNSUPPORTED (variant 1 for m = 256), STATE, CUDA.
+ * blocks_per_sm < 0), STATE, CUDA.
  */
 #define PTYCHO_LAUNCH_VARIANTS 2
 

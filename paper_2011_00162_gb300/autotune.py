@@ -156,12 +156,6 @@ def tune_plan(plan: api.Plan, n_iter: int = 15, warmup: int = 3, flush_l2: bool 
         if hit is not None:
             _apply(plan, hit)
             return dict(hit, cached=True)
-    if plan.geom.m == 256:
-        entry = {"variant": 0, "blocks_per_sm": 0, "us": None, "trials": {}}
-        api.ptycho_plan_set_launch(plan, 0, 0)
-        if use_cache:
-            store_cache(key, entry, path)
-        return dict(entry, cached=False)
     saved = {w: api.od2p_get_state(plan, w).clone() for w in _state_selectors(plan)}
     maxes = {}
     for v in range(api.LAUNCH_VARIANTS):
@@ -170,7 +164,10 @@ def tune_plan(plan: api.Plan, n_iter: int = 15, warmup: int = 3, flush_l2: bool 
     flush = _flush_buffer(plan.device, flush_l2)
     trials = {}
     api.ptycho_plan_set_fft(plan, 0)
-    for v, b in candidates(maxes):
+    # m = 256: the cluster launch against the three passes (no block cap)
+    shapes_to_time = ([(v, 0) for v in range(api.LAUNCH_VARIANTS)] if plan.geom.m == 256
+                      else candidates(maxes))
+    for v, b in shapes_to_time:
         api.ptycho_plan_set_launch(plan, v, b)
         for _ in range(warmup):
             api.od2p_iterate(plan, 1)

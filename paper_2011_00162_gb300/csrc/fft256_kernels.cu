@@ -16,6 +16,8 @@
 #include "od2p_internal.h"
 #include "fft_device.cuh"
 
+#include <mutex>
+
 namespace od2p {
 namespace {
 
@@ -300,6 +302,318 @@ __global__ void __launch_bounds__(NTB) rows_inv256_kernel(PassC a, const float2 
     }
 }
 
+// ---------------------------------------------------------------- single-pass frame update
+// One thread-block cluster of CL CTAs holds one 256 x 256 frame in its
+// distributed shared memory, so the frame crosses HBM once per direction and
+// no intermediate leaves the chip.  CTA c of the cluster owns rows
+// [RPC c, RPC c + RPC) of the frame while the rows are transformed (buffer A)
+// and position columns [CPC c, CPC c + CPC) while the columns are (buffer B).
+// Between the phases every CTA sends each part of its data to the CTA that
+// owns it next with asynchronous shared-memory stores into that CTA's other
+// buffer (st.async), each completing bytes on the receiver's transaction
+// barrier; a CTA proceeds once its barrier has counted all the bytes it is
+// owed.  Sending into the buffer the receiver is not reading needs no barrier
+// across the cluster: a CTA sends only values computed from what it has read.
+// The arithmetic is that of passes A, B and C above, operation for operation
+// (the same 16 x 16 splits, twiddles, prox and scaling); with CL = 16 a CTA's
+// columns are one column slab of pass B with the same thread mapping, so its
+// RF partial (one per CTA) is grouped as pass B's.  Every barrier wait is
+// bounded; a wait that gives up sets the plan's device error flag.
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait()
+{
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+// shared::cluster address of shared::cta address `a` in CTA `rank`
+__device__ __forceinline__ unsigned cluster_addr(unsigned a, unsigned rank)
+{
+    unsigned out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(a), "r"(rank));
+    return out;
+}
+__device__ __forceinline__ void st_async_v4(unsigned addr, float4 v, unsigned bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     addr),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async_v2(unsigned addr, float2 v, unsigned bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "f"(v.x), "f"(v.y), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void tbar_expect(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// wait for phase 0 of a transaction barrier; false after 2^22 polls
+__device__ __forceinline__ bool tbar_wait(uint64_t *bar)
+{
+    for (int i = 0; i < (1 << 22); ++i) {
+        unsigned ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok)
+                     : "r"(smem_addr(bar))
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void prefetch_bulk_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+#ifndef OD2P_CL256
+#define OD2P_CL256 16
+#endif
+template <int CL>
+struct Cl256 {
+    static constexpr int RPC = BM / CL;  // rows per CTA in the row phase
+    static constexpr int CPC = BM / CL;  // position columns per CTA in the column phase
+    static constexpr int NT = BR * RPC;  // one 16-point DFT per thread and stage
+    static constexpr int MINB = 768 / NT;
+    static constexpr int PR = BM + 1;    // buffer A pitch (odd: conflict-free stage-2 reads)
+    static constexpr int PC = CPC + 2;   // buffer B pitch (16-byte rows, spread banks)
+    static constexpr int A_ELEMS = RPC * PR, B_ELEMS = BM * PC;
+    static constexpr unsigned XBYTES = (unsigned)(BM * CPC * sizeof(float2));  // bytes owed per exchange
+    static constexpr size_t SMEM = sizeof(float2) * (BM + A_ELEMS + B_ELEMS) + 2 * sizeof(uint64_t) +
+                                   sizeof(float) * (NT / 32);
+};
+
+template <int CL>
+__global__ void __launch_bounds__(Cl256<CL>::NT, Cl256<CL>::MINB) frame_update256_cluster_kernel(FrameArgs a)
+{
+    using K = Cl256<CL>;
+    constexpr int RPC = K::RPC, CPC = K::CPC, NT = K::NT, PR = K::PR, PC = K::PC;
+    static_assert(RPC * 16 * CL == BM * 16 && K::XBYTES == (unsigned)(RPC * BM * sizeof(float2)), "layout");
+    extern __shared__ float4 smem4[];
+    float2 *tw = reinterpret_cast<float2 *>(smem4);
+    float2 *bufA = tw + BM;           // rows RPC c ..: RPC x PR
+    float2 *bufB = bufA + K::A_ELEMS;  // position columns CPC c ..: BM x PC
+    uint64_t *bar = reinterpret_cast<uint64_t *>(bufB + K::B_ELEMS);  // [0]: columns owed, [1]: rows owed
+    float *red = reinterpret_cast<float *>(bar + 2);
+    const int tid = threadIdx.x;
+    const unsigned c = cluster_rank();
+    const int j = blockIdx.x / CL;
+    const size_t fo = (size_t)j * BMM;
+    if (tid == 0) {
+        tbar_init(&bar[0]);
+        tbar_init(&bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // every CTA's barriers are initialised before any CTA sends to them (waited
+    // for just before the first send)
+    cluster_arrive_relaxed();
+    // this CTA's Gamma and sqrt f columns of every position row, into L2 while
+    // the row transforms run
+    for (int k = tid; k < 2 * BM; k += NT) {
+        const size_t gi = fo + (size_t)(k % BM) * BM + CPC * c;
+        if (k < BM)
+            prefetch_bulk_l2(a.gamma + gi, CPC * sizeof(float2));
+        else
+            prefetch_bulk_l2(a.sqrtf_ + gi, CPC * sizeof(float));
+    }
+    for (int k = tid; k < BM; k += NT) tw[k] = a.tw[k];
+    // ---- rows, stage 1: exit wave w o S_j u of row RPC c + r, DFTs over t at n1
+    {
+        const int n1 = tid % BR, r = tid / BR, row = RPC * c + r;
+        const float2 *w = (a.Wd ? a.Wd + (size_t)a.frame_sub[j] * BMM : a.w) + row * BM + n1;
+        const float2 *uj = a.u + a.frame_base[j] + (size_t)row * a.frame_pitch[j] + n1;
+        float2 x[BR];
+#pragma unroll
+        for (int t = 0; t < BR; ++t) x[t] = cmul(__ldg(w + BR * t), __ldg(uj + BR * t));
+        dft<BR, false>(x);
+        __syncthreads();  // twiddles in place
+        float2 *rp = bufA + r * PR;
+#pragma unroll
+        for (int s = 0; s < BR; ++s) rp[n1 + BR * s] = cmul(x[s], tw[n1 * s]);
+    }
+    __syncthreads();
+    // ---- rows, stage 2: DFTs over n1 -> positions 16 s + k; first exchange
+    {
+        const int r = tid % RPC, s = tid / RPC;
+        float2 x[BR];
+#pragma unroll
+        for (int t = 0; t < BR; ++t) x[t] = bufA[r * PR + BR * s + t];
+        dft<BR, false>(x);
+        if (tid == 0) tbar_expect(&bar[0], K::XBYTES);
+        cluster_wait();  // the receivers' barriers are initialised
+        // position columns 16 s .. 16 s + 15 of row RPC c + r belong to CTA 16 s / CPC
+        const unsigned dst = (unsigned)(BR * s) / CPC;
+        const unsigned da = cluster_addr(smem_addr(bufB + (RPC * c + r) * PC + (BR * s) % CPC), dst);
+        const unsigned db = cluster_addr(smem_addr(&bar[0]), dst);
+#pragma unroll
+        for (int k = 0; k < BR / 2; ++k)
+            st_async_v4(da + 16u * k, make_float4(x[2 * k].x, x[2 * k].y, x[2 * k + 1].x, x[2 * k + 1].y), db);
+    }
+    if (!tbar_wait(&bar[0])) *a.err = 1;  // every CTA's share of this CTA's columns has arrived
+    // ---- columns, stage 1: DFTs over t at n1 of position column CPC c + col
+    {
+        const int col = tid % CPC, n1 = tid / CPC;
+        float2 x[BR];
+#pragma unroll
+        for (int t = 0; t < BR; ++t) x[t] = bufB[(n1 + BR * t) * PC + col];
+        dft<BR, false>(x);
+#pragma unroll
+        for (int s = 0; s < BR; ++s) bufB[(n1 + BR * s) * PC + col] = cmul(x[s], tw[n1 * s]);
+    }
+    __syncthreads();
+    // ---- columns, stage 2, the ST-AGM prox and Gamma update (eqs. updateZ,
+    // updateM-1-multi) on position rows 16 s + t, inverse stage 2
+    float part = 0.f;
+    {
+        const int col = tid % CPC, s = tid / CPC, pc = CPC * c + col;
+        float2 x[BR];
+#pragma unroll
+        for (int t = 0; t < BR; ++t) x[t] = bufB[(BR * s + t) * PC + col];
+        float2 gmv[BR];
+        float sfv[BR];
+        const float2 *gp = a.gamma + fo + (size_t)(BR * s) * BM + pc;
+        const float *fp = a.sqrtf_ + fo + (size_t)(BR * s) * BM + pc;
+#pragma unroll
+        for (int t = 0; t < BR; ++t) {
+            sfv[t] = __ldg(fp + t * BM);
+            gmv[t] = gp[t * BM];
+        }
+        dft<BR, false>(x);
+        const float inv_m = 1.f / (float)BM;
+        float2 *gw = a.gamma + fo + (size_t)(BR * s) * BM + pc;
+#pragma unroll
+        for (int t = 0; t < BR; ++t) {
+            const float2 ax = cscale(x[t], inv_m);
+            const float sf = sfv[t];
+            const float a2 = ax.x * ax.x + ax.y * ax.y;
+            part += fabsf((a2 > 0.f ? a2 * rsqrtf(a2) : 0.f) - sf);
+            const float2 y = cadd(gmv[t], ax);
+            const float2 z = stagm_prox(y, sf, a.pc);
+            const float2 gn = csub(y, z);
+            gw[t * BM] = gn;
+            x[t] = csub(z, gn);
+        }
+        dft<BR, true>(x);
+#pragma unroll
+        for (int t = 0; t < BR; ++t) bufB[(BR * s + t) * PC + col] = x[t];
+    }
+    __syncthreads();
+    // ---- columns, inverse stage 1 -> spatial rows n1 + 16 t; second exchange
+    {
+        const int col = tid % CPC, n1 = tid / CPC, pc = CPC * c + col;
+        float2 x[BR];
+#pragma unroll
+        for (int s = 0; s < BR; ++s) x[s] = cmulc(bufB[(n1 + BR * s) * PC + col], tw[n1 * s]);
+        dft<BR, true>(x);
+        if (tid == 0) tbar_expect(&bar[1], K::XBYTES);
+#pragma unroll
+        for (int t = 0; t < BR; ++t) {
+            const int R = n1 + BR * t;  // spatial row, owned by CTA R / RPC
+            const unsigned dst = (unsigned)(R / RPC);
+            st_async_v2(cluster_addr(smem_addr(bufA + (R % RPC) * PR + pc), dst), x[t],
+                        cluster_addr(smem_addr(&bar[1]), dst));
+        }
+    }
+    if (!tbar_wait(&bar[1])) *a.err = 1;  // this CTA's rows have arrived
+    // ---- rows, inverse stage 2
+    {
+        const int r = tid % RPC, s = tid / RPC;
+        float2 *rp = bufA + r * PR + BR * s;
+        float2 x[BR];
+#pragma unroll
+        for (int t = 0; t < BR; ++t) x[t] = rp[t];
+        dft<BR, true>(x);
+#pragma unroll
+        for (int t = 0; t < BR; ++t) rp[t] = x[t];
+    }
+    __syncthreads();
+    // ---- rows, inverse stage 1 -> spatial columns n1 + 16 t; q_j, or conj(w) q_j
+    // into the gather slots (nonblind)
+    {
+        const int n1 = tid % BR, r = tid / BR, row = RPC * c + r;
+        const float2 *rp = bufA + r * PR;
+        float2 x[BR];
+#pragma unroll
+        for (int s = 0; s < BR; ++s) x[s] = cmulc(rp[n1 + BR * s], tw[n1 * s]);
+        dft<BR, true>(x);
+        const float sc = 1.f / (float)BM;
+        if (a.slot) {
+            const uint8_t *rk = a.rank + fo + row * BM + n1;
+            float2 *sl = a.slot + a.frame_base[j] + (size_t)row * a.frame_pitch[j] + n1;
+#pragma unroll
+            for (int t = 0; t < BR; ++t) {
+                const float2 v = cmulc(cscale(x[t], sc), __ldg(a.w + row * BM + n1 + BR * t));
+                sl[(size_t)__ldg(rk + BR * t) * a.slot_stride + BR * t] = v;
+            }
+        } else {
+            float2 *q = a.q + fo + row * BM + n1;
+#pragma unroll
+            for (int t = 0; t < BR; ++t) q[BR * t] = cscale(x[t], sc);
+        }
+    }
+    const float tot = block_sum_fixed(part, red);
+    if (tid == 0) a.rf_part[(size_t)j * CL + c] = tot;
+    // no CTA leaves while stores of its cluster may still be in flight
+    cluster_arrive_relaxed();
+    cluster_wait();
+}
+
+int cluster256_setup(const void *fn, size_t smem)
+{
+    static bool done[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    OD2P_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(PTYCHO_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+        OD2P_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        OD2P_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        done[dev] = true;
+    }
+    return PTYCHO_OK;
+}
+
+int frame_update_256_cluster(ptycho_plan_s *p, cudaStream_t s)
+{
+    using K = Cl256<OD2P_CL256>;
+    auto fn = frame_update256_cluster_kernel<OD2P_CL256>;
+    if (int rc = cluster256_setup(reinterpret_cast<const void *>(fn), K::SMEM)) return rc;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)p->J * OD2P_CL256);
+    cfg.blockDim = dim3(K::NT);
+    cfg.dynamicSmemBytes = K::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = OD2P_CL256;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    OD2P_CUDA(cudaLaunchKernelEx(&cfg, fn, p->h_fargs[p->cur]));
+    return PTYCHO_OK;
+}
+
 constexpr size_t SMEM_A = sizeof(float2) * (BM + SLAB * PA);
 constexpr size_t SMEM_B = sizeof(float2) * (BM + BM * PB) + sizeof(float) * (NTB / 32);
 
@@ -405,8 +719,11 @@ __global__ void probe_sum256_kernel(int D, const float2 *Wd, const float2 *Delta
 
 }  // namespace
 
+int rf_parts_256(int J, int variant) { return variant == 1 ? J * OD2P_CL256 : J * (BM / SLAB); }
+
 int frame_update_256(ptycho_plan_s *p, cudaStream_t s)
 {
+    if (p->k1_variant == 1) return frame_update_256_cluster(p, s);
     Pipeline P = base_pipeline(p);
     P.do_a = P.do_c = true;
     P.A.u = p->d_u[p->cur];

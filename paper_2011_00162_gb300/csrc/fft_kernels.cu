@@ -1280,11 +1280,12 @@ int frame_groups(int m, int J, int variant)
 }
 
 // RF partial sums written per iteration: one per warp of each frame group
-// (m <= 128), one per 16-column slab (m = 256).
+// (m <= 128); m = 256: one per 16-column slab of the column pass (variant 0)
+// or per CTA of a frame's cluster (variant 1).
 int rf_parts(int m, int J, int variant)
 {
     OD2P_K1_SHAPE(m, variant, return frame_groups(m, J, variant) * (K1Cfg<M_, V_>::NT / 32))
-    return J * 16;
+    return rf_parts_256(J, variant);
 }
 
 void fill_frame_args(const ptycho_plan_s *p, FrameArgs out[2])

@@ -261,8 +261,10 @@ int launch_frame_update_table(int m, int variant, const FrameArgs *tab, const in
                               cudaStream_t s);
 int prepare_kernels(int m);
 
-// fft256_kernels.cu (m = 256)
+// fft256_kernels.cu (m = 256): the frame update runs as the three passes over
+// an L2 intermediate (launch variant 0) or as one cluster launch (variant 1)
 int frame_update_256(ptycho_plan_s *p, cudaStream_t s);
+int rf_parts_256(int J, int variant);
 int forward_256(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out, cudaStream_t s);
 int ifft_256(const ptycho_plan_s *p, const float2 *in, float2 *out, cudaStream_t s);
 int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s);

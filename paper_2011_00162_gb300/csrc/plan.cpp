@@ -340,9 +340,17 @@ int apply_launch(ptycho_plan_s *p, int variant, int blocks_per_sm, cudaStream_t 
         p->k1_blocks_per_sm = blocks_per_sm;
         return PTYCHO_OK;
     }
-    if (p->M == 256) {
-        if (variant != 0) return fail(PTYCHO_ERR_UNSUPPORTED, "m = 256 has one launch shape (variant 0)");
+    if (p->M == 256) {  // variant 0: three passes; 1: one cluster launch (blocks_per_sm not used)
+        const int parts = rf_parts(p->M, p->J, variant);
+        if (parts != p->n_rf_parts || variant != p->k1_variant) {
+            const int cap = std::max(rf_parts(p->M, p->J, 0), rf_parts(p->M, p->J, 1));
+            OD2P_CUDA(cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * cap, s));
+        }
+        p->k1_variant = variant;
         p->k1_blocks_per_sm = 0;
+        p->n_rf_parts = parts;
+        drop_graphs(p->graph);
+        drop_graphs(p->until);
         return PTYCHO_OK;
     }
     int grid = 0;

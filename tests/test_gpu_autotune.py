@@ -47,7 +47,8 @@ def _states(plan, blind):
 
 CASES = [(16, (5, 4), 120, 6, False), (32, (2, 3), 200, 10, False), (64, (2, 2), 256, 16, False),
          (128, (2, 2), 384, 32, False), (32, (2, 2), 160, 8, True), (64, (1, 2), 192, 16, True),
-         (48, (2, 2), 192, 12, False), (80, (2, 2), 240, 20, False), (96, (2, 2), 288, 24, True)]
+         (48, (2, 2), 192, 12, False), (80, (2, 2), 240, 20, False), (96, (2, 2), 288, 24, True),
+         (256, (2, 2), 512, 64, False), (256, (2, 3), 560, 48, True)]
 
 
 @pytest.mark.parametrize("m,grid,n,step,blind", CASES)
@@ -65,12 +66,24 @@ def test_every_launch_shape_gives_identical_iterates(m, grid, n, step, blind):
         for cap in sorted({1, most}):
             plan = _plan(p, blind)
             od.ptycho_plan_set_launch(plan, v, cap)
-            assert od.ptycho_plan_get_launch(plan) == (v, cap, most)
+            # m = 256 has no block cap (reported as 0)
+            assert od.ptycho_plan_get_launch(plan) == (v, cap if m != 256 else 0, most)
             od.od2p_iterate(plan, 3)
             got = _states(plan, blind)
+            rf, re = od.od2p_metrics(plan)
+            if m == 256 and v != 0:
+                # m = 256: the cluster variant is a different kernel sequence, whose
+                # FP32 contractions the compiler may choose differently: equal to
+                # rounding (both are compared with the FP64 oracle in the parity tests)
+                for k in want:
+                    d = float(torch.linalg.vector_norm(got[k] - want[k]) /
+                              max(float(torch.linalg.vector_norm(want[k])), 1e-30))
+                    assert d <= 1e-5, (v, k, d)
+                assert abs(rf - rf_ref) <= 1e-5 * abs(rf_ref) and abs(re - re_ref) <= 1e-3 * abs(re_ref)
+                plan.close()
+                continue
             for k in want:
                 assert torch.equal(got[k], want[k]), (v, cap, k)
-            rf, re = od.od2p_metrics(plan)
             # RF partials are grouped per warp of a frame group: same value up to summation order
             assert abs(rf - rf_ref) <= 1e-5 * abs(rf_ref) and re == re_ref
             plan.close()
@@ -100,13 +113,13 @@ def test_set_launch_argument_errors():
     # a cap above what fits is clamped, not refused
     od.ptycho_plan_set_launch(plan, 0, 1000)
     assert od.ptycho_plan_get_launch(plan)[1] == 1000
+    # m = 256: variant 0 is the three passes, 1 the cluster launch; no block cap
     p256 = synth.Problem("t", 512, 256, 64, 2, 2, 2, 12, 1e5, 1, seed=3)
     plan256 = _plan(p256)
     od.ptycho_plan_set_launch(plan256, 0, 3)
     assert od.ptycho_plan_get_launch(plan256) == (0, 0, 1)
-    with pytest.raises(od.PtychoError) as e:
-        od.ptycho_plan_set_launch(plan256, 1, 0)
-    assert e.value.code == 2  # PTYCHO_ERR_UNSUPPORTED
+    od.ptycho_plan_set_launch(plan256, 1, 0)
+    assert od.ptycho_plan_get_launch(plan256) == (1, 0, 1)
 
 
 def test_tune_plan_restores_state_and_caches(tmp_path):

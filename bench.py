@@ -800,9 +800,11 @@ def run_table1(args):
 
 # ----------------------------------------------------------------------------- profiling case
 def run_profile_case(args):
-    """A medium blind m = 256 workload for kernel captures (a few GB on the
-    device, inputs larger than L2): 2048^2 image, 256^2 probe, step 48 +-4
-    (1444 frames), 4x4 subdomains, Poisson 1e5; five iterations after two of
+    """A blind m = 256 workload for kernel captures: by default the medium case
+    (a few GB on the device, inputs larger than L2) of a 2048^2 image, 256^2
+    probe, step 48 +-4 (1444 frames), 4x4 subdomains, Poisson 1e5;
+    --profile-n 4096 gives the headline workload (8x8 subdomains).  The frame
+    update runs launch variant --profile-variant; five iterations after two of
     warm-up, then one line with the time per iteration."""
     import dataclasses
 
@@ -814,16 +816,21 @@ def run_profile_case(args):
     odbuild.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    p = dataclasses.replace(synth.large_blind(), name="od2bp_2048px_m256_4x4", n=2048, sub_rows=4, sub_cols=4)
+    n = args.profile_n
+    grid = 8 if n >= 4096 else 4
+    p = dataclasses.replace(synth.large_blind(), name=f"od2bp_{n}px_m256_{grid}x{grid}", n=n, sub_rows=grid,
+                            sub_cols=grid)
     offs, u_true, w, f = _gpu_problem_inputs(od, p, dev)
     g = od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, 2.0, 0.5, mu=1.0, gamma=0.1,
                     blind=True)
     plan = od.ptycho_plan(g, f)
     od.od2p_init(plan, torch.from_numpy(synth.gaussian_probe(p.m)).to(dev))
+    od.ptycho_plan_set_launch(plan, args.profile_variant, 0)
     od.od2p_iterate(plan, 2)
     flush = torch.empty(1, device=dev)
     t = _event_times(lambda: od.od2p_iterate(plan, 1), 5, flush)
-    print(json.dumps({"workload": p.name, "frames": len(offs), "ms_per_iteration": round(1e3 * statistics.mean(t), 4),
+    print(json.dumps({"workload": p.name, "frames": len(offs), "variant": args.profile_variant,
+                      "ms_per_iteration": round(1e3 * statistics.mean(t), 4),
                       "rf_after": od.od2p_metrics(plan)[0]}), flush=True)
 
 
@@ -991,6 +998,10 @@ def main():
     ap.add_argument("--only", default="", help="with --configs: only workloads whose name contains this")
     ap.add_argument("--profile-case", action="store_true",
                     help="run a medium blind m = 256 workload (2048^2, 1444 frames) for kernel captures")
+    ap.add_argument("--profile-n", type=int, default=2048, choices=(2048, 4096),
+                    help="with --profile-case: image side (4096: the headline workload)")
+    ap.add_argument("--profile-variant", type=int, default=0, choices=(0, 1),
+                    help="with --profile-case: launch variant of the m = 256 frame update")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP32 FMA and shared-memory ceilings with the library's probes")
     ap.add_argument("--table1", action="store_true",

@@ -40,4 +40,5 @@ def record(test: str, **figures) -> None:
     if not path:
         return
     with open(path, "a") as fh:
-        fh.write(json.dumps({"test": test, **{k: float(v) for k, v in figures.items()}}) + "\n")
+        fh.write(json.dumps({"test": test, **{k: ([float(x) for x in v] if isinstance(v, (list, tuple)) else float(v))
+                                              for k, v in figures.items()}}) + "\n")

@@ -88,6 +88,7 @@ def _load():
             "orc_admm_merge": (None, [P, P]),
             "orc_admm_set_penalties": (None, [P, f64, f64]),
             "orc_admm_consensus": (f64, [P]),
+            "orc_admm_set_owned": (None, [P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -270,6 +271,17 @@ class ADMM:
     def set_penalties(self, eta: float, r: float) -> None:
         """Change eta and r, keeping the unscaled multipliers eta*Gamma and r*Lambda."""
         self._lib.orc_admm_set_penalties(self._h, float(eta), float(r))
+
+    def set_owned(self, owned) -> None:
+        """Update only the subdomains d with owned[d] != 0 (None: all of them);
+        the others' u, Lambda, W_d and Delta_d are halo copies set from outside."""
+        if owned is None:
+            self._lib.orc_admm_set_owned(self._h, None)
+            return
+        o = _c(owned, np.int32).reshape(-1)
+        if o.size != self.D:
+            raise ValueError(f"ownership mask: expected {self.D} entries, got {o.size}")
+        self._lib.orc_admm_set_owned(self._h, _p(o))
 
     def consensus(self) -> float:
         """||u_d - u_e|| over the pairs' overlaps relative to ||u||."""

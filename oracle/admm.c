@@ -26,6 +26,14 @@
  *  - RF (section 4) is accumulated from the frames A_d u_d^n (blind:
  *    F(W_d^n o S_j u_d^n)) formed in Step 1, i.e. it is the RF of the iterate
  *    entering the iteration.  RE = max_d ||u_d^{n+1} - u_d^n|| / ||u_d^{n+1}||.
+ *  - Subdomain ownership (section 3.1: the subdomains are independent but for
+ *    the overlap terms): with an ownership mask set, an iteration updates only
+ *    the owned subdomains -- their frames, u_d, Lambda_{d,e}, and (blind) W_d
+ *    and Delta_d -- and reads the other subdomains' u_e, Lambda_{e,d}, W_e and
+ *    Delta_e as they were last set (their halo copies).  RF and RE then cover
+ *    the owned part only.  Every owned value is computed exactly as without a
+ *    mask, so ranks that own disjoint sets and exchange those copies between
+ *    iterations reproduce the undivided iteration.
  */
 #include "od2p_oracle.h"
 
@@ -42,6 +50,7 @@ struct orc_admm {
     ocplx *w, *Wd, *Delta; /* mm, D*mm, D*mm */
     ocplx *u, *Gamma, *Lam, *v, *z;
     int64_t *u_off, *lam_off;
+    int32_t *owned;        /* D: 1 where this instance updates subdomain d */
     double rf, re;
 };
 
@@ -109,7 +118,14 @@ orc_admm *orc_admm_new(int H, int W, int m, int J, const int32_t *offs, int sub_
     s->z = (ocplx *)calloc((size_t)J * mm + 1, sizeof(ocplx));
     s->Lam = (ocplx *)calloc((size_t)s->lam_off[s->P] + 1, sizeof(ocplx));
     s->v = (ocplx *)calloc((size_t)s->lam_off[s->P] + 1, sizeof(ocplx));
+    s->owned = (int32_t *)malloc(sizeof(int32_t) * D);
+    for (int d = 0; d < D; ++d) s->owned[d] = 1;
     return s;
+}
+
+void orc_admm_set_owned(orc_admm *s, const int32_t *owned)
+{
+    for (int d = 0; d < s->D; ++d) s->owned[d] = owned ? (owned[d] != 0) : 1;
 }
 
 void orc_admm_free(orc_admm *s)
@@ -118,7 +134,7 @@ void orc_admm_free(orc_admm *s)
     free(s->offs); free(s->frame_sub); free(s->rect); free(s->pair); free(s->pair_rect);
     free(s->pair_of); free(s->f); free(s->mask); free(s->w); free(s->Wd); free(s->Delta);
     free(s->u); free(s->Gamma); free(s->Lam); free(s->v); free(s->z); free(s->u_off);
-    free(s->lam_off); free(s);
+    free(s->lam_off); free(s->owned); free(s);
 }
 
 int orc_admm_num_sub(const orc_admm *s) { return s->D; }
@@ -164,6 +180,8 @@ void orc_admm_iterate(orc_admm *s, int n_iter)
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < J; ++j) {
             const int d = s->frame_sub[j];
+            rfj[j] = 0.0;
+            if (!s->owned[d]) continue;
             const ocplx *wp = s->blind ? s->Wd + (size_t)d * mm : s->w;
             ocplx *x = X + (size_t)j * mm;
             const int r0 = s->offs[2 * j], c0 = s->offs[2 * j + 1];
@@ -182,12 +200,15 @@ void orc_admm_iterate(orc_admm *s, int n_iter)
         {
             double num = 0.0, den = 0.0;
             for (int j = 0; j < J; ++j) num += rfj[j];
-            for (int64_t i = 0; i < (int64_t)J * mm; ++i) den += sqrt(s->f[i]);
+            for (int j = 0; j < J; ++j)
+                if (s->owned[s->frame_sub[j]])
+                    for (int k = 0; k < mm; ++k) den += sqrt(s->f[(size_t)j * mm + k]);
             s->rf = den > 0.0 ? num / den : 0.0;
         }
         /* v_{i1,i2}^{n+1} = 1/2 (pi u_i1^n + pi u_i2^n + Lambda_{i1,i2}^n + Lambda_{i2,i1}^n) (eq. updateV-multi) */
         for (int k = 0; k < s->P; ++k) {
             const int d = s->pair[2 * k], e = s->pair[2 * k + 1];
+            if (!s->owned[d]) continue;
             const int i1 = d < e ? d : e, i2 = d < e ? e : d;
             const int k12 = s->pair_of[i1 * D + i2], k21 = s->pair_of[i2 * D + i1];
             const int32_t *prc = s->pair_rect + 4 * k;
@@ -198,11 +219,14 @@ void orc_admm_iterate(orc_admm *s, int n_iter)
                                *lam_at(s->Lam, s, k21, R, C));
         }
         /* ---------------- Step 2: Gamma^{n+1} = Gamma^n + A_d u_d^n - z^{n+1}  (eq. updateM-1-multi) */
-        for (int64_t i = 0; i < (int64_t)J * mm; ++i) s->Gamma[i] += X[i] - s->z[i];
+        for (int j = 0; j < J; ++j)
+            if (s->owned[s->frame_sub[j]])
+                for (int k = 0; k < mm; ++k) s->Gamma[(size_t)j * mm + k] += X[(size_t)j * mm + k] - s->z[(size_t)j * mm + k];
 
         /* q_j = F^*(z_j - Gamma_j^{n+1}) (shared by the blind W- and U-updates and A_d^*) */
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < J; ++j) {
+            if (!s->owned[s->frame_sub[j]]) continue;
             ocplx *q = Q + (size_t)j * mm;
             for (int k = 0; k < mm; ++k) q[k] = s->z[(size_t)j * mm + k] - s->Gamma[(size_t)j * mm + k];
             orc_fft2(q, m, 1);
@@ -212,6 +236,10 @@ void orc_admm_iterate(orc_admm *s, int n_iter)
         if (s->blind) {
             for (int d = 0; d < D; ++d) {
                 ocplx *Wn = Wnew + (size_t)d * mm;
+                if (!s->owned[d]) {  /* another instance's subdomain: keep its copy */
+                    memcpy(Wn, s->Wd + (size_t)d * mm, sizeof(ocplx) * mm);
+                    continue;
+                }
                 double *dd = (double *)calloc(mm, sizeof(double));
                 for (int k = 0; k < mm; ++k) Wn[k] = 0.0;
                 for (int j = 0; j < J; ++j) {
@@ -237,6 +265,7 @@ void orc_admm_iterate(orc_admm *s, int n_iter)
         memset(nrm, 0, sizeof(double) * (size_t)s->u_off[D]);
         for (int j = 0; j < J; ++j) {
             const int d = s->frame_sub[j];
+            if (!s->owned[d]) continue;
             const ocplx *wp = Wuse ? Wuse + (size_t)d * mm : s->w;
             const int r0 = s->offs[2 * j], c0 = s->offs[2 * j + 1];
             for (int r = 0; r < m; ++r)
@@ -250,6 +279,10 @@ void orc_admm_iterate(orc_admm *s, int n_iter)
         s->re = 0.0;
         for (int d = 0; d < D; ++d) {
             const int32_t *rc = s->rect + 4 * d;
+            if (!s->owned[d]) {  /* another instance's subdomain: keep its copy */
+                memcpy(unew + s->u_off[d], s->u + s->u_off[d], sizeof(ocplx) * (size_t)(s->u_off[d + 1] - s->u_off[d]));
+                continue;
+            }
             double dn = 0.0, nn = 0.0;
             for (int R = rc[0]; R < rc[2]; ++R)
                 for (int C = rc[1]; C < rc[3]; ++C) {
@@ -278,15 +311,18 @@ void orc_admm_iterate(orc_admm *s, int n_iter)
 
         /* ---------------- Step 4 / Step 5: multipliers (eqs. updateM-2-multi, admm_Delta, admm_Lambda) */
         if (s->blind) {
-            for (int d = 0; d < D; ++d)
+            for (int d = 0; d < D; ++d) {
+                if (!s->owned[d]) continue;
                 for (int k = 0; k < mm; ++k) {
                     s->Delta[(size_t)d * mm + k] += Wnew[(size_t)d * mm + k] - wnew[k];
                     s->Wd[(size_t)d * mm + k] = Wnew[(size_t)d * mm + k];
                 }
+            }
             memcpy(s->w, wnew, sizeof(ocplx) * mm);
         }
         for (int k = 0; k < s->P; ++k) {
             const int d = s->pair[2 * k];
+            if (!s->owned[d]) continue;
             const int32_t *prc = s->pair_rect + 4 * k;
             for (int R = prc[0]; R < prc[2]; ++R)
                 for (int C = prc[1]; C < prc[3]; ++C)

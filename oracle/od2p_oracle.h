@@ -91,6 +91,10 @@ int  orc_admm_num_pairs(const orc_admm *s);
 int64_t orc_admm_state_len(const orc_admm *s, int which);
 void orc_admm_get(const orc_admm *s, int which, ocplx *out);
 void orc_admm_set(orc_admm *s, int which, const ocplx *in);
+/* Ownership mask (D entries, nonzero = owned; NULL = all): an iteration then
+ * updates only the owned subdomains and reads the others' u, Lambda, W_d and
+ * Delta_d as last set (halo copies of another instance's subdomains).       */
+void orc_admm_set_owned(orc_admm *s, const int32_t *owned);
 /* RF of the iterate entering the last iteration and RE of the last update. */
 void orc_admm_metrics(const orc_admm *s, double *rf, double *re);
 /* Merged image (section 4 set-up: overlaps averaged) and shared probe. */

@@ -141,6 +141,57 @@ int ptycho_release_cached_memory(void);
 int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev,
                 ptycho_stream_t stream);
 
+/*
+ * The decomposition alone, on the host (no device work): frame_sub_host[J]
+ * receives each frame's subdomain and rect_host[D*4] (D = sub_rows *
+ * sub_cols) each subdomain's rectangle (r0, c0, r1, c1), half-open, by the
+ * rule stated above.  Either output may be NULL.  Used to split a problem
+ * over ranks before any plan exists.  Errors: INVALID_ARG, UNSUPPORTED (m).
+ */
+int ptycho_decompose(const ptycho_geometry *g, int32_t *frame_sub_host, int32_t *rect_host);
+
+/*
+ * Subdomain sharding of one reconstruction over several ranks (section 3.1:
+ * the subdomain problems are coupled only through their overlaps).  A shard
+ * plan holds the subdomains d with owner_host[d] == rank (owner_host: D ranks,
+ * host memory) -- their frames, u_d, Lambda_{d,e} and, blind, W_d and Delta_d
+ * -- and halo copies of every other subdomain's u, Lambda, W and Delta in the
+ * same layouts as a whole plan (od2p_state_len, od2p_get_state).  f_dev holds
+ * the intensities of the shard's own frames only (those j with
+ * owner[frame_sub[j]] == rank, ascending j; ptycho_decompose gives
+ * frame_sub), J_shard x m x m.  od2p_init, od2p_iterate and the stage calls
+ * then update only the shard's own values, each computed exactly as in the
+ * whole plan, provided the halo copies are current before every iteration:
+ * between iterations each rank packs, for every peer, the strips of its own
+ * u_e on the overlaps with the peer's subdomains and its Lambda_{e,d} (blind:
+ * also its W_e and Delta_e), moves the message to the peer (NCCL, MPI or
+ * host memory: the library does not communicate), and unpacks what it
+ * receives.  Message order (both sides derive it from the decomposition): for
+ * every ordered pair (e, d) in pair order with owner[e] = sender and owner[d]
+ * = receiver, the rows of u_e on Omega_e n Omega_d, then Lambda_{e,d}
+ * (row-major); blind, then W_e and Delta_e (m x m) of every e the sender owns,
+ * e ascending.  A shard's od2p_metrics covers its own frames and subdomains;
+ * its merge and its halo state are only as current as the last unpack.
+ * Errors: INVALID_ARG (owner out of [0, D), a rank owning no subdomain or no
+ * frame), and as ptycho_plan.
+ */
+int ptycho_plan_shard(ptycho_plan_t **out, const ptycho_geometry *g, const int32_t *owner_host, int32_t rank,
+                      const float *f_dev, ptycho_stream_t stream);
+/* Number of frames a plan holds and, for a shard, their global indices
+ * (global_index_host: n_frames entries; a whole plan gives 0 .. J-1).     */
+int ptycho_plan_frames(const ptycho_plan_t *plan, int32_t *n_frames, int32_t *global_index_host);
+/* Complex elements of the halo messages to and from `peer` (any output may be
+ * NULL).  Errors: INVALID_ARG (peer out of range or the shard's own rank),
+ * STATE (not a shard).                                                     */
+int od2p_halo_size(const ptycho_plan_t *plan, int32_t peer, int64_t *send_elems, int64_t *recv_elems);
+/* Write the message for `peer` from the shard's current state into send_dev
+ * (device, od2p_halo_size's send_elems complex), or write the message
+ * received from `peer` (recv_dev, recv_elems) into the shard's halo copies.
+ * Asynchronous on `stream`; call them between iterations.  Errors: as
+ * od2p_halo_size, INVALID_ARG (NULL buffer for a non-empty message), CUDA.  */
+int od2p_halo_pack(const ptycho_plan_t *plan, int32_t peer, ptycho_c32 *send_dev, ptycho_stream_t stream);
+int od2p_halo_unpack(ptycho_plan_t *plan, int32_t peer, const ptycho_c32 *recv_dev, ptycho_stream_t stream);
+
 /* Free a plan and everything it owns (synchronises the device). NULL is a no-op. */
 int ptycho_plan_destroy(ptycho_plan_t *plan);
 

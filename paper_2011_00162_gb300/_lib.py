@@ -43,6 +43,12 @@ SIGNATURES = {
     "ptycho_release_cached_memory": (ctypes.c_int, []),
     "ptycho_plan": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), _P, _P]),
     "ptycho_plan_destroy": (ctypes.c_int, [_P]),
+    "ptycho_decompose": (ctypes.c_int, [ctypes.POINTER(Geometry), _P, _P]),
+    "ptycho_plan_shard": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), _P, _I32, _P, _P]),
+    "ptycho_plan_frames": (ctypes.c_int, [_P, _P, _P]),
+    "od2p_halo_size": (ctypes.c_int, [_P, _I32, _P, _P]),
+    "od2p_halo_pack": (ctypes.c_int, [_P, _I32, _P, _P]),
+    "od2p_halo_unpack": (ctypes.c_int, [_P, _I32, _P, _P]),
     "ptycho_plan_dims": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "ptycho_plan_layout": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "ptycho_forward": (ctypes.c_int, [_P, _P, _P, _P, _P]),

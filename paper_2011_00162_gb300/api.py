@@ -27,7 +27,8 @@ __all__ = [
     "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr", "od2p_operator_norms", "ptycho_peak_probe",
            "od2p_iterate_until", "od2p_gamma_snapshot", "od2p_frame_residual", "ptycho_plan_set_fft",
            "ptycho_plan_get_fft",
-           "PROBE_FMA", "PROBE_SMEM",
+           "PROBE_FMA", "PROBE_SMEM", "ptycho_decompose", "ptycho_plan_shard", "ptycho_plan_frames",
+           "od2p_halo_size", "od2p_halo_pack", "od2p_halo_unpack",
 ]
 
 LAUNCH_VARIANTS = _lib.LAUNCH_VARIANTS
@@ -74,24 +75,38 @@ class Geometry:
 
 
 class Plan:
-    """Owns a ptycho_plan_t; freed by close() or garbage collection."""
+    """Owns a ptycho_plan_t; freed by close() or garbage collection.  With
+    `owner` (one rank per subdomain) it is the shard of rank `rank`, and f
+    holds only that shard's frames (see ptycho_plan_shard)."""
 
-    def __init__(self, geom: Geometry, f: torch.Tensor, stream=None):
+    def __init__(self, geom: Geometry, f: torch.Tensor, stream=None, owner=None, rank: int = 0):
         self._lib = _lib.load()
         self.geom = geom
         self._offs = np.ascontiguousarray(np.asarray(geom.offsets, np.int32).reshape(-1, 2))
         self._mask = (np.ascontiguousarray(np.asarray(geom.fourier_support, np.uint8))
                       if geom.fourier_support is not None else None)
         J = self._offs.shape[0]
-        if tuple(f.shape) != (J, geom.m, geom.m):
-            raise ValueError(f"f must be (J, m, m) = {(J, geom.m, geom.m)}, got {tuple(f.shape)}")
         g = _lib.Geometry(geom.img_h, geom.img_w, geom.m, J, self._offs.ctypes.data, geom.sub_rows,
                           geom.sub_cols, geom.overlap_px, geom.eps, geom.eta, geom.r, geom.mu,
                           geom.gamma, int(bool(geom.blind)),
                           self._mask.ctypes.data if self._mask is not None else None)
         h = ctypes.c_void_p()
-        check(self._lib.ptycho_plan(ctypes.byref(h), ctypes.byref(g), _ptr(f, torch.float32, "f"),
-                                    _stream(stream)))
+        if owner is None:
+            if tuple(f.shape) != (J, geom.m, geom.m):
+                raise ValueError(f"f must be (J, m, m) = {(J, geom.m, geom.m)}, got {tuple(f.shape)}")
+            check(self._lib.ptycho_plan(ctypes.byref(h), ctypes.byref(g), _ptr(f, torch.float32, "f"),
+                                        _stream(stream)))
+        else:
+            own = np.ascontiguousarray(np.asarray(owner, np.int32).reshape(-1))
+            fs, _ = ptycho_decompose(geom)
+            Js = int(np.count_nonzero(own[fs] == rank))
+            if tuple(f.shape) != (Js, geom.m, geom.m):
+                raise ValueError(f"f must hold the shard's {Js} frames, got {tuple(f.shape)}")
+            check(self._lib.ptycho_plan_shard(ctypes.byref(h), ctypes.byref(g), own.ctypes.data, int(rank),
+                                              _ptr(f, torch.float32, "f"), _stream(stream)))
+            J = Js
+        self.owner = None if owner is None else [int(x) for x in np.asarray(owner).reshape(-1)]
+        self.rank = int(rank)
         self._h = h
         self.device = f.device
         D, P = ctypes.c_int32(), ctypes.c_int32()
@@ -131,6 +146,53 @@ class Plan:
 
 def ptycho_plan(geom: Geometry, f: torch.Tensor, stream=None) -> Plan:
     return Plan(geom, f, stream)
+
+
+def ptycho_decompose(geom: Geometry):
+    """(frame_sub[J], rect[D, 4]) of the decomposition, computed on the host."""
+    g, keep = _geometry_struct(geom)
+    fs = np.empty(geom.n_frames, np.int32)
+    rect = np.empty((geom.sub_rows * geom.sub_cols, 4), np.int32)
+    check(_lib.load().ptycho_decompose(ctypes.byref(g), fs.ctypes.data, rect.ctypes.data))
+    del keep
+    return fs, rect
+
+
+def ptycho_plan_shard(geom: Geometry, owner, rank: int, f: torch.Tensor, stream=None) -> Plan:
+    """The shard of rank `rank` (owner[d] = rank of subdomain d); f: its own frames."""
+    return Plan(geom, f, stream, owner=owner, rank=rank)
+
+
+def ptycho_plan_frames(plan: Plan) -> np.ndarray:
+    """Global indices of the plan's frames."""
+    out = np.empty(plan.n_frames, np.int32)
+    check(plan._lib.ptycho_plan_frames(plan.handle, None, out.ctypes.data))
+    return out
+
+
+def od2p_halo_size(plan: Plan, peer: int) -> tuple[int, int]:
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    check(plan._lib.od2p_halo_size(plan.handle, int(peer), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def od2p_halo_pack(plan: Plan, peer: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    n, _ = od2p_halo_size(plan, peer)
+    if out is None:
+        out = torch.empty(n, dtype=torch.complex64, device=plan.device)
+    if out.numel() != n:
+        raise ValueError(f"send buffer must hold {n} complex values")
+    check(plan._lib.od2p_halo_pack(plan.handle, int(peer), _ptr(out, torch.complex64, "out") if n else None,
+                                   _stream(stream)))
+    return out
+
+
+def od2p_halo_unpack(plan: Plan, peer: int, msg: torch.Tensor, stream=None) -> None:
+    _, n = od2p_halo_size(plan, peer)
+    if msg.numel() != n:
+        raise ValueError(f"message must hold {n} complex values")
+    check(plan._lib.od2p_halo_unpack(plan.handle, int(peer), _ptr(msg, torch.complex64, "msg") if n else None,
+                                     _stream(stream)))
 
 
 def _geometry_struct(geom: Geometry):

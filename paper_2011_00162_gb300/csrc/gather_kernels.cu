@@ -1051,6 +1051,31 @@ int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, c
     return PTYCHO_OK;
 }
 
+// Halo rows of a shard: one warp per row, lanes along the row (coalesced).
+__global__ void halo_copy_kernel(const HaloRow *rows, int n_rows, float2 *u, float2 *lam, float2 *Wd,
+                                 float2 *Delta, float2 *msg, int pack)
+{
+    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (row >= n_rows) return;
+    const HaloRow r = rows[row];
+    float2 *a = r.arr == 0 ? u : r.arr == 1 ? lam : r.arr == 2 ? Wd : Delta;
+    if (pack)
+        for (int i = lane; i < r.len; i += 32) msg[r.msg + i] = a[r.off + i];
+    else
+        for (int i = lane; i < r.len; i += 32) a[r.off + i] = msg[r.msg + i];
+}
+
+int launch_halo_copy(const ptycho_plan_s *p, const HaloRow *rows, int n_rows, float2 *msg, bool pack,
+                     cudaStream_t s)
+{
+    if (n_rows <= 0) return PTYCHO_OK;
+    const int blocks = (n_rows + 7) / 8;  // eight warps per block
+    halo_copy_kernel<<<blocks, 256, 0, s>>>(rows, n_rows, p->d_u[p->cur], p->d_lam[p->cur], p->d_Wd, p->d_Delta, msg,
+                                            pack ? 1 : 0);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
 int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s)
 {
     loss_sum_kernel<<<1, 256, 0, s>>>(p->n_loss_blocks, p->d_loss_part, loss);

@@ -135,6 +135,13 @@ struct FrameArgs {
     ProxConst pc;
 };
 
+// One row of a halo message: `len` elements of array `arr` (0: u, 1: Lambda,
+// 2: W_d, 3: Delta_d) from offset `off`, at offset `msg` of the message.
+struct HaloRow {
+    int32_t arr, len;
+    int64_t off, msg;
+};
+
 // Arguments of one plan's subdomain update (one copy per buffer parity).
 struct SubArgs {
     int32_t M;
@@ -231,6 +238,16 @@ struct ptycho_plan_s {
     bool cond_checked = false;                       // conditional-node self check passed
     int32_t fft_kind = 0;                            // m = 64: 0 the 8 x 8 split, 1 / 2 the 16 x 4 split
     float2 *d_gamma_snap = nullptr;                  // Gamma snapshot (allocated on first use)
+    // ---- shards (ptycho_plan_shard): the subdomains of rank `rank` of `world`
+    std::vector<int32_t> global_j;   // global index of each of the plan's frames
+    std::vector<int32_t> owner;      // D: owning rank of each subdomain (empty: not a shard)
+    int32_t rank = 0, world = 1;
+    struct Halo {                    // messages to / from one peer
+        int64_t send_n = 0, recv_n = 0;
+        int32_t send_rows = 0, recv_rows = 0;
+        od2p::HaloRow *d_send = nullptr, *d_recv = nullptr;
+    };
+    std::vector<Halo> halo;          // by peer rank
     // ---- every device allocation, freed by ptycho_plan_destroy
     std::vector<void *> owned;
 };
@@ -304,6 +321,9 @@ int launch_init_state(ptycho_plan_s *p, const float2 *u0, const float2 *w0, cuda
 int launch_illumination(ptycho_plan_s *p, cudaStream_t s);
 int launch_q_from_slots(const ptycho_plan_s *p, float2 *dst, cudaStream_t s);
 int launch_merge(const ptycho_plan_s *p, float2 *out, cudaStream_t s);
+// copy the rows of a halo message between the plan's current state and msg
+int launch_halo_copy(const ptycho_plan_s *p, const HaloRow *rows, int n_rows, float2 *msg, bool pack,
+                     cudaStream_t s);
 int launch_prox(const float2 *y, const float *f, float2 *z, int64_t n, float eps, float lam,
                 cudaStream_t s);
 

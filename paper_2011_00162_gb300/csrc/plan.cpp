@@ -373,6 +373,84 @@ int apply_launch(ptycho_plan_s *p, int variant, int blocks_per_sm, cudaStream_t 
 }  // namespace
 }  // namespace od2p
 
+namespace od2p {
+
+int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev, const int32_t *owner,
+               int32_t rank, ptycho_stream_t stream);
+
+// Halo messages of a shard, one per peer and direction: for every ordered pair
+// (e, d) in pair order with owner[e] = sender and owner[d] = receiver, the rows
+// of u_e on Omega_e n Omega_d, then Lambda_{e,d}; blind, then W_e and Delta_e of
+// every subdomain e the sender owns, e ascending.  Stored as row copies
+// (array, length, offset in the array, offset in the message).
+void halo_rows(const ptycho_plan_s *p, int sender, int receiver, std::vector<HaloRow> &rows, int64_t &n)
+{
+    rows.clear();
+    n = 0;
+    for (int k = 0; k < p->P; ++k) {
+        const int e = p->pair[2 * k], d = p->pair[2 * k + 1];
+        if (p->owner[e] != sender || p->owner[d] != receiver) continue;
+        const int32_t *R = &p->rect[4 * e], *Pr = &p->pair_rect[4 * k];
+        const int pitch = R[3] - R[1], cols = Pr[3] - Pr[1];
+        for (int r = Pr[0]; r < Pr[2]; ++r) {
+            rows.push_back(HaloRow{0, cols, p->u_off[e] + (int64_t)(r - R[0]) * pitch + (Pr[1] - R[1]), n});
+            n += cols;
+        }
+        for (int r = 0; r < Pr[2] - Pr[0]; ++r) {
+            rows.push_back(HaloRow{1, cols, p->lam_off[k] + (int64_t)r * cols, n});
+            n += cols;
+        }
+    }
+    if (p->blind)
+        for (int e = 0; e < p->D; ++e)
+            if (p->owner[e] == sender) {
+                rows.push_back(HaloRow{2, p->MM, (int64_t)e * p->MM, n});
+                n += p->MM;
+                rows.push_back(HaloRow{3, p->MM, (int64_t)e * p->MM, n});
+                n += p->MM;
+            }
+}
+
+int build_halo_tables(ptycho_plan_s *p, cudaStream_t s)
+{
+    int world = 0;
+    for (int d = 0; d < p->D; ++d) world = std::max(world, p->owner[d] + 1);
+    p->world = world;
+    p->halo.assign(world, ptycho_plan_s::Halo{});
+    std::vector<HaloRow> rows;
+    for (int q = 0; q < world; ++q) {
+        if (q == p->rank) continue;
+        ptycho_plan_s::Halo &h = p->halo[q];
+        halo_rows(p, p->rank, q, rows, h.send_n);
+        h.send_rows = (int32_t)rows.size();
+        if (int rc = upload(&h.d_send, rows, p->owned, s)) return rc;
+        halo_rows(p, q, p->rank, rows, h.recv_n);
+        h.recv_rows = (int32_t)rows.size();
+        if (int rc = upload(&h.d_recv, rows, p->owned, s)) return rc;
+    }
+    return PTYCHO_OK;
+}
+
+// Checks of a problem description shared by plans, shards and ptycho_decompose.
+int check_geometry(const ptycho_geometry *g)
+{
+    if (!g || !g->offsets_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL geometry or offsets");
+    if (!supported_m(g->m)) return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
+    if (g->n_frames < 1 || g->img_h < g->m || g->img_w < g->m)
+        return fail(PTYCHO_ERR_INVALID_ARG, "need n_frames >= 1 and an image at least m x m");
+    if (g->sub_rows < 1 || g->sub_cols < 1 || g->sub_rows > g->img_h || g->sub_cols > g->img_w ||
+        g->overlap_px < 0)
+        return fail(PTYCHO_ERR_INVALID_ARG, "bad subdomain grid or overlap");
+    for (int j = 0; j < g->n_frames; ++j) {
+        const int r0 = g->offsets_host[2 * j], c0 = g->offsets_host[2 * j + 1];
+        if (r0 < 0 || c0 < 0 || r0 > g->img_h - g->m || c0 > g->img_w - g->m)
+            return fail(PTYCHO_ERR_INVALID_ARG, "offset of frame " + std::to_string(j) + " out of range");
+    }
+    return PTYCHO_OK;
+}
+
+}  // namespace od2p
+
 using namespace od2p;
 
 extern "C" {
@@ -388,6 +466,12 @@ int ptycho_release_cached_memory(void)
     OD2P_CUDA(cudaDeviceSynchronize());
     OD2P_CUDA(cudaMemPoolTrimTo(pool, 0));
     return PTYCHO_OK;
+}
+
+int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev,
+                ptycho_stream_t stream)
+{
+    return build_plan(out, g, f_dev, nullptr, 0, stream);
 }
 
 int ptycho_plan_destroy(ptycho_plan_t *plan)
@@ -406,241 +490,73 @@ int ptycho_plan_destroy(ptycho_plan_t *plan)
     return PTYCHO_OK;
 }
 
-int ptycho_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev,
-                ptycho_stream_t stream)
+int ptycho_decompose(const ptycho_geometry *g, int32_t *frame_sub_host, int32_t *rect_host)
+{
+    if (int rc = check_geometry(g)) return rc;
+    std::vector<int32_t> offs(g->offsets_host, g->offsets_host + 2 * g->n_frames);
+    Layout L = decompose(g->img_h, g->img_w, g->m, offs, g->sub_rows, g->sub_cols, g->overlap_px);
+    if (frame_sub_host) std::memcpy(frame_sub_host, L.frame_sub.data(), sizeof(int32_t) * g->n_frames);
+    if (rect_host) std::memcpy(rect_host, L.rect.data(), sizeof(int32_t) * L.rect.size());
+    return PTYCHO_OK;
+}
+
+int ptycho_plan_shard(ptycho_plan_t **out, const ptycho_geometry *g, const int32_t *owner_host, int32_t rank,
+                      const float *f_dev, ptycho_stream_t stream)
 {
     if (!out) return fail(PTYCHO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (!g || !f_dev || !g->offsets_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL geometry, f or offsets");
-    if (!supported_m(g->m)) return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
-    if (g->n_frames < 1 || g->img_h < g->m || g->img_w < g->m)
-        return fail(PTYCHO_ERR_INVALID_ARG, "need n_frames >= 1 and an image at least m x m");
-    if ((int64_t)g->img_h * g->img_w >= (1LL << 31))
-        return fail(PTYCHO_ERR_UNSUPPORTED, "image larger than 2^31 pixels");
-    if (g->sub_rows < 1 || g->sub_cols < 1 || g->sub_rows > g->img_h || g->sub_cols > g->img_w ||
-        g->overlap_px < 0)
-        return fail(PTYCHO_ERR_INVALID_ARG, "bad subdomain grid or overlap");
-    if (!(g->eps > 0.f && g->eps < 1.f)) return fail(PTYCHO_ERR_INVALID_ARG, "eps must be in (0, 1)");
-    if (!(g->eta > 0.f) || !(g->r >= 0.f) || !std::isfinite(g->eta) || !std::isfinite(g->r))
-        return fail(PTYCHO_ERR_INVALID_ARG, "need eta > 0 and r >= 0");
-    if (g->blind && (!(g->mu > 0.f) || !(g->gamma >= 0.f)))
-        return fail(PTYCHO_ERR_INVALID_ARG, "blind plans need mu > 0 and gamma >= 0");
-    const int J = g->n_frames, m = g->m;
-    for (int j = 0; j < J; ++j) {
-        const int r0 = g->offsets_host[2 * j], c0 = g->offsets_host[2 * j + 1];
-        if (r0 < 0 || c0 < 0 || r0 > g->img_h - m || c0 > g->img_w - m)
-            return fail(PTYCHO_ERR_INVALID_ARG, "offset of frame " + std::to_string(j) + " out of range");
+    if (int rc = check_geometry(g)) return rc;
+    if (!owner_host) return fail(PTYCHO_ERR_INVALID_ARG, "owner is NULL");
+    const int D = g->sub_rows * g->sub_cols;
+    bool mine = false;
+    for (int d = 0; d < D; ++d) {
+        if (owner_host[d] < 0 || owner_host[d] >= D) return fail(PTYCHO_ERR_INVALID_ARG, "owner out of range");
+        mine = mine || owner_host[d] == rank;
     }
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (rank < 0 || !mine) return fail(PTYCHO_ERR_INVALID_ARG, "rank owns no subdomain");
+    return build_plan(out, g, f_dev, owner_host, rank, stream);
+}
 
-    auto *p = new (std::nothrow) ptycho_plan_s();
-    if (!p) return fail(PTYCHO_ERR_OOM, "host allocation failed");
-    auto bail = [&](int rc) {
-        ptycho_plan_destroy(p);
-        return rc;
-    };
-    p->H = g->img_h;
-    p->W = g->img_w;
-    p->M = m;
-    p->MM = m * m;
-    p->J = J;
-    p->sub_rows = g->sub_rows;
-    p->sub_cols = g->sub_cols;
-    p->overlap_px = g->overlap_px;
-    p->eps = g->eps;
-    p->eta = g->eta;
-    p->r = g->r;
-    p->mu = g->mu;
-    p->gamma = g->gamma;
-    p->blind = g->blind ? 1 : 0;
-    p->offs.assign(g->offsets_host, g->offsets_host + 2 * J);
-
-    Layout L = decompose(p->H, p->W, m, p->offs, p->sub_rows, p->sub_cols, p->overlap_px);
-    p->D = p->sub_rows * p->sub_cols;
-    p->P = (int32_t)L.pair.size() / 2;
-    p->frame_sub = L.frame_sub;
-    p->rect = L.rect;
-    p->pair = L.pair;
-    p->pair_rect = L.pair_rect;
-    p->u_off.assign(p->D + 1, 0);
-    for (int d = 0; d < p->D; ++d)
-        p->u_off[d + 1] = p->u_off[d] + (int64_t)(p->rect[4 * d + 2] - p->rect[4 * d]) *
-                                            (p->rect[4 * d + 3] - p->rect[4 * d + 1]);
-    p->lam_off.assign(p->P + 1, 0);
-    for (int k = 0; k < p->P; ++k)
-        p->lam_off[k + 1] = p->lam_off[k] + (int64_t)(p->pair_rect[4 * k + 2] - p->pair_rect[4 * k]) *
-                                                (p->pair_rect[4 * k + 3] - p->pair_rect[4 * k + 1]);
-    p->u_len = p->u_off[p->D];
-    p->lam_len = p->lam_off[p->P];
-    // kernels index u, Lambda and the frame stacks with 32-bit integers
-    if (p->u_len >= (1LL << 31) || p->lam_len >= (1LL << 31) || (int64_t)J * p->MM >= (1LL << 31))
-        return bail(fail(PTYCHO_ERR_UNSUPPORTED, "subdomain, overlap or frame storage exceeds 2^31 elements"));
-
-    std::vector<int32_t> frame_base(J), frame_pitch(J), img_base(J), img_pitch(J, p->W);
-    std::vector<std::vector<int32_t>> sub_frames(p->D), all_frames(1);
-    for (int j = 0; j < J; ++j) {
-        const int d = p->frame_sub[j];
-        const int32_t *R = &p->rect[4 * d];
-        frame_pitch[j] = R[3] - R[1];
-        frame_base[j] = (int32_t)(p->u_off[d] + (int64_t)(p->offs[2 * j] - R[0]) * frame_pitch[j] +
-                                  (p->offs[2 * j + 1] - R[1]));
-        img_base[j] = p->offs[2 * j] * p->W + p->offs[2 * j + 1];
-        sub_frames[d].push_back(j);
-        all_frames[0].push_back(j);
-    }
-    std::vector<int32_t> nbr_ptr(p->D + 1, 0), nbr;
-    {
-        std::vector<int> pair_of((size_t)p->D * p->D, -1);
-        for (int k = 0; k < p->P; ++k) pair_of[(size_t)p->pair[2 * k] * p->D + p->pair[2 * k + 1]] = k;
-        for (int d = 0; d < p->D; ++d) {
-            for (int e = 0; e < p->D; ++e) {
-                const int kde = pair_of[(size_t)d * p->D + e];
-                if (kde < 0) continue;
-                nbr.insert(nbr.end(), {e, kde, pair_of[(size_t)e * p->D + d]});
-            }
-            nbr_ptr[d + 1] = (int32_t)(nbr.size() / 3);
-        }
-    }
-    std::vector<NbrInfo> nbr_info(nbr.size() / 3);
-    for (int d = 0; d < p->D; ++d)
-        for (int i = nbr_ptr[d]; i < nbr_ptr[d + 1]; ++i) {
-            const int e = nbr[3 * i], kde = nbr[3 * i + 1], ked = nbr[3 * i + 2];
-            const int32_t *Re = &p->rect[4 * e], *Pr = &p->pair_rect[4 * kde];
-            nbr_info[i] = NbrInfo{Re[0], Re[1], Re[2], Re[3], (int32_t)p->u_off[e], Re[3] - Re[1],
-                                  Pr[0], Pr[1], Pr[3] - Pr[1], (int32_t)p->lam_off[kde],
-                                  (int32_t)p->lam_off[ked], d < e ? 1 : 0};
-        }
-    HostTiles st = make_tiles(p->D, p->rect, sub_frames, p->offs, m);
-    // neighbours of each subdomain tile whose rectangle meets the tile
-    std::vector<int32_t> tile_nbr_ptr(1, 0);
-    std::vector<NbrInfo> tile_nbr;
-    for (const Tile &t : st.tiles) {
-        const int32_t *R = &p->rect[4 * t.reg];
-        const int r0 = R[0] + t.r0, c0 = R[1] + t.c0;
-        const int r1 = std::min(r0 + TILE_H, R[2]), c1 = std::min(c0 + TILE_W, R[3]);
-        for (int i = nbr_ptr[t.reg]; i < nbr_ptr[t.reg + 1]; ++i) {
-            const NbrInfo &nb = nbr_info[i];
-            if (nb.r0 < r1 && r0 < nb.r1 && nb.c0 < c1 && c0 < nb.c1) tile_nbr.push_back(nb);
-        }
-        tile_nbr_ptr.push_back((int32_t)tile_nbr.size());
-    }
-    std::vector<TileInfo> tile_info;
-    for (size_t t = 0; t < st.tiles.size(); ++t) {
-        const Tile &T = st.tiles[t];
-        const int32_t *R = &p->rect[4 * T.reg];
-        const int wd = R[3] - R[1], hd = R[2] - R[0];
-        tile_info.push_back(TileInfo{(int32_t)(p->u_off[T.reg] + (int64_t)T.r0 * wd + T.c0), wd,
-                                     std::min(TILE_H, hd - T.r0), std::min(TILE_W, wd - T.c0), R[0] + T.r0,
-                                     R[1] + T.c0, tile_nbr_ptr[t], tile_nbr_ptr[t + 1] - tile_nbr_ptr[t],
-                                     st.ptr[t], st.ptr[t + 1] - st.ptr[t], T.reg, R[2]});
-    }
-    std::vector<int32_t> img_rect = {0, 0, p->H, p->W};
-    HostTiles it = make_tiles(1, img_rect, all_frames, p->offs, m);
-
-    auto &own = p->owned;
-    const size_t JMM = (size_t)J * p->MM;
-    int rc;
-    if ((rc = upload(&p->d_offs, p->offs, own, s)) || (rc = upload(&p->d_frame_sub, p->frame_sub, own, s)) ||
-        (rc = upload(&p->d_frame_base, frame_base, own, s)) ||
-        (rc = upload(&p->d_frame_pitch, frame_pitch, own, s)) || (rc = upload(&p->d_img_base, img_base, own, s)) ||
-        (rc = upload(&p->d_img_pitch, img_pitch, own, s)) ||
-        (rc = upload(&p->d_rect, p->rect, own, s)) || (rc = upload(&p->d_nbr_ptr, nbr_ptr, own, s)) ||
-        (rc = upload(&p->d_nbr, nbr, own, s)) || (rc = upload(&p->d_pair_rect, p->pair_rect, own, s)) ||
-        (rc = upload(&p->d_pair, p->pair, own, s)) ||
-        (rc = upload(&p->d_nbr_info, nbr_info, own, s)) ||
-        (rc = upload(&p->d_u_off, p->u_off, own, s)) || (rc = upload(&p->d_lam_off, p->lam_off, own, s)) ||
-        (rc = upload_tiles(p->sub_tiles, st, own, s)) || (rc = upload_tiles(p->img_tiles, it, own, s)) ||
-        (rc = upload(&p->sub_tiles.nbr_ptr, tile_nbr_ptr, own, s)) ||
-        (rc = upload(&p->sub_tiles.nbr, tile_nbr, own, s)) ||
-        (rc = upload(&p->sub_tiles.info, tile_info, own, s)) ||
-        (rc = upload_groups(p->sub_groups, sub_frames, own, s)) ||
-        (rc = upload_groups(p->img_groups, all_frames, own, s)))
-        return bail(rc);
-    // twiddles exp(-2 pi i k / m), computed in double and rounded once
-    std::vector<float2> tw(m);
-    for (int k = 0; k < m; ++k) {
-        const double a = -2.0 * 3.14159265358979323846 * (double)k / (double)m;
-        tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    if ((rc = upload(&p->d_tw, tw, own, s))) return bail(rc);
-    if (p->blind && g->fourier_support_host) {
-        std::vector<float> mask(p->MM);
-        for (int k = 0; k < p->MM; ++k) mask[k] = g->fourier_support_host[k] ? 1.f : 0.f;
-        p->has_mask = true;
-        if ((rc = upload(&p->d_mask, mask, own, s))) return bail(rc);
-    }
-    p->n_rf_parts = rf_parts(m, J, 0);
-    // RF partials sized for either launch shape of the frame update
-    const int rf_cap = std::max(rf_parts(m, J, 0), rf_parts(m, J, 1));
-    if ((rc = prepare_kernels(m)) ||
-        (rc = frame_update_grid(m, 0, frame_groups(m, J, 0), 0, &p->n_k1_blocks, nullptr)))
-        return bail(rc);
-    p->n_loss_blocks = m == 256 ? J * 16 : (J + frames_per_block(m) - 1) / frames_per_block(m);
-    const int n_chunks = std::max(p->sub_groups.n_chunks, p->img_groups.n_chunks);
-    if ((rc = dev_alloc(&p->d_sqrtf, JMM, own, s)) || (rc = dev_alloc(&p->d_gamma, JMM, own, s)) ||
-        (rc = dev_alloc(&p->d_q, JMM, own, s)) || (rc = dev_alloc(&p->d_u[0], p->u_len, own, s)) ||
-        (rc = dev_alloc(&p->d_u[1], p->u_len, own, s)) || (rc = dev_alloc(&p->d_nrm, p->u_len, own, s)) ||
-        (rc = dev_alloc(&p->d_lam[0], p->lam_len, own, s)) ||
-        (rc = dev_alloc(&p->d_lam[1], p->lam_len, own, s)) || (rc = dev_alloc(&p->d_w, p->MM, own, s)) ||
-        (rc = dev_alloc(&p->d_wnew, p->MM, own, s)) ||
-        (rc = dev_alloc(&p->d_probe_part, (size_t)n_chunks * p->MM, own, s)) ||
-        (rc = dev_alloc(&p->d_probe_part_n, (size_t)n_chunks * p->MM, own, s)) ||
-        (rc = dev_alloc(&p->d_rf_part, rf_cap, own, s)) ||
-        (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own, s)) ||
-        (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own, s)) ||
-        (rc = dev_alloc(&p->d_metrics, 5, own, s)) || (rc = dev_alloc(&p->d_err, 1, own, s)) ||
-        (rc = dev_alloc(&p->d_rc_part, (size_t)(p->P + 1) * 64, own, s)) ||
-        (rc = dev_alloc(&p->d_snr_part, 2 * 152 * 4, own, s)) || (rc = dev_alloc(&p->d_snr, 3, own, s)) ||
-        (rc = dev_alloc(&p->d_opn, 2, own, s)) || (rc = dev_alloc(&p->d_until, 4, own, s)))
-        return bail(rc);
-    if (p->blind) {
-        if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own, s)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own, s)))
-            return bail(rc);
-    }
-    if (m == 256 && (rc = dev_alloc(&p->d_T, (size_t)WAVE_256 * p->MM, own, s))) return bail(rc);
-    if (!p->blind) {
-        // gather slots: ranks and counts on the device (one pass over the tile
-        // lists), then the slot array sized by the largest count
-        int32_t *d_setup = nullptr, h_setup[2] = {0, 0};
-        if ((rc = dev_alloc(&p->d_rank, JMM, own, s)) || (rc = dev_alloc(&p->d_cnt, (size_t)p->u_len, own, s)) ||
-            (rc = dev_alloc(&d_setup, 2, own, s)))
-            return bail(rc);
-        cudaError_t e1;
-        if ((e1 = cudaMemsetAsync(p->d_cnt, 0, (size_t)p->u_len, s)) != cudaSuccess ||
-            (e1 = cudaMemsetAsync(d_setup, 0, 2 * sizeof(int32_t), s)) != cudaSuccess)
-            return bail(cuda_fail(e1, "cudaMemsetAsync"));
-        if ((rc = launch_slot_rank(p, d_setup, s))) return bail(rc);
-        if ((e1 = cudaMemcpyAsync(h_setup, d_setup, sizeof(h_setup), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-            (e1 = cudaStreamSynchronize(s)) != cudaSuccess)
-            return bail(cuda_fail(e1, "slot ranks"));
-        p->slot_k = h_setup[1];
-        p->slots = !h_setup[0] && (int64_t)p->slot_k * p->u_len < (1LL << 32);
-        if (p->slots && (rc = dev_alloc(&p->d_slot, (size_t)std::max(p->slot_k, 1) * p->u_len, own, s)))
-            return bail(rc);
-    }
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(p->d_metrics, 0, 5 * sizeof(double), s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * rf_cap, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->d_re_part, 0, sizeof(float) * 2 * p->sub_tiles.n_tiles, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->d_w, 0, sizeof(float2) * p->MM, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), s)) != cudaSuccess)
-        return bail(cuda_fail(e, "cudaMemsetAsync"));
-    // kernel argument tables (buffer pointers are fixed from here on)
-    fill_frame_args(p, p->h_fargs);
-    fill_sub_args(p, p->h_sargs);
-    {
-        std::vector<FrameArgs> fa(p->h_fargs, p->h_fargs + 2);
-        std::vector<SubArgs> sa(p->h_sargs, p->h_sargs + 2);
-        if ((rc = upload(&p->d_fargs, fa, own, s)) || (rc = upload(&p->d_sargs, sa, own, s))) return bail(rc);
-    }
-    if ((rc = launch_ingest_f(p, f_dev, s)) || (rc = launch_sum_sqrtf(p, s))) return bail(rc);
-    // Step 0 with u = 1 and a zero probe until od2p_init
-    if ((rc = launch_init_state(p, nullptr, p->d_w, s))) return bail(rc);
-    if ((e = cudaMemsetAsync(p->d_gamma, 0, sizeof(float2) * JMM, s)) != cudaSuccess)
-        return bail(cuda_fail(e, "cudaMemsetAsync"));
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(cuda_fail(e, "cudaStreamSynchronize"));
-    *out = p;
+int ptycho_plan_frames(const ptycho_plan_t *plan, int32_t *n_frames, int32_t *global_index_host)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (n_frames) *n_frames = plan->J;
+    if (global_index_host) std::memcpy(global_index_host, plan->global_j.data(), sizeof(int32_t) * plan->J);
     return PTYCHO_OK;
+}
+
+static int halo_peer(const ptycho_plan_t *plan, int32_t peer)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (plan->owner.empty()) return fail(PTYCHO_ERR_STATE, "not a shard plan");
+    if (peer < 0 || peer >= plan->world || peer == plan->rank) return fail(PTYCHO_ERR_INVALID_ARG, "bad peer rank");
+    return PTYCHO_OK;
+}
+
+int od2p_halo_size(const ptycho_plan_t *plan, int32_t peer, int64_t *send_elems, int64_t *recv_elems)
+{
+    if (int rc = halo_peer(plan, peer)) return rc;
+    if (send_elems) *send_elems = plan->halo[peer].send_n;
+    if (recv_elems) *recv_elems = plan->halo[peer].recv_n;
+    return PTYCHO_OK;
+}
+
+int od2p_halo_pack(const ptycho_plan_t *plan, int32_t peer, ptycho_c32 *send_dev, ptycho_stream_t stream)
+{
+    if (int rc = halo_peer(plan, peer)) return rc;
+    const auto &h = plan->halo[peer];
+    if (h.send_n && !send_dev) return fail(PTYCHO_ERR_INVALID_ARG, "send buffer is NULL");
+    return launch_halo_copy(plan, h.d_send, h.send_rows, reinterpret_cast<float2 *>(send_dev), true,
+                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+int od2p_halo_unpack(ptycho_plan_t *plan, int32_t peer, const ptycho_c32 *recv_dev, ptycho_stream_t stream)
+{
+    if (int rc = halo_peer(plan, peer)) return rc;
+    const auto &h = plan->halo[peer];
+    if (h.recv_n && !recv_dev) return fail(PTYCHO_ERR_INVALID_ARG, "receive buffer is NULL");
+    return launch_halo_copy(plan, h.d_recv, h.recv_rows, const_cast<float2 *>(reinterpret_cast<const float2 *>(recv_dev)),
+                            false, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int ptycho_plan_dims(const ptycho_plan_t *plan, int32_t *n_sub, int32_t *n_pairs, int64_t *u_len,
@@ -1296,3 +1212,271 @@ int ptycho_batch_iterate(ptycho_batch_t *b, int32_t n_iter, ptycho_stream_t stre
 }
 
 }  // extern "C"
+
+namespace od2p {
+
+// A plan over the subdomains d with owner[d] == rank (see od2p.h); owner == null: all of them.
+int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev, const int32_t *owner,
+               int32_t rank, ptycho_stream_t stream)
+{
+    if (!out) return fail(PTYCHO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g || !f_dev || !g->offsets_host) return fail(PTYCHO_ERR_INVALID_ARG, "NULL geometry, f or offsets");
+    if (!supported_m(g->m)) return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
+    if (g->n_frames < 1 || g->img_h < g->m || g->img_w < g->m)
+        return fail(PTYCHO_ERR_INVALID_ARG, "need n_frames >= 1 and an image at least m x m");
+    if ((int64_t)g->img_h * g->img_w >= (1LL << 31))
+        return fail(PTYCHO_ERR_UNSUPPORTED, "image larger than 2^31 pixels");
+    if (g->sub_rows < 1 || g->sub_cols < 1 || g->sub_rows > g->img_h || g->sub_cols > g->img_w ||
+        g->overlap_px < 0)
+        return fail(PTYCHO_ERR_INVALID_ARG, "bad subdomain grid or overlap");
+    if (!(g->eps > 0.f && g->eps < 1.f)) return fail(PTYCHO_ERR_INVALID_ARG, "eps must be in (0, 1)");
+    if (!(g->eta > 0.f) || !(g->r >= 0.f) || !std::isfinite(g->eta) || !std::isfinite(g->r))
+        return fail(PTYCHO_ERR_INVALID_ARG, "need eta > 0 and r >= 0");
+    if (g->blind && (!(g->mu > 0.f) || !(g->gamma >= 0.f)))
+        return fail(PTYCHO_ERR_INVALID_ARG, "blind plans need mu > 0 and gamma >= 0");
+    const int m = g->m;
+    for (int j = 0; j < g->n_frames; ++j) {
+        const int r0 = g->offsets_host[2 * j], c0 = g->offsets_host[2 * j + 1];
+        if (r0 < 0 || c0 < 0 || r0 > g->img_h - m || c0 > g->img_w - m)
+            return fail(PTYCHO_ERR_INVALID_ARG, "offset of frame " + std::to_string(j) + " out of range");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the decomposition always comes from every frame; a shard keeps the frames
+    // of its own subdomains (ascending global index)
+    std::vector<int32_t> all_offs(g->offsets_host, g->offsets_host + 2 * g->n_frames);
+    Layout L = decompose(g->img_h, g->img_w, m, all_offs, g->sub_rows, g->sub_cols, g->overlap_px);
+    const int D_all = g->sub_rows * g->sub_cols;
+    std::vector<int32_t> sel;
+    for (int j = 0; j < g->n_frames; ++j)
+        if (!owner || owner[L.frame_sub[j]] == rank) sel.push_back(j);
+    if (sel.empty()) return fail(PTYCHO_ERR_INVALID_ARG, "the shard's subdomains hold no frames");
+    const int J = (int)sel.size();
+
+    auto *p = new (std::nothrow) ptycho_plan_s();
+    if (!p) return fail(PTYCHO_ERR_OOM, "host allocation failed");
+    auto bail = [&](int rc) {
+        ptycho_plan_destroy(p);
+        return rc;
+    };
+    p->H = g->img_h;
+    p->W = g->img_w;
+    p->M = m;
+    p->MM = m * m;
+    p->J = J;
+    p->sub_rows = g->sub_rows;
+    p->sub_cols = g->sub_cols;
+    p->overlap_px = g->overlap_px;
+    p->eps = g->eps;
+    p->eta = g->eta;
+    p->r = g->r;
+    p->mu = g->mu;
+    p->gamma = g->gamma;
+    p->blind = g->blind ? 1 : 0;
+    p->offs.resize(2 * (size_t)J);
+    p->frame_sub.resize(J);
+    p->global_j = sel;
+    for (int i = 0; i < J; ++i) {
+        p->offs[2 * i] = all_offs[2 * sel[i]];
+        p->offs[2 * i + 1] = all_offs[2 * sel[i] + 1];
+        p->frame_sub[i] = L.frame_sub[sel[i]];
+    }
+    p->D = D_all;
+    p->P = (int32_t)L.pair.size() / 2;
+    if (owner) {
+        p->owner.assign(owner, owner + D_all);
+        p->rank = rank;
+    }
+    p->rect = L.rect;
+    p->pair = L.pair;
+    p->pair_rect = L.pair_rect;
+    p->u_off.assign(p->D + 1, 0);
+    for (int d = 0; d < p->D; ++d)
+        p->u_off[d + 1] = p->u_off[d] + (int64_t)(p->rect[4 * d + 2] - p->rect[4 * d]) *
+                                            (p->rect[4 * d + 3] - p->rect[4 * d + 1]);
+    p->lam_off.assign(p->P + 1, 0);
+    for (int k = 0; k < p->P; ++k)
+        p->lam_off[k + 1] = p->lam_off[k] + (int64_t)(p->pair_rect[4 * k + 2] - p->pair_rect[4 * k]) *
+                                                (p->pair_rect[4 * k + 3] - p->pair_rect[4 * k + 1]);
+    p->u_len = p->u_off[p->D];
+    p->lam_len = p->lam_off[p->P];
+    // kernels index u, Lambda and the frame stacks with 32-bit integers
+    if (p->u_len >= (1LL << 31) || p->lam_len >= (1LL << 31) || (int64_t)J * p->MM >= (1LL << 31))
+        return bail(fail(PTYCHO_ERR_UNSUPPORTED, "subdomain, overlap or frame storage exceeds 2^31 elements"));
+
+    std::vector<int32_t> frame_base(J), frame_pitch(J), img_base(J), img_pitch(J, p->W);
+    std::vector<std::vector<int32_t>> sub_frames(p->D), all_frames(1);
+    for (int j = 0; j < J; ++j) {
+        const int d = p->frame_sub[j];
+        const int32_t *R = &p->rect[4 * d];
+        frame_pitch[j] = R[3] - R[1];
+        frame_base[j] = (int32_t)(p->u_off[d] + (int64_t)(p->offs[2 * j] - R[0]) * frame_pitch[j] +
+                                  (p->offs[2 * j + 1] - R[1]));
+        img_base[j] = p->offs[2 * j] * p->W + p->offs[2 * j + 1];
+        sub_frames[d].push_back(j);
+        all_frames[0].push_back(j);
+    }
+    std::vector<int32_t> nbr_ptr(p->D + 1, 0), nbr;
+    {
+        std::vector<int> pair_of((size_t)p->D * p->D, -1);
+        for (int k = 0; k < p->P; ++k) pair_of[(size_t)p->pair[2 * k] * p->D + p->pair[2 * k + 1]] = k;
+        for (int d = 0; d < p->D; ++d) {
+            for (int e = 0; e < p->D; ++e) {
+                const int kde = pair_of[(size_t)d * p->D + e];
+                if (kde < 0) continue;
+                nbr.insert(nbr.end(), {e, kde, pair_of[(size_t)e * p->D + d]});
+            }
+            nbr_ptr[d + 1] = (int32_t)(nbr.size() / 3);
+        }
+    }
+    std::vector<NbrInfo> nbr_info(nbr.size() / 3);
+    for (int d = 0; d < p->D; ++d)
+        for (int i = nbr_ptr[d]; i < nbr_ptr[d + 1]; ++i) {
+            const int e = nbr[3 * i], kde = nbr[3 * i + 1], ked = nbr[3 * i + 2];
+            const int32_t *Re = &p->rect[4 * e], *Pr = &p->pair_rect[4 * kde];
+            nbr_info[i] = NbrInfo{Re[0], Re[1], Re[2], Re[3], (int32_t)p->u_off[e], Re[3] - Re[1],
+                                  Pr[0], Pr[1], Pr[3] - Pr[1], (int32_t)p->lam_off[kde],
+                                  (int32_t)p->lam_off[ked], d < e ? 1 : 0};
+        }
+    // subdomain tiles: a shard tiles only its own subdomains (the others' rectangles
+    // hold halo copies that the subdomain update reads but never writes)
+    std::vector<int32_t> tile_rect = p->rect;
+    if (owner)
+        for (int d = 0; d < p->D; ++d)
+            if (owner[d] != rank) tile_rect[4 * d + 2] = tile_rect[4 * d];
+    HostTiles st = make_tiles(p->D, tile_rect, sub_frames, p->offs, m);
+    // neighbours of each subdomain tile whose rectangle meets the tile
+    std::vector<int32_t> tile_nbr_ptr(1, 0);
+    std::vector<NbrInfo> tile_nbr;
+    for (const Tile &t : st.tiles) {
+        const int32_t *R = &p->rect[4 * t.reg];
+        const int r0 = R[0] + t.r0, c0 = R[1] + t.c0;
+        const int r1 = std::min(r0 + TILE_H, R[2]), c1 = std::min(c0 + TILE_W, R[3]);
+        for (int i = nbr_ptr[t.reg]; i < nbr_ptr[t.reg + 1]; ++i) {
+            const NbrInfo &nb = nbr_info[i];
+            if (nb.r0 < r1 && r0 < nb.r1 && nb.c0 < c1 && c0 < nb.c1) tile_nbr.push_back(nb);
+        }
+        tile_nbr_ptr.push_back((int32_t)tile_nbr.size());
+    }
+    std::vector<TileInfo> tile_info;
+    for (size_t t = 0; t < st.tiles.size(); ++t) {
+        const Tile &T = st.tiles[t];
+        const int32_t *R = &p->rect[4 * T.reg];
+        const int wd = R[3] - R[1], hd = R[2] - R[0];
+        tile_info.push_back(TileInfo{(int32_t)(p->u_off[T.reg] + (int64_t)T.r0 * wd + T.c0), wd,
+                                     std::min(TILE_H, hd - T.r0), std::min(TILE_W, wd - T.c0), R[0] + T.r0,
+                                     R[1] + T.c0, tile_nbr_ptr[t], tile_nbr_ptr[t + 1] - tile_nbr_ptr[t],
+                                     st.ptr[t], st.ptr[t + 1] - st.ptr[t], T.reg, R[2]});
+    }
+    std::vector<int32_t> img_rect = {0, 0, p->H, p->W};
+    HostTiles it = make_tiles(1, img_rect, all_frames, p->offs, m);
+
+    auto &own = p->owned;
+    const size_t JMM = (size_t)J * p->MM;
+    int rc;
+    if ((rc = upload(&p->d_offs, p->offs, own, s)) || (rc = upload(&p->d_frame_sub, p->frame_sub, own, s)) ||
+        (rc = upload(&p->d_frame_base, frame_base, own, s)) ||
+        (rc = upload(&p->d_frame_pitch, frame_pitch, own, s)) || (rc = upload(&p->d_img_base, img_base, own, s)) ||
+        (rc = upload(&p->d_img_pitch, img_pitch, own, s)) ||
+        (rc = upload(&p->d_rect, p->rect, own, s)) || (rc = upload(&p->d_nbr_ptr, nbr_ptr, own, s)) ||
+        (rc = upload(&p->d_nbr, nbr, own, s)) || (rc = upload(&p->d_pair_rect, p->pair_rect, own, s)) ||
+        (rc = upload(&p->d_pair, p->pair, own, s)) ||
+        (rc = upload(&p->d_nbr_info, nbr_info, own, s)) ||
+        (rc = upload(&p->d_u_off, p->u_off, own, s)) || (rc = upload(&p->d_lam_off, p->lam_off, own, s)) ||
+        (rc = upload_tiles(p->sub_tiles, st, own, s)) || (rc = upload_tiles(p->img_tiles, it, own, s)) ||
+        (rc = upload(&p->sub_tiles.nbr_ptr, tile_nbr_ptr, own, s)) ||
+        (rc = upload(&p->sub_tiles.nbr, tile_nbr, own, s)) ||
+        (rc = upload(&p->sub_tiles.info, tile_info, own, s)) ||
+        (rc = upload_groups(p->sub_groups, sub_frames, own, s)) ||
+        (rc = upload_groups(p->img_groups, all_frames, own, s)))
+        return bail(rc);
+    // twiddles exp(-2 pi i k / m), computed in double and rounded once
+    std::vector<float2> tw(m);
+    for (int k = 0; k < m; ++k) {
+        const double a = -2.0 * 3.14159265358979323846 * (double)k / (double)m;
+        tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    if ((rc = upload(&p->d_tw, tw, own, s))) return bail(rc);
+    if (p->blind && g->fourier_support_host) {
+        std::vector<float> mask(p->MM);
+        for (int k = 0; k < p->MM; ++k) mask[k] = g->fourier_support_host[k] ? 1.f : 0.f;
+        p->has_mask = true;
+        if ((rc = upload(&p->d_mask, mask, own, s))) return bail(rc);
+    }
+    p->n_rf_parts = rf_parts(m, J, 0);
+    // RF partials sized for either launch shape of the frame update
+    const int rf_cap = std::max(rf_parts(m, J, 0), rf_parts(m, J, 1));
+    if ((rc = prepare_kernels(m)) ||
+        (rc = frame_update_grid(m, 0, frame_groups(m, J, 0), 0, &p->n_k1_blocks, nullptr)))
+        return bail(rc);
+    p->n_loss_blocks = m == 256 ? J * 16 : (J + frames_per_block(m) - 1) / frames_per_block(m);
+    const int n_chunks = std::max(p->sub_groups.n_chunks, p->img_groups.n_chunks);
+    if ((rc = dev_alloc(&p->d_sqrtf, JMM, own, s)) || (rc = dev_alloc(&p->d_gamma, JMM, own, s)) ||
+        (rc = dev_alloc(&p->d_q, JMM, own, s)) || (rc = dev_alloc(&p->d_u[0], p->u_len, own, s)) ||
+        (rc = dev_alloc(&p->d_u[1], p->u_len, own, s)) || (rc = dev_alloc(&p->d_nrm, p->u_len, own, s)) ||
+        (rc = dev_alloc(&p->d_lam[0], p->lam_len, own, s)) ||
+        (rc = dev_alloc(&p->d_lam[1], p->lam_len, own, s)) || (rc = dev_alloc(&p->d_w, p->MM, own, s)) ||
+        (rc = dev_alloc(&p->d_wnew, p->MM, own, s)) ||
+        (rc = dev_alloc(&p->d_probe_part, (size_t)n_chunks * p->MM, own, s)) ||
+        (rc = dev_alloc(&p->d_probe_part_n, (size_t)n_chunks * p->MM, own, s)) ||
+        (rc = dev_alloc(&p->d_rf_part, rf_cap, own, s)) ||
+        (rc = dev_alloc(&p->d_re_part, 2 * (size_t)p->sub_tiles.n_tiles, own, s)) ||
+        (rc = dev_alloc(&p->d_loss_part, std::max(J, p->n_loss_blocks), own, s)) ||
+        (rc = dev_alloc(&p->d_metrics, 5, own, s)) || (rc = dev_alloc(&p->d_err, 1, own, s)) ||
+        (rc = dev_alloc(&p->d_rc_part, (size_t)(p->P + 1) * 64, own, s)) ||
+        (rc = dev_alloc(&p->d_snr_part, 2 * 152 * 4, own, s)) || (rc = dev_alloc(&p->d_snr, 3, own, s)) ||
+        (rc = dev_alloc(&p->d_opn, 2, own, s)) || (rc = dev_alloc(&p->d_until, 4, own, s)))
+        return bail(rc);
+    if (p->blind) {
+        if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own, s)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own, s)))
+            return bail(rc);
+    }
+    if (m == 256 && (rc = dev_alloc(&p->d_T, (size_t)WAVE_256 * p->MM, own, s))) return bail(rc);
+    if (!p->blind) {
+        // gather slots: ranks and counts on the device (one pass over the tile
+        // lists), then the slot array sized by the largest count
+        int32_t *d_setup = nullptr, h_setup[2] = {0, 0};
+        if ((rc = dev_alloc(&p->d_rank, JMM, own, s)) || (rc = dev_alloc(&p->d_cnt, (size_t)p->u_len, own, s)) ||
+            (rc = dev_alloc(&d_setup, 2, own, s)))
+            return bail(rc);
+        cudaError_t e1;
+        if ((e1 = cudaMemsetAsync(p->d_cnt, 0, (size_t)p->u_len, s)) != cudaSuccess ||
+            (e1 = cudaMemsetAsync(d_setup, 0, 2 * sizeof(int32_t), s)) != cudaSuccess)
+            return bail(cuda_fail(e1, "cudaMemsetAsync"));
+        if ((rc = launch_slot_rank(p, d_setup, s))) return bail(rc);
+        if ((e1 = cudaMemcpyAsync(h_setup, d_setup, sizeof(h_setup), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e1 = cudaStreamSynchronize(s)) != cudaSuccess)
+            return bail(cuda_fail(e1, "slot ranks"));
+        p->slot_k = h_setup[1];
+        p->slots = !h_setup[0] && (int64_t)p->slot_k * p->u_len < (1LL << 32);
+        if (p->slots && (rc = dev_alloc(&p->d_slot, (size_t)std::max(p->slot_k, 1) * p->u_len, own, s)))
+            return bail(rc);
+    }
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->d_metrics, 0, 5 * sizeof(double), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_rf_part, 0, sizeof(float) * rf_cap, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_re_part, 0, sizeof(float) * 2 * p->sub_tiles.n_tiles, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_w, 0, sizeof(float2) * p->MM, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), s)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMemsetAsync"));
+    // kernel argument tables (buffer pointers are fixed from here on)
+    fill_frame_args(p, p->h_fargs);
+    fill_sub_args(p, p->h_sargs);
+    {
+        std::vector<FrameArgs> fa(p->h_fargs, p->h_fargs + 2);
+        std::vector<SubArgs> sa(p->h_sargs, p->h_sargs + 2);
+        if ((rc = upload(&p->d_fargs, fa, own, s)) || (rc = upload(&p->d_sargs, sa, own, s))) return bail(rc);
+    }
+    if ((rc = launch_ingest_f(p, f_dev, s)) || (rc = launch_sum_sqrtf(p, s))) return bail(rc);
+    // Step 0 with u = 1 and a zero probe until od2p_init
+    if ((rc = launch_init_state(p, nullptr, p->d_w, s))) return bail(rc);
+    if ((e = cudaMemsetAsync(p->d_gamma, 0, sizeof(float2) * JMM, s)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMemsetAsync"));
+    if (owner && (rc = build_halo_tables(p, s))) return bail(rc);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(cuda_fail(e, "cudaStreamSynchronize"));
+    *out = p;
+    return PTYCHO_OK;
+}
+
+}  // namespace od2p
+

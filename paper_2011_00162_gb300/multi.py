@@ -168,3 +168,41 @@ def exchange_halos(sched: HaloSchedule, arrays: dict, group=None) -> None:
             req.wait()
     for q, buf in inbox.items():
         sched.unpack(q, buf, arrays)
+
+
+def exchange_shard_halos(plan, group=None) -> None:
+    """One halo exchange of a library shard plan (api.ptycho_plan_shard) over
+    torch.distributed: the library packs each peer's message on the device, the
+    messages cross by isend / irecv (NCCL between GPUs), and the library
+    unpacks what arrived.  Call it before every od2p_iterate(plan, 1)."""
+    from . import api
+    world = max(plan.owner) + 1
+    ops, inbox = [], {}
+    for q in range(world):
+        if q == plan.rank:
+            continue
+        n_send, n_recv = api.od2p_halo_size(plan, q)
+        if n_recv:
+            buf = torch.empty(n_recv, dtype=torch.complex64, device=plan.device)
+            inbox[q] = buf
+            ops.append(dist.P2POp(dist.irecv, torch.view_as_real(buf), q, group))
+        if n_send:
+            ops.append(dist.P2POp(dist.isend, torch.view_as_real(api.od2p_halo_pack(plan, q)), q, group))
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+    for q, buf in inbox.items():
+        api.od2p_halo_unpack(plan, q, buf)
+
+
+def exchange_local(shards) -> None:
+    """The halo exchange among shard plans held by one process (shards[r] is
+    rank r's): every message is packed first, then every message unpacked."""
+    from . import api
+    msgs = {}
+    for a, pa in enumerate(shards):
+        for b in range(len(shards)):
+            if a != b and api.od2p_halo_size(pa, b)[0]:
+                msgs[(a, b)] = api.od2p_halo_pack(pa, b)
+    for (a, b), msg in msgs.items():
+        api.od2p_halo_unpack(shards[b], a, msg)

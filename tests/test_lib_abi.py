@@ -77,3 +77,19 @@ def test_plan_rejects_bad_geometry_before_device_work(lib):
         h = ctypes.c_void_p()
         assert lib.ptycho_plan(ctypes.byref(h), ctypes.byref(g), f, None) == code
         assert not h.value
+
+
+def test_decomposition_on_the_host_equals_the_oracle():
+    """ptycho_decompose runs on the host (no device work): bit-exact against the
+    oracle's decomposition, so ranks can split a problem before any plan exists."""
+    import numpy as np
+
+    import oracle
+    import paper_2011_00162_gb300 as od
+    from paper_2011_00162_gb300 import synth
+    for n, m, step, jit, grid, ov in [(512, 64, 16, 2, (4, 4), 16), (300, 32, 12, 3, (3, 5), 0),
+                                      (96, 16, 6, 1, (3, 3), 8), (4096, 256, 48, 4, (8, 8), 64)]:
+        offs = synth.raster_offsets(n, m, step, jit, seed=5)
+        fs, rect = od.ptycho_decompose(od.Geometry(n, n, m, offs, grid[0], grid[1], ov))
+        fo, ro = oracle.geometry(n, n, m, offs, grid[0], grid[1], ov)
+        assert np.array_equal(fs, fo) and np.array_equal(rect, ro)

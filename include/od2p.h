@@ -459,9 +459,23 @@ int od2p_set_state(ptycho_plan_t *plan, int32_t which, const ptycho_c32 *src_dev
  *      grad_w = sum_j conj(S_j u) o F^* grad g_j,
  * gradients in the d/dRe + i d/dIm convention.  u_dev: img_h x img_w;
  * w_dev: m x m; loss_dev: 1 float; grad_u_dev (img_h x img_w) and grad_w_dev
- * (m x m) may be NULL.  Frame exit waves are recomputed from u and w, never
- * stored (recompute must be 1; 0 is reserved).  Reductions have a fixed order.
- * Uses plan scratch: calls on one plan must not overlap.
+ * (m x m) may be NULL.  One pass over the frames forms each exit wave from u
+ * and w, its transform, g and grad g, and the gradient frame h_j = F^* grad
+ * g_j; the gradients are then gathered from the h_j.  recompute selects where
+ * the h_j live:
+ *   1: in the plan's frame scratch, for this call only (no extra memory; a
+ *      later call recomputes them);
+ *   0: in a plan-owned store of J x m x m complex values (allocated on the
+ *      first such call and kept until the plan is destroyed), together with
+ *      the loss, for a later call with recompute = 2;
+ *   2: no pass over the frames: the loss and the gradients come from the
+ *      store, which must hold the frames of the last recompute = 0 call with
+ *      the same u_dev and w_dev pointers (and unchanged contents: the library
+ *      cannot see writes to them) -- else PTYCHO_ERR_STATE.
+ * Storing trades J x m x m x 8 bytes for one pass over the frames in a later
+ * gradient (the autograd wrapper stores below a size budget and recomputes
+ * above it).  Reductions have a fixed order.  Uses plan scratch: calls on one
+ * plan must not overlap.  Errors: INVALID_ARG, STATE, OOM, CUDA.
  */
 int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c32 *w_dev,
                     float *loss_dev, ptycho_c32 *grad_u_dev, ptycho_c32 *grad_w_dev,

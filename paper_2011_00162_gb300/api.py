@@ -28,7 +28,7 @@ __all__ = [
            "od2p_iterate_until", "od2p_gamma_snapshot", "od2p_frame_residual", "ptycho_plan_set_fft",
            "ptycho_plan_get_fft",
            "PROBE_FMA", "PROBE_SMEM", "ptycho_decompose", "ptycho_plan_shard", "ptycho_plan_frames",
-           "od2p_halo_size", "od2p_halo_pack", "od2p_halo_unpack",
+           "od2p_halo_size", "od2p_halo_pack", "od2p_halo_unpack", "RECOMPUTE", "STORE", "FROM_STORE",
 ]
 
 LAUNCH_VARIANTS = _lib.LAUNCH_VARIANTS
@@ -490,14 +490,18 @@ def od2p_set_state(plan: Plan, which: int, src: torch.Tensor, stream=None) -> No
                                    _stream(stream)))
 
 
+RECOMPUTE, STORE, FROM_STORE = 1, 0, 2  # stagm_loss_grad's recompute argument
+
+
 def stagm_loss_grad(plan: Plan, u: torch.Tensor, w: torch.Tensor, grad_u: bool = True,
-                    grad_w: bool = True, stream=None):
-    """(loss[1] float32, grad_u or None, grad_w or None) on the current stream."""
+                    grad_w: bool = True, stream=None, recompute: int = RECOMPUTE):
+    """(loss[1] float32, grad_u or None, grad_w or None) on the current stream;
+    recompute = RECOMPUTE, STORE or FROM_STORE as in include/od2p.h."""
     g = plan.geom
     loss = torch.empty(1, dtype=torch.float32, device=u.device)
     gu = _c64((g.img_h, g.img_w), u.device) if grad_u else None
     gw = _c64((g.m, g.m), u.device) if grad_w else None
     check(plan._lib.stagm_loss_grad(plan.handle, _ptr(u, torch.complex64, "u"), _ptr(w, torch.complex64, "w"),
                                     _ptr(loss, torch.float32, "loss"), _ptr(gu, torch.complex64, "grad_u"),
-                                    _ptr(gw, torch.complex64, "grad_w"), 1, _stream(stream)))
+                                    _ptr(gw, torch.complex64, "grad_w"), int(recompute), _stream(stream)))
     return loss, gu, gw

@@ -770,7 +770,7 @@ int ifft_256(const ptycho_plan_s *p, const float2 *in, float2 *out, cudaStream_t
     return run_waves(P, p->J, WAVE_256, s);
 }
 
-int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s)
+int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, float2 *h_out)
 {
     Pipeline P = base_pipeline(p);
     P.do_a = P.do_c = true;
@@ -780,7 +780,7 @@ int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s)
     P.A.w = w;
     P.B.mode = B_LOSS;
     P.B.part = p->d_loss_part;
-    P.C.out = p->d_q;
+    P.C.out = h_out ? h_out : p->d_q;
     P.C.scale = 1.f / (float)BM;
     return run_waves(P, p->J, WAVE_256, s);
 }

@@ -1133,7 +1133,8 @@ int ifft_m(const ptycho_plan_s *p, const float2 *in, const float2 *w, float2 *ou
 // h_j to the plan's frame scratch; true: the plan's current subdomain copies
 // u_d with their probes (W_d when blind), loss partials only.
 template <int M>
-int loss_m(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, bool subdomain = false)
+int loss_m(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, bool subdomain = false,
+           float2 *h_out = nullptr)
 {
     if (int rc = set_smem<M>(loss_kernel<M>)) return rc;
     LossArgs a;
@@ -1146,7 +1147,7 @@ int loss_m(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, b
     a.w = w;
     a.Wd = subdomain && p->blind ? p->d_Wd : nullptr;
     a.sqrtf_ = p->d_sqrtf;
-    a.h = subdomain ? nullptr : p->d_q;
+    a.h = subdomain ? nullptr : (h_out ? h_out : p->d_q);
     a.loss_part = p->d_loss_part;
     a.tw = p->d_tw;
     a.eps = p->eps;
@@ -1405,17 +1406,17 @@ int launch_frames_ifft_weight(const ptycho_plan_s *p, const float2 *frames, cons
     }
 }
 
-int launch_loss_frames(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s)
+int launch_loss_frames(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, float2 *h_out)
 {
     switch (p->M) {
-    case 16: return loss_m<16>(p, u, w, s);
-    case 32: return loss_m<32>(p, u, w, s);
-    case 64: return loss_m<64>(p, u, w, s);
-    case 128: return loss_m<128>(p, u, w, s);
-    case 48: return loss_m<48>(p, u, w, s);
-    case 80: return loss_m<80>(p, u, w, s);
-    case 96: return loss_m<96>(p, u, w, s);
-    case 256: return loss_256(p, u, w, s);
+    case 16: return loss_m<16>(p, u, w, s, false, h_out);
+    case 32: return loss_m<32>(p, u, w, s, false, h_out);
+    case 64: return loss_m<64>(p, u, w, s, false, h_out);
+    case 128: return loss_m<128>(p, u, w, s, false, h_out);
+    case 48: return loss_m<48>(p, u, w, s, false, h_out);
+    case 80: return loss_m<80>(p, u, w, s, false, h_out);
+    case 96: return loss_m<96>(p, u, w, s, false, h_out);
+    case 256: return loss_256(p, u, w, s, h_out);
     default: return fail(PTYCHO_ERR_UNSUPPORTED, "probe side m must be 16, 32, 48, 64, 80, 96, 128 or 256");
     }
 }

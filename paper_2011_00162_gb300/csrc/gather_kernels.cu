@@ -1019,7 +1019,7 @@ int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w
 // grad_w == nullptr: blind W-update over the subdomain groups (u = current
 // subdomain buffer, h = d_q).  Otherwise: grad_w = sum over all frames of
 // conj(S_j u_img) h_j (one group).
-int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, cudaStream_t s)
+int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, cudaStream_t s, const float2 *h)
 {
     const od2p::ProbeGroups &G = grad_w ? p->img_groups : p->sub_groups;
     ProbeArgs a;
@@ -1030,7 +1030,7 @@ int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, c
     a.frame_pitch = grad_w ? nullptr : p->d_frame_pitch;
     a.pitch = p->W;
     a.u = grad_w ? u_img : p->d_u[p->cur];
-    a.h = p->d_q;
+    a.h = h ? h : p->d_q;
     a.part = p->d_probe_part;
     a.part_n = p->d_probe_part_n;
     const int MM = p->MM;

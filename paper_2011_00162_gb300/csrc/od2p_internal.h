@@ -238,6 +238,11 @@ struct ptycho_plan_s {
     bool cond_checked = false;                       // conditional-node self check passed
     int32_t fft_kind = 0;                            // m = 64: 0 the 8 x 8 split, 1 / 2 the 16 x 4 split
     float2 *d_gamma_snap = nullptr;                  // Gamma snapshot (allocated on first use)
+    // stagm_loss_grad's stored gradient frames (recompute = 0 stores, 2 reuses)
+    float2 *d_hstore = nullptr;                      // J*MM, allocated on first store
+    float *d_hloss = nullptr;                        // the loss of the stored pass
+    const void *h_u = nullptr, *h_w = nullptr;       // the u and w it was computed from
+    bool h_stored = false;
     // ---- shards (ptycho_plan_shard): the subdomains of rank `rank` of `world`
     std::vector<int32_t> global_j;   // global index of each of the plan's frames
     std::vector<int32_t> owner;      // D: owning rank of each subdomain (empty: not a shard)
@@ -261,7 +266,8 @@ int launch_forward(const ptycho_plan_s *p, const float2 *u, const float2 *w, flo
                    cudaStream_t s);
 int launch_frames_ifft_weight(const ptycho_plan_s *p, const float2 *frames, const float2 *w,
                               bool ifft, float2 *out, cudaStream_t s);
-int launch_loss_frames(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s);
+// h_j = F^* grad g of every frame into h_out (null: the plan's frame scratch) and loss partials
+int launch_loss_frames(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, float2 *h_out = nullptr);
 // ST-AGM loss partials of the current subdomain iterate (u_d, and W_d when blind)
 int launch_metrics_loss(ptycho_plan_s *p, cudaStream_t s);
 int launch_probe_avg(ptycho_plan_s *p, cudaStream_t s);
@@ -284,7 +290,7 @@ int frame_update_256(ptycho_plan_s *p, cudaStream_t s);
 int rf_parts_256(int J, int variant);
 int forward_256(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out, cudaStream_t s);
 int ifft_256(const ptycho_plan_s *p, const float2 *in, float2 *out, cudaStream_t s);
-int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s);
+int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, float2 *h_out = nullptr);
 int loss_256_sub(ptycho_plan_s *p, cudaStream_t s);
 int probe_avg_256(ptycho_plan_s *p, cudaStream_t s);
 int ingest_256(ptycho_plan_s *p, const float *f, float *part, cudaStream_t s);
@@ -297,7 +303,8 @@ int launch_subdomain_update_table(bool blind, const SubArgs *tab, const int2 *it
                                   cudaStream_t s);
 int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w, float2 *out,
                         cudaStream_t s);
-int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, cudaStream_t s);
+int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, cudaStream_t s,
+                        const float2 *h = nullptr);
 int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s);
 int launch_metrics(ptycho_plan_s *p, cudaStream_t s);
 int launch_scale(float2 *x, int64_t n, float sc, cudaStream_t s);

@@ -965,15 +965,37 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u, const ptycho_c32 *
                     ptycho_c32 *grad_u, ptycho_c32 *grad_w, int32_t recompute, ptycho_stream_t stream)
 {
     if (!plan || !u || !w || !loss) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
-    if (recompute != 1) return fail(PTYCHO_ERR_UNSUPPORTED, "only recompute = 1 is implemented");
+    if (recompute < 0 || recompute > 2) return fail(PTYCHO_ERR_INVALID_ARG, "recompute must be 0, 1 or 2");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float2 *uu = reinterpret_cast<const float2 *>(u), *ww = reinterpret_cast<const float2 *>(w);
-    if (int rc = launch_loss_frames(plan, uu, ww, s)) return rc;
-    if (int rc = launch_loss_reduce(plan, loss, s)) return rc;
+    const float2 *h = plan->d_q;
+    if (recompute == 2) {  // the gradient frames stored by the last recompute = 0 call
+        if (!plan->h_stored || plan->h_u != u || plan->h_w != w)
+            return fail(PTYCHO_ERR_STATE, "no stored gradient frames for this u and w (call with recompute = 0 first)");
+        h = plan->d_hstore;
+        OD2P_CUDA(cudaMemcpyAsync(loss, plan->d_hloss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    } else {
+        if (recompute == 0) {
+            if (!plan->d_hstore) {
+                if (int rc = dev_alloc(&plan->d_hstore, (size_t)plan->J * plan->MM, plan->owned, s)) return rc;
+                if (int rc = dev_alloc(&plan->d_hloss, 1, plan->owned, s)) return rc;
+            }
+            h = plan->d_hstore;
+            plan->h_stored = false;
+        }
+        if (int rc = launch_loss_frames(plan, uu, ww, s, const_cast<float2 *>(h))) return rc;
+        if (int rc = launch_loss_reduce(plan, loss, s)) return rc;
+        if (recompute == 0) {
+            OD2P_CUDA(cudaMemcpyAsync(plan->d_hloss, loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+            plan->h_stored = true;
+            plan->h_u = u;
+            plan->h_w = w;
+        }
+    }
     if (grad_u)
-        if (int rc = launch_image_gather(plan, plan->d_q, ww, reinterpret_cast<float2 *>(grad_u), s)) return rc;
+        if (int rc = launch_image_gather(plan, h, ww, reinterpret_cast<float2 *>(grad_u), s)) return rc;
     if (grad_w)
-        if (int rc = launch_probe_reduce(plan, uu, reinterpret_cast<float2 *>(grad_w), s)) return rc;
+        if (int rc = launch_probe_reduce(plan, uu, reinterpret_cast<float2 *>(grad_w), s, h)) return rc;
     return PTYCHO_OK;
 }
 

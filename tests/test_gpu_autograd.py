@@ -89,3 +89,50 @@ def test_gradient_descent_on_object_and_probe_lowers_the_loss():
         opt.step()
         L0 = L.item() if L0 is None else L0
     assert stagm_loss(u.detach(), w.detach(), plan).item() < 0.7 * L0
+
+
+@pytest.mark.parametrize("m,n,step", [(16, 64, 4), (128, 384, 48), (256, 512, 96), (48, 144, 12)])
+def test_stored_gradient_frames_equal_recomputed(m, n, step):
+    """recompute = 0 keeps the gradient frames, recompute = 2 gathers from them:
+    the same loss and gradients bit for bit as recomputing; a store made for
+    other u / w pointers, or none at all, is refused."""
+    plan, u0, w0, offs, f = _case(m=m, n=n, step=step, seed=m)
+    u = torch.from_numpy(u0).to(DEV)
+    w = torch.from_numpy(w0).to(DEV)
+    with pytest.raises(od.PtychoError) as e:
+        od.stagm_loss_grad(plan, u, w, recompute=od.FROM_STORE)
+    assert e.value.code == 6
+    L1, gu1, gw1 = od.stagm_loss_grad(plan, u, w, recompute=od.RECOMPUTE)
+    Ls, _, _ = od.stagm_loss_grad(plan, u, w, grad_u=False, grad_w=False, recompute=od.STORE)
+    # other frame work on the plan (here a recomputed loss elsewhere) leaves the store alone
+    od.stagm_loss_grad(plan, u * 0.5, w, recompute=od.RECOMPUTE)
+    L2, gu2, gw2 = od.stagm_loss_grad(plan, u, w, recompute=od.FROM_STORE)
+    assert torch.equal(L1, Ls) and torch.equal(L1, L2)
+    assert torch.equal(gu1, gu2) and torch.equal(gw1, gw2)
+    with pytest.raises(od.PtychoError) as e:
+        od.stagm_loss_grad(plan, u.clone(), w, recompute=od.FROM_STORE)
+    assert e.value.code == 6
+
+
+def test_autograd_store_and_recompute_agree():
+    from paper_2011_00162_gb300 import autograd
+    plan, u0, w0, offs, f = _case()
+    grads = []
+    for budget in (1 << 30, 0):  # frames kept for the backward; recomputed
+        autograd.STORE_BUDGET_BYTES = budget
+        u = torch.from_numpy(u0).to(DEV).requires_grad_(True)
+        w = torch.from_numpy(w0).to(DEV).requires_grad_(True)
+        stagm_loss(u, w, plan).backward()
+        grads.append((u.grad.clone(), w.grad.clone()))
+    autograd.STORE_BUDGET_BYTES = 1 << 30
+    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
+    # two graphs on one plan: the first backward finds the store replaced and recomputes
+    u1 = torch.from_numpy(u0).to(DEV).requires_grad_(True)
+    u2 = torch.from_numpy(u0 * 0.9).to(DEV).requires_grad_(True)
+    w = torch.from_numpy(w0).to(DEV)
+    L1, L2 = stagm_loss(u1, w, plan), stagm_loss(u2, w, plan)
+    L1.backward()
+    assert torch.equal(u1.grad, grads[0][0])
+    L2.backward()
+    _, gu2, _ = od.stagm_loss_grad(plan, u2.detach(), w)
+    assert torch.equal(u2.grad, gu2)

@@ -176,16 +176,19 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
 #pragma unroll
         for (int t = 0; t < BR; ++t) x[t] = buf[(BR * hi + t) * PB + cl];
         const int pc = cb * SLAB + cl;
-        // Gamma and sqrt f of the thread's column segment, loaded before any
-        // Gamma store (the compiler may not move loads past those stores)
+        // this thread's column segment of Gamma and sqrt f (position rows
+        // 16 hi .. 16 hi + 15), loaded before any Gamma store (the compiler may
+        // not move loads past those stores)
+        const size_t g0 = (size_t)j * BMM + (size_t)(BR * hi) * BM + pc;
+        float2 *gseg = a.gamma + g0;
+        const float *fseg = a.sqrtf_ + g0;
         float2 gmv[MODE == B_PROX ? BR : 1];
         float sfv[MODE == B_PROX || MODE == B_LOSS ? BR : 1];
         if (MODE == B_PROX || MODE == B_LOSS) {
 #pragma unroll
             for (int t = 0; t < BR; ++t) {
-                const size_t gi = (size_t)j * BMM + (size_t)(BR * hi + t) * BM + pc;
-                sfv[t] = __ldg(a.sqrtf_ + gi);
-                if (MODE == B_PROX) gmv[MODE == B_PROX ? t : 0] = a.gamma[gi];
+                sfv[t] = __ldg(fseg + t * BM);
+                if (MODE == B_PROX) gmv[MODE == B_PROX ? t : 0] = gseg[t * BM];
             }
         }
         if (MODE != B_IFFT_IN) dft<BR, false>(x);
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
                 const float2 y = cadd(gm, ax);
                 const float2 z = stagm_prox(y, sf, a.pc);
                 const float2 gn = csub(y, z);
-                a.gamma[gi] = gn;
+                gseg[t * BM] = gn;
                 x[t] = csub(z, gn);
             } else if (MODE == B_LOSS) {
                 const float2 xv = cscale(x[t], inv_m);
@@ -290,15 +293,29 @@ __global__ void __launch_bounds__(NTB) rows_inv256_kernel(PassC a, const float2 
         for (int t = 0; t < BR; ++t) rp[n1 + BR * t] = x[t];
     }
     __syncthreads();
-    for (int r = 0; r < SLAB; ++r) {
-        const int row = rb * SLAB + r;
-        float2 v = cscale(buf[r * PA + c], a.scale);
-        if (a.wconj) v = cmulc(v, __ldg(a.wconj + row * BM + c));
-        if (a.slot)
-            a.slot[(size_t)__ldg(a.rank + (size_t)j * BMM + row * BM + c) * a.slot_stride + a.frame_base[j] +
-                   row * a.frame_pitch[j] + c] = v;
-        else
-            a.out[(size_t)j * BMM + row * BM + c] = v;
+    // the output rows rb * SLAB .. of column c, with the mode tests and the
+    // per-frame bases hoisted out of the row loop
+    const float sc = a.scale;
+    const size_t r0 = (size_t)rb * SLAB;
+    if (a.slot) {  // nonblind gather slots: conj(w) o q_j at the pixel's rank
+        const int pitch = a.frame_pitch[j];
+        const uint8_t *rk = a.rank + (size_t)j * BMM + r0 * BM + c;
+        const float2 *wc = a.wconj + r0 * BM + c;
+        float2 *sl = a.slot + a.frame_base[j] + r0 * pitch + c;
+        const size_t stride = (size_t)a.slot_stride;
+#pragma unroll
+        for (int r = 0; r < SLAB; ++r)
+            sl[__ldg(rk + r * BM) * stride + (size_t)r * pitch] = cmulc(cscale(buf[r * PA + c], sc), __ldg(wc + r * BM));
+    } else {
+        float2 *o = a.out + (size_t)j * BMM + r0 * BM + c;
+        if (a.wconj) {
+            const float2 *wc = a.wconj + r0 * BM + c;
+#pragma unroll
+            for (int r = 0; r < SLAB; ++r) o[r * BM] = cmulc(cscale(buf[r * PA + c], sc), __ldg(wc + r * BM));
+        } else {
+#pragma unroll
+            for (int r = 0; r < SLAB; ++r) o[r * BM] = cscale(buf[r * PA + c], sc);
+        }
     }
 }
 

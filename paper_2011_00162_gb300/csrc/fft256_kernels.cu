@@ -187,8 +187,10 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
         if (MODE == B_PROX || MODE == B_LOSS) {
 #pragma unroll
             for (int t = 0; t < BR; ++t) {
-                sfv[t] = __ldg(fseg + t * BM);
-                if (MODE == B_PROX) gmv[MODE == B_PROX ? t : 0] = gseg[t * BM];
+                // read once per iteration: streaming loads (evict first) keep the
+                // intermediate T resident in L2
+                sfv[t] = __ldcs(fseg + t * BM);
+                if (MODE == B_PROX) gmv[MODE == B_PROX ? t : 0] = __ldcs(gseg + t * BM);
             }
         }
         if (MODE != B_IFFT_IN) dft<BR, false>(x);
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
                 const float2 y = cadd(gm, ax);
                 const float2 z = stagm_prox(y, sf, a.pc);
                 const float2 gn = csub(y, z);
-                gseg[t * BM] = gn;
+                __stcs(gseg + t * BM, gn);
                 x[t] = csub(z, gn);
             } else if (MODE == B_LOSS) {
                 const float2 xv = cscale(x[t], inv_m);
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(NTB) rows_inv256_kernel(PassC a, const float2 
             for (int r = 0; r < SLAB; ++r) o[r * BM] = cmulc(cscale(buf[r * PA + c], sc), __ldg(wc + r * BM));
         } else {
 #pragma unroll
-            for (int r = 0; r < SLAB; ++r) o[r * BM] = cscale(buf[r * PA + c], sc);
+            for (int r = 0; r < SLAB; ++r) __stcs(o + r * BM, cscale(buf[r * PA + c], sc));
         }
     }
 }

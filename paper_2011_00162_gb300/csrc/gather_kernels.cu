@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(GATHER_THREADS, BLIND ? OD2P_K2B_MINB : OD2P_K
                     const int dr = dr0 + r;
                     const bool hit = cok && r < nrows && (unsigned)dr < (unsigned)M;
                     const int o = hit ? dr * M + dc : 0;
-                    qv[u][r] = __ldg(a.q + (hit ? e.j * MM + o : 0));
+                    qv[u][r] = __ldcs(a.q + (hit ? e.j * MM + o : 0));  // read once: evict first
                     if (w) wv[u][r] = __ldg(w + o);
                     hits |= (hit ? 1u : 0u) << (u * TILE_ROWS + r);
                 }
@@ -408,7 +408,7 @@ __global__ void probe_partial_kernel(ProbeArgs a)
             const int j = a.group_frames[t];
             const int pitch = a.frame_pitch ? a.frame_pitch[j] : a.pitch;
             uv[u] = __ldg(a.u + a.frame_base[j] + (size_t)kr * pitch + kc);
-            hv[u] = __ldg(a.h + (size_t)j * MM + k);
+            hv[u] = __ldcs(a.h + (size_t)j * MM + k);  // read once per pass: evict first
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)

@@ -258,8 +258,9 @@ def batched_leg(od, dev, K: int = 10, W: int = 2, count: int = 64, tune=True, re
     """Config-3 workload: `count` independent nonblind reconstructions of mixed
     sizes.  The batch (one frame-update launch per probe side + one subdomain
     update per iteration, graph-replayed) against the same plans iterated one
-    after another, each plain plan on the transform split the batch uses, so
-    that equal error shows as bitwise-identical states."""
+    after another, each plain plan on the transform split the batch uses (the
+    16 x 4 split for m = 64, the two-stage split otherwise), so that equal
+    error shows as bitwise-identical states."""
     import torch
     from paper_2011_00162_gb300 import synth
     probs = synth.batched_problems(count, seed=3)
@@ -289,8 +290,11 @@ def batched_leg(od, dev, K: int = 10, W: int = 2, count: int = 64, tune=True, re
     if tune:
         from paper_2011_00162_gb300 import autotune
         autotune.tune_batch(batch, use_cache=not retune)
-        for pl in plains:  # launch shapes only: the batch keeps the default transform split
+        for pl in plains:  # launch shapes only: the transform split stays the batch's
             autotune.tune_plan(pl, use_cache=not retune, fft=False)
+    for pl in plains:  # the batch runs its m = 64 members on the 16 x 4 split (fft kind 2)
+        if pl.geom.m == 64:
+            od.ptycho_plan_set_fft(pl, 2)
     batch.iterate(W)
     for pl in plains:
         od.od2p_iterate(pl, W)

@@ -485,9 +485,12 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c
  * Batches of independent reconstructions (nonblind, probe sides up to 128,
  * mixed image, probe, scan and subdomain sizes).  One ADMM iteration of all
  * members is one frame-update launch per distinct probe side -- a persistent
- * kernel over the (member, frame group) work items -- and one subdomain-update
- * launch over the tiles of all members, replayed from a CUDA graph.  Each
- * member computes exactly what od2p_iterate computes on it alone (bitwise).
+ * kernel over the (member, frame group) work items; the launches of different
+ * probe sides run as parallel branches of the graph -- and one subdomain-update
+ * launch over the tiles of all members, replayed from a CUDA graph.  Members
+ * with m = 64 run the 16 x 4 transform split (ptycho_plan_set_fft kind 2, set
+ * by the batch).  Each member computes exactly what od2p_iterate computes on
+ * it alone in the same split (bitwise).
  *
  * ptycho_batch_plan: geoms[i], f_devs[i] as for ptycho_plan, i < n; the
  *   members are plans owned by the batch (ptycho_batch_member hands out

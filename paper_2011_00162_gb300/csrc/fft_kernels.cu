@@ -550,12 +550,18 @@ template <int SG> constexpr size_t f4_smem_bytes()
 
 __device__ __forceinline__ int pos64(int f) { return 8 * (f & 7) + (f >> 3); }
 
-template <int SG>
+// BATCHED: the work items are (plan, frame) pairs of several plans with m = 64,
+// each plan's arguments read from tab[2 plan + parity] (the batches' form of
+// the 16 x 4 split); otherwise item i is frame i of `single`.
+template <int SG, bool BATCHED>
 __global__ void __launch_bounds__(256, F4Cfg<SG>::MINB)
-    frame_update_f4_kernel(const FrameArgs sa, int n_items)
+    frame_update_f4_kernel(const FrameArgs single, const FrameArgs *__restrict__ tab,
+                           const int2 *__restrict__ items, int n_items, int parity)
 {
     constexpr int M = 64, P = 65, MM = 4096, NT = 256;
     extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ FrameArgs sa_batch;  // batches: arguments of the current item's plan
+    const FrameArgs &sa = BATCHED ? sa_batch : single;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     float2 *stg_g = reinterpret_cast<float2 *>(smem + 128);
     float *stg_f = reinterpret_cast<float *>(smem + 128 + (SG ? sizeof(float2) * MM : 0));
@@ -563,19 +569,27 @@ __global__ void __launch_bounds__(256, F4Cfg<SG>::MINB)
     float2 *buf = tw + M;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
 
-    auto issue = [&](int j) {  // one thread: stage frame j's Gamma / sqrt f
+    auto item = [&](int i) { return BATCHED ? items[i] : make_int2(0, i); };
+    auto args = [&](int2 it) -> const FrameArgs & { return BATCHED ? tab[2 * it.x + parity] : single; };
+    auto issue = [&](int i) {  // one thread: stage item i's Gamma / sqrt f
+        const int2 it = item(i);
+        const FrameArgs &ga = args(it);
+        const int j = it.y;
         const unsigned fbytes = (unsigned)(MM * sizeof(float));
         const unsigned gbytes = SG ? (unsigned)(MM * sizeof(float2)) : 0u;
         mbar_expect_tx(bar, fbytes + gbytes);
-        if (SG) bulk_g2s(stg_g, sa.gamma + (size_t)j * MM, gbytes, bar);
-        bulk_g2s(stg_f, sa.sqrtf_ + (size_t)j * MM, fbytes, bar);
-        if (sa.slot) bulk_prefetch_l2(sa.rank + (size_t)j * MM, (unsigned)MM);
+        if (SG) bulk_g2s(stg_g, ga.gamma + (size_t)j * MM, gbytes, bar);
+        bulk_g2s(stg_f, ga.sqrtf_ + (size_t)j * MM, fbytes, bar);
+        if (ga.slot) bulk_prefetch_l2(ga.rank + (size_t)j * MM, (unsigned)MM);
     };
-    auto prefetch_window = [&](int j) {  // all threads: frame j's exit-wave window into L2
+    auto prefetch_window = [&](int i) {  // all threads: item i's exit-wave window into L2
         constexpr int LINES = (M * 8 + 127) / 128 + 1;
+        const int2 it = item(i);
+        const FrameArgs &ga = args(it);
         for (int k = t; k < M * LINES; k += NT) {
             const int row = k / LINES, l = k % LINES;
-            const char *rp = reinterpret_cast<const char *>(sa.u + sa.frame_base[j] + (size_t)row * sa.frame_pitch[j]);
+            const char *rp =
+                reinterpret_cast<const char *>(ga.u + ga.frame_base[it.y] + (size_t)row * ga.frame_pitch[it.y]);
             prefetch_l2(rp + min(l * 128, M * 8 - 8));
         }
     };
@@ -584,14 +598,23 @@ __global__ void __launch_bounds__(256, F4Cfg<SG>::MINB)
         mbar_init(bar, 1);
         mbar_fence_init();
     }
-    for (int k = t; k < M; k += NT) tw[k] = sa.tw[k];
+    for (int k = t; k < M; k += NT) tw[k] = (BATCHED ? tab[parity] : single).tw[k];
     __syncthreads();
-    int j = blockIdx.x;
-    if (t == 0 && j < n_items) issue(j);
+    int i = blockIdx.x;
+    if (t == 0 && i < n_items) issue(i);
     unsigned phase = 0;
+    int plan_now = -1;
     const float inv_m = 1.f / (float)M;
-    for (; j < n_items; j += gridDim.x) {
-        if (j + (int)gridDim.x < n_items) prefetch_window(j + gridDim.x);
+    for (; i < n_items; i += gridDim.x) {
+        const int2 it = item(i);
+        if (BATCHED && it.x != plan_now) {  // uniform: every thread sees the same item
+            __syncthreads();
+            if (t == 0) sa_batch = tab[2 * it.x + parity];
+            __syncthreads();
+            plan_now = it.x;
+        }
+        const int j = it.y;
+        if (i + (int)gridDim.x < n_items) prefetch_window(i + gridDim.x);
         if (!SG && t == 0)
             for (unsigned off = 0; off < (unsigned)(MM * sizeof(float2)); off += 16384u)
                 bulk_prefetch_l2(reinterpret_cast<const char *>(sa.gamma + (size_t)j * MM) + off, 16384u);
@@ -681,10 +704,10 @@ __global__ void __launch_bounds__(256, F4Cfg<SG>::MINB)
 #pragma unroll
             for (int i = 0; i < 16; ++i) buf[rho * P + 16 * l1 + i] = z[i];
         }
-        __syncthreads();  // staging buffers are free: start the next frame's copies
-        if (t == 0 && j + (int)gridDim.x < n_items) {
+        __syncthreads();  // staging buffers are free: start the next item's copies
+        if (t == 0 && i + (int)gridDim.x < n_items) {
             fence_proxy_async_smem();
-            issue(j + gridDim.x);
+            issue(i + gridDim.x);
         }
         // ---- pass 4: inverse column radix-16, in place
         {
@@ -1332,11 +1355,13 @@ int f4_per_sm(int *per_sm_out, int *n_sm_out)
     if (dev < 0 || dev >= MAX_DEV) return fail(PTYCHO_ERR_UNSUPPORTED, "device ordinal above 63");
     std::lock_guard<std::mutex> lock(g_attr_mu);
     if (!per_sm[dev]) {
-        OD2P_CUDA(cudaFuncSetAttribute(frame_update_f4_kernel<SG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        OD2P_CUDA(cudaFuncSetAttribute(frame_update_f4_kernel<SG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)f4_smem_bytes<SG>()));
+        OD2P_CUDA(cudaFuncSetAttribute(frame_update_f4_kernel<SG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)f4_smem_bytes<SG>()));
         int a = 0, n = 0;
         OD2P_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
-        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, frame_update_f4_kernel<SG>, F4Cfg<SG>::NT,
+        OD2P_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, frame_update_f4_kernel<SG, true>, F4Cfg<SG>::NT,
                                                                 f4_smem_bytes<SG>()));
         if (a < 1) return fail(PTYCHO_ERR_UNSUPPORTED, "the 16 x 4 frame update does not fit on an SM");
         per_sm[dev] = a;
@@ -1347,11 +1372,25 @@ int f4_per_sm(int *per_sm_out, int *n_sm_out)
     return PTYCHO_OK;
 }
 
-int f4_grid(int kind, int J, int *grid)
+int f4_grid(int kind, int J, int *grid, int blocks_per_sm)
 {
     int per_sm = 0, n_sm = 0;
     if (int rc = kind == 1 ? f4_per_sm<1>(&per_sm, &n_sm) : f4_per_sm<0>(&per_sm, &n_sm)) return rc;
-    *grid = std::max(1, std::min(J, per_sm * n_sm));
+    const int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, per_sm) : per_sm;
+    *grid = std::max(1, std::min(J, bps * n_sm));
+    return PTYCHO_OK;
+}
+
+// The batches' m = 64 class on the 16 x 4 split (fft kind 2): one persistent
+// launch over the members' (plan, frame) items.
+int launch_frame_update_f4_table(const FrameArgs *tab, const int2 *items, int n_items, int grid, int parity,
+                                 cudaStream_t s)
+{
+    int per_sm = 0, n_sm = 0;
+    if (int rc = f4_per_sm<0>(&per_sm, &n_sm)) return rc;  // the shared-memory limit, once per device
+    if (n_items <= 0) return PTYCHO_OK;
+    frame_update_f4_kernel<0, true><<<grid, 256, f4_smem_bytes<0>(), s>>>(FrameArgs{}, tab, items, n_items, parity);
+    OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
 
@@ -1360,9 +1399,11 @@ int launch_frame_update(ptycho_plan_s *p, cudaStream_t s)
     if (p->M == 256) return frame_update_256(p, s);
     if (p->fft_kind) {
         if (p->fft_kind == 1)
-            frame_update_f4_kernel<1><<<p->n_k1_blocks, 256, f4_smem_bytes<1>(), s>>>(p->h_fargs[p->cur], p->J);
+            frame_update_f4_kernel<1, false><<<p->n_k1_blocks, 256, f4_smem_bytes<1>(), s>>>(
+                p->h_fargs[p->cur], nullptr, nullptr, p->J, 0);
         else
-            frame_update_f4_kernel<0><<<p->n_k1_blocks, 256, f4_smem_bytes<0>(), s>>>(p->h_fargs[p->cur], p->J);
+            frame_update_f4_kernel<0, false><<<p->n_k1_blocks, 256, f4_smem_bytes<0>(), s>>>(
+                p->h_fargs[p->cur], nullptr, nullptr, p->J, 0);
         OD2P_CUDA(cudaGetLastError());
         return PTYCHO_OK;
     }

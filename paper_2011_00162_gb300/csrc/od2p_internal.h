@@ -261,7 +261,9 @@ namespace od2p {
 
 // fft_kernels.cu
 int launch_frame_update(ptycho_plan_s *p, cudaStream_t s);
-int f4_grid(int kind, int J, int *grid);
+int f4_grid(int kind, int J, int *grid, int blocks_per_sm = 0);
+int launch_frame_update_f4_table(const FrameArgs *tab, const int2 *items, int n_items, int grid, int parity,
+                                 cudaStream_t s);
 int launch_forward(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out,
                    cudaStream_t s);
 int launch_frames_ifft_weight(const ptycho_plan_s *p, const float2 *frames, const float2 *w,

@@ -841,13 +841,19 @@ int ptycho_probe_init(ptycho_plan_t *plan, ptycho_c32 *w0_dev, ptycho_stream_t s
     return launch_probe_init(plan, reinterpret_cast<float2 *>(w0_dev), reinterpret_cast<cudaStream_t>(stream));
 }
 
+static int set_fft_kind(ptycho_plan_t *plan, int32_t kind, cudaStream_t s);
+
 int ptycho_plan_set_fft(ptycho_plan_t *plan, int32_t kind, ptycho_stream_t stream)
 {
     if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
     if (kind < 0 || kind > 2) return fail(PTYCHO_ERR_INVALID_ARG, "fft kind must be 0, 1 or 2");
     if (kind && plan->M != 64) return fail(PTYCHO_ERR_UNSUPPORTED, "fft kinds 1 and 2 are for m = 64");
     if (plan->batch_member) return fail(PTYCHO_ERR_STATE, "a batch member runs its batch's frame update");
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return set_fft_kind(plan, kind, reinterpret_cast<cudaStream_t>(stream));
+}
+
+static int set_fft_kind(ptycho_plan_t *plan, int32_t kind, cudaStream_t s)
+{
     if (kind == plan->fft_kind) return PTYCHO_OK;
     if (kind == 0) {
         plan->fft_kind = 0;
@@ -1004,6 +1010,7 @@ struct ptycho_batch_s {
     std::vector<ptycho_plan_s *> plans;
     struct Cls {  // the member plans of one probe side m
         int m = 0, grid = 0;
+        bool f4 = false;                 // m = 64: the 16 x 4 split, one frame per item
         int n_items[2] = {0, 0};         // (plan, frame group) items per launch shape
         od2p::FrameArgs *tab = nullptr;
         int2 *items[2] = {nullptr, nullptr};
@@ -1073,26 +1080,34 @@ int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const 
     for (auto *p : b->plans)
         if (std::find(ms.begin(), ms.end(), p->M) == ms.end()) ms.push_back(p->M);
     std::sort(ms.begin(), ms.end());
+    // m = 64 members take the 16 x 4 transform split (fft kind 2), alone and in the batch
+    for (auto *p : b->plans)
+        if (p->M == 64)
+            if (int rc = set_fft_kind(p, 2, s)) return bail(rc);
     for (auto *p : b->plans) p->batch_member = true;
     for (int m : ms) {
         std::vector<FrameArgs> tab;
         std::vector<int2> items[2];
+        const bool f4 = m == 64;
         for (auto *p : b->plans) {
             if (p->M != m) continue;
             const int local = (int)tab.size() / 2;
             tab.push_back(p->h_fargs[0]);
             tab.push_back(p->h_fargs[1]);
-            for (int v = 0; v < 2; ++v)
-                for (int g = 0; g < frame_groups(m, p->J, v); ++g) items[v].push_back(make_int2(local, g));
+            for (int v = 0; v < 2; ++v) {
+                const int n_it = f4 ? p->J : frame_groups(m, p->J, v);  // f4: one frame per item
+                for (int g = 0; g < n_it; ++g) items[v].push_back(make_int2(local, g));
+            }
         }
         ptycho_batch_s::Cls c;
         c.m = m;
+        c.f4 = f4;
         c.n_items[0] = (int)items[0].size();
         c.n_items[1] = (int)items[1].size();
         int rc;
         if ((rc = upload(&c.tab, tab, b->owned, s)) || (rc = upload(&c.items[0], items[0], b->owned, s)) ||
             (rc = upload(&c.items[1], items[1], b->owned, s)) ||
-            (rc = frame_update_grid(m, 0, c.n_items[0], 0, &c.grid, nullptr)))
+            (rc = f4 ? f4_grid(2, c.n_items[0], &c.grid) : frame_update_grid(m, 0, c.n_items[0], 0, &c.grid, nullptr)))
             return bail(rc);
         b->cls.push_back(c);
     }
@@ -1152,7 +1167,11 @@ int ptycho_batch_set_launch(ptycho_batch_t *b, int32_t variant, int32_t blocks_p
     std::vector<int> grids;
     for (const auto &c : b->cls) {
         int grid = 0;
-        if (int rc = frame_update_grid(c.m, variant, c.n_items[variant], blocks_per_sm, &grid, nullptr)) return rc;
+        // the m = 64 class's 16 x 4 kernel keeps every block that fits (the
+        // shape and cap are those of the two-stage kernels of the other classes)
+        if (int rc = c.f4 ? f4_grid(2, c.n_items[0], &grid, 0)
+                          : frame_update_grid(c.m, variant, c.n_items[variant], blocks_per_sm, &grid, nullptr))
+            return rc;
         grids.push_back(grid);
     }
     // members iterate alone in the same shape, so their RF partials keep one layout
@@ -1186,8 +1205,9 @@ static int batch_enqueue(ptycho_batch_s *b, int parity, cudaStream_t s)
     for (int k = 0; k < nc; ++k) {
         const auto &c = b->cls[k];
         cudaStream_t sk = k == 0 ? s : b->side[k - 1];
-        if (int rc = launch_frame_update_table(c.m, b->variant, c.tab, c.items[b->variant], c.n_items[b->variant],
-                                               c.grid, parity, sk))
+        if (int rc = c.f4 ? launch_frame_update_f4_table(c.tab, c.items[0], c.n_items[0], c.grid, parity, sk)
+                          : launch_frame_update_table(c.m, b->variant, c.tab, c.items[b->variant],
+                                                      c.n_items[b->variant], c.grid, parity, sk))
             return rc;
     }
     for (int k = 1; k < nc; ++k) {

@@ -424,9 +424,9 @@ def _traffic_256(variant: int):
     src = tr = None
     for line in txt.splitlines():
         if line.startswith("kernel_source_sha256_16:"):
-            src = line.split(":", 1)[1].strip()
+            src = (line.split(":", 1)[1].split() or [""])[0]
         if line.startswith("dram_bytes_per_frame:"):
-            tr = line.split(":", 1)[1].strip()
+            tr = (line.split(":", 1)[1].split() or [""])[0]
     h = hashlib.sha256()
     for rel in ("paper_2011_00162_gb300/csrc/fft256_kernels.cu", "paper_2011_00162_gb300/csrc/fft_device.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as fh:

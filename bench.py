@@ -674,12 +674,24 @@ def run_configs(args):
                 "l2": "flushed before every timed call"}
         if blind:
             u = od.od2p_merge(plan)
-            wcur = od.od2p_get_state(plan, od.STATE_W).reshape(p.m, p.m)
+            wcur = od.od2p_get_state(plan, od.STATE_W).reshape(p.m, p.m).contiguous()
             Kg = max(5, K // 3)
             t_g = _event_times(lambda: od.stagm_loss_grad(plan, u, wcur), Kg, flush)
             line["gradient_frames_per_s"] = round(J * Kg / sum(t_g), 1)
             line["ms_per_gradient"] = round(1e3 * statistics.mean(t_g), 5)
-            line["gradient"] = "ST-AGM loss + grad_u + grad_w, exit waves recomputed (none stored)"
+            line["gradient"] = "ST-AGM loss + grad_u + grad_w in one call (one pass over the frames, then the gathers)"
+            # a loss then a gradient (the autograd pattern): frames recomputed in the
+            # second call, or kept by the first (J x m x m complex) and gathered from
+            fwd_bwd_re = lambda: (od.stagm_loss_grad(plan, u, wcur, grad_u=False, grad_w=False),
+                                  od.stagm_loss_grad(plan, u, wcur))
+            fwd_bwd_st = lambda: (od.stagm_loss_grad(plan, u, wcur, grad_u=False, grad_w=False,
+                                                     recompute=od.STORE),
+                                  od.stagm_loss_grad(plan, u, wcur, recompute=od.FROM_STORE))
+            t_re = _event_times(fwd_bwd_re, Kg, flush)
+            t_st = _event_times(fwd_bwd_st, Kg, flush)
+            line["loss_then_gradient_ms"] = {"recompute": round(1e3 * statistics.mean(t_re), 5),
+                                             "stored": round(1e3 * statistics.mean(t_st), 5),
+                                             "stored_bytes": J * p.m * p.m * 8}
         rf, re = od.od2p_metrics(plan)
         line["rf_after"], line["re_after"] = rf, re
         line["snr_db_after"] = round(od.od2p_snr(plan, torch.from_numpy(np.asarray(u_true, np.complex64)).to(dev)), 3)

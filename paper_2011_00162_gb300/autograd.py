@@ -5,7 +5,7 @@ loss(u, w) = sum_j sum_k g_eps((F(w o S_j u))_k; f_jk)      (sections 2.2, 2.4)
 Forward and backward both run in libod2p.so.  The forward makes one pass over
 the frames: exit wave, transform, loss and gradient frame h_j = F^* grad g_j
 (the hand-written adjoint of eq. objgrad pulled back through F^*).  While the
-J x m x m gradient frames fit in STORE_BUDGET_BYTES the forward keeps them in
+J x m x m gradient frames fit in STORE_BUDGET_BYTES (8 GiB) the forward keeps them in
 the plan (stagm_loss_grad with STORE) and the backward only gathers them into
 the gradients (FROM_STORE); above the budget nothing is kept and the backward
 recomputes the exit waves from u and w (RECOMPUTE).  Gradients follow
@@ -19,7 +19,10 @@ import torch
 from ._lib import ERR_STATE
 from .api import FROM_STORE, RECOMPUTE, STORE, Plan, PtychoError, stagm_loss_grad
 
-STORE_BUDGET_BYTES = 1 << 30
+# storing always took less time than recomputing (4096^2 / 6561 frames of 256^2: loss then
+# gradient 6.9 ms stored against 12.3 ms recomputed, for 3.4 GB of frames), so the budget
+# only bounds memory
+STORE_BUDGET_BYTES = 8 << 30
 
 
 def stores_frames(plan: Plan) -> bool:

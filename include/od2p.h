@@ -482,12 +482,15 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c
                     int32_t recompute, ptycho_stream_t stream);
 
 /*
- * Batches of independent reconstructions (nonblind, probe sides up to 128,
- * mixed image, probe, scan and subdomain sizes).  One ADMM iteration of all
+ * Batches of independent reconstructions (nonblind or blind, probe sides up to
+ * 128, mixed image, probe, scan and subdomain sizes).  One ADMM iteration of all
  * members is one frame-update launch per distinct probe side -- a persistent
  * kernel over the (member, frame group) work items; the launches of different
  * probe sides run as parallel branches of the graph -- and one subdomain-update
- * launch over the tiles of all members, replayed from a CUDA graph.  Members
+ * launch over the tiles of all members (two: slot gathers and, for blind
+ * members and members with more than 255 frames over a pixel, frame-list
+ * gathers), with each blind member's probe update in between, replayed from a
+ * CUDA graph.  Members
  * with m = 64 run the 16 x 4 transform split (ptycho_plan_set_fft kind 2, set
  * by the batch).  Each member computes exactly what od2p_iterate computes on
  * it alone in the same split (bitwise).
@@ -498,9 +501,8 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c
  *   destroy them, and do not iterate a member on its own between batch
  *   iterations -- the call returns PTYCHO_ERR_STATE).
  * ptycho_batch_iterate: n_iter iterations of every member; od2p_init must
- *   have been called on each.  Errors: INVALID_ARG, UNSUPPORTED (a blind member,
- *   m = 256, or a member with more than 255 frames over one pixel), STATE, OOM,
- *   CUDA.
+ *   have been called on each.  Errors: INVALID_ARG, UNSUPPORTED (m = 256),
+ *   STATE, OOM, CUDA.
  */
 typedef struct ptycho_batch_s ptycho_batch_t;
 int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const float *const *f_devs, int32_t n,

@@ -1018,8 +1018,10 @@ struct ptycho_batch_s {
     int variant = 0, blocks_per_sm = 0;
     std::vector<Cls> cls;
     od2p::SubArgs *stab = nullptr;
-    int2 *titems = nullptr;
+    int2 *titems = nullptr;        // tiles of the members that gather through slots
     int n_titems = 0;
+    int2 *litems = nullptr;        // tiles of the members that gather through frame lists (blind)
+    int n_litems = 0;
     std::vector<void *> owned;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -1053,10 +1055,8 @@ int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const 
     if (!out) return fail(PTYCHO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!geoms || !f_devs || n < 1) return fail(PTYCHO_ERR_INVALID_ARG, "need n >= 1 geometries and intensity stacks");
-    for (int i = 0; i < n; ++i) {
-        if (geoms[i].blind) return fail(PTYCHO_ERR_UNSUPPORTED, "batches hold nonblind reconstructions only");
+    for (int i = 0; i < n; ++i)
         if (geoms[i].m > 128) return fail(PTYCHO_ERR_UNSUPPORTED, "batches hold probe sides up to 128");
-    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     auto *b = new (std::nothrow) ptycho_batch_s();
     if (!b) return fail(PTYCHO_ERR_OOM, "host allocation failed");
@@ -1070,9 +1070,6 @@ int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const 
         ptycho_plan_t *p = nullptr;
         if (int rc = ptycho_plan(&p, &geoms[i], f_devs[i], stream)) return bail(rc);
         b->plans.push_back(p);
-        if (!p->slots)
-            return bail(fail(PTYCHO_ERR_UNSUPPORTED, "batch member " + std::to_string(i) +
-                                                         ": more than 255 frames cover one pixel (list-gather plan)"));
     }
     // one table per probe side: the member plans' frame-update arguments and the
     // (plan, frame group) work items
@@ -1112,14 +1109,18 @@ int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const 
         b->cls.push_back(c);
     }
     // every subdomain tile of every plan for the single subdomain-update launch
+    // (slot gathers and frame-list gathers -- blind members, or more than 255
+    // frames over a pixel -- are two launches of the same kernel template)
     std::vector<SubArgs> stab;
-    std::vector<int2> titems;
+    std::vector<int2> titems, litems;
     for (int i = 0; i < n; ++i) {
         stab.push_back(b->plans[i]->h_sargs[0]);
         stab.push_back(b->plans[i]->h_sargs[1]);
-        for (int t = 0; t < b->plans[i]->sub_tiles.n_tiles; ++t) titems.push_back(make_int2(i, t));
+        const bool list = b->plans[i]->blind || !b->plans[i]->slots;
+        for (int t = 0; t < b->plans[i]->sub_tiles.n_tiles; ++t) (list ? litems : titems).push_back(make_int2(i, t));
     }
     b->n_titems = (int)titems.size();
+    b->n_litems = (int)litems.size();
     // streams and events for the per-class branches of the iteration graph
     for (size_t k = 1; k < b->cls.size(); ++k) {
         cudaStream_t t = nullptr;
@@ -1136,7 +1137,9 @@ int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const 
         if (e1 != cudaSuccess) return bail(cuda_fail(e1, "cudaEventCreateWithFlags"));
     }
     int rc;
-    if ((rc = upload(&b->stab, stab, b->owned, s)) || (rc = upload(&b->titems, titems, b->owned, s))) return bail(rc);
+    if ((rc = upload(&b->stab, stab, b->owned, s)) || (rc = upload(&b->titems, titems, b->owned, s)) ||
+        (rc = upload(&b->litems, litems, b->owned, s)))
+        return bail(rc);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamSynchronize"));
     *out = b;
@@ -1214,7 +1217,15 @@ static int batch_enqueue(ptycho_batch_s *b, int parity, cudaStream_t s)
         OD2P_CUDA(cudaEventRecord(b->side_done[k - 1], b->side[k - 1]));
         OD2P_CUDA(cudaStreamWaitEvent(s, b->side_done[k - 1], 0));
     }
-    return launch_subdomain_update_table(false, b->stab, b->titems, b->n_titems, parity, s);
+    // blind members: the probe update of each (Algorithm 3 Steps 1, 3, 5), as in its own iteration
+    for (auto *p : b->plans) {
+        if (!p->blind) continue;
+        if (int rc = launch_probe_avg(p, s)) return rc;
+        if (int rc = launch_probe_reduce(p, nullptr, nullptr, s)) return rc;
+        OD2P_CUDA(cudaMemcpyAsync(p->d_w, p->d_wnew, sizeof(float2) * p->MM, cudaMemcpyDeviceToDevice, s));
+    }
+    if (int rc = launch_subdomain_update_table(false, b->stab, b->titems, b->n_titems, parity, s)) return rc;
+    return launch_subdomain_update_table(true, b->stab, b->litems, b->n_litems, parity, s);
 }
 
 int ptycho_batch_iterate(ptycho_batch_t *b, int32_t n_iter, ptycho_stream_t stream)

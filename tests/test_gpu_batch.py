@@ -75,12 +75,48 @@ def test_batch_member_matches_oracle():
     batch.close()
 
 
-def test_batch_rejects_blind_members():
-    p = synth.small_2sub()
-    offs, u_true, w, f = make_case(p)
-    g = od.Geometry(p.n, p.n, p.m, offs, 1, 2, 8, 0.5, 0.1, 0.05, mu=1.0, blind=True)
-    with pytest.raises(od.PtychoError):
-        od.ptycho_batch_plan([g], [torch.from_numpy(f).to(DEV)])
+def test_batch_with_blind_and_dense_members_bitwise():
+    """Blind members (frame-list gather, probe update between the two launches),
+    a nonblind member with more than 255 frames over a pixel (frame-list gather
+    with the known probe) and slot-gather members in one batch: every member
+    equals itself iterated alone, and a blind member matches the oracle."""
+    specs = [(32, 96, 8, True, 2, 31), (64, 192, 16, True, 2, 32), (16, 64, 4, False, 2, 33),
+             (128, 384, 32, True, 2, 34), (32, 64, 2, False, 1, 35), (48, 144, 12, False, 2, 36)]
+    probs, cases, geoms, w0s = [], [], [], []
+    for m, n, step, blind, grid, seed in specs:
+        p = synth.Problem(f"bb{m}", n, m, step, 0 if step < 4 else 1, grid, grid, 8, 1e4, 1, eta=2.0, r=0.5,
+                          blind=blind, mu=1.0 if blind else 0.0, gamma=0.1 if blind else 0.0, seed=seed)
+        c = make_case(p, noise_seed=seed)
+        probs.append(p)
+        cases.append(c)
+        geoms.append(od.Geometry(p.n, p.n, p.m, c[0], p.sub_rows, p.sub_cols, p.overlap_px, 0.5, 2.0, 0.5,
+                                 mu=p.mu, gamma=p.gamma, blind=blind))
+        w0s.append(synth.gaussian_probe(m) if blind else np.asarray(c[2], np.complex64))
+    fs = [torch.from_numpy(np.asarray(c[3], np.float32)).to(DEV) for c in cases]
+    batch = od.ptycho_batch_plan(geoms, fs)
+    for mb, w0 in zip(batch.members, w0s):
+        od.od2p_init(mb, torch.from_numpy(w0).to(DEV))
+    batch.iterate(3)
+    for i, g in enumerate(geoms):
+        alone = od.ptycho_plan(g, fs[i])
+        od.od2p_init(alone, torch.from_numpy(w0s[i]).to(DEV))
+        if g.m == 64:  # the batch runs m = 64 members on the 16 x 4 split
+            od.ptycho_plan_set_fft(alone, 2)
+        od.od2p_iterate(alone, 3)
+        sel = [od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA] + (
+            [od.STATE_WD, od.STATE_DELTA, od.STATE_W] if g.blind else [])
+        for k in sel:
+            assert torch.equal(od.od2p_get_state(batch.members[i], k), od.od2p_get_state(alone, k)), (i, k)
+        alone.close()
+    # one blind member against the FP64 oracle (three iterations)
+    i = 0
+    p, (offs, u_true, w, f) = probs[i], cases[i]
+    ref = oracle.ADMM(f, w0s[i], offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, 0.5, 2.0, 0.5, blind=True,
+                      mu=p.mu, gamma=p.gamma)
+    ref.iterate(3)
+    for k, ko in ((od.STATE_U, oracle.U), (od.STATE_WD, oracle.WD), (od.STATE_W, oracle.W)):
+        assert rel_l2(od.od2p_get_state(batch.members[i], k).cpu().numpy(), ref.get(ko)) < 1e-5, k
+    batch.close()
 
 
 def test_batch_with_mixed_radix_probe_sides_bitwise():

@@ -386,8 +386,26 @@ def measure_workload(od, p, blind: bool, f_host: np.ndarray, dev, K: int, W: int
         od.od2p_subdomain_update(plan)
         evk[k][3].record(stream)
     torch.cuda.synchronize()
+    # the frame update alone, replayed from its own CUDA graph as the iteration's
+    # graph runs it (no host launch gaps between its kernels): the roofline's time
+    g_fu = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(stream)
+    with torch.cuda.graph(g_fu, stream=cap):
+        od.od2p_frame_update(plan)
+    torch.cuda.synchronize()
+    evg = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(Kk)]
+    for k in range(Kk):
+        if flush is not None:
+            flush.fill_(float(k))
+        evg[k][0].record(stream)
+        g_fu.replay()
+        evg[k][1].record(stream)
+    torch.cuda.synchronize()
     if clk is not None:
         clk.mark_end()
+    k1g_ms = [evg[k][0].elapsed_time(evg[k][1]) for k in range(Kk)]
+    del g_fu
     step_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
     k1_ms = [evk[k][0].elapsed_time(evk[k][1]) for k in range(Kk)]
     pu_ms = [evk[k][1].elapsed_time(evk[k][2]) for k in range(Kk)]
@@ -398,6 +416,7 @@ def measure_workload(od, p, blind: bool, f_host: np.ndarray, dev, K: int, W: int
     launch = od.ptycho_plan_get_launch(plan)
     fft_kind = od.ptycho_plan_get_fft(plan)
     out = {"plan": plan, "geom": geom, "offs": offs, "w0": w0, "J": J, "step_ms": step_ms, "k1_ms": k1_ms,
+           "k1g_ms": k1g_ms,
            "pu_ms": pu_ms, "k2_ms": k2_ms, "wall_s": wall1 - wall0, "rf": rf, "re": re, "loss": loss,
            "snr_db": snr_db, "launch": launch, "fft_kind": fft_kind, "tuned": tuned,
            "launches_per_iteration": launches_per_iteration(od, plan), "k1_launches": _k1_launches(od, plan)}
@@ -486,7 +505,7 @@ def run_gpu(args):
 
     peak, peak_kind = _peaks()
     alg_bytes = 20.0 * p.m * p.m * J  # f 4 B + Gamma read 8 B + write 8 B per frame pixel
-    k1_avg_s = statistics.mean(r["k1_ms"]) / 1e3
+    k1_avg_s = statistics.mean(r["k1g_ms"]) / 1e3  # the frame update replayed from its own graph
     achieved = alg_bytes / k1_avg_s / 1e9
     tpf = _traffic_256(launch[0]) if p.m == 256 else None
     clocks = clk.summary()
@@ -500,11 +519,14 @@ def run_gpu(args):
                    "step": "one blind ADMM iteration (Algorithm 3 Steps 1-5, all frames), replayed as a CUDA graph",
                    "l2": "inputs larger than L2 (about 12 GB of frame traffic per iteration against 129 MB)",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu",
-                   "frame_update_ms": round(statistics.mean(r["k1_ms"]), 5),
+                   "frame_update_ms": round(statistics.mean(r["k1g_ms"]), 5),
+                   "frame_update_stage_launched_ms": round(statistics.mean(r["k1_ms"]), 5),
                    "probe_update_ms": round(statistics.mean(r["pu_ms"]), 5),
                    "subdomain_update_ms": round(statistics.mean(r["k2_ms"]), 5),
                    "stage_timing": f"{len(r['k1_ms'])} more iterations launched stage by stage (events around "
-                                   "each stage), after the timed steps",
+                                   "each stage), then the frame update replayed from its own CUDA graph "
+                                   f"{len(r['k1g_ms'])} times (frame_update_ms, the roofline's time), after the "
+                                   "timed steps",
                    "rf_after": r["rf"], "re_after": r["re"], "loss_after": r["loss"],
                    "snr_db_after": round(r["snr_db"], 3),
                    "launch": {"variant": launch[0], "fft": fft_kind,
@@ -544,7 +566,7 @@ def config2_leg(od, dev, args, K: int = 200, W: int = 5):
     torch.cuda.empty_cache()
     J = r["J"]
     peak, _ = _peaks()
-    k1 = statistics.mean(r["k1_ms"]) / 1e3
+    k1 = statistics.mean(r["k1g_ms"]) / 1e3
     fft_kind, launch = r["fft_kind"], r["launch"]
     return {"workload": WORKLOAD2, "value": round(J * K / (sum(r["step_ms"]) / 1e3), 1), "unit": UNIT,
             "steps": K, "ms_per_step": round(statistics.mean(r["step_ms"]), 5),

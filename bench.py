@@ -200,11 +200,9 @@ def _initial_probe(p, blind: bool) -> np.ndarray:
 
 
 def _k1_launches(od, plan) -> int:
-    """Kernel launches of one frame update (m = 256, three-pass variant 0: three
-    per wave of 76 frames; every other frame update is one launch)."""
-    if plan.geom.m == 256 and od.ptycho_plan_get_launch(plan)[0] == 0:
-        return 3 * -(-plan.n_frames // 76)
-    return 1
+    """Kernel launches of one frame update, as the library reports them (m = 256,
+    three-pass variant 0: three per wave; every other frame update is one)."""
+    return od.ptycho_plan_get_waves(plan)[2]
 
 
 def launches_per_iteration(od, plan) -> int:
@@ -419,14 +417,16 @@ def measure_workload(od, p, blind: bool, f_host: np.ndarray, dev, K: int, W: int
            "k1g_ms": k1g_ms,
            "pu_ms": pu_ms, "k2_ms": k2_ms, "wall_s": wall1 - wall0, "rf": rf, "re": re, "loss": loss,
            "snr_db": snr_db, "launch": launch, "fft_kind": fft_kind, "tuned": tuned,
-           "launches_per_iteration": launches_per_iteration(od, plan), "k1_launches": _k1_launches(od, plan)}
+           "launches_per_iteration": launches_per_iteration(od, plan), "k1_launches": _k1_launches(od, plan),
+           "waves": od.ptycho_plan_get_waves(plan)}
     return out
 
 
-def _k1_name(m: int, launch, fft_kind: int) -> str:
+def _k1_name(m: int, launch, fft_kind: int, waves=(0, 1, 1)) -> str:
     if m == 256:
         return ("frame_update256_cluster_kernel<16> (one launch, a 16-CTA cluster per frame)" if launch[0] == 1
-                else "rows_fwd256 / cols256<PROX> / rows_inv256 (three passes per wave of 76 frames)")
+                else f"rows_fwd256 / cols256<PROX> / rows_inv256 (three passes per wave of {waves[0]} frames, "
+                     f"{waves[1]} chains of waves side by side)")
     if fft_kind:
         return f"frame_update_f4_kernel<{2 - fft_kind}> (16 x 4 transform split, fft kind {fft_kind})"
     return f"frame_update_kernel<{m}, variant {launch[0]}> (two-stage transform split)"
@@ -535,7 +535,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
                      "traffic": None if tpf is None else round(tpf * J, 1),
-                     "kernel": _k1_name(p.m, launch, fft_kind),
+                     "kernel": _k1_name(p.m, launch, fft_kind, r["waves"]),
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "frame_update_launches": r["k1_launches"]},
@@ -572,7 +572,7 @@ def config2_leg(od, dev, args, K: int = 200, W: int = 5):
             "steps": K, "ms_per_step": round(statistics.mean(r["step_ms"]), 5),
             "frame_update_ms": round(1e3 * k1, 5), "subdomain_update_ms": round(statistics.mean(r["k2_ms"]), 5),
             "frame_update_hbm_frac": round(20.0 * p.m * p.m * J / k1 / 1e9 / peak, 4),
-            "kernel": _k1_name(p.m, launch, fft_kind),
+            "kernel": _k1_name(p.m, launch, fft_kind, r["waves"]),
             "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
             "rf_after": r["rf"], "re_after": r["re"], "snr_db_after": round(r["snr_db"], 3),
             "launch": {"variant": launch[0], "blocks_per_sm": launch[1], "fft": fft_kind}}

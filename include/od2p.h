@@ -439,6 +439,17 @@ int ptycho_plan_get_fft(const ptycho_plan_t *plan, int32_t *kind);
 int ptycho_plan_set_launch(ptycho_plan_t *plan, int32_t variant, int32_t blocks_per_sm, ptycho_stream_t stream);
 int ptycho_plan_get_launch(const ptycho_plan_t *plan, int32_t *variant, int32_t *blocks_per_sm,
                            int32_t *max_blocks_per_sm);
+/*
+ * How the frame update is launched (the paper has no counterpart; Step 1 of
+ * Algorithms 2 and 3 runs over all frames at once).  m = 256 with launch
+ * variant 0 moves the frames through its three passes in waves of
+ * *wave_frames frames, the waves dealt round-robin to *chains chains that run
+ * side by side on streams of the plan (forked from and joined back into the
+ * caller's stream), 3 launches per wave; every other shape reports 0, 1 and one
+ * launch.  *launches: kernel launches of one frame update.  Any output may be
+ * NULL.  Errors: INVALID_ARG (plan NULL).
+ */
+int ptycho_plan_get_waves(const ptycho_plan_t *plan, int32_t *wave_frames, int32_t *chains, int32_t *launches);
 
 /* Element count (complex) of a state selector (PTYCHO_STATE_*). */
 int od2p_state_len(const ptycho_plan_t *plan, int32_t which, int64_t *n_out);

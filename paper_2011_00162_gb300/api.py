@@ -23,6 +23,7 @@ __all__ = [
     "od2p_metrics", "od2p_state_len", "od2p_get_state", "od2p_set_state", "stagm_loss_grad", "PtychoError",
     "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
+    "ptycho_plan_get_waves",
     "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
     "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr", "od2p_operator_norms", "ptycho_peak_probe",
            "od2p_iterate_until", "od2p_gamma_snapshot", "od2p_frame_residual", "ptycho_plan_set_fft",
@@ -380,6 +381,13 @@ def ptycho_plan_get_launch(plan: Plan) -> tuple[int, int, int]:
     v, b, mx = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     check(plan._lib.ptycho_plan_get_launch(plan.handle, ctypes.byref(v), ctypes.byref(b), ctypes.byref(mx)))
     return v.value, b.value, mx.value
+
+
+def ptycho_plan_get_waves(plan: Plan) -> tuple[int, int, int]:
+    """(frames per wave, chains of waves side by side, kernel launches of one frame update)."""
+    wf, ch, ln = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(plan._lib.ptycho_plan_get_waves(plan.handle, ctypes.byref(wf), ctypes.byref(ch), ctypes.byref(ln)))
+    return wf.value, ch.value, ln.value
 
 
 def ptycho_batch_set_launch(batch: Batch, variant: int, blocks_per_sm: int = 0, stream=None) -> None:

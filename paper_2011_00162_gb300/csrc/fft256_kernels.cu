@@ -2,17 +2,23 @@
 //
 // A 256 x 256 complex64 frame is 512 KB, more than one block's shared memory,
 // so its unitary 2-D FFT runs as three passes over frame slabs:
-//   A: 16-row slabs -- exit wave (or a plain frame), row FFTs (16 x 16 DIF);
+//   A: 16-row slabs -- exit wave (or a plain frame), row FFTs;
 //   B: 16-column slabs -- column FFTs, the elementwise step of the caller
 //      (ST-AGM prox + Gamma update, loss and gradient, Fourier mask, or output),
 //      then the inverse column FFTs;
 //   C: 16-row slabs -- inverse row FFTs, natural-order output.
-// The intermediate T (natural rows / position columns after A, the reverse
-// after B) is a plan-owned buffer of WAVE frames: frames go through A, B, C in
-// waves of WAVE frames (512 KB each), so T stays in L2 between the passes and HBM sees the
-// algorithmic traffic plus q.  Position p = 16 s + s' holds frequency s + 16 s'
-// along each axis (as for the smaller sizes); Gamma and sqrt f are stored at
-// position row-major index p_r * 256 + p_c.
+// Every 256-point transform is 16 x 16: with n = n1 + 16 n2 and k = k1 + 16 k2,
+// stage 1 takes a 16-point DFT over n2 at fixed n1, the twiddle
+// exp(-+2 pi i n1 k1 / 256), and stage 2 a 16-point DFT over n1 at fixed k1.
+// A thread that holds the elements n1 + 16 n2 of a row (stage 1) or the
+// frequencies k1 + 16 k2 (stage 2 output) reads or writes them straight from
+// or to global memory, sixteen lanes covering 128 contiguous bytes, so each
+// pass exchanges data through shared memory once per transform direction.
+// The intermediate T (spatial rows / frequency columns after A, the reverse
+// after B) is a plan-owned buffer per wave chain: frames go through A, B, C in
+// waves (512 KB a frame), so T stays in L2 between the passes and HBM sees the
+// algorithmic traffic plus q.  T, Gamma and sqrt f hold frequencies in natural
+// row-major order (k_r * 256 + k_c).
 #include "od2p_internal.h"
 #include "fft_device.cuh"
 
@@ -24,10 +30,8 @@ namespace {
 constexpr int BM = 256, BR = 16, BMM = BM * BM;
 constexpr int SLAB = 16;   // rows (A, C) or columns (B) per block
 constexpr int NTB = 256;   // threads per block
-constexpr int PA = BM + 1; // pitch of a row slab in shared memory
+constexpr int PX = BR * (BR + 1);  // pitch of a row in a row slab: 16 groups of 17
 constexpr int PB = SLAB + 1;
-
-__device__ __forceinline__ int freq_of(int p) { return p / BR + BR * (p % BR); }
 
 enum ModeB : int { B_PROX = 0, B_FWD_OUT = 1, B_LOSS = 2, B_MASK = 3, B_IFFT_IN = 4 };
 
@@ -72,59 +76,47 @@ __global__ void __launch_bounds__(NTB) rows_fwd256_kernel(PassA a)
 {
     extern __shared__ float4 smem4[];
     float2 *tw = reinterpret_cast<float2 *>(smem4);
-    float2 *buf = tw + BM;
+    float2 *buf = tw + BM;  // SLAB rows x PX: stage-1 output (k1, n1) at 17 k1 + n1
     const int f = blockIdx.x / (BM / SLAB), rb = blockIdx.x % (BM / SLAB), j = a.j0 + f;
     for (int k = threadIdx.x; k < BM; k += NTB) tw[k] = a.tw[k];
-    const int c = threadIdx.x;
-    // all of the thread's loads in flight before the first shared-memory store
-    float2 v[SLAB];
+    // thread (r, lo): stage 1 at n1 = lo, stage 2 at k1 = lo; sixteen lanes
+    // touch 128 contiguous bytes of one row in every global access
+    const int lo = threadIdx.x % BR, r = threadIdx.x / BR, row = rb * SLAB + r;
+    float2 x[BR];
     if (a.plain) {
+        const float2 *src = a.plain + (size_t)j * BMM + row * BM + lo;
 #pragma unroll
-        for (int r = 0; r < SLAB; ++r) v[r] = __ldg(a.plain + (size_t)j * BMM + (rb * SLAB + r) * BM + c);
+        for (int t = 0; t < BR; ++t) x[t] = __ldg(src + BR * t);
     } else {
-        const float2 *w = a.Wd ? a.Wd + (size_t)a.frame_sub[j] * BMM : a.w;
-        const float2 *uj = a.u + a.frame_base[j];
-        const int pitch = a.frame_pitch[j];
-        float2 wv[SLAB];
+        const float2 *w = (a.Wd ? a.Wd + (size_t)a.frame_sub[j] * BMM : a.w) + row * BM + lo;
+        const float2 *uj = a.u + a.frame_base[j] + (size_t)row * a.frame_pitch[j] + lo;
+        float2 wv[BR];
 #pragma unroll
-        for (int r = 0; r < SLAB; ++r) {
-            const int row = rb * SLAB + r;
-            wv[r] = __ldg(w + row * BM + c);
-            v[r] = __ldg(uj + (size_t)row * pitch + c);
+        for (int t = 0; t < BR; ++t) {
+            wv[t] = __ldg(w + BR * t);
+            x[t] = __ldg(uj + BR * t);
         }
 #pragma unroll
-        for (int r = 0; r < SLAB; ++r) v[r] = cmul(wv[r], v[r]);
+        for (int t = 0; t < BR; ++t) x[t] = cmul(wv[t], x[t]);
     }
+    // row stage 1: DFT over n2 of the elements n1 + 16 n2
+    dft<BR, false>(x);
+    __syncthreads();  // twiddles in place
+    float2 *rp = buf + r * PX;
 #pragma unroll
-    for (int r = 0; r < SLAB; ++r) buf[r * PA + c] = v[r];
+    for (int s = 0; s < BR; ++s) rp[(BR + 1) * s + lo] = cmul(x[s], tw[lo * s]);
     __syncthreads();
-    {   // row stage 1: lanes on rows (odd pitch), 16 strided elements each
-        const int r = threadIdx.x % SLAB, n1 = threadIdx.x / SLAB;
-        float2 *rp = buf + r * PA;
-        float2 x[BR];
+    // row stage 2: DFT over n1 -> frequencies k1 + 16 k2, stored in natural order
 #pragma unroll
-        for (int t = 0; t < BR; ++t) x[t] = rp[n1 + BR * t];
-        dft<BR, false>(x);
+    for (int t = 0; t < BR; ++t) x[t] = rp[(BR + 1) * lo + t];
+    dft<BR, false>(x);
+    float2 *o = a.T + ((size_t)f * BM + row) * BM + lo;
 #pragma unroll
-        for (int s = 0; s < BR; ++s) rp[n1 + BR * s] = cmul(x[s], tw[n1 * s]);
-    }
-    __syncthreads();
-    {   // row stage 2: 16 contiguous elements
-        const int r = threadIdx.x % SLAB, s = threadIdx.x / SLAB;
-        float2 *rp = buf + r * PA + BR * s;
-        float2 x[BR];
-#pragma unroll
-        for (int t = 0; t < BR; ++t) x[t] = rp[t];
-        dft<BR, false>(x);
-#pragma unroll
-        for (int t = 0; t < BR; ++t) rp[t] = x[t];
-    }
-    __syncthreads();
-    for (int r = 0; r < SLAB; ++r) a.T[((size_t)f * BM + rb * SLAB + r) * BM + c] = buf[r * PA + c];
+    for (int t = 0; t < BR; ++t) o[BR * t] = x[t];
 }
 
 #ifndef OD2P_COLS256_MINB
-#define OD2P_COLS256_MINB 4
+#define OD2P_COLS256_MINB 3
 #endif
 // MODE: the elementwise step between the column transforms (compile-time, so
 // that the per-element loop carries no mode tests).
@@ -133,53 +125,42 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
 {
     extern __shared__ float4 smem4[];
     float2 *tw = reinterpret_cast<float2 *>(smem4);
-    float2 *buf = tw + BM;                       // BM rows x PB
+    float2 *buf = tw + BM;                       // BM rows x PB: (k1, n1) at row 16 k1 + n1
     float *red = reinterpret_cast<float *>(buf + BM * PB);
     const int f = blockIdx.x / (BM / SLAB), cb = blockIdx.x % (BM / SLAB), j = a.j0 + f;
     if (MODE == B_PROX) {
-        // this slab's Gamma (128 B) and sqrt f (64 B) of each position row, into
+        // this slab's Gamma (128 B) and sqrt f (64 B) of each frequency row, into
         // L2 while the column FFT runs
         const size_t gi = (size_t)j * BMM + (size_t)threadIdx.x * BM + cb * SLAB;
         asm volatile("prefetch.global.L2 [%0];" ::"l"(a.gamma + gi));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(a.sqrtf_ + gi));
     }
     for (int k = threadIdx.x; k < BM; k += NTB) tw[k] = a.tw[k];
-    {
-        constexpr int NR = BM / (NTB / SLAB);  // rows per thread
-        const int cl = threadIdx.x % SLAB, r0 = threadIdx.x / SLAB;
-        float2 v[NR];
+    // thread (hi, cl) owns column kc; hi is n1 in stage 1 and k1 in stage 2
+    const int cl = threadIdx.x % SLAB, hi = threadIdx.x / SLAB, kc = cb * SLAB + cl;
+    float2 x[BR];
+    if (MODE == B_IFFT_IN) {
+        // frequency rows k1 + 16 k2 of column kc (k1 = hi): the inverse stage 2 input
 #pragma unroll
-        for (int i = 0; i < NR; ++i) {
-            const int r = r0 + i * (NTB / SLAB);
-            if (MODE == B_IFFT_IN)
-                v[i] = __ldg(a.in + (size_t)j * BMM + freq_of(r) * BM + freq_of(cb * SLAB + cl));
-            else
-                v[i] = a.T[((size_t)f * BM + r) * BM + cb * SLAB + cl];
-        }
+        for (int t = 0; t < BR; ++t) x[t] = __ldg(a.in + (size_t)j * BMM + (size_t)(hi + BR * t) * BM + kc);
+    } else {
+        // column stage 1: DFT over n2 of the spatial rows n1 + 16 n2
 #pragma unroll
-        for (int i = 0; i < NR; ++i) buf[(r0 + i * (NTB / SLAB)) * PB + cl] = v[i];
-    }
-    __syncthreads();
-    const int cl = threadIdx.x % SLAB, hi = threadIdx.x / SLAB;  // hi: n1 (stage 1) or s (stage 2)
-    if (MODE != B_IFFT_IN) {  // column stage 1
-        float2 x[BR];
-#pragma unroll
-        for (int t = 0; t < BR; ++t) x[t] = buf[(hi + BR * t) * PB + cl];
+        for (int t = 0; t < BR; ++t) x[t] = a.T[((size_t)f * BM + hi + BR * t) * BM + kc];
         dft<BR, false>(x);
+        __syncthreads();  // twiddles in place
 #pragma unroll
         for (int s = 0; s < BR; ++s) buf[(hi + BR * s) * PB + cl] = cmul(x[s], tw[hi * s]);
         __syncthreads();
-    }
-    float part = 0.f;
-    {   // column stage 2, the elementwise step, inverse column stage 2
-        float2 x[BR];
 #pragma unroll
         for (int t = 0; t < BR; ++t) x[t] = buf[(BR * hi + t) * PB + cl];
-        const int pc = cb * SLAB + cl;
-        // this thread's column segment of Gamma and sqrt f (position rows
-        // 16 hi .. 16 hi + 15), loaded before any Gamma store (the compiler may
-        // not move loads past those stores)
-        const size_t g0 = (size_t)j * BMM + (size_t)(BR * hi) * BM + pc;
+    }
+    float part = 0.f;
+    {   // column stage 2 (frequencies k1 + 16 k2), the elementwise step, inverse stage 2
+        // this thread's Gamma and sqrt f (frequency rows hi + 16 t of column kc),
+        // loaded before any Gamma store (the compiler may not move loads past those
+        // stores)
+        const size_t g0 = (size_t)j * BMM + (size_t)hi * BM + kc;
         float2 *gseg = a.gamma + g0;
         const float *fseg = a.sqrtf_ + g0;
         float2 gmv[MODE == B_PROX ? BR : 1];
@@ -189,16 +170,15 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
             for (int t = 0; t < BR; ++t) {
                 // read once per iteration: streaming loads (evict first) keep the
                 // intermediate T resident in L2
-                sfv[t] = __ldcs(fseg + t * BM);
-                if (MODE == B_PROX) gmv[MODE == B_PROX ? t : 0] = __ldcs(gseg + t * BM);
+                sfv[t] = __ldcs(fseg + BR * t * BM);
+                if (MODE == B_PROX) gmv[MODE == B_PROX ? t : 0] = __ldcs(gseg + BR * t * BM);
             }
         }
         if (MODE != B_IFFT_IN) dft<BR, false>(x);
         const float inv_m = 1.f / (float)BM;
 #pragma unroll
         for (int t = 0; t < BR; ++t) {
-            const int pr = BR * hi + t;
-            const size_t gi = (size_t)j * BMM + (size_t)pr * BM + pc;
+            const int kr = hi + BR * t;
             if (MODE == B_PROX) {
                 const float2 ax = cscale(x[t], inv_m);
                 const float sf = sfv[t];
@@ -208,7 +188,7 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
                 const float2 y = cadd(gm, ax);
                 const float2 z = stagm_prox(y, sf, a.pc);
                 const float2 gn = csub(y, z);
-                __stcs(gseg + t * BM, gn);
+                __stcs(gseg + BR * t * BM, gn);
                 x[t] = csub(z, gn);
             } else if (MODE == B_LOSS) {
                 const float2 xv = cscale(x[t], inv_m);
@@ -224,9 +204,9 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
                 }
                 x[t] = cscale(xv, gs);
             } else if (MODE == B_MASK) {
-                x[t] = cscale(x[t], inv_m * __ldg(a.mask + freq_of(pr) * BM + freq_of(pc)));
+                x[t] = cscale(x[t], inv_m * __ldg(a.mask + kr * BM + kc));
             } else if (MODE == B_FWD_OUT) {
-                a.out[(size_t)j * BMM + freq_of(pr) * BM + freq_of(pc)] = cscale(x[t], inv_m);
+                a.out[(size_t)j * BMM + kr * BM + kc] = cscale(x[t], inv_m);
             }
         }
         if (MODE != B_FWD_OUT) {
@@ -241,19 +221,12 @@ __global__ void __launch_bounds__(NTB, OD2P_COLS256_MINB) cols256_kernel(PassB a
     }
     if (MODE == B_FWD_OUT) return;
     __syncthreads();
-    {   // inverse column stage 1
-        float2 x[BR];
+    {   // inverse column stage 1 -> spatial rows n1 + 16 n2 (n1 = hi)
 #pragma unroll
         for (int s = 0; s < BR; ++s) x[s] = cmulc(buf[(hi + BR * s) * PB + cl], tw[hi * s]);
         dft<BR, true>(x);
 #pragma unroll
-        for (int t = 0; t < BR; ++t) buf[(hi + BR * t) * PB + cl] = x[t];
-    }
-    __syncthreads();
-    {
-        const int c2 = threadIdx.x % SLAB, r0 = threadIdx.x / SLAB;
-        for (int r = r0; r < BM; r += NTB / SLAB)
-            a.T[((size_t)f * BM + r) * BM + cb * SLAB + c2] = buf[r * PB + c2];
+        for (int t = 0; t < BR; ++t) a.T[((size_t)f * BM + hi + BR * t) * BM + kc] = x[t];
     }
 }
 
@@ -261,62 +234,48 @@ __global__ void __launch_bounds__(NTB) rows_inv256_kernel(PassC a, const float2 
 {
     extern __shared__ float4 smem4[];
     float2 *tw = reinterpret_cast<float2 *>(smem4);
-    float2 *buf = tw + BM;
+    float2 *buf = tw + BM;  // SLAB rows x PX: inverse stage-2 output (k1, n1) at 17 k1 + n1
     const int f = blockIdx.x / (BM / SLAB), rb = blockIdx.x % (BM / SLAB), j = a.j0 + f;
     for (int k = threadIdx.x; k < BM; k += NTB) tw[k] = twg[k];
-    const int c = threadIdx.x;
-    {
-        float2 v[SLAB];
+    // thread (r, lo): inverse stage 2 at k1 = lo, inverse stage 1 at n1 = lo
+    const int lo = threadIdx.x % BR, r = threadIdx.x / BR, row = rb * SLAB + r;
+    float2 x[BR];
+    {   // inverse row stage 2: DFT over k2 of the frequencies k1 + 16 k2
+        const float2 *src = a.T + ((size_t)f * BM + row) * BM + lo;
 #pragma unroll
-        for (int r = 0; r < SLAB; ++r) v[r] = a.T[((size_t)f * BM + rb * SLAB + r) * BM + c];
-#pragma unroll
-        for (int r = 0; r < SLAB; ++r) buf[r * PA + c] = v[r];
-    }
-    __syncthreads();
-    {   // inverse row stage 2
-        const int r = threadIdx.x % SLAB, s = threadIdx.x / SLAB;
-        float2 *rp = buf + r * PA + BR * s;
-        float2 x[BR];
-#pragma unroll
-        for (int t = 0; t < BR; ++t) x[t] = rp[t];
+        for (int t = 0; t < BR; ++t) x[t] = src[BR * t];
         dft<BR, true>(x);
+        float2 *rp = buf + r * PX + (BR + 1) * lo;
 #pragma unroll
         for (int t = 0; t < BR; ++t) rp[t] = x[t];
     }
-    __syncthreads();
-    {   // inverse row stage 1
-        const int r = threadIdx.x % SLAB, n1 = threadIdx.x / SLAB;
-        float2 *rp = buf + r * PA;
-        float2 x[BR];
+    __syncthreads();  // (and the twiddles)
+    {   // inverse row stage 1 -> spatial columns n1 + 16 n2
+        const float2 *rp = buf + r * PX + lo;
 #pragma unroll
-        for (int s = 0; s < BR; ++s) x[s] = cmulc(rp[n1 + BR * s], tw[n1 * s]);
+        for (int s = 0; s < BR; ++s) x[s] = cmulc(rp[(BR + 1) * s], tw[lo * s]);
         dft<BR, true>(x);
-#pragma unroll
-        for (int t = 0; t < BR; ++t) rp[n1 + BR * t] = x[t];
     }
-    __syncthreads();
-    // the output rows rb * SLAB .. of column c, with the mode tests and the
-    // per-frame bases hoisted out of the row loop
+    // the output row `row`, columns lo + 16 t, with the mode tests and the
+    // per-frame bases hoisted out of the loop
     const float sc = a.scale;
-    const size_t r0 = (size_t)rb * SLAB;
     if (a.slot) {  // nonblind gather slots: conj(w) o q_j at the pixel's rank
-        const int pitch = a.frame_pitch[j];
-        const uint8_t *rk = a.rank + (size_t)j * BMM + r0 * BM + c;
-        const float2 *wc = a.wconj + r0 * BM + c;
-        float2 *sl = a.slot + a.frame_base[j] + r0 * pitch + c;
+        const uint8_t *rk = a.rank + (size_t)j * BMM + row * BM + lo;
+        const float2 *wc = a.wconj + row * BM + lo;
+        float2 *sl = a.slot + a.frame_base[j] + (size_t)row * a.frame_pitch[j] + lo;
         const size_t stride = (size_t)a.slot_stride;
 #pragma unroll
-        for (int r = 0; r < SLAB; ++r)
-            sl[__ldg(rk + r * BM) * stride + (size_t)r * pitch] = cmulc(cscale(buf[r * PA + c], sc), __ldg(wc + r * BM));
+        for (int t = 0; t < BR; ++t)
+            sl[__ldg(rk + BR * t) * stride + BR * t] = cmulc(cscale(x[t], sc), __ldg(wc + BR * t));
     } else {
-        float2 *o = a.out + (size_t)j * BMM + r0 * BM + c;
+        float2 *o = a.out + (size_t)j * BMM + row * BM + lo;
         if (a.wconj) {
-            const float2 *wc = a.wconj + r0 * BM + c;
+            const float2 *wc = a.wconj + row * BM + lo;
 #pragma unroll
-            for (int r = 0; r < SLAB; ++r) o[r * BM] = cmulc(cscale(buf[r * PA + c], sc), __ldg(wc + r * BM));
+            for (int t = 0; t < BR; ++t) o[BR * t] = cmulc(cscale(x[t], sc), __ldg(wc + BR * t));
         } else {
 #pragma unroll
-            for (int r = 0; r < SLAB; ++r) __stcs(o + r * BM, cscale(buf[r * PA + c], sc));
+            for (int t = 0; t < BR; ++t) __stcs(o + BR * t, cscale(x[t], sc));
         }
     }
 }
@@ -326,7 +285,7 @@ __global__ void __launch_bounds__(NTB) rows_inv256_kernel(PassC a, const float2 
 // distributed shared memory, so the frame crosses HBM once per direction and
 // no intermediate leaves the chip.  CTA c of the cluster owns rows
 // [RPC c, RPC c + RPC) of the frame while the rows are transformed (buffer A)
-// and position columns [CPC c, CPC c + CPC) while the columns are (buffer B).
+// and column frequencies [CPC c, CPC c + CPC) while the columns are (buffer B).
 // Between the phases every CTA sends each part of its data to the CTA that
 // owns it next with asynchronous shared-memory stores into that CTA's other
 // buffer (st.async), each completing bytes on the receiver's transaction
@@ -362,13 +321,6 @@ __device__ __forceinline__ unsigned cluster_addr(unsigned a, unsigned rank)
     unsigned out;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(a), "r"(rank));
     return out;
-}
-__device__ __forceinline__ void st_async_v4(unsigned addr, float4 v, unsigned bar)
-{
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
-                     addr),
-                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
-                 : "memory");
 }
 __device__ __forceinline__ void st_async_v2(unsigned addr, float2 v, unsigned bar)
 {
@@ -410,11 +362,11 @@ __device__ __forceinline__ void prefetch_bulk_l2(const void *p, unsigned bytes)
 template <int CL>
 struct Cl256 {
     static constexpr int RPC = BM / CL;  // rows per CTA in the row phase
-    static constexpr int CPC = BM / CL;  // position columns per CTA in the column phase
+    static constexpr int CPC = BM / CL;  // column frequencies per CTA in the column phase
     static constexpr int NT = BR * RPC;  // one 16-point DFT per thread and stage
     static constexpr int MINB = 768 / NT;
-    static constexpr int PR = BM + 1;    // buffer A pitch (odd: conflict-free stage-2 reads)
-    static constexpr int PC = CPC + 2;   // buffer B pitch (16-byte rows, spread banks)
+    static constexpr int PR = BR * (BR + 1) + 1;  // buffer A pitch (rows hold 16 groups of 17)
+    static constexpr int PC = CPC + 2;   // buffer B pitch (spread banks)
     static constexpr int A_ELEMS = RPC * PR, B_ELEMS = BM * PC;
     static constexpr unsigned XBYTES = (unsigned)(BM * CPC * sizeof(float2));  // bytes owed per exchange
     static constexpr size_t SMEM = sizeof(float2) * (BM + A_ELEMS + B_ELEMS) + 2 * sizeof(uint64_t) +
@@ -430,7 +382,7 @@ __global__ void __launch_bounds__(Cl256<CL>::NT, Cl256<CL>::MINB) frame_update25
     extern __shared__ float4 smem4[];
     float2 *tw = reinterpret_cast<float2 *>(smem4);
     float2 *bufA = tw + BM;           // rows RPC c ..: RPC x PR
-    float2 *bufB = bufA + K::A_ELEMS;  // position columns CPC c ..: BM x PC
+    float2 *bufB = bufA + K::A_ELEMS;  // column frequencies CPC c ..: BM x PC
     uint64_t *bar = reinterpret_cast<uint64_t *>(bufB + K::B_ELEMS);  // [0]: columns owed, [1]: rows owed
     float *red = reinterpret_cast<float *>(bar + 2);
     const int tid = threadIdx.x;
@@ -445,7 +397,7 @@ __global__ void __launch_bounds__(Cl256<CL>::NT, Cl256<CL>::MINB) frame_update25
     // every CTA's barriers are initialised before any CTA sends to them (waited
     // for just before the first send)
     cluster_arrive_relaxed();
-    // this CTA's Gamma and sqrt f columns of every position row, into L2 while
+    // this CTA's Gamma and sqrt f columns of every frequency row, into L2 while
     // the row transforms run
     for (int k = tid; k < 2 * BM; k += NT) {
         const size_t gi = fo + (size_t)(k % BM) * BM + CPC * c;
@@ -470,7 +422,7 @@ __global__ void __launch_bounds__(Cl256<CL>::NT, Cl256<CL>::MINB) frame_update25
         for (int s = 0; s < BR; ++s) rp[n1 + BR * s] = cmul(x[s], tw[n1 * s]);
     }
     __syncthreads();
-    // ---- rows, stage 2: DFTs over n1 -> positions 16 s + k; first exchange
+    // ---- rows, stage 2: DFTs over n1 -> frequencies s + 16 t; first exchange
     {
         const int r = tid % RPC, s = tid / RPC;
         float2 x[BR];
@@ -479,16 +431,18 @@ __global__ void __launch_bounds__(Cl256<CL>::NT, Cl256<CL>::MINB) frame_update25
         dft<BR, false>(x);
         if (tid == 0) tbar_expect(&bar[0], K::XBYTES);
         cluster_wait();  // the receivers' barriers are initialised
-        // position columns 16 s .. 16 s + 15 of row RPC c + r belong to CTA 16 s / CPC
-        const unsigned dst = (unsigned)(BR * s) / CPC;
-        const unsigned da = cluster_addr(smem_addr(bufB + (RPC * c + r) * PC + (BR * s) % CPC), dst);
-        const unsigned db = cluster_addr(smem_addr(&bar[0]), dst);
+        // column frequency s + 16 t of row RPC c + r belongs to CTA (s + 16 t) / CPC
+        const unsigned bufB_row = smem_addr(bufB + (RPC * c + r) * PC), bar0 = smem_addr(&bar[0]);
 #pragma unroll
-        for (int k = 0; k < BR / 2; ++k)
-            st_async_v4(da + 16u * k, make_float4(x[2 * k].x, x[2 * k].y, x[2 * k + 1].x, x[2 * k + 1].y), db);
+        for (int t = 0; t < BR; ++t) {
+            const int kc = s + BR * t;
+            const unsigned dst = (unsigned)(kc / CPC);
+            st_async_v2(cluster_addr(bufB_row + (unsigned)(sizeof(float2) * (kc % CPC)), dst), x[t],
+                        cluster_addr(bar0, dst));
+        }
     }
     if (!tbar_wait(&bar[0])) *a.err = 1;  // every CTA's share of this CTA's columns has arrived
-    // ---- columns, stage 1: DFTs over t at n1 of position column CPC c + col
+    // ---- columns, stage 1: DFTs over t at n1 of column frequency CPC c + col
     {
         const int col = tid % CPC, n1 = tid / CPC;
         float2 x[BR];
@@ -500,25 +454,25 @@ __global__ void __launch_bounds__(Cl256<CL>::NT, Cl256<CL>::MINB) frame_update25
     }
     __syncthreads();
     // ---- columns, stage 2, the ST-AGM prox and Gamma update (eqs. updateZ,
-    // updateM-1-multi) on position rows 16 s + t, inverse stage 2
+    // updateM-1-multi) on frequency rows s + 16 t, inverse stage 2
     float part = 0.f;
     {
-        const int col = tid % CPC, s = tid / CPC, pc = CPC * c + col;
+        const int col = tid % CPC, s = tid / CPC, kc = CPC * c + col;
         float2 x[BR];
 #pragma unroll
         for (int t = 0; t < BR; ++t) x[t] = bufB[(BR * s + t) * PC + col];
         float2 gmv[BR];
         float sfv[BR];
-        const float2 *gp = a.gamma + fo + (size_t)(BR * s) * BM + pc;
-        const float *fp = a.sqrtf_ + fo + (size_t)(BR * s) * BM + pc;
+        const float2 *gp = a.gamma + fo + (size_t)s * BM + kc;
+        const float *fp = a.sqrtf_ + fo + (size_t)s * BM + kc;
 #pragma unroll
         for (int t = 0; t < BR; ++t) {
-            sfv[t] = __ldg(fp + t * BM);
-            gmv[t] = gp[t * BM];
+            sfv[t] = __ldg(fp + BR * t * BM);
+            gmv[t] = gp[BR * t * BM];
         }
         dft<BR, false>(x);
         const float inv_m = 1.f / (float)BM;
-        float2 *gw = a.gamma + fo + (size_t)(BR * s) * BM + pc;
+        float2 *gw = a.gamma + fo + (size_t)s * BM + kc;
 #pragma unroll
         for (int t = 0; t < BR; ++t) {
             const float2 ax = cscale(x[t], inv_m);
@@ -528,7 +482,7 @@ __global__ void __launch_bounds__(Cl256<CL>::NT, Cl256<CL>::MINB) frame_update25
             const float2 y = cadd(gmv[t], ax);
             const float2 z = stagm_prox(y, sf, a.pc);
             const float2 gn = csub(y, z);
-            gw[t * BM] = gn;
+            gw[BR * t * BM] = gn;
             x[t] = csub(z, gn);
         }
         dft<BR, true>(x);
@@ -538,7 +492,7 @@ __global__ void __launch_bounds__(Cl256<CL>::NT, Cl256<CL>::MINB) frame_update25
     __syncthreads();
     // ---- columns, inverse stage 1 -> spatial rows n1 + 16 t; second exchange
     {
-        const int col = tid % CPC, n1 = tid / CPC, pc = CPC * c + col;
+        const int col = tid % CPC, n1 = tid / CPC, kc = CPC * c + col;
         float2 x[BR];
 #pragma unroll
         for (int s = 0; s < BR; ++s) x[s] = cmulc(bufB[(n1 + BR * s) * PC + col], tw[n1 * s]);
@@ -548,21 +502,22 @@ __global__ void __launch_bounds__(Cl256<CL>::NT, Cl256<CL>::MINB) frame_update25
         for (int t = 0; t < BR; ++t) {
             const int R = n1 + BR * t;  // spatial row, owned by CTA R / RPC
             const unsigned dst = (unsigned)(R / RPC);
-            st_async_v2(cluster_addr(smem_addr(bufA + (R % RPC) * PR + pc), dst), x[t],
+            st_async_v2(cluster_addr(smem_addr(bufA + (R % RPC) * PR + kc), dst), x[t],
                         cluster_addr(smem_addr(&bar[1]), dst));
         }
     }
     if (!tbar_wait(&bar[1])) *a.err = 1;  // this CTA's rows have arrived
-    // ---- rows, inverse stage 2
+    // ---- rows, inverse stage 2: DFTs over k2 of the frequencies s + 16 k2
     {
         const int r = tid % RPC, s = tid / RPC;
-        float2 *rp = bufA + r * PR + BR * s;
+        float2 *rp = bufA + r * PR;
         float2 x[BR];
 #pragma unroll
-        for (int t = 0; t < BR; ++t) x[t] = rp[t];
+        for (int t = 0; t < BR; ++t) x[t] = rp[s + BR * t];
         dft<BR, true>(x);
+        __syncthreads();  // every frequency has been read
 #pragma unroll
-        for (int t = 0; t < BR; ++t) rp[t] = x[t];
+        for (int t = 0; t < BR; ++t) rp[(BR + 1) * s + t] = x[t];  // (k1, n1) at 17 k1 + n1
     }
     __syncthreads();
     // ---- rows, inverse stage 1 -> spatial columns n1 + 16 t; q_j, or conj(w) q_j
@@ -572,7 +527,7 @@ __global__ void __launch_bounds__(Cl256<CL>::NT, Cl256<CL>::MINB) frame_update25
         const float2 *rp = bufA + r * PR;
         float2 x[BR];
 #pragma unroll
-        for (int s = 0; s < BR; ++s) x[s] = cmulc(rp[n1 + BR * s], tw[n1 * s]);
+        for (int s = 0; s < BR; ++s) x[s] = cmulc(rp[(BR + 1) * s + n1], tw[n1 * s]);
         dft<BR, true>(x);
         const float sc = 1.f / (float)BM;
         if (a.slot) {
@@ -633,7 +588,7 @@ int frame_update_256_cluster(ptycho_plan_s *p, cudaStream_t s)
     return PTYCHO_OK;
 }
 
-constexpr size_t SMEM_A = sizeof(float2) * (BM + SLAB * PA);
+constexpr size_t SMEM_A = sizeof(float2) * (BM + SLAB * PX);
 constexpr size_t SMEM_B = sizeof(float2) * (BM + BM * PB) + sizeof(float) * (NTB / 32);
 
 // One pass-A / pass-B / pass-C sequence over frames [j0, j0 + J) in waves.
@@ -644,38 +599,68 @@ struct Pipeline {
     PassC C;
 };
 
-int run_waves(Pipeline P, int J, int waves_frames, cudaStream_t s)
+// Waves go round-robin to up to WAVE_CHAINS_256 chains -- the caller's stream
+// and the plan's wave streams, each chain with its own T buffer -- so that the
+// blocks of one chain's pass fill the SMs that another chain's pass leaves idle
+// at its tail, and the DRAM-bound column pass of one wave runs beside the
+// L2-bound row passes of others.  The chains fork from and join back into the
+// caller's stream (inside a graph capture these become graph edges).
+int run_waves(const ptycho_plan_s *p, Pipeline P, int J, int waves_frames, cudaStream_t s)
 {
     const int slabs = BM / SLAB;
-    for (int w0 = 0; w0 < J; w0 += waves_frames) {
-        const int nf = std::min(waves_frames, J - w0);
+    const int nch = std::max(1, std::min(p->t_waves, (J + waves_frames - 1) / waves_frames));
+    cudaStream_t st[WAVE_CHAINS_256];
+    float2 *T[WAVE_CHAINS_256];
+    for (int c = 0; c < nch; ++c) {
+        st[c] = c ? p->wave_stream[c] : s;
+        T[c] = p->d_T + (size_t)c * WAVE_256 * BMM;
+    }
+    if (nch > 1) {
+        OD2P_CUDA(cudaEventRecord(p->wave_ev[0], s));
+        for (int c = 1; c < nch; ++c) OD2P_CUDA(cudaStreamWaitEvent(st[c], p->wave_ev[0], 0));
+    }
+    cudaError_t e = cudaSuccess;
+    for (int w0 = 0, wi = 0; w0 < J && e == cudaSuccess; w0 += waves_frames, ++wi) {
+        const int nf = std::min(waves_frames, J - w0), ch = wi % nch;
+        const cudaStream_t sw = st[ch];
         if (P.do_a) {
             PassA a = P.A;
             a.j0 = w0;
             a.nf = nf;
-            rows_fwd256_kernel<<<nf * slabs, NTB, SMEM_A, s>>>(a);
-            OD2P_CUDA(cudaGetLastError());
+            a.T = T[ch];
+            rows_fwd256_kernel<<<nf * slabs, NTB, SMEM_A, sw>>>(a);
+            e = cudaGetLastError();
         }
         PassB b = P.B;
         b.j0 = w0;
         b.nf = nf;
         b.part_off = w0 * slabs;
-        switch (b.mode) {
-        case B_PROX: cols256_kernel<B_PROX><<<nf * slabs, NTB, SMEM_B, s>>>(b); break;
-        case B_FWD_OUT: cols256_kernel<B_FWD_OUT><<<nf * slabs, NTB, SMEM_B, s>>>(b); break;
-        case B_LOSS: cols256_kernel<B_LOSS><<<nf * slabs, NTB, SMEM_B, s>>>(b); break;
-        case B_MASK: cols256_kernel<B_MASK><<<nf * slabs, NTB, SMEM_B, s>>>(b); break;
-        default: cols256_kernel<B_IFFT_IN><<<nf * slabs, NTB, SMEM_B, s>>>(b); break;
+        b.T = T[ch];
+        if (e == cudaSuccess) {
+            switch (b.mode) {
+            case B_PROX: cols256_kernel<B_PROX><<<nf * slabs, NTB, SMEM_B, sw>>>(b); break;
+            case B_FWD_OUT: cols256_kernel<B_FWD_OUT><<<nf * slabs, NTB, SMEM_B, sw>>>(b); break;
+            case B_LOSS: cols256_kernel<B_LOSS><<<nf * slabs, NTB, SMEM_B, sw>>>(b); break;
+            case B_MASK: cols256_kernel<B_MASK><<<nf * slabs, NTB, SMEM_B, sw>>>(b); break;
+            default: cols256_kernel<B_IFFT_IN><<<nf * slabs, NTB, SMEM_B, sw>>>(b); break;
+            }
+            e = cudaGetLastError();
         }
-        OD2P_CUDA(cudaGetLastError());
-        if (P.do_c) {
+        if (P.do_c && e == cudaSuccess) {
             PassC c = P.C;
             c.j0 = w0;
             c.nf = nf;
-            rows_inv256_kernel<<<nf * slabs, NTB, SMEM_A, s>>>(c, P.B.tw);
-            OD2P_CUDA(cudaGetLastError());
+            c.T = T[ch];
+            rows_inv256_kernel<<<nf * slabs, NTB, SMEM_A, sw>>>(c, P.B.tw);
+            e = cudaGetLastError();
         }
     }
+    for (int c = 1; c < nch; ++c) {  // join even after a failed launch, so that a capture can end
+        const cudaError_t e1 = cudaEventRecord(p->wave_ev[c], st[c]);
+        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(s, p->wave_ev[c], 0) : e1;
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "m = 256 frame passes");
     return PTYCHO_OK;
 }
 
@@ -703,28 +688,12 @@ __global__ void ingest256_kernel(int J, const float *f, float *sqrtf_, float *pa
     const int j = blockIdx.x;
     float acc = 0.f;
     for (int k = threadIdx.x; k < BMM; k += blockDim.x) {
-        const int kr = k / BM, kc = k % BM;
-        const int pr = BR * (kr % BR) + kr / BR, pc = BR * (kc % BR) + kc / BR;
         const float v = sqrtf(fmaxf(__ldg(f + (size_t)j * BMM + k), 0.f));
-        sqrtf_[(size_t)j * BMM + pr * BM + pc] = v;
+        sqrtf_[(size_t)j * BMM + k] = v;  // natural order
         acc += v;
     }
     const float tot = block_sum_fixed(acc, red);
     if (threadIdx.x == 0) part[j] = tot;
-}
-
-__global__ void permute256_kernel(int J, const float2 *src, float2 *dst, bool to_natural)
-{
-    const size_t n = (size_t)J * BMM;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t j = e / BMM;
-        const int k = (int)(e % BMM), kr = k / BM, kc = k % BM;
-        const size_t t = j * BMM + (size_t)(BR * (kr % BR) + kr / BR) * BM + (BR * (kc % BR) + kc / BR);
-        if (to_natural)
-            dst[e] = src[t];
-        else
-            dst[t] = src[e];
-    }
 }
 
 __global__ void probe_sum256_kernel(int D, const float2 *Wd, const float2 *Delta, float2 *out, float scale)
@@ -760,7 +729,7 @@ int frame_update_256(ptycho_plan_s *p, cudaStream_t s)
         P.C.frame_pitch = p->d_frame_pitch;
         P.C.slot_stride = (int32_t)p->u_len;
     }
-    return run_waves(P, p->J, WAVE_256, s);
+    return run_waves(p, P, p->J, WAVE_256, s);
 }
 
 int forward_256(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out, cudaStream_t s)
@@ -774,7 +743,7 @@ int forward_256(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2
     P.A.w = w;
     P.B.mode = B_FWD_OUT;
     P.B.out = out;
-    return run_waves(P, p->J, WAVE_256, s);
+    return run_waves(p, P, p->J, WAVE_256, s);
 }
 
 int ifft_256(const ptycho_plan_s *p, const float2 *in, float2 *out, cudaStream_t s)
@@ -786,7 +755,7 @@ int ifft_256(const ptycho_plan_s *p, const float2 *in, float2 *out, cudaStream_t
     P.B.in = in;
     P.C.out = out;
     P.C.scale = 1.f / (float)BM;
-    return run_waves(P, p->J, WAVE_256, s);
+    return run_waves(p, P, p->J, WAVE_256, s);
 }
 
 int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, float2 *h_out)
@@ -801,7 +770,7 @@ int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s,
     P.B.part = p->d_loss_part;
     P.C.out = h_out ? h_out : p->d_q;
     P.C.scale = 1.f / (float)BM;
-    return run_waves(P, p->J, WAVE_256, s);
+    return run_waves(p, P, p->J, WAVE_256, s);
 }
 
 int loss_256_sub(ptycho_plan_s *p, cudaStream_t s)
@@ -814,7 +783,7 @@ int loss_256_sub(ptycho_plan_s *p, cudaStream_t s)
     P.A.Wd = p->blind ? p->d_Wd : nullptr;
     P.B.mode = B_LOSS;
     P.B.part = p->d_loss_part;
-    return run_waves(P, p->J, WAVE_256, s);
+    return run_waves(p, P, p->J, WAVE_256, s);
 }
 
 int probe_avg_256(ptycho_plan_s *p, cudaStream_t s)
@@ -835,7 +804,7 @@ int probe_avg_256(ptycho_plan_s *p, cudaStream_t s)
     P.B.mask = p->d_mask;
     P.C.out = p->d_wnew;
     P.C.scale = invD / (float)BM;
-    return run_waves(P, 1, 1, s);
+    return run_waves(p, P, 1, 1, s);
 }
 
 int ingest_256(ptycho_plan_s *p, const float *f, float *part, cudaStream_t s)
@@ -845,12 +814,11 @@ int ingest_256(ptycho_plan_s *p, const float *f, float *part, cudaStream_t s)
     return PTYCHO_OK;
 }
 
-int permute_256(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool to_natural, cudaStream_t s)
+// m = 256 keeps Gamma in natural order: getting or setting it is a copy
+int permute_256(const ptycho_plan_s *p, const float2 *src, float2 *dst, bool, cudaStream_t s)
 {
-    const size_t n = (size_t)p->J * BMM;
-    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-    permute256_kernel<<<blocks, 256, 0, s>>>(p->J, src, dst, to_natural);
-    OD2P_CUDA(cudaGetLastError());
+    if (src != dst)
+        OD2P_CUDA(cudaMemcpyAsync(dst, src, sizeof(float2) * (size_t)p->J * BMM, cudaMemcpyDeviceToDevice, s));
     return PTYCHO_OK;
 }
 

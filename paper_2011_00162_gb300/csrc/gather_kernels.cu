@@ -1085,7 +1085,7 @@ int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s)
 
 int launch_probe_init(ptycho_plan_s *p, float2 *w0, cudaStream_t s)
 {
-    int R1 = 16, R2 = 16, row_major = 1;  // m = 256
+    int R1 = 1, R2 = 256, row_major = 1;  // m = 256: natural order (k = p)
     if (p->M != 256) {
         rank_radix(p->M, &R1, &R2);  // m <= 128: transposed position layout
         row_major = 0;

@@ -28,12 +28,16 @@ constexpr int TILE_ROWS = TILE_H * TILE_W / GATHER_THREADS;
 #endif
 constexpr int PROBE_CHUNK = OD2P_PROBE_CHUNK;
 // m = 256 frames go through their three FFT passes in waves of this many
-// frames (a 38 MB intermediate that stays in L2; 76 frames x 16 column slabs
-// fill two rounds of the column pass at four blocks per SM).
+// frames (a 10 MB intermediate per wave that stays in L2), with up to
+// WAVE_CHAINS_256 waves in flight side by side.
 #ifndef OD2P_WAVE_256
-#define OD2P_WAVE_256 76
+#define OD2P_WAVE_256 19
 #endif
 constexpr int WAVE_256 = OD2P_WAVE_256;
+#ifndef OD2P_WAVE_CHAINS_256
+#define OD2P_WAVE_CHAINS_256 4
+#endif
+constexpr int WAVE_CHAINS_256 = OD2P_WAVE_CHAINS_256;
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
@@ -190,7 +194,10 @@ struct ptycho_plan_s {
     float *d_sqrtf = nullptr;      // J*MM
     float2 *d_gamma = nullptr;     // J*MM
     float2 *d_q = nullptr;         // J*MM frame residuals / scratch
-    float2 *d_T = nullptr;         // m = 256: WAVE_256 frames of FFT intermediate
+    float2 *d_T = nullptr;         // m = 256: t_waves x WAVE_256 frames of FFT intermediate
+    int32_t t_waves = 1;           // m = 256: chains of waves in flight (WAVE_CHAINS_256 at most)
+    cudaStream_t wave_stream[od2p::WAVE_CHAINS_256] = {};  // m = 256: streams of chains 1 ..
+    cudaEvent_t wave_ev[od2p::WAVE_CHAINS_256] = {};       // [0] fork, [c] join of chain c
     // Nonblind gather slots: frame j's weighted residual at window pixel k goes to
     // d_slot[rank_j(k) * u_len + (index of that pixel in the u buffer)], where
     // rank_j(k) counts the frames of the subdomain with smaller index that cover

@@ -484,6 +484,10 @@ int ptycho_plan_destroy(ptycho_plan_t *plan)
         if (p->until[i]) cudaGraphExecDestroy(p->until[i]);
     }
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (cudaStream_t ws : p->wave_stream)
+        if (ws) cudaStreamDestroy(ws);
+    for (cudaEvent_t ev : p->wave_ev)
+        if (ev) cudaEventDestroy(ev);
     release_owned(p->owned);
     delete p;
     cudaGetLastError();
@@ -901,6 +905,16 @@ int ptycho_plan_get_launch(const ptycho_plan_t *plan, int32_t *variant, int32_t 
     if (variant) *variant = plan->k1_variant;
     if (blocks_per_sm) *blocks_per_sm = plan->k1_blocks_per_sm;
     if (max_blocks_per_sm) *max_blocks_per_sm = most;
+    return PTYCHO_OK;
+}
+
+int ptycho_plan_get_waves(const ptycho_plan_t *plan, int32_t *wave_frames, int32_t *chains, int32_t *launches)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    const bool waves = plan->M == 256 && plan->k1_variant == 0;
+    if (wave_frames) *wave_frames = waves ? WAVE_256 : 0;
+    if (chains) *chains = waves ? plan->t_waves : 1;
+    if (launches) *launches = waves ? 3 * ((plan->J + WAVE_256 - 1) / WAVE_256) : 1;
     return PTYCHO_OK;
 }
 
@@ -1484,7 +1498,17 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
         if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own, s)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own, s)))
             return bail(rc);
     }
-    if (m == 256 && (rc = dev_alloc(&p->d_T, (size_t)WAVE_256 * p->MM, own, s))) return bail(rc);
+    if (m == 256) {
+        // up to WAVE_CHAINS_256 chains of waves run side by side, one per wave
+        p->t_waves = std::max(1, std::min(WAVE_CHAINS_256, (J + WAVE_256 - 1) / WAVE_256));
+        if ((rc = dev_alloc(&p->d_T, (size_t)p->t_waves * WAVE_256 * p->MM, own, s))) return bail(rc);
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < p->t_waves && e == cudaSuccess; ++i) {
+            if (i > 0) e = cudaStreamCreateWithFlags(&p->wave_stream[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess && p->t_waves > 1) e = cudaEventCreateWithFlags(&p->wave_ev[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return bail(cuda_fail(e, "wave streams"));
+    }
     if (!p->blind) {
         // gather slots: ranks and counts on the device (one pass over the tile
         // lists), then the slot array sized by the largest count

@@ -118,8 +118,14 @@ def test_set_launch_argument_errors():
     plan256 = _plan(p256)
     od.ptycho_plan_set_launch(plan256, 0, 3)
     assert od.ptycho_plan_get_launch(plan256) == (0, 0, 1)
+    # the three passes run in waves dealt to chains (at most one chain per wave)
+    wf, ch, ln = od.ptycho_plan_get_waves(plan256)
+    n_waves = -(-plan256.n_frames // wf)
+    assert wf > 0 and 1 <= ch <= n_waves and ln == 3 * n_waves
     od.ptycho_plan_set_launch(plan256, 1, 0)
     assert od.ptycho_plan_get_launch(plan256) == (1, 0, 1)
+    assert od.ptycho_plan_get_waves(plan256) == (0, 1, 1)
+    assert od.ptycho_plan_get_waves(plan) == (0, 1, 1)
 
 
 def test_tune_plan_restores_state_and_caches(tmp_path):

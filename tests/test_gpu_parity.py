@@ -526,7 +526,7 @@ def test_dense_scan_takes_the_list_gather():
     """More than 255 frames over a pixel (m = 32, step 2: up to 256): the
     nonblind plan gathers through frame lists with the known probe; one
     iteration from a scrambled state and the exported residual still match the
-    oracle, and a batch refuses such a member."""
+    oracle, and a batch member with such a scan equals its plan alone."""
     # one subdomain: its frames are all frames (coverage is counted per subdomain)
     p = synth.Problem("dense", 80, 32, 2, 0, 1, 1, 0, 1e5, 1, eta=0.3, r=0.2, seed=4)
     offs, u_true, w, f = make_case(p)
@@ -544,8 +544,17 @@ def test_dense_scan_takes_the_list_gather():
     q = host(od.od2p_get_state(plan, od.STATE_Q)).reshape(-1, p.m, p.m)
     for j in np.random.default_rng(2).choice(len(offs), 10, replace=False):
         assert rel_l2(q[j], np.conj(w) * oracle.fft2(z[j] - gam[j], True)) < ONE_ITER_TOL
-    with pytest.raises(od.PtychoError):
-        od.ptycho_batch_plan([geom_of(p, offs)], [f32(f)])
+    # a batch takes such a member: one iteration from the same start equals the plan alone
+    batch = od.ptycho_batch_plan([geom_of(p, offs)], [f32(f)])
+    alone = od.ptycho_plan(geom_of(p, offs), f32(f))
+    for pl in (batch.members[0], alone):
+        od.od2p_init(pl, c64(w))
+    batch.iterate(1)
+    od.od2p_iterate(alone, 1)
+    for k in (od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA):
+        assert torch.equal(od.od2p_get_state(batch.members[0], k), od.od2p_get_state(alone, k)), k
+    batch.close()
+    alone.close()
 
 
 def test_blind_checkpoint_resume_bitwise():

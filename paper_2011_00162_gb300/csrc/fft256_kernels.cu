@@ -32,6 +32,7 @@ constexpr int SLAB = 16;   // rows (A, C) or columns (B) per block
 constexpr int NTB = 256;   // threads per block
 constexpr int PX = BR * (BR + 1);  // pitch of a row in a row slab: 16 groups of 17
 constexpr int PB = SLAB + 1;
+static_assert(NTB * 128 == SLAB * BM * (int)sizeof(float2), "pass C: one 128-byte L2 line of its slab per thread");
 
 enum ModeB : int { B_PROX = 0, B_FWD_OUT = 1, B_LOSS = 2, B_MASK = 3, B_IFFT_IN = 4 };
 
@@ -250,6 +251,11 @@ __global__ void __launch_bounds__(NTB) rows_inv256_kernel(PassC a, const float2 
         for (int t = 0; t < BR; ++t) rp[t] = x[t];
     }
     __syncthreads();  // (and the twiddles)
+    {   // the block has read its slab of T, which nothing reads again: drop its 256
+        // L2 lines without writing them back (saves the DRAM write of dead data)
+        const float2 *line = a.T + ((size_t)f * BM + rb * SLAB) * BM + (size_t)threadIdx.x * (128 / sizeof(float2));
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(line) : "memory");
+    }
     {   // inverse row stage 1 -> spatial columns n1 + 16 n2
         const float2 *rp = buf + r * PX + lo;
 #pragma unroll

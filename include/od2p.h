@@ -493,11 +493,13 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c
                     int32_t recompute, ptycho_stream_t stream);
 
 /*
- * Batches of independent reconstructions (nonblind or blind, probe sides up to
- * 128, mixed image, probe, scan and subdomain sizes).  One ADMM iteration of all
- * members is one frame-update launch per distinct probe side -- a persistent
- * kernel over the (member, frame group) work items; the launches of different
- * probe sides run as parallel branches of the graph -- and one subdomain-update
+ * Batches of independent reconstructions (nonblind or blind, any supported
+ * probe side, mixed image, probe, scan and subdomain sizes).  One ADMM
+ * iteration of all members is one frame-update launch per distinct probe side
+ * up to 128 -- a persistent kernel over the (member, frame group) work items --
+ * and, for m = 256 members, each member's own wave passes in turn (a 256 x 256
+ * frame already spans 16 blocks); the frame updates of different probe sides
+ * run as parallel branches of the graph -- and one subdomain-update
  * launch over the tiles of all members (two: slot gathers and, for blind
  * members and members with more than 255 frames over a pixel, frame-list
  * gathers), with each blind member's probe update in between, replayed from a
@@ -512,8 +514,8 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u_dev, const ptycho_c
  *   destroy them, and do not iterate a member on its own between batch
  *   iterations -- the call returns PTYCHO_ERR_STATE).
  * ptycho_batch_iterate: n_iter iterations of every member; od2p_init must
- *   have been called on each.  Errors: INVALID_ARG, UNSUPPORTED (m = 256),
- *   STATE, OOM, CUDA.
+ *   have been called on each.  Errors: INVALID_ARG, UNSUPPORTED, STATE, OOM,
+ *   CUDA.
  */
 typedef struct ptycho_batch_s ptycho_batch_t;
 int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const float *const *f_devs, int32_t n,

@@ -1025,6 +1025,7 @@ struct ptycho_batch_s {
     struct Cls {  // the member plans of one probe side m
         int m = 0, grid = 0;
         bool f4 = false;                 // m = 64: the 16 x 4 split, one frame per item
+        std::vector<ptycho_plan_s *> waves;  // m = 256: members whose own wave passes run in turn
         int n_items[2] = {0, 0};         // (plan, frame group) items per launch shape
         od2p::FrameArgs *tab = nullptr;
         int2 *items[2] = {nullptr, nullptr};
@@ -1069,8 +1070,6 @@ int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const 
     if (!out) return fail(PTYCHO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!geoms || !f_devs || n < 1) return fail(PTYCHO_ERR_INVALID_ARG, "need n >= 1 geometries and intensity stacks");
-    for (int i = 0; i < n; ++i)
-        if (geoms[i].m > 128) return fail(PTYCHO_ERR_UNSUPPORTED, "batches hold probe sides up to 128");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     auto *b = new (std::nothrow) ptycho_batch_s();
     if (!b) return fail(PTYCHO_ERR_OOM, "host allocation failed");
@@ -1097,6 +1096,14 @@ int ptycho_batch_plan(ptycho_batch_t **out, const ptycho_geometry *geoms, const 
             if (int rc = set_fft_kind(p, 2, s)) return bail(rc);
     for (auto *p : b->plans) p->batch_member = true;
     for (int m : ms) {
+        if (m == 256) {  // a 256 x 256 frame spans 16 blocks: each member runs its own waves
+            ptycho_batch_s::Cls c;
+            c.m = m;
+            for (auto *p : b->plans)
+                if (p->M == m) c.waves.push_back(p);
+            b->cls.push_back(c);
+            continue;
+        }
         std::vector<FrameArgs> tab;
         std::vector<int2> items[2];
         const bool f4 = m == 64;
@@ -1185,10 +1192,12 @@ int ptycho_batch_set_launch(ptycho_batch_t *b, int32_t variant, int32_t blocks_p
     for (const auto &c : b->cls) {
         int grid = 0;
         // the m = 64 class's 16 x 4 kernel keeps every block that fits (the
-        // shape and cap are those of the two-stage kernels of the other classes)
-        if (int rc = c.f4 ? f4_grid(2, c.n_items[0], &grid, 0)
-                          : frame_update_grid(c.m, variant, c.n_items[variant], blocks_per_sm, &grid, nullptr))
-            return rc;
+        // shape and cap are those of the two-stage kernels of the other classes);
+        // m = 256 members take the variant through their own plans below
+        if (c.m != 256)
+            if (int rc = c.f4 ? f4_grid(2, c.n_items[0], &grid, 0)
+                              : frame_update_grid(c.m, variant, c.n_items[variant], blocks_per_sm, &grid, nullptr))
+                return rc;
         grids.push_back(grid);
     }
     // members iterate alone in the same shape, so their RF partials keep one layout
@@ -1222,6 +1231,11 @@ static int batch_enqueue(ptycho_batch_s *b, int parity, cudaStream_t s)
     for (int k = 0; k < nc; ++k) {
         const auto &c = b->cls[k];
         cudaStream_t sk = k == 0 ? s : b->side[k - 1];
+        if (c.m == 256) {  // each member's waves (forking onto its own wave streams and joining back)
+            for (auto *p : c.waves)
+                if (int rc = launch_frame_update(p, sk)) return rc;
+            continue;
+        }
         if (int rc = c.f4 ? launch_frame_update_f4_table(c.tab, c.items[0], c.n_items[0], c.grid, parity, sk)
                           : launch_frame_update_table(c.m, b->variant, c.tab, c.items[b->variant],
                                                       c.n_items[b->variant], c.grid, parity, sk))

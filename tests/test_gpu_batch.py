@@ -150,3 +150,50 @@ def test_batch_with_mixed_radix_probe_sides_bitwise():
     for k, ko in ((od.STATE_U, oracle.U), (od.STATE_GAMMA, oracle.GAMMA), (od.STATE_LAMBDA, oracle.LAMBDA)):
         assert rel_l2(od.od2p_get_state(batch.members[2], k).cpu().numpy(), ref.get(ko)) < 1e-5
     batch.close()
+
+
+def test_batch_with_m256_members_bitwise():
+    """m = 256 members (blind and nonblind, several waves each) beside m = 32 and
+    m = 64 members: each member equals itself iterated alone in the same launch
+    variant, for the three wave passes and for the cluster launch; one m = 256
+    member against the oracle."""
+    specs = [(256, 512, 64, True, 2, 41), (32, 128, 8, False, 2, 42), (256, 448, 48, False, 2, 43),
+             (64, 256, 16, True, 2, 44)]
+    probs, cases, geoms, w0s = [], [], [], []
+    for m, n, step, blind, grid, seed in specs:
+        p = synth.Problem(f"b{m}", n, m, step, 1, grid, grid, 8, 1e4, 1, eta=2.0, r=0.5, blind=blind,
+                          mu=1.0 if blind else 0.0, gamma=0.1 if blind else 0.0, seed=seed)
+        c = make_case(p, noise_seed=seed)
+        probs.append(p)
+        cases.append(c)
+        geoms.append(od.Geometry(p.n, p.n, p.m, c[0], p.sub_rows, p.sub_cols, p.overlap_px, 0.5, 2.0, 0.5,
+                                 mu=p.mu, gamma=p.gamma, blind=blind))
+        w0s.append(synth.gaussian_probe(m) if blind else np.asarray(c[2], np.complex64))
+    fs = [torch.from_numpy(np.asarray(c[3], np.float32)).to(DEV) for c in cases]
+    for variant in (0, 1):
+        batch = od.ptycho_batch_plan(geoms, fs)
+        od.ptycho_batch_set_launch(batch, variant, 0)
+        for mb, w0 in zip(batch.members, w0s):
+            od.od2p_init(mb, torch.from_numpy(w0).to(DEV))
+        assert od.ptycho_plan_get_waves(batch.members[0])[1] >= 1
+        batch.iterate(2)
+        for i, g in enumerate(geoms):
+            alone = od.ptycho_plan(g, fs[i])
+            od.ptycho_plan_set_launch(alone, variant, 0)
+            od.od2p_init(alone, torch.from_numpy(w0s[i]).to(DEV))
+            if g.m == 64:  # the batch runs m = 64 members on the 16 x 4 split
+                od.ptycho_plan_set_fft(alone, 2)
+            od.od2p_iterate(alone, 2)
+            sel = [od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA] + (
+                [od.STATE_WD, od.STATE_DELTA, od.STATE_W] if g.blind else [])
+            for k in sel:
+                assert torch.equal(od.od2p_get_state(batch.members[i], k), od.od2p_get_state(alone, k)), (variant, i, k)
+            alone.close()
+        if variant == 0:  # the blind m = 256 member against the FP64 oracle (two iterations)
+            p, (offs, u_true, w, f) = probs[0], cases[0]
+            ref = oracle.ADMM(f, w0s[0], offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, 0.5, 2.0, 0.5,
+                              blind=True, mu=p.mu, gamma=p.gamma)
+            ref.iterate(2)
+            for k, ko in ((od.STATE_U, oracle.U), (od.STATE_WD, oracle.WD), (od.STATE_W, oracle.W)):
+                assert rel_l2(od.od2p_get_state(batch.members[0], k).cpu().numpy(), ref.get(ko)) < 1e-5, k
+        batch.close()

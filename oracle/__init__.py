@@ -75,6 +75,10 @@ def _load():
             "orc_snr": (f64, [i64, P, P]),
             "orc_geometry": (i32, [i32, i32, i32, i32, P, i32, i32, i32, P, P]),
             "orc_pairs": (i32, [i32, P, i32, P, P]),
+            "orc_geometry_ext": (i32, [i32, i32, i32, i32, P, i32, i32, i32, i32, P, P, P]),
+            "orc_pairs_ext": (i32, [i32, P, i32, i32, i32, i32, P, P, P]),
+            "orc_admm_new_ext": (P, [i32, i32, i32, i32, P, i32, i32, i32, i32, P, P, P, f64, f64, f64,
+                                     i32, f64, f64, P]),
             "orc_admm_new": (P, [i32, i32, i32, i32, P, i32, i32, i32, P, P, P, f64, f64, f64,
                                  i32, f64, f64, P]),
             "orc_admm_free": (None, [P]),
@@ -197,27 +201,34 @@ def snr(ur, ug) -> float:
     return float(_load().orc_snr(ur.size, _p(ur), _p(ug)))
 
 
-def geometry(H: int, W: int, m: int, offs, sub_rows: int, sub_cols: int, overlap_px: int):
-    """(frame_sub[J], rect[D,4]) of the overlapping decomposition."""
+def geometry(H: int, W: int, m: int, offs, sub_rows: int, sub_cols: int, overlap_px: int,
+             periodic: bool = False, placed: bool = False):
+    """(frame_sub[J], rect[D,4]) of the overlapping decomposition; with
+    placed=True also the frames' offsets in extended coordinates (J, 2)."""
     offs = _c(offs, np.int32).reshape(-1, 2)
     J = offs.shape[0]
     fs = np.empty(max(J, 1), np.int32)
     rect = np.empty((sub_rows * sub_cols, 4), np.int32)
-    D = _load().orc_geometry(H, W, m, J, _p(offs), sub_rows, sub_cols, overlap_px, _p(fs), _p(rect))
+    ro = np.empty((max(J, 1), 2), np.int32)
+    D = _load().orc_geometry_ext(H, W, m, J, _p(offs), sub_rows, sub_cols, overlap_px, int(bool(periodic)),
+                                 _p(fs), _p(rect), _p(ro))
     if D < 0:
         raise ValueError(f"invalid geometry (code {D})")
-    return fs[:J], rect
+    return (fs[:J], rect, ro[:J]) if placed else (fs[:J], rect)
 
 
-def pairs(rect):
-    """Ordered intersecting pairs (d, e) and their intersection rectangles."""
+def pairs(rect, H: int = 0, W: int = 0, periodic: bool = False, shifts: bool = False):
+    """Ordered intersecting pairs (d, e) and their intersection rectangles (in
+    d's coordinates); with shifts=True also each pair's shift s (periods)."""
     rect = _c(rect, np.int32).reshape(-1, 4)
     lib = _load()
-    n = lib.orc_pairs(rect.shape[0], _p(rect), 0, None, None)
+    per = int(bool(periodic))
+    n = lib.orc_pairs_ext(rect.shape[0], _p(rect), H, W, per, 0, None, None, None)
     pr = np.empty((max(n, 1), 2), np.int32)
+    sh = np.empty((max(n, 1), 2), np.int32)
     prc = np.empty((max(n, 1), 4), np.int32)
-    lib.orc_pairs(rect.shape[0], _p(rect), n, _p(pr), _p(prc))
-    return pr[:n], prc[:n]
+    lib.orc_pairs_ext(rect.shape[0], _p(rect), H, W, per, n, _p(pr), _p(sh), _p(prc))
+    return (pr[:n], sh[:n], prc[:n]) if shifts else (pr[:n], prc[:n])
 
 
 def operator_norms(w, offs, H: int, W: int, sub_rows: int, sub_cols: int, overlap_px: int):
@@ -244,7 +255,7 @@ class ADMM:
 
     def __init__(self, f, w0, offs, H: int, W: int, sub_rows: int, sub_cols: int,
                  overlap_px: int, eps: float, eta: float, r: float, u0=None, blind: bool = False,
-                 mu: float = 0.0, gamma: float = 0.0, mask=None):
+                 mu: float = 0.0, gamma: float = 0.0, mask=None, periodic: bool = False):
         self._lib = _load()
         f = _c(f, np.float64)
         w0 = _c(w0, np.complex128)
@@ -254,9 +265,9 @@ class ADMM:
         self.m = w0.shape[0]
         self.J = offs.shape[0]
         self.H, self.W = H, W
-        self._h = self._lib.orc_admm_new(H, W, self.m, self.J, _p(offs), sub_rows, sub_cols,
-                                         overlap_px, _p(f), _p(w0), _p(u0c), eps, eta, r,
-                                         int(blind), mu, gamma, _p(maskc))
+        self._h = self._lib.orc_admm_new_ext(H, W, self.m, self.J, _p(offs), sub_rows, sub_cols,
+                                             overlap_px, int(bool(periodic)), _p(f), _p(w0), _p(u0c), eps, eta,
+                                             r, int(blind), mu, gamma, _p(maskc))
         if not self._h:
             raise ValueError("invalid ADMM geometry")
         self.D = self._lib.orc_admm_num_sub(self._h)

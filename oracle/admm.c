@@ -26,6 +26,14 @@
  *  - RF (section 4) is accumulated from the frames A_d u_d^n (blind:
  *    F(W_d^n o S_j u_d^n)) formed in Step 1, i.e. it is the RF of the iterate
  *    entering the iteration.  RE = max_d ||u_d^{n+1} - u_d^n|| / ||u_d^{n+1}||.
+ *  - Periodic boundaries (the torus reading in geometry.c): windows are read
+ *    at the frames' placed offsets in extended coordinates; pair k = (d, e, s)
+ *    couples pixel (R, C) of u_d with pixel (R - s_r H, C - s_c W) of u_e, and
+ *    Lambda_{e,d} is read at that pixel of the reverse pair (e, d, -s); v uses
+ *    the operand order of the pair listed first (d < e, or d = e with the
+ *    positive shift).  Step 0 reads u0 modulo the image; the merge averages
+ *    every copy of an image pixel.  Without periodic boundaries every shift is
+ *    0 and these are the steps above, operation for operation.
  *  - Subdomain ownership (section 3.1: the subdomains are independent but for
  *    the overlap terms): with an ownership mask set, an iteration updates only
  *    the owned subdomains -- their frames, u_d, Lambda_{d,e}, and (blind) W_d
@@ -42,9 +50,10 @@
 #include <string.h>
 
 struct orc_admm {
-    int H, W, m, mm, J, D, P, blind;
-    int32_t *offs, *frame_sub, *rect, *pair, *pair_rect;
-    int *pair_of;          /* D*D: index of ordered pair (d, e) or -1 */
+    int H, W, m, mm, J, D, P, blind, periodic;
+    int32_t *offs, *frame_sub, *rect, *pair, *pair_shift, *pair_rect;
+    int *rev, *first;      /* P: index of the reverse pair (e, d, -s); 1 for the pair listed first */
+    int *pd_begin;         /* D + 1: pairs of subdomain d are [pd_begin[d], pd_begin[d + 1]) */
     double eps, eta, r, mu, gamma;
     double *f, *mask;      /* J*mm, mm */
     ocplx *w, *Wd, *Delta; /* mm, D*mm, D*mm */
@@ -54,6 +63,7 @@ struct orc_admm {
     double rf, re;
 };
 
+static inline int wrapi(int x, int n) { int r = x % n; return r < 0 ? r + n : r; }
 static inline int rh(const int32_t *rc) { return rc[2] - rc[0]; }
 static inline int rw(const int32_t *rc) { return rc[3] - rc[1]; }
 
@@ -64,29 +74,44 @@ static inline int64_t rect_idx(const int32_t *rc, int R, int C)
     return (int64_t)(R - rc[0]) * rw(rc) + (C - rc[1]);
 }
 
-orc_admm *orc_admm_new(int H, int W, int m, int J, const int32_t *offs, int sub_rows,
-                       int sub_cols, int overlap_px, const double *f, const ocplx *w0,
-                       const ocplx *u0, double eps, double eta, double r, int blind,
-                       double mu, double gamma, const double *mask)
+orc_admm *orc_admm_new_ext(int H, int W, int m, int J, const int32_t *offs, int sub_rows,
+                           int sub_cols, int overlap_px, int periodic, const double *f, const ocplx *w0,
+                           const ocplx *u0, double eps, double eta, double r, int blind,
+                           double mu, double gamma, const double *mask)
 {
     orc_admm *s = (orc_admm *)calloc(1, sizeof(orc_admm));
-    s->H = H; s->W = W; s->m = m; s->mm = m * m; s->J = J; s->blind = blind;
+    s->H = H; s->W = W; s->m = m; s->mm = m * m; s->J = J; s->blind = blind; s->periodic = periodic != 0;
     s->eps = eps; s->eta = eta; s->r = r; s->mu = mu; s->gamma = gamma;
     const int mm = s->mm, D0 = sub_rows * sub_cols;
+    /* offs holds each frame's placed offset (extended coordinates; the given offset when not periodic) */
     s->offs = (int32_t *)malloc(sizeof(int32_t) * 2 * (J > 0 ? J : 1));
-    memcpy(s->offs, offs, sizeof(int32_t) * 2 * J);
     s->frame_sub = (int32_t *)malloc(sizeof(int32_t) * (J > 0 ? J : 1));
     s->rect = (int32_t *)malloc(sizeof(int32_t) * 4 * D0);
-    s->D = orc_geometry(H, W, m, J, offs, sub_rows, sub_cols, overlap_px, s->frame_sub, s->rect);
+    s->D = orc_geometry_ext(H, W, m, J, offs, sub_rows, sub_cols, overlap_px, s->periodic, s->frame_sub, s->rect,
+                            s->offs);
     if (s->D <= 0) { free(s->offs); free(s->frame_sub); free(s->rect); free(s); return NULL; }
     const int D = s->D;
-    s->P = orc_pairs(D, s->rect, 0, NULL, NULL);
+    s->P = orc_pairs_ext(D, s->rect, H, W, s->periodic, 0, NULL, NULL, NULL);
     s->pair = (int32_t *)malloc(sizeof(int32_t) * 2 * (s->P + 1));
+    s->pair_shift = (int32_t *)malloc(sizeof(int32_t) * 2 * (s->P + 1));
     s->pair_rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (s->P + 1));
-    orc_pairs(D, s->rect, s->P, s->pair, s->pair_rect);
-    s->pair_of = (int *)malloc(sizeof(int) * D * D);
-    for (int i = 0; i < D * D; ++i) s->pair_of[i] = -1;
-    for (int k = 0; k < s->P; ++k) s->pair_of[s->pair[2 * k] * D + s->pair[2 * k + 1]] = k;
+    orc_pairs_ext(D, s->rect, H, W, s->periodic, s->P, s->pair, s->pair_shift, s->pair_rect);
+    s->rev = (int *)malloc(sizeof(int) * (s->P + 1));
+    s->first = (int *)malloc(sizeof(int) * (s->P + 1));
+    for (int k = 0; k < s->P; ++k) {
+        const int d = s->pair[2 * k], e = s->pair[2 * k + 1], sr = s->pair_shift[2 * k], sc = s->pair_shift[2 * k + 1];
+        s->rev[k] = -1;
+        for (int q = 0; q < s->P; ++q)
+            if (s->pair[2 * q] == e && s->pair[2 * q + 1] == d && s->pair_shift[2 * q] == -sr &&
+                s->pair_shift[2 * q + 1] == -sc)
+                s->rev[k] = q;
+        s->first[k] = d < e || (d == e && (sr > 0 || (sr == 0 && sc > 0)));
+    }
+    s->pd_begin = (int *)malloc(sizeof(int) * (D + 1));
+    for (int d = 0, k = 0; d <= D; ++d) {
+        while (k < s->P && s->pair[2 * k] < d) ++k;
+        s->pd_begin[d] = k;
+    }
 
     s->u_off = (int64_t *)malloc(sizeof(int64_t) * (D + 1));
     s->u_off[0] = 0;
@@ -112,7 +137,7 @@ orc_admm *orc_admm_new(int H, int W, int m, int J, const int32_t *offs, int sub_
         const int32_t *rc = s->rect + 4 * d;
         for (int R = rc[0]; R < rc[2]; ++R)
             for (int C = rc[1]; C < rc[3]; ++C)
-                s->u[s->u_off[d] + rect_idx(rc, R, C)] = u0 ? u0[(size_t)R * W + C] : 1.0;
+                s->u[s->u_off[d] + rect_idx(rc, R, C)] = u0 ? u0[(size_t)wrapi(R, H) * W + wrapi(C, W)] : 1.0;
     }
     s->Gamma = (ocplx *)calloc((size_t)J * mm + 1, sizeof(ocplx));
     s->z = (ocplx *)calloc((size_t)J * mm + 1, sizeof(ocplx));
@@ -131,8 +156,8 @@ void orc_admm_set_owned(orc_admm *s, const int32_t *owned)
 void orc_admm_free(orc_admm *s)
 {
     if (!s) return;
-    free(s->offs); free(s->frame_sub); free(s->rect); free(s->pair); free(s->pair_rect);
-    free(s->pair_of); free(s->f); free(s->mask); free(s->w); free(s->Wd); free(s->Delta);
+    free(s->offs); free(s->frame_sub); free(s->rect); free(s->pair); free(s->pair_shift); free(s->pair_rect);
+    free(s->rev); free(s->first); free(s->pd_begin); free(s->f); free(s->mask); free(s->w); free(s->Wd); free(s->Delta);
     free(s->u); free(s->Gamma); free(s->Lam); free(s->v); free(s->z); free(s->u_off);
     free(s->lam_off); free(s->owned); free(s);
 }
@@ -207,16 +232,16 @@ void orc_admm_iterate(orc_admm *s, int n_iter)
         }
         /* v_{i1,i2}^{n+1} = 1/2 (pi u_i1^n + pi u_i2^n + Lambda_{i1,i2}^n + Lambda_{i2,i1}^n) (eq. updateV-multi) */
         for (int k = 0; k < s->P; ++k) {
-            const int d = s->pair[2 * k], e = s->pair[2 * k + 1];
+            const int d = s->pair[2 * k], e = s->pair[2 * k + 1], kr = s->rev[k];
             if (!s->owned[d]) continue;
-            const int i1 = d < e ? d : e, i2 = d < e ? e : d;
-            const int k12 = s->pair_of[i1 * D + i2], k21 = s->pair_of[i2 * D + i1];
+            const int sR = s->pair_shift[2 * k] * s->H, sC = s->pair_shift[2 * k + 1] * s->W;
             const int32_t *prc = s->pair_rect + 4 * k;
             for (int R = prc[0]; R < prc[2]; ++R)
-                for (int C = prc[1]; C < prc[3]; ++C)
-                    *lam_at(s->v, s, k, R, C) =
-                        0.5 * (*u_at(s, i1, R, C) + *u_at(s, i2, R, C) + *lam_at(s->Lam, s, k12, R, C) +
-                               *lam_at(s->Lam, s, k21, R, C));
+                for (int C = prc[1]; C < prc[3]; ++C) {
+                    const ocplx ud = *u_at(s, d, R, C), ue = *u_at(s, e, R - sR, C - sC);
+                    const ocplx ld = *lam_at(s->Lam, s, k, R, C), le = *lam_at(s->Lam, s, kr, R - sR, C - sC);
+                    *lam_at(s->v, s, k, R, C) = s->first[k] ? 0.5 * (ud + ue + ld + le) : 0.5 * (ue + ud + le + ld);
+                }
         }
         /* ---------------- Step 2: Gamma^{n+1} = Gamma^n + A_d u_d^n - z^{n+1}  (eq. updateM-1-multi) */
         for (int j = 0; j < J; ++j)
@@ -289,9 +314,8 @@ void orc_admm_iterate(orc_admm *s, int n_iter)
                     int64_t i = s->u_off[d] + rect_idx(rc, R, C);
                     ocplx num = s->eta * acc[i];
                     double den = s->eta * nrm[i];
-                    for (int e = 0; e < D; ++e) {
-                        int k = s->pair_of[d * D + e];
-                        if (k < 0 || rect_idx(s->pair_rect + 4 * k, R, C) < 0) continue;
+                    for (int k = s->pd_begin[d]; k < s->pd_begin[d + 1]; ++k) {
+                        if (rect_idx(s->pair_rect + 4 * k, R, C) < 0) continue;
                         num += s->r * (*lam_at(s->v, s, k, R, C) - *lam_at(s->Lam, s, k, R, C));
                         den += s->r;
                     }
@@ -380,16 +404,19 @@ void orc_admm_metrics(const orc_admm *s, double *rf, double *re)
 /* Section 4 set-up: non-overlapping pixels keep their value, overlaps are averaged. */
 void orc_admm_merge(const orc_admm *s, ocplx *u_out)
 {
+    const int smax = s->periodic ? 2 : 0;
     for (int R = 0; R < s->H; ++R)
         for (int C = 0; C < s->W; ++C) {
             ocplx t = 0.0;
             int n = 0;
-            for (int d = 0; d < s->D; ++d) {
-                int64_t i = rect_idx(s->rect + 4 * d, R, C);
-                if (i < 0) continue;
-                t += s->u[s->u_off[d] + i];
-                ++n;
-            }
+            for (int d = 0; d < s->D; ++d)
+                for (int sr = -smax; sr <= smax; ++sr)
+                    for (int sc = -smax; sc <= smax; ++sc) {
+                        int64_t i = rect_idx(s->rect + 4 * d, R + sr * s->H, C + sc * s->W);
+                        if (i < 0) continue;
+                        t += s->u[s->u_off[d] + i];
+                        ++n;
+                    }
             u_out[(size_t)R * s->W + C] = n ? t / (double)n : 1.0;
         }
 }
@@ -418,15 +445,25 @@ double orc_admm_consensus(const orc_admm *s)
     double num = 0.0, den = 0.0;
     for (int k = 0; k < s->P; ++k) {
         const int d = s->pair[2 * k], e = s->pair[2 * k + 1];
+        const int sR = s->pair_shift[2 * k] * s->H, sC = s->pair_shift[2 * k + 1] * s->W;
         const int32_t *pr = s->pair_rect + 4 * k;
         for (int R = pr[0]; R < pr[2]; ++R)
             for (int C = pr[1]; C < pr[3]; ++C) {
                 const ocplx a = s->u[s->u_off[d] + rect_idx(s->rect + 4 * d, R, C)];
-                const ocplx b = s->u[s->u_off[e] + rect_idx(s->rect + 4 * e, R, C)];
+                const ocplx b = s->u[s->u_off[e] + rect_idx(s->rect + 4 * e, R - sR, C - sC)];
                 const ocplx t = a - b;
                 num += creal(t) * creal(t) + cimag(t) * cimag(t);
             }
     }
     for (int64_t k = 0; k < s->u_off[s->D]; ++k) den += creal(s->u[k]) * creal(s->u[k]) + cimag(s->u[k]) * cimag(s->u[k]);
     return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+orc_admm *orc_admm_new(int H, int W, int m, int J, const int32_t *offs, int sub_rows,
+                       int sub_cols, int overlap_px, const double *f, const ocplx *w0,
+                       const ocplx *u0, double eps, double eta, double r, int blind,
+                       double mu, double gamma, const double *mask)
+{
+    return orc_admm_new_ext(H, W, m, J, offs, sub_rows, sub_cols, overlap_px, 0, f, w0, u0, eps, eta, r, blind, mu,
+                            gamma, mask);
 }

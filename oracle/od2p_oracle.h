@@ -64,6 +64,15 @@ int orc_geometry(int H, int W, int m, int J, const int32_t *offs, int sub_rows,
 /* Ordered pairs (d, e), d != e, whose rectangles intersect, sorted by (d, e).
  * pair[k*2..], pair_rect[k*4..]; returns the number of pairs (<= max_pairs).   */
 int orc_pairs(int D, const int32_t *rect, int max_pairs, int32_t *pair, int32_t *pair_rect);
+/* Either variant (periodic != 0: the torus reading in geometry.c).  roffs[J*2]
+ * (may be NULL): each frame's offset in extended coordinates.  Pairs (d, e, s)
+ * sorted by (d, e, s_r, s_c), s in {-2, ..., 2}^2 (only 0 when not periodic);
+ * pair_shift[k*2..] = s (may be NULL); pair_rect in d's coordinates.  -3: a
+ * rectangle reaching outside (-H, 2H) x (-W, 2W).                              */
+int orc_geometry_ext(int H, int W, int m, int J, const int32_t *offs, int sub_rows, int sub_cols,
+                     int overlap_px, int periodic, int32_t *frame_sub, int32_t *rect, int32_t *roffs);
+int orc_pairs_ext(int D, const int32_t *rect, int H, int W, int periodic, int max_pairs, int32_t *pair,
+                  int32_t *pair_shift, int32_t *pair_rect);
 
 /* ---- ADMM state: Algorithm 2 (OD2P_m, nonblind) and Algorithm 3 (OD2BP) ---- */
 typedef struct orc_admm orc_admm;
@@ -75,6 +84,11 @@ orc_admm *orc_admm_new(int H, int W, int m, int J, const int32_t *offs, int sub_
                        int sub_cols, int overlap_px, const double *f, const ocplx *w0,
                        const ocplx *u0, double eps, double eta, double r, int blind,
                        double mu, double gamma, const double *mask);
+/* Either boundary variant (periodic != 0: the torus reading in geometry.c). */
+orc_admm *orc_admm_new_ext(int H, int W, int m, int J, const int32_t *offs, int sub_rows,
+                           int sub_cols, int overlap_px, int periodic, const double *f, const ocplx *w0,
+                           const ocplx *u0, double eps, double eta, double r, int blind,
+                           double mu, double gamma, const double *mask);
 void orc_admm_free(orc_admm *s);
 void orc_admm_iterate(orc_admm *s, int n_iter);
 int  orc_admm_num_sub(const orc_admm *s);

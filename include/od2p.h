@@ -86,12 +86,31 @@ enum {
  * box of its core tile grown by ceil(overlap_px/2) on interior sides (clipped)
  * and of its frames' windows.  Ordered pairs (d, e) with intersecting Omega
  * carry Lambda_{d,e}; sorted by (d, e).
+ *
+ * Periodic boundaries (periodic = 1; section 4 names them as the usual
+ * alternative to its vacuum boundary of ones, and does not decompose a
+ * periodic image -- this is a reading): the image is a torus and window j
+ * covers pixels ((offs[j] + a) mod img_h, (offs[j] + b) mod img_w), offsets
+ * anywhere in [0, img_h) x [0, img_w).  Rectangles then live in extended
+ * coordinates (pixel (R, C) is image pixel (R mod img_h, C mod img_w)): every
+ * core tile grows on all sides and is not clipped, frame j is placed at the
+ * copy of its offset whose doubled centre 2 o + m - 1 lies in [0, 2 img_h) x
+ * [0, 2 img_w) (offs - img_h where it would not) and joins that centre's tile,
+ * and the pairs are (d, e, s) for shifts s in {-2, ..., 2}^2 periods such that
+ * Omega_d meets Omega_e moved by s (d = e included, s != 0), sorted by
+ * (d, e, s_r, s_c), each kept in d's coordinates -- (e, d, -s) is the same
+ * region seen from e.  A rectangle must stay within (-img_h, 2 img_h) x
+ * (-img_w, 2 img_w) (INVALID_ARG otherwise).  Step 0 reads u0 modulo the
+ * image and od2p_merge / od2p_snr average every copy of a pixel.  Not built
+ * for periodic plans (UNSUPPORTED): shards, and the image-space operators
+ * ptycho_forward, overlap_add and stagm_loss_grad.
  */
 typedef struct {
     int32_t img_h, img_w;           /* image size in pixels                                 */
     int32_t m;                      /* probe side: 16, 32, 48, 64, 80, 96, 128 or 256      */
     int32_t n_frames;               /* J >= 1                                              */
-    const int32_t *offsets_host;    /* J x 2 (row, col), 0 <= row <= img_h-m, col likewise  */
+    const int32_t *offsets_host;    /* J x 2 (row, col), 0 <= row <= img_h-m, col likewise
+                                       (periodic: 0 <= row < img_h, col likewise)          */
     int32_t sub_rows, sub_cols;     /* subdomain grid, >= 1                                */
     int32_t overlap_px;             /* requested minimum overlap width, >= 0               */
     float eps;                      /* ST-AGM truncation, 0 < eps < 1 (paper: 0.5)         */
@@ -101,6 +120,7 @@ typedef struct {
     float gamma;                    /* blind: proximal weight of the U-update, >= 0        */
     int32_t blind;                  /* 0: Algorithm 2 (known probe); 1: Algorithm 3        */
     const uint8_t *fourier_support_host; /* blind: m x m, 1 on the support of F w; NULL = all */
+    int32_t periodic;               /* 0: vacuum boundary (section 4); 1: periodic (above) */
 } ptycho_geometry;
 
 typedef struct ptycho_plan_s ptycho_plan_t;
@@ -204,6 +224,11 @@ int ptycho_plan_dims(const ptycho_plan_t *plan, int32_t *n_sub, int32_t *n_pairs
  * half-open, pair[P*2] = (d, e), pair_rect[P*4].  Any output may be NULL.     */
 int ptycho_plan_layout(const ptycho_plan_t *plan, int32_t *frame_sub_host, int32_t *rect_host,
                        int32_t *pair_host, int32_t *pair_rect_host);
+/* Each pair's shift pair_shift[P*2] = (s_r, s_c) in periods (all 0 without
+ * periodic boundaries) and each frame's placed offset placed[J*2] in extended
+ * coordinates (the given offset without periodic boundaries).  Any output may
+ * be NULL.  Errors: INVALID_ARG (plan NULL).                                  */
+int ptycho_plan_periodic_layout(const ptycho_plan_t *plan, int32_t *pair_shift_host, int32_t *placed_host);
 
 /*
  * Forward operator (section 2, operator A): frames_out[j] = F(w o S_j u) for

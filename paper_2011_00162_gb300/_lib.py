@@ -33,7 +33,7 @@ class Geometry(ctypes.Structure):
         ("img_h", _I32), ("img_w", _I32), ("m", _I32), ("n_frames", _I32),
         ("offsets_host", _P), ("sub_rows", _I32), ("sub_cols", _I32), ("overlap_px", _I32),
         ("eps", _F), ("eta", _F), ("r", _F), ("mu", _F), ("gamma", _F), ("blind", _I32),
-        ("fourier_support_host", _P),
+        ("fourier_support_host", _P), ("periodic", _I32),
     ]
 
 
@@ -51,6 +51,7 @@ SIGNATURES = {
     "od2p_halo_unpack": (ctypes.c_int, [_P, _I32, _P, _P]),
     "ptycho_plan_dims": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "ptycho_plan_layout": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "ptycho_plan_periodic_layout": (ctypes.c_int, [_P, _P, _P]),
     "ptycho_forward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "stagm_prox": (ctypes.c_int, [_P, _P, _P, _I64, _F, _F, _P]),
     "overlap_add": (ctypes.c_int, [_P, _P, _P, _P, _I32, _P]),

@@ -69,6 +69,7 @@ class Geometry:
     gamma: float = 0.0
     blind: bool = False
     fourier_support: np.ndarray | None = None  # (m, m) uint8, blind only
+    periodic: bool = False                     # windows wrap around the image (a torus)
 
     @property
     def n_frames(self) -> int:
@@ -90,7 +91,7 @@ class Plan:
         g = _lib.Geometry(geom.img_h, geom.img_w, geom.m, J, self._offs.ctypes.data, geom.sub_rows,
                           geom.sub_cols, geom.overlap_px, geom.eps, geom.eta, geom.r, geom.mu,
                           geom.gamma, int(bool(geom.blind)),
-                          self._mask.ctypes.data if self._mask is not None else None)
+                          self._mask.ctypes.data if self._mask is not None else None, int(bool(geom.periodic)))
         h = ctypes.c_void_p()
         if owner is None:
             if tuple(f.shape) != (J, geom.m, geom.m):
@@ -143,6 +144,13 @@ class Plan:
         check(self._lib.ptycho_plan_layout(self.handle, fs.ctypes.data, rect.ctypes.data,
                                            pr.ctypes.data, prc.ctypes.data))
         return fs, rect, pr[:self.n_pairs], prc[:self.n_pairs]
+
+    def periodic_layout(self):
+        """(pair_shift[P,2] in periods, placed offsets[J,2] in extended coordinates)."""
+        sh = np.empty((max(self.n_pairs, 1), 2), np.int32)
+        placed = np.empty((self.n_frames, 2), np.int32)
+        check(self._lib.ptycho_plan_periodic_layout(self.handle, sh.ctypes.data, placed.ctypes.data))
+        return sh[:self.n_pairs], placed
 
 
 def ptycho_plan(geom: Geometry, f: torch.Tensor, stream=None) -> Plan:
@@ -202,7 +210,8 @@ def _geometry_struct(geom: Geometry):
             if geom.fourier_support is not None else None)
     g = _lib.Geometry(geom.img_h, geom.img_w, geom.m, offs.shape[0], offs.ctypes.data, geom.sub_rows,
                       geom.sub_cols, geom.overlap_px, geom.eps, geom.eta, geom.r, geom.mu, geom.gamma,
-                      int(bool(geom.blind)), mask.ctypes.data if mask is not None else None)
+                      int(bool(geom.blind)), mask.ctypes.data if mask is not None else None,
+                      int(bool(geom.periodic)))
     return g, (offs, mask)
 
 

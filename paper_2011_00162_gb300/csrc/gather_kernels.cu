@@ -340,7 +340,9 @@ constexpr int RC_BLOCKS = 64;  // blocks per ordered pair / over u in the consen
 // part[k * RC_BLOCKS + b] = sum over block b's share (element-strided, fixed
 // order) of |u_d - u_e|^2 on ordered pair k's overlap; part[P * RC_BLOCKS + b]
 // likewise of |u|^2 over all subdomain pixels.
+// pair_shift (null without periodic boundaries): u_e is read at (R - s_r H, C - s_c W)
 __global__ void __launch_bounds__(256) consensus_partial_kernel(int P, const int32_t *pair, const int32_t *pair_rect,
+                                                                const int32_t *pair_shift, int H, int W,
                                                                 const int32_t *rect, const int64_t *u_off,
                                                                 int64_t u_len, const float2 *u, float *part)
 {
@@ -349,13 +351,14 @@ __global__ void __launch_bounds__(256) consensus_partial_kernel(int P, const int
     float acc = 0.f, dummy = 0.f;
     if (k < P) {
         const int d = pair[2 * k], e = pair[2 * k + 1];
+        const int sR = pair_shift ? pair_shift[2 * k] * H : 0, sC = pair_shift ? pair_shift[2 * k + 1] * W : 0;
         const int32_t *pr = pair_rect + 4 * k, *Rd = rect + 4 * d, *Re = rect + 4 * e;
         const int w = pr[3] - pr[1];
         const int64_t n = (int64_t)(pr[2] - pr[0]) * w;
         for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += RC_BLOCKS * 256) {
             const int R = pr[0] + (int)(i / w), C = pr[1] + (int)(i % w);
             const float2 a = u[u_off[d] + (int64_t)(R - Rd[0]) * (Rd[3] - Rd[1]) + (C - Rd[1])];
-            const float2 b = u[u_off[e] + (int64_t)(R - Re[0]) * (Re[3] - Re[1]) + (C - Re[1])];
+            const float2 b = u[u_off[e] + (int64_t)(R - sR - Re[0]) * (Re[3] - Re[1]) + (C - sC - Re[1])];
             acc += cabs2(csub(a, b));
         }
     } else {
@@ -653,8 +656,11 @@ __global__ void q_from_slots_kernel(int J, int M, int R1, int R2, const float2 *
 }
 
 // u_d = R_d u0 (or 1), over the subdomain tiles
+// H > 0: periodic boundaries, u0 read modulo H x W (rectangles in extended coordinates)
+__device__ __forceinline__ int wrap_index(int x, int n) { const int r = x % n; return r < 0 ? r + n : r; }
+
 __global__ void init_u_kernel(const Tile *tiles, const int32_t *rect, const int64_t *u_off, int W,
-                              const float2 *u0, float2 *u)
+                              const float2 *u0, float2 *u, int H)
 {
     const Tile tile = tiles[blockIdx.x];
     const int d = tile.reg;
@@ -666,8 +672,10 @@ __global__ void init_u_kernel(const Tile *tiles, const int32_t *rect, const int6
     for (int r = 0; r < TILE_ROWS; ++r) {
         const int lr = tile.r0 + ty0 + r;
         if (lr >= hd) break;
+        const int R = rc[0] + lr, C = rc[1] + lc;
         u[u_off[d] + (int64_t)lr * wd + lc] =
-            u0 ? u0[(size_t)(rc[0] + lr) * W + (rc[1] + lc)] : make_float2(1.f, 0.f);
+            u0 ? u0[H > 0 ? (size_t)wrap_index(R, H) * W + wrap_index(C, W) : (size_t)R * W + C]
+               : make_float2(1.f, 0.f);
     }
 }
 
@@ -681,23 +689,34 @@ __global__ void broadcast_probe_kernel(int MM, int D, const float2 *w0, float2 *
         for (int d = 0; d < D; ++d) Wd[(size_t)d * MM + k] = v;
 }
 
+// The merged image at pixel (R, C): the average of the subdomain copies that
+// hold it, d ascending (periodic boundaries, smax > 0: every copy (R + s_r H,
+// C + s_c W), s in [-smax, smax]^2 row-major, within each d), 1 where none does.
+__device__ __forceinline__ float2 merged_pixel(int R, int C, int H, int W, int D, int smax, const int32_t *rect,
+                                               const int64_t *u_off, const float2 *u)
+{
+    float2 t = make_float2(0.f, 0.f);
+    int cnt = 0;
+    for (int d = 0; d < D; ++d) {
+        const int32_t *rc = rect + 4 * d;
+        for (int sr = -smax; sr <= smax; ++sr)
+            for (int sc = -smax; sc <= smax; ++sc) {
+                const int RR = R + sr * H, CC = C + sc * W;
+                if (RR < rc[0] || RR >= rc[2] || CC < rc[1] || CC >= rc[3]) continue;
+                t = cadd(t, u[u_off[d] + (int64_t)(RR - rc[0]) * (rc[3] - rc[1]) + (CC - rc[1])]);
+                ++cnt;
+            }
+    }
+    return cnt ? make_float2(t.x / cnt, t.y / cnt) : make_float2(1.f, 0.f);
+}
+
 // section 4: overlaps averaged, single-subdomain pixels kept
-__global__ void merge_kernel(int H, int W, int D, const int32_t *rect, const int64_t *u_off,
+__global__ void merge_kernel(int H, int W, int D, int smax, const int32_t *rect, const int64_t *u_off,
                              const float2 *u, float2 *out)
 {
     const size_t n = (size_t)H * W;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const int R = (int)(e / W), C = (int)(e % W);
-        float2 t = make_float2(0.f, 0.f);
-        int cnt = 0;
-        for (int d = 0; d < D; ++d) {
-            const int32_t *rc = rect + 4 * d;
-            if (R < rc[0] || R >= rc[2] || C < rc[1] || C >= rc[3]) continue;
-            t = cadd(t, u[u_off[d] + (int64_t)(R - rc[0]) * (rc[3] - rc[1]) + (C - rc[1])]);
-            ++cnt;
-        }
-        out[e] = cnt ? make_float2(t.x / cnt, t.y / cnt) : make_float2(1.f, 0.f);
-    }
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = merged_pixel((int)(e / W), (int)(e % W), H, W, D, smax, rect, u_off, u);
 }
 
 // ---------------------------------------------------------------- peak probes
@@ -799,27 +818,11 @@ __global__ void __launch_bounds__(256) opnorm_kernel(int P, const int32_t *pair,
 // ---------------------------------------------------------------- SNR (section 4)
 constexpr int SNR_BLOCKS = 152 * 4;
 
-// The merged image at pixel (R, C): the average of the subdomain copies that
-// hold it, 1 where none does (as od2p_merge).
-__device__ __forceinline__ float2 merged_pixel(int R, int C, int D, const int32_t *rect, const int64_t *u_off,
-                                               const float2 *u)
-{
-    float2 t = make_float2(0.f, 0.f);
-    int cnt = 0;
-    for (int d = 0; d < D; ++d) {
-        const int32_t *rc = rect + 4 * d;
-        if (R < rc[0] || R >= rc[2] || C < rc[1] || C >= rc[3]) continue;
-        t = cadd(t, u[u_off[d] + (int64_t)(R - rc[0]) * (rc[3] - rc[1]) + (C - rc[1])]);
-        ++cnt;
-    }
-    return cnt ? make_float2(t.x / cnt, t.y / cnt) : make_float2(1.f, 0.f);
-}
-
 // Section 4's SNR of the recovery m (the merged image) against the truth t.
 // pass 0: part = sum conj(m) t per block; pass 1: part = (sum |e^{i theta} m - t|^2,
 // sum |m|^2) per block, e^{i theta} = ph.  Pixels where mask is 0 are left out
 // (mask may be NULL).  Pixels grid-strided, fixed order.
-__global__ void __launch_bounds__(256) snr_pass_kernel(int pass, int H, int W, int D, const int32_t *rect,
+__global__ void __launch_bounds__(256) snr_pass_kernel(int pass, int H, int W, int D, int smax, const int32_t *rect,
                                                        const int64_t *u_off, const float2 *u, const float2 *truth,
                                                        const uint8_t *mask, const double *ph, float *part)
 {
@@ -829,7 +832,7 @@ __global__ void __launch_bounds__(256) snr_pass_kernel(int pass, int H, int W, i
     float a = 0.f, b = 0.f;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
         if (mask && !mask[k]) continue;
-        const float2 m = merged_pixel((int)(k / W), (int)(k % W), D, rect, u_off, u);
+        const float2 m = merged_pixel((int)(k / W), (int)(k % W), H, W, D, smax, rect, u_off, u);
         const float2 t = truth[k];
         if (pass == 0) {
             const float2 c = cconjmul(m, t);
@@ -1112,7 +1115,9 @@ int launch_scale(float2 *x, int64_t n, float sc, cudaStream_t s)
 
 int launch_consensus(ptycho_plan_s *p, float *part, double *out, cudaStream_t s)
 {
-    consensus_partial_kernel<<<dim3(RC_BLOCKS, p->P + 1), 256, 0, s>>>(p->P, p->d_pair, p->d_pair_rect, p->d_rect,
+    consensus_partial_kernel<<<dim3(RC_BLOCKS, p->P + 1), 256, 0, s>>>(p->P, p->d_pair, p->d_pair_rect,
+                                                                        p->periodic ? p->d_pair_shift : nullptr,
+                                                                        p->H, p->W, p->d_rect,
                                                                         p->d_u_off, p->u_len, p->d_u[p->cur], part);
     OD2P_CUDA(cudaGetLastError());
     consensus_final_kernel<<<1, 32, 0, s>>>(p->P, part, out);
@@ -1138,7 +1143,8 @@ int launch_sum_sqrtf(ptycho_plan_s *p, cudaStream_t s)
 int launch_init_state(ptycho_plan_s *p, const float2 *u0, const float2 *w0, cudaStream_t s)
 {
     init_u_kernel<<<p->sub_tiles.n_tiles, GATHER_THREADS, 0, s>>>(p->sub_tiles.tiles, p->d_rect,
-                                                                  p->d_u_off, p->W, u0, p->d_u[p->cur]);
+                                                                  p->d_u_off, p->W, u0, p->d_u[p->cur],
+                                                                  p->periodic ? p->H : 0);
     OD2P_CUDA(cudaGetLastError());
     broadcast_probe_kernel<<<(p->MM + 255) / 256, 256, 0, s>>>(p->MM, p->D, w0, p->d_w,
                                                                 p->blind ? p->d_Wd : nullptr);
@@ -1181,7 +1187,8 @@ int launch_q_from_slots(const ptycho_plan_s *p, float2 *dst, cudaStream_t s)
 
 int launch_merge(const ptycho_plan_s *p, float2 *out, cudaStream_t s)
 {
-    merge_kernel<<<152 * 8, 256, 0, s>>>(p->H, p->W, p->D, p->d_rect, p->d_u_off, p->d_u[p->cur], out);
+    merge_kernel<<<152 * 8, 256, 0, s>>>(p->H, p->W, p->D, p->periodic ? PERIOD_SHIFTS : 0, p->d_rect, p->d_u_off,
+                                         p->d_u[p->cur], out);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
@@ -1296,7 +1303,8 @@ int launch_snr(ptycho_plan_s *p, const float2 *truth, const uint8_t *mask, float
                cudaStream_t s)
 {
     for (int pass = 0; pass < 2; ++pass) {
-        snr_pass_kernel<<<SNR_BLOCKS, 256, 0, s>>>(pass, p->H, p->W, p->D, p->d_rect, p->d_u_off, p->d_u[p->cur],
+        snr_pass_kernel<<<SNR_BLOCKS, 256, 0, s>>>(pass, p->H, p->W, p->D, p->periodic ? PERIOD_SHIFTS : 0,
+                                                   p->d_rect, p->d_u_off, p->d_u[p->cur],
                                                    truth, mask, out, part);
         OD2P_CUDA(cudaGetLastError());
         snr_final_kernel<<<1, 32, 0, s>>>(pass, part, out);

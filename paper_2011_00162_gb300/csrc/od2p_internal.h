@@ -38,6 +38,9 @@ constexpr int WAVE_256 = OD2P_WAVE_256;
 #define OD2P_WAVE_CHAINS_256 4
 #endif
 constexpr int WAVE_CHAINS_256 = OD2P_WAVE_CHAINS_256;
+// Periodic boundaries: rectangles inside (-H, 2H) x (-W, 2W) meet copies of each
+// other shifted by at most this many periods per axis.
+constexpr int PERIOD_SHIFTS = 2;
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
@@ -175,14 +178,16 @@ struct ptycho_plan_s {
     float eps = 0, eta = 0, r = 0, mu = 0, gamma = 0;
     int32_t blind = 0;
     bool has_mask = false;
-    // ---- host copies of the decomposition
-    std::vector<int32_t> offs, frame_sub, rect, pair, pair_rect;
+    bool periodic = false;         // periodic boundaries: rectangles in extended coordinates
+    // ---- host copies of the decomposition (offs: each frame's placed offset)
+    std::vector<int32_t> offs, frame_sub, rect, pair, pair_rect, pair_shift;
     std::vector<int64_t> u_off, lam_off;
     int64_t u_len = 0, lam_len = 0;
     // ---- device geometry
     int32_t *d_offs = nullptr, *d_frame_sub = nullptr, *d_frame_base = nullptr,
             *d_frame_pitch = nullptr, *d_rect = nullptr, *d_nbr_ptr = nullptr, *d_nbr = nullptr,
             *d_pair_rect = nullptr, *d_pair = nullptr, *d_img_base = nullptr,  // nbr: (e, pair d-e, pair e-d) per neighbour
+            *d_pair_shift = nullptr,                     // (s_r, s_c) per pair, in periods
             *d_img_pitch = nullptr;                      // img_w for every frame
     od2p::NbrInfo *d_nbr_info = nullptr;  // per neighbour entry, same order as d_nbr
     int64_t *d_u_off = nullptr, *d_lam_off = nullptr;

@@ -95,12 +95,18 @@ int upload(T **dst, const std::vector<T> &src, std::vector<void *> &owned, cudaS
 }
 
 // Overlapping decomposition (sections 2.1 and 3.1; rule stated in od2p.h).
+// Periodic boundaries: rectangles in extended coordinates (pixel (R, C) is image
+// pixel (R mod H, C mod W)), each frame at the copy of its offset whose centre
+// lies on the image (`placed`), and pairs (d, e, s) over shifts s of whole
+// periods, in d's coordinates, including a subdomain with copies of itself.
 struct Layout {
     std::vector<int32_t> frame_sub, rect, pair, pair_rect;
+    std::vector<int32_t> placed;      // J x 2: each frame's offset in extended coordinates
+    std::vector<int32_t> pair_shift;  // P x 2: (s_r, s_c) in periods (0 without periodic boundaries)
 };
 
 Layout decompose(int H, int W, int m, const std::vector<int32_t> &offs, int sub_rows, int sub_cols,
-                 int overlap_px)
+                 int overlap_px, bool periodic = false)
 {
     Layout L;
     const int J = (int)offs.size() / 2, D = sub_rows * sub_cols;
@@ -111,18 +117,29 @@ Layout decompose(int H, int W, int m, const std::vector<int32_t> &offs, int sub_
     L.rect.resize(4 * D);
     for (int d = 0; d < D; ++d) {
         const int a = d / sub_cols, b = d % sub_cols;
-        const int r0 = (int)rb[a] - (a > 0 ? grow : 0), r1 = (int)rb[a + 1] + (a + 1 < sub_rows ? grow : 0);
-        const int c0 = (int)cb[b] - (b > 0 ? grow : 0), c1 = (int)cb[b + 1] + (b + 1 < sub_cols ? grow : 0);
-        L.rect[4 * d + 0] = std::max(r0, 0);
-        L.rect[4 * d + 1] = std::max(c0, 0);
-        L.rect[4 * d + 2] = std::min(r1, H);
-        L.rect[4 * d + 3] = std::min(c1, W);
+        // on a torus every side of a tile faces a neighbour: grown on all sides, not clipped
+        const int r0 = (int)rb[a] - (periodic || a > 0 ? grow : 0);
+        const int r1 = (int)rb[a + 1] + (periodic || a + 1 < sub_rows ? grow : 0);
+        const int c0 = (int)cb[b] - (periodic || b > 0 ? grow : 0);
+        const int c1 = (int)cb[b + 1] + (periodic || b + 1 < sub_cols ? grow : 0);
+        L.rect[4 * d + 0] = periodic ? r0 : std::max(r0, 0);
+        L.rect[4 * d + 1] = periodic ? c0 : std::max(c0, 0);
+        L.rect[4 * d + 2] = periodic ? r1 : std::min(r1, H);
+        L.rect[4 * d + 3] = periodic ? c1 : std::min(c1, W);
     }
     // frame -> the core tile holding its window centre o + (m-1)/2, i.e. the last
     // boundary b with 2*b <= 2*o + m - 1
     L.frame_sub.resize(J);
+    L.placed.resize(2 * (size_t)J);
     for (int j = 0; j < J; ++j) {
-        const int64_t cr = 2LL * offs[2 * j] + m - 1, cc = 2LL * offs[2 * j + 1] + m - 1;
+        int orow = offs[2 * j], ocol = offs[2 * j + 1];
+        if (periodic) {  // the copy whose doubled centre lies in [0, 2H) x [0, 2W)
+            if (2LL * orow + m - 1 >= 2LL * H) orow -= H;
+            if (2LL * ocol + m - 1 >= 2LL * W) ocol -= W;
+        }
+        L.placed[2 * j] = orow;
+        L.placed[2 * j + 1] = ocol;
+        const int64_t cr = 2LL * orow + m - 1, cc = 2LL * ocol + m - 1;
         int a = 0, b = 0;
         for (int k = 1; k < sub_rows; ++k)
             if (2 * rb[k] <= cr) a = k;
@@ -131,23 +148,44 @@ Layout decompose(int H, int W, int m, const std::vector<int32_t> &offs, int sub_
         const int d = a * sub_cols + b;
         L.frame_sub[j] = d;
         int32_t *R = &L.rect[4 * d];
-        R[0] = std::min(R[0], offs[2 * j]);
-        R[1] = std::min(R[1], offs[2 * j + 1]);
-        R[2] = std::max(R[2], offs[2 * j] + m);
-        R[3] = std::max(R[3], offs[2 * j + 1] + m);
+        R[0] = std::min(R[0], orow);
+        R[1] = std::min(R[1], ocol);
+        R[2] = std::max(R[2], orow + m);
+        R[3] = std::max(R[3], ocol + m);
     }
+    const int smax = periodic ? PERIOD_SHIFTS : 0;
     for (int d = 0; d < D; ++d)
-        for (int e = 0; e < D; ++e) {
-            if (d == e) continue;
-            const int32_t *A = &L.rect[4 * d], *B = &L.rect[4 * e];
-            const int r0 = std::max(A[0], B[0]), c0 = std::max(A[1], B[1]);
-            const int r1 = std::min(A[2], B[2]), c1 = std::min(A[3], B[3]);
-            if (r0 < r1 && c0 < c1) {
-                L.pair.insert(L.pair.end(), {d, e});
-                L.pair_rect.insert(L.pair_rect.end(), {r0, c0, r1, c1});
-            }
-        }
+        for (int e = 0; e < D; ++e)
+            for (int sr = -smax; sr <= smax; ++sr)
+                for (int sc = -smax; sc <= smax; ++sc) {
+                    if (d == e && sr == 0 && sc == 0) continue;
+                    const int32_t *A = &L.rect[4 * d], *B = &L.rect[4 * e];
+                    const int r0 = std::max(A[0], B[0] + sr * H), c0 = std::max(A[1], B[1] + sc * W);
+                    const int r1 = std::min(A[2], B[2] + sr * H), c1 = std::min(A[3], B[3] + sc * W);
+                    if (r0 < r1 && c0 < c1) {
+                        L.pair.insert(L.pair.end(), {d, e});
+                        L.pair_shift.insert(L.pair_shift.end(), {sr, sc});
+                        L.pair_rect.insert(L.pair_rect.end(), {r0, c0, r1, c1});
+                    }
+                }
     return L;
+}
+
+// Pair k's reverse (e, d, -s) and whether k is the one listed first of the two
+// (d < e, or d = e with the positive shift), which fixes the operand order of v.
+void pair_links(const Layout &L, std::vector<int> &rev, std::vector<int> &first)
+{
+    const int P = (int)L.pair.size() / 2;
+    rev.assign(P, -1);
+    first.assign(P, 0);
+    for (int k = 0; k < P; ++k) {
+        const int d = L.pair[2 * k], e = L.pair[2 * k + 1], sr = L.pair_shift[2 * k], sc = L.pair_shift[2 * k + 1];
+        for (int q = 0; q < P; ++q)
+            if (L.pair[2 * q] == e && L.pair[2 * q + 1] == d && L.pair_shift[2 * q] == -sr &&
+                L.pair_shift[2 * q + 1] == -sc)
+                rev[k] = q;
+        first[k] = d < e || (d == e && (sr > 0 || (sr == 0 && sc > 0)));
+    }
 }
 
 // Tiles of TILE_H x TILE_W pixels over each region, with the frames whose
@@ -441,10 +479,26 @@ int check_geometry(const ptycho_geometry *g)
     if (g->sub_rows < 1 || g->sub_cols < 1 || g->sub_rows > g->img_h || g->sub_cols > g->img_w ||
         g->overlap_px < 0)
         return fail(PTYCHO_ERR_INVALID_ARG, "bad subdomain grid or overlap");
+    if (g->periodic != 0 && g->periodic != 1) return fail(PTYCHO_ERR_INVALID_ARG, "periodic must be 0 or 1");
     for (int j = 0; j < g->n_frames; ++j) {
         const int r0 = g->offsets_host[2 * j], c0 = g->offsets_host[2 * j + 1];
-        if (r0 < 0 || c0 < 0 || r0 > g->img_h - g->m || c0 > g->img_w - g->m)
-            return fail(PTYCHO_ERR_INVALID_ARG, "offset of frame " + std::to_string(j) + " out of range");
+        const bool bad = g->periodic ? (r0 < 0 || c0 < 0 || r0 >= g->img_h || c0 >= g->img_w)
+                                     : (r0 < 0 || c0 < 0 || r0 > g->img_h - g->m || c0 > g->img_w - g->m);
+        if (bad) return fail(PTYCHO_ERR_INVALID_ARG, "offset of frame " + std::to_string(j) + " out of range");
+    }
+    return PTYCHO_OK;
+}
+
+// Periodic boundaries: every rectangle within (-H, 2H) x (-W, 2W), so that shifts
+// of up to PERIOD_SHIFTS periods find every copy of a pixel.
+int check_periodic_rects(const ptycho_geometry *g, const Layout &L)
+{
+    if (!g->periodic) return PTYCHO_OK;
+    for (size_t d = 0; d < L.rect.size() / 4; ++d) {
+        const int32_t *R = &L.rect[4 * d];
+        if (R[0] <= -g->img_h || R[2] >= 2 * g->img_h || R[1] <= -g->img_w || R[3] >= 2 * g->img_w)
+            return fail(PTYCHO_ERR_INVALID_ARG, "periodic: subdomain " + std::to_string(d) +
+                                                    " reaches a period beyond the image (more subdomains or less overlap)");
     }
     return PTYCHO_OK;
 }
@@ -457,7 +511,7 @@ extern "C" {
 
 const char *ptycho_last_error(void) { return od2p::g_err.c_str(); }
 
-int32_t ptycho_abi_version(void) { return 2; }
+int32_t ptycho_abi_version(void) { return 3; }
 
 int ptycho_release_cached_memory(void)
 {
@@ -498,7 +552,8 @@ int ptycho_decompose(const ptycho_geometry *g, int32_t *frame_sub_host, int32_t 
 {
     if (int rc = check_geometry(g)) return rc;
     std::vector<int32_t> offs(g->offsets_host, g->offsets_host + 2 * g->n_frames);
-    Layout L = decompose(g->img_h, g->img_w, g->m, offs, g->sub_rows, g->sub_cols, g->overlap_px);
+    Layout L = decompose(g->img_h, g->img_w, g->m, offs, g->sub_rows, g->sub_cols, g->overlap_px, g->periodic != 0);
+    if (int rc = check_periodic_rects(g, L)) return rc;
     if (frame_sub_host) std::memcpy(frame_sub_host, L.frame_sub.data(), sizeof(int32_t) * g->n_frames);
     if (rect_host) std::memcpy(rect_host, L.rect.data(), sizeof(int32_t) * L.rect.size());
     return PTYCHO_OK;
@@ -510,6 +565,7 @@ int ptycho_plan_shard(ptycho_plan_t **out, const ptycho_geometry *g, const int32
     if (!out) return fail(PTYCHO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (int rc = check_geometry(g)) return rc;
+    if (g->periodic) return fail(PTYCHO_ERR_UNSUPPORTED, "shards of a periodic decomposition are not built");
     if (!owner_host) return fail(PTYCHO_ERR_INVALID_ARG, "owner is NULL");
     const int D = g->sub_rows * g->sub_cols;
     bool mine = false;
@@ -585,10 +641,26 @@ int ptycho_plan_layout(const ptycho_plan_t *plan, int32_t *frame_sub, int32_t *r
     return PTYCHO_OK;
 }
 
+int ptycho_plan_periodic_layout(const ptycho_plan_t *plan, int32_t *pair_shift, int32_t *placed)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (pair_shift && plan->P) std::memcpy(pair_shift, plan->pair_shift.data(), sizeof(int32_t) * 2 * plan->P);
+    if (placed) std::memcpy(placed, plan->offs.data(), sizeof(int32_t) * 2 * plan->J);
+    return PTYCHO_OK;
+}
+
+// the image-space operators read whole-image windows, which a periodic plan would wrap
+static int refuse_periodic(const ptycho_plan_t *plan, const char *what)
+{
+    return plan->periodic ? fail(PTYCHO_ERR_UNSUPPORTED, std::string(what) + " is not built for periodic plans")
+                          : PTYCHO_OK;
+}
+
 int ptycho_forward(const ptycho_plan_t *plan, const ptycho_c32 *u, const ptycho_c32 *w,
                    ptycho_c32 *frames_out, ptycho_stream_t stream)
 {
     if (!plan || !u || !w || !frames_out) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
+    if (int rc = refuse_periodic(plan, "ptycho_forward")) return rc;
     return launch_forward(plan, reinterpret_cast<const float2 *>(u), reinterpret_cast<const float2 *>(w),
                           reinterpret_cast<float2 *>(frames_out), reinterpret_cast<cudaStream_t>(stream));
 }
@@ -610,6 +682,7 @@ int overlap_add(ptycho_plan_t *plan, const ptycho_c32 *frames, const ptycho_c32 
 {
     if (!plan || !frames || !w || !image_out) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
     if (flags & ~PTYCHO_OA_IFFT) return fail(PTYCHO_ERR_INVALID_ARG, "unknown flag");
+    if (int rc = refuse_periodic(plan, "overlap_add")) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float2 *fr = reinterpret_cast<const float2 *>(frames);
     const float2 *wv = reinterpret_cast<const float2 *>(w);
@@ -986,6 +1059,7 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u, const ptycho_c32 *
 {
     if (!plan || !u || !w || !loss) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
     if (recompute < 0 || recompute > 2) return fail(PTYCHO_ERR_INVALID_ARG, "recompute must be 0, 1 or 2");
+    if (int rc = refuse_periodic(plan, "stagm_loss_grad")) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float2 *uu = reinterpret_cast<const float2 *>(u), *ww = reinterpret_cast<const float2 *>(w);
     const float2 *h = plan->d_q;
@@ -1317,16 +1391,14 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
     if (g->blind && (!(g->mu > 0.f) || !(g->gamma >= 0.f)))
         return fail(PTYCHO_ERR_INVALID_ARG, "blind plans need mu > 0 and gamma >= 0");
     const int m = g->m;
-    for (int j = 0; j < g->n_frames; ++j) {
-        const int r0 = g->offsets_host[2 * j], c0 = g->offsets_host[2 * j + 1];
-        if (r0 < 0 || c0 < 0 || r0 > g->img_h - m || c0 > g->img_w - m)
-            return fail(PTYCHO_ERR_INVALID_ARG, "offset of frame " + std::to_string(j) + " out of range");
-    }
+    if (int rc = check_geometry(g)) return rc;  // offsets (periodic: anywhere on the image)
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the decomposition always comes from every frame; a shard keeps the frames
     // of its own subdomains (ascending global index)
     std::vector<int32_t> all_offs(g->offsets_host, g->offsets_host + 2 * g->n_frames);
-    Layout L = decompose(g->img_h, g->img_w, m, all_offs, g->sub_rows, g->sub_cols, g->overlap_px);
+    const bool periodic = g->periodic != 0;
+    Layout L = decompose(g->img_h, g->img_w, m, all_offs, g->sub_rows, g->sub_cols, g->overlap_px, periodic);
+    if (int rc = check_periodic_rects(g, L)) return rc;
     const int D_all = g->sub_rows * g->sub_cols;
     std::vector<int32_t> sel;
     for (int j = 0; j < g->n_frames; ++j)
@@ -1354,12 +1426,13 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
     p->mu = g->mu;
     p->gamma = g->gamma;
     p->blind = g->blind ? 1 : 0;
+    p->periodic = periodic;
     p->offs.resize(2 * (size_t)J);
     p->frame_sub.resize(J);
     p->global_j = sel;
     for (int i = 0; i < J; ++i) {
-        p->offs[2 * i] = all_offs[2 * sel[i]];
-        p->offs[2 * i + 1] = all_offs[2 * sel[i] + 1];
+        p->offs[2 * i] = L.placed[2 * sel[i]];
+        p->offs[2 * i + 1] = L.placed[2 * sel[i] + 1];
         p->frame_sub[i] = L.frame_sub[sel[i]];
     }
     p->D = D_all;
@@ -1371,6 +1444,7 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
     p->rect = L.rect;
     p->pair = L.pair;
     p->pair_rect = L.pair_rect;
+    p->pair_shift = L.pair_shift;
     p->u_off.assign(p->D + 1, 0);
     for (int d = 0; d < p->D; ++d)
         p->u_off[d + 1] = p->u_off[d] + (int64_t)(p->rect[4 * d + 2] - p->rect[4 * d]) *
@@ -1397,27 +1471,25 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
         sub_frames[d].push_back(j);
         all_frames[0].push_back(j);
     }
+    // neighbours of each subdomain: its pairs in list order (e ascending, then the
+    // shift), each with its reverse pair and Omega_e moved into d's coordinates
     std::vector<int32_t> nbr_ptr(p->D + 1, 0), nbr;
-    {
-        std::vector<int> pair_of((size_t)p->D * p->D, -1);
-        for (int k = 0; k < p->P; ++k) pair_of[(size_t)p->pair[2 * k] * p->D + p->pair[2 * k + 1]] = k;
-        for (int d = 0; d < p->D; ++d) {
-            for (int e = 0; e < p->D; ++e) {
-                const int kde = pair_of[(size_t)d * p->D + e];
-                if (kde < 0) continue;
-                nbr.insert(nbr.end(), {e, kde, pair_of[(size_t)e * p->D + d]});
-            }
-            nbr_ptr[d + 1] = (int32_t)(nbr.size() / 3);
-        }
+    std::vector<int> rev, first;
+    pair_links(L, rev, first);
+    for (int k = 0; k < p->P; ++k) nbr.insert(nbr.end(), {p->pair[2 * k + 1], k, rev[k]});
+    for (int k = 0, d = 0; d < p->D; ++d) {
+        while (k < p->P && p->pair[2 * k] <= d) ++k;
+        nbr_ptr[d + 1] = k;
     }
     std::vector<NbrInfo> nbr_info(nbr.size() / 3);
     for (int d = 0; d < p->D; ++d)
         for (int i = nbr_ptr[d]; i < nbr_ptr[d + 1]; ++i) {
             const int e = nbr[3 * i], kde = nbr[3 * i + 1], ked = nbr[3 * i + 2];
+            const int sR = p->pair_shift[2 * kde] * p->H, sC = p->pair_shift[2 * kde + 1] * p->W;
             const int32_t *Re = &p->rect[4 * e], *Pr = &p->pair_rect[4 * kde];
-            nbr_info[i] = NbrInfo{Re[0], Re[1], Re[2], Re[3], (int32_t)p->u_off[e], Re[3] - Re[1],
+            nbr_info[i] = NbrInfo{Re[0] + sR, Re[1] + sC, Re[2] + sR, Re[3] + sC, (int32_t)p->u_off[e], Re[3] - Re[1],
                                   Pr[0], Pr[1], Pr[3] - Pr[1], (int32_t)p->lam_off[kde],
-                                  (int32_t)p->lam_off[ked], d < e ? 1 : 0};
+                                  (int32_t)p->lam_off[ked], first[kde]};
         }
     // subdomain tiles: a shard tiles only its own subdomains (the others' rectangles
     // hold halo copies that the subdomain update reads but never writes)
@@ -1461,7 +1533,7 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
         (rc = upload(&p->d_img_pitch, img_pitch, own, s)) ||
         (rc = upload(&p->d_rect, p->rect, own, s)) || (rc = upload(&p->d_nbr_ptr, nbr_ptr, own, s)) ||
         (rc = upload(&p->d_nbr, nbr, own, s)) || (rc = upload(&p->d_pair_rect, p->pair_rect, own, s)) ||
-        (rc = upload(&p->d_pair, p->pair, own, s)) ||
+        (rc = upload(&p->d_pair, p->pair, own, s)) || (rc = upload(&p->d_pair_shift, p->pair_shift, own, s)) ||
         (rc = upload(&p->d_nbr_info, nbr_info, own, s)) ||
         (rc = upload(&p->d_u_off, p->u_off, own, s)) || (rc = upload(&p->d_lam_off, p->lam_off, own, s)) ||
         (rc = upload_tiles(p->sub_tiles, st, own, s)) || (rc = upload_tiles(p->img_tiles, it, own, s)) ||

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_argument_errors(lib):
-    assert lib.ptycho_abi_version() == 2
+    assert lib.ptycho_abi_version() == 3
     # argument checks return before any device work
     assert lib.ptycho_plan(None, None, None, None) == _lib.ERR_INVALID_ARG
     h = ctypes.c_void_p()
@@ -93,3 +93,30 @@ def test_decomposition_on_the_host_equals_the_oracle():
         fs, rect = od.ptycho_decompose(od.Geometry(n, n, m, offs, grid[0], grid[1], ov))
         fo, ro = oracle.geometry(n, n, m, offs, grid[0], grid[1], ov)
         assert np.array_equal(fs, fo) and np.array_equal(rect, ro)
+
+
+def test_periodic_decomposition_on_the_host_equals_the_oracle():
+    """Periodic boundaries: the host decomposition (extended-coordinate
+    rectangles, frames placed at the copy whose centre lies on the image) is
+    bit-exact against the oracle's, and a rectangle reaching a period beyond the
+    image is refused."""
+    import numpy as np
+
+    import oracle
+    import paper_2011_00162_gb300 as od
+    rng = np.random.default_rng(8)
+    for n, m, step, grid, ov in [(96, 16, 6, (3, 3), 8), (128, 32, 8, (2, 4), 4), (64, 16, 4, (1, 1), 6),
+                                 (256, 64, 16, (4, 4), 16)]:
+        offs = np.array([(r, c) for r in range(0, n, step) for c in range(0, n, step)], np.int32)
+        offs = ((offs + rng.integers(-2, 3, offs.shape)) % n).astype(np.int32)
+        fs, rect = od.ptycho_decompose(od.Geometry(n, n, m, offs, grid[0], grid[1], ov, periodic=True))
+        fo, ro = oracle.geometry(n, n, m, offs, grid[0], grid[1], ov, periodic=True)
+        assert np.array_equal(fs, fo) and np.array_equal(rect, ro), (n, m, grid)
+    # offsets anywhere on the torus are accepted only with periodic boundaries
+    offs = np.array([[90, 90]], np.int32)
+    with pytest.raises(od.PtychoError):
+        od.ptycho_decompose(od.Geometry(96, 96, 16, offs, 1, 1, 0))
+    od.ptycho_decompose(od.Geometry(96, 96, 16, offs, 1, 1, 0, periodic=True))
+    # a 1 x 1 grid with a wide overlap reaches more than a period beyond the image
+    with pytest.raises(od.PtychoError):
+        od.ptycho_decompose(od.Geometry(32, 32, 16, offs % 32, 1, 1, 70, periodic=True))

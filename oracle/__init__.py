@@ -75,6 +75,9 @@ def _load():
             "orc_snr": (f64, [i64, P, P]),
             "orc_geometry": (i32, [i32, i32, i32, i32, P, i32, i32, i32, P, P]),
             "orc_pairs": (i32, [i32, P, i32, P, P]),
+            "orc_forward_ext": (None, [i32, i32, P, i32, P, i32, P, i32, P]),
+            "orc_adjoint_ext": (None, [i32, i32, i32, P, i32, P, i32, P, P]),
+            "orc_loss_grad_ext": (f64, [i32, i32, P, i32, P, i32, P, i32, P, f64, P, P]),
             "orc_geometry_ext": (i32, [i32, i32, i32, i32, P, i32, i32, i32, i32, P, P, P]),
             "orc_pairs_ext": (i32, [i32, P, i32, i32, i32, i32, P, P, P]),
             "orc_admm_new_ext": (P, [i32, i32, i32, i32, P, i32, i32, i32, i32, P, P, P, f64, f64, f64,
@@ -148,30 +151,30 @@ def stagm_prox(y, f, eps: float, lam: float) -> np.ndarray:
     return out
 
 
-def forward(u, w, offs) -> np.ndarray:
-    """All frames F(w o S_j u), shape (J, m, m)."""
+def forward(u, w, offs, periodic: bool = False) -> np.ndarray:
+    """All frames F(w o S_j u), shape (J, m, m) (periodic: windows wrap)."""
     u = _c(u, np.complex128)
     w = _c(w, np.complex128)
     offs = _c(offs, np.int32).reshape(-1, 2)
     H, W = u.shape
     m = w.shape[0]
     out = np.empty((offs.shape[0], m, m), np.complex128)
-    _load().orc_forward(H, W, _p(u), m, _p(w), offs.shape[0], _p(offs), _p(out))
+    _load().orc_forward_ext(H, W, _p(u), m, _p(w), offs.shape[0], _p(offs), int(bool(periodic)), _p(out))
     return out
 
 
-def adjoint(y, w, offs, H: int, W: int) -> np.ndarray:
-    """A^* y = sum_j S_j^T (conj(w) o F^* y_j), shape (H, W)."""
+def adjoint(y, w, offs, H: int, W: int, periodic: bool = False) -> np.ndarray:
+    """A^* y = sum_j S_j^T (conj(w) o F^* y_j), shape (H, W) (periodic: windows wrap)."""
     y = _c(y, np.complex128)
     w = _c(w, np.complex128)
     offs = _c(offs, np.int32).reshape(-1, 2)
     out = np.empty((H, W), np.complex128)
-    _load().orc_adjoint(H, W, w.shape[0], _p(w), offs.shape[0], _p(offs), _p(y), _p(out))
+    _load().orc_adjoint_ext(H, W, w.shape[0], _p(w), offs.shape[0], _p(offs), int(bool(periodic)), _p(y), _p(out))
     return out
 
 
-def loss_grad(u, w, offs, f, eps: float):
-    """(loss, grad_u, grad_w) of sum_j G_eps(F(w o S_j u); f_j)."""
+def loss_grad(u, w, offs, f, eps: float, periodic: bool = False):
+    """(loss, grad_u, grad_w) of sum_j G_eps(F(w o S_j u); f_j) (periodic: windows wrap)."""
     u = _c(u, np.complex128)
     w = _c(w, np.complex128)
     f = _c(f, np.float64)
@@ -179,8 +182,8 @@ def loss_grad(u, w, offs, f, eps: float):
     H, W = u.shape
     gu = np.empty_like(u)
     gw = np.empty_like(w)
-    loss = _load().orc_loss_grad(H, W, _p(u), w.shape[0], _p(w), offs.shape[0], _p(offs),
-                                 _p(f), eps, _p(gu), _p(gw))
+    loss = _load().orc_loss_grad_ext(H, W, _p(u), w.shape[0], _p(w), offs.shape[0], _p(offs),
+                                     int(bool(periodic)), _p(f), eps, _p(gu), _p(gw))
     return float(loss), gu, gw
 
 

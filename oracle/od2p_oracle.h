@@ -47,6 +47,13 @@ void orc_adjoint(int H, int W, int m, const ocplx *w, int J, const int32_t *offs
  * (d/dRe + i d/dIm) w.r.t. u (H x W) and w (m x m); either gradient may be NULL. */
 double orc_loss_grad(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
                      const int32_t *offs, const double *f, double eps, ocplx *gu, ocplx *gw);
+/* The same with periodic != 0: windows wrap modulo H x W (geometry.c's torus reading). */
+void orc_forward_ext(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
+                     const int32_t *offs, int periodic, ocplx *out);
+void orc_adjoint_ext(int H, int W, int m, const ocplx *w, int J, const int32_t *offs, int periodic,
+                     const ocplx *y, ocplx *u_out);
+double orc_loss_grad_ext(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
+                         const int32_t *offs, int periodic, const double *f, double eps, ocplx *gu, ocplx *gw);
 
 /* Data-driven initial probe of the blind experiments (section 4.2): the mean
  * over the J frames of the inverse unitary DFT of the measured amplitudes,

@@ -7,6 +7,9 @@
  * the image is not periodic, section 4 set-up).  A stacks all frames.
  * A^* y = sum_j S_j^T (conj(w) o F^* y_j) follows from F being unitary and S_j
  * being a 0/1 selection.  The windows are accumulated in ascending j.
+ * The _ext variants take `periodic`: then S_j reads and S_j^T adds at pixel
+ * ((offs[j] + a) mod H, (offs[j] + b) mod W) (the torus reading of the
+ * periodic boundary in geometry.c); the plain functions are periodic = 0.
  */
 #include "od2p_oracle.h"
 
@@ -14,10 +17,21 @@
 #include <stdlib.h>
 #include <string.h>
 
-void orc_forward(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
-                 const int32_t *offs, ocplx *out)
+/* index of window pixel (r0 + r, c0 + c) in the H x W image */
+static inline size_t pix(int H, int W, int periodic, int R, int C)
 {
-    (void)H;
+    if (periodic) {
+        R %= H;
+        C %= W;
+        if (R < 0) R += H;
+        if (C < 0) C += W;
+    }
+    return (size_t)R * W + C;
+}
+
+void orc_forward_ext(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
+                     const int32_t *offs, int periodic, ocplx *out)
+{
     const int mm = m * m;
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < J; ++j) {
@@ -25,13 +39,19 @@ void orc_forward(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
         const int r0 = offs[2 * j], c0 = offs[2 * j + 1];
         for (int r = 0; r < m; ++r)
             for (int c = 0; c < m; ++c)
-                x[r * m + c] = w[r * m + c] * u[(size_t)(r0 + r) * W + (c0 + c)];
+                x[r * m + c] = w[r * m + c] * u[pix(H, W, periodic, r0 + r, c0 + c)];
         orc_fft2(x, m, 0);
     }
 }
 
-void orc_adjoint(int H, int W, int m, const ocplx *w, int J, const int32_t *offs,
-                 const ocplx *y, ocplx *u_out)
+void orc_forward(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
+                 const int32_t *offs, ocplx *out)
+{
+    orc_forward_ext(H, W, u, m, w, J, offs, 0, out);
+}
+
+void orc_adjoint_ext(int H, int W, int m, const ocplx *w, int J, const int32_t *offs, int periodic,
+                     const ocplx *y, ocplx *u_out)
 {
     const int mm = m * m;
     ocplx *q = (ocplx *)malloc(sizeof(ocplx) * (size_t)J * mm);
@@ -47,9 +67,15 @@ void orc_adjoint(int H, int W, int m, const ocplx *w, int J, const int32_t *offs
         const int r0 = offs[2 * j], c0 = offs[2 * j + 1];
         for (int r = 0; r < m; ++r)
             for (int c = 0; c < m; ++c)
-                u_out[(size_t)(r0 + r) * W + (c0 + c)] += q[(size_t)j * mm + r * m + c];
+                u_out[pix(H, W, periodic, r0 + r, c0 + c)] += q[(size_t)j * mm + r * m + c];
     }
     free(q);
+}
+
+void orc_adjoint(int H, int W, int m, const ocplx *w, int J, const int32_t *offs,
+                 const ocplx *y, ocplx *u_out)
+{
+    orc_adjoint_ext(H, W, m, w, J, offs, 0, y, u_out);
 }
 
 /*
@@ -58,13 +84,13 @@ void orc_adjoint(int H, int W, int m, const ocplx *w, int J, const int32_t *offs
  * grad_w = sum_j conj(S_j u) o F^* grad g           (chain rule through w)
  * with grad g from eq. (objgrad).
  */
-double orc_loss_grad(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
-                     const int32_t *offs, const double *f, double eps, ocplx *gu, ocplx *gw)
+double orc_loss_grad_ext(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
+                         const int32_t *offs, int periodic, const double *f, double eps, ocplx *gu, ocplx *gw)
 {
     const int mm = m * m;
     ocplx *x = (ocplx *)malloc(sizeof(ocplx) * (size_t)J * mm);
     double *lj = (double *)malloc(sizeof(double) * (size_t)J);
-    orc_forward(H, W, u, m, w, J, offs, x);
+    orc_forward_ext(H, W, u, m, w, J, offs, periodic, x);
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < J; ++j) {
         double acc = 0.0;
@@ -85,7 +111,7 @@ double orc_loss_grad(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
             const int r0 = offs[2 * j], c0 = offs[2 * j + 1];
             for (int r = 0; r < m; ++r)
                 for (int c = 0; c < m; ++c)
-                    gu[(size_t)(r0 + r) * W + (c0 + c)] +=
+                    gu[pix(H, W, periodic, r0 + r, c0 + c)] +=
                         conj(w[r * m + c]) * x[(size_t)j * mm + r * m + c];
         }
     }
@@ -95,14 +121,19 @@ double orc_loss_grad(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
             const int r0 = offs[2 * j], c0 = offs[2 * j + 1];
             for (int r = 0; r < m; ++r)
                 for (int c = 0; c < m; ++c)
-                    gw[r * m + c] += conj(u[(size_t)(r0 + r) * W + (c0 + c)]) *
+                    gw[r * m + c] += conj(u[pix(H, W, periodic, r0 + r, c0 + c)]) *
                                      x[(size_t)j * mm + r * m + c];
         }
     }
-    (void)H;
     free(x);
     free(lj);
     return loss;
+}
+
+double orc_loss_grad(int H, int W, const ocplx *u, int m, const ocplx *w, int J,
+                     const int32_t *offs, const double *f, double eps, ocplx *gu, ocplx *gw)
+{
+    return orc_loss_grad_ext(H, W, u, m, w, J, offs, 0, f, eps, gu, gw);
 }
 
 void orc_probe_init(int m, int J, const double *f, ocplx *w0)

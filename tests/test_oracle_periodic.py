@@ -153,3 +153,49 @@ def test_periodic_geometry_and_pairs():
                     meet = max(A[0], B[0]) < min(A[2], B[2]) and max(A[1], B[1]) < min(A[3], B[3])
                     if meet and not (d == e and sr == 0 and sc == 0):
                         assert (d, e, sr, sc) in keys
+
+
+def test_periodic_forward_equals_rolled_windows_and_adjoint_identity():
+    """Periodic A: frames equal windows cut with np.roll; <A u, y> = <u, A^* y>;
+    without wrapping offsets it equals the vacuum operator."""
+    rng = np.random.default_rng(18)
+    H, W, m = 20, 14, 6
+    offs = np.array([(18, 11), (0, 0), (7, 12), (15, 3)], np.int32)
+    u, w = _image(H, W, 19), _probe(m, 20)
+    A = oracle.forward(u, w, offs, periodic=True)
+    np.testing.assert_allclose(A, _rolled_frames(u, w, offs), atol=1e-13)
+    y = rng.standard_normal(A.shape) + 1j * rng.standard_normal(A.shape)
+    lhs = np.vdot(y, A)
+    rhs = np.vdot(oracle.adjoint(y, w, offs, H, W, periodic=True), u)
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+    inside = np.array([(0, 0), (7, 5), (14, 8)], np.int32)
+    np.testing.assert_array_equal(oracle.forward(u, w, inside, periodic=True), oracle.forward(u, w, inside))
+
+
+def test_periodic_loss_gradient_finite_differences():
+    """Periodic loss: the u- and w-gradients against central differences (FP64)."""
+    rng = np.random.default_rng(21)
+    H, W, m = 12, 10, 4
+    offs = np.array([(10, 8), (3, 9), (0, 0), (6, 4)], np.int32)
+    u, w = _image(H, W, 22), _probe(m, 23)
+    f = np.abs(_rolled_frames(_image(H, W, 24), w, offs)) ** 2
+    loss, gu, gw = oracle.loss_grad(u, w, offs, f, 0.5, periodic=True)
+    h = 1e-6
+    for _ in range(6):
+        R, C = rng.integers(0, H), rng.integers(0, W)
+        for d in (1.0, 1j):
+            up, um = u.copy(), u.copy()
+            up[R, C] += h * d
+            um[R, C] -= h * d
+            fd = (oracle.loss_grad(up, w, offs, f, 0.5, periodic=True)[0] -
+                  oracle.loss_grad(um, w, offs, f, 0.5, periodic=True)[0]) / (2 * h)
+            # the gradient is d loss / d Re u + i d loss / d Im u
+            want = gu[R, C].real if d == 1.0 else gu[R, C].imag
+            assert abs(fd - want) < 1e-5 * max(1.0, abs(want)), (R, C, d, fd, want)
+    k = (1, 2)
+    wp, wm = w.copy(), w.copy()
+    wp[k] += h
+    wm[k] -= h
+    fd = (oracle.loss_grad(u, wp, offs, f, 0.5, periodic=True)[0] -
+          oracle.loss_grad(u, wm, offs, f, 0.5, periodic=True)[0]) / (2 * h)
+    assert abs(fd - gw[k].real) < 1e-5 * max(1.0, abs(fd))

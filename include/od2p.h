@@ -101,9 +101,12 @@ enum {
  * (d, e, s_r, s_c), each kept in d's coordinates -- (e, d, -s) is the same
  * region seen from e.  A rectangle must stay within (-img_h, 2 img_h) x
  * (-img_w, 2 img_w) (INVALID_ARG otherwise).  Step 0 reads u0 modulo the
- * image and od2p_merge / od2p_snr average every copy of a pixel.  Not built
- * for periodic plans (UNSUPPORTED): shards, and the image-space operators
- * ptycho_forward, overlap_add and stagm_loss_grad.
+ * image and od2p_merge / od2p_snr average every copy of a pixel.  The
+ * image-space operators (ptycho_forward, overlap_add, stagm_loss_grad) read
+ * whole-image windows from a plan-owned wrapped copy of (img_h + m - 1) x
+ * (img_w + m - 1) pixels and add their adjoints into the same grid, whose
+ * copies of each pixel are then summed onto the image in a fixed order.
+ * Shards of a periodic decomposition are not built (UNSUPPORTED).
  */
 typedef struct {
     int32_t img_h, img_w;           /* image size in pixels                                 */

@@ -1136,7 +1136,7 @@ int forward_m(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *
 {
     if (int rc = set_smem<M>(forward_kernel<M>)) return rc;
     const int blocks = (p->J + Radix<M>::FPB - 1) / Radix<M>::FPB;
-    forward_kernel<M><<<blocks, Radix<M>::NT, smem_bytes<M>(), s>>>(p->J, p->d_img_base, p->W, u, w,
+    forward_kernel<M><<<blocks, Radix<M>::NT, smem_bytes<M>(), s>>>(p->J, p->d_img_base, p->img_cols, u, w,
                                                                      out, p->d_tw);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
@@ -1162,7 +1162,7 @@ int loss_m(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, b
     if (int rc = set_smem<M>(loss_kernel<M>)) return rc;
     LossArgs a;
     a.J = p->J;
-    a.pitch = p->W;
+    a.pitch = p->img_cols;
     a.base = subdomain ? p->d_frame_base : p->d_img_base;
     a.pitch_arr = subdomain ? p->d_frame_pitch : nullptr;
     a.frame_sub = p->d_frame_sub;

@@ -1014,7 +1014,46 @@ int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w
                         cudaStream_t s)
 {
     image_gather_kernel<<<p->img_tiles.n_tiles, GATHER_THREADS, 0, s>>>(
-        p->M, p->H, p->W, p->img_tiles.tiles, p->img_tiles.ptr, p->img_tiles.list, q, w, out);
+        p->M, p->img_rows, p->img_cols, p->img_tiles.tiles, p->img_tiles.ptr, p->img_tiles.list, q, w, out);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+__global__ void wrap_pad_kernel(int H, int W, int Hp, int Wp, const float2 *__restrict__ u, float2 *__restrict__ up)
+{
+    const size_t n = (size_t)Hp * Wp;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int R = (int)(e / Wp), C = (int)(e % Wp);
+        up[e] = u[(size_t)(R < H ? R : R - H) * W + (C < W ? C : C - W)];
+    }
+}
+
+// each image pixel: its copies in the padded grid added in a fixed order
+__global__ void fold_kernel(int H, int W, int Hp, int Wp, const float2 *__restrict__ gp, float2 *__restrict__ out)
+{
+    const size_t n = (size_t)H * W;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int R = (int)(e / W), C = (int)(e % W);
+        float2 t = gp[(size_t)R * Wp + C];
+        if (C + W < Wp) t = cadd(t, gp[(size_t)R * Wp + C + W]);
+        if (R + H < Hp) {
+            t = cadd(t, gp[(size_t)(R + H) * Wp + C]);
+            if (C + W < Wp) t = cadd(t, gp[(size_t)(R + H) * Wp + C + W]);
+        }
+        out[e] = t;
+    }
+}
+
+int launch_wrap_pad(const ptycho_plan_s *p, const float2 *u, cudaStream_t s)
+{
+    wrap_pad_kernel<<<152 * 8, 256, 0, s>>>(p->H, p->W, p->img_rows, p->img_cols, u, p->d_upad);
+    OD2P_CUDA(cudaGetLastError());
+    return PTYCHO_OK;
+}
+
+int launch_fold(const ptycho_plan_s *p, float2 *out, cudaStream_t s)
+{
+    fold_kernel<<<152 * 8, 256, 0, s>>>(p->H, p->W, p->img_rows, p->img_cols, p->d_gpad, out);
     OD2P_CUDA(cudaGetLastError());
     return PTYCHO_OK;
 }
@@ -1031,7 +1070,7 @@ int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, c
     a.group_frames = G.frames;
     a.frame_base = grad_w ? p->d_img_base : p->d_frame_base;
     a.frame_pitch = grad_w ? nullptr : p->d_frame_pitch;
-    a.pitch = p->W;
+    a.pitch = p->img_cols;
     a.u = grad_w ? u_img : p->d_u[p->cur];
     a.h = h ? h : p->d_q;
     a.part = p->d_probe_part;

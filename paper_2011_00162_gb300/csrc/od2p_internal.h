@@ -179,6 +179,11 @@ struct ptycho_plan_s {
     int32_t blind = 0;
     bool has_mask = false;
     bool periodic = false;         // periodic boundaries: rectangles in extended coordinates
+    // whole-image windows (forward operator, loss, adjoint): the image itself
+    // (img_rows x img_cols = H x W), or for periodic plans a wrapped copy of
+    // (H + m - 1) x (W + m - 1) pixels in which no window wraps
+    int32_t img_rows = 0, img_cols = 0;
+    float2 *d_upad = nullptr, *d_gpad = nullptr;  // periodic: the wrapped image, the adjoint before folding
     // ---- host copies of the decomposition (offs: each frame's placed offset)
     std::vector<int32_t> offs, frame_sub, rect, pair, pair_rect, pair_shift;
     std::vector<int64_t> u_off, lam_off;
@@ -317,6 +322,11 @@ int launch_subdomain_update_table(bool blind, const SubArgs *tab, const int2 *it
                                   cudaStream_t s);
 int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w, float2 *out,
                         cudaStream_t s);
+// periodic plans: u (H x W) -> d_upad with u[(R mod H) (C mod W)] at (R, C);
+// d_gpad -> out (H x W), out(R, C) = the sum of d_gpad over (R + a H, C + b W),
+// (a, b) in {0, 1}^2 row-major, within img_rows x img_cols
+int launch_wrap_pad(const ptycho_plan_s *p, const float2 *u, cudaStream_t s);
+int launch_fold(const ptycho_plan_s *p, float2 *out, cudaStream_t s);
 int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, cudaStream_t s,
                         const float2 *h = nullptr);
 int launch_loss_reduce(ptycho_plan_s *p, float *loss, cudaStream_t s);

@@ -649,20 +649,34 @@ int ptycho_plan_periodic_layout(const ptycho_plan_t *plan, int32_t *pair_shift, 
     return PTYCHO_OK;
 }
 
-// the image-space operators read whole-image windows, which a periodic plan would wrap
-static int refuse_periodic(const ptycho_plan_t *plan, const char *what)
+// The image whose windows the image-space operators read: u itself, or for a
+// periodic plan its wrapped copy (no window wraps there).
+static const float2 *window_source(const ptycho_plan_t *plan, const float2 *u, cudaStream_t s, int *rc)
 {
-    return plan->periodic ? fail(PTYCHO_ERR_UNSUPPORTED, std::string(what) + " is not built for periodic plans")
-                          : PTYCHO_OK;
+    *rc = PTYCHO_OK;
+    if (!plan->periodic) return u;
+    *rc = launch_wrap_pad(plan, u, s);
+    return plan->d_upad;
+}
+
+// A^*-type sums of frames h into the image: straight into out, or for a periodic
+// plan into the padded grid and then folded onto the image.
+static int gather_image(const ptycho_plan_t *plan, const float2 *h, const float2 *w, float2 *out, cudaStream_t s)
+{
+    if (!plan->periodic) return launch_image_gather(plan, h, w, out, s);
+    if (int rc = launch_image_gather(plan, h, w, plan->d_gpad, s)) return rc;
+    return launch_fold(plan, out, s);
 }
 
 int ptycho_forward(const ptycho_plan_t *plan, const ptycho_c32 *u, const ptycho_c32 *w,
                    ptycho_c32 *frames_out, ptycho_stream_t stream)
 {
     if (!plan || !u || !w || !frames_out) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
-    if (int rc = refuse_periodic(plan, "ptycho_forward")) return rc;
-    return launch_forward(plan, reinterpret_cast<const float2 *>(u), reinterpret_cast<const float2 *>(w),
-                          reinterpret_cast<float2 *>(frames_out), reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int rc = PTYCHO_OK;
+    const float2 *src = window_source(plan, reinterpret_cast<const float2 *>(u), s, &rc);
+    if (rc) return rc;
+    return launch_forward(plan, src, reinterpret_cast<const float2 *>(w), reinterpret_cast<float2 *>(frames_out), s);
 }
 
 int stagm_prox(const ptycho_c32 *y, const float *f, ptycho_c32 *z, int64_t n, float eps, float lambda,
@@ -682,7 +696,6 @@ int overlap_add(ptycho_plan_t *plan, const ptycho_c32 *frames, const ptycho_c32 
 {
     if (!plan || !frames || !w || !image_out) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
     if (flags & ~PTYCHO_OA_IFFT) return fail(PTYCHO_ERR_INVALID_ARG, "unknown flag");
-    if (int rc = refuse_periodic(plan, "overlap_add")) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float2 *fr = reinterpret_cast<const float2 *>(frames);
     const float2 *wv = reinterpret_cast<const float2 *>(w);
@@ -690,7 +703,7 @@ int overlap_add(ptycho_plan_t *plan, const ptycho_c32 *frames, const ptycho_c32 
         if (int rc = launch_frames_ifft_weight(plan, fr, nullptr, true, plan->d_q, s)) return rc;
         fr = plan->d_q;
     }
-    return launch_image_gather(plan, fr, wv, reinterpret_cast<float2 *>(image_out), s);
+    return gather_image(plan, fr, wv, reinterpret_cast<float2 *>(image_out), s);
 }
 
 int od2p_init(ptycho_plan_t *plan, const ptycho_c32 *u0, const ptycho_c32 *w0, ptycho_stream_t stream)
@@ -1059,9 +1072,12 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u, const ptycho_c32 *
 {
     if (!plan || !u || !w || !loss) return fail(PTYCHO_ERR_INVALID_ARG, "NULL argument");
     if (recompute < 0 || recompute > 2) return fail(PTYCHO_ERR_INVALID_ARG, "recompute must be 0, 1 or 2");
-    if (int rc = refuse_periodic(plan, "stagm_loss_grad")) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const float2 *uu = reinterpret_cast<const float2 *>(u), *ww = reinterpret_cast<const float2 *>(w);
+    const float2 *ww = reinterpret_cast<const float2 *>(w);
+    int rc0 = PTYCHO_OK;
+    const float2 *uu = (recompute != 2 || grad_w) ? window_source(plan, reinterpret_cast<const float2 *>(u), s, &rc0)
+                                                  : reinterpret_cast<const float2 *>(u);
+    if (rc0) return rc0;
     const float2 *h = plan->d_q;
     if (recompute == 2) {  // the gradient frames stored by the last recompute = 0 call
         if (!plan->h_stored || plan->h_u != u || plan->h_w != w)
@@ -1087,7 +1103,7 @@ int stagm_loss_grad(ptycho_plan_t *plan, const ptycho_c32 *u, const ptycho_c32 *
         }
     }
     if (grad_u)
-        if (int rc = launch_image_gather(plan, h, ww, reinterpret_cast<float2 *>(grad_u), s)) return rc;
+        if (int rc = gather_image(plan, h, ww, reinterpret_cast<float2 *>(grad_u), s)) return rc;
     if (grad_w)
         if (int rc = launch_probe_reduce(plan, uu, reinterpret_cast<float2 *>(grad_w), s, h)) return rc;
     return PTYCHO_OK;
@@ -1427,6 +1443,8 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
     p->gamma = g->gamma;
     p->blind = g->blind ? 1 : 0;
     p->periodic = periodic;
+    p->img_rows = periodic ? p->H + m - 1 : p->H;
+    p->img_cols = periodic ? p->W + m - 1 : p->W;
     p->offs.resize(2 * (size_t)J);
     p->frame_sub.resize(J);
     p->global_j = sel;
@@ -1459,7 +1477,8 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
     if (p->u_len >= (1LL << 31) || p->lam_len >= (1LL << 31) || (int64_t)J * p->MM >= (1LL << 31))
         return bail(fail(PTYCHO_ERR_UNSUPPORTED, "subdomain, overlap or frame storage exceeds 2^31 elements"));
 
-    std::vector<int32_t> frame_base(J), frame_pitch(J), img_base(J), img_pitch(J, p->W);
+    // whole-image windows at the given offsets, in the image or its wrapped copy
+    std::vector<int32_t> frame_base(J), frame_pitch(J), img_base(J), img_pitch(J, p->img_cols), img_offs(2 * (size_t)J);
     std::vector<std::vector<int32_t>> sub_frames(p->D), all_frames(1);
     for (int j = 0; j < J; ++j) {
         const int d = p->frame_sub[j];
@@ -1467,7 +1486,9 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
         frame_pitch[j] = R[3] - R[1];
         frame_base[j] = (int32_t)(p->u_off[d] + (int64_t)(p->offs[2 * j] - R[0]) * frame_pitch[j] +
                                   (p->offs[2 * j + 1] - R[1]));
-        img_base[j] = p->offs[2 * j] * p->W + p->offs[2 * j + 1];
+        img_offs[2 * j] = all_offs[2 * sel[j]];
+        img_offs[2 * j + 1] = all_offs[2 * sel[j] + 1];
+        img_base[j] = img_offs[2 * j] * p->img_cols + img_offs[2 * j + 1];
         sub_frames[d].push_back(j);
         all_frames[0].push_back(j);
     }
@@ -1521,8 +1542,14 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
                                      R[1] + T.c0, tile_nbr_ptr[t], tile_nbr_ptr[t + 1] - tile_nbr_ptr[t],
                                      st.ptr[t], st.ptr[t + 1] - st.ptr[t], T.reg, R[2]});
     }
-    std::vector<int32_t> img_rect = {0, 0, p->H, p->W};
-    HostTiles it = make_tiles(1, img_rect, all_frames, p->offs, m);
+    std::vector<int32_t> img_rect = {0, 0, p->img_rows, p->img_cols};
+    HostTiles it = make_tiles(1, img_rect, all_frames, img_offs, m);
+    if (periodic) {
+        int rc0;
+        if ((rc0 = dev_alloc(&p->d_upad, (size_t)p->img_rows * p->img_cols, p->owned, s)) ||
+            (rc0 = dev_alloc(&p->d_gpad, (size_t)p->img_rows * p->img_cols, p->owned, s)))
+            return bail(rc0);
+    }
 
     auto &own = p->owned;
     const size_t JMM = (size_t)J * p->MM;

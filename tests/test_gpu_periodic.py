@@ -170,7 +170,7 @@ def test_periodic_equals_vacuum_when_nothing_wraps():
         p.close()
 
 
-def test_periodic_is_deterministic_and_refuses_image_space_operators():
+def test_periodic_is_deterministic_and_refuses_shards():
     H, m, step, jit, grid, ov = 96, 16, 6, 1, (3, 3), 8
     offs, u, w, f = _torus_case(H, m, step, jit, seed=14)
     states = []
@@ -178,15 +178,43 @@ def test_periodic_is_deterministic_and_refuses_image_space_operators():
         plan, _ref = _pair(H, m, offs, w, f, grid, ov, blind=True)
         od.od2p_iterate(plan, 4)
         states.append([od.od2p_get_state(plan, k).clone() for k in (od.STATE_U, od.STATE_LAMBDA, od.STATE_W)])
-        last = plan
+        plan.close()
     for a, b in zip(*states):
         assert torch.equal(a, b)
-    uu = torch.ones((H, H), dtype=torch.complex64, device=DEV)
-    ww = torch.from_numpy(np.asarray(w, np.complex64)).to(DEV)
-    with pytest.raises(od.PtychoError):
-        od.ptycho_forward(last, uu, ww)
-    with pytest.raises(od.PtychoError):
-        od.stagm_loss_grad(last, uu, ww)
     g = od.Geometry(H, H, m, offs, grid[0], grid[1], ov, 0.5, 0.3, 0.2, periodic=True)
     with pytest.raises((od.PtychoError, ValueError)):
         od.ptycho_plan_shard(g, np.zeros(9, np.int32), 0, torch.ones((len(offs), m, m), device=DEV))
+
+
+@pytest.mark.parametrize("m", [32, 64, 256])
+def test_periodic_image_space_operators_match_the_oracle(m):
+    """Forward operator, overlap-add (adjoint) and the ST-AGM loss with both
+    gradients on a periodic plan, windows wrapping around the image, against the
+    oracle's periodic operators; the gradient frames stored and reused give the
+    same gradients bit for bit."""
+    H, step = (4 * m, m // 2) if m < 256 else (512, 64)
+    offs, u, w, f = _torus_case(H, m, step, 2, seed=m + 3)
+    g = od.Geometry(H, H, m, offs, 2, 2, 8, 0.5, 0.3, 0.2, periodic=True)
+    plan = od.ptycho_plan(g, torch.from_numpy(np.asarray(f, np.float32)).to(DEV))
+    u32, w32 = u.astype(np.complex64), w.astype(np.complex64)
+    ud, wd = torch.from_numpy(u32).to(DEV), torch.from_numpy(w32).to(DEV)
+    out = {}
+    fr = od.ptycho_forward(plan, ud, wd).cpu().numpy()
+    out["forward"] = rel_l2(fr, oracle.forward(u32, w32, offs, periodic=True))
+    assert out["forward"] < TOL
+    rng = np.random.default_rng(m)
+    y = (rng.standard_normal(fr.shape) + 1j * rng.standard_normal(fr.shape)).astype(np.complex64)
+    img = od.overlap_add(plan, torch.from_numpy(y).to(DEV), wd, ifft=True).cpu().numpy()
+    out["adjoint"] = rel_l2(img, oracle.adjoint(y, w32, offs, H, H, periodic=True))
+    assert out["adjoint"] < TOL
+    loss, gu, gw = od.stagm_loss_grad(plan, ud, wd)
+    lo, guo, gwo = oracle.loss_grad(u32, w32, offs, np.asarray(f, np.float32), 0.5, periodic=True)
+    out["loss"] = abs(float(loss.item()) - lo) / lo
+    out["grad_u"] = rel_l2(gu.cpu().numpy(), guo)
+    out["grad_w"] = rel_l2(gw.cpu().numpy(), gwo)
+    assert out["loss"] < TOL and out["grad_u"] < TOL and out["grad_w"] < TOL, out
+    loss_s, _, _ = od.stagm_loss_grad(plan, ud, wd, grad_u=False, grad_w=False, recompute=od.STORE)
+    _, gu2, gw2 = od.stagm_loss_grad(plan, ud, wd, recompute=od.FROM_STORE)
+    assert torch.equal(gu2, gu) and torch.equal(gw2, gw) and float(loss_s.item()) == float(loss.item())
+    record(f"periodic_image_operators_m{m}", **out)
+    plan.close()

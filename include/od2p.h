@@ -106,7 +106,8 @@ enum {
  * whole-image windows from a plan-owned wrapped copy of (img_h + m - 1) x
  * (img_w + m - 1) pixels and add their adjoints into the same grid, whose
  * copies of each pixel are then summed onto the image in a fixed order.
- * Shards of a periodic decomposition are not built (UNSUPPORTED).
+ * Shards exchange the same messages, pair by pair (a pair with both ends on
+ * one rank, a subdomain's pair with itself included, sends nothing).
  */
 typedef struct {
     int32_t img_h, img_w;           /* image size in pixels                                 */

@@ -565,7 +565,6 @@ int ptycho_plan_shard(ptycho_plan_t **out, const ptycho_geometry *g, const int32
     if (!out) return fail(PTYCHO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (int rc = check_geometry(g)) return rc;
-    if (g->periodic) return fail(PTYCHO_ERR_UNSUPPORTED, "shards of a periodic decomposition are not built");
     if (!owner_host) return fail(PTYCHO_ERR_INVALID_ARG, "owner is NULL");
     const int D = g->sub_rows * g->sub_cols;
     bool mine = false;

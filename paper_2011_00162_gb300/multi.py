@@ -80,7 +80,9 @@ class HaloSchedule:
     """The strips one rank sends to and receives from each peer, in a fixed
     order both sides derive from the decomposition: for every ordered pair
     (e, d) in pair order with owner[e] = sender and owner[d] = receiver, the
-    strip u_e[Omega_e n Omega_d] (row-major) followed by Lambda_{e,d}; then,
+    strip of u_e on the pair's rectangle (Omega_e n Omega_d, in e's coordinates;
+    with periodic boundaries Omega_d moved by the pair's shift), row-major,
+    followed by Lambda_{e,d}; then,
     blind, W_e and Delta_e (m x m each) of every e the sender owns, e
     ascending.  Arrays are the concatenated layouts of the state (u by
     subdomain rectangles, Lambda by pair rectangles, W_d and Delta_d by d)."""

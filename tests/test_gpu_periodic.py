@@ -2,7 +2,8 @@
 (the torus reading of section 4's periodic boundary): the decomposition with
 its shifted pairs and self-pairs, one iteration from a scrambled state, a run
 from u = 1, Step 0 modulo the image, the merge, the SNR and the consensus
-residual; the reduction to the vacuum boundary; refusals."""
+residual; the image-space operators; the reduction to the vacuum boundary
+(shards of a periodic plan: tests/test_gpu_shard.py)."""
 import numpy as np
 import pytest
 import torch
@@ -170,7 +171,7 @@ def test_periodic_equals_vacuum_when_nothing_wraps():
         p.close()
 
 
-def test_periodic_is_deterministic_and_refuses_shards():
+def test_periodic_is_deterministic():
     H, m, step, jit, grid, ov = 96, 16, 6, 1, (3, 3), 8
     offs, u, w, f = _torus_case(H, m, step, jit, seed=14)
     states = []
@@ -181,9 +182,6 @@ def test_periodic_is_deterministic_and_refuses_shards():
         plan.close()
     for a, b in zip(*states):
         assert torch.equal(a, b)
-    g = od.Geometry(H, H, m, offs, grid[0], grid[1], ov, 0.5, 0.3, 0.2, periodic=True)
-    with pytest.raises((od.PtychoError, ValueError)):
-        od.ptycho_plan_shard(g, np.zeros(9, np.int32), 0, torch.ones((len(offs), m, m), device=DEV))
 
 
 @pytest.mark.parametrize("m", [32, 64, 256])

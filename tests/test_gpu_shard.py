@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2011_00162_gb300 as od
 from paper_2011_00162_gb300 import multi, synth
 from paper_2011_00162_gb300 import build as odbuild
@@ -25,19 +26,24 @@ def _built():
     odbuild.build()
 
 
-CASES = [("nonblind_m64_4x4", 384, 64, 16, 4, False), ("blind_m32_3x3", 160, 32, 8, 3, True),
-         ("blind_m256_2x2", 512, 256, 64, 2, True), ("nonblind_m48_3x2", 192, 48, 12, 3, False)]
+CASES = [("nonblind_m64_4x4", 384, 64, 16, 4, False, False), ("blind_m32_3x3", 160, 32, 8, 3, True, False),
+         ("blind_m256_2x2", 512, 256, 64, 2, True, False), ("nonblind_m48_3x2", 192, 48, 12, 3, False, False),
+         ("periodic_blind_m32_3x3", 160, 32, 8, 3, True, True), ("periodic_nonblind_m64_2x2", 256, 64, 16, 2, False, True)]
 
 
-@pytest.mark.parametrize("name,n,m,step,grid,blind", CASES)
+@pytest.mark.parametrize("name,n,m,step,grid,blind,periodic", CASES)
 @pytest.mark.parametrize("world", [2, 4])
-def test_shards_equal_whole_plan(name, n, m, step, grid, blind, world):
+def test_shards_equal_whole_plan(name, n, m, step, grid, blind, periodic, world):
     p = synth.Problem(name, n, m, step, 1, grid, grid - (1 if name.endswith("3x2") else 0), 8, 1e4, 1,
                       eta=2.0, r=0.5, blind=blind, mu=1.0 if blind else 0.0, gamma=0.1 if blind else 0.0, seed=41)
     offs, u_true, w, f = make_case(p)
+    if periodic:  # a raster over the whole torus: windows wrap around the image
+        offs = np.array([(r, c) for r in range(0, n, step) for c in range(0, n, step)], np.int32)
+        offs = ((offs + np.random.default_rng(4).integers(-1, 2, offs.shape)) % n).astype(np.int32)
+        f = np.abs(oracle.forward(u_true, w, offs, periodic=True)) ** 2
     w0 = synth.gaussian_probe(m) if blind else w
     g = od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, p.eta, p.r, mu=p.mu,
-                    gamma=p.gamma, blind=blind)
+                    gamma=p.gamma, blind=blind, periodic=periodic)
     fs, rect = od.ptycho_decompose(g)
     D = len(rect)
     if world > D:

@@ -29,31 +29,34 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _case(blind):
+def _case(blind, periodic=False):
     p = synth.Problem("shard", 96, 16, 6, 1, 3, 3, 8, 1e3, 1, eta=2.0, r=0.5, seed=17)
     offs = p.offsets()
+    if periodic:  # a raster over the whole torus: windows wrap around the image
+        offs = np.array([(r, c) for r in range(0, p.n, p.step) for c in range(0, p.n, p.step)], np.int32)
+        offs = ((offs + np.random.default_rng(3).integers(-1, 2, offs.shape)) % p.n).astype(np.int32)
     u, w = p.truth(), p.probe()
-    f = synth.poissonize(np.abs(oracle.forward(u, w, offs)) ** 2, p.peak, 5).astype(np.float64)
+    f = synth.poissonize(np.abs(oracle.forward(u, w, offs, periodic=periodic)) ** 2, p.peak, 5).astype(np.float64)
     w0 = synth.gaussian_probe(p.m) if blind else w
     return p, offs, f, w0
 
 
-def _admm(p, offs, f, w0, blind):
+def _admm(p, offs, f, w0, blind, periodic=False):
     return oracle.ADMM(f, w0, offs, p.n, p.n, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, p.eta, p.r,
-                       blind=blind, mu=1.0 if blind else 0.0, gamma=0.1 if blind else 0.0)
+                       blind=blind, mu=1.0 if blind else 0.0, gamma=0.1 if blind else 0.0, periodic=periodic)
 
 
 SEL = {"u": oracle.U, "lam": oracle.LAMBDA, "W": oracle.WD, "Delta": oracle.DELTA}
 
 
-def _worker(rank, world, port, blind, out):
+def _worker(rank, world, port, blind, periodic, out):
     torch.set_num_threads(1)
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), OMP_NUM_THREADS="1")
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    p, offs, f, w0 = _case(blind)
-    a = _admm(p, offs, f, w0, blind)
-    fs, rect = oracle.geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px)
-    pr, prc = oracle.pairs(rect)
+    p, offs, f, w0 = _case(blind, periodic)
+    a = _admm(p, offs, f, w0, blind, periodic)
+    fs, rect = oracle.geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, periodic=periodic)
+    pr, prc = oracle.pairs(rect, p.n, p.n, periodic=periodic)
     owner = multi.partition_subdomains(fs, len(rect), world)
     a.set_owned([1 if o == rank else 0 for o in owner])
     sched = multi.HaloSchedule(rect, pr, prc, owner, rank, p.m, blind)
@@ -75,18 +78,19 @@ def _worker(rank, world, port, blind, out):
     dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("periodic", [False, True])
 @pytest.mark.parametrize("blind", [False, True])
 @pytest.mark.parametrize("world", [2, 4])
-def test_sharded_oracle_equals_single_process(world, blind):
-    p, offs, f, w0 = _case(blind)
-    ref = _admm(p, offs, f, w0, blind)
+def test_sharded_oracle_equals_single_process(world, blind, periodic):
+    p, offs, f, w0 = _case(blind, periodic)
+    ref = _admm(p, offs, f, w0, blind, periodic)
     ref.iterate(N_IT)
-    fs, rect = oracle.geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px)
-    pr, prc = oracle.pairs(rect)
+    fs, rect = oracle.geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, periodic=periodic)
+    pr, prc = oracle.pairs(rect, p.n, p.n, periodic=periodic)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, blind, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, blind, periodic, q)) for r in range(world)]
     for pc in procs:
         pc.start()
     got = q.get(timeout=300)

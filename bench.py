@@ -223,15 +223,27 @@ def e2e_run(od, geom, f, w0, offs, p, dev, ws, tune=True, n_e2e=3):
     e2e_times = []
     out_host = torch.empty((p.n, p.n), dtype=torch.complex64).pin_memory()
     plan_s = None
-    for i in range(n_e2e + 1):
+    phases = {}
+    for i in range(n_e2e + 2):
+        # the last pass is not timed: it synchronises after every set-up phase to split them
+        split = i == n_e2e + 1
+
+        def mark(name):
+            if split:
+                torch.cuda.synchronize()
+                phases[name] = round(1e3 * (time.perf_counter() - t0), 3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         fd = f_pin.to(dev, non_blocking=True)
         wd = w_pin.to(dev, non_blocking=True)
+        mark("h2d")
         pl = od.ptycho_plan(geom, fd)
+        mark("plan")
         od.od2p_init(pl, wd)
+        mark("init")
         if tune:
             autotune.tune_plan(pl)  # measured in the untimed first pass, a cache hit afterwards
+        mark("tune")
         if i == 1:  # one extra synchronisation, to split the set-up from the iterations
             torch.cuda.synchronize()
             plan_s = time.perf_counter() - t0
@@ -242,14 +254,15 @@ def e2e_run(od, geom, f, w0, offs, p, dev, ws, tune=True, n_e2e=3):
         t1 = time.perf_counter()
         pl.close()
         del fd
-        if i > 0:
+        if 0 < i <= n_e2e:
             e2e_times.append(t1 - t0)
     value = len(offs) * p.n_iter * ws / statistics.median(e2e_times)
     return {"value": round(value, 1), "unit": UNIT,
             "h2d_bytes_per_step": int(f.nbytes + w0.nbytes),
             "d2h_bytes_per_step": int(out_host.numel() * 8),
             "step": f"one reconstruction: H2D f and w0, plan, init, {p.n_iter} iterations, merge, D2H image",
-            "setup_ms": round(1e3 * plan_s, 3) if plan_s is not None else None}
+            "setup_ms": round(1e3 * plan_s, 3) if plan_s is not None else None,
+            "setup_split_ms": {"cumulative, untimed pass": phases}}
 
 
 def batched_leg(od, dev, K: int = 10, W: int = 2, count: int = 64, tune=True, retune=False):

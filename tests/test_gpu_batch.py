@@ -197,3 +197,38 @@ def test_batch_with_m256_members_bitwise():
             for k, ko in ((od.STATE_U, oracle.U), (od.STATE_WD, oracle.WD), (od.STATE_W, oracle.W)):
                 assert rel_l2(od.od2p_get_state(batch.members[0], k).cpu().numpy(), ref.get(ko)) < 1e-5, k
         batch.close()
+
+
+def test_batch_with_periodic_members_bitwise():
+    """Periodic members (windows wrapping around their images, pairs across the
+    boundary) beside a vacuum member: each equals itself iterated alone."""
+    specs = [(32, 128, 8, False, True, 51), (64, 192, 16, True, True, 52), (32, 96, 8, True, False, 53)]
+    geoms, fs, w0s = [], [], []
+    for m, n, step, blind, periodic, seed in specs:
+        rng = np.random.default_rng(seed)
+        if periodic:
+            offs = np.array([(r, c) for r in range(0, n, step) for c in range(0, n, step)], np.int32)
+            offs = ((offs + rng.integers(-2, 3, offs.shape)) % n).astype(np.int32)
+        else:
+            offs = synth.raster_offsets(n, m, step, 1, seed=seed)
+        u = (0.5 + 0.5 * rng.random((n, n))) * np.exp(1j * rng.uniform(-1, 1, (n, n)))
+        w = synth.make_probe(m).astype(complex)
+        f = np.abs(oracle.forward(u, w, offs, periodic=periodic)) ** 2
+        geoms.append(od.Geometry(n, n, m, offs, 2, 2, 8, 0.5, 2.0, 0.5, mu=1.0 if blind else 0.0,
+                                 gamma=0.1 if blind else 0.0, blind=blind, periodic=periodic))
+        fs.append(torch.from_numpy(f.astype(np.float32)).to(DEV))
+        w0s.append(synth.gaussian_probe(m) if blind else w.astype(np.complex64))
+    batch = od.ptycho_batch_plan(geoms, fs)
+    for mb, w0 in zip(batch.members, w0s):
+        od.od2p_init(mb, torch.from_numpy(np.asarray(w0, np.complex64)).to(DEV))
+    batch.iterate(3)
+    for i, g in enumerate(geoms):
+        alone = od.ptycho_plan(g, fs[i])
+        od.od2p_init(alone, torch.from_numpy(np.asarray(w0s[i], np.complex64)).to(DEV))
+        if g.m == 64:  # the batch runs m = 64 members on the 16 x 4 split
+            od.ptycho_plan_set_fft(alone, 2)
+        od.od2p_iterate(alone, 3)
+        for k in (od.STATE_U, od.STATE_GAMMA, od.STATE_LAMBDA):
+            assert torch.equal(od.od2p_get_state(batch.members[i], k), od.od2p_get_state(alone, k)), (i, k)
+        alone.close()
+    batch.close()

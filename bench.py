@@ -592,13 +592,24 @@ def config2_leg(od, dev, args, K: int = 200, W: int = 5):
 
 
 # ----------------------------------------------------------------------------- all workloads
-def _gpu_problem_inputs(od, p, dev, seed: int = 7):
+def _torus_offsets(p, n=None):
+    """A raster over the whole torus of side n (default p.n) with p's step and
+    jitter, wrapped modulo the image: the scan of a periodic workload."""
+    n = p.n if n is None else n
+    offs = np.array([(r, c) for r in range(0, n, p.step) for c in range(0, n, p.step)], np.int32)
+    if p.jitter:
+        offs = offs + np.random.default_rng(p.seed + 1000).integers(-p.jitter, p.jitter + 1, offs.shape)
+    return (offs % n).astype(np.int32)
+
+
+def _gpu_problem_inputs(od, p, dev, seed: int = 7, periodic: bool = False):
     """Truth, probe, scan and intensities for problem p, the intensities made on
-    the GPU (the library's forward operator, torch.poisson at p.peak)."""
+    the GPU (the library's forward operator, torch.poisson at p.peak); periodic:
+    a scan over the whole torus and windows that wrap."""
     import torch
-    offs = p.offsets()
+    offs = _torus_offsets(p) if periodic else p.offsets()
     u_true, w = p.truth(), p.probe()
-    tmp = od.ptycho_plan(od.Geometry(p.n, p.n, p.m, offs),
+    tmp = od.ptycho_plan(od.Geometry(p.n, p.n, p.m, offs, periodic=periodic),
                          torch.ones((len(offs), p.m, p.m), dtype=torch.float32, device=dev))
     fr = od.ptycho_forward(tmp, torch.from_numpy(u_true).to(dev), torch.from_numpy(w).to(dev))
     tmp.close()
@@ -626,25 +637,32 @@ def _event_times(fn, K: int, flush):
     return [a.elapsed_time(b) / 1e3 for a, b in ev]
 
 
-def _oracle_sample(p, blind, params, budget_s, max_frames):
+def _oracle_sample(p, blind, params, budget_s, max_frames, periodic: bool = False):
     """Frame-updates/s of the FP64 oracle on the host cores, on a bounded sample of
     problem p: a square crop holding at most max_frames frames of the same probe,
-    step and subdomain grid, iterated until budget_s has passed (at least once)."""
+    step and subdomain grid (periodic: a smaller torus with the same step),
+    iterated until budget_s has passed (at least once)."""
     import dataclasses
 
     import oracle
     from paper_2011_00162_gb300 import synth
-    n = p.m + ((p.n - p.m) // p.step) * p.step
-    while n > 2 * p.m and len(synth.raster_offsets(n, p.m, p.step)) > max_frames:
-        n -= p.step
+    if periodic:
+        n = p.n
+        while n > 2 * p.m and (n // p.step) ** 2 > max_frames:
+            n -= p.step
+    else:
+        n = p.m + ((p.n - p.m) // p.step) * p.step
+        while n > 2 * p.m and len(synth.raster_offsets(n, p.m, p.step)) > max_frames:
+            n -= p.step
     grid = max(2, n // (2 * p.m)) if n >= 2 * p.m else 1
     q = dataclasses.replace(p, n=n, sub_rows=min(p.sub_rows, grid), sub_cols=min(p.sub_cols, grid))
-    offs = q.offsets()
+    offs = _torus_offsets(q) if periodic else q.offsets()
     u_true, w = q.truth(), q.probe()
-    f = synth.poissonize(np.abs(oracle.forward(u_true, w, offs)) ** 2, q.peak, 7)
+    f = synth.poissonize(np.abs(oracle.forward(u_true, w, offs, periodic=periodic)) ** 2, q.peak, 7)
     w0 = synth.gaussian_probe(q.m) if blind else w
     a = oracle.ADMM(f, w0, offs, q.n, q.n, q.sub_rows, q.sub_cols, q.overlap_px, q.eps, params["eta"],
-                    params["r"], blind=blind, mu=params.get("mu", 0.0), gamma=params.get("gamma", 0.0))
+                    params["r"], blind=blind, mu=params.get("mu", 0.0), gamma=params.get("gamma", 0.0),
+                    periodic=periodic)
     it = 0
     t0 = time.perf_counter()
     while True:
@@ -655,8 +673,8 @@ def _oracle_sample(p, blind, params, budget_s, max_frames):
             break
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": round(len(offs) * it / el, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{it} oracle iterations of a {q.n}^2 crop ({len(offs)} frames of {q.m}^2, "
-                      f"{q.sub_rows}x{q.sub_cols} subdomains), {el:.1f} s"}
+            "sample": f"{it} oracle iterations of a {q.n}^2 {'torus' if periodic else 'crop'} ({len(offs)} frames "
+                      f"of {q.m}^2, {q.sub_rows}x{q.sub_cols} subdomains), {el:.1f} s"}
 
 
 def run_configs(args):
@@ -681,14 +699,21 @@ def run_configs(args):
          {"eta": 2.0, "r": 0.5, "mu": 1.0, "gamma": 0.1}, 300),
         ("config5_od2bp_4096px_m256_6561frames_8x8sub_poisson1e5", synth.large_blind(), True,
          {"eta": 2.0, "r": 0.5, "mu": 1.0, "gamma": 0.1}, 30),
+        # a mixed-radix probe side (80 = 16 x 5) and a periodic scan (windows wrapping around a torus)
+        ("mixed_radix_od2p_480px_m80_441frames_3x3sub_poisson1e4",
+         synth.Problem("mr80", 480, 80, 20, 2, 3, 3, 16, 1e4, 1), False, {"eta": 2.0, "r": 0.5}, 1000),
+        ("periodic_od2bp_512px_m64_1024frames_torus_4x4sub_poisson1e4",
+         synth.Problem("per64", 512, 64, 16, 2, 4, 4, 16, 1e4, 1), True,
+         {"eta": 2.0, "r": 0.5, "mu": 1.0, "gamma": 0.1}, 1000, True),
     ]
-    for name, p, blind, prm, K in table:
+    for name, p, blind, prm, K, *periodic in table:
+        periodic = bool(periodic and periodic[0])
         if args.only and args.only not in name:
             continue
-        offs, u_true, w, f = _gpu_problem_inputs(od, p, dev)
+        offs, u_true, w, f = _gpu_problem_inputs(od, p, dev, periodic=periodic)
         J = len(offs)
         g = od.Geometry(p.n, p.n, p.m, offs, p.sub_rows, p.sub_cols, p.overlap_px, p.eps, prm["eta"], prm["r"],
-                        mu=prm.get("mu", 0.0), gamma=prm.get("gamma", 0.0), blind=blind)
+                        mu=prm.get("mu", 0.0), gamma=prm.get("gamma", 0.0), blind=blind, periodic=periodic)
         plan = od.ptycho_plan(g, f)
         w0 = torch.from_numpy(synth.gaussian_probe(p.m) if blind else w).to(dev)
         od.od2p_init(plan, w0)
@@ -698,7 +723,7 @@ def run_configs(args):
             od.od2p_iterate(plan, 1)
         t_it = _event_times(lambda: od.od2p_iterate(plan, 1), K, flush)
         t_k1 = _event_times(lambda: od.od2p_frame_update(plan), max(10, K // 10), flush)
-        line = {"workload": name, "frames": J, "image": p.n, "probe": p.m, "blind": blind,
+        line = {"workload": name, "frames": J, "image": p.n, "probe": p.m, "blind": blind, "periodic": periodic,
                 "subdomains": f"{p.sub_rows}x{p.sub_cols}", "iterations_timed": K,
                 "frame_updates_per_s": round(J * K / sum(t_it), 1),
                 "ms_per_iteration": round(1e3 * statistics.mean(t_it), 5),
@@ -735,7 +760,7 @@ def run_configs(args):
         torch.cuda.empty_cache()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = _oracle_sample(p, blind, prm, budget_s=args.cpu_budget,
-                                                  max_frames=200 if p.m >= 128 else 900)
+                                                  max_frames=200 if p.m >= 128 else 900, periodic=periodic)
         print(json.dumps(line), flush=True)
 
 

@@ -120,3 +120,41 @@ def test_periodic_decomposition_on_the_host_equals_the_oracle():
     # a 1 x 1 grid with a wide overlap reaches more than a period beyond the image
     with pytest.raises(od.PtychoError):
         od.ptycho_decompose(od.Geometry(32, 32, 16, offs % 32, 1, 1, 70, periodic=True))
+
+
+def test_decomposition_fuzz_against_the_oracle():
+    """Random geometries (image sides, probe sides up to the image, steps, jitter,
+    grids up to 5 x 5, overlaps), vacuum and periodic boundaries: the host
+    decomposition equals the oracle's bit for bit, and both refuse the same
+    inputs."""
+    import numpy as np
+
+    import oracle
+    import paper_2011_00162_gb300 as od
+    rng = np.random.default_rng(2024)
+    checked = 0
+    for _ in range(120):
+        m = int(rng.choice([16, 32, 48, 64]))
+        n = int(rng.integers(m, 4 * m + 1))
+        step = int(rng.integers(max(1, m // 8), m + 1))
+        rows, cols = int(rng.integers(1, 6)), int(rng.integers(1, 6))
+        ov = int(rng.integers(0, 2 * m))
+        periodic = bool(rng.integers(0, 2))
+        if periodic:
+            offs = np.array([(r, c) for r in range(0, n, step) for c in range(0, n, step)], np.int32)
+            offs = ((offs + rng.integers(-3, 4, offs.shape)) % n).astype(np.int32)
+        else:
+            lim = n - m
+            offs = np.array([(r, c) for r in range(0, lim + 1, step) for c in range(0, lim + 1, step)], np.int32)
+            offs = np.clip(offs + rng.integers(-3, 4, offs.shape), 0, lim).astype(np.int32)
+        g = od.Geometry(n, n, m, offs, rows, cols, ov, periodic=periodic)
+        try:
+            fo, ro = oracle.geometry(n, n, m, offs, rows, cols, ov, periodic=periodic)
+        except ValueError:
+            with pytest.raises(od.PtychoError):
+                od.ptycho_decompose(g)
+            continue
+        fs, rect = od.ptycho_decompose(g)
+        assert np.array_equal(fs, fo) and np.array_equal(rect, ro), (n, m, step, rows, cols, ov, periodic)
+        checked += 1
+    assert checked > 60

@@ -479,6 +479,13 @@ int ptycho_plan_get_launch(const ptycho_plan_t *plan, int32_t *variant, int32_t 
  * NULL.  Errors: INVALID_ARG (plan NULL).
  */
 int ptycho_plan_get_waves(const ptycho_plan_t *plan, int32_t *wave_frames, int32_t *chains, int32_t *launches);
+/* m = 256: frames per wave (1 .. 152) and chains of waves side by side (1 .. 8;
+ * at most one per wave) for launch variant 0 (default 19 frames, 4 chains).
+ * Every shape gives the same iterates bit for bit; the plan grows its
+ * intermediate (chains x wave_frames frames of 512 KB) and makes streams as
+ * needed.  Drops the captured graphs.  Errors: INVALID_ARG, UNSUPPORTED
+ * (m != 256), OOM.                                                            */
+int ptycho_plan_set_waves(ptycho_plan_t *plan, int32_t wave_frames, int32_t chains, ptycho_stream_t stream);
 
 /* Element count (complex) of a state selector (PTYCHO_STATE_*). */
 int od2p_state_len(const ptycho_plan_t *plan, int32_t which, int64_t *n_out);

@@ -86,6 +86,7 @@ SIGNATURES = {
     "ptycho_plan_set_launch": (ctypes.c_int, [_P, _I32, _I32, _P]),
     "ptycho_plan_get_launch": (ctypes.c_int, [_P, _P, _P, _P]),
     "ptycho_plan_get_waves": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ptycho_plan_set_waves": (ctypes.c_int, [_P, _I32, _I32, _P]),
     "ptycho_batch_set_launch": (ctypes.c_int, [_P, _I32, _I32, _P]),
     "ptycho_batch_get_launch": (ctypes.c_int, [_P, _P, _P]),
 }

@@ -23,7 +23,7 @@ __all__ = [
     "od2p_metrics", "od2p_state_len", "od2p_get_state", "od2p_set_state", "stagm_loss_grad", "PtychoError",
     "STATE_U", "STATE_GAMMA", "STATE_LAMBDA", "STATE_WD", "STATE_DELTA", "STATE_W", "STATE_Q",
     "Batch", "ptycho_batch_plan", "ptycho_batch_iterate", "ptycho_plan_set_launch", "ptycho_plan_get_launch",
-    "ptycho_plan_get_waves",
+    "ptycho_plan_get_waves", "ptycho_plan_set_waves",
     "ptycho_batch_set_launch", "ptycho_batch_get_launch", "LAUNCH_VARIANTS", "ptycho_probe_init",
     "ptycho_release_cached_memory", "od2p_set_penalties", "od2p_consensus_residual", "od2p_snr", "od2p_operator_norms", "ptycho_peak_probe",
            "od2p_iterate_until", "od2p_gamma_snapshot", "od2p_frame_residual", "ptycho_plan_set_fft",
@@ -390,6 +390,11 @@ def ptycho_plan_get_launch(plan: Plan) -> tuple[int, int, int]:
     v, b, mx = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     check(plan._lib.ptycho_plan_get_launch(plan.handle, ctypes.byref(v), ctypes.byref(b), ctypes.byref(mx)))
     return v.value, b.value, mx.value
+
+
+def ptycho_plan_set_waves(plan: Plan, wave_frames: int, chains: int, stream=None) -> None:
+    """m = 256: frames per wave and chains of waves side by side (same iterates for every shape)."""
+    check(plan._lib.ptycho_plan_set_waves(plan.handle, int(wave_frames), int(chains), _stream(stream)))
 
 
 def ptycho_plan_get_waves(plan: Plan) -> tuple[int, int, int]:

@@ -132,11 +132,17 @@ def _flush_buffer(device, flush_l2: bool):
     return torch.empty(64 << 20, dtype=torch.float32, device=device) if flush_l2 else None
 
 
+# m = 256, three passes: (frames per wave, chains side by side) tried by tune_plan
+WAVE_SHAPES = [(19, 4), (38, 2), (12, 8), (16, 6), (28, 4)]
+
+
 def _apply(plan: api.Plan, entry: dict) -> None:
     api.ptycho_plan_set_fft(plan, 0)
     api.ptycho_plan_set_launch(plan, int(entry["variant"]), int(entry["blocks_per_sm"]))
     if entry.get("fft", 0):
         api.ptycho_plan_set_fft(plan, int(entry["fft"]))
+    if entry.get("waves"):
+        api.ptycho_plan_set_waves(plan, int(entry["waves"][0]), int(entry["waves"][1]))
 
 
 def tune_plan(plan: api.Plan, n_iter: int = 15, warmup: int = 3, flush_l2: bool = False, use_cache: bool = True,
@@ -176,15 +182,29 @@ def tune_plan(plan: api.Plan, n_iter: int = 15, warmup: int = 3, flush_l2: bool 
     best_shape = min(shapes, key=shapes.get)
     v, b = (int(x) for x in best_shape.split(":"))
     api.ptycho_plan_set_launch(plan, v, b)
+    waves = None
+    if plan.geom.m == 256 and v == 0:  # the wave shape of the three passes
+        wtrials = {}
+        for wf, ch in WAVE_SHAPES:
+            api.ptycho_plan_set_waves(plan, wf, ch)
+            for _ in range(warmup):
+                api.od2p_iterate(plan, 1)
+            wtrials[f"waves{wf}x{ch}"] = _time_iterations(lambda: api.od2p_iterate(plan, 1), n_iter, flush)
+        trials.update(wtrials)
+        best_w = min(wtrials, key=wtrials.get)
+        waves = [int(x) for x in best_w[5:].split("x")]
+        api.ptycho_plan_set_waves(plan, *waves)
     for k in ((1, 2) if fft else ()):
         api.ptycho_plan_set_fft(plan, k)
         for _ in range(warmup):
             api.od2p_iterate(plan, 1)
         trials[f"fft{k}"] = _time_iterations(lambda: api.od2p_iterate(plan, 1), n_iter, flush)
     api.ptycho_plan_set_fft(plan, 0)
-    best = min(trials, key=trials.get)
+    best = min((k for k in trials if not k.startswith("waves")), key=trials.get)
+    if waves:
+        best = f"waves{waves[0]}x{waves[1]}"
     entry = {"variant": v, "blocks_per_sm": b, "fft": int(best[3:]) if best.startswith("fft") else 0,
-             "us": trials[best], "trials": trials}
+             "us": trials[best], "trials": trials, "waves": waves}
     _apply(plan, entry)
     for w, t in saved.items():
         api.od2p_set_state(plan, w, t)

@@ -605,7 +605,7 @@ struct Pipeline {
     PassC C;
 };
 
-// Waves go round-robin to up to WAVE_CHAINS_256 chains -- the caller's stream
+// Waves go round-robin to the plan's chains (t_waves) -- the caller's stream
 // and the plan's wave streams, each chain with its own T buffer -- so that the
 // blocks of one chain's pass fill the SMs that another chain's pass leaves idle
 // at its tail, and the DRAM-bound column pass of one wave runs beside the
@@ -615,11 +615,11 @@ int run_waves(const ptycho_plan_s *p, Pipeline P, int J, int waves_frames, cudaS
 {
     const int slabs = BM / SLAB;
     const int nch = std::max(1, std::min(p->t_waves, (J + waves_frames - 1) / waves_frames));
-    cudaStream_t st[WAVE_CHAINS_256];
-    float2 *T[WAVE_CHAINS_256];
+    cudaStream_t st[MAX_WAVE_CHAINS];
+    float2 *T[MAX_WAVE_CHAINS];
     for (int c = 0; c < nch; ++c) {
         st[c] = c ? p->wave_stream[c] : s;
-        T[c] = p->d_T + (size_t)c * WAVE_256 * BMM;
+        T[c] = p->d_T + (size_t)c * p->wave_frames * BMM;
     }
     if (nch > 1) {
         OD2P_CUDA(cudaEventRecord(p->wave_ev[0], s));
@@ -735,7 +735,7 @@ int frame_update_256(ptycho_plan_s *p, cudaStream_t s)
         P.C.frame_pitch = p->d_frame_pitch;
         P.C.slot_stride = (int32_t)p->u_len;
     }
-    return run_waves(p, P, p->J, WAVE_256, s);
+    return run_waves(p, P, p->J, p->wave_frames, s);
 }
 
 int forward_256(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2 *out, cudaStream_t s)
@@ -749,7 +749,7 @@ int forward_256(const ptycho_plan_s *p, const float2 *u, const float2 *w, float2
     P.A.w = w;
     P.B.mode = B_FWD_OUT;
     P.B.out = out;
-    return run_waves(p, P, p->J, WAVE_256, s);
+    return run_waves(p, P, p->J, p->wave_frames, s);
 }
 
 int ifft_256(const ptycho_plan_s *p, const float2 *in, float2 *out, cudaStream_t s)
@@ -761,7 +761,7 @@ int ifft_256(const ptycho_plan_s *p, const float2 *in, float2 *out, cudaStream_t
     P.B.in = in;
     P.C.out = out;
     P.C.scale = 1.f / (float)BM;
-    return run_waves(p, P, p->J, WAVE_256, s);
+    return run_waves(p, P, p->J, p->wave_frames, s);
 }
 
 int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s, float2 *h_out)
@@ -776,7 +776,7 @@ int loss_256(ptycho_plan_s *p, const float2 *u, const float2 *w, cudaStream_t s,
     P.B.part = p->d_loss_part;
     P.C.out = h_out ? h_out : p->d_q;
     P.C.scale = 1.f / (float)BM;
-    return run_waves(p, P, p->J, WAVE_256, s);
+    return run_waves(p, P, p->J, p->wave_frames, s);
 }
 
 int loss_256_sub(ptycho_plan_s *p, cudaStream_t s)
@@ -789,7 +789,7 @@ int loss_256_sub(ptycho_plan_s *p, cudaStream_t s)
     P.A.Wd = p->blind ? p->d_Wd : nullptr;
     P.B.mode = B_LOSS;
     P.B.part = p->d_loss_part;
-    return run_waves(p, P, p->J, WAVE_256, s);
+    return run_waves(p, P, p->J, p->wave_frames, s);
 }
 
 int probe_avg_256(ptycho_plan_s *p, cudaStream_t s)

@@ -29,7 +29,9 @@ constexpr int TILE_ROWS = TILE_H * TILE_W / GATHER_THREADS;
 constexpr int PROBE_CHUNK = OD2P_PROBE_CHUNK;
 // m = 256 frames go through their three FFT passes in waves of this many
 // frames (a 10 MB intermediate per wave that stays in L2), with up to
-// WAVE_CHAINS_256 waves in flight side by side.
+// WAVE_CHAINS_256 waves in flight side by side: the default shape of a plan,
+// which ptycho_plan_set_waves changes (up to MAX_WAVE_CHAINS chains of at most
+// MAX_WAVE_FRAMES frames).
 #ifndef OD2P_WAVE_256
 #define OD2P_WAVE_256 19
 #endif
@@ -38,6 +40,9 @@ constexpr int WAVE_256 = OD2P_WAVE_256;
 #define OD2P_WAVE_CHAINS_256 4
 #endif
 constexpr int WAVE_CHAINS_256 = OD2P_WAVE_CHAINS_256;
+constexpr int MAX_WAVE_CHAINS = 8, MAX_WAVE_FRAMES = 152;
+static_assert(WAVE_CHAINS_256 >= 1 && WAVE_CHAINS_256 <= MAX_WAVE_CHAINS && WAVE_256 >= 1 &&
+                  WAVE_256 <= MAX_WAVE_FRAMES, "default wave shape");
 // Periodic boundaries: rectangles inside (-H, 2H) x (-W, 2W) meet copies of each
 // other shifted by at most this many periods per axis.
 constexpr int PERIOD_SHIFTS = 2;
@@ -204,10 +209,12 @@ struct ptycho_plan_s {
     float *d_sqrtf = nullptr;      // J*MM
     float2 *d_gamma = nullptr;     // J*MM
     float2 *d_q = nullptr;         // J*MM frame residuals / scratch
-    float2 *d_T = nullptr;         // m = 256: t_waves x WAVE_256 frames of FFT intermediate
-    int32_t t_waves = 1;           // m = 256: chains of waves in flight (WAVE_CHAINS_256 at most)
-    cudaStream_t wave_stream[od2p::WAVE_CHAINS_256] = {};  // m = 256: streams of chains 1 ..
-    cudaEvent_t wave_ev[od2p::WAVE_CHAINS_256] = {};       // [0] fork, [c] join of chain c
+    float2 *d_T = nullptr;         // m = 256: t_waves x wave_frames frames of FFT intermediate
+    int64_t t_cap_frames = 0;      // m = 256: frames d_T holds
+    int32_t wave_frames = 0;       // m = 256: frames per wave
+    int32_t t_waves = 1;           // m = 256: chains of waves in flight
+    cudaStream_t wave_stream[od2p::MAX_WAVE_CHAINS] = {};  // m = 256: streams of chains 1 .. (made on demand)
+    cudaEvent_t wave_ev[od2p::MAX_WAVE_CHAINS] = {};       // [0] fork, [c] join of chain c
     // Nonblind gather slots: frame j's weighted residual at window pixel k goes to
     // d_slot[rank_j(k) * u_len + (index of that pixel in the u buffer)], where
     // rank_j(k) counts the frames of the subdomain with smaller index that cover
@@ -325,6 +332,9 @@ int launch_image_gather(const ptycho_plan_s *p, const float2 *q, const float2 *w
 // periodic plans: u (H x W) -> d_upad with u[(R mod H) (C mod W)] at (R, C);
 // d_gpad -> out (H x W), out(R, C) = the sum of d_gpad over (R + a H, C + b W),
 // (a, b) in {0, 1}^2 row-major, within img_rows x img_cols
+// m = 256: frames per wave and chains of waves side by side (chains capped by
+// the number of waves); grows the intermediate and makes streams as needed.
+int configure_waves(ptycho_plan_s *p, int wave_frames, int chains, cudaStream_t s);
 int launch_wrap_pad(const ptycho_plan_s *p, const float2 *u, cudaStream_t s);
 int launch_fold(const ptycho_plan_s *p, float2 *out, cudaStream_t s);
 int launch_probe_reduce(ptycho_plan_s *p, const float2 *u_img, float2 *grad_w, cudaStream_t s,

@@ -413,6 +413,28 @@ int apply_launch(ptycho_plan_s *p, int variant, int blocks_per_sm, cudaStream_t 
 
 namespace od2p {
 
+int configure_waves(ptycho_plan_s *p, int wave_frames, int chains, cudaStream_t s)
+{
+    const int nch = std::max(1, std::min(chains, (p->J + wave_frames - 1) / wave_frames));
+    const int64_t need = (int64_t)nch * wave_frames;
+    if (need > p->t_cap_frames) {  // a larger intermediate; the old one stays with the plan until it is freed
+        float2 *T = nullptr;
+        if (int rc = dev_alloc(&T, (size_t)need * p->MM, p->owned, s)) return rc;
+        p->d_T = T;
+        p->t_cap_frames = need;
+    }
+    for (int i = 0; i < nch; ++i) {
+        cudaError_t e = cudaSuccess;
+        if (i > 0 && !p->wave_stream[i]) e = cudaStreamCreateWithFlags(&p->wave_stream[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess && nch > 1 && !p->wave_ev[i]) e = cudaEventCreateWithFlags(&p->wave_ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "wave streams");
+    }
+    p->wave_frames = wave_frames;
+    p->t_waves = nch;
+    return PTYCHO_OK;
+}
+
+
 int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev, const int32_t *owner,
                int32_t rank, ptycho_stream_t stream);
 
@@ -997,9 +1019,21 @@ int ptycho_plan_get_waves(const ptycho_plan_t *plan, int32_t *wave_frames, int32
 {
     if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
     const bool waves = plan->M == 256 && plan->k1_variant == 0;
-    if (wave_frames) *wave_frames = waves ? WAVE_256 : 0;
+    if (wave_frames) *wave_frames = waves ? plan->wave_frames : 0;
     if (chains) *chains = waves ? plan->t_waves : 1;
-    if (launches) *launches = waves ? 3 * ((plan->J + WAVE_256 - 1) / WAVE_256) : 1;
+    if (launches) *launches = waves ? 3 * ((plan->J + plan->wave_frames - 1) / plan->wave_frames) : 1;
+    return PTYCHO_OK;
+}
+
+int ptycho_plan_set_waves(ptycho_plan_t *plan, int32_t wave_frames, int32_t chains, ptycho_stream_t stream)
+{
+    if (!plan) return fail(PTYCHO_ERR_INVALID_ARG, "plan is NULL");
+    if (plan->M != 256) return fail(PTYCHO_ERR_UNSUPPORTED, "wave shapes exist for m = 256 only");
+    if (wave_frames < 1 || wave_frames > MAX_WAVE_FRAMES || chains < 1 || chains > MAX_WAVE_CHAINS)
+        return fail(PTYCHO_ERR_INVALID_ARG, "need 1 <= wave_frames <= 152 and 1 <= chains <= 8");
+    if (int rc = configure_waves(plan, wave_frames, chains, reinterpret_cast<cudaStream_t>(stream))) return rc;
+    drop_graphs(plan->graph);
+    drop_graphs(plan->until);
     return PTYCHO_OK;
 }
 
@@ -1610,17 +1644,8 @@ int build_plan(ptycho_plan_t **out, const ptycho_geometry *g, const float *f_dev
         if ((rc = dev_alloc(&p->d_Wd, (size_t)p->D * p->MM, own, s)) || (rc = dev_alloc(&p->d_Delta, (size_t)p->D * p->MM, own, s)))
             return bail(rc);
     }
-    if (m == 256) {
-        // up to WAVE_CHAINS_256 chains of waves run side by side, one per wave
-        p->t_waves = std::max(1, std::min(WAVE_CHAINS_256, (J + WAVE_256 - 1) / WAVE_256));
-        if ((rc = dev_alloc(&p->d_T, (size_t)p->t_waves * WAVE_256 * p->MM, own, s))) return bail(rc);
-        cudaError_t e = cudaSuccess;
-        for (int i = 0; i < p->t_waves && e == cudaSuccess; ++i) {
-            if (i > 0) e = cudaStreamCreateWithFlags(&p->wave_stream[i], cudaStreamNonBlocking);
-            if (e == cudaSuccess && p->t_waves > 1) e = cudaEventCreateWithFlags(&p->wave_ev[i], cudaEventDisableTiming);
-        }
-        if (e != cudaSuccess) return bail(cuda_fail(e, "wave streams"));
-    }
+    if (m == 256)  // the default wave shape: chains of waves side by side, at most one per wave
+        if ((rc = configure_waves(p, WAVE_256, WAVE_CHAINS_256, s))) return bail(rc);
     if (!p->blind) {
         // gather slots: ranks and counts on the device (one pass over the tile
         // lists), then the slot array sized by the largest count

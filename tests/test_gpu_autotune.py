@@ -210,3 +210,40 @@ def test_tune_plan_times_the_transform_kinds_for_m64(tmp_path):
     assert hit["cached"] is True and od.ptycho_plan_get_fft(again) == entry["fft"]
     shapes_only = autotune.tune_plan(_plan(p), n_iter=2, warmup=1, path=path, fft=False)
     assert not any(k.startswith("fft") for k in shapes_only["trials"]) and shapes_only["fft"] == 0
+
+
+@pytest.mark.parametrize("blind", [False, True])
+def test_m256_wave_shapes_give_identical_iterates(tmp_path, blind):
+    """m = 256: every wave shape (frames per wave, chains side by side) gives the
+    same iterates bit for bit, reports its launches, and the tuner picks one of
+    its shapes and caches it."""
+    p = synth.Problem("w", 512, 256, 32, 2, 2, 2, 12, 1e5, 1, eta=2.0, r=0.5, seed=6)
+    ref = _plan(p, blind)
+    J = ref.n_frames
+    od.od2p_iterate(ref, 2)
+    want = _states(ref, blind)
+    for wf, ch in [(1, 1), (5, 3), (19, 4), (40, 8), (152, 2)]:
+        pl = _plan(p, blind)
+        od.ptycho_plan_set_waves(pl, wf, ch)
+        n_waves = -(-J // wf)
+        assert od.ptycho_plan_get_waves(pl) == (wf, min(ch, n_waves), 3 * n_waves)
+        od.od2p_iterate(pl, 2)
+        for k, t in _states(pl, blind).items():
+            assert torch.equal(t, want[k]), (wf, ch, k)
+        pl.close()
+    for bad in [(0, 1), (153, 1), (4, 0), (4, 9)]:
+        with pytest.raises(od.PtychoError) as e:
+            od.ptycho_plan_set_waves(ref, *bad)
+        assert e.value.code == 1  # PTYCHO_ERR_INVALID_ARG
+    small = _plan(synth.Problem("s", 64, 16, 8, 0, 1, 1, 0, None, 1))
+    with pytest.raises(od.PtychoError):
+        od.ptycho_plan_set_waves(small, 4, 2)
+    # the tuner times its wave shapes for the three passes and caches the choice
+    od.ptycho_plan_set_launch(ref, 0, 0)
+    entry = autotune.tune_plan(ref, n_iter=2, warmup=1, path=str(tmp_path / "w.json"))
+    if entry["variant"] == 0:
+        assert tuple(entry["waves"]) in autotune.WAVE_SHAPES
+        assert od.ptycho_plan_get_waves(ref)[:2] == (entry["waves"][0], min(entry["waves"][1], -(-J // entry["waves"][0])))
+        again = _plan(p, blind)
+        assert autotune.tune_plan(again, path=str(tmp_path / "w.json"))["cached"] is True
+        assert od.ptycho_plan_get_waves(again)[:2] == od.ptycho_plan_get_waves(ref)[:2]
